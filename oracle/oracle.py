@@ -1,0 +1,465 @@
+"""FP64 CPU oracle for "A Parareal Algorithm with Low-Rank Coarse Solvers"
+(Gander, Ohlberger, Rave; arXiv 2508.08873).
+
+TEST INFRASTRUCTURE ONLY.  Only tests, the smoke check and the CPU-baseline leg
+of the benchmark may import this module.  It shares no code with the CUDA
+library: the numerics live in oracle/orc.c (loaded through ctypes) and the
+method's steps are written out here in the paper's order and notation.
+
+Conventions (0-based in code, 1-based in the paper):
+  * interval i = 0..N-1 is the paper's interval n = i+1, [t_i, t_{i+1}];
+  * vectors are rows of C-contiguous arrays: a batch of vectors is (nvec, n);
+  * the fine solver F_i is M backward-Euler steps of u_t = -A u + f with the
+    separable source f(t, x) = sum_q c_q(t) g_q(x) sampled at the end of each
+    step; the coefficient array c has shape (N*M, Q), row J-1 holding the
+    values at the fine time t = J*dt, J = 1..N*M.
+
+Parity of each function is pinned by tests/test_oracle_*.py against closed
+forms, library routines and the paper's theorems.  Functions whose results are
+only checked through invariants say so in their docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def lib():
+    """Load (building on first use) the oracle's C primitives."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        d, i, u32, u64, L_ = (ctypes.c_double, ctypes.c_int, ctypes.c_uint32,
+                              ctypes.c_uint64, ctypes.c_long)
+        P = ctypes.c_void_p
+        L.orc_gauss.restype = d
+        L.orc_gauss.argtypes = [u64, u32, u32, u32, u32]
+        L.orc_gauss_block.argtypes = [u64, u32, u32, i, i, P]
+        L.orc_philox4x32_10.argtypes = [P, P, P]
+        L.orc_philox_rows.argtypes = [u64, u32, u32, u32, i, P]
+        L.orc_thomas.restype = i
+        L.orc_thomas.argtypes = [i, P, P, P, P, P, P]
+        L.orc_tridiag_propagate_many.restype = i
+        L.orc_tridiag_propagate_many.argtypes = [i, P, P, P, d, i, i, i, P, P, L_, i, P]
+        L.orc_stencil_propagate_many.restype = i
+        L.orc_stencil_propagate_many.argtypes = [i, i, P, P, P, P, P, d, i, i, i, P, P, L_, i, P]
+        L.orc_stencil_dense.restype = i
+        L.orc_stencil_dense.argtypes = [i, i, P, P, P, P, P, d, P]
+        L.orc_band_lu.restype = i
+        L.orc_band_lu.argtypes = [i, i, P]
+        L.orc_mgs2.restype = i
+        L.orc_mgs2.argtypes = [i, i, P, d, P, P]
+        L.orc_jacobi_svd.restype = i
+        L.orc_jacobi_svd.argtypes = [i, i, P, P, P, P]
+        L.orc_num_threads.restype = i
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    return lib().orc_num_threads()
+
+
+# ----------------------------------------------------------------------------
+# Operators (the semi-discretisation A of u_t = -A u + f is an input)
+# ----------------------------------------------------------------------------
+@dataclass
+class Tridiag:
+    """Tridiagonal A: row i is lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1]."""
+    lo: np.ndarray
+    di: np.ndarray
+    up: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return self.di.shape[0]
+
+    def dense(self) -> np.ndarray:
+        n = self.n
+        A = np.diag(self.di.astype(np.float64))
+        A[np.arange(1, n), np.arange(0, n - 1)] = self.lo[1:]
+        A[np.arange(0, n - 1), np.arange(1, n)] = self.up[:-1]
+        return A
+
+
+@dataclass
+class Stencil5:
+    """5-point A on an mx x my grid, node p = iy*mx + ix:
+    (A x)_p = C x_p + W x_{p-1} + E x_{p+1} + S x_{p-mx} + N x_{p+mx}."""
+    mx: int
+    my: int
+    C: np.ndarray
+    W: np.ndarray
+    E: np.ndarray
+    S: np.ndarray
+    N: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return self.mx * self.my
+
+    def dense_B(self, dt: float) -> np.ndarray:
+        """Dense I + dt*A (tiny grids only)."""
+        n = self.n
+        out = np.zeros((n, n))
+        rc = lib().orc_stencil_dense(self.mx, self.my, _p(_f64(self.C)), _p(_f64(self.W)),
+                                     _p(_f64(self.E)), _p(_f64(self.S)), _p(_f64(self.N)),
+                                     float(dt), _p(out))
+        assert rc == 0
+        return out
+
+
+# ----------------------------------------------------------------------------
+# Random sketch vectors (rSVD step 1; generator: Philox4x32-10 + Box-Muller)
+# ----------------------------------------------------------------------------
+STREAM_OMEGA = 0
+
+
+def gauss_block(seed: int, interval: int, n: int, ncol: int, stream: int = STREAM_OMEGA):
+    """(ncol, n) block of N(0,1) deviates omega_{interval, col}[row]."""
+    out = np.empty((ncol, n))
+    lib().orc_gauss_block(seed, stream, interval, n, ncol, _p(out))
+    return out
+
+
+def philox(ctr, key) -> np.ndarray:
+    c = np.asarray(ctr, dtype=np.uint32)
+    k = np.asarray(key, dtype=np.uint32)
+    out = np.zeros(4, dtype=np.uint32)
+    lib().orc_philox4x32_10(_p(c), _p(k), _p(out))
+    return out
+
+
+def philox_rows(seed: int, stream: int, interval: int, column: int, n: int) -> np.ndarray:
+    out = np.zeros((n, 4), dtype=np.uint32)
+    lib().orc_philox_rows(seed, stream, interval, column, n, _p(out))
+    return out
+
+
+# ----------------------------------------------------------------------------
+# Fine propagators F_i, F_i' and F_i'^* (Sec. 4 backward Euler; Eq. (F_n_affine))
+# ----------------------------------------------------------------------------
+def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
+              g: Optional[np.ndarray] = None, cvals: Optional[np.ndarray] = None) -> np.ndarray:
+    """Apply M backward-Euler steps to every row of X (nvec, n).
+
+    g: (Q, n) spatial source profiles or None (linear part F').
+    cvals: (M, Q) shared by all rows, or (nvec, M, Q) per row: c_q at the end
+    of each step.  adjoint=True applies F'^* (no source allowed)."""
+    X = np.array(X, dtype=np.float64, order="C", copy=True)
+    if X.ndim == 1:
+        return propagate(op, dt, M, X[None, :], adjoint, g, cvals)[0]
+    nvec, n = X.shape
+    if nvec == 0:
+        return X
+    Q = 0
+    gp = cp = None
+    cstride = 0
+    if g is not None:
+        assert not adjoint, "the adjoint acts on the linear part only"
+        g = _f64(np.atleast_2d(g))
+        Q = g.shape[0]
+        cvals = _f64(cvals)
+        if cvals.ndim == 2:
+            assert cvals.shape == (M, Q)
+        else:
+            assert cvals.shape == (nvec, M, Q)
+            cstride = M * Q
+        gp, cp = _p(g), _p(cvals)
+    L = lib()
+    if isinstance(op, Tridiag):
+        rc = L.orc_tridiag_propagate_many(n, _p(_f64(op.lo)), _p(_f64(op.di)), _p(_f64(op.up)),
+                                          float(dt), int(M), int(adjoint), Q, gp, cp, cstride,
+                                          nvec, _p(X))
+    else:
+        rc = L.orc_stencil_propagate_many(op.mx, op.my, _p(_f64(op.C)), _p(_f64(op.W)),
+                                          _p(_f64(op.E)), _p(_f64(op.S)), _p(_f64(op.N)),
+                                          float(dt), int(M), int(adjoint), Q, gp, cp, cstride,
+                                          nvec, _p(X))
+    if rc != 0:
+        raise RuntimeError("oracle propagation failed (zero pivot)")
+    return X
+
+
+def interval_cvals(c: Optional[np.ndarray], i: int, M: int) -> Optional[np.ndarray]:
+    """Source coefficients of interval i: rows i*M .. i*M+M-1 of c (N*M, Q)."""
+    if c is None:
+        return None
+    return c[i * M:(i + 1) * M]
+
+
+def fine_solve(op, dt, M, v, i, g=None, c=None) -> np.ndarray:
+    """F_i v: the full (affine) fine solver of interval i."""
+    if g is None:
+        return propagate(op, dt, M, v)
+    return propagate(op, dt, M, v, g=g, cvals=interval_cvals(c, i, M))
+
+
+def sequential_fine(op, dt, M, N, u0, g=None, c=None) -> np.ndarray:
+    """u_{n+1} = F_{n+1} u_n (Sec. 2 problem statement): (N+1, n)."""
+    u = np.zeros((N + 1, u0.shape[0]))
+    u[0] = u0
+    for i in range(N):
+        u[i + 1] = fine_solve(op, dt, M, u[i], i, g, c)
+    return u
+
+
+# ----------------------------------------------------------------------------
+# Randomized SVD (Sec. 2.1, steps 1-6)
+# ----------------------------------------------------------------------------
+MGS_TAU = 1e-13
+
+
+def mgs2(Y: np.ndarray, tau: float = MGS_TAU):
+    """Orthonormal basis of the span of the rows of Y (k, n): modified
+    Gram-Schmidt applied twice with deflation (a row whose norm drops below
+    tau times its original norm is discarded).  Returns (Q (r, n), keep)."""
+    Y = _f64(Y)
+    k, n = Y.shape
+    Q = np.zeros((max(k, 1), n))
+    keep = np.zeros(max(k, 1), dtype=np.int32)
+    r = lib().orc_mgs2(n, k, _p(Y), float(tau), _p(Q), _p(keep))
+    assert r >= 0
+    return Q[:r].copy(), keep[:k].astype(bool)
+
+
+def jacobi_svd(A: np.ndarray):
+    """SVD of a small dense matrix A (m, k) by one-sided Jacobi.  Returns
+    (U (m, r), s (r,), V (k, r)) with r = min(m, k), s descending."""
+    A = np.asarray(A, dtype=np.float64)
+    m, k = A.shape
+    if m < k:
+        V, s, U = jacobi_svd(A.T)
+        return U, s, V
+    Acm = np.asfortranarray(A)          # column-major m x k
+    U = np.zeros((k, m))                 # rows = columns of U
+    s = np.zeros(k)
+    V = np.zeros((k, k))
+    sweeps = lib().orc_jacobi_svd(m, k, Acm.ctypes.data_as(ctypes.c_void_p), _p(U), _p(s), _p(V))
+    if sweeps < 0:
+        raise RuntimeError("Jacobi SVD did not converge")
+    return U.T.copy(), s, V.T.copy()
+
+
+@dataclass
+class CoarseInterval:
+    """Factors of G_i' = U diag(S) V^T plus the data needed for the bounds."""
+    U: np.ndarray            # (n, R_i)  left singular vectors psi
+    S: np.ndarray            # (R_i,)    sigma_{i,1..R_i}
+    V: np.ndarray            # (n, R_i)  right singular vectors phi
+    sigma: np.ndarray        # all singular values of the small matrix (desc.)
+    rank_w: int              # dim of span{F' omega}   after deflation
+    rank_v: int              # dim of span{F'^* w}     after deflation
+    sigma_next: float        # sigma_{i, R_i + 1} estimate (0 if unavailable)
+    fine_evals: int          # forward + adjoint propagations spent
+
+
+def rsvd_interval(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval:
+    """Randomized SVD of F_i' in the steps of Sec. 2.1.
+
+    The lifting in step 5 uses the left singular vectors of the small matrix
+    with the basis w (image of F') and the right ones with the basis v
+    (image of F'^*): with M_{ij} = (F'^* w_i, v_j) = (w_i, F' v_j) one has
+    P_W F' = W M V^T, so the lifted SVD is (W Psi) Sigma (V Phi)^T.  (The
+    paper's text pairs them the other way round; this follows its own formula
+    for P_W F' in step 4.)"""
+    n = op.n
+    ell = R + p
+    omega = gauss_block(seed, i, n, ell)                         # step 1
+    Y = propagate(op, dt, M, omega)                              # F' omega
+    W, _ = mgs2(Y, tau)                                          # step 2
+    Z = propagate(op, dt, M, W, adjoint=True)                    # step 3
+    Vb, _ = mgs2(Z, tau)                                         # step 4
+    Mm = Z @ Vb.T                                                # step 5: M_ij = (F'^*w_i, v_j)
+    if Mm.size == 0:
+        return CoarseInterval(np.zeros((n, 0)), np.zeros(0), np.zeros((n, 0)), np.zeros(0),
+                              W.shape[0], Vb.shape[0], 0.0, ell + W.shape[0])
+    Psi, s, Phi = jacobi_svd(Mm)
+    Ri = min(R, s.shape[0])                                      # step 6
+    U = W.T @ Psi[:, :Ri]
+    V = Vb.T @ Phi[:, :Ri]
+    # sigma_{R+1} from the oversampled small SVD; when deflation left no
+    # (R+1)-th value, the directions dropped were below tau * sigma_1
+    sig_next = float(s[Ri]) if s.shape[0] > Ri else tau * float(s[0])
+    return CoarseInterval(U, s[:Ri].copy(), V, s, W.shape[0], Vb.shape[0], sig_next,
+                          ell + W.shape[0])
+
+
+@dataclass
+class Coarse:
+    intervals: List[CoarseInterval]
+    R: int
+    p: int
+
+    @property
+    def delta(self) -> float:
+        """delta := max_n sigma_{n,1} (Eq. (bounds_delta_eps))."""
+        return max((float(c.sigma[0]) if c.sigma.size else 0.0) for c in self.intervals)
+
+    @property
+    def eps(self) -> float:
+        """eps := max_n sigma_{n,R_n+1} (Eq. (bounds_delta_eps)), estimated
+        from the oversampled small SVD as in Sec. 4.5."""
+        return max(c.sigma_next for c in self.intervals)
+
+    def apply_lin(self, i: int, v: np.ndarray) -> np.ndarray:
+        """G_i' v = sum_r psi_r sigma_r (phi_r, v) (Eq. (spectral_G) without b)."""
+        c = self.intervals[i]
+        return c.U @ (c.S * (c.V.T @ v))
+
+
+def build_coarse(op, dt, M, N, R, p, seed) -> Coarse:
+    """Coarse solvers of all N intervals (each an independent rSVD)."""
+    return Coarse([rsvd_interval(op, dt, M, i, R, p, seed) for i in range(N)], R, p)
+
+
+def exact_coarse(op, dt, M, N, R) -> Coarse:
+    """Truncated SVD of the dense F' (small n only): the exact G_n of
+    Eq. (spectral_G), used by tests as a comparison coarse solver."""
+    n = op.n
+    Fp = propagate(op, dt, M, np.eye(n)).T           # column j = F' e_j
+    Uf, s, Vt = np.linalg.svd(Fp)
+    ci = CoarseInterval(Uf[:, :R].copy(), s[:R].copy(), Vt[:R].T.copy(), s.copy(), n, n,
+                        float(s[R]) if R < n else 0.0, 0)
+    return Coarse([ci] * N, R, 0)
+
+
+# ----------------------------------------------------------------------------
+# Parareal (Eq. (def_Parareal)) with the a posteriori bound (Eq. (apost_bound))
+# ----------------------------------------------------------------------------
+@dataclass
+class PararealResult:
+    iterates: List[np.ndarray]           # u^k, each (N+1, n), k = 0..k_done
+    bounds: List[np.ndarray]             # a posteriori bound per k>=1, (N+1,), entry 0 = 0
+    b: np.ndarray                        # affine parts b_i = F_i 0, (N, n)
+    k_done: int
+    fine_evals: int                      # fine evaluations per interval (Eq. (num_F_eval))
+
+
+def apost_bound(delta: float, eps: float, du: np.ndarray) -> np.ndarray:
+    """eps * sum_{m=1}^{n-1} delta^{n-m-1} ||u^k_m - u^{k-1}_m||  for n = 0..N
+    (Eq. (apost_bound)); du[m] = ||u^k_m - u^{k-1}_m||, m = 0..N."""
+    Np1 = du.shape[0]
+    out = np.zeros(Np1)
+    for n in range(1, Np1):
+        out[n] = eps * sum(delta ** (n - m - 1) * du[m] for m in range(1, n))
+    return out
+
+
+def parareal(op, dt, M, N, coarse: Coarse, u0, g=None, c=None, K: Optional[int] = None,
+             tol: Optional[float] = None) -> PararealResult:
+    """Parareal with G_i v = G_i' v + b_i, literal form of Eq. (def_Parareal):
+
+      u^0_0 = u0,  u^0_{i+1} = G_i u^0_i;
+      u^{k+1}_0 = u0,  u^{k+1}_{i+1} = F_i u^k_i + G_i u^{k+1}_i - G_i u^k_i.
+
+    Stops after K iterations (clamped to N, where the iterates equal the fine
+    solution), or earlier at the first k >= 1 with
+    max_n bound_n^k <= tol * max_n ||u^k_n|| when tol is given."""
+    u0 = _f64(u0)
+    n = u0.shape[0]
+    Kmax = N if K is None else min(int(K), N)
+    # affine parts b_i = F_i 0 (Eq. (F_n_affine)); one fine evaluation each
+    if g is None:
+        b = np.zeros((N, n))
+    else:
+        b = np.stack([fine_solve(op, dt, M, np.zeros(n), i, g, c) for i in range(N)])
+    evals = 1
+
+    def G(i, v):
+        return coarse.apply_lin(i, v) + b[i]
+
+    u = np.zeros((N + 1, n))
+    u[0] = u0
+    for i in range(N):
+        u[i + 1] = G(i, u[i])
+    iterates = [u]
+    bounds = []
+    delta, eps = coarse.delta, coarse.eps
+    k = 0
+    while k < Kmax:
+        prev = iterates[-1]
+        Fprev = np.stack([fine_solve(op, dt, M, prev[i], i, g, c) for i in range(N)])
+        evals += 1
+        new = np.zeros_like(prev)
+        new[0] = u0
+        for i in range(N):
+            new[i + 1] = Fprev[i] + G(i, new[i]) - G(i, prev[i])
+        k += 1
+        iterates.append(new)
+        du = np.linalg.norm(new - prev, axis=1)
+        bounds.append(apost_bound(delta, eps, du))
+        if tol is not None and tol > 0:
+            scale = np.max(np.linalg.norm(new, axis=1))
+            if np.max(bounds[-1]) <= tol * scale:
+                break
+    return PararealResult(iterates, bounds, b, k, evals)
+
+
+# ----------------------------------------------------------------------------
+# A priori bounds (Theorem 1)
+# ----------------------------------------------------------------------------
+def apriori_initial(delta: float, eps: float, bnorm: np.ndarray) -> np.ndarray:
+    """Eq. (error_bound_initial): bound on ||e^0_n||, n = 0..N, where
+    bnorm[m] = ||b_m|| with b_0 := u0 and b_m the affine part of the paper's
+    F_m (m = 1..N-1)."""
+    N = bnorm.shape[0]
+    out = np.zeros(N + 1)
+    for n in range(1, N + 1):
+        out[n] = sum(min(2 * delta, (n - m) * eps) * delta ** (n - m - 1) * bnorm[m]
+                     for m in range(0, n))
+    return out
+
+
+def apriori_k(delta: float, eps: float, bnorm: np.ndarray, k: int) -> np.ndarray:
+    """Eq. (error_bound_eps_delta2): 2 eps^k sum_{m=0}^{n-k-1} C(n-m, k)
+    delta^{n-m-k} ||b_m||, n = 0..N (k >= 1)."""
+    N = bnorm.shape[0]
+    out = np.zeros(N + 1)
+    for n in range(1, N + 1):
+        out[n] = 2 * eps ** k * sum(math.comb(n - m, k) * delta ** (n - m - k) * bnorm[m]
+                                    for m in range(0, n - k))
+    return out
+
+
+def apriori_from_e0(delta: float, eps: float, e0: np.ndarray, k: int) -> np.ndarray:
+    """Eq. (error_bound_eps_delta): eps^k sum_{m=1}^{n-k} C(n-m, k-1)
+    delta^{n-m-k} ||e^0_m||, n = 0..N; e0[m] = ||e^0_m||."""
+    Np1 = e0.shape[0]
+    out = np.zeros(Np1)
+    for n in range(1, Np1):
+        out[n] = eps ** k * sum(math.comb(n - m, k - 1) * delta ** (n - m - k) * e0[m]
+                                for m in range(1, n - k + 1))
+    return out
+
+
+def efficiency(err_max: float, bound: np.ndarray) -> float:
+    """eta^k of Eq. (def_efficiency) with the bound maximised over 1 <= n <= N
+    (the paper's n < N reads as a typo for n <= N; both are stated)."""
+    b = float(np.max(bound[1:])) if bound.shape[0] > 1 else 0.0
+    return err_max / b if b > 0 else math.inf
+
+
+def rel_err(iterate: np.ndarray, ref: np.ndarray) -> float:
+    """max_n ||u^k_n - u_n|| / max_n ||u_n|| (the paper's max-over-time l2 error,
+    normalised)."""
+    return float(np.max(np.linalg.norm(iterate - ref, axis=1)) /
+                 np.max(np.linalg.norm(ref, axis=1)))

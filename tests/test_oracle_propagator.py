@@ -1,0 +1,155 @@
+"""Oracle: tridiagonal / banded direct solves and the backward-Euler fine
+propagators F, F' and F'^* (Sec. 4: backward Euler; Eq. (F_n_affine)).
+
+Pins: dense library solves, the closed-form DST spectrum of the 1D heat
+operator, the closed-form geometric sum for a constant source, the adjoint
+identity (F'^* w, v) = (w, F' v) (Sec. 2.1 step 3), and interval bookkeeping.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_08873_gb300 import workloads as W
+
+
+def _rand_tridiag(rng, n):
+    lo = rng.uniform(-1, 0, n)
+    up = rng.uniform(-1, 0, n)
+    di = 2.5 + rng.uniform(0, 1, n)
+    return lo, di, up
+
+
+@pytest.mark.parametrize("n", [1, 2, 3, 17, 64])
+def test_thomas_matches_dense_solve(orc, n):
+    rng = np.random.default_rng(n)
+    op = orc.Tridiag(*_rand_tridiag(rng, n))
+    d = rng.standard_normal(n)
+    x = np.zeros(n)
+    work = np.zeros(n)
+    rc = orc.lib().orc_thomas(n, orc._p(op.lo), orc._p(op.di), orc._p(op.up), orc._p(d),
+                              orc._p(x), orc._p(work))
+    assert rc == 0
+    np.testing.assert_allclose(x, np.linalg.solve(op.dense(), d), rtol=1e-13, atol=1e-14)
+
+
+def _heat_modes(n, dt, M):
+    h = 1.0 / (n + 1)
+    j = np.arange(1, n + 1)
+    lam = 4.0 / h ** 2 * np.sin(j * np.pi * h / 2) ** 2
+    sig = (1.0 + dt * lam) ** (-M)
+    x = np.arange(1, n + 1) * h
+    V = np.sqrt(2 * h) * np.sin(np.pi * np.outer(j, x))      # rows: orthonormal DST-I modes
+    return sig, V
+
+
+def test_heat_propagator_on_dst_modes(orc):
+    """F' v_j = (1 + dt lam_j)^(-M) v_j for the DST-I eigenvectors."""
+    P = W.heat1d()
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    sig, V = _heat_modes(P.n, P.dt, P.M)
+    for j in (0, 1, 4, 50, 254):
+        out = orc.propagate(op, P.dt, P.M, V[j])
+        # cond(I + dt A) ~ 260: rounding of 64 solves stays near 1e-12 relative
+        np.testing.assert_allclose(out, sig[j] * V[j], rtol=0, atol=1e-12 * sig[0] * np.abs(V[j]).max())
+
+
+def test_heat_dense_singular_values_closed_form(orc):
+    """Singular values of the dense F' (255 propagations) = (1+dt lam_j)^-M."""
+    P = W.heat1d()
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    Fp = orc.propagate(op, P.dt, P.M, np.eye(P.n)).T
+    s = np.linalg.svd(Fp, compute_uv=False)
+    sig, _ = _heat_modes(P.n, P.dt, P.M)
+    ref = np.sort(sig)[::-1]
+    # 64 solves with cond ~260 and a dense SVD: ~1e-13 sigma_1 absolute
+    np.testing.assert_allclose(s[:4], ref[:4], rtol=1e-12)
+    assert np.max(np.abs(s - ref)) < 1e-12 * ref[0]
+    # the survey values for sigma_1..sigma_3 (configuration of Experiment 1's FD analogue)
+    np.testing.assert_allclose(s[:3], [5.4124e-1, 8.8841e-2, 4.8763e-3], rtol=1e-4)
+
+
+@pytest.mark.parametrize("maker", ["adr", "heat"])
+def test_adjoint_is_transpose(orc, maker):
+    n, dt, M = 23, 1e-3, 7
+    lo, di, up = W.adr1d_op(n) if maker == "adr" else W.heat1d_op(n)
+    op = orc.Tridiag(lo, di, up)
+    Fp = orc.propagate(op, dt, M, np.eye(n)).T
+    Fa = orc.propagate(op, dt, M, np.eye(n), adjoint=True).T
+    np.testing.assert_allclose(Fa, Fp.T, rtol=1e-13, atol=1e-16)
+    B = np.eye(n) + dt * op.dense()
+    np.testing.assert_allclose(Fp, np.linalg.matrix_power(np.linalg.inv(B), M),
+                               rtol=1e-11, atol=1e-15)
+    rng = np.random.default_rng(1)
+    v, w = rng.standard_normal(n), rng.standard_normal(n)
+    lhs = orc.propagate(op, dt, M, w, adjoint=True) @ v
+    rhs = w @ orc.propagate(op, dt, M, v)
+    assert abs(lhs - rhs) <= 1e-13 * abs(rhs) + 1e-15
+
+
+def test_constant_source_closed_form(orc):
+    """With c_q(t) = 1: F 0 = sum_{j=1}^M dt B^{-j} g = (I - B^{-M}) A^{-1} g."""
+    n, dt, M = 31, 2e-3, 9
+    lo, di, up = W.adr1d_op(n, nu=0.05)
+    op = orc.Tridiag(lo, di, up)
+    A = op.dense()
+    B = np.eye(n) + dt * A
+    g = np.exp(-((np.arange(1, n + 1) / (n + 1) - 0.4) / 0.2) ** 2)
+    out = orc.propagate(op, dt, M, np.zeros(n), g=g[None], cvals=np.ones((M, 1)))
+    expect = (np.eye(n) - np.linalg.matrix_power(np.linalg.inv(B), M)) @ np.linalg.solve(A, g)
+    np.testing.assert_allclose(out, expect, rtol=1e-12, atol=1e-15)
+
+
+def test_affine_split_and_interval_bookkeeping(orc):
+    """F v = F' v + F 0 (Eq. (F_n_affine)); two intervals of M steps equal one
+    propagation of 2M steps with the concatenated source samples."""
+    P = W.heat1d(n=63, N=4, M=16)
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    v = P.u0
+    full = orc.fine_solve(op, P.dt, P.M, v, 1, P.g, P.c)
+    lin = orc.propagate(op, P.dt, P.M, v)
+    aff = orc.fine_solve(op, P.dt, P.M, np.zeros(P.n), 1, P.g, P.c)
+    np.testing.assert_allclose(full, lin + aff, rtol=1e-13, atol=1e-15)
+    two = orc.fine_solve(op, P.dt, P.M, orc.fine_solve(op, P.dt, P.M, v, 1, P.g, P.c), 2, P.g, P.c)
+    one = orc.propagate(op, P.dt, 2 * P.M, v, g=P.g, cvals=P.c[P.M:3 * P.M])
+    np.testing.assert_allclose(two, one, rtol=1e-14, atol=1e-16)
+    seq = orc.sequential_fine(op, P.dt, P.M, P.N, v, P.g, P.c)
+    direct = orc.propagate(op, P.dt, P.N * P.M, v, g=P.g, cvals=P.c)
+    np.testing.assert_allclose(seq[-1], direct, rtol=1e-13, atol=1e-16)
+
+
+@pytest.mark.parametrize("kind", ["diff", "adv"])
+def test_band_solve_matches_dense(orc, kind):
+    m = 6
+    if kind == "diff":
+        st = W.diff2d_op(m, 10 ** np.random.default_rng(0).uniform(0, 2, (8, 8)))
+    else:
+        st = W.adv2d_op(m, 0.01)
+    op = orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"])
+    dt, M = 1e-3, 3
+    B = op.dense_B(dt)
+    Fp = orc.propagate(op, dt, M, np.eye(m * m)).T
+    np.testing.assert_allclose(Fp, np.linalg.matrix_power(np.linalg.inv(B), M), rtol=1e-11,
+                               atol=1e-15)
+    Fa = orc.propagate(op, dt, M, np.eye(m * m), adjoint=True).T
+    np.testing.assert_allclose(Fa, Fp.T, rtol=1e-12, atol=1e-15)
+    if kind == "diff":
+        np.testing.assert_allclose(B, B.T, rtol=0, atol=1e-12 * np.abs(B).max())
+    # stencil rows against the operator definition on an interior node
+    A = (B - np.eye(m * m)) / dt
+    p = 2 * m + 3
+    assert np.isclose(A[p, p], st["C"][p]) and np.isclose(A[p, p - 1], st["W"][p])
+    assert np.isclose(A[p, p + m], st["N"][p]) and np.isclose(A[p, p - m], st["S"][p])
+
+
+def test_diff2d_constant_kappa_modes(orc):
+    """Constant kappa: sin(kx pi x) sin(ky pi y) are eigenvectors of F' with
+    eigenvalue (1 + dt (kappa 4/h^2 (sin^2(kx pi h/2) + sin^2(ky pi h/2)) + c))^-M."""
+    m, dt, M, kappa = 15, 1e-3, 5, 3.0
+    st = W.diff2d_op(m, np.full((8, 8), kappa), react=1.0)
+    op = orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"])
+    h = 1.0 / (m + 1)
+    x = np.arange(1, m + 1) * h
+    for kx, ky in ((1, 1), (2, 5), (15, 3)):
+        v = np.outer(np.sin(ky * np.pi * x), np.sin(kx * np.pi * x)).ravel()
+        lam = kappa * 4 / h ** 2 * (np.sin(kx * np.pi * h / 2) ** 2 + np.sin(ky * np.pi * h / 2) ** 2) + 1.0
+        out = orc.propagate(op, dt, M, v)
+        np.testing.assert_allclose(out, (1 + dt * lam) ** (-M) * v, rtol=0, atol=1e-13 * np.abs(v).max())

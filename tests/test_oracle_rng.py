@@ -1,0 +1,60 @@
+"""Oracle: Philox4x32-10 counter-based generator and Box-Muller normals.
+
+The paper draws i.i.d. Gaussian sketch vectors (Sec. 2.1, rSVD step 1) but fixes
+no generator.  The exact bit pattern is pinned by bitwise agreement with the
+CUDA side (tests/test_gpu_*.py); here the properties the method needs are
+pinned: determinism, counter/key sensitivity, and standard-normal statistics.
+"""
+import numpy as np
+import pytest
+from scipy import stats
+
+
+def test_philox_deterministic_and_counter_sensitive(orc):
+    a = orc.philox([1, 2, 3, 4], [5, 6])
+    assert np.array_equal(a, orc.philox([1, 2, 3, 4], [5, 6]))
+    outs = {tuple(a)}
+    for pos in range(4):
+        c = [1, 2, 3, 4]
+        c[pos] += 1
+        outs.add(tuple(orc.philox(c, [5, 6])))
+    for pos in range(2):
+        k = [5, 6]
+        k[pos] += 1
+        outs.add(tuple(orc.philox([1, 2, 3, 4], k)))
+    assert len(outs) == 7
+
+
+def test_philox_bits_uniform(orc):
+    w = orc.philox_rows(7, 0, 3, 2, 40000).ravel()
+    # each of the 32 bit positions is set about half the time
+    bits = ((w[:, None] >> np.arange(32, dtype=np.uint32)) & 1).mean(axis=0)
+    assert np.all(np.abs(bits - 0.5) < 5 * 0.5 / np.sqrt(w.size))
+    # bytes uniform (chi-square)
+    by = w.view(np.uint8)
+    hist = np.bincount(by, minlength=256)
+    chi = stats.chisquare(hist)
+    assert chi.pvalue > 1e-4
+
+
+def test_gauss_is_standard_normal(orc):
+    z = np.concatenate([orc.gauss_block(0, i, 5000, 8).ravel() for i in range(5)])
+    n = z.size
+    assert abs(z.mean()) < 5 / np.sqrt(n)
+    assert abs(z.var() - 1) < 5 * np.sqrt(2 / n)
+    assert abs(stats.kurtosis(z, fisher=False) - 3) < 5 * np.sqrt(24 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-4
+    # independence across columns / intervals: sample correlation ~ 0
+    A = orc.gauss_block(0, 0, 20000, 4)
+    C = np.corrcoef(A)
+    assert np.max(np.abs(C - np.eye(4))) < 5 / np.sqrt(20000)
+
+
+def test_gauss_block_layout(orc):
+    blk = orc.gauss_block(11, 3, 17, 5)
+    lib = orc.lib()
+    for col in (0, 4):
+        for row in (0, 16):
+            assert blk[col, row] == lib.orc_gauss(11, 0, 3, col, row)
+    assert not np.allclose(orc.gauss_block(11, 3, 17, 5), orc.gauss_block(12, 3, 17, 5))
+    assert not np.allclose(orc.gauss_block(11, 3, 17, 5), orc.gauss_block(11, 4, 17, 5))

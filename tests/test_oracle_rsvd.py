@@ -1,0 +1,74 @@
+"""Oracle: randomized SVD of the transfer operators (Sec. 2.1 steps 1-6).
+Pins: the closed-form spectrum and DST-I singular vectors of the 1D heat
+propagator; exactness of the rSVD when the sketch spans the whole space
+(brute force against numpy's dense SVD); the orientation of the lifted
+singular vectors, F' phi_r = sigma_r psi_r (Eq. (svd))."""
+import numpy as np
+import pytest
+
+from paper_2508_08873_gb300 import workloads as W
+
+
+def _heat_closed_form(n, dt, M):
+    h = 1.0 / (n + 1)
+    j = np.arange(1, n + 1)
+    lam = 4.0 / h ** 2 * np.sin(j * np.pi * h / 2) ** 2
+    x = np.arange(1, n + 1) * h
+    return (1.0 + dt * lam) ** (-M), np.sqrt(2 * h) * np.sin(np.pi * np.outer(j, x))
+
+
+@pytest.mark.parametrize("interval", [0, 9])
+def test_rsvd_heat1d_closed_form(orc, interval):
+    P = W.heat1d()                                   # n=255, M=64, dt=1/1024, R=8, p=4
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    c = orc.rsvd_interval(op, P.dt, P.M, interval, P.R, P.p, P.seed)
+    sig, modes = _heat_closed_form(P.n, P.dt, P.M)
+    assert c.S.shape[0] == P.R
+    # |sigma_hat_j - sigma_j| <= 1e-12 sigma_1 for j <= R
+    assert np.max(np.abs(c.S - sig[:P.R])) <= 1e-12 * sig[0]
+    # singular vectors = DST-I modes up to sign, for the well separated j <= 5
+    for j in range(5):
+        for vec in (c.U[:, j], c.V[:, j]):
+            assert abs(abs(vec @ modes[j]) - 1.0) < 1e-10
+    # the sketch of rank ~8 in 12 columns: deflation keeps the basis orthonormal
+    assert c.rank_w <= P.R + P.p
+
+
+@pytest.mark.parametrize("maker", ["heat", "adr"])
+def test_rsvd_exact_when_sketch_spans_space(orc, maker):
+    n, dt, M = 12, 1e-3, 5
+    lo, di, up = W.heat1d_op(n) if maker == "heat" else W.adr1d_op(n, nu=0.05)
+    op = orc.Tridiag(lo, di, up)
+    Fp = orc.propagate(op, dt, M, np.eye(n)).T
+    Uf, sf, Vft = np.linalg.svd(Fp)
+    R = 5
+    c = orc.rsvd_interval(op, dt, M, 0, R, n - R + 2, seed=3)   # ell = n + 2 >= n
+    np.testing.assert_allclose(c.S, sf[:R], rtol=0, atol=1e-12 * sf[0])
+    G = c.U @ np.diag(c.S) @ c.V.T
+    Gex = Uf[:, :R] @ np.diag(sf[:R]) @ Vft[:R]
+    np.testing.assert_allclose(G, Gex, atol=1e-11 * sf[0])
+    # Eq. (truncation_error): ||F' - G'|| = sigma_{R+1}
+    assert abs(np.linalg.norm(Fp - G, 2) - sf[R]) <= 1e-11 * sf[0]
+    assert abs(c.sigma_next - sf[R]) <= 1e-12 * sf[0]
+
+
+def test_rsvd_vector_orientation_nonsymmetric(orc):
+    """F' phi_r = sigma_r psi_r and F'^* psi_r = sigma_r phi_r: the left vectors
+    lie in the image of F' (basis w), the right ones in that of F'^*."""
+    n, dt, M = 40, 1e-3, 6
+    op = orc.Tridiag(*W.adr1d_op(n, nu=0.02))
+    c = orc.rsvd_interval(op, dt, M, 2, 4, 40, seed=5)
+    FV = orc.propagate(op, dt, M, c.V.T).T
+    np.testing.assert_allclose(FV, c.U * c.S, atol=1e-11 * c.S[0])
+    FtU = orc.propagate(op, dt, M, c.U.T, adjoint=True).T
+    np.testing.assert_allclose(FtU, c.V * c.S, atol=1e-11 * c.S[0])
+
+
+def test_rsvd_independent_intervals_and_seed(orc):
+    P = W.heat1d(n=63, N=3, M=16, R=4, p=2)
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    a = orc.rsvd_interval(op, P.dt, P.M, 0, P.R, P.p, 0)
+    b = orc.rsvd_interval(op, P.dt, P.M, 1, P.R, P.p, 0)
+    # different sketches, same operator: same leading singular values
+    np.testing.assert_allclose(a.S[:3], b.S[:3], rtol=1e-9)
+    assert a.fine_evals == 2 * (P.R + P.p)
