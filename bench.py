@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark: Parareal solves/s at 1e-8 relative error versus the FP64 oracle.
+
+Workload (one step = one pass of the whole hot path): the 1D advection-
+diffusion-reaction problem u_t = 0.01 u_xx - u_x - 0.1 u, n = 4095 interior
+nodes, T = 1 in N = 64 intervals of M = 256 backward-Euler steps, rank
+R = 16 with p = 8 oversampling, u0 = 5 seeded Gaussian bumps, f = 0.  A step
+builds the coarse solvers (randomized SVD: forward sketch, orthonormalisation,
+adjoint sketch, orthonormalisation, small SVD, lift) and runs one Parareal
+solve to the a posteriori tolerance 1e-8 (fine solves, coarse sweeps, bounds).
+The default arithmetic is the mixed mode (FP32 sketches, FP64 Parareal).
+
+value: solves/s with inputs resident in HBM (device-timed with CUDA events on
+the library's stream).  e2e: the same through the C ABI with host buffers (the
+operator coefficients and u0 uploaded, the iterate read back inside the timed
+region).  --impl reference times the FP64 CPU oracle on a bounded sample of the
+same workload on the host cores.
+
+Multi-GPU: the path does not shard; --gpus N runs N independent replicas (one
+process per GPU under torchrun), value = all solves / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Parareal solves/s at 1e-8 rel err vs FP64 oracle"
+UNIT = "solves/s"
+TOL = 1e-8
+WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--prec", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=20.0,
+                    help="seconds of oracle work for the cpu_baseline sample")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm / cpu baseline: the FP64 oracle on a bounded sample
+# ---------------------------------------------------------------------------
+def oracle_sample(P, budget_s: float):
+    """Time the oracle on a sample of the workload and extrapolate to one solve:
+    rSVD of a subset of intervals (scaled by N / intervals done) plus a few
+    Parareal iterations (scaled by the iteration count of the full solve)."""
+    from oracle import oracle as orc
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    t0 = time.perf_counter()
+    nb = 0
+    coarse = []
+    while nb < P.N:
+        coarse.append(orc.rsvd_interval(oop, P.dt, P.M, nb, P.R, P.p, P.seed))
+        nb += 1
+        if time.perf_counter() - t0 > 0.4 * budget_s:
+            break
+    t_build = (time.perf_counter() - t0) * P.N / nb
+    # Parareal iterations: each is N fine solves plus the sequential sweep
+    co = orc.Coarse([coarse[i % nb] for i in range(P.N)], P.R, P.p)
+    t1 = time.perf_counter()
+    kdone = 0
+    u = None
+    while True:
+        res = orc.parareal(oop, P.dt, P.M, P.N, co, P.u0, K=kdone + 1)
+        kdone += 1
+        if time.perf_counter() - t1 > 0.6 * budget_s or kdone >= 3:
+            break
+    # parareal(K) recomputes from scratch: time of the last call ~ K iterations
+    t2 = time.perf_counter()
+    res = orc.parareal(oop, P.dt, P.M, P.N, co, P.u0, K=kdone)
+    t_iter = (time.perf_counter() - t2) / kdone
+    return t_build, t_iter, nb, kdone, orc.num_threads()
+
+
+def run_reference(args, P, k_iters: int):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    times = []
+    info = None
+    for s in range(args.warmup + args.steps):
+        tb, ti, nb, kd, cores = oracle_sample(P, budget_s=min(args.cpu_budget, 8.0))
+        est = tb + ti * k_iters
+        if s >= args.warmup:
+            times.append(est)
+        info = (nb, kd, cores)
+    sec = statistics.mean(times)
+    val = 1.0 / sec
+    nb, kd, cores = info
+    sample = ("oracle rSVD of %d of %d intervals scaled to %d, plus %d Parareal iterations "
+              "scaled to the %d the solve needs" % (nb, P.N, P.N, kd, k_iters))
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# native arm
+# ---------------------------------------------------------------------------
+FP64_PEAK_GFLOPS = 152 * 4 * 2.070      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.07 GHz
+FP32_PEAK_GFLOPS = 152 * 256 * 2.070    # 128 FP32 FMA/clk/SM
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2508_08873_gb300 import workloads as W
+    P = W.adr1d()
+    K_ITERS_REF = 29          # iterations the tol-1e-8 solve performs (measured on the oracle)
+    if args.impl == "reference":
+        run_reference(args, P, K_ITERS_REF)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2508_08873_gb300 import api
+
+    ctx = api.Context(local)
+    stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    u0_d = torch.tensor(P.u0, dtype=torch.float64, device=dev)
+    out_d = torch.empty((P.N + 1, P.n), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+
+    def step(op_, u0, out):
+        co = api.Coarse(ctx, op_, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=args.prec)
+        u, info = api.parareal_solve(ctx, co, u0, K=P.N, tol=TOL, out=out, bounds=False)
+        co.close()
+        return info
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+            torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        info = step(op, u0_d, out_d)
+    # ---- timed region (device time, inputs resident) -------------------------
+    ctx.set_kernel_timing(True)
+    ctx.reset_kernel_time()
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    ev = []
+    launches0 = ctx.launch_count()
+    k_list = []
+    t_wall0 = time.perf_counter()
+    for s in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step(op, u0_d, out_d)
+        e1.record(stream)
+        ev.append((e0, e1))
+        k_list.append(info["k_done"])
+    barrier()
+    t_wall = time.perf_counter() - t_wall0
+    launches = ctx.launch_count() - launches0
+    ms = [a.elapsed_time(b) for a, b in ev]
+    kern = {f: ctx.kernel_time(f) for f in ("propagate_f64", "propagate_f32", "sweep", "orth",
+                                            "svd", "lift")}
+    ctx.set_kernel_timing(False)
+    clk = clocks.stop()
+    ms_step = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * 1000.0 / ms_step
+    # amortised (serving view): solves only, coarse solvers built once
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=args.prec)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.steps):
+        api.parareal_solve(ctx, co, u0_d, K=P.N, tol=TOL, out=out_d, bounds=False)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    amort = 1000.0 * args.steps / a0.elapsed_time(a1)
+    # ---- e2e: host buffers through the C ABI ---------------------------------
+    u0_h = torch.tensor(P.u0, dtype=torch.float64).pin_memory()
+    out_h = torch.empty((P.N + 1, P.n), dtype=torch.float64).pin_memory()
+    lo_h, di_h, up_h = (torch.tensor(a, dtype=torch.float64).pin_memory() for a in (P.lo, P.di, P.up))
+    e2e_ms = []
+    for s in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op_h = api.Operator.tridiag(ctx, lo_h.numpy(), di_h.numpy(), up_h.numpy())
+        info_h = step(op_h, u0_h.numpy(), out_h.numpy())
+        op_h.close()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+    # ---- accuracy of the timed solve vs the oracle's sequential fine solution -
+    err = None
+    if rank == 0:
+        from oracle import oracle as orc
+        ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0)
+        err = orc.rel_err(out_d.cpu().numpy(), ref)
+    # ---- roofline of the dominant kernel ---------------------------------------
+    fam = max(("propagate_f64", "propagate_f32"), key=lambda f: kern[f][1])
+    nl, tot = kern[fam]
+    # algorithmic FP64/FP32 flops: Thomas with precomputed pivots = 5 flop per
+    # row-step (1 FMA forward, 1 MUL + 1 FMA backward), n rows, M steps, per system
+    k_mean = statistics.mean(k_list)
+    systems_per_step = (P.N * k_mean - k_mean * (k_mean - 1) / 2) if fam == "propagate_f64" \
+        else 2 * P.N * (P.R + P.p)
+    flops_step = 5.0 * P.n * P.M * systems_per_step
+    launches_per_step = nl / args.steps
+    achieved = flops_step / (tot / args.steps) / 1e6 if tot > 0 else 0.0   # GFLOP/s
+    peak = FP64_PEAK_GFLOPS if fam == "propagate_f64" else FP32_PEAK_GFLOPS
+    roof = {"bound": "alu", "kernel": fam, "achieved": achieved / 1e3, "peak": peak / 1e3,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "launches_per_step": launches_per_step,
+            "share_of_step": (tot / args.steps) / ms_step,
+            "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe: 1.195 TFLOP/s); "
+                         "FP32: 128 FMA/clk/SM"}
+    kernels = {f: {"launches": v[0], "ms_total": v[1]} for f, v in kern.items()}
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        tb, ti, nb, kd, cores = oracle_sample(P, args.cpu_budget)
+        est = tb + ti * K_ITERS_REF
+        cpu = {"value": 1.0 / est, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "rSVD of %d/%d intervals + %d of %d Parareal iterations, "
+                         "extrapolated to one solve (%.1f s)" % (nb, P.N, kd, K_ITERS_REF, est)}
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64" if args.prec == "f64" else "f32+f64",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "precision": args.prec,
+                           "step": "build_coarse + parareal_solve(tol=1e-8)",
+                           "l2": "flushed (256 MB write) between timed steps",
+                           "parallelism": "replicas" if world > 1 else "1 GPU"},
+                "iterations": k_list[-1], "rel_err_vs_oracle": err,
+                "amortised_solves_per_s": amort * world,
+                "e2e": {"value": e2e_val, "unit": UNIT,
+                        "h2d_bytes_per_step": 8 * (P.n + 3 * P.n),
+                        "d2h_bytes_per_step": 8 * (P.N + 1) * P.n},
+                "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
+                "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu,
+                "wall_s_timed": t_wall}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

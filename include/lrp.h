@@ -1,0 +1,185 @@
+/*
+ * lrp.h - C ABI of the GB300 (sm_103a) library for Parareal with low-rank
+ * coarse solvers (Gander, Ohlberger, Rave, arXiv 2508.08873).
+ *
+ * Problem (Sec. 2): a linear semi-discretisation u_t = -A u + f on [0, T] is
+ * split into N coarse intervals of M backward-Euler steps each (dt = T/(N M)).
+ * The fine solver of interval i is F_i v = F_i' v + b_i (Eq. F_n_affine).
+ * The coarse solver is the rank-R truncated SVD of F_i' plus b_i
+ * (Eq. spectral_G), computed by the randomized SVD of Sec. 2.1, and Parareal
+ * (Eq. def_Parareal) corrects the fine solves with it.
+ *
+ * Conventions shared by every entry point:
+ *  - Intervals are 0-based: interval i maps t_i to t_{i+1} (the paper's n=i+1).
+ *  - A vector of length n is contiguous; a batch of vectors is row-major
+ *    (vector v occupies [v*n, (v+1)*n)).
+ *  - Sources are separable, f(t, x) = sum_{q<Q} c_q(t) g_q(x): g is Q x n,
+ *    and c holds c_q at the end of every fine step, c[(J-1)*Q + q] at
+ *    t = J*dt for J = 1..N*M (fully implicit Euler samples f at t_{j+1}).
+ *  - Every pointer argument may be host memory or device memory of the
+ *    context's device; the library detects which.  The caller owns all
+ *    buffers it passes; the library owns the handles it returns and the device
+ *    memory behind them.  Host outputs are complete when the call returns;
+ *    device outputs are complete in stream order on the context's stream.
+ *  - Errors are returned as lrp_status; nothing is thrown across the ABI.
+ *    lrp_last_error() gives a message for the last failure on a context.
+ *  - A context is used by one host thread at a time.
+ *  - The inner product is the Euclidean one on the coefficient vectors, so
+ *    the adjoint of F_i' is its transpose (Sec. 2.1, step 3).
+ */
+#ifndef LRP_H
+#define LRP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRP_OK = 0,
+  LRP_EINVAL = 1,      /* bad argument (size, null pointer, unsupported shape) */
+  LRP_ENOMEM = 2,      /* device allocation failed or the HBM budget is exceeded */
+  LRP_ENOTCONV = 3,    /* an iteration cap was hit; outputs hold the last iterate */
+  LRP_EBREAKDOWN = 4,  /* a zero pivot or a breakdown in an iterative solver */
+  LRP_ETIMEOUT = 5,    /* a bounded device wait expired */
+  LRP_ECUDA = 6,       /* a CUDA runtime error; see lrp_last_error() */
+  LRP_EBUSY = 7        /* the request queue is full */
+} lrp_status;
+
+/* Arithmetic of the coarse-solver build (rSVD steps 1-6).
+ * LRP_PREC_F64:   sketches, orthonormalisation, SVD and factors in FP64.
+ * LRP_PREC_MIXED: sketch propagation and orthonormalisation in FP32, the small
+ *                 SVD in FP64, factors kept in FP32 and FP64.
+ * Parareal fine solves, corrections and bounds are FP64 in both modes. */
+typedef enum { LRP_PREC_F64 = 0, LRP_PREC_MIXED = 1 } lrp_precision;
+
+typedef struct lrp_ctx lrp_ctx;
+typedef struct lrp_operator lrp_operator;
+typedef struct lrp_coarse lrp_coarse;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`.  hbm_budget_bytes caps the device
+ * memory the context may hold (0 = no cap beyond the free memory).  The
+ * context creates its own non-blocking stream. */
+lrp_status lrp_create(lrp_ctx** out, int device, size_t hbm_budget_bytes);
+void lrp_destroy(lrp_ctx* ctx);
+/* Use the caller's cudaStream_t (passed as void*) for all later work; NULL
+ * returns to the context's own stream.  The caller keeps ownership. */
+lrp_status lrp_set_stream(lrp_ctx* ctx, void* cuda_stream);
+void* lrp_get_stream(lrp_ctx* ctx);
+/* Wait until all work of the context's stream has finished. */
+lrp_status lrp_synchronize(lrp_ctx* ctx);
+const char* lrp_status_string(lrp_status s);
+const char* lrp_last_error(lrp_ctx* ctx);
+/* Device bytes currently held by the context. */
+size_t lrp_bytes_in_use(lrp_ctx* ctx);
+/* Number of kernels the context has launched so far (all kernel families). */
+long lrp_launch_count(lrp_ctx* ctx);
+
+/* Per-kernel timing with CUDA events recorded around every launch of the
+ * named kernel family on the context's stream (off by default).  Families:
+ * "propagate_f64" and "propagate_f32" (the batched fine propagator in each
+ * arithmetic), "sweep" (the coarse sweep), "orth", "svd", "lift".  lrp_kernel_time returns the launches and the summed
+ * event time (ms) since the last reset; it synchronises the stream. */
+lrp_status lrp_set_kernel_timing(lrp_ctx* ctx, int enable);
+lrp_status lrp_kernel_time(lrp_ctx* ctx, const char* family, int* launches, double* total_ms);
+lrp_status lrp_reset_kernel_time(lrp_ctx* ctx);
+
+/* ---- operators (the semi-discretisation A; inputs, copied to the device) -- */
+
+/* Tridiagonal A, row i: lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1] (lo[0] and
+ * up[n-1] are ignored).  I + dt*A must be diagonally dominant: the
+ * propagator eliminates without pivoting.  2 <= n <= 32768. */
+lrp_status lrp_operator_tridiag(lrp_ctx* ctx, int n, const double* lo, const double* di,
+                                const double* up, lrp_operator** out);
+/* 5-point A on an mx x my grid of interior nodes, node p = iy*mx + ix:
+ * (A x)_p = C[p] x_p + W[p] x_{p-1} + E[p] x_{p+1} + S[p] x_{p-mx} + N[p] x_{p+mx};
+ * coefficients that reach outside the grid are ignored (homogeneous Dirichlet). */
+lrp_status lrp_operator_stencil5(lrp_ctx* ctx, int mx, int my, const double* C,
+                                 const double* W, const double* E, const double* S,
+                                 const double* N, lrp_operator** out);
+void lrp_operator_free(lrp_operator* op);
+int lrp_operator_size(const lrp_operator* op);
+
+/* Linear solver controls of 2D operators (Krylov per implicit-Euler step):
+ * relative residual tolerances for FP64 and FP32 propagation and the
+ * iteration cap per step.  Defaults: 1e-12, 1e-6, 20000. */
+lrp_status lrp_operator_set_krylov(lrp_operator* op, double rtol_f64, double rtol_f32,
+                                   int max_iter);
+
+/* ---- the batched fine propagator (Sec. 4: backward Euler) ---------------- */
+
+/* Apply M backward-Euler steps (I + dt A) x_{j+1} = x_j + dt f(t_{j+1}) to each
+ * of nvec vectors.  x_in, x_out: nvec x n (may alias).  adjoint != 0 applies
+ * the transpose solves (F'^*; requires Q = 0).  Q > 0 adds the source: g is
+ * Q x n and c is nvec x M x Q (the source samples of each vector's steps).
+ * prec selects FP64 or FP32 arithmetic (LRP_PREC_MIXED = FP32). */
+lrp_status lrp_propagate(lrp_ctx* ctx, const lrp_operator* op, double dt, int M, int adjoint,
+                         int nvec, const double* x_in, double* x_out, int Q, const double* g,
+                         const double* c, lrp_precision prec);
+
+/* The Gaussian sketch vectors of rSVD step 1 (Sec. 2.1) exactly as the build
+ * draws them in its kernels: out[c*n + r] = omega_{interval, c}[r] for
+ * c < ncol, r < n.  prec selects the FP64 or the FP32 deviate.  out: host or
+ * device, ncol x n doubles. */
+lrp_status lrp_gaussian(lrp_ctx* ctx, uint64_t seed, int interval, int ncol, int n,
+                        lrp_precision prec, double* out);
+
+/* ---- coarse solvers (Sec. 2.1, randomized SVD steps 1-6) ----------------- */
+
+/* Build G_i' = U_i diag(S_i) V_i^T for i = 0..N-1 from rank + oversample
+ * Gaussian sketch vectors per interval (Philox4x32-10 keyed by seed; counter
+ * (row, column, interval, 0); Box-Muller).  The factors stay on the device. */
+lrp_status lrp_build_coarse(lrp_ctx* ctx, const lrp_operator* op, double dt, int M, int N,
+                            int rank, int oversample, uint64_t seed, lrp_precision prec,
+                            lrp_coarse** out);
+void lrp_coarse_free(lrp_coarse* co);
+/* R_i (kept rank), the dimensions of the deflated bases of steps 2 and 4, all
+ * singular values of the small matrix of step 5 (N x (rank+oversample),
+ * zero-padded), delta = max_i sigma_{i,1} and eps = max_i sigma_{i,R_i+1}
+ * (Eq. bounds_delta_eps).  Any output pointer may be NULL. Host outputs. */
+lrp_status lrp_coarse_info(const lrp_coarse* co, int* R_i, int* rank_w, int* rank_v,
+                           double* sigma, double* delta, double* eps);
+/* Copy the factors of interval i: U and V are R_i x n (row r = psi_r / phi_r),
+ * S has R_i entries (host or device outputs). */
+lrp_status lrp_coarse_factors(const lrp_coarse* co, int interval, double* U, double* S,
+                              double* V);
+
+/* ---- Parareal (Eq. def_Parareal) ----------------------------------------- */
+
+typedef struct {
+  int k_done;          /* iterations performed */
+  int fine_evals;      /* fine evaluations per interval in this solve (b_i + k) */
+  int converged;       /* 1 if the tol criterion was met */
+  double final_bound;  /* max_n a posteriori bound of the last iterate */
+  double scale;        /* max_n ||u^k_n|| of the last iterate */
+  double device_ms;    /* device time of the solve (events on the stream) */
+} lrp_solve_stats;
+
+/* Solve with coarse solvers `co` from u0 (n) and the source (Q, g, c as in
+ * the conventions; Q = 0 for f = 0).  Runs at most K_max iterations (clamped
+ * to N: u^N equals the fine solution).  If tol > 0 it stops at the first
+ * k >= 1 with max_n bound_n^k <= tol * max_n ||u^k_n||, bound_n^k being the
+ * a posteriori bound eps sum_{m=1}^{n-1} delta^{n-m-1} ||u^k_m - u^{k-1}_m||
+ * (Eq. apost_bound).  Outputs: u_out ((N+1) x n, the last iterate),
+ * bound_out (K_max x (N+1), row k-1 = bound of iterate k, may be NULL),
+ * k_done and stats (may be NULL).  Returns LRP_ENOTCONV when tol > 0 was not
+ * met within K_max iterations (outputs are valid). */
+lrp_status lrp_parareal_solve(lrp_ctx* ctx, const lrp_coarse* co, const double* u0, int Q,
+                              const double* g, const double* c, int K_max, double tol,
+                              double* u_out, double* bound_out, int* k_done,
+                              lrp_solve_stats* stats);
+
+/* The sequential fine solution u_{i+1} = F_i u_i (Sec. 2), (N+1) x n, with the
+ * same propagator: the fixed point Parareal converges to. */
+lrp_status lrp_fine_solution(lrp_ctx* ctx, const lrp_operator* op, double dt, int M, int N,
+                             const double* u0, int Q, const double* g, const double* c,
+                             double* u_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRP_H */

@@ -1,0 +1,253 @@
+"""Python wrappers over the C ABI of include/lrp.h (argument marshalling only).
+
+Arrays: numpy (host) or torch tensors (host or CUDA), float64, C-contiguous.
+Outputs are numpy arrays unless an `out` array is passed.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+
+from . import _native as nat
+from ._native import PREC_F64, PREC_MIXED, check, ptr
+
+
+def _prec(p) -> int:
+    if p in (PREC_F64, "f64", "fp64", None):
+        return PREC_F64
+    if p in (PREC_MIXED, "mixed", "f32", "fp32"):
+        return PREC_MIXED
+    raise ValueError("precision must be 'f64' or 'mixed'")
+
+
+class Context:
+    """A library context on one CUDA device (lrp_create)."""
+
+    def __init__(self, device: int = 0, hbm_budget: int = 0):
+        self.lib = nat.load()
+        h = ctypes.c_void_p()
+        st = self.lib.lrp_create(ctypes.byref(h), device, hbm_budget)
+        if st != nat.LRP_OK:
+            raise nat.LrpError(st, "lrp_create failed (is a CUDA device visible?)")
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None) and not nat.exiting():
+            self.lib.lrp_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def stream(self) -> int:
+        return self.lib.lrp_get_stream(self.h) or 0
+
+    def set_stream(self, stream_handle: Optional[int]):
+        check(self.lib.lrp_set_stream(self.h, stream_handle), self.h)
+
+    def synchronize(self):
+        check(self.lib.lrp_synchronize(self.h), self.h)
+
+    def bytes_in_use(self) -> int:
+        return self.lib.lrp_bytes_in_use(self.h)
+
+    def launch_count(self) -> int:
+        return self.lib.lrp_launch_count(self.h)
+
+    def set_kernel_timing(self, on: bool):
+        check(self.lib.lrp_set_kernel_timing(self.h, int(on)), self.h)
+
+    def kernel_time(self, family: str):
+        nl = ctypes.c_int()
+        ms = ctypes.c_double()
+        check(self.lib.lrp_kernel_time(self.h, family.encode(), ctypes.byref(nl), ctypes.byref(ms)),
+              self.h)
+        return nl.value, ms.value
+
+    def reset_kernel_time(self):
+        check(self.lib.lrp_reset_kernel_time(self.h), self.h)
+
+    def last_error(self) -> str:
+        return (self.lib.lrp_last_error(self.h) or b"").decode()
+
+
+class Operator:
+    """A semi-discretisation A of u_t = -A u + f held on the device."""
+
+    def __init__(self, ctx: Context, handle, n: int, kind: str):
+        self.ctx, self.h, self.n, self.kind = ctx, handle, n, kind
+
+    @classmethod
+    def tridiag(cls, ctx: Context, lo, di, up) -> "Operator":
+        lo, di, up = (np.ascontiguousarray(a, dtype=np.float64) for a in (lo, di, up))
+        h = ctypes.c_void_p()
+        check(ctx.lib.lrp_operator_tridiag(ctx.h, di.shape[0], ptr(lo), ptr(di), ptr(up),
+                                           ctypes.byref(h)), ctx.h)
+        return cls(ctx, h, di.shape[0], "tridiag")
+
+    @classmethod
+    def stencil5(cls, ctx: Context, mx: int, my: int, st: dict) -> "Operator":
+        arr = [np.ascontiguousarray(st[k], dtype=np.float64) for k in ("C", "W", "E", "S", "N")]
+        h = ctypes.c_void_p()
+        check(ctx.lib.lrp_operator_stencil5(ctx.h, mx, my, *[ptr(a) for a in arr],
+                                            ctypes.byref(h)), ctx.h)
+        return cls(ctx, h, mx * my, "stencil5")
+
+    @classmethod
+    def from_problem(cls, ctx: Context, P) -> "Operator":
+        if P.kind == "tridiag":
+            return cls.tridiag(ctx, P.lo, P.di, P.up)
+        return cls.stencil5(ctx, P.mx, P.my, P.st)
+
+    def set_krylov(self, rtol_f64: float = 1e-12, rtol_f32: float = 1e-6, max_iter: int = 20000):
+        check(self.ctx.lib.lrp_operator_set_krylov(self.h, rtol_f64, rtol_f32, max_iter), self.ctx.h)
+
+    def close(self):
+        if getattr(self, "h", None) and not nat.exiting():
+            self.ctx.lib.lrp_operator_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _as_c(a):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return np.ascontiguousarray(a, dtype=np.float64)
+    return a
+
+
+def propagate(ctx: Context, op: Operator, dt: float, M: int, X, adjoint: bool = False,
+              g=None, c=None, prec="f64", out=None):
+    """M backward-Euler steps on each row of X (nvec, n) (lrp_propagate).
+    c: (nvec, M, Q) source samples per row, or (M, Q) shared."""
+    X = _as_c(X)
+    squeeze = False
+    if isinstance(X, np.ndarray) and X.ndim == 1:
+        X = X[None, :]
+        squeeze = True
+    nvec = X.shape[0]
+    Q = 0
+    if g is not None:
+        g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
+        Q = g.shape[0]
+        c = _as_c(c)
+        if isinstance(c, np.ndarray) and c.ndim == 2:
+            c = np.ascontiguousarray(np.broadcast_to(c, (nvec,) + c.shape))
+    if out is None:
+        out = np.empty((nvec, op.n))
+    check(ctx.lib.lrp_propagate(ctx.h, op.h, float(dt), int(M), int(adjoint), nvec, ptr(X),
+                                ptr(out), Q, ptr(g), ptr(c), _prec(prec)), ctx.h)
+    return out[0] if squeeze else out
+
+
+def gaussian(ctx: Context, seed: int, interval: int, ncol: int, n: int, prec="f64", out=None):
+    """The sketch vectors omega_{interval, c}, c < ncol, as the build draws them."""
+    if out is None:
+        out = np.empty((ncol, n))
+    check(ctx.lib.lrp_gaussian(ctx.h, int(seed), int(interval), int(ncol), int(n), _prec(prec),
+                               ptr(out)), ctx.h)
+    return out
+
+
+class Coarse:
+    """Low-rank coarse solvers G_i' = U_i diag(S_i) V_i^T of all intervals."""
+
+    def __init__(self, ctx: Context, op: Operator, dt: float, M: int, N: int, rank: int,
+                 oversample: int, seed: int = 0, prec="f64"):
+        self.ctx, self.op = ctx, op
+        self.dt, self.M, self.N, self.R, self.p = dt, M, N, rank, oversample
+        self.prec = _prec(prec)
+        h = ctypes.c_void_p()
+        check(ctx.lib.lrp_build_coarse(ctx.h, op.h, float(dt), int(M), int(N), int(rank),
+                                       int(oversample), int(seed), self.prec, ctypes.byref(h)),
+              ctx.h)
+        self.h = h
+
+    def info(self) -> dict:
+        N, ell = self.N, self.R + self.p
+        Ri = np.zeros(N, dtype=np.int32)
+        rw = np.zeros(N, dtype=np.int32)
+        rv = np.zeros(N, dtype=np.int32)
+        sig = np.zeros((N, ell))
+        d = ctypes.c_double()
+        e = ctypes.c_double()
+        check(self.ctx.lib.lrp_coarse_info(self.h, Ri.ctypes.data, rw.ctypes.data, rv.ctypes.data,
+                                           sig.ctypes.data, ctypes.addressof(d),
+                                           ctypes.addressof(e)), self.ctx.h)
+        return dict(R=Ri, rank_w=rw, rank_v=rv, sigma=sig, delta=d.value, eps=e.value)
+
+    def factors(self, i: int):
+        Ri = int(self.info()["R"][i])
+        U = np.zeros((Ri, self.op.n))
+        V = np.zeros((Ri, self.op.n))
+        S = np.zeros(Ri)
+        check(self.ctx.lib.lrp_coarse_factors(self.h, i, U.ctypes.data, S.ctypes.data,
+                                              V.ctypes.data), self.ctx.h)
+        return U, S, V
+
+    def close(self):
+        if getattr(self, "h", None) and not nat.exiting():
+            self.ctx.lib.lrp_coarse_free(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def parareal_solve(ctx: Context, co: Coarse, u0, g=None, c=None, K: Optional[int] = None,
+                   tol: float = 0.0, out=None, bounds: bool = True, allow_notconv: bool = True):
+    """Parareal iterations (lrp_parareal_solve).  Returns (u (N+1, n), info)."""
+    N, n = co.N, co.op.n
+    Kmax = N if K is None else int(K)
+    u0 = _as_c(u0)
+    Q = 0
+    if g is not None:
+        g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
+        Q = g.shape[0]
+        c = _as_c(c)
+    if out is None:
+        out = np.empty((N + 1, n))
+    bnd = np.zeros((max(Kmax, 1), N + 1)) if bounds else None
+    kd = ctypes.c_int()
+    stats = nat.SolveStats()
+    ok = (nat.LRP_OK, nat.LRP_ENOTCONV) if allow_notconv else (nat.LRP_OK,)
+    st = check(ctx.lib.lrp_parareal_solve(ctx.h, co.h, ptr(u0), Q, ptr(g), ptr(c), Kmax,
+                                          float(tol), ptr(out),
+                                          bnd.ctypes.data if bnd is not None else None,
+                                          ctypes.byref(kd), ctypes.byref(stats)), ctx.h, ok)
+    info = dict(k_done=kd.value, fine_evals=stats.fine_evals, converged=bool(stats.converged),
+                final_bound=stats.final_bound, scale=stats.scale, device_ms=stats.device_ms,
+                status=st, bounds=bnd[:kd.value] if bnd is not None else None)
+    return out, info
+
+
+def fine_solution(ctx: Context, op: Operator, dt: float, M: int, N: int, u0, g=None, c=None,
+                  out=None):
+    """Sequential fine solution u_{i+1} = F_i u_i on the device, (N+1, n)."""
+    u0 = _as_c(u0)
+    Q = 0
+    if g is not None:
+        g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
+        Q = g.shape[0]
+        c = _as_c(c)
+    if out is None:
+        out = np.empty((N + 1, op.n))
+    check(ctx.lib.lrp_fine_solution(ctx.h, op.h, float(dt), int(M), int(N), ptr(u0), Q, ptr(g),
+                                    ptr(c), ptr(out)), ctx.h)
+    return out

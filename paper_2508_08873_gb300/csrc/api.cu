@@ -1,0 +1,719 @@
+// C ABI of the library (include/lrp.h): contexts, operators, the batched fine
+// propagator, the coarse-solver build (randomized SVD, Sec. 2.1) and the
+// Parareal solve (Eq. def_Parareal).  Host code only orchestrates kernels;
+// every arithmetic step of the method runs on the device.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+using namespace lrp;
+
+struct lrp_ctx : public Ctx {};
+struct lrp_operator : public Operator {};
+struct lrp_coarse : public Coarse {};
+
+namespace lrp {
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+lrp_status set_err(Ctx* c, lrp_status s, const std::string& msg) {
+  if (c) c->last_error = msg;
+  return s;
+}
+
+lrp_status cuda_err(Ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (e == cudaErrorMemoryAllocation) return set_err(c, LRP_ENOMEM, m);
+  return set_err(c, LRP_ECUDA, m);
+}
+
+DevBuf::~DevBuf() { release(); }
+
+void ctx_retain(Ctx* c) { if (c) c->refs += 1; }
+
+void ctx_release(Ctx* c) {
+  if (!c || --c->refs > 0) return;
+  cudaSetDevice(c->device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->timers)
+    for (auto& pr : kv.second.pairs) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+  delete static_cast<lrp_ctx*>(c);
+}
+
+// Buffers are released before the context reference is dropped.
+Operator::~Operator() {
+  Ctx* c = ctx;
+  plans.clear();
+  for (auto& b : a64) b.release();
+  for (auto& b : a32) b.release();
+  ctx_release(c);
+}
+
+Coarse::~Coarse() {
+  Ctx* c = ctx;
+  for (DevBuf* b : {&U, &S, &V, &U32, &S32, &V32, &ws_u, &ws_F, &ws_b, &ws_norm, &ws_d, &ws_g, &ws_c})
+    b->release();
+  ctx_release(c);
+}
+
+void DevBuf::release() {
+  if (ptr) {
+    cudaFree(ptr);
+    if (ctx) ctx->in_use -= bytes;
+  }
+  ptr = nullptr;
+  bytes = 0;
+}
+
+lrp_status dev_alloc(Ctx* c, DevBuf& b, size_t bytes) {
+  b.release();
+  if (bytes == 0) bytes = 16;
+  if (c->budget && c->in_use + bytes > c->budget)
+    return set_err(c, LRP_ENOMEM, "HBM budget of the context exceeded");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e) { cudaGetLastError(); return cuda_err(c, e, "cudaMalloc"); }
+  b.ctx = c;
+  b.ptr = p;
+  b.bytes = bytes;
+  c->in_use += bytes;
+  return LRP_OK;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, p);
+  if (e != cudaSuccess) { cudaGetLastError(); return false; }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+void timer_begin(Ctx* c, const char* fam, cudaEvent_t* ev) {
+  *ev = nullptr;
+  if (!c->timing) return;
+  cudaEventCreate(ev);
+  cudaEventRecord(*ev, c->stream);
+}
+
+void timer_end(Ctx* c, const char* fam, cudaEvent_t ev) {
+  c->launches += 1;
+  if (!c->timing || !ev) return;
+  cudaEvent_t e2;
+  cudaEventCreate(&e2);
+  cudaEventRecord(e2, c->stream);
+  c->timers[fam].pairs.emplace_back(ev, e2);
+}
+
+// copy `bytes` from a host or device pointer into a device buffer
+static lrp_status to_device(Ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return LRP_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+  return e ? cuda_err(c, e, "copy to device") : LRP_OK;
+}
+
+static lrp_status from_device(Ctx* c, void* dst, const void* src, size_t bytes) {
+  if (!bytes) return LRP_OK;
+  cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, c->stream);
+  if (e) return cuda_err(c, e, "copy from device");
+  if (!is_device_ptr(dst)) {
+    e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_err(c, e, "synchronize");
+  }
+  return LRP_OK;
+}
+
+// A device view of caller data: the pointer itself when it is device memory,
+// else a temporary device copy.
+struct DevView {
+  const void* p = nullptr;
+  DevBuf tmp;
+};
+static lrp_status device_view(Ctx* c, const void* src, size_t bytes, DevView& v) {
+  if (!src || !bytes) { v.p = nullptr; return LRP_OK; }
+  if (is_device_ptr(src)) { v.p = src; return LRP_OK; }
+  lrp_status s = dev_alloc(c, v.tmp, bytes);
+  if (s) return s;
+  if ((s = to_device(c, v.tmp.ptr, src, bytes))) return s;
+  v.p = v.tmp.ptr;
+  return LRP_OK;
+}
+
+}  // namespace lrp
+
+// ===========================================================================
+// context
+// ===========================================================================
+extern "C" {
+
+const char* lrp_status_string(lrp_status s) {
+  switch (s) {
+    case LRP_OK: return "ok";
+    case LRP_EINVAL: return "invalid argument";
+    case LRP_ENOMEM: return "out of device memory or HBM budget";
+    case LRP_ENOTCONV: return "not converged within the iteration cap";
+    case LRP_EBREAKDOWN: return "breakdown (zero pivot)";
+    case LRP_ETIMEOUT: return "device wait timed out";
+    case LRP_ECUDA: return "CUDA error";
+    case LRP_EBUSY: return "queue full";
+  }
+  return "unknown status";
+}
+
+lrp_status lrp_create(lrp_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return LRP_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e || device < 0 || device >= ndev) { cudaGetLastError(); return LRP_ECUDA; }
+  e = cudaSetDevice(device);
+  if (e) return LRP_ECUDA;
+  auto* c = new lrp_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e) { delete c; return LRP_ECUDA; }
+  c->stream = c->own_stream;
+  *out = c;
+  return LRP_OK;
+}
+
+void lrp_destroy(lrp_ctx* c) {
+  if (!c) return;
+  ctx_release(c);   // freed now, or when its last operator / coarse handle goes
+}
+
+lrp_status lrp_set_stream(lrp_ctx* c, void* s) {
+  if (!c) return LRP_EINVAL;
+  c->stream = s ? (cudaStream_t)s : c->own_stream;
+  return LRP_OK;
+}
+
+void* lrp_get_stream(lrp_ctx* c) { return c ? (void*)c->stream : nullptr; }
+
+lrp_status lrp_synchronize(lrp_ctx* c) {
+  if (!c) return LRP_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e ? cuda_err(c, e, "synchronize") : LRP_OK;
+}
+
+const char* lrp_last_error(lrp_ctx* c) { return c ? c->last_error.c_str() : ""; }
+
+size_t lrp_bytes_in_use(lrp_ctx* c) { return c ? c->in_use : 0; }
+
+long lrp_launch_count(lrp_ctx* c) { return c ? c->launches : 0; }
+
+lrp_status lrp_set_kernel_timing(lrp_ctx* c, int enable) {
+  if (!c) return LRP_EINVAL;
+  c->timing = enable != 0;
+  return LRP_OK;
+}
+
+lrp_status lrp_kernel_time(lrp_ctx* c, const char* fam, int* launches, double* total_ms) {
+  if (!c || !fam) return LRP_EINVAL;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "synchronize");
+  auto it = c->timers.find(fam);
+  int nl = 0;
+  double tot = 0.0;
+  if (it != c->timers.end()) {
+    KernelTimer& t = it->second;
+    for (auto& pr : t.pairs) {
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, pr.first, pr.second);
+      t.total_ms += ms;
+      t.launches += 1;
+      cudaEventDestroy(pr.first);
+      cudaEventDestroy(pr.second);
+    }
+    t.pairs.clear();
+    nl = t.launches;
+    tot = t.total_ms;
+  }
+  if (launches) *launches = nl;
+  if (total_ms) *total_ms = tot;
+  return LRP_OK;
+}
+
+lrp_status lrp_reset_kernel_time(lrp_ctx* c) {
+  if (!c) return LRP_EINVAL;
+  cudaStreamSynchronize(c->stream);
+  for (auto& kv : c->timers)
+    for (auto& pr : kv.second.pairs) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+  c->timers.clear();
+  return LRP_OK;
+}
+
+// ===========================================================================
+// operators
+// ===========================================================================
+lrp_status lrp_operator_tridiag(lrp_ctx* c, int n, const double* lo, const double* di,
+                                const double* up, lrp_operator** out) {
+  if (!c || !out || !lo || !di || !up) return LRP_EINVAL;
+  if (n < 2 || n > 32768) return set_err(c, LRP_EINVAL, "tridiagonal size must be 2..32768");
+  cudaSetDevice(c->device);
+  auto op = std::make_unique<lrp_operator>();
+  op->ctx = c;
+  ctx_retain(c);
+  op->kind = 0;
+  op->n = n;
+  const double* src[3] = {lo, di, up};
+  for (int k = 0; k < 3; ++k) {
+    lrp_status s = dev_alloc(c, op->a64[k], sizeof(double) * n);
+    if (s) return s;
+    if ((s = to_device(c, op->a64[k].ptr, src[k], sizeof(double) * n))) return s;
+  }
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "operator upload");
+  *out = op.release();
+  return LRP_OK;
+}
+
+void lrp_operator_free(lrp_operator* op) {
+  if (!op) return;
+  cudaSetDevice(op->ctx->device);
+  cudaStreamSynchronize(op->ctx->stream);
+  delete op;
+}
+
+int lrp_operator_size(const lrp_operator* op) { return op ? op->n : 0; }
+
+lrp_status lrp_operator_set_krylov(lrp_operator* op, double rtol_f64, double rtol_f32,
+                                   int max_iter) {
+  if (!op || !(rtol_f64 > 0) || !(rtol_f32 > 0) || max_iter < 0) return LRP_EINVAL;
+  op->rtol64 = rtol_f64;
+  op->rtol32 = rtol_f32;
+  op->max_iter = max_iter;
+  return LRP_OK;
+}
+
+}  // extern "C"
+
+// ===========================================================================
+// propagation dispatch
+// ===========================================================================
+namespace lrp {
+lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
+                             int prec, const PropIn& in, const PropOut& out, const PropSrc& src);
+
+static lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
+                                int prec, const PropIn& in, const PropOut& out,
+                                const PropSrc& src) {
+  if (op->kind == 0) {
+    TriPlan* plan = nullptr;
+    lrp_status s = tri_get_plan(c, op, dt, adjoint, &plan);
+    if (s) return s;
+    return tri_propagate(c, op, plan, M, nsys, prec, in, out, src);
+  }
+  return stencil_propagate(c, op, dt, M, adjoint, nsys, prec, in, out, src);
+}
+}  // namespace lrp
+
+extern "C" {
+
+lrp_status lrp_propagate(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int adjoint,
+                         int nvec, const double* x_in, double* x_out, int Q, const double* g,
+                         const double* cv, lrp_precision prec) {
+  if (!c || !opc || !x_out || nvec < 0 || M < 0 || !(dt > 0) || Q < 0) return LRP_EINVAL;
+  if (adjoint && Q > 0) return set_err(c, LRP_EINVAL, "the adjoint propagates the linear part only");
+  if (Q > 0 && (!g || !cv)) return LRP_EINVAL;
+  if (nvec == 0) return LRP_OK;
+  cudaSetDevice(c->device);
+  Operator* op = const_cast<lrp_operator*>(opc);
+  const int n = op->n;
+  size_t vb = sizeof(double) * (size_t)nvec * n;
+  DevView xin, gv, cvv;
+  lrp_status s;
+  if ((s = device_view(c, x_in, vb, xin))) return s;
+  if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)nvec * M * Q, cvv))) return s;
+  bool out_dev = is_device_ptr(x_out);
+  DevBuf tmp_out;
+  void* dout = x_out;
+  if (!out_dev) {
+    if ((s = dev_alloc(c, tmp_out, vb))) return s;
+    dout = tmp_out.ptr;
+  }
+  PropIn in;
+  in.x = xin.p;
+  in.x_f64 = 1;
+  in.ldx = n;
+  PropOut o;
+  o.y = dout;
+  o.y_f64 = 1;
+  o.ldy = n;
+  PropSrc src;
+  src.Q = Q;
+  src.g = (const double*)gv.p;
+  src.c = (const double*)cvv.p;
+  src.cstride = (long)M * Q;
+  if ((s = propagate_any(c, op, dt, M, adjoint, nvec, prec == LRP_PREC_MIXED ? 1 : 0, in, o, src)))
+    return s;
+  if (!out_dev) {
+    if ((s = from_device(c, x_out, dout, vb))) return s;
+  } else {
+    cudaError_t e = cudaStreamSynchronize(c->stream);  // temporaries are freed on return
+    if (e) return cuda_err(c, e, "propagate");
+  }
+  return LRP_OK;
+}
+
+lrp_status lrp_gaussian(lrp_ctx* c, uint64_t seed, int interval, int ncol, int n,
+                        lrp_precision prec, double* out) {
+  if (!c || !out || ncol < 0 || n < 0 || interval < 0) return LRP_EINVAL;
+  cudaSetDevice(c->device);
+  size_t bytes = sizeof(double) * (size_t)ncol * n;
+  bool dev = is_device_ptr(out);
+  DevBuf tmp;
+  double* d = out;
+  lrp_status s;
+  if (!dev) {
+    if ((s = dev_alloc(c, tmp, bytes))) return s;
+    d = tmp.as<double>();
+  }
+  if ((s = gaussian(c, seed, interval, ncol, n, prec == LRP_PREC_MIXED, d))) return s;
+  if (!dev) return from_device(c, out, d, bytes);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e ? cuda_err(c, e, "gaussian") : LRP_OK;
+}
+
+// ===========================================================================
+// coarse solvers: randomized SVD of every interval (Sec. 2.1)
+// ===========================================================================
+lrp_status lrp_build_coarse(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int N,
+                            int rank, int oversample, uint64_t seed, lrp_precision prec,
+                            lrp_coarse** out) {
+  if (!c || !opc || !out || !(dt > 0) || M < 1 || N < 1 || rank < 0 || oversample < 0)
+    return LRP_EINVAL;
+  const int ell = rank + oversample;
+  if (ell < 1) return set_err(c, LRP_EINVAL, "rank + oversample must be >= 1");
+  if (rank > 64 || ell > 128) return set_err(c, LRP_EINVAL, "rank <= 64 and rank+oversample <= 128");
+  cudaSetDevice(c->device);
+  Operator* op = const_cast<lrp_operator*>(opc);
+  const int n = op->n;
+  if (ell > n) return set_err(c, LRP_EINVAL, "rank + oversample exceeds the dimension");
+  auto co = std::make_unique<lrp_coarse>();
+  co->ctx = c;
+  ctx_retain(c);
+  co->op = op;
+  co->dt = dt;
+  co->M = M;
+  co->N = N;
+  co->R = rank;
+  co->p = oversample;
+  co->ell = ell;
+  co->seed = seed;
+  co->prec = prec;
+  const int f32 = prec == LRP_PREC_MIXED;
+  const size_t es = f32 ? 4 : 8;
+  const size_t blk = (size_t)N * ell * n;
+  DevBuf Y, Z, Rw, Rz, rw, rv, sv, Psi, Phi, st, Rid;
+  lrp_status s;
+  if ((s = dev_alloc(c, Y, blk * es))) return s;
+  if ((s = dev_alloc(c, Z, blk * es))) return s;
+  if ((s = dev_alloc(c, Rw, sizeof(double) * N * ell * ell))) return s;
+  if ((s = dev_alloc(c, Rz, sizeof(double) * N * ell * ell))) return s;
+  if ((s = dev_alloc(c, rw, sizeof(int) * N))) return s;
+  if ((s = dev_alloc(c, rv, sizeof(int) * N))) return s;
+  if ((s = dev_alloc(c, sv, sizeof(double) * N * ell))) return s;
+  if ((s = dev_alloc(c, Psi, sizeof(double) * N * ell * ell))) return s;
+  if ((s = dev_alloc(c, Phi, sizeof(double) * N * ell * ell))) return s;
+  if ((s = dev_alloc(c, st, sizeof(int)))) return s;
+  if ((s = dev_alloc(c, Rid, sizeof(int) * N))) return s;
+  cudaMemsetAsync(st.ptr, 0, sizeof(int), c->stream);
+  // step 1: Y = F' Omega, Omega generated in the kernel (N*ell systems)
+  PropIn in;
+  in.gen = 1;
+  in.seed = seed;
+  in.ncol = ell;
+  in.interval0 = 0;
+  PropOut o;
+  o.y = Y.ptr;
+  o.y_f64 = !f32;
+  o.ldy = n;
+  PropSrc nosrc;
+  if ((s = propagate_any(c, op, dt, M, 0, N * ell, f32, in, o, nosrc))) return s;
+  // step 2: W = orth(Y), in place
+  const double tau = f32 ? 2e-5 : 1e-13;
+  if ((s = orth_cgs2(c, N, ell, n, Y.ptr, !f32, tau, Rw.as<double>(), rw.as<int>()))) return s;
+  // step 3: Z = F'^* W
+  PropIn in2;
+  in2.x = Y.ptr;
+  in2.x_f64 = !f32;
+  in2.ldx = n;
+  PropOut o2;
+  o2.y = Z.ptr;
+  o2.y_f64 = !f32;
+  o2.ldy = n;
+  if ((s = propagate_any(c, op, dt, M, 1, N * ell, f32, in2, o2, nosrc))) return s;
+  // step 4: Vh = orth(Z) in place; M_ij = (z_i, v_j) = Rz[j][i]
+  if ((s = orth_cgs2(c, N, ell, n, Z.ptr, !f32, tau, Rz.as<double>(), rv.as<int>()))) return s;
+  // step 5: SVD of M
+  if ((s = small_svd(c, N, ell, Rz.as<double>(), rv.as<int>(), sv.as<double>(), Psi.as<double>(),
+                     Phi.as<double>(), st.as<int>())))
+    return s;
+  // ranks and singular values to the host: R_i, sigma_{R_i+1}, delta, eps
+  co->rank_w.resize(N);
+  co->rank_v.resize(N);
+  co->sigma.resize((size_t)N * ell);
+  int svd_status = 0;
+  cudaMemcpyAsync(co->rank_w.data(), rw.ptr, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(co->rank_v.data(), rv.ptr, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(co->sigma.data(), sv.ptr, sizeof(double) * N * ell, cudaMemcpyDeviceToHost, c->stream);
+  cudaMemcpyAsync(&svd_status, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "build_coarse");
+  if (svd_status) return set_err(c, LRP_ENOTCONV, "Jacobi SVD did not converge");
+  co->Ri.resize(N);
+  co->delta = 0.0;
+  co->eps = 0.0;
+  for (int i = 0; i < N; ++i) {
+    int kk = std::min(co->rank_w[i], co->rank_v[i]);
+    int Ri = std::min(rank, kk);
+    co->Ri[i] = Ri;
+    const double* si = &co->sigma[(size_t)i * ell];
+    for (int r = kk; r < ell; ++r) co->sigma[(size_t)i * ell + r] = 0.0;
+    double s1 = kk > 0 ? si[0] : 0.0;
+    // sigma_{R_i+1} from the oversampled SVD; when deflation left no (R_i+1)-th
+    // value, the dropped directions were below tau * sigma_1
+    double sn = (kk > Ri) ? si[Ri] : tau * s1;
+    co->delta = std::max(co->delta, s1);
+    co->eps = std::max(co->eps, sn);
+  }
+  // step 6: lift the leading R_i singular vectors
+  const int Rm = std::max(rank, 1);
+  if ((s = dev_alloc(c, co->U, sizeof(double) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->V, sizeof(double) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->S, sizeof(double) * N * Rm))) return s;
+  if ((s = dev_alloc(c, co->U32, sizeof(float) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->V32, sizeof(float) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->S32, sizeof(float) * N * Rm))) return s;
+  cudaMemsetAsync(co->U.ptr, 0, co->U.bytes, c->stream);
+  cudaMemsetAsync(co->V.ptr, 0, co->V.bytes, c->stream);
+  cudaMemsetAsync(co->U32.ptr, 0, co->U32.bytes, c->stream);
+  cudaMemsetAsync(co->V32.ptr, 0, co->V32.bytes, c->stream);
+  if ((s = to_device(c, Rid.ptr, co->Ri.data(), sizeof(int) * N))) return s;
+  if ((s = lift(c, N, ell, rank, n, Y.ptr, Z.ptr, !f32, Psi.as<double>(), Phi.as<double>(),
+                Rid.as<int>(), co->U.as<double>(), co->V.as<double>(), co->U32.as<float>(),
+                co->V32.as<float>())))
+    return s;
+  std::vector<double> S64((size_t)N * Rm, 0.0);
+  std::vector<float> S32f((size_t)N * Rm, 0.f);
+  for (int i = 0; i < N; ++i)
+    for (int r = 0; r < co->Ri[i]; ++r) {
+      S64[(size_t)i * Rm + r] = co->sigma[(size_t)i * ell + r];
+      S32f[(size_t)i * Rm + r] = (float)co->sigma[(size_t)i * ell + r];
+    }
+  if ((s = to_device(c, co->S.ptr, S64.data(), S64.size() * 8))) return s;
+  if ((s = to_device(c, co->S32.ptr, S32f.data(), S32f.size() * 4))) return s;
+  e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "build_coarse");
+  *out = co.release();
+  return LRP_OK;
+}
+
+void lrp_coarse_free(lrp_coarse* co) {
+  if (!co) return;
+  cudaSetDevice(co->ctx->device);
+  cudaStreamSynchronize(co->ctx->stream);
+  delete co;
+}
+
+lrp_status lrp_coarse_info(const lrp_coarse* co, int* R_i, int* rank_w, int* rank_v,
+                           double* sigma, double* delta, double* eps) {
+  if (!co) return LRP_EINVAL;
+  const int N = co->N;
+  if (R_i) std::memcpy(R_i, co->Ri.data(), sizeof(int) * N);
+  if (rank_w) std::memcpy(rank_w, co->rank_w.data(), sizeof(int) * N);
+  if (rank_v) std::memcpy(rank_v, co->rank_v.data(), sizeof(int) * N);
+  if (sigma) std::memcpy(sigma, co->sigma.data(), sizeof(double) * N * co->ell);
+  if (delta) *delta = co->delta;
+  if (eps) *eps = co->eps;
+  return LRP_OK;
+}
+
+lrp_status lrp_coarse_factors(const lrp_coarse* co, int interval, double* U, double* S,
+                              double* V) {
+  if (!co || interval < 0 || interval >= co->N) return LRP_EINVAL;
+  Ctx* c = co->ctx;
+  const int n = co->op->n, Rm = std::max(co->R, 1), Ri = co->Ri[interval];
+  size_t off = (size_t)interval * Rm * n;
+  lrp_status s;
+  if (U && (s = from_device(c, U, co->U.as<double>() + off, sizeof(double) * Ri * n))) return s;
+  if (V && (s = from_device(c, V, co->V.as<double>() + off, sizeof(double) * Ri * n))) return s;
+  if (S && (s = from_device(c, S, co->S.as<double>() + (size_t)interval * Rm, sizeof(double) * Ri)))
+    return s;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e ? cuda_err(c, e, "coarse_factors") : LRP_OK;
+}
+
+// ===========================================================================
+// Parareal solve (Eq. def_Parareal in the delta form of Remark rem:affine_g_n)
+// ===========================================================================
+lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u0, int Q,
+                              const double* g, const double* cv, int K_max, double tol,
+                              double* u_out, double* bound_out, int* k_done,
+                              lrp_solve_stats* stats) {
+  if (!c || !coc || !u0 || !u_out || Q < 0 || K_max < 0) return LRP_EINVAL;
+  if (Q > 0 && (!g || !cv)) return LRP_EINVAL;
+  cudaSetDevice(c->device);
+  lrp_coarse* co = const_cast<lrp_coarse*>(coc);
+  Operator* op = const_cast<Operator*>(co->op);
+  const int n = op->n, N = co->N, M = co->M, Rm = std::max(co->R, 1);
+  const int K = std::min(K_max, N);
+  lrp_status s;
+  // workspace
+  if (!co->ws_u.ptr) {
+    if ((s = dev_alloc(c, co->ws_u, sizeof(double) * (size_t)(N + 1) * n))) return s;
+    if ((s = dev_alloc(c, co->ws_F, sizeof(double) * (size_t)N * n))) return s;
+    if ((s = dev_alloc(c, co->ws_b, sizeof(double) * (size_t)N * n))) return s;
+    if ((s = dev_alloc(c, co->ws_d, sizeof(double) * (size_t)n))) return s;
+    if ((s = dev_alloc(c, co->ws_norm, sizeof(double) * (size_t)(3 * (N + 1) + 2)))) return s;
+  }
+  double* du = co->ws_norm.as<double>();
+  double* unorm = du + (N + 1);
+  double* bnd = unorm + (N + 1);
+  double* summ = bnd + (N + 1);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  // inputs
+  if ((s = to_device(c, co->ws_u.ptr, u0, sizeof(double) * n))) return s;
+  DevView gv, cvv;
+  if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * Q, cvv))) return s;
+  const int f32 = co->prec == LRP_PREC_MIXED;
+  // b_i = F_i 0 for all intervals in one launch (Eq. F_n_affine)
+  PropSrc src;
+  src.Q = Q;
+  src.g = (const double*)gv.p;
+  src.c = (const double*)cvv.p;
+  src.cstride = (long)M * Q;
+  int evals = 0;
+  if (Q > 0) {
+    PropIn zin;               // zero initial values
+    zin.x = nullptr;
+    PropOut bo;
+    bo.y = co->ws_b.ptr;
+    bo.ldy = n;
+    cudaMemsetAsync(co->ws_b.ptr, 0, co->ws_b.bytes, c->stream);
+    if ((s = propagate_any(c, op, co->dt, M, 0, N, 0, zin, bo, src))) return s;
+    evals = 1;
+  } else {
+    cudaMemsetAsync(co->ws_b.ptr, 0, co->ws_b.bytes, c->stream);
+  }
+  SweepArgs a;
+  a.N = N;
+  a.n = n;
+  a.R = Rm;
+  a.u = co->ws_u.as<double>();
+  a.U = f32 ? co->U32.ptr : co->U.ptr;
+  a.S = f32 ? co->S32.ptr : co->S.ptr;
+  a.V = f32 ? co->V32.ptr : co->V.ptr;
+  a.f32 = f32;
+  a.dscr = co->ws_d.as<double>();
+  a.delta = co->delta;
+  a.eps = co->eps;
+  a.du = du;
+  a.unorm = unorm;
+  a.summary = summ;
+  // initial coarse sweep u^0_{i+1} = G_i u^0_i
+  a.first = 0;
+  a.initial = 1;
+  a.F = co->ws_b.as<double>();
+  a.bound = nullptr;
+  if ((s = coarse_sweep(c, a))) return s;
+  int k = 0, converged = 0;
+  double hsum[2] = {0.0, 0.0};
+  a.initial = 0;
+  a.F = co->ws_F.as<double>();
+  a.bound = bnd;
+  while (k < K) {
+    const int first = k;            // F u^k_i for i < k equals the previous value
+    PropIn in;
+    in.x = co->ws_u.as<double>() + (size_t)first * n;
+    in.x_f64 = 1;
+    in.ldx = n;
+    PropOut o;
+    o.y = co->ws_F.as<double>() + (size_t)first * n;
+    o.y_f64 = 1;
+    o.ldy = n;
+    PropSrc sk = src;
+    if (Q > 0) sk.c = src.c + (size_t)first * M * Q;
+    if ((s = propagate_any(c, op, co->dt, M, 0, N - first, 0, in, o, sk))) return s;
+    a.first = first;
+    if ((s = coarse_sweep(c, a))) return s;
+    ++k;
+    ++evals;
+    if (bound_out) {
+      if ((s = from_device(c, bound_out + (size_t)(k - 1) * (N + 1), bnd, sizeof(double) * (N + 1))))
+        return s;
+    }
+    cudaError_t e = cudaMemcpyAsync(hsum, summ, sizeof(hsum), cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_err(c, e, "parareal iteration");
+    if (tol > 0 && hsum[0] <= tol * hsum[1]) { converged = 1; break; }
+  }
+  if ((s = from_device(c, u_out, co->ws_u.ptr, sizeof(double) * (size_t)(N + 1) * n))) return s;
+  cudaEventRecord(e1, c->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e) return cuda_err(c, e, "parareal solve");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (k_done) *k_done = k;
+  if (stats) {
+    stats->k_done = k;
+    stats->fine_evals = evals;
+    stats->converged = converged;
+    stats->final_bound = hsum[0];
+    stats->scale = hsum[1];
+    stats->device_ms = ms;
+  }
+  if (tol > 0 && !converged) return set_err(c, LRP_ENOTCONV, "tolerance not met within K_max");
+  return LRP_OK;
+}
+
+lrp_status lrp_fine_solution(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int N,
+                             const double* u0, int Q, const double* g, const double* cv,
+                             double* u_out) {
+  if (!c || !opc || !u0 || !u_out || N < 1 || M < 1 || !(dt > 0) || Q < 0) return LRP_EINVAL;
+  if (Q > 0 && (!g || !cv)) return LRP_EINVAL;
+  cudaSetDevice(c->device);
+  Operator* op = const_cast<lrp_operator*>(opc);
+  const int n = op->n;
+  DevBuf u;
+  lrp_status s;
+  if ((s = dev_alloc(c, u, sizeof(double) * (size_t)(N + 1) * n))) return s;
+  if ((s = to_device(c, u.ptr, u0, sizeof(double) * n))) return s;
+  DevView gv, cvv;
+  if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * Q, cvv))) return s;
+  for (int i = 0; i < N; ++i) {
+    PropIn in;
+    in.x = u.as<double>() + (size_t)i * n;
+    in.ldx = n;
+    PropOut o;
+    o.y = u.as<double>() + (size_t)(i + 1) * n;
+    o.ldy = n;
+    PropSrc src;
+    src.Q = Q;
+    src.g = (const double*)gv.p;
+    src.c = Q > 0 ? (const double*)cvv.p + (size_t)i * M * Q : nullptr;
+    src.cstride = (long)M * Q;
+    if ((s = propagate_any(c, op, dt, M, 0, 1, 0, in, o, src))) return s;
+  }
+  return from_device(c, u_out, u.ptr, sizeof(double) * (size_t)(N + 1) * n);
+}
+
+}  // extern "C"

@@ -1,0 +1,178 @@
+// Internal host-side structures and kernel launchers of the library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/lrp.h"
+
+namespace lrp {
+
+struct Ctx;
+
+// Device allocation owned by a context (counted against its HBM budget).
+struct DevBuf {
+  Ctx* ctx = nullptr;
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf();
+  void release();
+  template <typename T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// Events recorded around the launches of one kernel family.
+struct KernelTimer {
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pairs;
+  int launches = 0;
+  double total_ms = 0.0;
+};
+
+struct Ctx {
+  int device = 0;
+  size_t budget = 0;
+  size_t in_use = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  std::string last_error;
+  bool timing = false;
+  std::map<std::string, KernelTimer> timers;
+  int num_sms = 0;
+  long launches = 0;       // kernels launched by this context (all families)
+  // Handles (operators, coarse solvers) hold a reference; the context is
+  // deleted when lrp_destroy has been called and the last handle is freed.
+  int refs = 1;
+};
+void ctx_retain(Ctx* c);
+void ctx_release(Ctx* c);
+
+// Per-(dt, direction) factorisation of B = I + dt*A (or its transpose) for the
+// partitioned tridiagonal solve: P chunks of m rows, interior Thomas factors,
+// spikes, and the parallel-cyclic-reduction coefficients of the interface
+// system.  Coefficients are stored chunk-minor: entry (row i of chunk t) at
+// i*P + t.  Both FP64 and FP32 copies.
+struct TriPlan {
+  double dt = 0.0;
+  int adjoint = 0;
+  int n = 0, m = 0, P = 0, levels = 0;
+  DevBuf coef64, coef32;   // [5][m][P]: l, inv, u, p, q
+  DevBuf pcr64, pcr32;     // [2*levels + 1][P]: k1 per level, k2 per level, dinv
+  DevBuf status;           // int: 0 ok, 1 zero pivot
+};
+
+struct StencilPlan;
+
+struct Operator {
+  Ctx* ctx = nullptr;
+  ~Operator();
+  int kind = 0;            // 0 tridiagonal, 1 5-point stencil
+  int n = 0, mx = 0, my = 0;
+  DevBuf a64[5];           // tridiagonal: lo, di, up; stencil: C, W, E, S, N
+  DevBuf a32[5];
+  double rtol64 = 1e-12, rtol32 = 1e-6;
+  int max_iter = 20000;
+  std::vector<std::unique_ptr<TriPlan>> plans;
+};
+
+struct Coarse {
+  Ctx* ctx = nullptr;
+  ~Coarse();
+  const Operator* op = nullptr;
+  double dt = 0.0;
+  int M = 0, N = 0, R = 0, p = 0, ell = 0;
+  uint64_t seed = 0;
+  lrp_precision prec = LRP_PREC_F64;
+  DevBuf U, S, V;          // FP64 factors: U, V [N][R][n], S [N][R] (zero padded)
+  DevBuf U32, S32, V32;    // FP32 copies (coarse apply of the mixed mode)
+  std::vector<int> Ri, rank_w, rank_v;
+  std::vector<double> sigma;  // N x ell
+  double delta = 0.0, eps = 0.0;
+  // solve workspace (allocated on first use)
+  DevBuf ws_u, ws_F, ws_b, ws_norm, ws_d, ws_g, ws_c;
+  size_t ws_gc_bytes = 0;
+};
+
+// ---- helpers ---------------------------------------------------------------
+lrp_status set_err(Ctx* c, lrp_status s, const std::string& msg);
+lrp_status cuda_err(Ctx* c, cudaError_t e, const char* where);
+lrp_status dev_alloc(Ctx* c, DevBuf& b, size_t bytes);
+bool is_device_ptr(const void* p);
+void timer_begin(Ctx* c, const char* fam, cudaEvent_t* ev);
+void timer_end(Ctx* c, const char* fam, cudaEvent_t ev);
+
+// ---- tridiagonal propagator (tridiag.cu) -----------------------------------
+lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out);
+
+// Input of a propagation: either vectors in memory or Gaussian sketch vectors
+// generated in the kernel (system s -> interval s / ncol, column s % ncol).
+struct PropIn {
+  const void* x = nullptr;  // nsys x n (row stride ldx), type given by x_f64
+  int x_f64 = 1;
+  long ldx = 0;
+  int gen = 0;              // 1: generate N(0,1) entries instead of reading x
+  uint64_t seed = 0;
+  int ncol = 1;
+  int interval0 = 0;        // interval of system 0 (generated input)
+};
+struct PropOut {
+  void* y = nullptr;        // nsys x n (row stride ldy)
+  int y_f64 = 1;
+  long ldy = 0;
+};
+struct PropSrc {
+  int Q = 0;
+  const double* g = nullptr;   // Q x n (device)
+  const double* c = nullptr;   // per system: c + s*cstride, M x Q (device)
+  long cstride = 0;
+};
+
+// prec: 0 FP64, 1 FP32 arithmetic.
+lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, int prec,
+                         const PropIn& in, const PropOut& out, const PropSrc& src);
+
+// ---- orthonormalisation, small SVD, lift (linalg.cu) -----------------------
+// CGS2 with deflation of every interval's ell x n block (rows = vectors), in
+// place.  Kept vectors are compacted to the front, dropped rows zeroed.
+// Rcoef [N][ell][ell] (FP64): Rcoef[c][j] = coefficient of basis vector c in
+// input vector j.  rank[N] (device int).
+lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau,
+                     double* Rcoef, int* rank);
+// One-sided Jacobi SVD of M_i = Rz_i^T (ell x ell) for every interval.
+// Outputs: s [N][ell] descending, Psi [N][ell][ell] (column r = left vector r,
+// stored Psi[i*ell + r]), Phi [N][ell][ell] likewise; status (int) 0/1.
+lrp_status small_svd(Ctx* c, int N, int ell, const double* Rz, const int* rank_v, double* s,
+                     double* Psi, double* Phi, int* status);
+// U_i[r] = sum_j Psi[j][r] W_i[j], V_i[r] = sum_j Phi[j][r] Vh_i[j], r < R.
+lrp_status lift(Ctx* c, int N, int ell, int R, int n, const void* W, const void* Vh, int b_f64,
+                const double* Psi, const double* Phi, const int* Ri, double* U, double* V,
+                float* U32, float* V32);
+
+lrp_status gaussian(Ctx* c, uint64_t seed, int interval, int ncol, int n, int f32, double* out);
+
+// ---- coarse sweep (sweep.cu) ------------------------------------------------
+struct SweepArgs {
+  int N = 0, n = 0, R = 0;
+  int first = 0;                  // interval where the sweep starts (delta = 0 there)
+  double* u = nullptr;            // (N+1) x n, in place: u^{k-1} -> u^k
+  const double* F = nullptr;      // N x n: F_i u^{k-1}_i (or b_i for the initial sweep)
+  const void* U = nullptr;        // [N][R][n] (FP64, or FP32 when f32 = 1)
+  const void* S = nullptr;        // [N][R]
+  const void* V = nullptr;        // [N][R][n]
+  int f32 = 0;                    // coarse apply G'delta in FP32 (mixed mode)
+  double* dscr = nullptr;         // n: delta scratch
+  int initial = 0;                // 1: u^{-1} := 0 (initial coarse sweep)
+  double delta = 0.0, eps = 0.0;
+  double* du = nullptr;           // N+1: ||u^k_m - u^{k-1}_m||
+  double* unorm = nullptr;        // N+1: ||u^k_m||
+  double* bound = nullptr;        // N+1: a posteriori bound (Eq. apost_bound)
+  double* summary = nullptr;      // [0] = max bound, [1] = max ||u^k_m||
+};
+lrp_status coarse_sweep(Ctx* c, const SweepArgs& a);
+
+}  // namespace lrp

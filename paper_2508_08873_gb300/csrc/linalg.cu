@@ -1,0 +1,318 @@
+// Randomized-SVD finishing steps (Sec. 2.1, steps 2, 4, 5, 6):
+//   * orthonormal bases of the sketches by classical Gram-Schmidt applied twice
+//     ("twice is enough") with deflation of numerically dependent vectors;
+//   * the small matrix M_ij = (F'^* w_i, v_j) read off the Gram-Schmidt
+//     coefficients of the adjoint sketch, and its SVD by one-sided Jacobi
+//     (Hestenes) in FP64 with a round-robin pair ordering;
+//   * the lift of the leading R singular vectors to the bases.
+// One CTA per coarse interval for the orthonormalisation and the SVD; the lift
+// runs over (interval, row block).
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrp {
+
+// ---------------------------------------------------------------------------
+// CGS2 with deflation.  X: N blocks of ell rows of length n (row = vector).
+// For input vector j: h = Q^T v, v -= Q h, twice; Rcoef[c][j] accumulates h;
+// keep v / ||v|| as the next basis vector when ||v|| > tau * ||y_j||.
+// ---------------------------------------------------------------------------
+constexpr int ORTH_THREADS = 512;
+
+template <typename T>
+__device__ double block_sum(T v, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double d = warp_sum<double>((double)v);
+  __syncthreads();
+  if (lane == 0) red[w] = d;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(ORTH_THREADS) k_cgs2(int ell, int n, T* __restrict__ X,
+                                                        double tau, double* __restrict__ Rcoef,
+                                                        int* __restrict__ rank) {
+  extern __shared__ double sm[];
+  const int nw = blockDim.x >> 5;
+  double* red = sm;                 // [ell][nw] partial dots
+  double* h = red + ell * nw;       // [ell]
+  double* red1 = h + ell;           // [nw]
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  T* B = X + (size_t)blockIdx.x * ell * n;
+  double* Rc = Rcoef + (size_t)blockIdx.x * ell * ell;
+  for (int k = threadIdx.x; k < ell * ell; k += blockDim.x) Rc[k] = 0.0;
+  int r = 0;
+  for (int j = 0; j < ell; ++j) {
+    T* v = B + (size_t)j * n;
+    T acc = T(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * v[i];
+    double nrm0 = sqrt(block_sum(acc, red1));
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int c = 0; c < r; ++c) {
+        const T* q = B + (size_t)c * n;
+        T pc = T(0);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) pc += q[i] * v[i];
+        double d = warp_sum<double>((double)pc);
+        if (lane == 0) red[c * nw + w] = d;
+      }
+      __syncthreads();
+      if (threadIdx.x < r) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += red[threadIdx.x * nw + i];
+        h[threadIdx.x] = s;
+        Rc[threadIdx.x * ell + j] += s;
+      }
+      __syncthreads();
+      for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        T s = v[i];
+        for (int c = 0; c < r; ++c) s -= (T)h[c] * B[(size_t)c * n + i];
+        v[i] = s;
+      }
+      __syncthreads();
+    }
+    acc = T(0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * v[i];
+    double nrm = sqrt(block_sum(acc, red1));
+    if (nrm0 > 0.0 && nrm > tau * nrm0) {
+      T inv = (T)(1.0 / nrm);
+      T* q = B + (size_t)r * n;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) q[i] = v[i] * inv;
+      if (threadIdx.x == 0) Rc[r * ell + j] = nrm;
+      ++r;
+    }
+    __syncthreads();
+  }
+  for (int c = r; c < ell; ++c)
+    for (int i = threadIdx.x; i < n; i += blockDim.x) B[(size_t)c * n + i] = T(0);
+  if (threadIdx.x == 0) rank[blockIdx.x] = r;
+}
+
+lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau,
+                     double* Rcoef, int* rank) {
+  if (N <= 0) return LRP_OK;
+  const int nw = ORTH_THREADS / 32;
+  size_t smem = sizeof(double) * ((size_t)ell * nw + ell + nw);
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "orth", &ev);
+  if (x_f64)
+    k_cgs2<double><<<N, ORTH_THREADS, smem, c->stream>>>(ell, n, (double*)X, tau, Rcoef, rank);
+  else
+    k_cgs2<float><<<N, ORTH_THREADS, smem, c->stream>>>(ell, n, (float*)X, tau, Rcoef, rank);
+  cudaError_t e = cudaGetLastError();
+  timer_end(c, "orth", ev);
+  return e ? cuda_err(c, e, "k_cgs2") : LRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One-sided Jacobi SVD of M (ell rows x kv columns), M[i][c] = Rz[c][i].
+// Column pairs are rotated in round-robin order, one warp per pair, until a
+// full sweep performs no rotation (|a_p.a_q| <= eps sqrt(|a_p|^2 |a_q|^2)).
+// ---------------------------------------------------------------------------
+constexpr int SVD_THREADS = 256;
+constexpr int SVD_MAX_SWEEPS = 60;
+
+__global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* __restrict__ Rz,
+                                                         const int* __restrict__ rank_v,
+                                                         double* __restrict__ s_out,
+                                                         double* __restrict__ Psi,
+                                                         double* __restrict__ Phi,
+                                                         int* __restrict__ status) {
+  extern __shared__ double sm[];
+  const int iv = blockIdx.x;
+  const int kv = rank_v[iv];
+  const int m = ell;
+  double* A = sm;                     // [kv][m] column-major (column c at c*m)
+  double* Vw = A + (size_t)ell * m;   // [kv][kv] (column c at c*ell)
+  double* nrm = Vw + (size_t)ell * ell;
+  int* order = reinterpret_cast<int*>(nrm + ell);
+  __shared__ int rotated;
+  const double* Rzi = Rz + (size_t)iv * ell * ell;
+  for (int k = threadIdx.x; k < ell * m; k += blockDim.x) {
+    int c = k / m, i = k % m;
+    A[k] = (c < kv) ? Rzi[(size_t)c * ell + i] : 0.0;
+  }
+  for (int k = threadIdx.x; k < ell * ell; k += blockDim.x)
+    Vw[k] = ((k / ell) == (k % ell)) ? 1.0 : 0.0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int kp = kv + (kv & 1);       // players, padded to even
+  const double eps = 2.220446049250313e-16;
+  int sweep = 0, done = (kv < 2);
+  while (!done && sweep < SVD_MAX_SWEEPS) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int rd = 0; rd < kp - 1; ++rd) {
+      for (int pi = w; pi < kp / 2; pi += nw) {
+        int p, q;
+        if (pi == 0) { p = kp - 1; q = rd; }
+        else { p = (rd + pi) % (kp - 1); q = (rd - pi + (kp - 1)) % (kp - 1); }
+        if (p > q) { int tmp = p; p = q; q = tmp; }
+        if (q >= kv) continue;
+        double* ap = A + (size_t)p * m;
+        double* aq = A + (size_t)q * m;
+        double al = 0, be = 0, ga = 0;
+        for (int i = lane; i < m; i += 32) {
+          al += ap[i] * ap[i];
+          be += aq[i] * aq[i];
+          ga += ap[i] * aq[i];
+        }
+        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        if (ga == 0.0 || fabs(ga) <= eps * sqrt(al * be)) continue;
+        double zeta = (be - al) / (2.0 * ga);
+        double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        double cs = 1.0 / sqrt(1.0 + tt * tt);
+        double sn = cs * tt;
+        for (int i = lane; i < m; i += 32) {
+          double x = ap[i], y = aq[i];
+          ap[i] = cs * x - sn * y;
+          aq[i] = sn * x + cs * y;
+        }
+        double* vp = Vw + (size_t)p * ell;
+        double* vq = Vw + (size_t)q * ell;
+        for (int i = lane; i < kv; i += 32) {
+          double x = vp[i], y = vq[i];
+          vp[i] = cs * x - sn * y;
+          vq[i] = sn * x + cs * y;
+        }
+        if (lane == 0) rotated = 1;
+      }
+      __syncthreads();
+    }
+    ++sweep;
+    done = !rotated;
+    __syncthreads();
+  }
+  // singular values and descending order
+  for (int c = threadIdx.x; c < ell; c += blockDim.x) {
+    double t = 0.0;
+    if (c < kv)
+      for (int i = 0; i < m; ++i) t += A[(size_t)c * m + i] * A[(size_t)c * m + i];
+    nrm[c] = sqrt(t);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int c = 0; c < ell; ++c) order[c] = c;
+    for (int a = 0; a < kv; ++a)
+      for (int b = a + 1; b < kv; ++b)
+        if (nrm[order[b]] > nrm[order[a]]) { int t = order[a]; order[a] = order[b]; order[b] = t; }
+    if (!done) atomicOr(status, 1);
+  }
+  __syncthreads();
+  double* so = s_out + (size_t)iv * ell;
+  double* Ps = Psi + (size_t)iv * ell * ell;
+  double* Ph = Phi + (size_t)iv * ell * ell;
+  for (int k = threadIdx.x; k < ell * ell; k += blockDim.x) {
+    int r = k / ell, i = k % ell;          // column r of the outputs
+    double val_psi = 0.0, val_phi = 0.0;
+    if (r < kv) {
+      int c = order[r];
+      double sc = nrm[c];
+      val_psi = sc > 0.0 ? A[(size_t)c * m + i] / sc : 0.0;
+      val_phi = (i < kv) ? Vw[(size_t)c * ell + i] : 0.0;
+    }
+    Ps[k] = val_psi;
+    Ph[k] = val_phi;
+  }
+  for (int r = threadIdx.x; r < ell; r += blockDim.x) so[r] = (r < kv) ? nrm[order[r]] : 0.0;
+}
+
+lrp_status small_svd(Ctx* c, int N, int ell, const double* Rz, const int* rank_v, double* s,
+                     double* Psi, double* Phi, int* status) {
+  if (N <= 0) return LRP_OK;
+  size_t smem = sizeof(double) * ((size_t)2 * ell * ell + ell) + sizeof(int) * ell;
+  cudaError_t e = cudaFuncSetAttribute(k_jacobi, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return cuda_err(c, e, "jacobi smem");
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "svd", &ev);
+  k_jacobi<<<N, SVD_THREADS, smem, c->stream>>>(ell, Rz, rank_v, s, Psi, Phi, status);
+  e = cudaGetLastError();
+  timer_end(c, "svd", ev);
+  return e ? cuda_err(c, e, "k_jacobi") : LRP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Lift: U_i[r] = sum_j Psi_i[r][j] W_i[j], V_i[r] = sum_j Phi_i[r][j] Vh_i[j]
+// for r < R_i (zero rows beyond).  grid = (row blocks, N).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_lift(int ell, int R, int n, const T* __restrict__ W, const T* __restrict__ Vh,
+                       const double* __restrict__ Psi, const double* __restrict__ Phi,
+                       const int* __restrict__ Ri, double* __restrict__ U, double* __restrict__ V,
+                       float* __restrict__ U32, float* __restrict__ V32) {
+  extern __shared__ double sm[];
+  const int iv = blockIdx.y;
+  double* sPsi = sm;                  // [R][ell]
+  double* sPhi = sm + (size_t)R * ell;
+  const int rk = Ri[iv];
+  for (int k = threadIdx.x; k < R * ell; k += blockDim.x) {
+    sPsi[k] = Psi[(size_t)iv * ell * ell + k];
+    sPhi[k] = Phi[(size_t)iv * ell * ell + k];
+  }
+  __syncthreads();
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n) return;
+  const T* Wi = W + (size_t)iv * ell * n;
+  const T* Vi = Vh + (size_t)iv * ell * n;
+  for (int r = 0; r < R; ++r) {
+    double u = 0.0, v = 0.0;
+    if (r < rk) {
+      for (int j = 0; j < ell; ++j) {
+        u += sPsi[r * ell + j] * (double)Wi[(size_t)j * n + row];
+        v += sPhi[r * ell + j] * (double)Vi[(size_t)j * n + row];
+      }
+    }
+    size_t o = ((size_t)iv * R + r) * n + row;
+    U[o] = u;
+    V[o] = v;
+    U32[o] = (float)u;
+    V32[o] = (float)v;
+  }
+}
+
+lrp_status lift(Ctx* c, int N, int ell, int R, int n, const void* W, const void* Vh, int b_f64,
+                const double* Psi, const double* Phi, const int* Ri, double* U, double* V,
+                float* U32, float* V32) {
+  if (N <= 0 || R <= 0) return LRP_OK;
+  dim3 grid((n + 255) / 256, N);
+  size_t smem = sizeof(double) * 2 * (size_t)R * ell;
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "lift", &ev);
+  if (b_f64)
+    k_lift<double><<<grid, 256, smem, c->stream>>>(ell, R, n, (const double*)W, (const double*)Vh,
+                                                   Psi, Phi, Ri, U, V, U32, V32);
+  else
+    k_lift<float><<<grid, 256, smem, c->stream>>>(ell, R, n, (const float*)W, (const float*)Vh,
+                                                  Psi, Phi, Ri, U, V, U32, V32);
+  cudaError_t e = cudaGetLastError();
+  timer_end(c, "lift", ev);
+  return e ? cuda_err(c, e, "k_lift") : LRP_OK;
+}
+
+// Sketch vectors of one interval, written as doubles.
+template <typename T>
+__global__ void k_gaussian(uint64_t seed, int interval, int ncol, int n, double* out) {
+  long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= (long)ncol * n) return;
+  int col = (int)(k / n), row = (int)(k % n);
+  out[k] = (double)gauss<T>(seed, 0u, (uint32_t)interval, (uint32_t)col, (uint32_t)row);
+}
+
+lrp_status gaussian(Ctx* c, uint64_t seed, int interval, int ncol, int n, int f32, double* out) {
+  long tot = (long)ncol * n;
+  if (tot <= 0) return LRP_OK;
+  int blocks = (int)((tot + 255) / 256);
+  if (f32)
+    k_gaussian<float><<<blocks, 256, 0, c->stream>>>(seed, interval, ncol, n, out);
+  else
+    k_gaussian<double><<<blocks, 256, 0, c->stream>>>(seed, interval, ncol, n, out);
+  cudaError_t e = cudaGetLastError();
+  return e ? cuda_err(c, e, "k_gaussian") : LRP_OK;
+}
+
+}  // namespace lrp

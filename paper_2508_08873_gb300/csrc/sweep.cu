@@ -1,0 +1,187 @@
+// Sequential coarse sweep fused with the Parareal correction, in the delta
+// form of Remark rem:affine_g_n:
+//   u^k_{i+1} = F_i u^{k-1}_i + G_i'(u^k_i - u^{k-1}_i),  G_i' = U_i diag(S_i) V_i^T,
+// and, for the initial sweep, u^0_{i+1} = b_i + G_i' u^0_i (Eq. def_Parareal
+// with u^{-1} := 0).  The iterate is updated in place; the norms
+// ||u^k_m - u^{k-1}_m|| and ||u^k_m|| are recorded on the way and the a
+// posteriori bound eps sum_{m<n} delta^{n-m-1} ||u^k_m - u^{k-1}_m||
+// (Eq. apost_bound) is evaluated by its recurrence B_n = delta B_{n-1} +
+// eps ||u^k_{n-1} - u^{k-1}_{n-1}|| at the end.
+//
+// The sweep is sequential over intervals but each step is two skinny products
+// with n x R factors, so one problem runs on a thread-block cluster: every CTA
+// owns a contiguous slice of the n rows, computes partial V_i^T delta for its
+// slice, and the partial sums are exchanged through distributed shared memory
+// with one cluster barrier per interval (double-buffered).  All CTAs add the
+// partials in the same order, so the result does not depend on timing.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace lrp {
+
+constexpr int SWEEP_THREADS = 256;
+constexpr int SWEEP_MAXR = 64;
+constexpr int SWEEP_MAXCS = 16;
+constexpr int SWEEP_MAXROWS = 20480;     // rows per CTA (delta kept in shared memory)
+
+template <typename TF>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int crank = (int)cl.block_rank();
+  const int cs = (int)cl.num_blocks();
+  const int n = a.n, R = a.R, N = a.N;
+  const int nv = R + 2;                                 // R dots, ||delta||^2, ||u||^2
+  extern __shared__ double dsm[];                       // delta of this CTA's rows
+  __shared__ double part[2][SWEEP_MAXR + 2];
+  __shared__ double red[SWEEP_THREADS / 32][SWEEP_MAXR + 2];
+  __shared__ double gath[SWEEP_MAXCS][SWEEP_MAXR + 2];
+  __shared__ double coef[SWEEP_MAXR + 2];
+  const int per = (n + cs - 1) / cs;
+  const int lo = crank * per, hi = min(n, lo + per), rows = max(0, hi - lo);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const TF* U = static_cast<const TF*>(a.U);
+  const TF* S = static_cast<const TF*>(a.S);
+  const TF* V = static_cast<const TF*>(a.V);
+  // delta at the first interval: 0 (u^k_first == u^{k-1}_first), or u0 initially
+  for (int i = threadIdx.x; i < rows; i += blockDim.x)
+    dsm[i] = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
+  if (crank == 0 && threadIdx.x == 0 && !a.initial)
+    for (int m = 0; m <= a.first; ++m) a.du[m] = 0.0;
+  __syncthreads();
+  int buf = 0;
+  for (int iv = a.first; iv <= N; ++iv) {
+    // ---- partial reductions over this CTA's rows ---------------------------
+    const double* ui = a.u + (size_t)iv * n + lo;
+    double acc_d = 0.0, acc_u = 0.0;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      double d = dsm[i];
+      acc_d += d * d;
+      acc_u += ui[i] * ui[i];
+    }
+    acc_d = warp_sum(acc_d);
+    acc_u = warp_sum(acc_u);
+    if (lane == 0) { red[w][R] = acc_d; red[w][R + 1] = acc_u; }
+    if (iv < N) {
+      // one warp per factor row r: (V_iv[r], delta) over this CTA's rows
+      const TF* Vi = V + (size_t)iv * R * n + lo;
+      for (int r = w; r < R; r += nw) {
+        const TF* vr = Vi + (size_t)r * n;
+        TF pr = TF(0);
+        for (int i = lane; i < rows; i += 32) pr += vr[i] * (TF)dsm[i];
+        double d = warp_sum((double)pr);
+        if (lane == 0) part[buf][r] = d;   // this CTA's partial dot (single writer)
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      double s = 0.0;
+      for (int k = 0; k < nw; ++k) s += red[k][R + threadIdx.x];
+      part[buf][R + threadIdx.x] = s;
+    }
+    cl.sync();
+    // ---- gather the partials of all CTAs with one remote read each ---------
+    for (int k = threadIdx.x; k < cs * nv; k += blockDim.x) {
+      int q = k / nv, j = k % nv;
+      if (iv < N || j >= R) {
+        const double* rp = cl.map_shared_rank(&part[buf][0], q);
+        gath[q][j] = rp[j];
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) {
+      double s = 0.0;
+      if (iv < N || threadIdx.x >= R)
+        for (int q = 0; q < cs; ++q) s += gath[q][threadIdx.x];    // same order in every CTA
+      coef[threadIdx.x] = s;
+    }
+    __syncthreads();
+    if (crank == 0 && threadIdx.x == 0) {
+      if (iv > a.first || a.initial) a.du[iv] = sqrt(coef[R]);
+      a.unorm[iv] = sqrt(coef[R + 1]);
+    }
+    if (iv == N) break;
+    // ---- u^k_{iv+1} = F_iv + U_iv (S_iv * c) on this CTA's rows ------------
+    const TF* Ui = U + (size_t)iv * R * n + lo;
+    const TF* Si = S + (size_t)iv * R;
+    const double* Fi = a.F + (size_t)iv * n + lo;
+    double* un = a.u + (size_t)(iv + 1) * n + lo;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      TF g = TF(0);
+      for (int r = 0; r < R; ++r) g += Ui[(size_t)r * n + i] * (Si[r] * (TF)coef[r]);
+      double nv_ = Fi[i] + (double)g;
+      double old = a.initial ? 0.0 : un[i];
+      dsm[i] = nv_ - old;
+      un[i] = nv_;
+    }
+    buf ^= 1;
+    __syncthreads();
+  }
+  // ---- bound recurrence and summary (one thread) ------------------------------
+  if (crank == 0 && threadIdx.x == 0) {
+    double B = 0.0, bmax = 0.0, umax = 0.0;
+    for (int m = 0; m <= N; ++m) umax = fmax(umax, a.unorm[m]);
+    if (a.bound) {
+      a.bound[0] = 0.0;
+      for (int m = 1; m <= N; ++m) {
+        B = a.delta * B + a.eps * a.du[m - 1];
+        a.bound[m] = B;
+        bmax = fmax(bmax, B);
+      }
+    }
+    a.summary[0] = bmax;
+    a.summary[1] = umax;
+  }
+  cl.sync();  // no CTA leaves while its shared memory may still be read
+}
+
+lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
+  if (a.R > SWEEP_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
+  if ((a.n + SWEEP_MAXCS - 1) / SWEEP_MAXCS > SWEEP_MAXROWS)
+    return set_err(c, LRP_EINVAL, "state dimension too large for the coarse sweep");
+  int cs = 16;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  auto kern = a.f32 ? (void (*)(SweepArgs))k_sweep<float> : (void (*)(SweepArgs))k_sweep<double>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e) { cudaGetLastError(); cs = 8; }
+  // small problems: fewer CTAs per cluster
+  while (cs > 1 && (a.n + cs - 1) / cs < 64) cs >>= 1;
+  size_t dyn = sizeof(double) * (size_t)((a.n + cs - 1) / cs);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(sizeof(double) * SWEEP_MAXROWS));
+  if (e) return cuda_err(c, e, "sweep smem attribute");
+  cfg.gridDim = dim3(cs);
+  cfg.blockDim = dim3(SWEEP_THREADS);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = c->stream;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "sweep", &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  timer_end(c, "sweep", ev);
+  if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
+    // retry with a portable cluster size
+    cudaGetLastError();
+    cs = std::min(cs, 8);
+    cfg.gridDim = dim3(cs);
+    cfg.dynamicSmemBytes = sizeof(double) * (size_t)((a.n + cs - 1) / cs);
+    attr[0].val.clusterDim.x = cs;
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+  }
+  if (e) return cuda_err(c, e, "k_sweep launch");
+  return LRP_OK;
+}
+
+}  // namespace lrp

@@ -1,0 +1,392 @@
+// Batched backward-Euler propagator for tridiagonal operators (the fine solver
+// F_i, its linear part F_i' and adjoint F_i'^* of Sec. 2 / Sec. 4).
+//
+// Every implicit-Euler step solves (I + dt A) x_{j+1} = x_j + dt f(t_{j+1}).
+// The matrix is the same for every step, interval and right-hand side, so it is
+// factored once per (dt, direction) into a partitioned form and the per-step
+// work is pure substitution:
+//   * the n rows are cut into P chunks of m rows; the last row of each chunk is
+//     an interface unknown y_t, the other m-1 rows are interior;
+//   * interior rows: Thomas forward/backward substitution with precomputed
+//     multipliers, giving g = A_int^{-1} d, and the precomputed "spikes" p, q
+//     with x_int = g - p y_{t-1} - q y_t;
+//   * the interface unknowns satisfy a P x P tridiagonal system whose matrix is
+//     fixed; it is solved by parallel cyclic reduction with precomputed
+//     elimination factors (log2 P levels of r_t -= k1 r_{t-s} + k2 r_{t+s}).
+// One thread owns one chunk and keeps its m state values in registers for all
+// M steps; only 2 values per thread cross shared memory per PCR level.  The
+// factorisation is Gaussian elimination without pivoting, valid for the
+// diagonally dominant I + dt A of the parabolic operators targeted here.
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrp {
+
+// ---------------------------------------------------------------------------
+// Factorisation (one CTA of P threads, FP64).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double b_lo(const double* lo, const double* up, int n, double dt,
+                                       int adj, int r) {
+  if (r <= 0 || r >= n) return 0.0;
+  return dt * (adj ? up[r - 1] : lo[r]);
+}
+__device__ __forceinline__ double b_di(const double* di, int n, double dt, int r) {
+  return r < n ? 1.0 + dt * di[r] : 1.0;
+}
+__device__ __forceinline__ double b_up(const double* lo, const double* up, int n, double dt,
+                                       int adj, int r) {
+  if (r >= n - 1) return 0.0;
+  return dt * (adj ? lo[r + 1] : up[r]);
+}
+
+__global__ void k_tri_factor(const double* __restrict__ lo, const double* __restrict__ di,
+                             const double* __restrict__ up, int n, double dt, int adj, int m,
+                             int P, int L, double* __restrict__ coef, float* __restrict__ coef32,
+                             double* __restrict__ pcr, float* __restrict__ pcr32,
+                             int* __restrict__ status) {
+  extern __shared__ double sh[];
+  double* sa = sh;            // alpha
+  double* sb = sa + P;        // beta
+  double* sc = sb + P;        // gamma
+  double* sp0 = sc + P;       // p_t[0]
+  double* sq0 = sp0 + P;      // q_t[0]
+  const int t = threadIdx.x;
+  const int mi = m - 1;       // interior rows
+  const size_t MP = (size_t)m * P;
+  double* cl = coef;
+  double* cinv = coef + MP;
+  double* cu = coef + 2 * MP;
+  double* cp = coef + 3 * MP;
+  double* cq = coef + 4 * MP;
+  int bad = 0;
+  double pl = 0.0, ql = 0.0, aE = 0.0, bE = 1.0, cE = 0.0;
+  if (t < P) {
+    const int r0 = t * m;
+    // interior block: rows r0 .. r0+mi-1; eliminate without pivoting
+    double piv = b_di(di, n, dt, r0);
+    if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = 1;
+    cl[t] = 0.0;
+    cinv[t] = 1.0 / piv;
+    for (int i = 1; i < mi; ++i) {
+      int r = r0 + i;
+      double mult = b_lo(lo, up, n, dt, adj, r) / piv;
+      double bu_prev = b_up(lo, up, n, dt, adj, r - 1);
+      piv = b_di(di, n, dt, r) - mult * bu_prev;
+      if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = 1;
+      cl[(size_t)i * P + t] = mult;
+      cinv[(size_t)i * P + t] = 1.0 / piv;
+    }
+    for (int i = 0; i < mi; ++i)
+      cu[(size_t)i * P + t] = (i < mi - 1) ? b_up(lo, up, n, dt, adj, r0 + i) * cinv[(size_t)i * P + t] : 0.0;
+    // spikes: A_int p = bl(r0) e_0, A_int q = bu(r0+mi-1) e_{mi-1}
+    const double left = b_lo(lo, up, n, dt, adj, r0);
+    const double right = b_up(lo, up, n, dt, adj, r0 + mi - 1);
+    double fp = left, fq = 0.0;           // forward elimination of both RHS
+    cp[t] = fp;
+    cq[t] = (mi == 1) ? right : 0.0;
+    for (int i = 1; i < mi; ++i) {
+      double mult = cl[(size_t)i * P + t];
+      fp = 0.0 - mult * fp;
+      fq = ((i == mi - 1) ? right : 0.0) - mult * fq;
+      cp[(size_t)i * P + t] = fp;
+      cq[(size_t)i * P + t] = fq;
+    }
+    double gp = 0.0, gq = 0.0;            // backward substitution
+    for (int i = mi - 1; i >= 0; --i) {
+      size_t k = (size_t)i * P + t;
+      gp = cp[k] * cinv[k] - cu[k] * gp;
+      gq = cq[k] * cinv[k] - cu[k] * gq;
+      cp[k] = gp;
+      cq[k] = gq;
+    }
+    pl = cp[(size_t)(mi - 1) * P + t];
+    ql = cq[(size_t)(mi - 1) * P + t];
+    const int e = r0 + mi;                // interface row
+    aE = b_lo(lo, up, n, dt, adj, e);
+    bE = b_di(di, n, dt, e);
+    cE = b_up(lo, up, n, dt, adj, e);
+    size_t k = (size_t)mi * P + t;
+    cl[k] = aE;
+    cinv[k] = bE;
+    cu[k] = cE;
+    cp[k] = 0.0;
+    cq[k] = 0.0;
+    sp0[t] = cp[t];
+    sq0[t] = cq[t];
+  }
+  __syncthreads();
+  if (t < P) {
+    double pn = (t + 1 < P) ? sp0[t + 1] : 0.0;
+    double qn = (t + 1 < P) ? sq0[t + 1] : 0.0;
+    sa[t] = -aE * pl;
+    sb[t] = bE - aE * ql - cE * pn;
+    sc[t] = -cE * qn;
+  }
+  __syncthreads();
+  // parallel cyclic reduction of the interface system: precompute factors
+  for (int lev = 0, s = 1; lev < L; ++lev, s <<= 1) {
+    double a = 0, b = 1, c = 0, k1 = 0, k2 = 0, na = 0, nb = 1, nc = 0;
+    if (t < P) {
+      a = sa[t]; b = sb[t]; c = sc[t];
+      double a1 = 0, b1 = 1, c1 = 0, a2 = 0, b2 = 1, c2 = 0;
+      if (t - s >= 0) { a1 = sa[t - s]; b1 = sb[t - s]; c1 = sc[t - s]; }
+      if (t + s < P) { a2 = sa[t + s]; b2 = sb[t + s]; c2 = sc[t + s]; }
+      k1 = (t - s >= 0) ? a / b1 : 0.0;
+      k2 = (t + s < P) ? c / b2 : 0.0;
+      na = -k1 * a1;
+      nc = -k2 * c2;
+      nb = b - k1 * c1 - k2 * a2;
+      if (!(fabs(nb) > 0.0) || !isfinite(nb)) bad = 1;
+      pcr[(size_t)lev * P + t] = k1;
+      pcr[(size_t)(L + lev) * P + t] = k2;
+    }
+    __syncthreads();
+    if (t < P) { sa[t] = na; sb[t] = nb; sc[t] = nc; }
+    __syncthreads();
+  }
+  if (t < P) pcr[(size_t)(2 * L) * P + t] = 1.0 / sb[t];
+  __syncthreads();
+  // FP32 copies
+  for (size_t k = t; k < 5 * MP; k += blockDim.x) coef32[k] = (float)coef[k];
+  for (size_t k = t; k < (size_t)(2 * L + 1) * P; k += blockDim.x) pcr32[k] = (float)pcr[k];
+  if (bad) atomicOr(status, 1);
+}
+
+// ---------------------------------------------------------------------------
+// Propagation kernel.  blockDim.x = P * G: G systems per CTA, one chunk per
+// thread.  Systems are visited grid-stride; all threads take part in every
+// barrier (inactive slots compute on zeros and do not store).
+// ---------------------------------------------------------------------------
+struct TriKArgs {
+  int n, P, L, G, M, nsys;
+  double dt;
+  const void* coef;
+  const void* pcr;
+  PropIn in;
+  PropOut out;
+  PropSrc src;
+};
+
+template <typename T, int MM>
+__global__ void __launch_bounds__(1024) k_tri_propagate(TriKArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* s_coef = reinterpret_cast<T*>(smem_raw);                 // [5][MM][P]
+  const int P = a.P, L = a.L, G = a.G;
+  T* s_pcr = s_coef + 5 * MM * P;                             // [2L+1][P]
+  T* s_x = s_pcr + (2 * L + 1) * P;                           // [G][3][P]
+  const int nco = 5 * MM * P, npc = (2 * L + 1) * P;
+  const T* gco = static_cast<const T*>(a.coef);
+  const T* gpc = static_cast<const T*>(a.pcr);
+  for (int k = threadIdx.x; k < nco; k += blockDim.x) s_coef[k] = gco[k];
+  for (int k = threadIdx.x; k < npc; k += blockDim.x) s_pcr[k] = gpc[k];
+  __syncthreads();
+
+  const int t = threadIdx.x % P;
+  const int gslot = threadIdx.x / P;
+  T* xb = s_x + (size_t)gslot * 3 * P;
+  const T* cl = s_coef;
+  const T* ci = s_coef + MM * P;
+  const T* cu = s_coef + 2 * MM * P;
+  const T* cp = s_coef + 3 * MM * P;
+  const T* cq = s_coef + 4 * MM * P;
+  const T dt = (T)a.dt;
+  const int n = a.n;
+  const int r0 = t * MM;
+
+  for (int base = blockIdx.x * G; base < a.nsys; base += gridDim.x * G) {
+    const int sys = base + gslot;
+    const bool active = sys < a.nsys;
+    T x[MM];
+    // ---- load the initial vector ---------------------------------------
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      int r = r0 + i;
+      T v = T(0);
+      if (active && r < n) {
+        if (a.in.gen) {
+          v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                       (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+        } else if (a.in.x == nullptr) {
+          v = T(0);                                   // zero initial value (b_i = F_i 0)
+        } else if (a.in.x_f64) {
+          v = (T) static_cast<const double*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+        } else {
+          v = (T) static_cast<const float*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+        }
+      }
+      x[i] = v;
+    }
+    const double* csys = (active && a.src.Q > 0) ? a.src.c + (size_t)sys * a.src.cstride : nullptr;
+    // ---- M implicit-Euler steps ------------------------------------------
+    for (int j = 0; j < a.M; ++j) {
+      if (csys) {
+        for (int q = 0; q < a.src.Q; ++q) {
+          T cq_ = dt * (T)csys[(size_t)j * a.src.Q + q];
+          const double* gq = a.src.g + (size_t)q * n;
+#pragma unroll
+          for (int i = 0; i < MM; ++i) {
+            int r = r0 + i;
+            if (r < n) x[i] += cq_ * (T)gq[r];
+          }
+        }
+      }
+      // interior forward elimination and back substitution: x[0..MM-2] := g
+#pragma unroll
+      for (int i = 1; i < MM - 1; ++i) x[i] -= cl[i * P + t] * x[i - 1];
+      x[MM - 2] *= ci[(MM - 2) * P + t];
+#pragma unroll
+      for (int i = MM - 3; i >= 0; --i) x[i] = x[i] * ci[i * P + t] - cu[i * P + t] * x[i + 1];
+      // interface right-hand side needs g_{t+1}[0]
+      xb[2 * P + t] = x[0];
+      __syncthreads();
+      T gnext = (t + 1 < P) ? xb[2 * P + t + 1] : T(0);
+      T r = x[MM - 1] - cl[(MM - 1) * P + t] * x[MM - 2] - cu[(MM - 1) * P + t] * gnext;
+      // parallel cyclic reduction with precomputed factors
+      int buf = 0;
+      for (int lev = 0, s = 1; lev < L; ++lev, s <<= 1) {
+        xb[buf * P + t] = r;
+        __syncthreads();
+        T rm = (t - s >= 0) ? xb[buf * P + t - s] : T(0);
+        T rp = (t + s < P) ? xb[buf * P + t + s] : T(0);
+        r = r - s_pcr[lev * P + t] * rm - s_pcr[(L + lev) * P + t] * rp;
+        buf ^= 1;
+      }
+      T y = r * s_pcr[2 * L * P + t];
+      xb[buf * P + t] = y;
+      __syncthreads();
+      T yl = (t > 0) ? xb[buf * P + t - 1] : T(0);
+      // interior correction with the spikes
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - cp[i * P + t] * yl - cq[i * P + t] * y;
+      x[MM - 1] = y;
+    }
+    // ---- store -------------------------------------------------------------
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < MM; ++i) {
+        int r = r0 + i;
+        if (r < n) {
+          if (a.out.y_f64)
+            static_cast<double*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (double)x[i];
+          else
+            static_cast<float*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (float)x[i];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static int choose_m(int n) {
+  if (n >= 1024) return 32;
+  if (n >= 256) return 16;
+  if (n >= 32) return 8;
+  return 4;
+}
+
+lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out) {
+  for (auto& p : op->plans)
+    if (p->dt == dt && p->adjoint == adjoint) { *out = p.get(); return LRP_OK; }
+  auto pl = std::make_unique<TriPlan>();
+  pl->dt = dt;
+  pl->adjoint = adjoint;
+  pl->n = op->n;
+  pl->m = choose_m(op->n);
+  pl->P = (op->n + pl->m - 1) / pl->m;
+  if (pl->P > 1024) return set_err(c, LRP_EINVAL, "tridiagonal operator too large (n > 32768)");
+  int L = 0;
+  while ((1 << L) < pl->P) ++L;
+  pl->levels = L;
+  size_t MP = (size_t)pl->m * pl->P;
+  lrp_status s;
+  if ((s = dev_alloc(c, pl->coef64, 5 * MP * 8))) return s;
+  if ((s = dev_alloc(c, pl->coef32, 5 * MP * 4))) return s;
+  if ((s = dev_alloc(c, pl->pcr64, (size_t)(2 * L + 1) * pl->P * 8))) return s;
+  if ((s = dev_alloc(c, pl->pcr32, (size_t)(2 * L + 1) * pl->P * 4))) return s;
+  if ((s = dev_alloc(c, pl->status, sizeof(int)))) return s;
+  cudaError_t e = cudaMemsetAsync(pl->status.ptr, 0, sizeof(int), c->stream);
+  if (e) return cuda_err(c, e, "memset");
+  int threads = ((pl->P + 31) / 32) * 32;
+  k_tri_factor<<<1, threads, 5 * pl->P * sizeof(double), c->stream>>>(
+      op->a64[0].as<double>(), op->a64[1].as<double>(), op->a64[2].as<double>(), op->n, dt,
+      adjoint, pl->m, pl->P, L, pl->coef64.as<double>(), pl->coef32.as<float>(),
+      pl->pcr64.as<double>(), pl->pcr32.as<float>(), pl->status.as<int>());
+  e = cudaGetLastError();
+  if (e) return cuda_err(c, e, "k_tri_factor launch");
+  int st = 0;
+  e = cudaMemcpyAsync(&st, pl->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "k_tri_factor");
+  if (st) return set_err(c, LRP_EBREAKDOWN, "zero pivot in the tridiagonal factorisation");
+  *out = pl.get();
+  op->plans.push_back(std::move(pl));
+  return LRP_OK;
+}
+
+template <typename T, int MM>
+static lrp_status launch_tri(Ctx* c, TriPlan* plan, TriKArgs& a) {
+  const int P = a.P;
+  int Gmax = std::max(1, 512 / P);
+  // spread small batches over the SMs before packing systems into a CTA
+  int G = std::max(1, std::min(Gmax, a.nsys / std::max(1, c->num_sms)));
+  a.G = G;
+  size_t smem = sizeof(T) * ((size_t)5 * MM * P + (size_t)(2 * a.L + 1) * P + (size_t)G * 3 * P);
+  auto kern = k_tri_propagate<T, MM>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return cuda_err(c, e, "tri smem attribute");
+  int per_sm = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P * G, smem);
+  if (e) return cuda_err(c, e, "tri occupancy");
+  if (per_sm < 1) return set_err(c, LRP_EINVAL, "tridiagonal kernel does not fit on an SM");
+  int groups = (a.nsys + G - 1) / G;
+  int grid = std::min(groups, per_sm * c->num_sms);
+  const char* fam = sizeof(T) == 8 ? "propagate_f64" : "propagate_f32";
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, fam, &ev);
+  kern<<<grid, P * G, smem, c->stream>>>(a);
+  e = cudaGetLastError();
+  timer_end(c, fam, ev);
+  if (e) return cuda_err(c, e, "k_tri_propagate launch");
+  return LRP_OK;
+}
+
+lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, int prec,
+                         const PropIn& in, const PropOut& out, const PropSrc& src) {
+  if (nsys <= 0) return LRP_OK;
+  TriKArgs a{};
+  a.n = plan->n;
+  a.P = plan->P;
+  a.L = plan->levels;
+  a.M = M;
+  a.nsys = nsys;
+  a.dt = plan->dt;
+  a.in = in;
+  a.out = out;
+  a.src = src;
+  if (prec == 0) {
+    a.coef = plan->coef64.ptr;
+    a.pcr = plan->pcr64.ptr;
+    switch (plan->m) {
+      case 4: return launch_tri<double, 4>(c, plan, a);
+      case 8: return launch_tri<double, 8>(c, plan, a);
+      case 16: return launch_tri<double, 16>(c, plan, a);
+      default: return launch_tri<double, 32>(c, plan, a);
+    }
+  }
+  a.coef = plan->coef32.ptr;
+  a.pcr = plan->pcr32.ptr;
+  switch (plan->m) {
+    case 4: return launch_tri<float, 4>(c, plan, a);
+    case 8: return launch_tri<float, 8>(c, plan, a);
+    case 16: return launch_tri<float, 16>(c, plan, a);
+    default: return launch_tri<float, 32>(c, plan, a);
+  }
+}
+
+}  // namespace lrp

@@ -1,0 +1,257 @@
+"""GPU parity of the 1D (tridiagonal) hot path against the FP64 oracle.
+
+Rows covered: sketch vectors (rSVD step 1), the batched fine propagator F, F'
+and F'^* (forward and adjoint sketches, b_i, Parareal fine solves), the coarse
+build (rSVD steps 2-6), and the Parareal solve with the fused coarse sweep and
+the a posteriori bound.  Tolerances: 1e-10 relative L2 in the all-FP64 path;
+the FP32 paths state theirs per test.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_08873_gb300 import api, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return api.Context(0)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# sketch vectors
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("interval,ncol,n", [(0, 12, 255), (37, 3, 4095), (5, 1, 1)])
+def test_gaussian_matches_oracle(ctx, orc, interval, ncol, n):
+    got = api.gaussian(ctx, 0, interval, ncol, n)
+    want = orc.gauss_block(0, interval, n, ncol)
+    # same Philox words; libm vs CUDA log/cos differ by a few ulp
+    np.testing.assert_allclose(got, want, rtol=0, atol=1e-14)
+    got32 = api.gaussian(ctx, 0, interval, ncol, n, prec="mixed")
+    # FP32 deviate from 24-bit uniforms: agrees to FP32 accuracy except where
+    # U1 is tiny (its 24-bit rounding then shows in log U1)
+    close = np.abs(got32 - want) <= 2e-5 * (1 + np.abs(want))
+    assert close.mean() >= 0.999 and np.max(np.abs(got32 - want)) < 0.05
+
+
+# ---------------------------------------------------------------------------
+# fine propagator
+# ---------------------------------------------------------------------------
+OPS = {
+    "heat": lambda n: W.heat1d_op(n),
+    "adr": lambda n: W.adr1d_op(n),
+}
+
+
+@pytest.mark.parametrize("kind", ["heat", "adr"])
+@pytest.mark.parametrize("n", [2, 3, 17, 255, 1000, 4095])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_propagate_f64_parity(ctx, orc, kind, n, adjoint):
+    lo, di, up = OPS[kind](n)
+    dt, M = 1.0 / 16384, 9
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((5, n))
+    got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+    want = orc.propagate(orc.Tridiag(lo, di, up), dt, M, X, adjoint=adjoint)
+    # rounding of two different elimination orders: ~ cond(I + dt A) u per step
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    for v in range(X.shape[0]):
+        e = rel(got[v], want[v])
+        assert e <= tol, (e, tol)
+
+
+@pytest.mark.parametrize("n", [255, 4095])
+def test_propagate_source_parity(ctx, orc, n):
+    P = W.heat1d(n=n, N=4, M=16)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    X = np.stack([P.u0, np.zeros(n), P.u0 * 3])
+    cs = np.stack([P.c[0:16], P.c[16:32], P.c[32:48]])
+    got = api.propagate(ctx, op, P.dt, P.M, X, g=P.g, c=cs)
+    want = orc.propagate(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, X, g=P.g, cvals=cs)
+    cond = 1 + 4 * P.dt * (P.n + 1) ** 2
+    tol = max(1e-12, 4 * P.M * cond * 2.2e-16)
+    for v in range(3):
+        e = rel(got[v], want[v])
+        assert e <= tol, (e, tol)
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_propagate_f32_parity(ctx, orc, adjoint):
+    P = W.adr1d(n=4095, N=64, M=256)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    X = np.random.default_rng(3).standard_normal((7, P.n))
+    got = api.propagate(ctx, op, P.dt, P.M, X, adjoint=adjoint, prec="mixed")
+    want = orc.propagate(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, X, adjoint=adjoint)
+    for v in range(X.shape[0]):
+        assert rel(got[v], want[v]) <= 2e-5          # FP32 arithmetic, 256 steps
+
+
+def test_propagate_many_systems_and_empty(ctx, orc):
+    """A batch spanning several CTAs per SM and a ragged count of systems."""
+    lo, di, up = W.adr1d_op(255)
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    X = np.random.default_rng(5).standard_normal((1237, 255))
+    got = api.propagate(ctx, op, 1e-3, 4, X)
+    want = orc.propagate(orc.Tridiag(lo, di, up), 1e-3, 4, X)
+    assert np.max(np.linalg.norm(got - want, axis=1) / np.linalg.norm(want, axis=1)) <= 1e-12
+    empty = api.propagate(ctx, op, 1e-3, 4, np.zeros((0, 255)))
+    assert empty.shape == (0, 255)
+    same = api.propagate(ctx, op, 1e-3, 0, X[:3])
+    np.testing.assert_array_equal(same, X[:3])
+
+
+# ---------------------------------------------------------------------------
+# coarse build (rSVD)
+# ---------------------------------------------------------------------------
+def _operator_diff(orc_c, U, S, V, probes):
+    Go = orc_c.U @ np.diag(orc_c.S) @ orc_c.V.T
+    Gg = U.T @ np.diag(S) @ V
+    return max(np.linalg.norm((Gg - Go) @ x) / np.linalg.norm(x) for x in probes)
+
+
+@pytest.mark.parametrize("which", ["heat1d", "adr1d_small"])
+def test_build_coarse_f64_parity(ctx, orc, which):
+    if which == "heat1d":
+        P = W.heat1d()                     # n=255, N=16, M=64, R=8, p=4
+        check = range(P.N)
+    else:
+        P = W.adr1d(n=511, N=8, M=32, R=6, p=4)
+        check = range(P.N)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    info = co.info()
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    probes = np.random.default_rng(9).standard_normal((4, P.n))
+    for i in check:
+        oc = orc.rsvd_interval(oop, P.dt, P.M, i, P.R, P.p, P.seed)
+        assert info["R"][i] == oc.S.shape[0]
+        s1 = oc.sigma[0]
+        kk = min(info["rank_w"][i], info["rank_v"][i])
+        m = min(kk, oc.sigma.shape[0])
+        assert np.max(np.abs(info["sigma"][i, :m] - oc.sigma[:m])) <= 1e-10 * s1
+        U, S, V = co.factors(i)
+        assert _operator_diff(oc, U, S, V, probes) <= 1e-10 * s1
+    assert abs(info["delta"] - max(orc.rsvd_interval(oop, P.dt, P.M, i, P.R, P.p, P.seed).sigma[0]
+                                   for i in check)) <= 1e-10
+
+
+def test_build_coarse_heat_closed_form(ctx):
+    """sigma_j = (1 + dt lam_j)^-M for the 1D heat operator (both precisions)."""
+    P = W.heat1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    h = 1.0 / (P.n + 1)
+    j = np.arange(1, P.R + 1)
+    sig = (1 + P.dt * 4 / h ** 2 * np.sin(j * np.pi * h / 2) ** 2) ** (-P.M)
+    for prec, tol in (("f64", 1e-12), ("mixed", 1e-5)):
+        co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=prec)
+        info = co.info()
+        R = info["R"].min()
+        assert R >= (P.R if prec == "f64" else 4)
+        assert np.max(np.abs(info["sigma"][:, :R] - sig[None, :R])) <= tol * sig[0]
+
+
+def test_build_coarse_mixed_operator_error(ctx, orc):
+    """Mixed build: G' within 1e-4 sigma_1 of the FP64 oracle's on probes."""
+    P = W.adr1d(n=1023, N=4, M=64, R=8, p=4)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed")
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    probes = np.random.default_rng(1).standard_normal((3, P.n))
+    for i in range(P.N):
+        oc = orc.rsvd_interval(oop, P.dt, P.M, i, P.R, P.p, P.seed)
+        U, S, V = co.factors(i)
+        assert _operator_diff(oc, U, S, V, probes) <= 1e-4 * oc.sigma[0]
+
+
+# ---------------------------------------------------------------------------
+# Parareal
+# ---------------------------------------------------------------------------
+def _run_both(ctx, orc, P, K=None, tol=0.0, prec="f64"):
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=prec)
+    u, info = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=K, tol=tol)
+    return op, co, u, info
+
+
+@pytest.mark.parametrize("K", [0, 1, 3])
+def test_parareal_f64_iterates_match_oracle(ctx, orc, K):
+    P = W.adr1d(n=511, N=8, M=32, R=4, p=2)
+    P.g, P.c = W.heat1d(n=511, N=8, M=32).g, W.heat1d(n=511, N=8, M=32).c
+    op, co, u, info = _run_both(ctx, orc, P, K=K)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, P.g, P.c, K=K)
+    assert info["k_done"] == res.k_done == K
+    assert rel(u, res.iterates[-1]) <= 1e-10
+    for k in range(1, K + 1):
+        np.testing.assert_allclose(info["bounds"][k - 1], res.bounds[k - 1], rtol=1e-8, atol=1e-14)
+
+
+def test_parareal_heat1d_full_K_equals_N(ctx, orc):
+    """Config: n=255, N=16, M=64, R=8, p=4, source sin(2 pi t) exp(-100(x-1/2)^2)."""
+    P = W.heat1d()
+    op, co, u, info = _run_both(ctx, orc, P, K=P.N)
+    ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0, P.g, P.c)
+    assert info["k_done"] == P.N
+    assert orc.rel_err(u, ref) <= 1e-10
+    # and the device's own sequential sweep (same propagator) agrees to rounding
+    fine = api.fine_solution(ctx, op, P.dt, P.M, P.N, P.u0, P.g, P.c)
+    assert orc.rel_err(fine, ref) <= 1e-12
+    assert np.max(np.abs(u - fine)) <= 1e-13 * np.abs(fine).max()
+
+
+def test_parareal_heat1d_tol(ctx, orc):
+    P = W.heat1d()
+    op, co, u, info = _run_both(ctx, orc, P, K=P.N, tol=1e-10)
+    ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0, P.g, P.c)
+    assert info["converged"]
+    assert orc.rel_err(u, ref) <= 1e-10
+    assert info["k_done"] <= 2
+
+
+def test_parareal_finite_termination_and_R0(ctx, orc):
+    P = W.adr1d(n=255, N=6, M=16, R=0, p=2)
+    op, co, u, info = _run_both(ctx, orc, P, K=2)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+    err = np.linalg.norm(u - ref, axis=1)
+    assert np.all(err[:3] <= 1e-13 * np.abs(ref).max())      # u^k_n exact for n <= k
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, K=2)
+    assert rel(u, res.iterates[-1]) <= 1e-10
+
+
+@pytest.mark.parametrize("prec", ["f64", "mixed"])
+def test_parareal_adr1d_full_size_to_1e8(ctx, orc, prec):
+    """Full configuration n=4095, N=64, M=256, R=16, p=8 with tol 1e-8: the
+    last iterate is within 1e-8 (relative, max over time) of the oracle's
+    sequential FP64 fine solution, and the build's singular values match the
+    oracle's randomized SVD on sampled intervals."""
+    P = W.adr1d()
+    op, co, u, info = _run_both(ctx, orc, P, K=P.N, tol=1e-8, prec=prec)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+    assert info["converged"]
+    assert orc.rel_err(u, ref) <= 1e-8
+    inf = co.info()
+    for i in (0, 41):
+        oc = orc.rsvd_interval(oop, P.dt, P.M, i, P.R, P.p, P.seed)
+        tol = 1e-10 if prec == "f64" else 1e-4
+        assert np.max(np.abs(inf["sigma"][i] - oc.sigma)) <= tol * oc.sigma[0]
+
+
+def test_parareal_invalid_arguments(ctx):
+    P = W.heat1d(n=31, N=2, M=4, R=2, p=1)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    from paper_2508_08873_gb300 import _native
+    with pytest.raises(_native.LrpError):
+        api.Coarse(ctx, op, P.dt, P.M, P.N, 40, 1, 0)       # rank + p > n
+    with pytest.raises(_native.LrpError):
+        api.Coarse(ctx, op, -1.0, P.M, P.N, 2, 1, 0)
