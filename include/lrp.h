@@ -128,6 +128,33 @@ lrp_status lrp_propagate(lrp_ctx* ctx, const lrp_operator* op, double dt, int M,
 lrp_status lrp_gaussian(lrp_ctx* ctx, uint64_t seed, int interval, int ncol, int n,
                         lrp_precision prec, double* out);
 
+/* Allocation-free variant of lrp_propagate (the paper has no counterpart).
+ * It exists for callers that cannot allocate device memory: hosts that forbid
+ * allocation after start-up (real-time and embedded deployments), frameworks
+ * that own every device byte through their own memory pool, and latency-
+ * sensitive callers that must avoid cudaFree, which synchronises the whole
+ * device.  It takes no context and calls no cudaMalloc, cudaFree or
+ * allocating library routine.  The operator (lo, di, up as in
+ * lrp_operator_tridiag), x_in (nvec x n, or NULL for zero initial values),
+ * x_out (nvec x n) and, when Q > 0, g (Q x n) and c (nvec x M x Q) must all be
+ * DEVICE pointers of `device`; the caller allocates them.  Work is queued on
+ * `stream` (a cudaStream_t, NULL = the default stream); the call waits on that
+ * stream for the factorisation's pivot check and returns with the
+ * propagation queued behind it.
+ * The factorisation of I + dt*A is written to one fixed device array of
+ * 300 KiB per GPU (held by every GPU that loads the library until the process
+ * exits), so n is limited to LRP_NOALLOC_MAX_N; larger n returns LRP_EINVAL.
+ * The first call on a device looks up that array's device address (a one-time
+ * set-up per device).  Every call shares the array and overwrites the previous
+ * call's factorisation: calls that overlap on the GPU (several streams or host
+ * threads) race and must be serialised by the caller.  Returns LRP_EBREAKDOWN
+ * on a zero pivot. */
+#define LRP_NOALLOC_MAX_N 4096
+lrp_status lrp_propagate_noalloc(int device, void* stream, int n, const double* lo,
+                                 const double* di, const double* up, double dt, int M,
+                                 int adjoint, int nvec, const double* x_in, double* x_out,
+                                 int Q, const double* g, const double* c, lrp_precision prec);
+
 /* ---- coarse solvers (Sec. 2.1, randomized SVD steps 1-6) ----------------- */
 
 /* Build G_i' = U_i diag(S_i) V_i^T for i = 0..N-1 from rank + oversample

@@ -74,6 +74,7 @@ SIGNATURES = [
     ("lrp_operator_size", _I, [_P]),
     ("lrp_operator_set_krylov", _I, [_P, _D, _D, _I]),
     ("lrp_propagate", _I, [_P, _P, _D, _I, _I, _I, _P, _P, _I, _P, _P, _I]),
+    ("lrp_propagate_noalloc", _I, [_I, _P, _I, _P, _P, _P, _D, _I, _I, _I, _P, _P, _I, _P, _P, _I]),
     ("lrp_gaussian", _I, [_P, _U64, _I, _I, _I, _I, _P]),
     ("lrp_build_coarse", _I, [_P, _P, _D, _I, _I, _I, _I, _U64, _I, _PP]),
     ("lrp_coarse_free", None, [_P]),

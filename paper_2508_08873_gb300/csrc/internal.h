@@ -136,6 +136,13 @@ struct PropSrc {
 lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src);
 
+// Allocation-free variant: factorisation into caller-provided scratch.
+size_t tri_raw_scratch_bytes(int n);
+lrp_status tri_raw_propagate(cudaStream_t stream, int num_sms, void* scratch, int n,
+                             const double* lo, const double* di, const double* up, double dt,
+                             int adjoint, int M, int nsys, int prec, const PropIn& in,
+                             const PropOut& out, const PropSrc& src);
+
 // ---- orthonormalisation, small SVD, lift (linalg.cu) -----------------------
 // CGS2 with deflation of every interval's ell x n block (rows = vectors), in
 // place.  Kept vectors are compacted to the front, dropped rows zeroed.

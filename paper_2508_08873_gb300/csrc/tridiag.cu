@@ -389,4 +389,73 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
   }
 }
 
+// ---------------------------------------------------------------------------
+// Launchers on caller-provided memory (used by the allocation-free entry
+// point): the factorisation is written into `scratch` instead of buffers owned
+// by an operator.  Layout of the scratch: coef64 [5][m][P] | pcr64
+// [2L+1][P] | coef32 | pcr32 | status (int), each part 256-byte aligned.
+// ---------------------------------------------------------------------------
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t tri_raw_scratch_bytes(int n) {
+  int m = choose_m(n), P = (n + m - 1) / m, L = 0;
+  while ((1 << L) < P) ++L;
+  size_t MP = (size_t)m * P, Lp = (size_t)(2 * L + 1) * P;
+  return align256(5 * MP * 8) + align256(Lp * 8) + align256(5 * MP * 4) + align256(Lp * 4) + 256;
+}
+
+lrp_status tri_raw_propagate(cudaStream_t stream, int num_sms, void* scratch, int n,
+                             const double* lo, const double* di, const double* up, double dt,
+                             int adjoint, int M, int nsys, int prec, const PropIn& in,
+                             const PropOut& out, const PropSrc& src) {
+  int m = choose_m(n), P = (n + m - 1) / m, L = 0;
+  while ((1 << L) < P) ++L;
+  size_t MP = (size_t)m * P, Lp = (size_t)(2 * L + 1) * P;
+  char* base = static_cast<char*>(scratch);
+  double* coef64 = reinterpret_cast<double*>(base);
+  base += align256(5 * MP * 8);
+  double* pcr64 = reinterpret_cast<double*>(base);
+  base += align256(Lp * 8);
+  float* coef32 = reinterpret_cast<float*>(base);
+  base += align256(5 * MP * 4);
+  float* pcr32 = reinterpret_cast<float*>(base);
+  base += align256(Lp * 4);
+  int* status = reinterpret_cast<int*>(base);
+  cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int), stream);
+  if (e) return LRP_ECUDA;
+  int threads = ((P + 31) / 32) * 32;
+  k_tri_factor<<<1, threads, 5 * P * sizeof(double), stream>>>(lo, di, up, n, dt, adjoint, m, P, L,
+                                                              coef64, coef32, pcr64, pcr32, status);
+  if (cudaGetLastError()) return LRP_ECUDA;
+  int st = 0;
+  e = cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, stream);
+  if (!e) e = cudaStreamSynchronize(stream);
+  if (e) return LRP_ECUDA;
+  if (st) return LRP_EBREAKDOWN;
+  if (nsys <= 0) return LRP_OK;
+  TriKArgs a{};
+  a.n = n; a.P = P; a.L = L; a.M = M; a.nsys = nsys; a.dt = dt;
+  a.in = in; a.out = out; a.src = src;
+  a.coef = prec == 0 ? (const void*)coef64 : (const void*)coef32;
+  a.pcr = prec == 0 ? (const void*)pcr64 : (const void*)pcr32;
+  Ctx tmp;                       // stream and SM count for the shared launcher
+  tmp.stream = stream;
+  tmp.num_sms = num_sms;
+  TriPlan* none = nullptr;
+  if (prec == 0) {
+    switch (m) {
+      case 4: return launch_tri<double, 4>(&tmp, none, a);
+      case 8: return launch_tri<double, 8>(&tmp, none, a);
+      case 16: return launch_tri<double, 16>(&tmp, none, a);
+      default: return launch_tri<double, 32>(&tmp, none, a);
+    }
+  }
+  switch (m) {
+    case 4: return launch_tri<float, 4>(&tmp, none, a);
+    case 8: return launch_tri<float, 8>(&tmp, none, a);
+    case 16: return launch_tri<float, 16>(&tmp, none, a);
+    default: return launch_tri<float, 32>(&tmp, none, a);
+  }
+}
+
 }  // namespace lrp
