@@ -79,6 +79,14 @@ size_t lrp_bytes_in_use(lrp_ctx* ctx);
 /* Number of kernels the context has launched so far (all kernel families). */
 long lrp_launch_count(lrp_ctx* ctx);
 
+/* Launch tuning (0 = automatic, the default):
+ *   "sweep_cluster": CTAs per thread-block cluster of the coarse sweep (1..16,
+ *                    a power of two);
+ *   "tri_cluster":   CTAs per tridiagonal system for small batches (1, 2, 4).
+ * Results do not depend on these settings beyond rounding. */
+lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);
+lrp_status lrp_get_param(lrp_ctx* ctx, const char* name, int* value);
+
 /* Per-kernel timing with CUDA events recorded around every launch of the
  * named kernel family on the context's stream (off by default).  Families:
  * "propagate_f64" and "propagate_f32" (the batched fine propagator in each
@@ -92,7 +100,7 @@ lrp_status lrp_reset_kernel_time(lrp_ctx* ctx);
 
 /* Tridiagonal A, row i: lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1] (lo[0] and
  * up[n-1] are ignored).  I + dt*A must be diagonally dominant: the
- * propagator eliminates without pivoting.  2 <= n <= 32768. */
+ * propagator eliminates without pivoting.  2 <= n <= 16384. */
 lrp_status lrp_operator_tridiag(lrp_ctx* ctx, int n, const double* lo, const double* di,
                                 const double* up, lrp_operator** out);
 /* 5-point A on an mx x my grid of interior nodes, node p = iy*mx + ix:
@@ -103,10 +111,17 @@ lrp_status lrp_operator_stencil5(lrp_ctx* ctx, int mx, int my, const double* C,
                                  const double* N, lrp_operator** out);
 void lrp_operator_free(lrp_operator* op);
 int lrp_operator_size(const lrp_operator* op);
+/* Krylov iterations spent so far by 2D propagations with this operator. */
+unsigned long long lrp_operator_krylov_iterations(const lrp_operator* op);
 
-/* Linear solver controls of 2D operators (Krylov per implicit-Euler step):
- * relative residual tolerances for FP64 and FP32 propagation and the
- * iteration cap per step.  Defaults: 1e-12, 1e-6, 20000. */
+/* Linear solver controls of 2D operators.  Each implicit-Euler step is solved
+ * by Jacobi-preconditioned conjugate gradients when the stencil is symmetric
+ * (W[p] = E[p-1] and S[p] = N[p-mx] for all interior couplings), else by
+ * Jacobi-preconditioned BiCGStab, warm-started from the previous step, to
+ * ||d - B x||_2 <= rtol ||d||_2 (B = I + dt A, d the step's right-hand side).
+ * Arguments: the relative tolerances for FP64 and FP32 propagation and the
+ * iteration cap per step (reaching it makes the call return LRP_ENOTCONV with
+ * the outputs written).  Defaults: 1e-12, 1e-6, 20000. */
 lrp_status lrp_operator_set_krylov(lrp_operator* op, double rtol_f64, double rtol_f32,
                                    int max_iter);
 

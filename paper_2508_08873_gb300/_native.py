@@ -65,6 +65,8 @@ SIGNATURES = [
     ("lrp_last_error", ctypes.c_char_p, [_P]),
     ("lrp_bytes_in_use", _S, [_P]),
     ("lrp_launch_count", ctypes.c_long, [_P]),
+    ("lrp_set_param", _I, [_P, ctypes.c_char_p, _I]),
+    ("lrp_get_param", _I, [_P, ctypes.c_char_p, _PI]),
     ("lrp_set_kernel_timing", _I, [_P, _I]),
     ("lrp_kernel_time", _I, [_P, ctypes.c_char_p, _PI, _PD]),
     ("lrp_reset_kernel_time", _I, [_P]),
@@ -72,6 +74,7 @@ SIGNATURES = [
     ("lrp_operator_stencil5", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _PP]),
     ("lrp_operator_free", None, [_P]),
     ("lrp_operator_size", _I, [_P]),
+    ("lrp_operator_krylov_iterations", ctypes.c_ulonglong, [_P]),
     ("lrp_operator_set_krylov", _I, [_P, _D, _D, _I]),
     ("lrp_propagate", _I, [_P, _P, _D, _I, _I, _I, _P, _P, _I, _P, _P, _I]),
     ("lrp_propagate_noalloc", _I, [_I, _P, _I, _P, _P, _P, _D, _I, _I, _I, _P, _P, _I, _P, _P, _I]),

@@ -61,6 +61,14 @@ class Context:
     def launch_count(self) -> int:
         return self.lib.lrp_launch_count(self.h)
 
+    def set_param(self, name: str, value: int):
+        check(self.lib.lrp_set_param(self.h, name.encode(), int(value)), self.h)
+
+    def get_param(self, name: str) -> int:
+        v = ctypes.c_int()
+        check(self.lib.lrp_get_param(self.h, name.encode(), ctypes.byref(v)), self.h)
+        return v.value
+
     def set_kernel_timing(self, on: bool):
         check(self.lib.lrp_set_kernel_timing(self.h, int(on)), self.h)
 
@@ -105,6 +113,9 @@ class Operator:
         if P.kind == "tridiag":
             return cls.tridiag(ctx, P.lo, P.di, P.up)
         return cls.stencil5(ctx, P.mx, P.my, P.st)
+
+    def krylov_iterations(self) -> int:
+        return int(self.ctx.lib.lrp_operator_krylov_iterations(self.h))
 
     def set_krylov(self, rtol_f64: float = 1e-12, rtol_f32: float = 1e-6, max_iter: int = 20000):
         check(self.ctx.lib.lrp_operator_set_krylov(self.h, rtol_f64, rtol_f32, max_iter), self.ctx.h)

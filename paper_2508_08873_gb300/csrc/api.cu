@@ -52,6 +52,10 @@ void ctx_release(Ctx* c) {
 Operator::~Operator() {
   Ctx* c = ctx;
   plans.clear();
+  cplans.clear();
+  splans.clear();
+  kws.release();
+  kstat.release();
   for (auto& b : a64) b.release();
   for (auto& b : a32) b.release();
   ctx_release(c);
@@ -211,6 +215,30 @@ size_t lrp_bytes_in_use(lrp_ctx* c) { return c ? c->in_use : 0; }
 
 long lrp_launch_count(lrp_ctx* c) { return c ? c->launches : 0; }
 
+lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
+  if (!c || !name) return LRP_EINVAL;
+  std::string k(name);
+  if (k == "sweep_cluster") {
+    if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
+    c->p_sweep_cluster = value;
+  } else if (k == "tri_cluster") {
+    if (value != 0 && value != 1 && value != 2 && value != 4) return LRP_EINVAL;
+    c->p_tri_cluster = value;
+  } else {
+    return set_err(c, LRP_EINVAL, "unknown parameter");
+  }
+  return LRP_OK;
+}
+
+lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
+  if (!c || !name || !value) return LRP_EINVAL;
+  std::string k(name);
+  if (k == "sweep_cluster") *value = c->p_sweep_cluster;
+  else if (k == "tri_cluster") *value = c->p_tri_cluster;
+  else return set_err(c, LRP_EINVAL, "unknown parameter");
+  return LRP_OK;
+}
+
 lrp_status lrp_set_kernel_timing(lrp_ctx* c, int enable) {
   if (!c) return LRP_EINVAL;
   c->timing = enable != 0;
@@ -258,7 +286,7 @@ lrp_status lrp_reset_kernel_time(lrp_ctx* c) {
 lrp_status lrp_operator_tridiag(lrp_ctx* c, int n, const double* lo, const double* di,
                                 const double* up, lrp_operator** out) {
   if (!c || !out || !lo || !di || !up) return LRP_EINVAL;
-  if (n < 2 || n > 32768) return set_err(c, LRP_EINVAL, "tridiagonal size must be 2..32768");
+  if (n < 2 || n > 16384) return set_err(c, LRP_EINVAL, "tridiagonal size must be 2..16384");
   cudaSetDevice(c->device);
   auto op = std::make_unique<lrp_operator>();
   op->ctx = c;
@@ -286,6 +314,10 @@ void lrp_operator_free(lrp_operator* op) {
 
 int lrp_operator_size(const lrp_operator* op) { return op ? op->n : 0; }
 
+unsigned long long lrp_operator_krylov_iterations(const lrp_operator* op) {
+  return op ? op->krylov_iters : 0;
+}
+
 lrp_status lrp_operator_set_krylov(lrp_operator* op, double rtol_f64, double rtol_f32,
                                    int max_iter) {
   if (!op || !(rtol_f64 > 0) || !(rtol_f32 > 0) || max_iter < 0) return LRP_EINVAL;
@@ -308,6 +340,23 @@ static lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjo
                                 int prec, const PropIn& in, const PropOut& out,
                                 const PropSrc& src) {
   if (op->kind == 0) {
+    // Small batches of long systems: spread every system over a cluster of
+    // 2 or 4 CTAs so that more SMs take part; otherwise one CTA per system.
+    int C = 1;
+    const int P = (op->n + 15) / 16;               // chunks of 16 rows
+    auto fits = [&](int cc) { int Pc = (P + cc - 1) / cc; return Pc >= 32 && Pc <= 256; };
+    if (c->p_tri_cluster > 1 && fits(c->p_tri_cluster)) {
+      C = c->p_tri_cluster;
+    } else if (c->p_tri_cluster == 0 && op->n >= 2048) {
+      for (int cc : {4, 2})
+        if (nsys * cc <= c->num_sms && fits(cc)) { C = cc; break; }
+    }
+    if (C > 1) {
+      ClPlan* cp = nullptr;
+      lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, C, &cp);
+      if (s) return s;
+      return tri_propagate_cluster(c, cp, M, nsys, prec, in, out, src);
+    }
     TriPlan* plan = nullptr;
     lrp_status s = tri_get_plan(c, op, dt, adjoint, &plan);
     if (s) return s;

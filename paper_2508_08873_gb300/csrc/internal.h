@@ -45,6 +45,9 @@ struct Ctx {
   std::map<std::string, KernelTimer> timers;
   int num_sms = 0;
   long launches = 0;       // kernels launched by this context (all families)
+  // Tunable launch parameters (0 = automatic choice); see lrp_set_param.
+  int p_sweep_cluster = 0;   // CTAs per coarse-sweep cluster (1..16)
+  int p_tri_cluster = 0;     // CTAs per tridiagonal system for small batches (1, 2, 4)
   // Handles (operators, coarse solvers) hold a reference; the context is
   // deleted when lrp_destroy has been called and the last handle is freed.
   int refs = 1;
@@ -66,7 +69,24 @@ struct TriPlan {
   DevBuf status;           // int: 0 ok, 1 zero pivot
 };
 
-struct StencilPlan;
+// Two-level partition of B = I + dt*A for one system spread over a cluster of
+// C CTAs (tridiag_cluster.cu): per-CTA chunk factors, local PCR factors,
+// local spikes and the C x C super system.  b[k]: coef, lpcr, spk, sup.
+struct ClPlan {
+  double dt = 0.0;
+  int adjoint = 0, C = 1, n = 0, m = 0, P = 0, Pc = 0, L = 0;
+  size_t sz[4] = {0, 0, 0, 0};
+  DevBuf b64[4], b32[4];
+  DevBuf status;
+};
+
+// B = I + dt*A (or its transpose) of a 5-point operator: [6][n] = centre,
+// west, east, south, north couplings and 1/centre, FP64 and FP32 copies.
+struct StencilPlan {
+  double dt = 0.0;
+  int adjoint = 0;
+  DevBuf b64, b32;
+};
 
 struct Operator {
   Ctx* ctx = nullptr;
@@ -77,7 +97,12 @@ struct Operator {
   DevBuf a32[5];
   double rtol64 = 1e-12, rtol32 = 1e-6;
   int max_iter = 20000;
+  bool symmetric = false;  // 5-point: CG when symmetric, else BiCGStab
   std::vector<std::unique_ptr<TriPlan>> plans;
+  std::vector<std::unique_ptr<ClPlan>> cplans;
+  std::vector<std::unique_ptr<StencilPlan>> splans;
+  DevBuf kws, kstat;       // Krylov workspace and status of 2D propagations
+  unsigned long long krylov_iters = 0;
 };
 
 struct Coarse {
@@ -136,6 +161,11 @@ struct PropSrc {
 lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src);
 
+// One system per cluster of C CTAs (small batches, n >= 2048).
+lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, ClPlan** out);
+lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, const PropIn& in,
+                                 const PropOut& out, const PropSrc& src);
+
 // Allocation-free variant: factorisation into caller-provided scratch.
 size_t tri_raw_scratch_bytes(int n);
 lrp_status tri_raw_propagate(cudaStream_t stream, int num_sms, void* scratch, int n,
@@ -179,6 +209,7 @@ struct SweepArgs {
   double* unorm = nullptr;        // N+1: ||u^k_m||
   double* bound = nullptr;        // N+1: a posteriori bound (Eq. apost_bound)
   double* summary = nullptr;      // [0] = max bound, [1] = max ||u^k_m||
+  int stage = 0;                  // set by the launcher: factors staged in smem
 };
 lrp_status coarse_sweep(Ctx* c, const SweepArgs& a);
 

@@ -26,10 +26,23 @@ namespace cg = cooperative_groups;
 
 namespace lrp {
 
+// 4- or 8-byte asynchronous global->shared copies (cp.async, completion
+// tracked per thread with commit/wait groups).
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
+  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
 constexpr int SWEEP_THREADS = 256;
 constexpr int SWEEP_MAXR = 64;
 constexpr int SWEEP_MAXCS = 16;
 constexpr int SWEEP_MAXROWS = 20480;     // rows per CTA (delta kept in shared memory)
+constexpr size_t SWEEP_STAGE_MAX = 192 * 1024;   // dynamic smem when staging factors
+constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
 
 template <typename TF>
 __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
@@ -49,6 +62,32 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
   const TF* U = static_cast<const TF*>(a.U);
   const TF* S = static_cast<const TF*>(a.S);
   const TF* V = static_cast<const TF*>(a.V);
+  // Optional staging of the next interval's factor slices and F slice in
+  // shared memory (double-buffered cp.async), so that their load latency
+  // overlaps the current interval's reductions and cluster barrier.
+  const bool stage = a.stage != 0;
+  TF* sU = reinterpret_cast<TF*>(dsm + per);                  // [2][R][per]
+  TF* sV = sU + (size_t)2 * R * per;                          // [2][R][per]
+  double* sF = reinterpret_cast<double*>(sV + (size_t)2 * R * per);   // [2][per]
+  double* sO = sF + (size_t)2 * per;                          // [2][per] u^{k-1}_{iv+1}
+  auto issue = [&](int iv, int b) {
+    if (!stage || iv >= N) return;
+    const TF* Ug = U + (size_t)iv * R * n + lo;
+    const TF* Vg = V + (size_t)iv * R * n + lo;
+    const double* Fg = a.F + (size_t)iv * n + lo;
+    for (int k = threadIdx.x; k < R * rows; k += blockDim.x) {
+      int r = k / rows, i = k % rows;
+      cp_async<sizeof(TF)>(sU + ((size_t)b * R + r) * per + i, Ug + (size_t)r * n + i);
+      cp_async<sizeof(TF)>(sV + ((size_t)b * R + r) * per + i, Vg + (size_t)r * n + i);
+    }
+    const double* Og = a.u + (size_t)(iv + 1) * n + lo;
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      cp_async<8>(sF + (size_t)b * per + i, Fg + i);
+      if (!a.initial) cp_async<8>(sO + (size_t)b * per + i, Og + i);
+    }
+  };
+  issue(a.first, 0);
+  cp_async_commit();
   // delta at the first interval: 0 (u^k_first == u^{k-1}_first), or u0 initially
   for (int i = threadIdx.x; i < rows; i += blockDim.x)
     dsm[i] = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
@@ -56,23 +95,33 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
     for (int m = 0; m <= a.first; ++m) a.du[m] = 0.0;
   __syncthreads();
   int buf = 0;
+  // ||u^k_first||^2 of this thread's rows; later intervals carry it from the update
+  double acc_u_next = 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    double v = a.u[(size_t)a.first * n + lo + i];
+    acc_u_next += v * v;
+  }
   for (int iv = a.first; iv <= N; ++iv) {
+    const int sb = (iv - a.first) & 1;      // staging buffer of this interval
+    issue(iv + 1, sb ^ 1);
+    cp_async_commit();
+    cp_async_wait<1>();                     // this interval's slices have landed
+    __syncthreads();
     // ---- partial reductions over this CTA's rows ---------------------------
-    const double* ui = a.u + (size_t)iv * n + lo;
-    double acc_d = 0.0, acc_u = 0.0;
+    double acc_d = 0.0, acc_u = acc_u_next;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
       double d = dsm[i];
       acc_d += d * d;
-      acc_u += ui[i] * ui[i];
     }
     acc_d = warp_sum(acc_d);
     acc_u = warp_sum(acc_u);
     if (lane == 0) { red[w][R] = acc_d; red[w][R + 1] = acc_u; }
     if (iv < N) {
       // one warp per factor row r: (V_iv[r], delta) over this CTA's rows
-      const TF* Vi = V + (size_t)iv * R * n + lo;
+      const TF* Vi = stage ? sV + (size_t)sb * R * per : V + (size_t)iv * R * n + lo;
+      const size_t ldv = stage ? (size_t)per : (size_t)n;
       for (int r = w; r < R; r += nw) {
-        const TF* vr = Vi + (size_t)r * n;
+        const TF* vr = Vi + (size_t)r * ldv;
         TF pr = TF(0);
         for (int i = lane; i < rows; i += 32) pr += vr[i] * (TF)dsm[i];
         double d = warp_sum((double)pr);
@@ -108,17 +157,20 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
     }
     if (iv == N) break;
     // ---- u^k_{iv+1} = F_iv + U_iv (S_iv * c) on this CTA's rows ------------
-    const TF* Ui = U + (size_t)iv * R * n + lo;
+    const TF* Ui = stage ? sU + (size_t)sb * R * per : U + (size_t)iv * R * n + lo;
+    const size_t ldu = stage ? (size_t)per : (size_t)n;
     const TF* Si = S + (size_t)iv * R;
-    const double* Fi = a.F + (size_t)iv * n + lo;
+    const double* Fi = stage ? sF + (size_t)sb * per : a.F + (size_t)iv * n + lo;
     double* un = a.u + (size_t)(iv + 1) * n + lo;
+    acc_u_next = 0.0;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
       TF g = TF(0);
-      for (int r = 0; r < R; ++r) g += Ui[(size_t)r * n + i] * (Si[r] * (TF)coef[r]);
+      for (int r = 0; r < R; ++r) g += Ui[(size_t)r * ldu + i] * (Si[r] * (TF)coef[r]);
       double nv_ = Fi[i] + (double)g;
-      double old = a.initial ? 0.0 : un[i];
+      double old = a.initial ? 0.0 : (stage ? sO[(size_t)sb * per + i] : un[i]);
       dsm[i] = nv_ - old;
       un[i] = nv_;
+      acc_u_next += nv_ * nv_;
     }
     buf ^= 1;
     __syncthreads();
@@ -138,6 +190,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
     a.summary[0] = bmax;
     a.summary[1] = umax;
   }
+  cp_async_wait<0>();
   cl.sync();  // no CTA leaves while its shared memory may still be read
 }
 
@@ -153,9 +206,19 @@ lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
   if (e) { cudaGetLastError(); cs = 8; }
   // small problems: fewer CTAs per cluster
   while (cs > 1 && (a.n + cs - 1) / cs < 64) cs >>= 1;
-  size_t dyn = sizeof(double) * (size_t)((a.n + cs - 1) / cs);
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(sizeof(double) * SWEEP_MAXROWS));
+  if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
+  while (cs < SWEEP_MAXCS && (a.n + cs - 1) / cs > SWEEP_MAXROWS) cs <<= 1;
+  const size_t tf = a.f32 ? 4 : 8;
+  auto dyn_for = [&](int csz, int stage) {
+    size_t per = (size_t)((a.n + csz - 1) / csz);
+    size_t b = sizeof(double) * per;
+    if (stage) b += 4 * (size_t)a.R * per * tf + 4 * per * sizeof(double);
+    return b;
+  };
+  SweepArgs aa = a;
+  aa.stage = dyn_for(cs, 1) <= SWEEP_STAGE_MAX ? 1 : 0;
+  size_t dyn = dyn_for(cs, aa.stage);
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_MAX);
   if (e) return cuda_err(c, e, "sweep smem attribute");
   cfg.gridDim = dim3(cs);
   cfg.blockDim = dim3(SWEEP_THREADS);
@@ -169,16 +232,17 @@ lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
   cfg.numAttrs = 1;
   cudaEvent_t ev = nullptr;
   timer_begin(c, "sweep", &ev);
-  e = cudaLaunchKernelEx(&cfg, kern, a);
+  e = cudaLaunchKernelEx(&cfg, kern, aa);
   timer_end(c, "sweep", ev);
   if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
     // retry with a portable cluster size
     cudaGetLastError();
     cs = std::min(cs, 8);
     cfg.gridDim = dim3(cs);
-    cfg.dynamicSmemBytes = sizeof(double) * (size_t)((a.n + cs - 1) / cs);
+    aa.stage = dyn_for(cs, 1) <= SWEEP_STAGE_MAX ? 1 : 0;
+    cfg.dynamicSmemBytes = dyn_for(cs, aa.stage);
     attr[0].val.clusterDim.x = cs;
-    e = cudaLaunchKernelEx(&cfg, kern, a);
+    e = cudaLaunchKernelEx(&cfg, kern, aa);
   }
   if (e) return cuda_err(c, e, "k_sweep launch");
   return LRP_OK;

@@ -22,27 +22,14 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "tri_common.cuh"
 
 namespace lrp {
 
 // ---------------------------------------------------------------------------
 // Factorisation (one CTA of P threads, FP64).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double b_lo(const double* lo, const double* up, int n, double dt,
-                                       int adj, int r) {
-  if (r <= 0 || r >= n) return 0.0;
-  return dt * (adj ? up[r - 1] : lo[r]);
-}
-__device__ __forceinline__ double b_di(const double* di, int n, double dt, int r) {
-  return r < n ? 1.0 + dt * di[r] : 1.0;
-}
-__device__ __forceinline__ double b_up(const double* lo, const double* up, int n, double dt,
-                                       int adj, int r) {
-  if (r >= n - 1) return 0.0;
-  return dt * (adj ? lo[r + 1] : up[r]);
-}
-
-__global__ void k_tri_factor(const double* __restrict__ lo, const double* __restrict__ di,
+__global__ void __launch_bounds__(1024) k_tri_factor(const double* __restrict__ lo, const double* __restrict__ di,
                              const double* __restrict__ up, int n, double dt, int adj, int m,
                              int P, int L, double* __restrict__ coef, float* __restrict__ coef32,
                              double* __restrict__ pcr, float* __restrict__ pcr32,
@@ -170,8 +157,10 @@ struct TriKArgs {
   PropSrc src;
 };
 
+// At most 512 threads per CTA, so that up to 128 registers per thread keep the
+// whole chunk state (MM values) in registers.
 template <typename T, int MM>
-__global__ void __launch_bounds__(1024) k_tri_propagate(TriKArgs a) {
+__global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_coef = reinterpret_cast<T*>(smem_raw);                 // [5][MM][P]
   const int P = a.P, L = a.L, G = a.G;
@@ -299,7 +288,7 @@ lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** 
   pl->n = op->n;
   pl->m = choose_m(op->n);
   pl->P = (op->n + pl->m - 1) / pl->m;
-  if (pl->P > 1024) return set_err(c, LRP_EINVAL, "tridiagonal operator too large (n > 32768)");
+  if (pl->P > 512) return set_err(c, LRP_EINVAL, "tridiagonal operator too large (n > 16384)");
   int L = 0;
   while ((1 << L) < pl->P) ++L;
   pl->levels = L;

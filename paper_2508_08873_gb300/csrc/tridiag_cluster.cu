@@ -1,0 +1,504 @@
+// Tridiagonal backward-Euler propagation with one system spread over a
+// thread-block cluster of C CTAs (C = 2 or 4), for batches too small to fill
+// the GPU with one CTA per system (the Parareal fine solves: one system per
+// coarse interval, FP64).
+//
+// The partitioned solve of tridiag.cu is applied on two levels:
+//   * rows -> chunks of m rows (one thread each): interior Thomas substitution
+//     and spikes, leaving one interface unknown y_t per chunk;
+//   * chunks -> C CTAs of Pc chunks: in every CTA the interface unknowns but
+//     the last form a local tridiagonal system, solved by parallel cyclic
+//     reduction with precomputed factors, whose solution is
+//     z0 - P2 Y_{c-1} - Q2 Y_c in terms of the last interface unknowns Y_c of
+//     the CTAs; these C unknowns satisfy a small tridiagonal "super" system
+//     with a precomputed LU factorisation, which every CTA solves redundantly
+//     after one exchange of 4 scalars per CTA through distributed shared
+//     memory.
+// So each implicit-Euler step costs one cluster barrier, and each CTA holds
+// only its own slice of the factorisation in shared memory.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "common.cuh"
+#include "internal.h"
+#include "tri_common.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace lrp {
+
+constexpr int CL_MAXC = 4;
+
+// index helpers for the per-CTA layouts
+__host__ __device__ __forceinline__ size_t cl_coef(int c, int k, int i, int tl, int m, int Pc) {
+  return (((size_t)c * 5 + k) * m + i) * Pc + tl;
+}
+
+// ---------------------------------------------------------------------------
+// Factorisation (one CTA of P threads, FP64).  Outputs (see ClPlan):
+//   coef [C][5][m][Pc]; lpcr [C][2L+1][Pc]; spk [C][2][Pc]; sup [C][6].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_tri_factor_cl(const double* __restrict__ lo, const double* __restrict__ di,
+                                const double* __restrict__ up, int n, double dt, int adj, int m,
+                                int P, int C, int L, double* __restrict__ coef,
+                                double* __restrict__ lpcr, double* __restrict__ spk,
+                                double* __restrict__ sup, int* __restrict__ status) {
+  extern __shared__ double sh[];
+  double* ag = sh;             // interface system (whole system)
+  double* bg = ag + P;
+  double* cg_ = bg + P;
+  double* p0 = cg_ + P;
+  double* q0 = p0 + P;
+  double* la = q0 + P;         // local PCR state
+  double* lb = la + P;
+  double* lc = lb + P;
+  double* r1 = lc + P;
+  double* r2 = r1 + P;
+  double* cEs = r2 + P;
+  const int t = threadIdx.x;
+  const int Pc = P / C, Pl = Pc - 1;
+  const int c = t / Pc, tl = t % Pc;
+  const int mi = m - 1;
+  int bad = 0;
+  double pl = 0, ql = 0, aE = 0, bE = 1, cE = 0;
+  if (t < P) {
+    const int r0 = t * m;
+    double piv = b_di(di, n, dt, r0);
+    if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = 1;
+    double* cl = coef + cl_coef(c, 0, 0, tl, m, Pc);
+    double* ci = coef + cl_coef(c, 1, 0, tl, m, Pc);
+    double* cu = coef + cl_coef(c, 2, 0, tl, m, Pc);
+    double* cp = coef + cl_coef(c, 3, 0, tl, m, Pc);
+    double* cq = coef + cl_coef(c, 4, 0, tl, m, Pc);
+    cl[0] = 0.0;
+    ci[0] = 1.0 / piv;
+    for (int i = 1; i < mi; ++i) {
+      int r = r0 + i;
+      double mult = b_lo(lo, up, n, dt, adj, r) / piv;
+      piv = b_di(di, n, dt, r) - mult * b_up(lo, up, n, dt, adj, r - 1);
+      if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = 1;
+      cl[(size_t)i * Pc] = mult;
+      ci[(size_t)i * Pc] = 1.0 / piv;
+    }
+    for (int i = 0; i < mi; ++i)
+      cu[(size_t)i * Pc] = (i < mi - 1) ? b_up(lo, up, n, dt, adj, r0 + i) * ci[(size_t)i * Pc] : 0.0;
+    const double left = b_lo(lo, up, n, dt, adj, r0);
+    const double right = b_up(lo, up, n, dt, adj, r0 + mi - 1);
+    double fp = left, fq = (mi == 1) ? right : 0.0;
+    cp[0] = fp;
+    cq[0] = fq;
+    for (int i = 1; i < mi; ++i) {
+      double mult = cl[(size_t)i * Pc];
+      fp = 0.0 - mult * fp;
+      fq = ((i == mi - 1) ? right : 0.0) - mult * fq;
+      cp[(size_t)i * Pc] = fp;
+      cq[(size_t)i * Pc] = fq;
+    }
+    double gp = 0.0, gq = 0.0;
+    for (int i = mi - 1; i >= 0; --i) {
+      size_t k = (size_t)i * Pc;
+      gp = cp[k] * ci[k] - cu[k] * gp;
+      gq = cq[k] * ci[k] - cu[k] * gq;
+      cp[k] = gp;
+      cq[k] = gq;
+    }
+    pl = cp[(size_t)(mi - 1) * Pc];
+    ql = cq[(size_t)(mi - 1) * Pc];
+    const int e = r0 + mi;
+    aE = b_lo(lo, up, n, dt, adj, e);
+    bE = b_di(di, n, dt, e);
+    cE = b_up(lo, up, n, dt, adj, e);
+    size_t k = (size_t)mi * Pc;
+    cl[k] = aE;
+    ci[k] = bE;
+    cu[k] = cE;
+    cp[k] = 0.0;
+    cq[k] = 0.0;
+    p0[t] = cp[0];
+    q0[t] = cq[0];
+    cEs[t] = cE;
+  }
+  __syncthreads();
+  if (t < P) {
+    double pn = (t + 1 < P) ? p0[t + 1] : 0.0;
+    double qn = (t + 1 < P) ? q0[t + 1] : 0.0;
+    ag[t] = -aE * pl;
+    bg[t] = bE - aE * ql - cE * pn;
+    cg_[t] = -cE * qn;
+  }
+  __syncthreads();
+  // ---- local PCR factors over each CTA's unknowns tl = 0 .. Pl-1 -------------
+  if (t < P) {
+    la[t] = (tl > 0 && tl < Pl) ? ag[t] : 0.0;
+    lb[t] = (tl < Pl) ? bg[t] : 1.0;
+    lc[t] = (tl < Pl - 1) ? cg_[t] : 0.0;
+  }
+  __syncthreads();
+  double* lp = lpcr + (size_t)c * (2 * L + 1) * Pc;
+  for (int lev = 0, s = 1; lev < L; ++lev, s <<= 1) {
+    double na = 0, nb = 1, nc = 0, k1 = 0, k2 = 0;
+    if (t < P && tl < Pl) {
+      double a = la[t], b = lb[t], cc = lc[t];
+      double a1 = 0, b1 = 1, c1 = 0, a2 = 0, b2 = 1, c2 = 0;
+      bool hm = tl - s >= 0, hp = tl + s < Pl;
+      if (hm) { a1 = la[t - s]; b1 = lb[t - s]; c1 = lc[t - s]; }
+      if (hp) { a2 = la[t + s]; b2 = lb[t + s]; c2 = lc[t + s]; }
+      k1 = hm ? a / b1 : 0.0;
+      k2 = hp ? cc / b2 : 0.0;
+      na = -k1 * a1;
+      nc = -k2 * c2;
+      nb = b - k1 * c1 - k2 * a2;
+      if (!(fabs(nb) > 0.0) || !isfinite(nb)) bad = 1;
+    }
+    if (t < P) {
+      lp[(size_t)lev * Pc + tl] = k1;
+      lp[(size_t)(L + lev) * Pc + tl] = k2;
+    }
+    __syncthreads();
+    if (t < P && tl < Pl) { la[t] = na; lb[t] = nb; lc[t] = nc; }
+    __syncthreads();
+  }
+  if (t < P) lp[(size_t)(2 * L) * Pc + tl] = (tl < Pl) ? 1.0 / lb[t] : 0.0;
+  // ---- spikes of the local systems: P2 (left coupling), Q2 (right) ----------
+  if (t < P) {
+    r1[t] = (tl == 0 && Pl > 0) ? ag[t] : 0.0;
+    r2[t] = (tl == Pl - 1) ? cg_[t] : 0.0;
+  }
+  __syncthreads();
+  for (int lev = 0, s = 1; lev < L; ++lev, s <<= 1) {
+    double n1 = 0, n2 = 0;
+    if (t < P && tl < Pl) {
+      double k1 = lp[(size_t)lev * Pc + tl], k2 = lp[(size_t)(L + lev) * Pc + tl];
+      double m1 = tl - s >= 0 ? r1[t - s] : 0.0, m2 = tl - s >= 0 ? r2[t - s] : 0.0;
+      double p1 = tl + s < Pl ? r1[t + s] : 0.0, p2 = tl + s < Pl ? r2[t + s] : 0.0;
+      n1 = r1[t] - k1 * m1 - k2 * p1;
+      n2 = r2[t] - k1 * m2 - k2 * p2;
+    }
+    __syncthreads();
+    if (t < P && tl < Pl) { r1[t] = n1; r2[t] = n2; }
+    __syncthreads();
+  }
+  if (t < P) {
+    double dv = (tl < Pl) ? lp[(size_t)(2 * L) * Pc + tl] : 0.0;
+    spk[((size_t)c * 2 + 0) * Pc + tl] = r1[t] * dv;
+    spk[((size_t)c * 2 + 1) * Pc + tl] = r2[t] * dv;
+  }
+  __syncthreads();
+  // ---- super system over the last interface unknown of every CTA ------------
+  if (t == 0) {
+    double piv_prev = 1.0, gs_prev = 0.0;
+    for (int cc = 0; cc < C; ++cc) {
+      int tc = cc * Pc + Pc - 1;
+      double P2l = spk[((size_t)cc * 2 + 0) * Pc + Pl - 1];
+      double Q2l = spk[((size_t)cc * 2 + 1) * Pc + Pl - 1];
+      double P2n = cc + 1 < C ? spk[((size_t)(cc + 1) * 2 + 0) * Pc + 0] : 0.0;
+      double Q2n = cc + 1 < C ? spk[((size_t)(cc + 1) * 2 + 1) * Pc + 0] : 0.0;
+      double as = -ag[tc] * P2l;
+      double bs = bg[tc] - ag[tc] * Q2l - cg_[tc] * P2n;
+      double gs = -cg_[tc] * Q2n;
+      double mult = cc > 0 ? as / piv_prev : 0.0;
+      double piv = bs - mult * gs_prev;
+      if (!(fabs(piv) > 0.0) || !isfinite(piv)) bad = 1;
+      double* su = sup + (size_t)cc * 6;
+      su[0] = ag[tc];
+      su[1] = cg_[tc];
+      su[2] = cEs[tc];
+      su[3] = mult;
+      su[4] = 1.0 / piv;
+      su[5] = gs;
+      piv_prev = piv;
+      gs_prev = gs;
+    }
+  }
+  if (bad) atomicOr(status, 1);
+}
+
+__global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) b[k] = (float)a[k];
+}
+
+// ---------------------------------------------------------------------------
+// Propagation kernel: cluster of C CTAs per system, blockDim = Pc (one chunk
+// per thread).  Clusters loop over systems.
+// ---------------------------------------------------------------------------
+struct ClKArgs {
+  int n, Pc, C, L, M, nsys;
+  double dt;
+  const void* coef;
+  const void* lpcr;
+  const void* spk;
+  const void* sup;
+  PropIn in;
+  PropOut out;
+  PropSrc src;
+};
+
+template <typename T, int MM>
+__global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int Pc = a.Pc, L = a.L, C = a.C, Pl = Pc - 1;
+  const int c = (int)cl.block_rank();
+  T* s_coef = reinterpret_cast<T*>(smem_raw);            // [5][MM][Pc]
+  T* s_pcr = s_coef + 5 * MM * Pc;                        // [2L+1][Pc]
+  T* s_spk = s_pcr + (2 * L + 1) * Pc;                    // [2][Pc]
+  T* s_sup = s_spk + 2 * Pc;                              // [C][6]
+  T* xb = s_sup + 6 * CL_MAXC;                            // [3][Pc]
+  T* Ysh = xb + 3 * Pc;                                   // [CL_MAXC]
+  __shared__ double pub[2][4];
+  {
+    const T* gco = static_cast<const T*>(a.coef) + (size_t)c * 5 * MM * Pc;
+    const T* gpc = static_cast<const T*>(a.lpcr) + (size_t)c * (2 * L + 1) * Pc;
+    const T* gsp = static_cast<const T*>(a.spk) + (size_t)c * 2 * Pc;
+    const T* gsu = static_cast<const T*>(a.sup);
+    for (int k = threadIdx.x; k < 5 * MM * Pc; k += blockDim.x) s_coef[k] = gco[k];
+    for (int k = threadIdx.x; k < (2 * L + 1) * Pc; k += blockDim.x) s_pcr[k] = gpc[k];
+    for (int k = threadIdx.x; k < 2 * Pc; k += blockDim.x) s_spk[k] = gsp[k];
+    for (int k = threadIdx.x; k < 6 * C; k += blockDim.x) s_sup[k] = gsu[k];
+  }
+  __syncthreads();
+  const int tl = threadIdx.x;
+  const int t = c * Pc + tl;
+  const T* cl_ = s_coef;
+  const T* ci = s_coef + MM * Pc;
+  const T* cu = s_coef + 2 * MM * Pc;
+  const T* cp = s_coef + 3 * MM * Pc;
+  const T* cq = s_coef + 4 * MM * Pc;
+  const T dt = (T)a.dt;
+  const int n = a.n;
+  const int r0 = t * MM;
+  const int nclu = gridDim.x / C;
+  int pb = 0;
+  for (int sys = blockIdx.x / C; sys < a.nsys; sys += nclu) {
+    T x[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      int r = r0 + i;
+      T v = T(0);
+      if (r < n) {
+        if (a.in.gen)
+          v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                       (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+        else if (a.in.x == nullptr)
+          v = T(0);
+        else if (a.in.x_f64)
+          v = (T) static_cast<const double*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+        else
+          v = (T) static_cast<const float*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+      }
+      x[i] = v;
+    }
+    const double* csys = a.src.Q > 0 ? a.src.c + (size_t)sys * a.src.cstride : nullptr;
+    for (int j = 0; j < a.M; ++j) {
+      if (csys) {
+        for (int q = 0; q < a.src.Q; ++q) {
+          T cq_ = dt * (T)csys[(size_t)j * a.src.Q + q];
+          const double* gq = a.src.g + (size_t)q * n;
+#pragma unroll
+          for (int i = 0; i < MM; ++i)
+            if (r0 + i < n) x[i] += cq_ * (T)gq[r0 + i];
+        }
+      }
+#pragma unroll
+      for (int i = 1; i < MM - 1; ++i) x[i] -= cl_[i * Pc + tl] * x[i - 1];
+      x[MM - 2] *= ci[(MM - 2) * Pc + tl];
+#pragma unroll
+      for (int i = MM - 3; i >= 0; --i) x[i] = x[i] * ci[i * Pc + tl] - cu[i * Pc + tl] * x[i + 1];
+      xb[2 * Pc + tl] = x[0];
+      __syncthreads();
+      T gnext = (tl + 1 < Pc) ? xb[2 * Pc + tl + 1] : T(0);
+      T r = x[MM - 1] - cl_[(MM - 1) * Pc + tl] * x[MM - 2] - cu[(MM - 1) * Pc + tl] * gnext;
+      // local parallel cyclic reduction (unknowns 0 .. Pl-1 of this CTA)
+      int buf = 0;
+      for (int lev = 0, s = 1; lev < L; ++lev, s <<= 1) {
+        xb[buf * Pc + tl] = r;
+        __syncthreads();
+        if (tl < Pl) {
+          T rm = (tl - s >= 0) ? xb[buf * Pc + tl - s] : T(0);
+          T rp = (tl + s < Pl) ? xb[buf * Pc + tl + s] : T(0);
+          r = r - s_pcr[lev * Pc + tl] * rm - s_pcr[(L + lev) * Pc + tl] * rp;
+        }
+        buf ^= 1;
+      }
+      const T z0 = (tl < Pl) ? r * s_pcr[2 * L * Pc + tl] : T(0);
+      // publish the values the super system needs, then one cluster barrier
+      if (tl == 0) { pub[pb][0] = (double)z0; pub[pb][3] = (double)x[0]; }
+      if (tl == Pl - 1) pub[pb][1] = (double)z0;
+      if (tl == Pc - 1) pub[pb][2] = (double)r;
+      cl.sync();
+      if (tl == 0) {
+        // gather the 4 published scalars of every CTA, then solve the C x C
+        // super system by its precomputed LU (fixed-size unrolled loops)
+        double zf[CL_MAXC], zl[CL_MAXC], rpart[CL_MAXC], g0[CL_MAXC], w[CL_MAXC];
+#pragma unroll
+        for (int q = 0; q < CL_MAXC; ++q) {
+          zf[q] = zl[q] = rpart[q] = g0[q] = w[q] = 0.0;
+          if (q < C) {
+            const double* pp = cl.map_shared_rank(&pub[pb][0], q);
+            zf[q] = pp[0]; zl[q] = pp[1]; rpart[q] = pp[2]; g0[q] = pp[3];
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < CL_MAXC; ++q) {
+          if (q < C) {
+            const T* su = s_sup + 6 * q;
+            double v = rpart[q] - (double)su[0] * zl[q];
+            if (q + 1 < C) v -= (double)su[2] * g0[q + 1] + (double)su[1] * zf[q + 1];
+            w[q] = v - (q > 0 ? (double)su[3] * w[q - 1] : 0.0);
+          }
+        }
+        double Y = 0.0;
+#pragma unroll
+        for (int q = CL_MAXC - 1; q >= 0; --q) {
+          if (q < C) {
+            Y = (w[q] - (q + 1 < C ? (double)s_sup[6 * q + 5] * Y : 0.0)) * (double)s_sup[6 * q + 4];
+            Ysh[q] = (T)Y;
+          }
+        }
+      }
+      __syncthreads();
+      const T Yl = c > 0 ? Ysh[c - 1] : T(0);
+      const T Yc = Ysh[c];
+      const T y = (tl < Pl) ? z0 - s_spk[tl] * Yl - s_spk[Pc + tl] * Yc : Yc;
+      xb[buf * Pc + tl] = y;
+      __syncthreads();
+      const T yl = (tl > 0) ? xb[buf * Pc + tl - 1] : Yl;
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - cp[i * Pc + tl] * yl - cq[i * Pc + tl] * y;
+      x[MM - 1] = y;
+      pb ^= 1;
+    }
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      int r = r0 + i;
+      if (r < n) {
+        if (a.out.y_f64)
+          static_cast<double*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (double)x[i];
+        else
+          static_cast<float*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (float)x[i];
+      }
+    }
+    __syncthreads();
+  }
+  cl.sync();  // remote reads of pub have finished before any CTA exits
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+static constexpr int CL_M = 16;
+
+lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C,
+                                ClPlan** out) {
+  for (auto& p : op->cplans)
+    if (p->dt == dt && p->adjoint == adjoint && p->C == C) { *out = p.get(); return LRP_OK; }
+  auto pl = std::make_unique<ClPlan>();
+  pl->dt = dt;
+  pl->adjoint = adjoint;
+  pl->C = C;
+  pl->n = op->n;
+  pl->m = CL_M;
+  int P = (op->n + CL_M - 1) / CL_M;
+  P = (P + C - 1) / C * C;
+  pl->P = P;
+  pl->Pc = P / C;
+  if (pl->Pc < 32 || pl->Pc > 256 || P > 1024)
+    return set_err(c, LRP_EINVAL, "cluster tridiagonal plan out of range");
+  int L = 0;
+  while ((1 << L) < pl->Pc - 1) ++L;
+  pl->L = L;
+  const size_t ncoef = (size_t)5 * CL_M * P, npcr = (size_t)C * (2 * L + 1) * pl->Pc,
+               nspk = (size_t)2 * P, nsup = 6 * CL_MAXC;
+  pl->sz[0] = ncoef; pl->sz[1] = npcr; pl->sz[2] = nspk; pl->sz[3] = nsup;
+  lrp_status s;
+  for (int k = 0; k < 4; ++k) {
+    if ((s = dev_alloc(c, pl->b64[k], pl->sz[k] * 8))) return s;
+    if ((s = dev_alloc(c, pl->b32[k], pl->sz[k] * 4))) return s;
+    cudaMemsetAsync(pl->b64[k].ptr, 0, pl->sz[k] * 8, c->stream);
+  }
+  if ((s = dev_alloc(c, pl->status, sizeof(int)))) return s;
+  cudaMemsetAsync(pl->status.ptr, 0, sizeof(int), c->stream);
+  int threads = ((P + 31) / 32) * 32;
+  cudaError_t e0 = cudaFuncSetAttribute(k_tri_factor_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(11 * P * sizeof(double)));
+  if (e0) return cuda_err(c, e0, "cluster factor smem attribute");
+  k_tri_factor_cl<<<1, threads, 11 * P * sizeof(double), c->stream>>>(
+      op->a64[0].as<double>(), op->a64[1].as<double>(), op->a64[2].as<double>(), op->n, dt,
+      adjoint, CL_M, P, C, L, pl->b64[0].as<double>(), pl->b64[1].as<double>(),
+      pl->b64[2].as<double>(), pl->b64[3].as<double>(), pl->status.as<int>());
+  cudaError_t e = cudaGetLastError();
+  if (e) return cuda_err(c, e, "k_tri_factor_cl launch");
+  for (int k = 0; k < 4; ++k)
+    k_to_f32<<<(unsigned)((pl->sz[k] + 255) / 256), 256, 0, c->stream>>>(
+        pl->b64[k].as<double>(), pl->b32[k].as<float>(), pl->sz[k]);
+  int st = 0;
+  e = cudaMemcpyAsync(&st, pl->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "k_tri_factor_cl");
+  if (st) return set_err(c, LRP_EBREAKDOWN, "zero pivot in the tridiagonal factorisation");
+  *out = pl.get();
+  op->cplans.push_back(std::move(pl));
+  return LRP_OK;
+}
+
+template <typename T>
+static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  const int Pc = pl->Pc, L = pl->L, C = pl->C;
+  size_t smem = sizeof(T) * ((size_t)5 * CL_M * Pc + (size_t)(2 * L + 1) * Pc + 2 * Pc +
+                             6 * CL_MAXC + 3 * Pc + CL_MAXC);
+  auto kern = k_tri_cluster<T, CL_M>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return cuda_err(c, e, "cluster tri smem attribute");
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(Pc);
+  cfg.gridDim = dim3(C);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = c->stream;
+  int maxc = 0;
+  e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+  if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
+  const int ncl = std::min(a.nsys, maxc);
+  cfg.gridDim = dim3(ncl * C);
+  const char* fam = sizeof(T) == 8 ? "propagate_f64" : "propagate_f32";
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, fam, &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  timer_end(c, fam, ev);
+  if (e) return cuda_err(c, e, "k_tri_cluster launch");
+  return LRP_OK;
+}
+
+lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, const PropIn& in,
+                                 const PropOut& out, const PropSrc& src) {
+  if (nsys <= 0) return LRP_OK;
+  ClKArgs a{};
+  a.n = pl->n;
+  a.Pc = pl->Pc;
+  a.C = pl->C;
+  a.L = pl->L;
+  a.M = M;
+  a.nsys = nsys;
+  a.dt = pl->dt;
+  a.in = in;
+  a.out = out;
+  a.src = src;
+  const int f = prec == 0 ? 0 : 1;
+  DevBuf* b = f ? pl->b32 : pl->b64;
+  a.coef = b[0].ptr;
+  a.lpcr = b[1].ptr;
+  a.spk = b[2].ptr;
+  a.sup = b[3].ptr;
+  return f ? launch_cl<float>(c, pl, a) : launch_cl<double>(c, pl, a);
+}
+
+}  // namespace lrp

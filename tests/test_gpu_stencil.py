@@ -1,0 +1,130 @@
+"""GPU parity of the 2D (5-point stencil) hot path against the FP64 oracle.
+
+The per-step solves are Krylov (CG for the symmetric diffusion operator,
+BiCGStab for the upwind advection-diffusion operator); the oracle solves every
+step with a banded LU.  Parity tests tighten the Krylov tolerance to 1e-14 so
+that the comparison is limited by rounding, and compare at 1e-10 relative L2
+(FP64); the FP32 path is compared at the tolerance its rtol 1e-6 allows.
+Grids: 15^2 .. 255^2, so that one-CTA and multi-CTA cluster systems are both
+exercised.
+"""
+import numpy as np
+import pytest
+
+from paper_2508_08873_gb300 import _native, api, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    return api.Context(0)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def _problem(kind, m):
+    if kind == "diff":
+        st = W.diff2d_op(m, 10 ** np.random.default_rng(0).uniform(0, 2, (8, 8)))
+    else:
+        st = W.adv2d_op(m, 0.01)
+    return st
+
+
+def _ops(ctx, orc, kind, m, rtol64=1e-14, rtol32=1e-6):
+    st = _problem(kind, m)
+    op = api.Operator.stencil5(ctx, m, m, st)
+    op.set_krylov(rtol64, rtol32, 20000)
+    oop = orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"])
+    return op, oop
+
+
+@pytest.mark.parametrize("kind", ["diff", "adv"])
+@pytest.mark.parametrize("m", [15, 63, 127])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_stencil_propagate_f64_parity(ctx, orc, kind, m, adjoint):
+    op, oop = _ops(ctx, orc, kind, m)
+    dt, M = 1.0 / 2048, 4
+    X = np.random.default_rng(m).standard_normal((3, m * m))
+    got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+    want = orc.propagate(oop, dt, M, X, adjoint=adjoint)
+    for v in range(3):
+        e = rel(got[v], want[v])
+        assert e <= 1e-10, e
+    assert op.krylov_iterations() > 0
+
+
+def test_stencil_propagate_large_cluster(ctx, orc):
+    """255^2 grid: the system spans an 8-CTA cluster."""
+    op, oop = _ops(ctx, orc, "adv", 255, rtol64=1e-13)
+    dt, M = 1.0 / 2048, 2
+    X = np.random.default_rng(1).standard_normal((2, 255 * 255))
+    got = api.propagate(ctx, op, dt, M, X)
+    want = orc.propagate(oop, dt, M, X)
+    for v in range(2):
+        assert rel(got[v], want[v]) <= 1e-9
+
+
+@pytest.mark.parametrize("kind", ["diff", "adv"])
+def test_stencil_propagate_f32(ctx, orc, kind):
+    op, oop = _ops(ctx, orc, kind, 63)
+    dt, M = 1.0 / 4096, 8
+    X = np.random.default_rng(2).standard_normal((4, 63 * 63))
+    got = api.propagate(ctx, op, dt, M, X, prec="mixed")
+    want = orc.propagate(oop, dt, M, X)
+    for v in range(4):
+        assert rel(got[v], want[v]) <= 5e-5
+
+
+def test_stencil_source_and_batch(ctx, orc):
+    m, dt, M = 31, 1.0 / 1024, 5
+    op, oop = _ops(ctx, orc, "diff", m)
+    g = np.random.default_rng(3).standard_normal((2, m * m))
+    c = np.random.default_rng(4).standard_normal((7, M, 2))
+    X = np.random.default_rng(5).standard_normal((7, m * m))
+    got = api.propagate(ctx, op, dt, M, X, g=g, c=c)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=c)
+    for v in range(7):
+        assert rel(got[v], want[v]) <= 1e-10
+
+
+def test_stencil_iteration_cap_reports_notconv(ctx, orc):
+    op, oop = _ops(ctx, orc, "diff", 31)
+    op.set_krylov(1e-14, 1e-6, 2)
+    X = np.random.default_rng(6).standard_normal((2, 31 * 31))
+    with pytest.raises(_native.LrpError) as ei:
+        api.propagate(ctx, op, 1.0 / 64, 3, X)
+    assert ei.value.status == _native.LRP_ENOTCONV
+
+
+@pytest.mark.parametrize("kind", ["diff", "adv"])
+def test_stencil_build_and_parareal_f64(ctx, orc, kind):
+    m = 31
+    if kind == "diff":
+        P = W.diff2d(m=m, N=4, M=8, R=5, p=3)
+    else:
+        P = W.adv2d(0, m=m, N=4, M=8, R=5, p=3)
+    op = api.Operator.stencil5(ctx, m, m, P.st)
+    op.set_krylov(1e-14, 1e-6, 20000)
+    oop = orc.Stencil5(m, m, P.st["C"], P.st["W"], P.st["E"], P.st["S"], P.st["N"])
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    info = co.info()
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    probes = np.random.default_rng(7).standard_normal((3, P.n))
+    for i in range(P.N):
+        oc = oco.intervals[i]
+        s1 = oc.sigma[0]
+        assert info["R"][i] == oc.S.shape[0]
+        assert np.max(np.abs(info["sigma"][i, :oc.S.shape[0]] - oc.S)) <= 1e-9 * s1
+        U, S, V = co.factors(i)
+        Go = oc.U @ np.diag(oc.S) @ oc.V.T
+        Gg = U.T @ np.diag(S) @ V
+        assert max(np.linalg.norm((Gg - Go) @ x) / np.linalg.norm(x) for x in probes) <= 1e-9 * s1
+    u, pinfo = api.parareal_solve(ctx, co, P.u0, K=2)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, K=2)
+    assert rel(u, res.iterates[-1]) <= 1e-9
+    u, pinfo = api.parareal_solve(ctx, co, P.u0, K=P.N)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+    assert orc.rel_err(u, ref) <= 1e-10

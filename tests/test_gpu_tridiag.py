@@ -255,3 +255,21 @@ def test_parareal_invalid_arguments(ctx):
         api.Coarse(ctx, op, P.dt, P.M, P.N, 40, 1, 0)       # rank + p > n
     with pytest.raises(_native.LrpError):
         api.Coarse(ctx, op, -1.0, P.M, P.N, 2, 1, 0)
+
+
+@pytest.mark.parametrize("n,nvec", [(2048, 60), (4095, 5), (4095, 60), (7777, 3), (16384, 2)])
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_propagate_cluster_paths_f64(ctx, orc, n, nvec, adjoint):
+    """Batches small enough to spread each system over a 2- or 4-CTA cluster."""
+    lo, di, up = W.adr1d_op(n)
+    dt, M = 1.0 / 16384, 7
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    X = np.random.default_rng(n + nvec).standard_normal((nvec, n))
+    got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+    want = orc.propagate(orc.Tridiag(lo, di, up), dt, M, X, adjoint=adjoint)
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    e = max(rel(got[v], want[v]) for v in range(nvec))
+    assert e <= tol, (e, tol)
+    got32 = api.propagate(ctx, op, dt, M, X[:2], adjoint=adjoint, prec="mixed")
+    assert max(rel(got32[v], want[v]) for v in range(2)) <= 2e-5
