@@ -45,7 +45,8 @@ typedef enum {
   LRP_EBREAKDOWN = 4,  /* a zero pivot or a breakdown in an iterative solver */
   LRP_ETIMEOUT = 5,    /* a bounded device wait expired */
   LRP_ECUDA = 6,       /* a CUDA runtime error; see lrp_last_error() */
-  LRP_EBUSY = 7        /* the request queue is full */
+  LRP_EBUSY = 7,       /* the request queue is full */
+  LRP_PENDING = 8      /* a served request has not finished yet */
 } lrp_status;
 
 /* Arithmetic of the coarse-solver build (rSVD steps 1-6).
@@ -82,7 +83,9 @@ long lrp_launch_count(lrp_ctx* ctx);
 /* Launch tuning (0 = automatic, the default):
  *   "sweep_cluster": CTAs per thread-block cluster of the coarse sweep (1..16,
  *                    a power of two);
- *   "tri_cluster":   CTAs per tridiagonal system for small batches (1, 2, 4).
+ *   "tri_cluster":   CTAs per tridiagonal system for small batches (1, 2, 4);
+ *   "queue_cluster": CTAs per cluster of the batched 2D work queue (1..16,
+ *                    a power of two).
  * Results do not depend on these settings beyond rounding. */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);
 lrp_status lrp_get_param(lrp_ctx* ctx, const char* name, int* value);
@@ -220,6 +223,78 @@ lrp_status lrp_parareal_solve(lrp_ctx* ctx, const lrp_coarse* co, const double* 
 lrp_status lrp_fine_solution(lrp_ctx* ctx, const lrp_operator* op, double dt, int M, int N,
                              const double* u0, int Q, const double* g, const double* c,
                              double* u_out);
+
+/* ---- many 2D problems of uneven size at once ------------------------------ */
+
+/* Coarse solvers for `count` 5-point operators (grids may differ) sharing the
+ * time grid, rank, oversampling, seed and precision.  Each propagation stage
+ * of the randomized SVD runs as one persistent launch over a device work
+ * queue of (problem, system) items, largest grids first, and the whole build
+ * is captured into one CUDA graph and launched once.  out[p] receives the
+ * handle of problem p (free each with lrp_coarse_free).  The queue's cluster
+ * size is the "queue_cluster" parameter (default 4). */
+lrp_status lrp_build_coarse_batch(lrp_ctx* ctx, int count, lrp_operator* const* ops, double dt,
+                                  int M, int N, int rank, int oversample, uint64_t seed,
+                                  lrp_precision prec, lrp_coarse** out);
+/* Parareal (f = 0) for `count` 2D problems with handles from any build of
+ * equal N, M, rank and precision: per iteration the fine solves of all
+ * unconverged intervals of all problems run as one queue launch and the coarse
+ * sweeps are batched per grid size.  u0[p]: n_p values; u_out[p]: (N+1) x n_p
+ * (host or device); k_done[p]: iterations of problem p (tol as in
+ * lrp_parareal_solve, per problem). */
+lrp_status lrp_parareal_solve_batch(lrp_ctx* ctx, int count, lrp_coarse* const* cos,
+                                    const double* const* u0, int K_max, double tol,
+                                    double* const* u_out, int* k_done);
+
+/* ---- serving: continuous batching over resident coarse solvers ----------- */
+
+/* The coarse solvers depend on the operator and the time grid only (Sec. 2.1,
+ * Remark rem:affine_g_n), so built handles serve a stream of solves with new
+ * u0 and new sources.  A server owns a worker thread and its own context on
+ * the device of `ctx`.  Requests are admitted into slots (device memory for
+ * the iterate, F outputs, b_i and the source of one request; at most
+ * max_slots per coarse handle and as many as half the free HBM -- and the
+ * budget, if nonzero -- allow); waiting requests stay queued.  Each tick runs
+ * one Parareal iteration for every admitted request: the fine solves of all
+ * their unconverged intervals in one launch and all their coarse sweeps in
+ * one batched launch; requests arriving meanwhile join at the next tick.
+ * max_terms bounds Q (the number of source terms) of a request. */
+typedef struct lrp_server lrp_server;
+typedef struct {
+  int k_done;           /* Parareal iterations performed */
+  int status;           /* LRP_OK, LRP_ENOTCONV (tol not met by K_max), or an error */
+  double final_bound;   /* max_n a posteriori bound of the returned iterate */
+  double scale;         /* max_n ||u^k_n|| of the returned iterate */
+  double queue_ms;      /* submit -> admitted into a slot */
+  double latency_ms;    /* submit -> result ready on the host */
+} lrp_request_info;
+typedef struct {
+  unsigned long long completed, ticks;
+  size_t queued;
+  int active, slots, error;
+  double busy_ms;       /* worker time spent in ticks */
+} lrp_server_stats;
+
+lrp_status lrp_server_create(lrp_ctx* ctx, int max_slots, int max_terms,
+                             size_t hbm_budget_bytes, lrp_server** out);
+/* Stop the worker (requests still queued or running are abandoned) and free
+ * the server.  Coarse handles in use must outlive the server. */
+void lrp_server_destroy(lrp_server* srv);
+/* Queue a solve with coarse solvers `co` (same arguments as
+ * lrp_parareal_solve; host pointers; copied before the call returns).
+ * Returns LRP_EBUSY when the queue is full. */
+lrp_status lrp_server_submit(lrp_server* srv, const lrp_coarse* co, const double* u0, int Q,
+                             const double* g, const double* c, int K_max, double tol,
+                             uint64_t* ticket);
+/* Non-blocking: LRP_PENDING while the request runs; otherwise its status,
+ * with u_out ((N+1) x n, host, may be NULL) and info filled.  A finished
+ * request can be fetched once. */
+lrp_status lrp_server_poll(lrp_server* srv, uint64_t ticket, double* u_out,
+                           lrp_request_info* info);
+/* Blocking variant; timeout_s <= 0 waits without limit, else LRP_ETIMEOUT. */
+lrp_status lrp_server_wait(lrp_server* srv, uint64_t ticket, double timeout_s, double* u_out,
+                           lrp_request_info* info);
+lrp_status lrp_server_stats_get(lrp_server* srv, lrp_server_stats* stats);
 
 #ifdef __cplusplus
 }

@@ -50,6 +50,20 @@ class SolveStats(ctypes.Structure):
                 ("scale", ctypes.c_double), ("device_ms", ctypes.c_double)]
 
 
+class RequestInfo(ctypes.Structure):
+    _fields_ = [("k_done", ctypes.c_int), ("status", ctypes.c_int),
+                ("final_bound", ctypes.c_double), ("scale", ctypes.c_double),
+                ("queue_ms", ctypes.c_double), ("latency_ms", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_ulonglong), ("ticks", ctypes.c_ulonglong),
+                ("queued", ctypes.c_size_t), ("active", ctypes.c_int), ("slots", ctypes.c_int),
+                ("error", ctypes.c_int), ("busy_ms", ctypes.c_double)]
+
+
+LRP_PENDING = 8
+
 # (name, restype, argtypes)
 _P, _I, _D, _S, _U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64
 _PP = ctypes.POINTER(ctypes.c_void_p)
@@ -86,6 +100,14 @@ SIGNATURES = [
     ("lrp_parareal_solve", _I, [_P, _P, _P, _I, _P, _P, _I, _D, _P, _P, _PI,
                                 ctypes.POINTER(SolveStats)]),
     ("lrp_fine_solution", _I, [_P, _P, _D, _I, _I, _P, _I, _P, _P, _P]),
+    ("lrp_build_coarse_batch", _I, [_P, _I, _P, _D, _I, _I, _I, _I, _U64, _I, _P]),
+    ("lrp_parareal_solve_batch", _I, [_P, _I, _P, _P, _I, _D, _P, _P]),
+    ("lrp_server_create", _I, [_P, _I, _I, _S, _PP]),
+    ("lrp_server_destroy", None, [_P]),
+    ("lrp_server_submit", _I, [_P, _P, _P, _I, _P, _P, _I, _D, ctypes.POINTER(ctypes.c_uint64)]),
+    ("lrp_server_poll", _I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(RequestInfo)]),
+    ("lrp_server_wait", _I, [_P, ctypes.c_uint64, _D, _P, ctypes.POINTER(RequestInfo)]),
+    ("lrp_server_stats_get", _I, [_P, ctypes.POINTER(ServerStats)]),
 ]
 
 

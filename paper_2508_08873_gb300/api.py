@@ -221,6 +221,44 @@ class Coarse:
             pass
 
 
+def build_coarse_batch(ctx: Context, ops, dt: float, M: int, N: int, rank: int, oversample: int,
+                       seed: int = 0, prec="f64"):
+    """Coarse solvers of many 2D operators in one graph-captured build
+    (lrp_build_coarse_batch).  Returns a list of Coarse handles."""
+    cnt = len(ops)
+    harr = (ctypes.c_void_p * cnt)(*[o.h.value for o in ops])
+    outs = (ctypes.c_void_p * cnt)()
+    check(ctx.lib.lrp_build_coarse_batch(ctx.h, cnt, ctypes.cast(harr, ctypes.c_void_p), float(dt),
+                                         int(M), int(N), int(rank), int(oversample), int(seed),
+                                         _prec(prec), ctypes.cast(outs, ctypes.c_void_p)), ctx.h)
+    res = []
+    for i, o in enumerate(ops):
+        c = Coarse.__new__(Coarse)
+        c.ctx, c.op = ctx, o
+        c.dt, c.M, c.N, c.R, c.p = dt, M, N, rank, oversample
+        c.prec = _prec(prec)
+        c.h = ctypes.c_void_p(outs[i])
+        res.append(c)
+    return res
+
+
+def parareal_solve_batch(ctx: Context, cos, u0s, K: Optional[int] = None, tol: float = 0.0):
+    """Parareal for many 2D problems at once (lrp_parareal_solve_batch)."""
+    cnt = len(cos)
+    u0s = [np.ascontiguousarray(u, dtype=np.float64) for u in u0s]
+    outs = [np.empty((co.N + 1, co.op.n)) for co in cos]
+    harr = (ctypes.c_void_p * cnt)(*[co.h.value for co in cos])
+    uarr = (ctypes.c_void_p * cnt)(*[u.ctypes.data for u in u0s])
+    oarr = (ctypes.c_void_p * cnt)(*[o.ctypes.data for o in outs])
+    kd = np.zeros(cnt, dtype=np.int32)
+    st = ctx.lib.lrp_parareal_solve_batch(ctx.h, cnt, ctypes.cast(harr, ctypes.c_void_p),
+                                          ctypes.cast(uarr, ctypes.c_void_p),
+                                          cos[0].N if K is None else int(K), float(tol),
+                                          ctypes.cast(oarr, ctypes.c_void_p), kd.ctypes.data)
+    check(st, ctx.h)
+    return outs, kd
+
+
 def parareal_solve(ctx: Context, co: Coarse, u0, g=None, c=None, K: Optional[int] = None,
                    tol: float = 0.0, out=None, bounds: bool = True, allow_notconv: bool = True):
     """Parareal iterations (lrp_parareal_solve).  Returns (u (N+1, n), info)."""
@@ -262,3 +300,75 @@ def fine_solution(ctx: Context, op: Operator, dt: float, M: int, N: int, u0, g=N
     check(ctx.lib.lrp_fine_solution(ctx.h, op.h, float(dt), int(M), int(N), ptr(u0), Q, ptr(g),
                                     ptr(c), ptr(out)), ctx.h)
     return out
+
+
+class Server:
+    """Continuous-batching server over resident coarse solvers (lrp_server_*)."""
+
+    def __init__(self, ctx: Context, max_slots: int = 64, max_terms: int = 4, hbm_budget: int = 0):
+        self.ctx = ctx
+        self.lib = ctx.lib
+        h = ctypes.c_void_p()
+        check(self.lib.lrp_server_create(ctx.h, int(max_slots), int(max_terms), int(hbm_budget),
+                                         ctypes.byref(h)), ctx.h)
+        self.h = h
+        self._shape = {}
+
+    def submit(self, co: Coarse, u0, g=None, c=None, K: Optional[int] = None, tol: float = 1e-8) -> int:
+        u0 = np.ascontiguousarray(u0, dtype=np.float64)
+        Q = 0
+        if g is not None:
+            g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64)
+            c = np.ascontiguousarray(c, dtype=np.float64)
+            Q = g.shape[0]
+        t = ctypes.c_uint64()
+        st = self.lib.lrp_server_submit(self.h, co.h, u0.ctypes.data, Q,
+                                        g.ctypes.data if g is not None else None,
+                                        c.ctypes.data if c is not None else None,
+                                        co.N if K is None else int(K), float(tol), ctypes.byref(t))
+        if st != nat.LRP_OK:
+            raise nat.LrpError(st, "submit failed")
+        self._shape[t.value] = (co.N + 1, co.op.n)
+        return t.value
+
+    def _info(self, inf: "nat.RequestInfo", st: int) -> dict:
+        return dict(k_done=inf.k_done, status=inf.status, final_bound=inf.final_bound,
+                    scale=inf.scale, queue_ms=inf.queue_ms, latency_ms=inf.latency_ms,
+                    converged=(st == nat.LRP_OK))
+
+    def poll(self, ticket: int):
+        """(done, u, info); u is None while the request runs."""
+        u = np.empty(self._shape[ticket])
+        inf = nat.RequestInfo()
+        st = self.lib.lrp_server_poll(self.h, ticket, u.ctypes.data, ctypes.byref(inf))
+        if st == nat.LRP_PENDING:
+            return False, None, None
+        self._shape.pop(ticket, None)
+        if st not in (nat.LRP_OK, nat.LRP_ENOTCONV):
+            raise nat.LrpError(st, "served request failed")
+        return True, u, self._info(inf, st)
+
+    def wait(self, ticket: int, timeout: float = 0.0):
+        u = np.empty(self._shape[ticket])
+        inf = nat.RequestInfo()
+        st = self.lib.lrp_server_wait(self.h, ticket, float(timeout), u.ctypes.data, ctypes.byref(inf))
+        self._shape.pop(ticket, None)
+        if st not in (nat.LRP_OK, nat.LRP_ENOTCONV):
+            raise nat.LrpError(st, "served request failed")
+        return u, self._info(inf, st)
+
+    def stats(self) -> dict:
+        s = nat.ServerStats()
+        check(self.lib.lrp_server_stats_get(self.h, ctypes.byref(s)))
+        return {f: getattr(s, f) for f, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and not nat.exiting():
+            self.lib.lrp_server_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -211,7 +211,7 @@ lrp_status lrp_synchronize(lrp_ctx* c) {
 
 const char* lrp_last_error(lrp_ctx* c) { return c ? c->last_error.c_str() : ""; }
 
-size_t lrp_bytes_in_use(lrp_ctx* c) { return c ? c->in_use : 0; }
+size_t lrp_bytes_in_use(lrp_ctx* c) { return c ? c->in_use.load() : 0; }
 
 long lrp_launch_count(lrp_ctx* c) { return c ? c->launches : 0; }
 
@@ -224,6 +224,15 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_cluster") {
     if (value != 0 && value != 1 && value != 2 && value != 4) return LRP_EINVAL;
     c->p_tri_cluster = value;
+  } else if (k == "tri_spt") {
+    if (value != 0 && value != 1 && value != 2) return LRP_EINVAL;
+    c->p_tri_spt = value;
+  } else if (k == "tri_chunk") {
+    if (value != 0 && value != 8 && value != 16) return LRP_EINVAL;
+    c->p_tri_chunk = value;
+  } else if (k == "queue_cluster") {
+    if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
+    c->p_queue_cluster = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -235,6 +244,9 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   std::string k(name);
   if (k == "sweep_cluster") *value = c->p_sweep_cluster;
   else if (k == "tri_cluster") *value = c->p_tri_cluster;
+  else if (k == "queue_cluster") *value = c->p_queue_cluster;
+  else if (k == "tri_spt") *value = c->p_tri_spt;
+  else if (k == "tri_chunk") *value = c->p_tri_chunk;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
 }
@@ -336,26 +348,37 @@ namespace lrp {
 lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
                              int prec, const PropIn& in, const PropOut& out, const PropSrc& src);
 
-static lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
-                                int prec, const PropIn& in, const PropOut& out,
-                                const PropSrc& src) {
+lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys, int prec,
+                         const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (op->kind == 0) {
     // Small batches of long systems: spread every system over a cluster of
-    // 2 or 4 CTAs so that more SMs take part; otherwise one CTA per system.
-    int C = 1;
-    const int P = (op->n + 15) / 16;               // chunks of 16 rows
-    auto fits = [&](int cc) { int Pc = (P + cc - 1) / cc; return Pc >= 32 && Pc <= 256; };
-    if (c->p_tri_cluster > 1 && fits(c->p_tri_cluster)) {
+    // C CTAs (chunks of m rows, spt systems per thread) so that more SMs take
+    // part; otherwise one CTA per system.
+    int C = 1, m = 16, spt = 1;
+    auto fits = [&](int cc, int mm) {
+      int P = (op->n + mm - 1) / mm;
+      int Pc = (P + cc - 1) / cc;
+      return Pc >= 32 && Pc <= 256;
+    };
+    if (c->p_tri_cluster > 1) {
       C = c->p_tri_cluster;
+      m = c->p_tri_chunk ? c->p_tri_chunk : 16;
+      spt = c->p_tri_spt ? c->p_tri_spt : 1;
+      if (!fits(C, m)) C = 1;
     } else if (c->p_tri_cluster == 0 && op->n >= 2048) {
-      for (int cc : {4, 2})
-        if (nsys * cc <= c->num_sms && fits(cc)) { C = cc; break; }
+      // measured on GB300 (adr1d, n = 4095): 2 CTAs per system beat 1 by
+      // 1.45x and 4 by 2%, so 4 is used only when 2 do not fit a system
+      if (nsys * 2 <= c->num_sms && fits(2, 16)) C = 2;
+      else if (nsys * 4 <= c->num_sms && fits(4, 16)) C = 4;
+      if (c->p_tri_chunk) m = c->p_tri_chunk;
+      if (c->p_tri_spt) spt = c->p_tri_spt;
+      if (C > 1 && !fits(C, m)) { C = 1; }
     }
     if (C > 1) {
       ClPlan* cp = nullptr;
-      lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, C, &cp);
+      lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, C, m, &cp);
       if (s) return s;
-      return tri_propagate_cluster(c, cp, M, nsys, prec, in, out, src);
+      return tri_propagate_cluster(c, cp, M, nsys, prec, spt, in, out, src);
     }
     TriPlan* plan = nullptr;
     lrp_status s = tri_get_plan(c, op, dt, adjoint, &plan);

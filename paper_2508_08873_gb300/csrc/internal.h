@@ -2,8 +2,10 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <vector>
@@ -37,7 +39,7 @@ struct KernelTimer {
 struct Ctx {
   int device = 0;
   size_t budget = 0;
-  size_t in_use = 0;
+  std::atomic<size_t> in_use{0};
   cudaStream_t own_stream = nullptr;
   cudaStream_t stream = nullptr;
   std::string last_error;
@@ -48,6 +50,9 @@ struct Ctx {
   // Tunable launch parameters (0 = automatic choice); see lrp_set_param.
   int p_sweep_cluster = 0;   // CTAs per coarse-sweep cluster (1..16)
   int p_tri_cluster = 0;     // CTAs per tridiagonal system for small batches (1, 2, 4)
+  int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
+  int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
+  int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
   // Handles (operators, coarse solvers) hold a reference; the context is
   // deleted when lrp_destroy has been called and the last handle is freed.
   int refs = 1;
@@ -98,6 +103,7 @@ struct Operator {
   double rtol64 = 1e-12, rtol32 = 1e-6;
   int max_iter = 20000;
   bool symmetric = false;  // 5-point: CG when symmetric, else BiCGStab
+  std::mutex plan_mu;      // plan lookup/creation (a server thread may propagate too)
   std::vector<std::unique_ptr<TriPlan>> plans;
   std::vector<std::unique_ptr<ClPlan>> cplans;
   std::vector<std::unique_ptr<StencilPlan>> splans;
@@ -136,10 +142,18 @@ lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** 
 
 // Input of a propagation: either vectors in memory or Gaussian sketch vectors
 // generated in the kernel (system s -> interval s / ncol, column s % ncol).
+// With a system map (2 ints per system: slot, interval), the vector of system
+// s is at base + slot * slot_stride + interval * ld instead of base + s * ld.
+__host__ __device__ inline long sys_offset(const int* map, long slot_stride, long ld, int s) {
+  return map ? (long)map[2 * s] * slot_stride + (long)map[2 * s + 1] * ld : (long)s * ld;
+}
+
 struct PropIn {
   const void* x = nullptr;  // nsys x n (row stride ldx), type given by x_f64
   int x_f64 = 1;
   long ldx = 0;
+  const int* map = nullptr; // optional system map (see sys_offset)
+  long slot_stride = 0;
   int gen = 0;              // 1: generate N(0,1) entries instead of reading x
   uint64_t seed = 0;
   int ncol = 1;
@@ -149,22 +163,33 @@ struct PropOut {
   void* y = nullptr;        // nsys x n (row stride ldy)
   int y_f64 = 1;
   long ldy = 0;
+  const int* map = nullptr;
+  long slot_stride = 0;
 };
 struct PropSrc {
   int Q = 0;
-  const double* g = nullptr;   // Q x n (device)
+  const double* g = nullptr;   // Q x n (device); with a map: + slot * g_slot_stride
   const double* c = nullptr;   // per system: c + s*cstride, M x Q (device)
   long cstride = 0;
+  const int* map = nullptr;    // with a map: c + slot * c_slot_stride + interval * cstride
+  long c_slot_stride = 0;
+  long g_slot_stride = 0;
 };
+
+// Any operator: picks the tridiagonal (one CTA or a cluster per system) or the
+// stencil propagator.  prec: 0 FP64, 1 FP32 arithmetic.
+lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys, int prec,
+                         const PropIn& in, const PropOut& out, const PropSrc& src);
 
 // prec: 0 FP64, 1 FP32 arithmetic.
 lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src);
 
 // One system per cluster of C CTAs (small batches, n >= 2048).
-lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, ClPlan** out);
-lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, const PropIn& in,
-                                 const PropOut& out, const PropSrc& src);
+lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, int m,
+                                ClPlan** out);
+lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
+                                 const PropIn& in, const PropOut& out, const PropSrc& src);
 
 // Allocation-free variant: factorisation into caller-provided scratch.
 size_t tri_raw_scratch_bytes(int n);
@@ -172,6 +197,28 @@ lrp_status tri_raw_propagate(cudaStream_t stream, int num_sms, void* scratch, in
                              const double* lo, const double* di, const double* up, double dt,
                              int adjoint, int M, int nsys, int prec, const PropIn& in,
                              const PropOut& out, const PropSrc& src);
+
+// ---- 5-point stencil propagation (stencil.cu) --------------------------------
+// One Krylov propagation problem (5-point operator, a batch of systems).
+struct KryArgs {
+  int mx, my, n, M, nsys, bicg;
+  double dt, rtol;
+  int max_iter;
+  const void* B;            // [6][n]: c, w, e, s, n, dinv (type T)
+  void* ws;                 // per cluster slot: nvec * n values of type T
+  int nvec;
+  PropIn in;
+  PropOut out;
+  PropSrc src;
+  unsigned long long* iters;   // total Krylov iterations
+  int* status;                 // bit 0: cap hit, bit 1: breakdown
+};
+lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out);
+size_t krylov_queue_nvec(int bicg);
+int krylov_queue_clusters(Ctx* c, int prec, int cs);
+lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const int* d_items,
+                               int nitems, unsigned int* d_counter, void* ws, size_t ws_stride,
+                               int cs, int nclusters);
 
 // ---- orthonormalisation, small SVD, lift (linalg.cu) -----------------------
 // CGS2 with deflation of every interval's ell x n block (rows = vectors), in
@@ -212,5 +259,9 @@ struct SweepArgs {
   int stage = 0;                  // set by the launcher: factors staged in smem
 };
 lrp_status coarse_sweep(Ctx* c, const SweepArgs& a);
+// Batched sweeps: nprob problems of equal n and R, arguments on the device.
+int coarse_sweep_batch_stage(Ctx* c, const SweepArgs& proto, int nprob);
+lrp_status coarse_sweep_batch(Ctx* c, const SweepArgs& proto, SweepArgs* d_args, int nprob,
+                              int* cs_out);
 
 }  // namespace lrp

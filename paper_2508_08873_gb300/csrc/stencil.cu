@@ -58,19 +58,7 @@ __global__ void k_stencil_plan(int mx, int my, double dt, int adj, const double*
   }
 }
 
-struct KryArgs {
-  int mx, my, n, M, nsys, bicg;
-  double dt, rtol;
-  int max_iter;
-  const void* B;            // [6][n]: c, w, e, s, n, dinv (type T)
-  void* ws;                 // per cluster slot: nvec * n values of type T
-  int nvec;
-  PropIn in;
-  PropOut out;
-  PropSrc src;
-  unsigned long long* iters;   // total Krylov iterations
-  int* status;                 // bit 0: cap hit, bit 1: breakdown
-};
+
 
 struct ClRed {
   double part[2][KRY_MAXNV];
@@ -121,19 +109,19 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ B, int n, int m
   return acc;
 }
 
+// One system (vector `sys` of the problem described by `a`) on this cluster,
+// using the workspace `ws` (a.nvec vectors of a.n values).
 template <typename T>
-__global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
-  cg::cluster_group cl = cg::this_cluster();
-  __shared__ ClRed sh;
+__device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_group& cl, ClRed& sh,
+                                              int& buf, int sys, T* ws,
+                                              unsigned long long& my_iters, int& my_status) {
   const int cs = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
-  const int slot = blockIdx.x / cs, nslots = gridDim.x / cs;
   const int n = a.n, mx = a.mx;
   const int rows_per = (a.my + cs - 1) / cs;
   const int k0 = min(a.n, crank * rows_per * mx), k1 = min(a.n, (crank + 1) * rows_per * mx);
   const T* B = static_cast<const T*>(a.B);
   const T* Bd = B + (size_t)5 * n;                         // 1 / diag
-  T* ws = static_cast<T*>(a.ws) + (size_t)slot * a.nvec * n;
   T* x = ws;
   T* r = ws + (size_t)n;
   T* p = ws + (size_t)2 * n;          // CG: p; BiCG: p
@@ -144,10 +132,6 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
   T* shh = ws + (size_t)7 * n;        // BiCG: D^-1 s
   T* tv = ws + (size_t)8 * n;         // BiCG: t = B D^-1 s
   const T dt = (T)a.dt;
-  int buf = 0;
-  unsigned long long my_iters = 0;
-  int my_status = 0;
-  for (int sys = slot; sys < a.nsys; sys += nslots) {
     // ---- initial vector ----------------------------------------------------
     for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
       T v = T(0);
@@ -157,13 +141,16 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
       else if (a.in.x == nullptr)
         v = T(0);
       else if (a.in.x_f64)
-        v = (T) static_cast<const double*>(a.in.x)[(size_t)sys * a.in.ldx + k];
+        v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
       else
-        v = (T) static_cast<const float*>(a.in.x)[(size_t)sys * a.in.ldx + k];
+        v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
       x[k] = v;
     }
     cl.sync();
-    const double* csys = a.src.Q > 0 ? a.src.c + (size_t)sys * a.src.cstride : nullptr;
+    const double* csys = a.src.Q > 0
+        ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+    const double* gsys = (a.src.Q > 0 && a.src.map)
+        ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
     for (int j = 0; j < a.M; ++j) {
       // ---- right-hand side d = x + dt f, residual r = d - B x --------------
       double red3[3] = {0.0, 0.0, 0.0};    // d.d, r.r, rho
@@ -171,7 +158,7 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
         T d = x[k];
         if (csys)
           for (int qq = 0; qq < a.src.Q; ++qq)
-            d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)a.src.g[(size_t)qq * n + k];
+            d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
         T rk = d - stencil_apply(B, n, mx, k, x);
         r[k] = rk;
         red3[0] += (double)d * (double)d;
@@ -277,32 +264,85 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
       cl.sync();
     }
     // ---- store ---------------------------------------------------------------
+    const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
     for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
       if (a.out.y_f64)
-        static_cast<double*>(a.out.y)[(size_t)sys * a.out.ldy + k] = (double)x[k];
+        static_cast<double*>(a.out.y)[oy + k] = (double)x[k];
       else
-        static_cast<float*>(a.out.y)[(size_t)sys * a.out.ldy + k] = (float)x[k];
+        static_cast<float*>(a.out.y)[oy + k] = (float)x[k];
     }
     cl.sync();
-  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ ClRed sh;
+  const int cs = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int slot = blockIdx.x / cs, nslots = gridDim.x / cs;
+  T* ws = static_cast<T*>(a.ws) + (size_t)slot * a.nvec * a.n;
+  int buf = 0;
+  unsigned long long my_iters = 0;
+  int my_status = 0;
+  for (int sys = slot; sys < a.nsys; sys += nslots)
+    krylov_system<T>(a, cl, sh, buf, sys, ws, my_iters, my_status);
   if (threadIdx.x == 0 && crank == 0) {
     if (my_iters) atomicAdd(a.iters, my_iters);
     if (my_status) atomicOr(a.status, my_status);
   }
 }
 
+// Many problems (different grids and operators) in one persistent launch: a
+// device work queue of items (problem, system), largest grids first; each
+// cluster takes the next item from a global counter (rank 0 draws it and
+// the other CTAs read it through distributed shared memory).
+template <typename T>
+__global__ void __launch_bounds__(KRY_THREADS) k_krylov_queue(const KryArgs* __restrict__ probs,
+                                                               const int* __restrict__ items,
+                                                               int nitems,
+                                                               unsigned int* __restrict__ counter,
+                                                               void* ws_all, size_t ws_stride) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ ClRed sh;
+  __shared__ int next_item;
+  const int cs = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int slot = blockIdx.x / cs;
+  T* ws = reinterpret_cast<T*>(static_cast<char*>(ws_all) + (size_t)slot * ws_stride);
+  int buf = 0;
+  unsigned long long my_iters = 0;
+  int my_status = 0;
+  const KryArgs* last = nullptr;
+  while (true) {
+    if (crank == 0 && threadIdx.x == 0) next_item = (int)atomicAdd(counter, 1u);
+    cl.sync();
+    const int it = *cl.map_shared_rank(&next_item, 0);
+    cl.sync();                        // rank 0 may overwrite next_item only after all read it
+    if (it >= nitems) break;
+    const KryArgs& a = probs[items[2 * it]];
+    last = &a;
+    krylov_system<T>(a, cl, sh, buf, items[2 * it + 1], ws, my_iters, my_status);
+  }
+  if (threadIdx.x == 0 && crank == 0 && last) {
+    if (my_iters) atomicAdd(last->iters, my_iters);
+    if (my_status) atomicOr(last->status, my_status);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static lrp_status stencil_get_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out) {
+lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out) {
+  std::lock_guard<std::mutex> plan_lock(op->plan_mu);
   for (auto& p : op->splans)
     if (p->dt == dt && p->adjoint == adjoint) { *out = p.get(); return LRP_OK; }
   auto pl = std::make_unique<StencilPlan>();
   pl->dt = dt;
   pl->adjoint = adjoint;
   lrp_status s;
-  if ((s = dev_alloc(c, pl->b64, sizeof(double) * 6 * (size_t)op->n))) return s;
-  if ((s = dev_alloc(c, pl->b32, sizeof(float) * 6 * (size_t)op->n))) return s;
+  if ((s = dev_alloc(op->ctx, pl->b64, sizeof(double) * 6 * (size_t)op->n))) return s;
+  if ((s = dev_alloc(op->ctx, pl->b32, sizeof(float) * 6 * (size_t)op->n))) return s;
   k_stencil_plan<<<(op->n + 255) / 256, 256, 0, c->stream>>>(
       op->mx, op->my, dt, adjoint, op->a64[0].as<double>(), op->a64[1].as<double>(),
       op->a64[2].as<double>(), op->a64[3].as<double>(), op->a64[4].as<double>(),
@@ -326,7 +366,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
                              int prec, const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (nsys <= 0) return LRP_OK;
   StencilPlan* plan = nullptr;
-  lrp_status s = stencil_get_plan(c, op, dt, adjoint, &plan);
+  lrp_status s = stencil_plan(c, op, dt, adjoint, &plan);
   if (s) return s;
   const int cs = cluster_size_for(op->mx, op->my);
   const int bicg = op->symmetric ? 0 : 1;
@@ -389,6 +429,59 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   int st = (int)(hs[1] & 0xffffffffu);
   if (st & 2) return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in a 2D propagation");
   if (st & 1) return set_err(c, LRP_ENOTCONV, "Krylov iteration cap reached in a 2D propagation");
+  return LRP_OK;
+}
+
+// ---- work-queue launches (batched problems of uneven size) -----------------
+size_t krylov_queue_nvec(int bicg) { return bicg ? 9 : 4; }
+
+int krylov_queue_clusters(Ctx* c, int prec, int cs) {
+  auto kern = prec == 0 ? (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<double>
+                        : (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<float>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(KRY_THREADS);
+  cfg.gridDim = dim3(cs);
+  int maxc = 0;
+  if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) != cudaSuccess || maxc < 1) {
+    cudaGetLastError();
+    maxc = std::max(1, c->num_sms / cs);
+  }
+  return maxc;
+}
+
+lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const int* d_items,
+                               int nitems, unsigned int* d_counter, void* ws, size_t ws_stride,
+                               int cs, int nclusters) {
+  if (nitems <= 0) return LRP_OK;
+  auto kern = prec == 0 ? (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<double>
+                        : (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<float>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e) return cuda_err(c, e, "queue cluster attribute");
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(KRY_THREADS);
+  cfg.gridDim = dim3(nclusters * cs);
+  cfg.stream = c->stream;
+  const char* fam = prec == 0 ? "propagate_f64" : "propagate_f32";
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, fam, &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, d_probs, d_items, nitems, d_counter, ws, ws_stride);
+  timer_end(c, fam, ev);
+  if (e) return cuda_err(c, e, "k_krylov_queue launch");
   return LRP_OK;
 }
 

@@ -40,12 +40,11 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 constexpr int SWEEP_THREADS = 256;
 constexpr int SWEEP_MAXR = 64;
 constexpr int SWEEP_MAXCS = 16;
-constexpr int SWEEP_MAXROWS = 20480;     // rows per CTA (delta kept in shared memory)
 constexpr size_t SWEEP_STAGE_MAX = 192 * 1024;   // dynamic smem when staging factors
 constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
 
 template <typename TF>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
+__device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   cg::cluster_group cl = cg::this_cluster();
   const int crank = (int)cl.block_rank();
   const int cs = (int)cl.num_blocks();
@@ -56,6 +55,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
   __shared__ double red[SWEEP_THREADS / 32][SWEEP_MAXR + 2];
   __shared__ double gath[SWEEP_MAXCS][SWEEP_MAXR + 2];
   __shared__ double coef[SWEEP_MAXR + 2];
+  __shared__ TF scoef[SWEEP_MAXR];                      // S_r * c_r in the apply type
+  __shared__ TF sS[2][SWEEP_MAXR];                      // staged S of the next interval
   const int per = (n + cs - 1) / cs;
   const int lo = crank * per, hi = min(n, lo + per), rows = max(0, hi - lo);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -66,7 +67,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
   // shared memory (double-buffered cp.async), so that their load latency
   // overlaps the current interval's reductions and cluster barrier.
   const bool stage = a.stage != 0;
-  TF* sU = reinterpret_cast<TF*>(dsm + per);                  // [2][R][per]
+  // delta in the apply type: a separate FP32 copy in the mixed mode (so the
+  // R dot products need no conversions), the FP64 array itself otherwise
+  constexpr bool kSep = sizeof(TF) != sizeof(double);
+  TF* dsT = kSep ? reinterpret_cast<TF*>(dsm + per) : reinterpret_cast<TF*>(dsm);
+  TF* sU = reinterpret_cast<TF*>(dsm + per) + (kSep ? per + (per & 1) : 0);   // [2][R][per]
   TF* sV = sU + (size_t)2 * R * per;                          // [2][R][per]
   double* sF = reinterpret_cast<double*>(sV + (size_t)2 * R * per);   // [2][per]
   double* sO = sF + (size_t)2 * per;                          // [2][per] u^{k-1}_{iv+1}
@@ -75,12 +80,18 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
     const TF* Ug = U + (size_t)iv * R * n + lo;
     const TF* Vg = V + (size_t)iv * R * n + lo;
     const double* Fg = a.F + (size_t)iv * n + lo;
-    for (int k = threadIdx.x; k < R * rows; k += blockDim.x) {
-      int r = k / rows, i = k % rows;
-      cp_async<sizeof(TF)>(sU + ((size_t)b * R + r) * per + i, Ug + (size_t)r * n + i);
-      cp_async<sizeof(TF)>(sV + ((size_t)b * R + r) * per + i, Vg + (size_t)r * n + i);
+    for (int r = 0; r < R; ++r) {                 // no integer division per element
+      TF* du = sU + ((size_t)b * R + r) * per;
+      TF* dv = sV + ((size_t)b * R + r) * per;
+      const TF* gu = Ug + (size_t)r * n;
+      const TF* gv = Vg + (size_t)r * n;
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        cp_async<sizeof(TF)>(du + i, gu + i);
+        cp_async<sizeof(TF)>(dv + i, gv + i);
+      }
     }
     const double* Og = a.u + (size_t)(iv + 1) * n + lo;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) cp_async<sizeof(TF)>(&sS[b][r], S + (size_t)iv * R + r);
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
       cp_async<8>(sF + (size_t)b * per + i, Fg + i);
       if (!a.initial) cp_async<8>(sO + (size_t)b * per + i, Og + i);
@@ -89,8 +100,11 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
   issue(a.first, 0);
   cp_async_commit();
   // delta at the first interval: 0 (u^k_first == u^{k-1}_first), or u0 initially
-  for (int i = threadIdx.x; i < rows; i += blockDim.x)
-    dsm[i] = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+    double d0 = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
+    dsm[i] = d0;
+    if (kSep) dsT[i] = (TF)d0;
+  }
   if (crank == 0 && threadIdx.x == 0 && !a.initial)
     for (int m = 0; m <= a.first; ++m) a.du[m] = 0.0;
   __syncthreads();
@@ -123,7 +137,7 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
       for (int r = w; r < R; r += nw) {
         const TF* vr = Vi + (size_t)r * ldv;
         TF pr = TF(0);
-        for (int i = lane; i < rows; i += 32) pr += vr[i] * (TF)dsm[i];
+        for (int i = lane; i < rows; i += 32) pr += vr[i] * dsT[i];
         double d = warp_sum((double)pr);
         if (lane == 0) part[buf][r] = d;   // this CTA's partial dot (single writer)
       }
@@ -149,6 +163,8 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
       if (iv < N || threadIdx.x >= R)
         for (int q = 0; q < cs; ++q) s += gath[q][threadIdx.x];    // same order in every CTA
       coef[threadIdx.x] = s;
+      if (threadIdx.x < R && iv < N)
+        scoef[threadIdx.x] = (stage ? sS[sb][threadIdx.x] : S[(size_t)iv * R + threadIdx.x]) * (TF)s;
     }
     __syncthreads();
     if (crank == 0 && threadIdx.x == 0) {
@@ -159,16 +175,17 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
     // ---- u^k_{iv+1} = F_iv + U_iv (S_iv * c) on this CTA's rows ------------
     const TF* Ui = stage ? sU + (size_t)sb * R * per : U + (size_t)iv * R * n + lo;
     const size_t ldu = stage ? (size_t)per : (size_t)n;
-    const TF* Si = S + (size_t)iv * R;
     const double* Fi = stage ? sF + (size_t)sb * per : a.F + (size_t)iv * n + lo;
     double* un = a.u + (size_t)(iv + 1) * n + lo;
     acc_u_next = 0.0;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
       TF g = TF(0);
-      for (int r = 0; r < R; ++r) g += Ui[(size_t)r * ldu + i] * (Si[r] * (TF)coef[r]);
+      for (int r = 0; r < R; ++r) g += Ui[(size_t)r * ldu + i] * scoef[r];
       double nv_ = Fi[i] + (double)g;
       double old = a.initial ? 0.0 : (stage ? sO[(size_t)sb * per + i] : un[i]);
-      dsm[i] = nv_ - old;
+      const double dn = nv_ - old;
+      dsm[i] = dn;
+      if (kSep) dsT[i] = (TF)dn;
       un[i] = nv_;
       acc_u_next += nv_ * nv_;
     }
@@ -194,9 +211,22 @@ __global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
   cl.sync();  // no CTA leaves while its shared memory may still be read
 }
 
+// One problem per launch.
+template <typename TF>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
+  sweep_body<TF>(a);
+}
+
+// A batch of problems (same n, R, staging), one cluster each: args[cluster].
+template <typename TF>
+__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep_batch(const SweepArgs* __restrict__ args) {
+  const SweepArgs a = args[blockIdx.x / cg::this_cluster().num_blocks()];
+  sweep_body<TF>(a);
+}
+
 lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
   if (a.R > SWEEP_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
-  if ((a.n + SWEEP_MAXCS - 1) / SWEEP_MAXCS > SWEEP_MAXROWS)
+  if ((size_t)((a.n + SWEEP_MAXCS - 1) / SWEEP_MAXCS) * (a.f32 ? 12 : 8) > SWEEP_SMEM_MAX)
     return set_err(c, LRP_EINVAL, "state dimension too large for the coarse sweep");
   int cs = 16;
   cudaLaunchConfig_t cfg = {};
@@ -207,11 +237,11 @@ lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
   // small problems: fewer CTAs per cluster
   while (cs > 1 && (a.n + cs - 1) / cs < 64) cs >>= 1;
   if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
-  while (cs < SWEEP_MAXCS && (a.n + cs - 1) / cs > SWEEP_MAXROWS) cs <<= 1;
+  while (cs < SWEEP_MAXCS && (size_t)((a.n + cs - 1) / cs) * (a.f32 ? 12 : 8) > SWEEP_SMEM_MAX) cs <<= 1;
   const size_t tf = a.f32 ? 4 : 8;
   auto dyn_for = [&](int csz, int stage) {
     size_t per = (size_t)((a.n + csz - 1) / csz);
-    size_t b = sizeof(double) * per;
+    size_t b = sizeof(double) * per + (tf == 8 ? 0 : tf * (per + (per & 1)));
     if (stage) b += 4 * (size_t)a.R * per * tf + 4 * per * sizeof(double);
     return b;
   };
@@ -246,6 +276,66 @@ lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
   }
   if (e) return cuda_err(c, e, "k_sweep launch");
   return LRP_OK;
+}
+
+lrp_status coarse_sweep_batch(Ctx* c, const SweepArgs& proto, SweepArgs* d_args, int nprob,
+                              int* cs_out) {
+  if (nprob <= 0) return LRP_OK;
+  if (proto.R > SWEEP_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
+  auto kern = proto.f32 ? (void (*)(const SweepArgs*))k_sweep_batch<float>
+                        : (void (*)(const SweepArgs*))k_sweep_batch<double>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  int cs = e ? 8 : 16;
+  if (e) cudaGetLastError();
+  // several problems share the GPU: fewer CTAs per problem when many run
+  while (cs > 1 && (size_t)nprob * cs > (size_t)c->num_sms) cs >>= 1;
+  while (cs > 1 && (proto.n + cs - 1) / cs < 64) cs >>= 1;
+  if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
+  const size_t tf = proto.f32 ? 4 : 8;
+  while (cs < SWEEP_MAXCS && (size_t)((proto.n + cs - 1) / cs) * (proto.f32 ? 12 : 8) > SWEEP_SMEM_MAX)
+    cs <<= 1;
+  const size_t per = (size_t)((proto.n + cs - 1) / cs);
+  size_t dyn = sizeof(double) * per + (tf == 8 ? 0 : tf * (per + (per & 1)));
+  const size_t dyn_stage = dyn + 4 * (size_t)proto.R * per * tf + 4 * per * sizeof(double);
+  const int stage = dyn_stage <= SWEEP_STAGE_MAX ? 1 : 0;
+  if (stage) dyn = dyn_stage;
+  if (stage != proto.stage) return set_err(c, LRP_EINVAL, "sweep batch staging mismatch");
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_MAX);
+  if (e) return cuda_err(c, e, "sweep smem attribute");
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.gridDim = dim3(nprob * cs);
+  cfg.blockDim = dim3(SWEEP_THREADS);
+  cfg.dynamicSmemBytes = dyn;
+  cfg.stream = c->stream;
+  if (cs_out) *cs_out = cs;
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "sweep", &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, (const SweepArgs*)d_args);
+  timer_end(c, "sweep", ev);
+  if (e) return cuda_err(c, e, "k_sweep_batch launch");
+  return LRP_OK;
+}
+
+// Staging decision of a batched sweep (the caller stores it in every
+// problem's SweepArgs before copying them to the device).
+int coarse_sweep_batch_stage(Ctx* c, const SweepArgs& proto, int nprob) {
+  int cs = 16;
+  while (cs > 1 && (size_t)nprob * cs > (size_t)c->num_sms) cs >>= 1;
+  while (cs > 1 && (proto.n + cs - 1) / cs < 64) cs >>= 1;
+  if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
+  const size_t tf = proto.f32 ? 4 : 8;
+  while (cs < SWEEP_MAXCS && (size_t)((proto.n + cs - 1) / cs) * (proto.f32 ? 12 : 8) > SWEEP_SMEM_MAX)
+    cs <<= 1;
+  const size_t per = (size_t)((proto.n + cs - 1) / cs);
+  size_t dyn = sizeof(double) * per + (tf == 8 ? 0 : tf * (per + (per & 1)));
+  return dyn + 4 * (size_t)proto.R * per * tf + 4 * per * sizeof(double) <= SWEEP_STAGE_MAX ? 1 : 0;
 }
 
 }  // namespace lrp

@@ -201,20 +201,23 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
         } else if (a.in.x == nullptr) {
           v = T(0);                                   // zero initial value (b_i = F_i 0)
         } else if (a.in.x_f64) {
-          v = (T) static_cast<const double*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+          v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
         } else {
-          v = (T) static_cast<const float*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+          v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
         }
       }
       x[i] = v;
     }
-    const double* csys = (active && a.src.Q > 0) ? a.src.c + (size_t)sys * a.src.cstride : nullptr;
+    const double* csys = (active && a.src.Q > 0)
+        ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+    const double* gsys = (active && a.src.Q > 0 && a.src.map)
+        ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
     // ---- M implicit-Euler steps ------------------------------------------
     for (int j = 0; j < a.M; ++j) {
       if (csys) {
         for (int q = 0; q < a.src.Q; ++q) {
           T cq_ = dt * (T)csys[(size_t)j * a.src.Q + q];
-          const double* gq = a.src.g + (size_t)q * n;
+          const double* gq = gsys + (size_t)q * n;
 #pragma unroll
           for (int i = 0; i < MM; ++i) {
             int r = r0 + i;
@@ -258,10 +261,11 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
       for (int i = 0; i < MM; ++i) {
         int r = r0 + i;
         if (r < n) {
+          const long o = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys) + r;
           if (a.out.y_f64)
-            static_cast<double*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (double)x[i];
+            static_cast<double*>(a.out.y)[o] = (double)x[i];
           else
-            static_cast<float*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (float)x[i];
+            static_cast<float*>(a.out.y)[o] = (float)x[i];
         }
       }
     }
@@ -280,6 +284,7 @@ static int choose_m(int n) {
 }
 
 lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out) {
+  std::lock_guard<std::mutex> plan_lock(op->plan_mu);
   for (auto& p : op->plans)
     if (p->dt == dt && p->adjoint == adjoint) { *out = p.get(); return LRP_OK; }
   auto pl = std::make_unique<TriPlan>();
@@ -294,11 +299,11 @@ lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** 
   pl->levels = L;
   size_t MP = (size_t)pl->m * pl->P;
   lrp_status s;
-  if ((s = dev_alloc(c, pl->coef64, 5 * MP * 8))) return s;
-  if ((s = dev_alloc(c, pl->coef32, 5 * MP * 4))) return s;
-  if ((s = dev_alloc(c, pl->pcr64, (size_t)(2 * L + 1) * pl->P * 8))) return s;
-  if ((s = dev_alloc(c, pl->pcr32, (size_t)(2 * L + 1) * pl->P * 4))) return s;
-  if ((s = dev_alloc(c, pl->status, sizeof(int)))) return s;
+  if ((s = dev_alloc(op->ctx, pl->coef64, 5 * MP * 8))) return s;
+  if ((s = dev_alloc(op->ctx, pl->coef32, 5 * MP * 4))) return s;
+  if ((s = dev_alloc(op->ctx, pl->pcr64, (size_t)(2 * L + 1) * pl->P * 8))) return s;
+  if ((s = dev_alloc(op->ctx, pl->pcr32, (size_t)(2 * L + 1) * pl->P * 4))) return s;
+  if ((s = dev_alloc(op->ctx, pl->status, sizeof(int)))) return s;
   cudaError_t e = cudaMemsetAsync(pl->status.ptr, 0, sizeof(int), c->stream);
   if (e) return cuda_err(c, e, "memset");
   int threads = ((pl->P + 31) / 32) * 32;

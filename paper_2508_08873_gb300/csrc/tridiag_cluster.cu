@@ -236,7 +236,11 @@ struct ClKArgs {
   PropSrc src;
 };
 
-template <typename T, int MM>
+// SPT systems per thread: a cluster advances SPT independent systems in
+// lockstep, so that every thread has SPT independent dependency chains (FP64
+// latency is exposed with one warp per scheduler) and the factors read from
+// shared memory serve SPT systems.
+template <typename T, int MM, int SPT>
 __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -246,9 +250,9 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
   T* s_pcr = s_coef + 5 * MM * Pc;                        // [2L+1][Pc]
   T* s_spk = s_pcr + (2 * L + 1) * Pc;                    // [2][Pc]
   T* s_sup = s_spk + 2 * Pc;                              // [C][6]
-  T* xb = s_sup + 6 * CL_MAXC;                            // [3][Pc]
-  T* Ysh = xb + 3 * Pc;                                   // [CL_MAXC]
-  __shared__ double pub[2][4];
+  T* xb = s_sup + 6 * CL_MAXC;                            // [SPT][3][Pc]
+  T* Ysh = xb + SPT * 3 * Pc;                             // [SPT][CL_MAXC]
+  __shared__ double pub[2][SPT][4];
   {
     const T* gco = static_cast<const T*>(a.coef) + (size_t)c * 5 * MM * Pc;
     const T* gpc = static_cast<const T*>(a.lpcr) + (size_t)c * (2 * L + 1) * Pc;
@@ -272,72 +276,113 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
   const int r0 = t * MM;
   const int nclu = gridDim.x / C;
   int pb = 0;
-  for (int sys = blockIdx.x / C; sys < a.nsys; sys += nclu) {
-    T x[MM];
+  for (int base = (blockIdx.x / C) * SPT; base < a.nsys; base += nclu * SPT) {
+    T x[SPT][MM];
+    const double* csys[SPT];
+    const double* gsys[SPT];
 #pragma unroll
-    for (int i = 0; i < MM; ++i) {
-      int r = r0 + i;
-      T v = T(0);
-      if (r < n) {
-        if (a.in.gen)
-          v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
-                       (uint32_t)(sys % a.in.ncol), (uint32_t)r);
-        else if (a.in.x == nullptr)
-          v = T(0);
-        else if (a.in.x_f64)
-          v = (T) static_cast<const double*>(a.in.x)[(size_t)sys * a.in.ldx + r];
-        else
-          v = (T) static_cast<const float*>(a.in.x)[(size_t)sys * a.in.ldx + r];
+    for (int s = 0; s < SPT; ++s) {
+      const int sys = base + s;
+      const bool act = sys < a.nsys;
+#pragma unroll
+      for (int i = 0; i < MM; ++i) {
+        int r = r0 + i;
+        T v = T(0);
+        if (act && r < n) {
+          if (a.in.gen)
+            v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                         (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+          else if (a.in.x == nullptr)
+            v = T(0);
+          else if (a.in.x_f64)
+            v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+          else
+            v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+        }
+        x[s][i] = v;
       }
-      x[i] = v;
+      csys[s] = (act && a.src.Q > 0)
+          ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+      gsys[s] = (act && a.src.Q > 0 && a.src.map)
+          ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
     }
-    const double* csys = a.src.Q > 0 ? a.src.c + (size_t)sys * a.src.cstride : nullptr;
     for (int j = 0; j < a.M; ++j) {
-      if (csys) {
-        for (int q = 0; q < a.src.Q; ++q) {
-          T cq_ = dt * (T)csys[(size_t)j * a.src.Q + q];
-          const double* gq = a.src.g + (size_t)q * n;
 #pragma unroll
-          for (int i = 0; i < MM; ++i)
-            if (r0 + i < n) x[i] += cq_ * (T)gq[r0 + i];
+      for (int s = 0; s < SPT; ++s) {
+        if (csys[s]) {
+          for (int q = 0; q < a.src.Q; ++q) {
+            T cq_ = dt * (T)csys[s][(size_t)j * a.src.Q + q];
+            const double* gq = gsys[s] + (size_t)q * n;
+#pragma unroll
+            for (int i = 0; i < MM; ++i)
+              if (r0 + i < n) x[s][i] += cq_ * (T)gq[r0 + i];
+          }
         }
       }
+      // interior forward elimination and back substitution (SPT chains)
 #pragma unroll
-      for (int i = 1; i < MM - 1; ++i) x[i] -= cl_[i * Pc + tl] * x[i - 1];
-      x[MM - 2] *= ci[(MM - 2) * Pc + tl];
+      for (int i = 1; i < MM - 1; ++i) {
+        const T l = cl_[i * Pc + tl];
 #pragma unroll
-      for (int i = MM - 3; i >= 0; --i) x[i] = x[i] * ci[i * Pc + tl] - cu[i * Pc + tl] * x[i + 1];
-      xb[2 * Pc + tl] = x[0];
+        for (int s = 0; s < SPT; ++s) x[s][i] -= l * x[s][i - 1];
+      }
+      {
+        const T iv = ci[(MM - 2) * Pc + tl];
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) x[s][MM - 2] *= iv;
+      }
+#pragma unroll
+      for (int i = MM - 3; i >= 0; --i) {
+        const T iv = ci[i * Pc + tl], u = cu[i * Pc + tl];
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) x[s][i] = x[s][i] * iv - u * x[s][i + 1];
+      }
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) xb[(s * 3 + 2) * Pc + tl] = x[s][0];
       __syncthreads();
-      T gnext = (tl + 1 < Pc) ? xb[2 * Pc + tl + 1] : T(0);
-      T r = x[MM - 1] - cl_[(MM - 1) * Pc + tl] * x[MM - 2] - cu[(MM - 1) * Pc + tl] * gnext;
+      T r[SPT];
+      const T aE = cl_[(MM - 1) * Pc + tl], cE = cu[(MM - 1) * Pc + tl];
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        T gnext = (tl + 1 < Pc) ? xb[(s * 3 + 2) * Pc + tl + 1] : T(0);
+        r[s] = x[s][MM - 1] - aE * x[s][MM - 2] - cE * gnext;
+      }
       // local parallel cyclic reduction (unknowns 0 .. Pl-1 of this CTA)
       int buf = 0;
-      for (int lev = 0, s = 1; lev < L; ++lev, s <<= 1) {
-        xb[buf * Pc + tl] = r;
+      for (int lev = 0, sh = 1; lev < L; ++lev, sh <<= 1) {
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) xb[(s * 3 + buf) * Pc + tl] = r[s];
         __syncthreads();
         if (tl < Pl) {
-          T rm = (tl - s >= 0) ? xb[buf * Pc + tl - s] : T(0);
-          T rp = (tl + s < Pl) ? xb[buf * Pc + tl + s] : T(0);
-          r = r - s_pcr[lev * Pc + tl] * rm - s_pcr[(L + lev) * Pc + tl] * rp;
+          const T k1 = s_pcr[lev * Pc + tl], k2 = s_pcr[(L + lev) * Pc + tl];
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            T rm = (tl - sh >= 0) ? xb[(s * 3 + buf) * Pc + tl - sh] : T(0);
+            T rp = (tl + sh < Pl) ? xb[(s * 3 + buf) * Pc + tl + sh] : T(0);
+            r[s] = r[s] - k1 * rm - k2 * rp;
+          }
         }
         buf ^= 1;
       }
-      const T z0 = (tl < Pl) ? r * s_pcr[2 * L * Pc + tl] : T(0);
-      // publish the values the super system needs, then one cluster barrier
-      if (tl == 0) { pub[pb][0] = (double)z0; pub[pb][3] = (double)x[0]; }
-      if (tl == Pl - 1) pub[pb][1] = (double)z0;
-      if (tl == Pc - 1) pub[pb][2] = (double)r;
+      T z0[SPT];
+      const T dv = (tl < Pl) ? s_pcr[2 * L * Pc + tl] : T(0);
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        z0[s] = (tl < Pl) ? r[s] * dv : T(0);
+        if (tl == 0) { pub[pb][s][0] = (double)z0[s]; pub[pb][s][3] = (double)x[s][0]; }
+        if (tl == Pl - 1) pub[pb][s][1] = (double)z0[s];
+        if (tl == Pc - 1) pub[pb][s][2] = (double)r[s];
+      }
       cl.sync();
-      if (tl == 0) {
-        // gather the 4 published scalars of every CTA, then solve the C x C
-        // super system by its precomputed LU (fixed-size unrolled loops)
+      if (tl < SPT) {
+        // thread s solves the C x C super system of system s
+        const int s = tl;
         double zf[CL_MAXC], zl[CL_MAXC], rpart[CL_MAXC], g0[CL_MAXC], w[CL_MAXC];
 #pragma unroll
         for (int q = 0; q < CL_MAXC; ++q) {
           zf[q] = zl[q] = rpart[q] = g0[q] = w[q] = 0.0;
           if (q < C) {
-            const double* pp = cl.map_shared_rank(&pub[pb][0], q);
+            const double* pp = cl.map_shared_rank(&pub[pb][s][0], q);
             zf[q] = pp[0]; zl[q] = pp[1]; rpart[q] = pp[2]; g0[q] = pp[3];
           }
         }
@@ -355,30 +400,44 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
         for (int q = CL_MAXC - 1; q >= 0; --q) {
           if (q < C) {
             Y = (w[q] - (q + 1 < C ? (double)s_sup[6 * q + 5] * Y : 0.0)) * (double)s_sup[6 * q + 4];
-            Ysh[q] = (T)Y;
+            Ysh[s * CL_MAXC + q] = (T)Y;
           }
         }
       }
       __syncthreads();
-      const T Yl = c > 0 ? Ysh[c - 1] : T(0);
-      const T Yc = Ysh[c];
-      const T y = (tl < Pl) ? z0 - s_spk[tl] * Yl - s_spk[Pc + tl] * Yc : Yc;
-      xb[buf * Pc + tl] = y;
-      __syncthreads();
-      const T yl = (tl > 0) ? xb[buf * Pc + tl - 1] : Yl;
+      T y[SPT], Yl[SPT];
+      const T p2 = s_spk[tl], q2 = s_spk[Pc + tl];
 #pragma unroll
-      for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - cp[i * Pc + tl] * yl - cq[i * Pc + tl] * y;
-      x[MM - 1] = y;
+      for (int s = 0; s < SPT; ++s) {
+        Yl[s] = c > 0 ? Ysh[s * CL_MAXC + c - 1] : T(0);
+        const T Yc = Ysh[s * CL_MAXC + c];
+        y[s] = (tl < Pl) ? z0[s] - p2 * Yl[s] - q2 * Yc : Yc;
+        xb[(s * 3 + buf) * Pc + tl] = y[s];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        const T yl = (tl > 0) ? xb[(s * 3 + buf) * Pc + tl - 1] : Yl[s];
+#pragma unroll
+        for (int i = 0; i < MM - 1; ++i) x[s][i] = x[s][i] - cp[i * Pc + tl] * yl - cq[i * Pc + tl] * y[s];
+        x[s][MM - 1] = y[s];
+      }
       pb ^= 1;
     }
 #pragma unroll
-    for (int i = 0; i < MM; ++i) {
-      int r = r0 + i;
-      if (r < n) {
-        if (a.out.y_f64)
-          static_cast<double*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (double)x[i];
-        else
-          static_cast<float*>(a.out.y)[(size_t)sys * a.out.ldy + r] = (float)x[i];
+    for (int s = 0; s < SPT; ++s) {
+      const int sys = base + s;
+      if (sys >= a.nsys) continue;
+#pragma unroll
+      for (int i = 0; i < MM; ++i) {
+        int r = r0 + i;
+        if (r < n) {
+          const long o = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys) + r;
+          if (a.out.y_f64)
+            static_cast<double*>(a.out.y)[o] = (double)x[s][i];
+          else
+            static_cast<float*>(a.out.y)[o] = (float)x[s][i];
+        }
       }
     }
     __syncthreads();
@@ -389,12 +448,12 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
-static constexpr int CL_M = 16;
-
-lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C,
+lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, int m,
                                 ClPlan** out) {
+  const int CL_M = m;
+  std::lock_guard<std::mutex> plan_lock(op->plan_mu);
   for (auto& p : op->cplans)
-    if (p->dt == dt && p->adjoint == adjoint && p->C == C) { *out = p.get(); return LRP_OK; }
+    if (p->dt == dt && p->adjoint == adjoint && p->C == C && p->m == m) { *out = p.get(); return LRP_OK; }
   auto pl = std::make_unique<ClPlan>();
   pl->dt = dt;
   pl->adjoint = adjoint;
@@ -415,11 +474,11 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
   pl->sz[0] = ncoef; pl->sz[1] = npcr; pl->sz[2] = nspk; pl->sz[3] = nsup;
   lrp_status s;
   for (int k = 0; k < 4; ++k) {
-    if ((s = dev_alloc(c, pl->b64[k], pl->sz[k] * 8))) return s;
-    if ((s = dev_alloc(c, pl->b32[k], pl->sz[k] * 4))) return s;
+    if ((s = dev_alloc(op->ctx, pl->b64[k], pl->sz[k] * 8))) return s;
+    if ((s = dev_alloc(op->ctx, pl->b32[k], pl->sz[k] * 4))) return s;
     cudaMemsetAsync(pl->b64[k].ptr, 0, pl->sz[k] * 8, c->stream);
   }
-  if ((s = dev_alloc(c, pl->status, sizeof(int)))) return s;
+  if ((s = dev_alloc(op->ctx, pl->status, sizeof(int)))) return s;
   cudaMemsetAsync(pl->status.ptr, 0, sizeof(int), c->stream);
   int threads = ((P + 31) / 32) * 32;
   cudaError_t e0 = cudaFuncSetAttribute(k_tri_factor_cl, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -444,12 +503,12 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
   return LRP_OK;
 }
 
-template <typename T>
+template <typename T, int MM, int SPT>
 static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   const int Pc = pl->Pc, L = pl->L, C = pl->C;
-  size_t smem = sizeof(T) * ((size_t)5 * CL_M * Pc + (size_t)(2 * L + 1) * Pc + 2 * Pc +
-                             6 * CL_MAXC + 3 * Pc + CL_MAXC);
-  auto kern = k_tri_cluster<T, CL_M>;
+  size_t smem = sizeof(T) * ((size_t)5 * MM * Pc + (size_t)(2 * L + 1) * Pc + 2 * Pc +
+                             6 * CL_MAXC + (size_t)SPT * 3 * Pc + (size_t)SPT * CL_MAXC);
+  auto kern = k_tri_cluster<T, MM, SPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return cuda_err(c, e, "cluster tri smem attribute");
   cudaLaunchConfig_t cfg = {};
@@ -467,7 +526,8 @@ static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   int maxc = 0;
   e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
   if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
-  const int ncl = std::min(a.nsys, maxc);
+  const int groups = (a.nsys + SPT - 1) / SPT;
+  const int ncl = std::min(groups, maxc);
   cfg.gridDim = dim3(ncl * C);
   const char* fam = sizeof(T) == 8 ? "propagate_f64" : "propagate_f32";
   cudaEvent_t ev = nullptr;
@@ -478,8 +538,8 @@ static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   return LRP_OK;
 }
 
-lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, const PropIn& in,
-                                 const PropOut& out, const PropSrc& src) {
+lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
+                                 const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (nsys <= 0) return LRP_OK;
   ClKArgs a{};
   a.n = pl->n;
@@ -498,7 +558,12 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
   a.lpcr = b[1].ptr;
   a.spk = b[2].ptr;
   a.sup = b[3].ptr;
-  return f ? launch_cl<float>(c, pl, a) : launch_cl<double>(c, pl, a);
+  if (pl->m == 8) {
+    if (spt == 2) return f ? launch_cl<float, 8, 2>(c, pl, a) : launch_cl<double, 8, 2>(c, pl, a);
+    return f ? launch_cl<float, 8, 1>(c, pl, a) : launch_cl<double, 8, 1>(c, pl, a);
+  }
+  if (spt == 2) return f ? launch_cl<float, 16, 2>(c, pl, a) : launch_cl<double, 16, 2>(c, pl, a);
+  return f ? launch_cl<float, 16, 1>(c, pl, a) : launch_cl<double, 16, 1>(c, pl, a);
 }
 
 }  // namespace lrp

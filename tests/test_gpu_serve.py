@@ -1,0 +1,102 @@
+"""Continuous-batching server: requests with new u0 and new sources on
+resident coarse solvers of two operators (the 1D heat and 1D advection-
+diffusion-reaction problems).  Each served result equals the direct solve of
+the same request (alone) within 1e-12 relative, whatever else shares the
+launches, and meets its tolerance against the oracle's fine solution."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from paper_2508_08873_gb300 import api, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def setup():
+    ctx = api.Context(0)
+    Ph = W.heat1d()
+    Pa = W.adr1d(n=1023, N=16, M=64, R=8, p=4)
+    oph = api.Operator.tridiag(ctx, Ph.lo, Ph.di, Ph.up)
+    opa = api.Operator.tridiag(ctx, Pa.lo, Pa.di, Pa.up)
+    coh = api.Coarse(ctx, oph, Ph.dt, Ph.M, Ph.N, Ph.R, Ph.p, 0, prec="mixed")
+    coa = api.Coarse(ctx, opa, Pa.dt, Pa.M, Pa.N, Pa.R, Pa.p, 0, prec="mixed")
+    return ctx, (Ph, oph, coh), (Pa, opa, coa)
+
+
+def _request(P, k):
+    u0, g, c = W.serving_request(P.n, P.N, P.M, P.dt, k)
+    return u0, g, c
+
+
+def test_served_equals_direct_alone_and_in_mix(setup, orc):
+    ctx, H, A = setup
+    srv = api.Server(ctx, max_slots=8, max_terms=4)
+    reqs = []
+    for k in range(10):
+        P, op, co = (H, A)[k % 2]
+        u0, g, c = _request(P, k)
+        t = srv.submit(co, u0, g, c, K=P.N, tol=1e-10)
+        reqs.append((t, P, op, co, u0, g, c))
+    for t, P, op, co, u0, g, c in reqs:
+        u, info = srv.wait(t, timeout=120)
+        direct, dinfo = api.parareal_solve(ctx, co, u0, g, c, K=P.N, tol=1e-10)
+        assert info["k_done"] == dinfo["k_done"]
+        assert np.linalg.norm(u - direct) <= 1e-12 * np.linalg.norm(direct)
+        ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, u0, g, c)
+        assert orc.rel_err(u, ref) <= 1e-9
+        assert info["latency_ms"] >= info["queue_ms"] >= 0
+    # the same request alone on a fresh server
+    t0, P, op, co, u0, g, c = reqs[3]
+    srv2 = api.Server(ctx, max_slots=8, max_terms=4)
+    u_alone, _ = srv2.wait(srv2.submit(co, u0, g, c, K=P.N, tol=1e-10), timeout=60)
+    direct, _ = api.parareal_solve(ctx, co, u0, g, c, K=P.N, tol=1e-10)
+    assert np.linalg.norm(u_alone - direct) <= 1e-12 * np.linalg.norm(direct)
+    st = srv.stats()
+    assert st["completed"] == 10 and st["error"] == 0
+    srv.close()
+    srv2.close()
+
+
+def test_admission_queue_and_poll(setup):
+    """More requests than slots: the rest wait in the queue and are admitted
+    as slots free up; poll is non-blocking."""
+    ctx, H, A = setup
+    P, op, co = A
+    srv = api.Server(ctx, max_slots=2, max_terms=4)
+    tickets = [srv.submit(co, *_request(P, 100 + k), K=3, tol=0.0) for k in range(7)]
+    done = {}
+    t_end = time.time() + 120
+    while len(done) < len(tickets) and time.time() < t_end:
+        for t in tickets:
+            if t not in done:
+                ok, u, info = srv.poll(t)
+                if ok:
+                    done[t] = info
+        time.sleep(0.001)
+    assert len(done) == 7
+    assert all(d["k_done"] == 3 for d in done.values())
+    assert max(d["queue_ms"] for d in done.values()) > 0
+    srv.close()
+
+
+def test_concurrent_submitters(setup):
+    ctx, H, A = setup
+    P, op, co = H
+    srv = api.Server(ctx, max_slots=16, max_terms=4)
+    out = {}
+
+    def client(k):
+        u0, g, c = _request(P, 200 + k)
+        t = srv.submit(co, u0, g, c, K=P.N, tol=1e-10)
+        out[k] = srv.wait(t, timeout=120)
+
+    th = [threading.Thread(target=client, args=(k,)) for k in range(6)]
+    for x in th:
+        x.start()
+    for x in th:
+        x.join()
+    assert len(out) == 6 and all(v[1]["converged"] for v in out.values())
+    srv.close()
