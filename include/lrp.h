@@ -84,6 +84,10 @@ long lrp_launch_count(lrp_ctx* ctx);
  *   "sweep_cluster": CTAs per thread-block cluster of the coarse sweep (1..16,
  *                    a power of two);
  *   "tri_cluster":   CTAs per tridiagonal system for small batches (1, 2, 4);
+ *   "tri_chunk":     rows per chunk of the cluster tridiagonal kernel (8, 16);
+ *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);
+ *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
+ *                    kernel (1..16, at most 512 threads per CTA);
  *   "queue_cluster": CTAs per cluster of the batched 2D work queue (1..16,
  *                    a power of two).
  * Results do not depend on these settings beyond rounding. */

@@ -1,0 +1,70 @@
+"""Autotuner for the launch parameters of the library (lrp_set_param).
+
+For a given coarse handle it times a short Parareal solve under each candidate
+setting of the tridiagonal cluster split (CTAs per system, rows per chunk,
+systems per thread) and of the coarse-sweep cluster size, using the library's
+per-kernel CUDA-event timers, and leaves the fastest setting applied to the
+context.  Results are cached in memory per (n, N, precision, device name).
+Every candidate computes the same solution up to rounding; the tuner only
+picks launch shapes.
+"""
+from __future__ import annotations
+
+from typing import Dict, Iterable, Optional, Tuple
+
+from . import api
+
+_CACHE: Dict[Tuple, Dict[str, int]] = {}
+
+TRI_CANDIDATES = ((0, 0, 0), (2, 16, 1), (2, 8, 2), (4, 8, 2), (4, 8, 1), (1, 16, 1))
+SWEEP_CANDIDATES = (0, 8, 16)
+
+
+def _device_name(ctx: api.Context) -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(ctx.device)
+    except Exception:
+        return "cuda:%d" % ctx.device
+
+
+def _apply(ctx: api.Context, params: Dict[str, int]):
+    for k, v in params.items():
+        ctx.set_param(k, v)
+
+
+def tune_solve(ctx: api.Context, co: api.Coarse, u0, K: int = 6,
+               tri: Iterable = TRI_CANDIDATES, sweep: Iterable = SWEEP_CANDIDATES,
+               verbose: bool = False) -> Dict[str, int]:
+    """Pick the launch parameters minimising the device time of K Parareal
+    iterations (fine propagations + coarse sweeps) for this coarse handle."""
+    key = (co.op.n, co.N, co.prec, _device_name(ctx))
+    if key in _CACHE:
+        _apply(ctx, _CACHE[key])
+        return dict(_CACHE[key])
+    best: Optional[Tuple[float, Dict[str, int]]] = None
+    for (tc, m, spt) in tri:
+        for sc in sweep:
+            params = {"tri_cluster": tc, "tri_chunk": m, "tri_spt": spt, "sweep_cluster": sc}
+            try:
+                _apply(ctx, params)
+                api.parareal_solve(ctx, co, u0, K=2, bounds=False)        # plans, warm-up
+                ctx.set_kernel_timing(True)
+                ctx.reset_kernel_time()
+                api.parareal_solve(ctx, co, u0, K=K, bounds=False)
+                t = sum(ctx.kernel_time(f)[1] for f in ("propagate_f64", "propagate_f32", "sweep"))
+            except Exception:
+                continue
+            finally:
+                ctx.set_kernel_timing(False)
+            if verbose:
+                print("autotune", params, "%.3f ms" % t)
+            if best is None or t < best[0]:
+                best = (t, params)
+    if best is None:
+        params = {"tri_cluster": 0, "tri_chunk": 0, "tri_spt": 0, "sweep_cluster": 0}
+    else:
+        params = best[1]
+    _apply(ctx, params)
+    _CACHE[key] = dict(params)
+    return dict(params)

@@ -36,12 +36,15 @@ lrp_status cuda_err(Ctx* c, cudaError_t e, const char* where) {
 
 DevBuf::~DevBuf() { release(); }
 
+static void pool_drain(Ctx* c);
+
 void ctx_retain(Ctx* c) { if (c) c->refs += 1; }
 
 void ctx_release(Ctx* c) {
   if (!c || --c->refs > 0) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  pool_drain(c);
   for (auto& kv : c->timers)
     for (auto& pr : kv.second.pairs) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
@@ -68,22 +71,69 @@ Coarse::~Coarse() {
   ctx_release(c);
 }
 
+// Buffers go back to the context's pool (the memory stays allocated and
+// counted in in_use) unless the pool is full.  Users of a buffer finish in
+// stream order before it is released: every path synchronises the
+// context's stream before dropping temporaries.
 void DevBuf::release() {
   if (ptr) {
-    cudaFree(ptr);
-    if (ctx) ctx->in_use -= bytes;
+    bool kept = false;
+    if (ctx) {
+      std::lock_guard<std::mutex> lk(ctx->pool_mu);
+      if (ctx->pool_bytes + bytes <= ctx->pool_cap) {
+        ctx->pool.emplace(bytes, ptr);
+        ctx->pool_bytes += bytes;
+        kept = true;
+      }
+    }
+    if (!kept) {
+      cudaFree(ptr);
+      if (ctx) ctx->in_use -= bytes;
+    }
   }
   ptr = nullptr;
   bytes = 0;
 }
 
+static void pool_drain(Ctx* c) {
+  std::lock_guard<std::mutex> lk(c->pool_mu);
+  for (auto& kv : c->pool) {
+    cudaFree(kv.second);
+    c->in_use -= kv.first;
+  }
+  c->pool.clear();
+  c->pool_bytes = 0;
+}
+
 lrp_status dev_alloc(Ctx* c, DevBuf& b, size_t bytes) {
   b.release();
   if (bytes == 0) bytes = 16;
-  if (c->budget && c->in_use + bytes > c->budget)
-    return set_err(c, LRP_ENOMEM, "HBM budget of the context exceeded");
+  bytes = (bytes + 255) & ~(size_t)255;
+  {
+    // reuse a pooled block of at least `bytes` and at most twice that
+    std::lock_guard<std::mutex> lk(c->pool_mu);
+    auto it = c->pool.lower_bound(bytes);
+    if (it != c->pool.end() && it->first <= 2 * bytes) {
+      b.ctx = c;
+      b.ptr = it->second;
+      b.bytes = it->first;
+      c->pool_bytes -= it->first;
+      c->pool.erase(it);
+      return LRP_OK;
+    }
+  }
+  if (c->budget && c->in_use + bytes > c->budget) {
+    pool_drain(c);
+    if (c->in_use + bytes > c->budget)
+      return set_err(c, LRP_ENOMEM, "HBM budget of the context exceeded");
+  }
   void* p = nullptr;
   cudaError_t e = cudaMalloc(&p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    pool_drain(c);
+    e = cudaMalloc(&p, bytes);
+  }
   if (e) { cudaGetLastError(); return cuda_err(c, e, "cudaMalloc"); }
   b.ctx = c;
   b.ptr = p;
@@ -230,6 +280,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_chunk") {
     if (value != 0 && value != 8 && value != 16) return LRP_EINVAL;
     c->p_tri_chunk = value;
+  } else if (k == "tri_group") {
+    if (value < 0 || value > 16) return LRP_EINVAL;
+    c->p_tri_group = value;
   } else if (k == "queue_cluster") {
     if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
     c->p_queue_cluster = value;
@@ -247,6 +300,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "queue_cluster") *value = c->p_queue_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
   else if (k == "tri_chunk") *value = c->p_tri_chunk;
+  else if (k == "tri_group") *value = c->p_tri_group;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
 }
@@ -380,8 +434,11 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       if (s) return s;
       return tri_propagate_cluster(c, cp, M, nsys, prec, spt, in, out, src);
     }
+    // FP32 with n in [256, 4096]: chunks of 16 rows keep the factors in
+    // registers (k_tri_propagate_rc)
+    const int m_req = (prec == 1 && op->n >= 256 && op->n <= 4096) ? 16 : 0;
     TriPlan* plan = nullptr;
-    lrp_status s = tri_get_plan(c, op, dt, adjoint, &plan);
+    lrp_status s = tri_get_plan(c, op, dt, adjoint, &plan, m_req);
     if (s) return s;
     return tri_propagate(c, op, plan, M, nsys, prec, in, out, src);
   }

@@ -53,6 +53,14 @@ struct Ctx {
   int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
+  int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
+  // Caching allocator: released buffers are kept (up to pool_cap bytes) and
+  // reused by later allocations of a similar size, so repeated builds and
+  // solves do not pay cudaMalloc/cudaFree (cudaFree synchronises the device).
+  std::mutex pool_mu;
+  std::multimap<size_t, void*> pool;
+  size_t pool_bytes = 0;
+  size_t pool_cap = (size_t)16 << 30;
   // Handles (operators, coarse solvers) hold a reference; the context is
   // deleted when lrp_destroy has been called and the last handle is freed.
   int refs = 1;
@@ -138,7 +146,8 @@ void timer_begin(Ctx* c, const char* fam, cudaEvent_t* ev);
 void timer_end(Ctx* c, const char* fam, cudaEvent_t ev);
 
 // ---- tridiagonal propagator (tridiag.cu) -----------------------------------
-lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out);
+// m_req = 0: the default chunk size for n; else the requested rows per chunk.
+lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out, int m_req = 0);
 
 // Input of a propagation: either vectors in memory or Gaussian sketch vectors
 // generated in the kernel (system s -> interval s / ncol, column s % ncol).

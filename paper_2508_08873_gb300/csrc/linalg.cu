@@ -22,10 +22,13 @@ namespace lrp {
 // ---------------------------------------------------------------------------
 constexpr int ORTH_THREADS = 512;
 
+// Warp sums stay in the vector's type (FP32 in the mixed mode: FP64 arithmetic
+// runs at 1/64 of the FP32 rate on GB300); the per-warp results are combined
+// in FP64.
 template <typename T>
 __device__ double block_sum(T v, double* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  double d = warp_sum<double>((double)v);
+  double d = (double)warp_sum<T>(v);
   __syncthreads();
   if (lane == 0) red[w] = d;
   __syncthreads();
@@ -40,9 +43,8 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_cgs2(int ell, int n, T* __rest
                                                         int* __restrict__ rank) {
   extern __shared__ double sm[];
   const int nw = blockDim.x >> 5;
-  double* red = sm;                 // [ell][nw] partial dots
-  double* h = red + ell * nw;       // [ell]
-  double* red1 = h + ell;           // [nw]
+  double* red1 = sm;                // [nw] block-sum scratch
+  T* hT = reinterpret_cast<T*>(red1 + nw);   // [ell] projection coefficients
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   T* B = X + (size_t)blockIdx.x * ell * n;
   double* Rc = Rcoef + (size_t)blockIdx.x * ell * ell;
@@ -54,24 +56,23 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_cgs2(int ell, int n, T* __rest
     for (int i = threadIdx.x; i < n; i += blockDim.x) acc += v[i] * v[i];
     double nrm0 = sqrt(block_sum(acc, red1));
     for (int pass = 0; pass < 2; ++pass) {
-      for (int c = 0; c < r; ++c) {
+      // one warp per basis vector c: lanes stride the rows, so the loads of
+      // a warp are independent and the dot needs no cross-warp reduction
+      for (int c = w; c < r; c += nw) {
         const T* q = B + (size_t)c * n;
         T pc = T(0);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) pc += q[i] * v[i];
-        double d = warp_sum<double>((double)pc);
-        if (lane == 0) red[c * nw + w] = d;
-      }
-      __syncthreads();
-      if (threadIdx.x < r) {
-        double s = 0.0;
-        for (int i = 0; i < nw; ++i) s += red[threadIdx.x * nw + i];
-        h[threadIdx.x] = s;
-        Rc[threadIdx.x * ell + j] += s;
+#pragma unroll 4
+        for (int i = lane; i < n; i += 32) pc += q[i] * v[i];
+        pc = warp_sum<T>(pc);
+        if (lane == 0) {
+          hT[c] = pc;
+          Rc[c * ell + j] += (double)pc;
+        }
       }
       __syncthreads();
       for (int i = threadIdx.x; i < n; i += blockDim.x) {
         T s = v[i];
-        for (int c = 0; c < r; ++c) s -= (T)h[c] * B[(size_t)c * n + i];
+        for (int c = 0; c < r; ++c) s -= hT[c] * B[(size_t)c * n + i];
         v[i] = s;
       }
       __syncthreads();
@@ -97,7 +98,7 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
                      double* Rcoef, int* rank) {
   if (N <= 0) return LRP_OK;
   const int nw = ORTH_THREADS / 32;
-  size_t smem = sizeof(double) * ((size_t)ell * nw + ell + nw);
+  size_t smem = sizeof(double) * ((size_t)ell + nw);
   cudaEvent_t ev = nullptr;
   timer_begin(c, "orth", &ev);
   if (x_f64)
@@ -260,16 +261,16 @@ __global__ void k_lift(int ell, int R, int n, const T* __restrict__ W, const T* 
   const T* Wi = W + (size_t)iv * ell * n;
   const T* Vi = Vh + (size_t)iv * ell * n;
   for (int r = 0; r < R; ++r) {
-    double u = 0.0, v = 0.0;
+    T u = T(0), v = T(0);               // the bases' precision (FP32 in the mixed mode)
     if (r < rk) {
       for (int j = 0; j < ell; ++j) {
-        u += sPsi[r * ell + j] * (double)Wi[(size_t)j * n + row];
-        v += sPhi[r * ell + j] * (double)Vi[(size_t)j * n + row];
+        u += (T)sPsi[r * ell + j] * Wi[(size_t)j * n + row];
+        v += (T)sPhi[r * ell + j] * Vi[(size_t)j * n + row];
       }
     }
     size_t o = ((size_t)iv * R + r) * n + row;
-    U[o] = u;
-    V[o] = v;
+    U[o] = (double)u;
+    V[o] = (double)v;
     U32[o] = (float)u;
     V32[o] = (float)v;
   }

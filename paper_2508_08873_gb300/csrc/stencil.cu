@@ -64,7 +64,15 @@ struct ClRed {
   double part[2][KRY_MAXNV];
   double red[KRY_THREADS / 32][KRY_MAXNV];
   double gath[KRY_MAXCS][KRY_MAXNV];
+  const double* rpart[KRY_MAXCS];   // part[][] of every CTA of the cluster (DSMEM), mapped once
 };
+
+// Map the partial-sum arrays of all CTAs of the cluster once per kernel.
+__device__ __forceinline__ void cl_map(cg::cluster_group& cl, ClRed& sh) {
+  for (int q = threadIdx.x; q < (int)cl.num_blocks(); q += blockDim.x)
+    sh.rpart[q] = cl.map_shared_rank(&sh.part[0][0], q);
+  __syncthreads();
+}
 
 // Cluster-wide sum of nv values (deterministic order); also a cluster barrier.
 template <int NV>
@@ -83,10 +91,8 @@ __device__ __forceinline__ void cl_sum(cg::cluster_group& cl, double (&v)[NV], C
   }
   cl.sync();
   const int cs = (int)cl.num_blocks();
-  for (int k = threadIdx.x; k < cs * NV; k += blockDim.x) {
-    const double* rp = cl.map_shared_rank(&sh.part[buf][0], k / NV);
-    sh.gath[k / NV][k % NV] = rp[k % NV];
-  }
+  for (int k = threadIdx.x; k < cs * NV; k += blockDim.x)
+    sh.gath[k / NV][k % NV] = sh.rpart[k / NV][buf * KRY_MAXNV + k % NV];
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
@@ -153,7 +159,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
         ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
     for (int j = 0; j < a.M; ++j) {
       // ---- right-hand side d = x + dt f, residual r = d - B x --------------
-      double red3[3] = {0.0, 0.0, 0.0};    // d.d, r.r, rho
+      T red3t[3] = {T(0), T(0), T(0)};    // d.d, r.r, rho (per-thread partials in T)
       for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         T d = x[k];
         if (csys)
@@ -161,18 +167,19 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
             d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
         T rk = d - stencil_apply(B, n, mx, k, x);
         r[k] = rk;
-        red3[0] += (double)d * (double)d;
-        red3[1] += (double)rk * (double)rk;
+        red3t[0] += d * d;
+        red3t[1] += rk * rk;
         if (a.bicg) {
           rh[k] = rk;
           p[k] = rk;
-          red3[2] += (double)rk * (double)rk;
+          red3t[2] += rk * rk;
         } else {
           T z = rk * Bd[k];
           p[k] = z;
-          red3[2] += (double)rk * (double)z;
+          red3t[2] += rk * z;
         }
       }
+      double red3[3] = {(double)red3t[0], (double)red3t[1], (double)red3t[2]};
       cl_sum<3>(cl, red3, sh, buf);
       const double tol2 = a.rtol * a.rtol * red3[0];
       double rr = red3[1], rho = red3[2];
@@ -180,23 +187,25 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
       if (!a.bicg) {
         // ---- preconditioned conjugate gradients ----------------------------
         while (rr > tol2 && it < a.max_iter) {
-          double pq[1] = {0.0};
+          T pqt = T(0);
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             T qk = stencil_apply(B, n, mx, k, p);
             q[k] = qk;
-            pq[0] += (double)p[k] * (double)qk;
+            pqt += p[k] * qk;
           }
+          double pq[1] = {(double)pqt};
           cl_sum<1>(cl, pq, sh, buf);
           if (!(pq[0] > 0.0)) { my_status |= 2; break; }
           const T alpha = (T)(rho / pq[0]);
-          double rz[2] = {0.0, 0.0};
+          T rz0 = T(0), rz1 = T(0);
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             x[k] += alpha * p[k];
             T rk = r[k] - alpha * q[k];
             r[k] = rk;
-            rz[0] += (double)rk * (double)(rk * Bd[k]);
-            rz[1] += (double)rk * (double)rk;
+            rz0 += rk * (rk * Bd[k]);
+            rz1 += rk * rk;
           }
+          double rz[2] = {(double)rz0, (double)rz1};
           cl_sum<2>(cl, rz, sh, buf);
           const T beta = (T)(rz[0] / rho);
           rho = rz[0];
@@ -219,12 +228,13 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
           first = false;
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) ph[k] = p[k] * Bd[k];
           cl.sync();
-          double rv[1] = {0.0};
+          T rvt = T(0);
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             T vk = stencil_apply(B, n, mx, k, ph);
             q[k] = vk;
-            rv[0] += (double)rh[k] * (double)vk;
+            rvt += rh[k] * vk;
           }
+          double rv[1] = {(double)rvt};
           cl_sum<1>(cl, rv, sh, buf);
           if (rv[0] == 0.0 || !isfinite(rv[0])) { my_status |= 2; break; }
           alpha = (T)(rho / rv[0]);
@@ -234,23 +244,25 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
             shh[k] = s * Bd[k];
           }
           cl.sync();
-          double ts[2] = {0.0, 0.0};
+          T ts0 = T(0), ts1 = T(0);
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             T t = stencil_apply(B, n, mx, k, shh);
             tv[k] = t;
-            ts[0] += (double)t * (double)sv[k];
-            ts[1] += (double)t * (double)t;
+            ts0 += t * sv[k];
+            ts1 += t * t;
           }
+          double ts[2] = {(double)ts0, (double)ts1};
           cl_sum<2>(cl, ts, sh, buf);
           omega = ts[1] > 0.0 ? (T)(ts[0] / ts[1]) : T(0);
-          double rr2[2] = {0.0, 0.0};
+          T rr0 = T(0), rr1 = T(0);
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
             x[k] += alpha * ph[k] + omega * shh[k];
             T rk = sv[k] - omega * tv[k];
             r[k] = rk;
-            rr2[0] += (double)rh[k] * (double)rk;
-            rr2[1] += (double)rk * (double)rk;
+            rr0 += rh[k] * rk;
+            rr1 += rk * rk;
           }
+          double rr2[2] = {(double)rr0, (double)rr1};
           cl_sum<2>(cl, rr2, sh, buf);
           rho_prev = rho;
           rho = rr2[0];
@@ -282,6 +294,7 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
   const int crank = (int)cl.block_rank();
   const int slot = blockIdx.x / cs, nslots = gridDim.x / cs;
   T* ws = static_cast<T*>(a.ws) + (size_t)slot * a.nvec * a.n;
+  cl_map(cl, sh);
   int buf = 0;
   unsigned long long my_iters = 0;
   int my_status = 0;
@@ -310,6 +323,7 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov_queue(const KryArgs* __r
   const int crank = (int)cl.block_rank();
   const int slot = blockIdx.x / cs;
   T* ws = reinterpret_cast<T*>(static_cast<char*>(ws_all) + (size_t)slot * ws_stride);
+  cl_map(cl, sh);
   int buf = 0;
   unsigned long long my_iters = 0;
   int my_status = 0;

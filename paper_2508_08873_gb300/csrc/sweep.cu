@@ -57,6 +57,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   __shared__ double coef[SWEEP_MAXR + 2];
   __shared__ TF scoef[SWEEP_MAXR];                      // S_r * c_r in the apply type
   __shared__ TF sS[2][SWEEP_MAXR];                      // staged S of the next interval
+  __shared__ const double* rpart[SWEEP_MAXCS];          // part[][] of every CTA (DSMEM)
   const int per = (n + cs - 1) / cs;
   const int lo = crank * per, hi = min(n, lo + per), rows = max(0, hi - lo);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -99,6 +100,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   };
   issue(a.first, 0);
   cp_async_commit();
+  // distributed-shared-memory addresses of every CTA's partial sums, mapped once
+  for (int q = threadIdx.x; q < cs; q += blockDim.x) rpart[q] = cl.map_shared_rank(&part[0][0], q);
   // delta at the first interval: 0 (u^k_first == u^{k-1}_first), or u0 initially
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
     double d0 = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
@@ -110,9 +113,9 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   __syncthreads();
   int buf = 0;
   // ||u^k_first||^2 of this thread's rows; later intervals carry it from the update
-  double acc_u_next = 0.0;
+  TF acc_u_next = TF(0);
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    double v = a.u[(size_t)a.first * n + lo + i];
+    TF v = (TF)a.u[(size_t)a.first * n + lo + i];
     acc_u_next += v * v;
   }
   for (int iv = a.first; iv <= N; ++iv) {
@@ -122,14 +125,16 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     cp_async_wait<1>();                     // this interval's slices have landed
     __syncthreads();
     // ---- partial reductions over this CTA's rows ---------------------------
-    double acc_d = 0.0, acc_u = acc_u_next;
+    // norms for the bound in the apply type (FP32 in the mixed mode: FP64
+    // instructions issue at 1/64 of the FP32 rate on GB300)
+    TF acc_d = TF(0), acc_u = acc_u_next;
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-      double d = dsm[i];
+      TF d = dsT[i];
       acc_d += d * d;
     }
-    acc_d = warp_sum(acc_d);
-    acc_u = warp_sum(acc_u);
-    if (lane == 0) { red[w][R] = acc_d; red[w][R + 1] = acc_u; }
+    acc_d = warp_sum<TF>(acc_d);
+    acc_u = warp_sum<TF>(acc_u);
+    if (lane == 0) { red[w][R] = (double)acc_d; red[w][R + 1] = (double)acc_u; }
     if (iv < N) {
       // one warp per factor row r: (V_iv[r], delta) over this CTA's rows
       const TF* Vi = stage ? sV + (size_t)sb * R * per : V + (size_t)iv * R * n + lo;
@@ -138,8 +143,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
         const TF* vr = Vi + (size_t)r * ldv;
         TF pr = TF(0);
         for (int i = lane; i < rows; i += 32) pr += vr[i] * dsT[i];
-        double d = warp_sum((double)pr);
-        if (lane == 0) part[buf][r] = d;   // this CTA's partial dot (single writer)
+        pr = warp_sum<TF>(pr);
+        if (lane == 0) part[buf][r] = (double)pr;   // this CTA's partial dot (single writer)
       }
     }
     __syncthreads();
@@ -152,10 +157,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     // ---- gather the partials of all CTAs with one remote read each ---------
     for (int k = threadIdx.x; k < cs * nv; k += blockDim.x) {
       int q = k / nv, j = k % nv;
-      if (iv < N || j >= R) {
-        const double* rp = cl.map_shared_rank(&part[buf][0], q);
-        gath[q][j] = rp[j];
-      }
+      if (iv < N || j >= R) gath[q][j] = rpart[q][buf * (SWEEP_MAXR + 2) + j];
     }
     __syncthreads();
     if (threadIdx.x < nv) {
@@ -177,7 +179,7 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     const size_t ldu = stage ? (size_t)per : (size_t)n;
     const double* Fi = stage ? sF + (size_t)sb * per : a.F + (size_t)iv * n + lo;
     double* un = a.u + (size_t)(iv + 1) * n + lo;
-    acc_u_next = 0.0;
+    acc_u_next = TF(0);
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
       TF g = TF(0);
       for (int r = 0; r < R; ++r) g += Ui[(size_t)r * ldu + i] * scoef[r];
@@ -187,7 +189,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
       dsm[i] = dn;
       if (kSep) dsT[i] = (TF)dn;
       un[i] = nv_;
-      acc_u_next += nv_ * nv_;
+      const TF nt = (TF)nv_;
+      acc_u_next += nt * nt;
     }
     buf ^= 1;
     __syncthreads();

@@ -273,6 +273,151 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
   }
 }
 
+// Register-resident variant: every thread keeps its chunk's factors (5 MM
+// values) and its PCR factors in registers for the whole launch and advances
+// SPT systems at once, so a step reads no factors from shared memory (the
+// FP32 kernel above is bound by shared-memory bandwidth: 5 loads per
+// row-step) and one set of barriers serves SPT systems.  FP32, MM = 16.
+template <typename T, int MM, int LMAX, int SPT>
+__global__ void __launch_bounds__(256) k_tri_propagate_rc(TriKArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int P = a.P, L = a.L;
+  T* xb = reinterpret_cast<T*>(smem_raw);                  // [SPT][3][P]
+  const int t = threadIdx.x;
+  const T* gco = static_cast<const T*>(a.coef);
+  const T* gpc = static_cast<const T*>(a.pcr);
+  T cl[MM], ci[MM], cu[MM], cp[MM], cq[MM], k1[LMAX], k2[LMAX];
+#pragma unroll
+  for (int i = 0; i < MM; ++i) {
+    cl[i] = gco[(size_t)(0 * MM + i) * P + t];
+    ci[i] = gco[(size_t)(1 * MM + i) * P + t];
+    cu[i] = gco[(size_t)(2 * MM + i) * P + t];
+    cp[i] = gco[(size_t)(3 * MM + i) * P + t];
+    cq[i] = gco[(size_t)(4 * MM + i) * P + t];
+  }
+#pragma unroll
+  for (int l = 0; l < LMAX; ++l) {
+    k1[l] = l < L ? gpc[(size_t)l * P + t] : T(0);
+    k2[l] = l < L ? gpc[(size_t)(L + l) * P + t] : T(0);
+  }
+  const T dinv = gpc[(size_t)(2 * L) * P + t];
+  const T dt = (T)a.dt;
+  const int n = a.n;
+  const int r0 = t * MM;
+  for (int base = blockIdx.x * SPT; base < a.nsys; base += gridDim.x * SPT) {
+    T x[SPT][MM];
+    const double* csys[SPT];
+    const double* gsys[SPT];
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+      const int sys = base + s;
+      const bool active = sys < a.nsys;
+#pragma unroll
+      for (int i = 0; i < MM; ++i) {
+        int r = r0 + i;
+        T v = T(0);
+        if (active && r < n) {
+          if (a.in.gen)
+            v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                         (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+          else if (a.in.x == nullptr)
+            v = T(0);
+          else if (a.in.x_f64)
+            v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+          else
+            v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+        }
+        x[s][i] = v;
+      }
+      csys[s] = (active && a.src.Q > 0)
+          ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+      gsys[s] = (active && a.src.Q > 0 && a.src.map)
+          ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
+    }
+    for (int j = 0; j < a.M; ++j) {
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        if (csys[s]) {
+          for (int q = 0; q < a.src.Q; ++q) {
+            T cq_ = dt * (T)csys[s][(size_t)j * a.src.Q + q];
+            const double* gq = gsys[s] + (size_t)q * n;
+#pragma unroll
+            for (int i = 0; i < MM; ++i)
+              if (r0 + i < n) x[s][i] += cq_ * (T)gq[r0 + i];
+          }
+        }
+      }
+#pragma unroll
+      for (int i = 1; i < MM - 1; ++i)
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) x[s][i] -= cl[i] * x[s][i - 1];
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) x[s][MM - 2] *= ci[MM - 2];
+#pragma unroll
+      for (int i = MM - 3; i >= 0; --i)
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) x[s][i] = x[s][i] * ci[i] - cu[i] * x[s][i + 1];
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) xb[(s * 3 + 2) * P + t] = x[s][0];
+      __syncthreads();
+      T r[SPT];
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        T gnext = (t + 1 < P) ? xb[(s * 3 + 2) * P + t + 1] : T(0);
+        r[s] = x[s][MM - 1] - cl[MM - 1] * x[s][MM - 2] - cu[MM - 1] * gnext;
+      }
+      int buf = 0;
+#pragma unroll
+      for (int lev = 0; lev < LMAX; ++lev) {
+        if (lev < L) {
+          const int sh = 1 << lev;
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) xb[(s * 3 + buf) * P + t] = r[s];
+          __syncthreads();
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            T rm = (t - sh >= 0) ? xb[(s * 3 + buf) * P + t - sh] : T(0);
+            T rp = (t + sh < P) ? xb[(s * 3 + buf) * P + t + sh] : T(0);
+            r[s] = r[s] - k1[lev] * rm - k2[lev] * rp;
+          }
+          buf ^= 1;
+        }
+      }
+      T y[SPT];
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        y[s] = r[s] * dinv;
+        xb[(s * 3 + buf) * P + t] = y[s];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < SPT; ++s) {
+        const T yl = (t > 0) ? xb[(s * 3 + buf) * P + t - 1] : T(0);
+#pragma unroll
+        for (int i = 0; i < MM - 1; ++i) x[s][i] = x[s][i] - cp[i] * yl - cq[i] * y[s];
+        x[s][MM - 1] = y[s];
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < SPT; ++s) {
+      const int sys = base + s;
+      if (sys >= a.nsys) continue;
+#pragma unroll
+      for (int i = 0; i < MM; ++i) {
+        int r = r0 + i;
+        if (r < n) {
+          const long o = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys) + r;
+          if (a.out.y_f64)
+            static_cast<double*>(a.out.y)[o] = (double)x[s][i];
+          else
+            static_cast<float*>(a.out.y)[o] = (float)x[s][i];
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
@@ -283,15 +428,18 @@ static int choose_m(int n) {
   return 4;
 }
 
-lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out) {
+lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** out, int m_req) {
   std::lock_guard<std::mutex> plan_lock(op->plan_mu);
   for (auto& p : op->plans)
-    if (p->dt == dt && p->adjoint == adjoint) { *out = p.get(); return LRP_OK; }
+    if (p->dt == dt && p->adjoint == adjoint && (m_req == 0 ? p->m == choose_m(op->n) : p->m == m_req)) {
+      *out = p.get();
+      return LRP_OK;
+    }
   auto pl = std::make_unique<TriPlan>();
   pl->dt = dt;
   pl->adjoint = adjoint;
   pl->n = op->n;
-  pl->m = choose_m(op->n);
+  pl->m = m_req ? m_req : choose_m(op->n);
   pl->P = (op->n + pl->m - 1) / pl->m;
   if (pl->P > 512) return set_err(c, LRP_EINVAL, "tridiagonal operator too large (n > 16384)");
   int L = 0;
@@ -326,7 +474,10 @@ lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** 
 template <typename T, int MM>
 static lrp_status launch_tri(Ctx* c, TriPlan* plan, TriKArgs& a) {
   const int P = a.P;
-  int Gmax = std::max(1, 512 / P);
+  // up to 256 threads per CTA: two CTAs share an SM, so one CTA's barriers
+  // overlap the other's arithmetic (c->p_tri_group overrides, tuning)
+  int Gmax = std::max(1, (c->p_tri_group > 0 ? c->p_tri_group * P : 256) / P);
+  if (P * Gmax > 512) Gmax = std::max(1, 512 / P);
   // spread small batches over the SMs before packing systems into a CTA
   int G = std::max(1, std::min(Gmax, a.nsys / std::max(1, c->num_sms)));
   a.G = G;
@@ -347,6 +498,29 @@ static lrp_status launch_tri(Ctx* c, TriPlan* plan, TriKArgs& a) {
   e = cudaGetLastError();
   timer_end(c, fam, ev);
   if (e) return cuda_err(c, e, "k_tri_propagate launch");
+  return LRP_OK;
+}
+
+template <typename T, int MM, int LMAX, int SPT>
+static lrp_status launch_tri_rc(Ctx* c, TriKArgs& a) {
+  const int P = a.P;
+  const int G = SPT;                  // systems per CTA
+  a.G = 1;
+  size_t smem = sizeof(T) * (size_t)SPT * 3 * P;
+  auto kern = k_tri_propagate_rc<T, MM, LMAX, SPT>;
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P, smem);
+  if (e) return cuda_err(c, e, "tri rc occupancy");
+  if (per_sm < 1) return set_err(c, LRP_EINVAL, "tridiagonal kernel does not fit on an SM");
+  int groups = (a.nsys + G - 1) / G;
+  int grid = std::min(groups, per_sm * c->num_sms);
+  const char* fam = sizeof(T) == 8 ? "propagate_f64" : "propagate_f32";
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, fam, &ev);
+  kern<<<grid, P, smem, c->stream>>>(a);
+  e = cudaGetLastError();
+  timer_end(c, fam, ev);
+  if (e) return cuda_err(c, e, "k_tri_propagate_rc launch");
   return LRP_OK;
 }
 
@@ -375,6 +549,12 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
   }
   a.coef = plan->coef32.ptr;
   a.pcr = plan->pcr32.ptr;
+  if (plan->m == 16 && plan->P <= 256 && plan->levels <= 8) {
+    // enough systems to fill the SMs with 4 per CTA, else 2 or 1
+    if (nsys >= 4 * c->num_sms) return launch_tri_rc<float, 16, 8, 4>(c, a);
+    if (nsys >= 2 * c->num_sms) return launch_tri_rc<float, 16, 8, 2>(c, a);
+    return launch_tri_rc<float, 16, 8, 1>(c, a);
+  }
   switch (plan->m) {
     case 4: return launch_tri<float, 4>(c, plan, a);
     case 8: return launch_tri<float, 8>(c, plan, a);
