@@ -197,6 +197,22 @@ lrp_status lrp_coarse_info(const lrp_coarse* co, int* R_i, int* rank_w, int* ran
 lrp_status lrp_coarse_factors(const lrp_coarse* co, int interval, double* U, double* S,
                               double* V);
 
+/* Checkpoint of a coarse handle (the factors depend on the operator and the
+ * time grid only, so a saved handle serves later solves with any source).
+ * meta_i[6] = {M, N, rank, oversample, n, precision}, meta_d[3] = {dt, delta,
+ * eps}; R_i, rank_w, rank_v: N ints; sigma: N x (rank+oversample); U, V:
+ * N x max(rank,1) x n; S: N x max(rank,1) (all host or device memory).  The
+ * export fills what is not NULL; the import creates a handle for `op`
+ * (whose size must be n) from the same arrays. */
+lrp_status lrp_coarse_export(const lrp_coarse* co, int* meta_i, double* meta_d, uint64_t* seed,
+                             int* R_i, int* rank_w, int* rank_v, double* sigma, double* U,
+                             double* S, double* V);
+lrp_status lrp_coarse_import(lrp_ctx* ctx, const lrp_operator* op, const int* meta_i,
+                             const double* meta_d, uint64_t seed, const int* R_i,
+                             const int* rank_w, const int* rank_v, const double* sigma,
+                             const double* U, const double* S, const double* V,
+                             lrp_coarse** out);
+
 /* ---- Parareal (Eq. def_Parareal) ----------------------------------------- */
 
 typedef struct {

@@ -97,6 +97,8 @@ SIGNATURES = [
     ("lrp_coarse_free", None, [_P]),
     ("lrp_coarse_info", _I, [_P, _P, _P, _P, _P, _P, _P]),
     ("lrp_coarse_factors", _I, [_P, _I, _P, _P, _P]),
+    ("lrp_coarse_export", _I, [_P, _P, _P, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P, _P, _P, _P, _P]),
+    ("lrp_coarse_import", _I, [_P, _P, _P, _P, _U64, _P, _P, _P, _P, _P, _P, _P, _PP]),
     ("lrp_parareal_solve", _I, [_P, _P, _P, _I, _P, _P, _I, _D, _P, _P, _PI,
                                 ctypes.POINTER(SolveStats)]),
     ("lrp_fine_solution", _I, [_P, _P, _D, _I, _I, _P, _I, _P, _P, _P]),

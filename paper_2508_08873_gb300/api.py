@@ -209,6 +209,45 @@ class Coarse:
                                               V.ctypes.data), self.ctx.h)
         return U, S, V
 
+    def save(self, path: str):
+        """Checkpoint the factors and metadata to an .npz file."""
+        N, n, ell = self.N, self.op.n, self.R + self.p
+        Rm = max(self.R, 1)
+        mi = np.zeros(6, dtype=np.int32)
+        md = np.zeros(3)
+        seed = ctypes.c_uint64()
+        Ri, rw, rv = (np.zeros(N, dtype=np.int32) for _ in range(3))
+        sig = np.zeros((N, ell))
+        U = np.zeros((N, Rm, n))
+        V = np.zeros((N, Rm, n))
+        S = np.zeros((N, Rm))
+        check(self.ctx.lib.lrp_coarse_export(self.h, mi.ctypes.data, md.ctypes.data, ctypes.byref(seed),
+                                             Ri.ctypes.data, rw.ctypes.data, rv.ctypes.data,
+                                             sig.ctypes.data, U.ctypes.data, S.ctypes.data,
+                                             V.ctypes.data), self.ctx.h)
+        np.savez(path, meta_i=mi, meta_d=md, seed=np.uint64(seed.value), Ri=Ri, rank_w=rw,
+                 rank_v=rv, sigma=sig, U=U, S=S, V=V)
+
+    @classmethod
+    def load(cls, ctx: Context, op: Operator, path: str) -> "Coarse":
+        z = np.load(path)
+        mi = np.ascontiguousarray(z["meta_i"], dtype=np.int32)
+        md = np.ascontiguousarray(z["meta_d"], dtype=np.float64)
+        arrs = {k: np.ascontiguousarray(z[k]) for k in ("Ri", "rank_w", "rank_v", "sigma", "U", "S", "V")}
+        h = ctypes.c_void_p()
+        check(ctx.lib.lrp_coarse_import(ctx.h, op.h, mi.ctypes.data, md.ctypes.data, int(z["seed"]),
+                                        arrs["Ri"].ctypes.data, arrs["rank_w"].ctypes.data,
+                                        arrs["rank_v"].ctypes.data, arrs["sigma"].ctypes.data,
+                                        arrs["U"].ctypes.data, arrs["S"].ctypes.data,
+                                        arrs["V"].ctypes.data, ctypes.byref(h)), ctx.h)
+        c = cls.__new__(cls)
+        c.ctx, c.op = ctx, op
+        c.M, c.N, c.R, c.p = int(mi[0]), int(mi[1]), int(mi[2]), int(mi[3])
+        c.dt = float(md[0])
+        c.prec = int(mi[5])
+        c.h = h
+        return c
+
     def close(self):
         if getattr(self, "h", None) and not nat.exiting():
             self.ctx.lib.lrp_coarse_free(self.h)

@@ -420,10 +420,23 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       spt = c->p_tri_spt ? c->p_tri_spt : 1;
       if (!fits(C, m)) C = 1;
     } else if (c->p_tri_cluster == 0 && op->n >= 2048) {
-      // measured on GB300 (adr1d, n = 4095): 2 CTAs per system beat 1 by
-      // 1.45x and 4 by 2%, so 4 is used only when 2 do not fit a system
-      if (nsys * 2 <= c->num_sms && fits(2, 16)) C = 2;
-      else if (nsys * 4 <= c->num_sms && fits(4, 16)) C = 4;
+      // measured on GB300 (adr1d, n = 4095, 64 systems, FP64): 4 CTAs with
+      // 8-row chunks 1.13 ms, 2 CTAs with 16-row chunks 1.26 ms, one CTA per
+      // system 1.90 ms; clusters beyond the resident ones run in a second wave.
+      // Systems too long for one CTA's shared memory always take a cluster.
+      const int m1 = op->n >= 1024 ? 32 : 16;
+      const int P1 = (op->n + m1 - 1) / m1;
+      int L1 = 0;
+      while ((1 << L1) < P1) ++L1;
+      const size_t one_cta = (size_t)(prec == 0 ? 8 : 4) *
+                             ((size_t)5 * m1 * P1 + (size_t)(2 * L1 + 1) * P1 + 3 * (size_t)P1);
+      const bool small_batch = nsys * 2 <= c->num_sms;
+      const bool must = (one_cta > 220 * 1024 || P1 > 512) && !(prec == 1 && op->n <= 4096);
+      if (small_batch || must) {
+        const int cand[3][2] = {{4, 8}, {2, 16}, {4, 16}};
+        for (auto& cm : cand)
+          if (fits(cm[0], cm[1])) { C = cm[0]; m = cm[1]; break; }
+      }
       if (c->p_tri_chunk) m = c->p_tri_chunk;
       if (c->p_tri_spt) spt = c->p_tri_spt;
       if (C > 1 && !fits(C, m)) { C = 1; }
@@ -682,6 +695,80 @@ lrp_status lrp_coarse_factors(const lrp_coarse* co, int interval, double* U, dou
     return s;
   cudaError_t e = cudaStreamSynchronize(c->stream);
   return e ? cuda_err(c, e, "coarse_factors") : LRP_OK;
+}
+
+// ---- checkpoint: export / import of a coarse handle ------------------------
+lrp_status lrp_coarse_export(const lrp_coarse* co, int* meta_i, double* meta_d, uint64_t* seed,
+                             int* R_i, int* rank_w, int* rank_v, double* sigma, double* U,
+                             double* S, double* V) {
+  if (!co || !meta_i || !meta_d) return LRP_EINVAL;
+  Ctx* c = co->ctx;
+  const int n = co->op->n, N = co->N, Rm = std::max(co->R, 1);
+  meta_i[0] = co->M; meta_i[1] = N; meta_i[2] = co->R; meta_i[3] = co->p; meta_i[4] = n;
+  meta_i[5] = (int)co->prec;
+  meta_d[0] = co->dt; meta_d[1] = co->delta; meta_d[2] = co->eps;
+  if (seed) *seed = co->seed;
+  if (R_i) std::memcpy(R_i, co->Ri.data(), sizeof(int) * N);
+  if (rank_w) std::memcpy(rank_w, co->rank_w.data(), sizeof(int) * N);
+  if (rank_v) std::memcpy(rank_v, co->rank_v.data(), sizeof(int) * N);
+  if (sigma) std::memcpy(sigma, co->sigma.data(), sizeof(double) * (size_t)N * co->ell);
+  lrp_status s;
+  if (U && (s = from_device(c, U, co->U.ptr, sizeof(double) * (size_t)N * Rm * n))) return s;
+  if (V && (s = from_device(c, V, co->V.ptr, sizeof(double) * (size_t)N * Rm * n))) return s;
+  if (S && (s = from_device(c, S, co->S.ptr, sizeof(double) * (size_t)N * Rm))) return s;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  return e ? cuda_err(c, e, "coarse export") : LRP_OK;
+}
+
+__global__ static void k_copy_f32(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+  size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) b[k] = (float)a[k];
+}
+
+lrp_status lrp_coarse_import(lrp_ctx* c, const lrp_operator* opc, const int* meta_i,
+                             const double* meta_d, uint64_t seed, const int* R_i,
+                             const int* rank_w, const int* rank_v, const double* sigma,
+                             const double* U, const double* S, const double* V,
+                             lrp_coarse** out) {
+  if (!c || !opc || !meta_i || !meta_d || !R_i || !rank_w || !rank_v || !sigma || !U || !S || !V ||
+      !out)
+    return LRP_EINVAL;
+  if (meta_i[4] != opc->n || meta_i[1] < 1 || meta_i[2] < 0 || meta_i[3] < 0 || meta_i[0] < 1)
+    return set_err(c, LRP_EINVAL, "checkpoint does not match the operator");
+  cudaSetDevice(c->device);
+  auto co = std::make_unique<lrp_coarse>();
+  co->ctx = c;
+  ctx_retain(c);
+  co->op = const_cast<lrp_operator*>(opc);
+  co->M = meta_i[0]; co->N = meta_i[1]; co->R = meta_i[2]; co->p = meta_i[3];
+  co->ell = co->R + co->p;
+  co->prec = (lrp_precision)meta_i[5];
+  co->dt = meta_d[0]; co->delta = meta_d[1]; co->eps = meta_d[2];
+  co->seed = seed;
+  const int N = co->N, n = opc->n, Rm = std::max(co->R, 1);
+  co->Ri.assign(R_i, R_i + N);
+  co->rank_w.assign(rank_w, rank_w + N);
+  co->rank_v.assign(rank_v, rank_v + N);
+  co->sigma.assign(sigma, sigma + (size_t)N * co->ell);
+  const size_t nf = (size_t)N * Rm * n, ns = (size_t)N * Rm;
+  lrp_status s;
+  if ((s = dev_alloc(c, co->U, 8 * nf))) return s;
+  if ((s = dev_alloc(c, co->V, 8 * nf))) return s;
+  if ((s = dev_alloc(c, co->S, 8 * ns))) return s;
+  if ((s = dev_alloc(c, co->U32, 4 * nf))) return s;
+  if ((s = dev_alloc(c, co->V32, 4 * nf))) return s;
+  if ((s = dev_alloc(c, co->S32, 4 * ns))) return s;
+  if ((s = to_device(c, co->U.ptr, U, 8 * nf))) return s;
+  if ((s = to_device(c, co->V.ptr, V, 8 * nf))) return s;
+  if ((s = to_device(c, co->S.ptr, S, 8 * ns))) return s;
+  k_copy_f32<<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(co->U.as<double>(), co->U32.as<float>(), nf);
+  k_copy_f32<<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(co->V.as<double>(), co->V32.as<float>(), nf);
+  k_copy_f32<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(co->S.as<double>(), co->S32.as<float>(), ns);
+  cudaError_t e = cudaGetLastError();
+  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "coarse import");
+  *out = co.release();
+  return LRP_OK;
 }
 
 // ===========================================================================

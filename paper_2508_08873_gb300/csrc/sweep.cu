@@ -51,13 +51,14 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   const int n = a.n, R = a.R, N = a.N;
   const int nv = R + 2;                                 // R dots, ||delta||^2, ||u||^2
   extern __shared__ double dsm[];                       // delta of this CTA's rows
-  __shared__ double part[2][SWEEP_MAXR + 2];
   __shared__ double red[SWEEP_THREADS / 32][SWEEP_MAXR + 2];
-  __shared__ double gath[SWEEP_MAXCS][SWEEP_MAXR + 2];
+  // partial sums of every CTA, pushed here by their owners before the barrier
+  // (remote stores), so that no remote read sits on the critical path
+  __shared__ double gath[2][SWEEP_MAXCS][SWEEP_MAXR + 2];
   __shared__ double coef[SWEEP_MAXR + 2];
   __shared__ TF scoef[SWEEP_MAXR];                      // S_r * c_r in the apply type
   __shared__ TF sS[2][SWEEP_MAXR];                      // staged S of the next interval
-  __shared__ const double* rpart[SWEEP_MAXCS];          // part[][] of every CTA (DSMEM)
+  __shared__ double* rgath[SWEEP_MAXCS];                // gath[][][] of every CTA (DSMEM)
   const int per = (n + cs - 1) / cs;
   const int lo = crank * per, hi = min(n, lo + per), rows = max(0, hi - lo);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -101,7 +102,8 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
   issue(a.first, 0);
   cp_async_commit();
   // distributed-shared-memory addresses of every CTA's partial sums, mapped once
-  for (int q = threadIdx.x; q < cs; q += blockDim.x) rpart[q] = cl.map_shared_rank(&part[0][0], q);
+  for (int q = threadIdx.x; q < cs; q += blockDim.x) rgath[q] = cl.map_shared_rank(&gath[0][0][0], q);
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
   // delta at the first interval: 0 (u^k_first == u^{k-1}_first), or u0 initially
   for (int i = threadIdx.x; i < rows; i += blockDim.x) {
     double d0 = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
@@ -144,26 +146,24 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
         TF pr = TF(0);
         for (int i = lane; i < rows; i += 32) pr += vr[i] * dsT[i];
         pr = warp_sum<TF>(pr);
-        if (lane == 0) part[buf][r] = (double)pr;   // this CTA's partial dot (single writer)
+        if (lane == 0) {                   // push this CTA's partial dot to every CTA
+          const int o = (buf * SWEEP_MAXCS + crank) * (SWEEP_MAXR + 2) + r;
+          for (int q = 0; q < cs; ++q) rgath[q][o] = (double)pr;
+        }
       }
     }
     __syncthreads();
     if (threadIdx.x < 2) {
       double s = 0.0;
       for (int k = 0; k < nw; ++k) s += red[k][R + threadIdx.x];
-      part[buf][R + threadIdx.x] = s;
+      const int o = (buf * SWEEP_MAXCS + crank) * (SWEEP_MAXR + 2) + R + threadIdx.x;
+      for (int q = 0; q < cs; ++q) rgath[q][o] = s;
     }
     cl.sync();
-    // ---- gather the partials of all CTAs with one remote read each ---------
-    for (int k = threadIdx.x; k < cs * nv; k += blockDim.x) {
-      int q = k / nv, j = k % nv;
-      if (iv < N || j >= R) gath[q][j] = rpart[q][buf * (SWEEP_MAXR + 2) + j];
-    }
-    __syncthreads();
     if (threadIdx.x < nv) {
       double s = 0.0;
       if (iv < N || threadIdx.x >= R)
-        for (int q = 0; q < cs; ++q) s += gath[q][threadIdx.x];    // same order in every CTA
+        for (int q = 0; q < cs; ++q) s += gath[buf][q][threadIdx.x];    // same order in every CTA
       coef[threadIdx.x] = s;
       if (threadIdx.x < R && iv < N)
         scoef[threadIdx.x] = (stage ? sS[sb][threadIdx.x] : S[(size_t)iv * R + threadIdx.x]) * (TF)s;

@@ -134,7 +134,10 @@ __global__ void __launch_bounds__(1024) k_tri_factor(const double* __restrict__ 
     if (t < P) { sa[t] = na; sb[t] = nb; sc[t] = nc; }
     __syncthreads();
   }
-  if (t < P) pcr[(size_t)(2 * L) * P + t] = 1.0 / sb[t];
+  if (t < P) {
+    if (!(fabs(sb[t]) > 0.0) || !isfinite(sb[t])) bad = 1;
+    pcr[(size_t)(2 * L) * P + t] = 1.0 / sb[t];
+  }
   __syncthreads();
   // FP32 copies
   for (size_t k = t; k < 5 * MP; k += blockDim.x) coef32[k] = (float)coef[k];

@@ -160,7 +160,10 @@ __global__ void __launch_bounds__(1024) k_tri_factor_cl(const double* __restrict
     if (t < P && tl < Pl) { la[t] = na; lb[t] = nb; lc[t] = nc; }
     __syncthreads();
   }
-  if (t < P) lp[(size_t)(2 * L) * Pc + tl] = (tl < Pl) ? 1.0 / lb[t] : 0.0;
+  if (t < P) {
+    if (tl < Pl && (!(fabs(lb[t]) > 0.0) || !isfinite(lb[t]))) bad = 1;
+    lp[(size_t)(2 * L) * Pc + tl] = (tl < Pl) ? 1.0 / lb[t] : 0.0;
+  }
   // ---- spikes of the local systems: P2 (left coupling), Q2 (right) ----------
   if (t < P) {
     r1[t] = (tl == 0 && Pl > 0) ? ag[t] : 0.0;
@@ -211,6 +214,19 @@ __global__ void __launch_bounds__(1024) k_tri_factor_cl(const double* __restrict
       piv_prev = piv;
       gs_prev = gs;
     }
+    // dense inverse of the C x C super system (columns: solves with e_p), so
+    // that every step solves it with one short product per CTA
+    double* minv = sup + 6 * CL_MAXC;
+    for (int pcol = 0; pcol < C; ++pcol) {
+      double w[CL_MAXC];
+      for (int q = 0; q < C; ++q)
+        w[q] = (q == pcol ? 1.0 : 0.0) - (q > 0 ? sup[(size_t)q * 6 + 3] * w[q - 1] : 0.0);
+      double Y = 0.0;
+      for (int q = C - 1; q >= 0; --q) {
+        Y = (w[q] - (q + 1 < C ? sup[(size_t)q * 6 + 5] * Y : 0.0)) * sup[(size_t)q * 6 + 4];
+        minv[q * CL_MAXC + pcol] = Y;
+      }
+    }
   }
   if (bad) atomicOr(status, 1);
 }
@@ -250,9 +266,13 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
   T* s_pcr = s_coef + 5 * MM * Pc;                        // [2L+1][Pc]
   T* s_spk = s_pcr + (2 * L + 1) * Pc;                    // [2][Pc]
   T* s_sup = s_spk + 2 * Pc;                              // [C][6]
-  T* xb = s_sup + 6 * CL_MAXC;                            // [SPT][3][Pc]
+  T* xb = s_sup + 6 * CL_MAXC + CL_MAXC * CL_MAXC;        // [SPT][3][Pc]
   T* Ysh = xb + SPT * 3 * Pc;                             // [SPT][CL_MAXC]
-  __shared__ double pub[2][SPT][4];
+  // values every CTA publishes for the super system, pushed into the shared
+  // memory of all CTAs of the cluster before the barrier (no remote read on
+  // the critical path after it): pubg[parity][system][cta][4]
+  __shared__ double pubg[2][SPT][CL_MAXC][4];
+  __shared__ double* rpub[CL_MAXC];
   {
     const T* gco = static_cast<const T*>(a.coef) + (size_t)c * 5 * MM * Pc;
     const T* gpc = static_cast<const T*>(a.lpcr) + (size_t)c * (2 * L + 1) * Pc;
@@ -261,9 +281,10 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
     for (int k = threadIdx.x; k < 5 * MM * Pc; k += blockDim.x) s_coef[k] = gco[k];
     for (int k = threadIdx.x; k < (2 * L + 1) * Pc; k += blockDim.x) s_pcr[k] = gpc[k];
     for (int k = threadIdx.x; k < 2 * Pc; k += blockDim.x) s_spk[k] = gsp[k];
-    for (int k = threadIdx.x; k < 6 * C; k += blockDim.x) s_sup[k] = gsu[k];
+    for (int k = threadIdx.x; k < 6 * CL_MAXC + CL_MAXC * CL_MAXC; k += blockDim.x) s_sup[k] = gsu[k];
+    for (int q = threadIdx.x; q < C; q += blockDim.x) rpub[q] = cl.map_shared_rank(&pubg[0][0][0][0], q);
   }
-  __syncthreads();
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
   const int tl = threadIdx.x;
   const int t = c * Pc + tl;
   const T* cl_ = s_coef;
@@ -369,40 +390,38 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
 #pragma unroll
       for (int s = 0; s < SPT; ++s) {
         z0[s] = (tl < Pl) ? r[s] * dv : T(0);
-        if (tl == 0) { pub[pb][s][0] = (double)z0[s]; pub[pb][s][3] = (double)x[s][0]; }
-        if (tl == Pl - 1) pub[pb][s][1] = (double)z0[s];
-        if (tl == Pc - 1) pub[pb][s][2] = (double)r[s];
+        const int o = ((pb * SPT + s) * CL_MAXC + c) * 4;
+        if (tl == 0) {
+          for (int q = 0; q < C; ++q) { rpub[q][o + 0] = (double)z0[s]; rpub[q][o + 3] = (double)x[s][0]; }
+        }
+        if (tl == Pl - 1)
+          for (int q = 0; q < C; ++q) rpub[q][o + 1] = (double)z0[s];
+        if (tl == Pc - 1)
+          for (int q = 0; q < C; ++q) rpub[q][o + 2] = (double)r[s];
       }
       cl.sync();
-      if (tl < SPT) {
-        // thread s solves the C x C super system of system s
-        const int s = tl;
-        double zf[CL_MAXC], zl[CL_MAXC], rpart[CL_MAXC], g0[CL_MAXC], w[CL_MAXC];
-#pragma unroll
-        for (int q = 0; q < CL_MAXC; ++q) {
-          zf[q] = zl[q] = rpart[q] = g0[q] = w[q] = 0.0;
-          if (q < C) {
-            const double* pp = cl.map_shared_rank(&pub[pb][s][0], q);
-            zf[q] = pp[0]; zl[q] = pp[1]; rpart[q] = pp[2]; g0[q] = pp[3];
-          }
+      if (tl < SPT * C) {
+        // lane s*C + q forms the right-hand side of super unknown q of system
+        // s, the C lanes of a system exchange them by shuffles and each
+        // applies one row of the precomputed inverse
+        const int s = tl / C, q = tl % C;
+        const double* pq = &pubg[pb][s][q][0];
+        double rhs = pq[2] - (double)s_sup[6 * q] * pq[1];
+        if (q + 1 < C) {
+          const double* pn = &pubg[pb][s][q + 1][0];
+          rhs -= (double)s_sup[6 * q + 2] * pn[3] + (double)s_sup[6 * q + 1] * pn[0];
         }
-#pragma unroll
-        for (int q = 0; q < CL_MAXC; ++q) {
-          if (q < C) {
-            const T* su = s_sup + 6 * q;
-            double v = rpart[q] - (double)su[0] * zl[q];
-            if (q + 1 < C) v -= (double)su[2] * g0[q + 1] + (double)su[1] * zf[q + 1];
-            w[q] = v - (q > 0 ? (double)su[3] * w[q - 1] : 0.0);
-          }
-        }
+        const unsigned mask = (SPT * C >= 32) ? 0xffffffffu : ((1u << (SPT * C)) - 1u);
+        const T* minv = s_sup + 6 * CL_MAXC + q * CL_MAXC;
         double Y = 0.0;
 #pragma unroll
-        for (int q = CL_MAXC - 1; q >= 0; --q) {
-          if (q < C) {
-            Y = (w[q] - (q + 1 < C ? (double)s_sup[6 * q + 5] * Y : 0.0)) * (double)s_sup[6 * q + 4];
-            Ysh[s * CL_MAXC + q] = (T)Y;
+        for (int pcol = 0; pcol < CL_MAXC; ++pcol) {
+          if (pcol < C) {
+            double rp = __shfl_sync(mask, rhs, s * C + pcol);
+            Y += (double)minv[pcol] * rp;
           }
         }
+        Ysh[s * CL_MAXC + q] = (T)Y;
       }
       __syncthreads();
       T y[SPT], Yl[SPT];
@@ -470,7 +489,7 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
   while ((1 << L) < pl->Pc - 1) ++L;
   pl->L = L;
   const size_t ncoef = (size_t)5 * CL_M * P, npcr = (size_t)C * (2 * L + 1) * pl->Pc,
-               nspk = (size_t)2 * P, nsup = 6 * CL_MAXC;
+               nspk = (size_t)2 * P, nsup = 6 * CL_MAXC + CL_MAXC * CL_MAXC;
   pl->sz[0] = ncoef; pl->sz[1] = npcr; pl->sz[2] = nspk; pl->sz[3] = nsup;
   lrp_status s;
   for (int k = 0; k < 4; ++k) {
@@ -507,7 +526,8 @@ template <typename T, int MM, int SPT>
 static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   const int Pc = pl->Pc, L = pl->L, C = pl->C;
   size_t smem = sizeof(T) * ((size_t)5 * MM * Pc + (size_t)(2 * L + 1) * Pc + 2 * Pc +
-                             6 * CL_MAXC + (size_t)SPT * 3 * Pc + (size_t)SPT * CL_MAXC);
+                             6 * CL_MAXC + CL_MAXC * CL_MAXC + (size_t)SPT * 3 * Pc +
+                             (size_t)SPT * CL_MAXC);
   auto kern = k_tri_cluster<T, MM, SPT>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return cuda_err(c, e, "cluster tri smem attribute");

@@ -273,3 +273,19 @@ def test_propagate_cluster_paths_f64(ctx, orc, n, nvec, adjoint):
     assert e <= tol, (e, tol)
     got32 = api.propagate(ctx, op, dt, M, X[:2], adjoint=adjoint, prec="mixed")
     assert max(rel(got32[v], want[v]) for v in range(2)) <= 2e-5
+
+
+def test_coarse_checkpoint_roundtrip(ctx, tmp_path):
+    """A saved coarse handle reproduces the solves of the original bitwise."""
+    P = W.heat1d(n=255, N=8, M=32, R=6, p=3)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, 0, prec="mixed")
+    u1, i1 = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=3)
+    path = str(tmp_path / "coarse.npz")
+    co.save(path)
+    co2 = api.Coarse.load(ctx, op, path)
+    u2, i2 = api.parareal_solve(ctx, co2, P.u0, P.g, P.c, K=3)
+    np.testing.assert_array_equal(u1, u2)
+    a, b = co.info(), co2.info()
+    np.testing.assert_array_equal(a["sigma"], b["sigma"])
+    assert a["eps"] == b["eps"] and a["delta"] == b["delta"]
