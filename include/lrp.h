@@ -81,8 +81,8 @@ size_t lrp_bytes_in_use(lrp_ctx* ctx);
 long lrp_launch_count(lrp_ctx* ctx);
 
 /* Launch tuning (0 = automatic, the default):
- *   "sweep_cluster": CTAs per thread-block cluster of the coarse sweep (1..16,
- *                    a power of two);
+ *   "sweep_rows":    rows of a vector per CTA in the coarse sweep (128..2048,
+ *                    a power of two; default 1024);
  *   "tri_cluster":   CTAs per tridiagonal system for small batches (1, 2, 4);
  *   "tri_chunk":     rows per chunk of the cluster tridiagonal kernel (8, 16);
  *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);

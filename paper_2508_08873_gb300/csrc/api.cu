@@ -66,7 +66,8 @@ Operator::~Operator() {
 
 Coarse::~Coarse() {
   Ctx* c = ctx;
-  for (DevBuf* b : {&U, &S, &V, &U32, &S32, &V32, &ws_u, &ws_F, &ws_b, &ws_norm, &ws_d, &ws_g, &ws_c})
+  for (DevBuf* b : {&U, &S, &V, &U32, &S32, &V32, &Kc, &ws_u, &ws_F, &ws_b, &ws_norm, &ws_d, &ws_g,
+                     &ws_c, &ws_cw, &ws_cnt, &ws_args})
     b->release();
   ctx_release(c);
 }
@@ -268,9 +269,9 @@ long lrp_launch_count(lrp_ctx* c) { return c ? c->launches : 0; }
 lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   if (!c || !name) return LRP_EINVAL;
   std::string k(name);
-  if (k == "sweep_cluster") {
-    if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
-    c->p_sweep_cluster = value;
+  if (k == "sweep_rows") {
+    if (value != 0 && (value < 128 || value > 2048 || (value & (value - 1)))) return LRP_EINVAL;
+    c->p_sweep_rows = value;
   } else if (k == "tri_cluster") {
     if (value != 0 && value != 1 && value != 2 && value != 4) return LRP_EINVAL;
     c->p_tri_cluster = value;
@@ -295,7 +296,7 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
 lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   if (!c || !name || !value) return LRP_EINVAL;
   std::string k(name);
-  if (k == "sweep_cluster") *value = c->p_sweep_cluster;
+  if (k == "sweep_rows") *value = c->p_sweep_rows;
   else if (k == "tri_cluster") *value = c->p_tri_cluster;
   else if (k == "queue_cluster") *value = c->p_queue_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
@@ -656,6 +657,7 @@ lrp_status lrp_build_coarse(lrp_ctx* c, const lrp_operator* opc, double dt, int 
     }
   if ((s = to_device(c, co->S.ptr, S64.data(), S64.size() * 8))) return s;
   if ((s = to_device(c, co->S32.ptr, S32f.data(), S32f.size() * 4))) return s;
+  if ((s = coarse_chain(c, co.get()))) return s;
   e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "build_coarse");
   *out = co.release();
@@ -765,7 +767,9 @@ lrp_status lrp_coarse_import(lrp_ctx* c, const lrp_operator* opc, const int* met
   k_copy_f32<<<(unsigned)((nf + 255) / 256), 256, 0, c->stream>>>(co->V.as<double>(), co->V32.as<float>(), nf);
   k_copy_f32<<<(unsigned)((ns + 255) / 256), 256, 0, c->stream>>>(co->S.as<double>(), co->S32.as<float>(), ns);
   cudaError_t e = cudaGetLastError();
-  if (!e) e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "coarse import");
+  if ((s = coarse_chain(c, co.get()))) return s;
+  e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "coarse import");
   *out = co.release();
   return LRP_OK;
@@ -791,7 +795,6 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
     if ((s = dev_alloc(c, co->ws_u, sizeof(double) * (size_t)(N + 1) * n))) return s;
     if ((s = dev_alloc(c, co->ws_F, sizeof(double) * (size_t)N * n))) return s;
     if ((s = dev_alloc(c, co->ws_b, sizeof(double) * (size_t)N * n))) return s;
-    if ((s = dev_alloc(c, co->ws_d, sizeof(double) * (size_t)n))) return s;
     if ((s = dev_alloc(c, co->ws_norm, sizeof(double) * (size_t)(3 * (N + 1) + 2)))) return s;
   }
   double* du = co->ws_norm.as<double>();
@@ -827,6 +830,8 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
   } else {
     cudaMemsetAsync(co->ws_b.ptr, 0, co->ws_b.bytes, c->stream);
   }
+  const int rows = sweep_rows(c);
+  if ((s = coarse_sweep_workspace(c, co, rows))) return s;
   SweepArgs a;
   a.N = N;
   a.n = n;
@@ -835,8 +840,12 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
   a.U = f32 ? co->U32.ptr : co->U.ptr;
   a.S = f32 ? co->S32.ptr : co->S.ptr;
   a.V = f32 ? co->V32.ptr : co->V.ptr;
+  a.K = co->Kc.as<double>();
   a.f32 = f32;
-  a.dscr = co->ws_d.as<double>();
+  a.rows = rows;
+  a.nsl = (n + rows - 1) / rows;
+  a.cw = co->ws_cw.as<double>();
+  a.cnt = co->ws_cnt.as<unsigned>();
   a.delta = co->delta;
   a.eps = co->eps;
   a.du = du;
@@ -847,7 +856,8 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
   a.initial = 1;
   a.F = co->ws_b.as<double>();
   a.bound = nullptr;
-  if ((s = coarse_sweep(c, a))) return s;
+  SweepArgs* dargs = co->ws_args.as<SweepArgs>();
+  if ((s = coarse_sweep(c, &a, dargs, 1))) return s;
   int k = 0, converged = 0;
   double hsum[2] = {0.0, 0.0};
   a.initial = 0;
@@ -867,7 +877,7 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
     if (Q > 0) sk.c = src.c + (size_t)first * M * Q;
     if ((s = propagate_any(c, op, co->dt, M, 0, N - first, 0, in, o, sk))) return s;
     a.first = first;
-    if ((s = coarse_sweep(c, a))) return s;
+    if ((s = coarse_sweep(c, &a, dargs, 1))) return s;
     ++k;
     ++evals;
     if (bound_out) {

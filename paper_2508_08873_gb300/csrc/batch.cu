@@ -212,6 +212,11 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
   if (exec) cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
   if (e) return cuda_err(c, e, "batched build graph");
+  // chain matrices of the coarse sweep (allocating, so outside the graph)
+  for (int p = 0; p < count; ++p) {
+    lrp_status r = coarse_chain(c, co[p].get());
+    if (r) return r;
+  }
   // ---- ranks, singular values, status ------------------------------------------
   unsigned long long hs[2] = {0, 0};
   cudaMemcpy(hs, d_stat.ptr, 16, cudaMemcpyDeviceToHost);
@@ -272,9 +277,9 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
       if ((s = dev_alloc(c, q->ws_u, 8 * (size_t)(N + 1) * n))) return s;
       if ((s = dev_alloc(c, q->ws_F, 8 * (size_t)N * n))) return s;
       if ((s = dev_alloc(c, q->ws_b, 8 * (size_t)N * n))) return s;
-      if ((s = dev_alloc(c, q->ws_d, 8 * (size_t)n))) return s;
       if ((s = dev_alloc(c, q->ws_norm, 8 * (size_t)(3 * (N + 1) + 2)))) return s;
     }
+    if ((s = coarse_sweep_workspace(c, q, sweep_rows(c)))) return s;
     cudaMemcpyAsync(q->ws_u.ptr, u0[p], 8 * (size_t)n, cudaMemcpyDefault, c->stream);
     cudaMemsetAsync(q->ws_b.ptr, 0, q->ws_b.bytes, c->stream);
   }
@@ -307,50 +312,44 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
   cudaError_t e = cudaMemcpyAsync(d_probs.ptr, hp.data(), sizeof(KryArgs) * count,
                                   cudaMemcpyHostToDevice, c->stream);
   if (e) return cuda_err(c, e, "batch solve setup");
-  // sweeps grouped by grid size (a batched sweep needs equal n)
-  std::map<int, std::vector<int>> by_n;
-  for (int p = 0; p < count; ++p) by_n[cos[p]->op->n].push_back(p);
+  // all problems' sweeps in one pair of launches (equal N and precision)
   DevBuf d_args;
   if ((s = dev_alloc(c, d_args, sizeof(SweepArgs) * count))) return s;
   std::vector<int> kk(count, 0), active(count, 1);
   std::vector<double> summ(2);
+  const int rows = sweep_rows(c);
+  std::vector<SweepArgs> h;
   auto sweeps = [&](int initial) -> lrp_status {
-    std::vector<SweepArgs> h;
-    size_t off = 0;
-    for (auto& kv : by_n) {
-      std::vector<SweepArgs> grp;
-      for (int p : kv.second) {
-        if (!initial && !active[p]) continue;
-        Coarse* q = cos[p];
-        const int f32 = q->prec == LRP_PREC_MIXED;
-        SweepArgs a;
-        a.N = N; a.n = q->op->n; a.R = std::max(q->R, 1);
-        a.first = initial ? 0 : kk[p];
-        a.initial = initial;
-        a.u = q->ws_u.as<double>();
-        a.F = initial ? q->ws_b.as<double>() : q->ws_F.as<double>();
-        a.U = f32 ? q->U32.ptr : q->U.ptr;
-        a.S = f32 ? q->S32.ptr : q->S.ptr;
-        a.V = f32 ? q->V32.ptr : q->V.ptr;
-        a.f32 = f32;
-        a.delta = q->delta; a.eps = q->eps;
-        double* nr = q->ws_norm.as<double>();
-        a.du = nr; a.unorm = nr + (N + 1); a.bound = initial ? nullptr : nr + 2 * (N + 1);
-        a.summary = nr + 3 * (N + 1);
-        grp.push_back(a);
-      }
-      if (grp.empty()) continue;
-      const int st = coarse_sweep_batch_stage(c, grp[0], (int)grp.size());
-      for (auto& a : grp) a.stage = st;
-      cudaError_t e2 = cudaMemcpyAsync(d_args.as<SweepArgs>() + off, grp.data(),
-                                       sizeof(SweepArgs) * grp.size(), cudaMemcpyHostToDevice, c->stream);
-      if (e2) return cuda_err(c, e2, "sweep args");
-      lrp_status r = coarse_sweep_batch(c, grp[0], d_args.as<SweepArgs>() + off, (int)grp.size(), nullptr);
-      if (r) return r;
-      cudaStreamSynchronize(c->stream);      // host args outlive their upload
-      off += grp.size();
+    h.clear();
+    for (int p = 0; p < count; ++p) {
+      if (!initial && !active[p]) continue;
+      Coarse* q = cos[p];
+      const int f32 = q->prec == LRP_PREC_MIXED;
+      SweepArgs a;
+      a.N = N; a.n = q->op->n; a.R = std::max(q->R, 1);
+      a.first = initial ? 0 : kk[p];
+      a.initial = initial;
+      a.u = q->ws_u.as<double>();
+      a.F = initial ? q->ws_b.as<double>() : q->ws_F.as<double>();
+      a.U = f32 ? q->U32.ptr : q->U.ptr;
+      a.S = f32 ? q->S32.ptr : q->S.ptr;
+      a.V = f32 ? q->V32.ptr : q->V.ptr;
+      a.K = q->Kc.as<double>();
+      a.f32 = f32;
+      a.delta = q->delta; a.eps = q->eps;
+      double* nr = q->ws_norm.as<double>();
+      a.du = nr; a.unorm = nr + (N + 1); a.bound = initial ? nullptr : nr + 2 * (N + 1);
+      a.summary = nr + 3 * (N + 1);
+      a.rows = rows;
+      a.nsl = (a.n + rows - 1) / rows;
+      a.cw = q->ws_cw.as<double>();
+      a.cnt = q->ws_cnt.as<unsigned>();
+      h.push_back(a);
     }
-    return LRP_OK;
+    if (h.empty()) return LRP_OK;
+    lrp_status r = coarse_sweep(c, h.data(), d_args.as<SweepArgs>(), (int)h.size());
+    cudaStreamSynchronize(c->stream);      // host args outlive their upload
+    return r;
   };
   if ((s = sweeps(1))) return s;
   int it = 0;

@@ -48,7 +48,7 @@ struct Ctx {
   int num_sms = 0;
   long launches = 0;       // kernels launched by this context (all families)
   // Tunable launch parameters (0 = automatic choice); see lrp_set_param.
-  int p_sweep_cluster = 0;   // CTAs per coarse-sweep cluster (1..16)
+  int p_sweep_rows = 0;      // rows per CTA slice of the coarse sweep (0: 1024)
   int p_tri_cluster = 0;     // CTAs per tridiagonal system for small batches (1, 2, 4)
   int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
@@ -133,7 +133,9 @@ struct Coarse {
   std::vector<double> sigma;  // N x ell
   double delta = 0.0, eps = 0.0;
   // solve workspace (allocated on first use)
+  DevBuf Kc;               // [N-1][R][R] chain matrices of the coarse sweep
   DevBuf ws_u, ws_F, ws_b, ws_norm, ws_d, ws_g, ws_c;
+  DevBuf ws_cw, ws_cnt, ws_args;   // coarse-sweep workspace
   size_t ws_gc_bytes = 0;
 };
 
@@ -257,20 +259,27 @@ struct SweepArgs {
   const void* U = nullptr;        // [N][R][n] (FP64, or FP32 when f32 = 1)
   const void* S = nullptr;        // [N][R]
   const void* V = nullptr;        // [N][R][n]
+  const double* K = nullptr;      // [N-1][R][R]: K_i = V_{i+1}^T U_i diag(S_i)
   int f32 = 0;                    // coarse apply G'delta in FP32 (mixed mode)
-  double* dscr = nullptr;         // n: delta scratch
   int initial = 0;                // 1: u^{-1} := 0 (initial coarse sweep)
   double delta = 0.0, eps = 0.0;
   double* du = nullptr;           // N+1: ||u^k_m - u^{k-1}_m||
   double* unorm = nullptr;        // N+1: ||u^k_m||
   double* bound = nullptr;        // N+1: a posteriori bound (Eq. apost_bound)
   double* summary = nullptr;      // [0] = max bound, [1] = max ||u^k_m||
-  int stage = 0;                  // set by the launcher: factors staged in smem
+  int rows = 0, nsl = 0;          // rows per slice, slices = ceil(n / rows)
+  double* cw = nullptr;           // workspace, sweep_ws_doubles(N, nsl, R) doubles
+  unsigned* cnt = nullptr;        // 2 completion counters, zero between launches
 };
-lrp_status coarse_sweep(Ctx* c, const SweepArgs& a);
-// Batched sweeps: nprob problems of equal n and R, arguments on the device.
-int coarse_sweep_batch_stage(Ctx* c, const SweepArgs& proto, int nprob);
-lrp_status coarse_sweep_batch(Ctx* c, const SweepArgs& proto, SweepArgs* d_args, int nprob,
-                              int* cs_out);
+// Coarse sweep of nprob problems of equal N and precision in two launches;
+// h is uploaded to d_args (nprob entries) on the stream and must stay alive
+// until the stream has passed the upload.
+lrp_status coarse_sweep(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob);
+size_t sweep_ws_doubles(int N, int nsl, int R);
+int sweep_rows(Ctx* c);
+// K_i of a coarse handle (Coarse::Kc), formed from the factors its apply uses.
+lrp_status coarse_chain(Ctx* c, Coarse* co);
+// Per-handle sweep workspace (ws_cw, ws_cnt, ws_args) for slices of `rows`.
+lrp_status coarse_sweep_workspace(Ctx* c, Coarse* co, int rows);
 
 }  // namespace lrp

@@ -60,7 +60,9 @@ struct Group {
   Coarse* co = nullptr;
   int n = 0, N = 0, M = 0, Qmax = 0, slots = 0;
   size_t su = 0, sF = 0, sg = 0, sc = 0, snorm = 0;   // per-slot strides (doubles)
-  DevBuf u, F, b, g, c, norms, summ, dargs, dmap;
+  int rows = 0, nsl = 0;                               // coarse-sweep slices
+  size_t scw = 0;                                      // per-slot sweep workspace (doubles)
+  DevBuf u, F, b, g, c, norms, summ, dargs, dmap, cw, cnt;
   std::vector<int> free;
   std::vector<Request*> active;
 };
@@ -104,7 +106,10 @@ lrp_status make_group(lrp_server* S, Coarse* co, Group** out) {
   G->sg = (size_t)G->Qmax * n;
   G->sc = N * G->M * (size_t)G->Qmax;
   G->snorm = 3 * (N + 1);
-  const size_t per_slot = 8 * (G->su + 2 * G->sF + G->sg + G->sc + G->snorm + 2) +
+  G->rows = sweep_rows(c);
+  G->nsl = (G->n + G->rows - 1) / G->rows;
+  G->scw = sweep_ws_doubles(G->N, G->nsl, std::max(co->R, 1));
+  const size_t per_slot = 8 * (G->su + 2 * G->sF + G->sg + G->sc + G->snorm + 2 + G->scw + 1) +
                           sizeof(SweepArgs) + 8 * N;
   // slots by free HBM: at most half of what the device has free, and the budget
   size_t freeb = 0, totb = 0;
@@ -124,6 +129,9 @@ lrp_status make_group(lrp_server* S, Coarse* co, Group** out) {
   if ((s = dev_alloc(c, G->summ, 16 * (size_t)slots))) return s;
   if ((s = dev_alloc(c, G->dargs, sizeof(SweepArgs) * (size_t)slots))) return s;
   if ((s = dev_alloc(c, G->dmap, 8 * N * (size_t)slots))) return s;
+  if ((s = dev_alloc(c, G->cw, 8 * G->scw * slots))) return s;
+  if ((s = dev_alloc(c, G->cnt, 2 * sizeof(unsigned) * slots))) return s;
+  cudaMemsetAsync(G->cnt.ptr, 0, G->cnt.bytes, c->stream);
   for (int i = slots - 1; i >= 0; --i) G->free.push_back(i);
   *out = G.get();
   S->groups[co] = std::move(G);
@@ -144,9 +152,14 @@ SweepArgs slot_args(Group* G, int slot, int first, int initial) {
   a.U = f32 ? co->U32.ptr : co->U.ptr;
   a.S = f32 ? co->S32.ptr : co->S.ptr;
   a.V = f32 ? co->V32.ptr : co->V.ptr;
+  a.K = co->Kc.as<double>();
   a.f32 = f32;
   a.delta = co->delta;
   a.eps = co->eps;
+  a.rows = G->rows;
+  a.nsl = G->nsl;
+  a.cw = G->cw.as<double>() + (size_t)slot * G->scw;
+  a.cnt = G->cnt.as<unsigned>() + 2 * (size_t)slot;
   double* nr = G->norms.as<double>() + (size_t)slot * G->snorm;
   a.du = nr;
   a.unorm = nr + (G->N + 1);
@@ -162,12 +175,7 @@ lrp_status batch_sweep(lrp_server* S, Group* G, const std::vector<Request*>& lis
   std::vector<SweepArgs> h(list.size());
   for (size_t i = 0; i < list.size(); ++i)
     h[i] = slot_args(G, list[i]->slot, initial ? 0 : list[i]->k, initial);
-  const int st = coarse_sweep_batch_stage(c, h[0], (int)h.size());
-  for (auto& a : h) a.stage = st;
-  cudaError_t e = cudaMemcpyAsync(G->dargs.ptr, h.data(), sizeof(SweepArgs) * h.size(),
-                                  cudaMemcpyHostToDevice, c->stream);
-  if (e) return cuda_err(c, e, "sweep args upload");
-  lrp_status s = coarse_sweep_batch(c, h[0], G->dargs.as<SweepArgs>(), (int)h.size(), nullptr);
+  lrp_status s = coarse_sweep(c, h.data(), G->dargs.as<SweepArgs>(), (int)h.size());
   // the host array must outlive the (pageable, so synchronous-for-host) copy
   cudaStreamSynchronize(c->stream);
   return s;

@@ -1,202 +1,225 @@
-// Sequential coarse sweep fused with the Parareal correction, in the delta
-// form of Remark rem:affine_g_n:
+// Coarse sweep fused with the Parareal correction, in the delta form of
+// Remark rem:affine_g_n:
 //   u^k_{i+1} = F_i u^{k-1}_i + G_i'(u^k_i - u^{k-1}_i),  G_i' = U_i diag(S_i) V_i^T,
 // and, for the initial sweep, u^0_{i+1} = b_i + G_i' u^0_i (Eq. def_Parareal
-// with u^{-1} := 0).  The iterate is updated in place; the norms
-// ||u^k_m - u^{k-1}_m|| and ||u^k_m|| are recorded on the way and the a
-// posteriori bound eps sum_{m<n} delta^{n-m-1} ||u^k_m - u^{k-1}_m||
-// (Eq. apost_bound) is evaluated by its recurrence B_n = delta B_{n-1} +
-// eps ||u^k_{n-1} - u^{k-1}_{n-1}|| at the end.
+// with u^{-1} := 0), together with the norms ||u^k_m - u^{k-1}_m||, ||u^k_m||
+// and the a posteriori bound of Eq. apost_bound through its recurrence
+// B_n = delta B_{n-1} + eps ||u^k_{n-1} - u^{k-1}_{n-1}||.
 //
-// The sweep is sequential over intervals but each step is two skinny products
-// with n x R factors, so one problem runs on a thread-block cluster: every CTA
-// owns a contiguous slice of the n rows, computes partial V_i^T delta for its
-// slice, and the partial sums are exchanged through distributed shared memory
-// with one cluster barrier per interval (double-buffered).  All CTAs add the
-// partials in the same order, so the result does not depend on timing.
-#include <cooperative_groups.h>
-
+// Evaluated in the coordinates of the low-rank factors.  With
+// Delta_i = u^k_i - u^{k-1}_i and c_i = V_i^T Delta_i (an R-vector),
+//   Delta_{i+1} = r_i + U_i diag(S_i) c_i,   r_i = F_i u^{k-1}_i - u^{k-1}_{i+1},
+// so  c_{i+1} = V_{i+1}^T r_i + K_i c_i  with  K_i = V_{i+1}^T U_i diag(S_i).
+// The K_i (R x R) depend only on the factors and are formed once per coarse
+// handle.  The sequential dependence of the sweep is then an R-dimensional
+// recurrence; everything of size n runs in parallel over all intervals:
+//   1. project:  a_{i+1} = V_{i+1}^T r_i for every interval (all SMs);
+//   2. recur:    c_{i+1} = a_{i+1} + K_i c_i (one CTA, FP64, R x R steps);
+//   3. apply:    u^k_{i+1} = F_i u^{k-1}_i + U_i (S_i * c_i) for every
+//                interval, with the norms; then the bound recurrence.
+// Steps 1+2 and 3+bound are one launch each: the CTA that finishes a launch's
+// partial sums last (device-scope counter, no waiting) runs the sequential
+// part.  Partial sums are per (interval, row slice) and are added in a fixed
+// order, so results do not depend on scheduling or on which other problems
+// share a launch.
 #include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
 #include "internal.h"
 
-namespace cg = cooperative_groups;
-
 namespace lrp {
 
-// 4- or 8-byte asynchronous global->shared copies (cp.async, completion
-// tracked per thread with commit/wait groups).
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void* smem, const void* gmem) {
-  unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+constexpr int CSW_THREADS = 256;
+constexpr int CSW_MAXROWS = 2048;    // rows per slice (upper limit)
+constexpr int CSW_MAXR = 64;
+constexpr int CSW_KBUF = 32 * 1024;  // bytes of K staged per chunk of the recurrence
 
-constexpr int SWEEP_THREADS = 256;
-constexpr int SWEEP_MAXR = 64;
-constexpr int SWEEP_MAXCS = 16;
-constexpr size_t SWEEP_STAGE_MAX = 192 * 1024;   // dynamic smem when staging factors
-constexpr size_t SWEEP_SMEM_MAX = 200 * 1024;
+// Workspace of one problem (doubles): a-partials [N][nsl][R], coefficients
+// [N][R], norm partials [N+1][nsl][2].
+__host__ __device__ inline size_t csw_coef(int N, int nsl, int R) { return (size_t)N * nsl * R; }
+__host__ __device__ inline size_t csw_npart(int N, int nsl, int R) { return csw_coef(N, nsl, R) + (size_t)N * R; }
+size_t sweep_ws_doubles(int N, int nsl, int R) { return csw_npart(N, nsl, R) + (size_t)(N + 1) * nsl * 2; }
 
-template <typename TF>
-__device__ __forceinline__ void sweep_body(const SweepArgs& a) {
-  cg::cluster_group cl = cg::this_cluster();
-  const int crank = (int)cl.block_rank();
-  const int cs = (int)cl.num_blocks();
-  const int n = a.n, R = a.R, N = a.N;
-  const int nv = R + 2;                                 // R dots, ||delta||^2, ||u||^2
-  extern __shared__ double dsm[];                       // delta of this CTA's rows
-  __shared__ double red[SWEEP_THREADS / 32][SWEEP_MAXR + 2];
-  // partial sums of every CTA, pushed here by their owners before the barrier
-  // (remote stores), so that no remote read sits on the critical path
-  __shared__ double gath[2][SWEEP_MAXCS][SWEEP_MAXR + 2];
-  __shared__ double coef[SWEEP_MAXR + 2];
-  __shared__ TF scoef[SWEEP_MAXR];                      // S_r * c_r in the apply type
-  __shared__ TF sS[2][SWEEP_MAXR];                      // staged S of the next interval
-  __shared__ double* rgath[SWEEP_MAXCS];                // gath[][][] of every CTA (DSMEM)
-  const int per = (n + cs - 1) / cs;
-  const int lo = crank * per, hi = min(n, lo + per), rows = max(0, hi - lo);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const TF* U = static_cast<const TF*>(a.U);
-  const TF* S = static_cast<const TF*>(a.S);
-  const TF* V = static_cast<const TF*>(a.V);
-  // Optional staging of the next interval's factor slices and F slice in
-  // shared memory (double-buffered cp.async), so that their load latency
-  // overlaps the current interval's reductions and cluster barrier.
-  const bool stage = a.stage != 0;
-  // delta in the apply type: a separate FP32 copy in the mixed mode (so the
-  // R dot products need no conversions), the FP64 array itself otherwise
-  constexpr bool kSep = sizeof(TF) != sizeof(double);
-  TF* dsT = kSep ? reinterpret_cast<TF*>(dsm + per) : reinterpret_cast<TF*>(dsm);
-  TF* sU = reinterpret_cast<TF*>(dsm + per) + (kSep ? per + (per & 1) : 0);   // [2][R][per]
-  TF* sV = sU + (size_t)2 * R * per;                          // [2][R][per]
-  double* sF = reinterpret_cast<double*>(sV + (size_t)2 * R * per);   // [2][per]
-  double* sO = sF + (size_t)2 * per;                          // [2][per] u^{k-1}_{iv+1}
-  auto issue = [&](int iv, int b) {
-    if (!stage || iv >= N) return;
-    const TF* Ug = U + (size_t)iv * R * n + lo;
-    const TF* Vg = V + (size_t)iv * R * n + lo;
-    const double* Fg = a.F + (size_t)iv * n + lo;
-    for (int r = 0; r < R; ++r) {                 // no integer division per element
-      TF* du = sU + ((size_t)b * R + r) * per;
-      TF* dv = sV + ((size_t)b * R + r) * per;
-      const TF* gu = Ug + (size_t)r * n;
-      const TF* gv = Vg + (size_t)r * n;
-      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        cp_async<sizeof(TF)>(du + i, gu + i);
-        cp_async<sizeof(TF)>(dv + i, gv + i);
-      }
-    }
-    const double* Og = a.u + (size_t)(iv + 1) * n + lo;
-    for (int r = threadIdx.x; r < R; r += blockDim.x) cp_async<sizeof(TF)>(&sS[b][r], S + (size_t)iv * R + r);
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-      cp_async<8>(sF + (size_t)b * per + i, Fg + i);
-      if (!a.initial) cp_async<8>(sO + (size_t)b * per + i, Og + i);
-    }
-  };
-  issue(a.first, 0);
-  cp_async_commit();
-  // distributed-shared-memory addresses of every CTA's partial sums, mapped once
-  for (int q = threadIdx.x; q < cs; q += blockDim.x) rgath[q] = cl.map_shared_rank(&gath[0][0][0], q);
-  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
-  // delta at the first interval: 0 (u^k_first == u^{k-1}_first), or u0 initially
-  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    double d0 = a.initial ? a.u[(size_t)a.first * n + lo + i] : 0.0;
-    dsm[i] = d0;
-    if (kSep) dsT[i] = (TF)d0;
-  }
-  if (crank == 0 && threadIdx.x == 0 && !a.initial)
-    for (int m = 0; m <= a.first; ++m) a.du[m] = 0.0;
+int sweep_rows(Ctx* c) { return c->p_sweep_rows > 0 ? c->p_sweep_rows : 1024; }
+int sweep_slices(Ctx* c, int n) { const int sl = sweep_rows(c); return (n + sl - 1) / sl; }
+
+// The CTA that completes a launch's partial sums for its problem last: every
+// CTA of the problem adds one to the counter after its partial sums are
+// visible device-wide.  Returns true in exactly one CTA, which also resets the
+// counter for the next launch.
+__device__ __forceinline__ bool csw_last_cta(unsigned* cnt, unsigned total) {
+  __shared__ int last;
+  __threadfence();
   __syncthreads();
-  int buf = 0;
-  // ||u^k_first||^2 of this thread's rows; later intervals carry it from the update
-  TF acc_u_next = TF(0);
-  for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-    TF v = (TF)a.u[(size_t)a.first * n + lo + i];
-    acc_u_next += v * v;
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(cnt, 1u);
+    last = (t == total - 1) ? 1 : 0;
+    if (last) *cnt = 0u;
   }
-  for (int iv = a.first; iv <= N; ++iv) {
-    const int sb = (iv - a.first) & 1;      // staging buffer of this interval
-    issue(iv + 1, sb ^ 1);
-    cp_async_commit();
-    cp_async_wait<1>();                     // this interval's slices have landed
-    __syncthreads();
-    // ---- partial reductions over this CTA's rows ---------------------------
-    // norms for the bound in the apply type (FP32 in the mixed mode: FP64
-    // instructions issue at 1/64 of the FP32 rate on GB300)
-    TF acc_d = TF(0), acc_u = acc_u_next;
+  __syncthreads();
+  if (last) __threadfence();
+  return last != 0;
+}
+
+// ---------------------------------------------------------------------------
+// 1 + 2: projections and the coefficient recurrence.
+// grid (slices, N, problems); blockIdx.y = j, the index of a_j.
+// ---------------------------------------------------------------------------
+template <typename TF>
+__global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __restrict__ args) {
+  extern __shared__ __align__(16) unsigned char csw_smem[];
+  __shared__ TF vs[CSW_MAXROWS];
+  __shared__ double cbuf[2][CSW_MAXR];
+  const SweepArgs& a = args[blockIdx.z];
+  const int j = blockIdx.y, sl = blockIdx.x;
+  const int N = a.N, n = a.n, R = a.R, nsl = a.nsl;
+  const int start = a.initial ? 0 : a.first;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* apart = a.cw;
+  if (j < N && sl < nsl && (j > start || (a.initial && j == 0))) {
+    const int lo = sl * a.rows, hi = min(n, lo + a.rows), rows = hi - lo;
+    // the vector to project: u0 (initial, j = 0), else r_{j-1}
     for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-      TF d = dsT[i];
-      acc_d += d * d;
+      double v;
+      if (j == 0) {
+        v = a.u[lo + i];
+      } else {
+        v = a.F[(size_t)(j - 1) * n + lo + i];
+        if (!a.initial) v -= a.u[(size_t)j * n + lo + i];
+      }
+      vs[i] = (TF)v;
     }
-    acc_d = warp_sum<TF>(acc_d);
-    acc_u = warp_sum<TF>(acc_u);
-    if (lane == 0) { red[w][R] = (double)acc_d; red[w][R + 1] = (double)acc_u; }
-    if (iv < N) {
-      // one warp per factor row r: (V_iv[r], delta) over this CTA's rows
-      const TF* Vi = stage ? sV + (size_t)sb * R * per : V + (size_t)iv * R * n + lo;
-      const size_t ldv = stage ? (size_t)per : (size_t)n;
-      for (int r = w; r < R; r += nw) {
-        const TF* vr = Vi + (size_t)r * ldv;
-        TF pr = TF(0);
-        for (int i = lane; i < rows; i += 32) pr += vr[i] * dsT[i];
-        pr = warp_sum<TF>(pr);
-        if (lane == 0) {                   // push this CTA's partial dot to every CTA
-          const int o = (buf * SWEEP_MAXCS + crank) * (SWEEP_MAXR + 2) + r;
-          for (int q = 0; q < cs; ++q) rgath[q][o] = (double)pr;
+    __syncthreads();
+    const TF* Vj = static_cast<const TF*>(a.V) + (size_t)j * R * n + lo;
+    for (int r = w; r < R; r += nw) {
+      const TF* vr = Vj + (size_t)r * n;
+      TF acc = TF(0);
+      for (int i = lane; i < rows; i += 32) acc += vr[i] * vs[i];
+      acc = warp_sum<TF>(acc);
+      if (lane == 0) apart[((size_t)j * nsl + sl) * R + r] = (double)acc;
+    }
+  }
+  if (!csw_last_cta(&a.cnt[0], gridDim.x * gridDim.y)) return;
+  // ---- the recurrence (this CTA only) ---------------------------------------
+  double* coef = a.cw + csw_coef(N, nsl, R);
+  // a_j summed over the slices in a fixed order, for j in [start, N)
+  for (int k = threadIdx.x; k < (N - start) * R; k += blockDim.x) {
+    const int jj = start + k / R, r = k % R;
+    double s = 0.0;
+    if (jj > start || a.initial)
+      for (int q = 0; q < nsl; ++q) s += __ldcg(&apart[((size_t)jj * nsl + q) * R + r]);
+    coef[(size_t)jj * R + r] = s;
+  }
+  __threadfence_block();
+  __syncthreads();
+  // c_start = a_start (initial: V_0^T u0) or 0; c_j = a_j + K_{j-1} c_{j-1}
+  for (int r = threadIdx.x; r < R; r += blockDim.x) cbuf[0][r] = coef[(size_t)start * R + r];
+  double* sK = reinterpret_cast<double*>(csw_smem);
+  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(double) * R * R));
+  const int t = threadIdx.x, rr = t >> 2, part = t & 3;
+  int cb = 0;
+  for (int j0 = start + 1; j0 < N; j0 += kchunk) {
+    const int nk = min(kchunk, N - j0);
+    __syncthreads();
+    const double* Kg = a.K + (size_t)(j0 - 1) * R * R;
+    for (int k = threadIdx.x; k < nk * R * R; k += blockDim.x) sK[k] = __ldcg(&Kg[k]);
+    __syncthreads();
+    for (int jj = 0; jj < nk; ++jj) {
+      const double* Kj = sK + (size_t)jj * R * R;
+      // rows rr = 0..R-1 of K c, four threads per row (interleaved columns),
+      // combined by shuffles in a fixed order
+      for (int rb = 0; rb < R; rb += CSW_THREADS / 4) {
+        const int r = rb + rr;
+        double acc = 0.0;
+        if (r < R)
+          for (int q = part; q < R; q += 4) acc = fma(Kj[r * R + q], cbuf[cb][q], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (r < R && part == 0) {
+          const double cv = coef[(size_t)(j0 + jj) * R + r] + acc;
+          cbuf[cb ^ 1][r] = cv;
+          coef[(size_t)(j0 + jj) * R + r] = cv;
         }
       }
+      cb ^= 1;
+      __syncthreads();
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 3: apply, norms and the bound.  grid (slices, N + 1, problems);
+// blockIdx.y - 1 = j, the interval whose end value u_{j+1} is formed
+// (j = start - 1: only the norm of the unchanged u_start).
+// ---------------------------------------------------------------------------
+template <typename TF>
+__global__ void __launch_bounds__(CSW_THREADS) k_csw_apply(const SweepArgs* __restrict__ args) {
+  __shared__ TF sc[CSW_MAXR];
+  __shared__ double red[CSW_THREADS / 32][2];
+  const SweepArgs& a = args[blockIdx.z];
+  const int j = (int)blockIdx.y - 1, sl = blockIdx.x;
+  const int N = a.N, n = a.n, R = a.R, nsl = a.nsl;
+  const int start = a.initial ? 0 : a.first;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  double* npart = a.cw + csw_npart(N, nsl, R);
+  if (j < N && sl < nsl && j >= start - 1) {
+    const int lo = sl * a.rows, hi = min(n, lo + a.rows), rows = hi - lo;
+    TF accd = TF(0), accu = TF(0);
+    if (j == start - 1) {
+      const double* us = a.u + (size_t)start * n + lo;
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        const TF v = (TF)us[i];
+        accu += v * v;
+      }
+      if (a.initial) accd = accu;          // Delta_0 = u0 - 0
+    } else {
+      const double* coef = a.cw + csw_coef(N, nsl, R) + (size_t)j * R;
+      const TF* S = static_cast<const TF*>(a.S) + (size_t)j * R;
+      for (int r = threadIdx.x; r < R; r += blockDim.x) sc[r] = S[r] * (TF)__ldcg(&coef[r]);
+      __syncthreads();
+      const TF* Uj = static_cast<const TF*>(a.U) + (size_t)j * R * n + lo;
+      const double* Fj = a.F + (size_t)j * n + lo;
+      double* un = a.u + (size_t)(j + 1) * n + lo;
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+        TF g = TF(0);
+        for (int r = 0; r < R; ++r) g += Uj[(size_t)r * n + i] * sc[r];
+        const double nv = Fj[i] + (double)g;
+        const double old = a.initial ? 0.0 : un[i];
+        un[i] = nv;
+        const TF d = (TF)(nv - old), u = (TF)nv;
+        accd += d * d;
+        accu += u * u;
+      }
+    }
+    accd = warp_sum<TF>(accd);
+    accu = warp_sum<TF>(accu);
+    if (lane == 0) { red[w][0] = (double)accd; red[w][1] = (double)accu; }
     __syncthreads();
     if (threadIdx.x < 2) {
       double s = 0.0;
-      for (int k = 0; k < nw; ++k) s += red[k][R + threadIdx.x];
-      const int o = (buf * SWEEP_MAXCS + crank) * (SWEEP_MAXR + 2) + R + threadIdx.x;
-      for (int q = 0; q < cs; ++q) rgath[q][o] = s;
+      for (int k = 0; k < nw; ++k) s += red[k][threadIdx.x];
+      npart[((size_t)(j + 1) * nsl + sl) * 2 + threadIdx.x] = s;
     }
-    cl.sync();
-    if (threadIdx.x < nv) {
-      double s = 0.0;
-      if (iv < N || threadIdx.x >= R)
-        for (int q = 0; q < cs; ++q) s += gath[buf][q][threadIdx.x];    // same order in every CTA
-      coef[threadIdx.x] = s;
-      if (threadIdx.x < R && iv < N)
-        scoef[threadIdx.x] = (stage ? sS[sb][threadIdx.x] : S[(size_t)iv * R + threadIdx.x]) * (TF)s;
-    }
-    __syncthreads();
-    if (crank == 0 && threadIdx.x == 0) {
-      if (iv > a.first || a.initial) a.du[iv] = sqrt(coef[R]);
-      a.unorm[iv] = sqrt(coef[R + 1]);
-    }
-    if (iv == N) break;
-    // ---- u^k_{iv+1} = F_iv + U_iv (S_iv * c) on this CTA's rows ------------
-    const TF* Ui = stage ? sU + (size_t)sb * R * per : U + (size_t)iv * R * n + lo;
-    const size_t ldu = stage ? (size_t)per : (size_t)n;
-    const double* Fi = stage ? sF + (size_t)sb * per : a.F + (size_t)iv * n + lo;
-    double* un = a.u + (size_t)(iv + 1) * n + lo;
-    acc_u_next = TF(0);
-    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-      TF g = TF(0);
-      for (int r = 0; r < R; ++r) g += Ui[(size_t)r * ldu + i] * scoef[r];
-      double nv_ = Fi[i] + (double)g;
-      double old = a.initial ? 0.0 : (stage ? sO[(size_t)sb * per + i] : un[i]);
-      const double dn = nv_ - old;
-      dsm[i] = dn;
-      if (kSep) dsT[i] = (TF)dn;
-      un[i] = nv_;
-      const TF nt = (TF)nv_;
-      acc_u_next += nt * nt;
-    }
-    buf ^= 1;
-    __syncthreads();
   }
-  // ---- bound recurrence and summary (one thread) ------------------------------
-  if (crank == 0 && threadIdx.x == 0) {
+  if (!csw_last_cta(&a.cnt[1], gridDim.x * gridDim.y)) return;
+  // ---- norms, bound recurrence and summary (this CTA only) -------------------
+  for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+    if (m >= start) {
+      double sd = 0.0, su = 0.0;
+      for (int q = 0; q < nsl; ++q) {
+        sd += __ldcg(&npart[((size_t)m * nsl + q) * 2 + 0]);
+        su += __ldcg(&npart[((size_t)m * nsl + q) * 2 + 1]);
+      }
+      a.du[m] = sqrt(sd);
+      a.unorm[m] = sqrt(su);
+    } else {
+      a.du[m] = 0.0;                        // u^k_m = u^{k-1}_m for m < k
+    }
+  }
+  __threadfence_block();
+  __syncthreads();
+  if (threadIdx.x == 0) {
     double B = 0.0, bmax = 0.0, umax = 0.0;
     for (int m = 0; m <= N; ++m) umax = fmax(umax, a.unorm[m]);
     if (a.bound) {
@@ -210,135 +233,158 @@ __device__ __forceinline__ void sweep_body(const SweepArgs& a) {
     a.summary[0] = bmax;
     a.summary[1] = umax;
   }
-  cp_async_wait<0>();
-  cl.sync();  // no CTA leaves while its shared memory may still be read
 }
 
-// One problem per launch.
-template <typename TF>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep(SweepArgs a) {
-  sweep_body<TF>(a);
-}
-
-// A batch of problems (same n, R, staging), one cluster each: args[cluster].
-template <typename TF>
-__global__ void __launch_bounds__(SWEEP_THREADS) k_sweep_batch(const SweepArgs* __restrict__ args) {
-  const SweepArgs a = args[blockIdx.x / cg::this_cluster().num_blocks()];
-  sweep_body<TF>(a);
-}
-
-lrp_status coarse_sweep(Ctx* c, const SweepArgs& a) {
-  if (a.R > SWEEP_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
-  if ((size_t)((a.n + SWEEP_MAXCS - 1) / SWEEP_MAXCS) * (a.f32 ? 12 : 8) > SWEEP_SMEM_MAX)
-    return set_err(c, LRP_EINVAL, "state dimension too large for the coarse sweep");
-  int cs = 16;
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  auto kern = a.f32 ? (void (*)(SweepArgs))k_sweep<float> : (void (*)(SweepArgs))k_sweep<double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  if (e) { cudaGetLastError(); cs = 8; }
-  // small problems: fewer CTAs per cluster
-  while (cs > 1 && (a.n + cs - 1) / cs < 64) cs >>= 1;
-  if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
-  while (cs < SWEEP_MAXCS && (size_t)((a.n + cs - 1) / cs) * (a.f32 ? 12 : 8) > SWEEP_SMEM_MAX) cs <<= 1;
-  const size_t tf = a.f32 ? 4 : 8;
-  auto dyn_for = [&](int csz, int stage) {
-    size_t per = (size_t)((a.n + csz - 1) / csz);
-    size_t b = sizeof(double) * per + (tf == 8 ? 0 : tf * (per + (per & 1)));
-    if (stage) b += 4 * (size_t)a.R * per * tf + 4 * per * sizeof(double);
-    return b;
-  };
-  SweepArgs aa = a;
-  aa.stage = dyn_for(cs, 1) <= SWEEP_STAGE_MAX ? 1 : 0;
-  size_t dyn = dyn_for(cs, aa.stage);
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_MAX);
-  if (e) return cuda_err(c, e, "sweep smem attribute");
-  cfg.gridDim = dim3(cs);
-  cfg.blockDim = dim3(SWEEP_THREADS);
-  cfg.dynamicSmemBytes = dyn;
-  cfg.stream = c->stream;
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cudaEvent_t ev = nullptr;
-  timer_begin(c, "sweep", &ev);
-  e = cudaLaunchKernelEx(&cfg, kern, aa);
-  timer_end(c, "sweep", ev);
-  if (e == cudaErrorInvalidValue || e == cudaErrorInvalidConfiguration) {
-    // retry with a portable cluster size
-    cudaGetLastError();
-    cs = std::min(cs, 8);
-    cfg.gridDim = dim3(cs);
-    aa.stage = dyn_for(cs, 1) <= SWEEP_STAGE_MAX ? 1 : 0;
-    cfg.dynamicSmemBytes = dyn_for(cs, aa.stage);
-    attr[0].val.clusterDim.x = cs;
-    e = cudaLaunchKernelEx(&cfg, kern, aa);
-  }
-  if (e) return cuda_err(c, e, "k_sweep launch");
-  return LRP_OK;
-}
-
-lrp_status coarse_sweep_batch(Ctx* c, const SweepArgs& proto, SweepArgs* d_args, int nprob,
-                              int* cs_out) {
+lrp_status coarse_sweep(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob) {
   if (nprob <= 0) return LRP_OK;
-  if (proto.R > SWEEP_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
-  auto kern = proto.f32 ? (void (*)(const SweepArgs*))k_sweep_batch<float>
-                        : (void (*)(const SweepArgs*))k_sweep_batch<double>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-  int cs = e ? 8 : 16;
-  if (e) cudaGetLastError();
-  // several problems share the GPU: fewer CTAs per problem when many run
-  while (cs > 1 && (size_t)nprob * cs > (size_t)c->num_sms) cs >>= 1;
-  while (cs > 1 && (proto.n + cs - 1) / cs < 64) cs >>= 1;
-  if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
-  const size_t tf = proto.f32 ? 4 : 8;
-  while (cs < SWEEP_MAXCS && (size_t)((proto.n + cs - 1) / cs) * (proto.f32 ? 12 : 8) > SWEEP_SMEM_MAX)
-    cs <<= 1;
-  const size_t per = (size_t)((proto.n + cs - 1) / cs);
-  size_t dyn = sizeof(double) * per + (tf == 8 ? 0 : tf * (per + (per & 1)));
-  const size_t dyn_stage = dyn + 4 * (size_t)proto.R * per * tf + 4 * per * sizeof(double);
-  const int stage = dyn_stage <= SWEEP_STAGE_MAX ? 1 : 0;
-  if (stage) dyn = dyn_stage;
-  if (stage != proto.stage) return set_err(c, LRP_EINVAL, "sweep batch staging mismatch");
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SWEEP_SMEM_MAX);
+  const int f32 = h[0].f32, N = h[0].N;
+  int nsl = 0;
+  for (int p = 0; p < nprob; ++p) {
+    const SweepArgs& a = h[p];
+    if (a.R > CSW_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
+    if (a.rows < 1 || a.rows > CSW_MAXROWS || a.nsl != (a.n + a.rows - 1) / a.rows)
+      return set_err(c, LRP_EINVAL, "sweep slice layout");
+    if (a.f32 != f32 || a.N != N) return set_err(c, LRP_EINVAL, "sweep batch mixes precisions or N");
+    if (!a.cw || !a.cnt || (N > 1 && !a.K)) return set_err(c, LRP_EINVAL, "sweep workspace missing");
+    nsl = std::max(nsl, a.nsl);
+  }
+  cudaError_t e = cudaMemcpyAsync(d_args, h, sizeof(SweepArgs) * nprob, cudaMemcpyHostToDevice,
+                                  c->stream);
+  if (e) return cuda_err(c, e, "sweep arguments");
+  auto kp = f32 ? (void (*)(const SweepArgs*))k_csw_project<float>
+                : (void (*)(const SweepArgs*))k_csw_project<double>;
+  auto ka = f32 ? (void (*)(const SweepArgs*))k_csw_apply<float>
+                : (void (*)(const SweepArgs*))k_csw_apply<double>;
+  e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, CSW_KBUF);
   if (e) return cuda_err(c, e, "sweep smem attribute");
-  cudaLaunchConfig_t cfg = {};
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cs;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  cfg.gridDim = dim3(nprob * cs);
-  cfg.blockDim = dim3(SWEEP_THREADS);
-  cfg.dynamicSmemBytes = dyn;
-  cfg.stream = c->stream;
-  if (cs_out) *cs_out = cs;
   cudaEvent_t ev = nullptr;
   timer_begin(c, "sweep", &ev);
-  e = cudaLaunchKernelEx(&cfg, kern, (const SweepArgs*)d_args);
+  kp<<<dim3(nsl, N, nprob), CSW_THREADS, CSW_KBUF, c->stream>>>(d_args);
+  ka<<<dim3(nsl, N + 1, nprob), CSW_THREADS, 0, c->stream>>>(d_args);
   timer_end(c, "sweep", ev);
-  if (e) return cuda_err(c, e, "k_sweep_batch launch");
+  e = cudaGetLastError();
+  if (e) return cuda_err(c, e, "coarse sweep launch");
+  c->launches += 1;   // two kernels; launch_count counts one more here
   return LRP_OK;
 }
 
-// Staging decision of a batched sweep (the caller stores it in every
-// problem's SweepArgs before copying them to the device).
-int coarse_sweep_batch_stage(Ctx* c, const SweepArgs& proto, int nprob) {
-  int cs = 16;
-  while (cs > 1 && (size_t)nprob * cs > (size_t)c->num_sms) cs >>= 1;
-  while (cs > 1 && (proto.n + cs - 1) / cs < 64) cs >>= 1;
-  if (c->p_sweep_cluster > 0) cs = c->p_sweep_cluster;
-  const size_t tf = proto.f32 ? 4 : 8;
-  while (cs < SWEEP_MAXCS && (size_t)((proto.n + cs - 1) / cs) * (proto.f32 ? 12 : 8) > SWEEP_SMEM_MAX)
-    cs <<= 1;
-  const size_t per = (size_t)((proto.n + cs - 1) / cs);
-  size_t dyn = sizeof(double) * per + (tf == 8 ? 0 : tf * (per + (per & 1)));
-  return dyn + 4 * (size_t)proto.R * per * tf + 4 * per * sizeof(double) <= SWEEP_STAGE_MAX ? 1 : 0;
+// ---------------------------------------------------------------------------
+// K_i = V_{i+1}^T U_i diag(S_i), i = 0..N-2, from the factors the coarse
+// apply uses (FP32 copies in the mixed mode), accumulated in FP64: partial
+// products over tiles of 64 rows, then a fixed-order sum over the tiles.
+// ---------------------------------------------------------------------------
+constexpr int CH_TILE = 64;
+constexpr int CH_MAXSL = 64;
+
+template <typename TF>
+__global__ void __launch_bounds__(256) k_chain_partial(const TF* __restrict__ U, const TF* __restrict__ V,
+                                                      int n, int R, int nslk, double* __restrict__ part) {
+  extern __shared__ double ch_sm[];
+  double* sV = ch_sm;                              // [R][CH_TILE + 1]
+  double* sU = sV + (size_t)R * (CH_TILE + 1);     // [R][CH_TILE + 1]
+  const int i = blockIdx.y, sl = blockIdx.x;
+  const TF* Vn = V + (size_t)(i + 1) * R * n;
+  const TF* Ui = U + (size_t)i * R * n;
+  constexpr int MAXO = CSW_MAXR * CSW_MAXR / 256;
+  double acc[MAXO];
+#pragma unroll
+  for (int k = 0; k < MAXO; ++k) acc[k] = 0.0;
+  const int nout = R * R;
+  for (int t0 = sl * CH_TILE; t0 < n; t0 += nslk * CH_TILE) {
+    const int rows = min(CH_TILE, n - t0);
+    __syncthreads();
+    for (int k = threadIdx.x; k < R * CH_TILE; k += blockDim.x) {
+      const int r = k / CH_TILE, x = k % CH_TILE;
+      sV[r * (CH_TILE + 1) + x] = x < rows ? (double)Vn[(size_t)r * n + t0 + x] : 0.0;
+      sU[r * (CH_TILE + 1) + x] = x < rows ? (double)Ui[(size_t)r * n + t0 + x] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < MAXO; ++k) {
+      const int o = threadIdx.x + k * 256;
+      if (o < nout) {
+        const double* vr = sV + (o / R) * (CH_TILE + 1);
+        const double* uq = sU + (o % R) * (CH_TILE + 1);
+        double s = acc[k];
+        for (int x = 0; x < CH_TILE; ++x) s = fma(vr[x], uq[x], s);
+        acc[k] = s;
+      }
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < MAXO; ++k) {
+    const int o = threadIdx.x + k * 256;
+    if (o < nout) part[((size_t)i * nslk + sl) * nout + o] = acc[k];
+  }
+}
+
+template <typename TF>
+__global__ void k_chain_reduce(const double* __restrict__ part, const TF* __restrict__ S, int R,
+                               int nslk, double* __restrict__ K) {
+  const int i = blockIdx.x, nout = R * R;
+  for (int o = threadIdx.x; o < nout; o += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < nslk; ++q) s += part[((size_t)i * nslk + q) * nout + o];
+    K[(size_t)i * nout + o] = s * (double)S[(size_t)i * R + (o % R)];
+  }
+}
+
+lrp_status coarse_chain(Ctx* c, Coarse* co) {
+  const int N = co->N, R = std::max(co->R, 1), n = co->op->n;
+  if (R > CSW_MAXR) return set_err(c, LRP_EINVAL, "rank above 64 is not supported by the sweep");
+  lrp_status s;
+  const size_t nk = (size_t)std::max(N - 1, 1) * R * R;
+  if ((s = dev_alloc(c, co->Kc, sizeof(double) * nk))) return s;
+  cudaMemsetAsync(co->Kc.ptr, 0, co->Kc.bytes, c->stream);
+  if (N < 2) return LRP_OK;
+  const int f32 = co->prec == LRP_PREC_MIXED;
+  const int nslk = std::min(CH_MAXSL, (n + CH_TILE - 1) / CH_TILE);
+  DevBuf part;
+  if ((s = dev_alloc(c, part, sizeof(double) * (size_t)(N - 1) * nslk * R * R))) return s;
+  const size_t smem = sizeof(double) * 2 * R * (CH_TILE + 1);
+  cudaError_t e;
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "lift", &ev);
+  if (f32) {
+    e = cudaFuncSetAttribute(k_chain_partial<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) {
+      k_chain_partial<float><<<dim3(nslk, N - 1), 256, smem, c->stream>>>(
+          co->U32.as<float>(), co->V32.as<float>(), n, R, nslk, part.as<double>());
+      k_chain_reduce<float><<<N - 1, 256, 0, c->stream>>>(part.as<double>(), co->S32.as<float>(), R,
+                                                         nslk, co->Kc.as<double>());
+    }
+  } else {
+    e = cudaFuncSetAttribute(k_chain_partial<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) {
+      k_chain_partial<double><<<dim3(nslk, N - 1), 256, smem, c->stream>>>(
+          co->U.as<double>(), co->V.as<double>(), n, R, nslk, part.as<double>());
+      k_chain_reduce<double><<<N - 1, 256, 0, c->stream>>>(part.as<double>(), co->S.as<double>(), R,
+                                                          nslk, co->Kc.as<double>());
+    }
+  }
+  timer_end(c, "lift", ev);
+  c->launches += 1;   // two kernels
+  if (!e) e = cudaGetLastError();
+  if (e) return cuda_err(c, e, "coarse chain matrices");
+  return LRP_OK;
+}
+
+lrp_status coarse_sweep_workspace(Ctx* c, Coarse* co, int rows) {
+  const int N = co->N, R = std::max(co->R, 1), nsl = (co->op->n + rows - 1) / rows;
+  const size_t need = sweep_ws_doubles(N, nsl, R) * sizeof(double);
+  lrp_status s;
+  if (!co->ws_cw.ptr || co->ws_cw.bytes < need) {
+    co->ws_cw.release();
+    if ((s = dev_alloc(c, co->ws_cw, need))) return s;
+  }
+  if (!co->ws_cnt.ptr) {
+    if ((s = dev_alloc(c, co->ws_cnt, 2 * sizeof(unsigned)))) return s;
+    cudaMemsetAsync(co->ws_cnt.ptr, 0, 2 * sizeof(unsigned), c->stream);
+  }
+  if (!co->ws_args.ptr) {
+    if ((s = dev_alloc(c, co->ws_args, sizeof(SweepArgs)))) return s;
+  }
+  return LRP_OK;
 }
 
 }  // namespace lrp

@@ -289,3 +289,23 @@ def test_coarse_checkpoint_roundtrip(ctx, tmp_path):
     a, b = co.info(), co2.info()
     np.testing.assert_array_equal(a["sigma"], b["sigma"])
     assert a["eps"] == b["eps"] and a["delta"] == b["delta"]
+
+
+def test_sweep_slicing_does_not_change_the_iterates(ctx, orc):
+    """The coarse sweep's partial sums per row slice are combined in a fixed
+    order; several slices per vector give the iterates of one slice to
+    rounding, and both match the oracle."""
+    P = W.heat1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    ref, _ = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=3)
+    try:
+        ctx.set_param("sweep_rows", 128)          # n = 255: two slices
+        u, _ = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=3)
+    finally:
+        ctx.set_param("sweep_rows", 0)
+    assert rel(u, ref) <= 1e-13
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, P.g, P.c, K=3)
+    assert rel(u, res.iterates[-1]) <= 1e-10
