@@ -83,8 +83,10 @@ long lrp_launch_count(lrp_ctx* ctx);
 /* Launch tuning (0 = automatic, the default):
  *   "sweep_rows":    rows of a vector per CTA in the coarse sweep (128..2048,
  *                    a power of two; default 1024);
- *   "tri_cluster":   CTAs per tridiagonal system for small batches (1, 2, 4);
+ *   "tri_cluster":   CTAs per tridiagonal system for small batches (1..8);
  *   "tri_chunk":     rows per chunk of the cluster tridiagonal kernel (8, 16);
+ *   "tri_warp":      1 disables the one-warp-per-CTA FP64 cluster kernel that
+ *                    small batches with n <= 4096 use by default;
  *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);
  *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
  *                    kernel (1..16, at most 512 threads per CTA);

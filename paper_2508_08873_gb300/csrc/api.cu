@@ -273,8 +273,11 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
     if (value != 0 && (value < 128 || value > 2048 || (value & (value - 1)))) return LRP_EINVAL;
     c->p_sweep_rows = value;
   } else if (k == "tri_cluster") {
-    if (value != 0 && value != 1 && value != 2 && value != 4) return LRP_EINVAL;
+    if (value < 0 || value > 8) return LRP_EINVAL;
     c->p_tri_cluster = value;
+  } else if (k == "tri_warp") {
+    if (value != 0 && value != 1) return LRP_EINVAL;
+    c->p_tri_warp = value;
   } else if (k == "tri_spt") {
     if (value != 0 && value != 1 && value != 2) return LRP_EINVAL;
     c->p_tri_spt = value;
@@ -300,6 +303,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_cluster") *value = c->p_tri_cluster;
   else if (k == "queue_cluster") *value = c->p_queue_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
+  else if (k == "tri_warp") *value = c->p_tri_warp;
   else if (k == "tri_chunk") *value = c->p_tri_chunk;
   else if (k == "tri_group") *value = c->p_tri_group;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
@@ -413,7 +417,7 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     auto fits = [&](int cc, int mm) {
       int P = (op->n + mm - 1) / mm;
       int Pc = (P + cc - 1) / cc;
-      return Pc >= 32 && Pc <= 256;
+      return Pc >= 32 && Pc <= 256 && Pc * cc <= 1024;
     };
     if (c->p_tri_cluster > 1) {
       C = c->p_tri_cluster;
@@ -434,13 +438,29 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       const bool small_batch = nsys * 2 <= c->num_sms;
       const bool must = (one_cta > 220 * 1024 || P1 > 512) && !(prec == 1 && op->n <= 4096);
       if (small_batch || must) {
-        const int cand[3][2] = {{4, 8}, {2, 16}, {4, 16}};
+        // block kernel (FP32, or the one-warp kernel disabled): measured on
+        // GB300 (n = 4095, FP64): 4-CTA clusters of 8-row chunks 1.26 ms per
+        // 256 steps, 8-CTA 1.10-1.26, 2-CTA 1.35, 3/5/6/7-CTA up to 1.7 (their
+        // clusters do not all fit at once)
+        const int cand[4][2] = {{4, 8}, {8, 8}, {2, 16}, {4, 16}};
         for (auto& cm : cand)
           if (fits(cm[0], cm[1])) { C = cm[0]; m = cm[1]; break; }
       }
       if (c->p_tri_chunk) m = c->p_tri_chunk;
       if (c->p_tri_spt) spt = c->p_tri_spt;
       if (C > 1 && !fits(C, m)) { C = 1; }
+    }
+    // FP64 small batches with n <= 4096: the one-warp-per-CTA cluster kernel
+    // (factors in registers, no block barrier; 32 chunks of 8 rows per CTA)
+    if (C > 1 && prec == 0 && c->p_tri_warp == 0 && c->p_tri_cluster == 0 && c->p_tri_chunk == 0 &&
+        c->p_tri_spt == 0) {
+      const int Cw = ((op->n + 7) / 8 + 31) / 32;
+      if (Cw >= 2 && Cw <= 16) {
+        ClPlan* cp = nullptr;
+        lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, 8, &cp, 1);
+        if (s) return s;
+        return tri_propagate_cluster(c, cp, M, nsys, prec, 1, in, out, src);
+      }
     }
     if (C > 1) {
       ClPlan* cp = nullptr;

@@ -49,7 +49,8 @@ struct Ctx {
   long launches = 0;       // kernels launched by this context (all families)
   // Tunable launch parameters (0 = automatic choice); see lrp_set_param.
   int p_sweep_rows = 0;      // rows per CTA slice of the coarse sweep (0: 1024)
-  int p_tri_cluster = 0;     // CTAs per tridiagonal system for small batches (1, 2, 4)
+  int p_tri_cluster = 0;     // CTAs per tridiagonal system for small batches (1..8)
+  int p_tri_warp = 0;        // one-warp cluster kernel for FP64 small batches (0 auto, 1 off)
   int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
@@ -88,6 +89,7 @@ struct TriPlan {
 struct ClPlan {
   double dt = 0.0;
   int adjoint = 0, C = 1, n = 0, m = 0, P = 0, Pc = 0, L = 0;
+  int warp = 0;   // factors laid out for the one-warp-per-CTA kernel (Pc = 32)
   size_t sz[4] = {0, 0, 0, 0};
   DevBuf b64[4], b32[4];
   DevBuf status;
@@ -197,8 +199,9 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
                          const PropIn& in, const PropOut& out, const PropSrc& src);
 
 // One system per cluster of C CTAs (small batches, n >= 2048).
+// warp = 1: the one-warp-per-CTA FP64 kernel (8-row chunks, 32 chunks per CTA)
 lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, int m,
-                                ClPlan** out);
+                                ClPlan** out, int warp = 0);
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src);
 

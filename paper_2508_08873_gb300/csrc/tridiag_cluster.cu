@@ -1,5 +1,5 @@
 // Tridiagonal backward-Euler propagation with one system spread over a
-// thread-block cluster of C CTAs (C = 2 or 4), for batches too small to fill
+// thread-block cluster of C CTAs (2 <= C <= 8), for batches too small to fill
 // the GPU with one CTA per system (the Parareal fine solves: one system per
 // coarse interval, FP64).
 //
@@ -29,7 +29,7 @@ namespace cg = cooperative_groups;
 
 namespace lrp {
 
-constexpr int CL_MAXC = 4;
+constexpr int CL_MAXC = 16;
 
 // index helpers for the per-CTA layouts
 __host__ __device__ __forceinline__ size_t cl_coef(int c, int k, int i, int tl, int m, int Pc) {
@@ -465,22 +465,193 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
 }
 
 // ---------------------------------------------------------------------------
+// One-warp variant: every CTA of the cluster is a single warp of 32 chunks
+// (Pc = 32), with its slice of the factorisation held in registers.  The local
+// interface system of a CTA is then solved by parallel cyclic reduction with
+// warp shuffles and the C x C super system by two warp sums, so a step needs
+// no block barrier at all: only the cluster barrier that publishes the four
+// values of every CTA.  (FP64, 8-row chunks.)
+// ---------------------------------------------------------------------------
+constexpr int CLW_MM = 8;
+constexpr int CLW_L = 5;    // PCR levels over the 31 local interface unknowns
+
+__global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  constexpr int MM = CLW_MM;
+  __shared__ double pubg[2][CL_MAXC][4];
+  __shared__ double* rpub[CL_MAXC];
+  const int C = a.C;
+  const int c = (int)cl.block_rank();
+  const int tl = threadIdx.x;
+  const int t = c * 32 + tl;
+  const int n = a.n;
+  const int r0 = t * MM;
+  const unsigned FULL = 0xffffffffu;
+  // ---- this thread's factors, in registers ---------------------------------
+  const double* gco = static_cast<const double*>(a.coef) + (size_t)c * 5 * MM * 32;
+  const double* gpc = static_cast<const double*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
+  const double* gsp = static_cast<const double*>(a.spk) + (size_t)c * 2 * 32;
+  const double* gsu = static_cast<const double*>(a.sup);
+  double fl[MM], fi[MM], fu[MM], fp[MM], fq[MM];
+#pragma unroll
+  for (int i = 0; i < MM; ++i) {
+    fl[i] = gco[(0 * MM + i) * 32 + tl];
+    fi[i] = gco[(1 * MM + i) * 32 + tl];
+    fu[i] = gco[(2 * MM + i) * 32 + tl];
+    fp[i] = gco[(3 * MM + i) * 32 + tl];
+    fq[i] = gco[(4 * MM + i) * 32 + tl];
+  }
+  double k1[CLW_L], k2[CLW_L];
+#pragma unroll
+  for (int l = 0; l < CLW_L; ++l) {
+    k1[l] = gpc[l * 32 + tl];
+    k2[l] = gpc[(CLW_L + l) * 32 + tl];
+  }
+  const double dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] : 0.0;
+  const double p2 = gsp[tl], q2 = gsp[32 + tl];
+  // super system: row `tl` (lanes < C) and the inverse rows of CTAs c-1, c
+  const int q = tl;
+  const double sa = q < C ? gsu[6 * q + 0] : 0.0;
+  const double sc1 = q < C ? gsu[6 * q + 1] : 0.0;
+  const double sc2 = q < C ? gsu[6 * q + 2] : 0.0;
+  const double* minv = gsu + 6 * CL_MAXC;
+  const double mc = q < C ? minv[c * CL_MAXC + q] : 0.0;
+  const double mcl = (q < C && c > 0) ? minv[(c - 1) * CL_MAXC + q] : 0.0;
+  if (tl < C) rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
+  __syncwarp();
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
+  const double dt = a.dt;
+  const int nclu = gridDim.x / C;
+  int pb = 0;
+  for (int sys = blockIdx.x / C; sys < a.nsys; sys += nclu) {
+    double x[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      const int r = r0 + i;
+      double v = 0.0;
+      if (r < n) {
+        if (a.in.gen)
+          v = gauss<double>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                            (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+        else if (a.in.x == nullptr)
+          v = 0.0;
+        else if (a.in.x_f64)
+          v = static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+        else
+          v = (double)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+      }
+      x[i] = v;
+    }
+    const double* csys = a.src.Q > 0
+        ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+    const double* gsys = (a.src.Q > 0 && a.src.map)
+        ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
+    for (int j = 0; j < a.M; ++j) {
+      if (csys) {
+        for (int qq = 0; qq < a.src.Q; ++qq) {
+          const double cq_ = dt * csys[(size_t)j * a.src.Q + qq];
+          const double* gq = gsys + (size_t)qq * n;
+#pragma unroll
+          for (int i = 0; i < MM; ++i)
+            if (r0 + i < n) x[i] += cq_ * gq[r0 + i];
+        }
+      }
+      // chunk interior: forward elimination and back substitution
+#pragma unroll
+      for (int i = 1; i < MM - 1; ++i) x[i] -= fl[i] * x[i - 1];
+      x[MM - 2] *= fi[MM - 2];
+#pragma unroll
+      for (int i = MM - 3; i >= 0; --i) x[i] = x[i] * fi[i] - fu[i] * x[i + 1];
+      // interface row of the chunk
+      double gnext = __shfl_down_sync(FULL, x[0], 1);
+      if (tl == 31) gnext = 0.0;
+      double r = x[MM - 1] - fl[MM - 1] * x[MM - 2] - fu[MM - 1] * gnext;
+      // local PCR over lanes 0..30 (lane 31 is the CTA's super unknown)
+#pragma unroll
+      for (int l = 0; l < CLW_L; ++l) {
+        const double rm = __shfl_up_sync(FULL, r, 1 << l);
+        const double rp = __shfl_down_sync(FULL, r, 1 << l);
+        if (tl < 31) r = r - k1[l] * rm - k2[l] * rp;
+      }
+      const double z0 = r * dv;              // 0 on lane 31 (dv = 0)
+      // publish: z0 of the first and last local unknown, the super row's r,
+      // the first row of the first chunk; lane q stores into CTA q
+      const double v0 = __shfl_sync(FULL, z0, 0);
+      const double v1 = __shfl_sync(FULL, z0, 30);
+      const double v2 = __shfl_sync(FULL, r, 31);
+      const double v3 = __shfl_sync(FULL, x[0], 0);
+      if (tl < C) {
+        double* dst = rpub[tl] + (pb * CL_MAXC + c) * 4;
+        dst[0] = v0; dst[1] = v1; dst[2] = v2; dst[3] = v3;
+      }
+      cl.sync();
+      // super system: lane q forms the right-hand side of unknown q; Y_c and
+      // Y_{c-1} are rows of the precomputed inverse applied by warp sums
+      double rhs = 0.0;
+      if (q < C) {
+        const double* pq = &pubg[pb][q][0];
+        rhs = pq[2] - sa * pq[1];
+        if (q + 1 < C) {
+          const double* pn = &pubg[pb][q + 1][0];
+          rhs -= sc2 * pn[3] + sc1 * pn[0];
+        }
+      }
+      double Yc = mc * rhs, Yl = mcl * rhs;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        Yc += __shfl_xor_sync(FULL, Yc, o);
+        Yl += __shfl_xor_sync(FULL, Yl, o);
+      }
+      const double y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
+      double yl = __shfl_up_sync(FULL, y, 1);
+      if (tl == 0) yl = Yl;
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - fp[i] * yl - fq[i] * y;
+      x[MM - 1] = y;
+      pb ^= 1;
+    }
+    const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      const int r = r0 + i;
+      if (r < n) {
+        if (a.out.y_f64)
+          static_cast<double*>(a.out.y)[oy + r] = x[i];
+        else
+          static_cast<float*>(a.out.y)[oy + r] = (float)x[i];
+      }
+    }
+  }
+  cl.sync();  // no CTA leaves while others may still store into its shared memory
+}
+
+// ---------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------
 lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, int m,
-                                ClPlan** out) {
+                                ClPlan** out, int warp) {
   const int CL_M = m;
   std::lock_guard<std::mutex> plan_lock(op->plan_mu);
   for (auto& p : op->cplans)
-    if (p->dt == dt && p->adjoint == adjoint && p->C == C && p->m == m) { *out = p.get(); return LRP_OK; }
+    if (p->dt == dt && p->adjoint == adjoint && p->C == C && p->m == m && p->warp == warp) {
+      *out = p.get();
+      return LRP_OK;
+    }
   auto pl = std::make_unique<ClPlan>();
   pl->dt = dt;
   pl->adjoint = adjoint;
   pl->C = C;
   pl->n = op->n;
   pl->m = CL_M;
+  pl->warp = warp;
   int P = (op->n + CL_M - 1) / CL_M;
   P = (P + C - 1) / C * C;
+  if (warp) {
+    // one warp per CTA: exactly 32 chunks of 8 rows per CTA (padding chunks
+    // are identity rows)
+    if (CL_M != CLW_MM || P > 32 * C) return set_err(c, LRP_EINVAL, "warp cluster plan out of range");
+    P = 32 * C;
+  }
   pl->P = P;
   pl->Pc = P / C;
   if (pl->Pc < 32 || pl->Pc > 256 || P > 1024)
@@ -558,6 +729,38 @@ static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   return LRP_OK;
 }
 
+static lrp_status launch_cl_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  const int C = pl->C;
+  cudaError_t e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(k_tri_cluster_w, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e) return cuda_err(c, e, "cluster size 16 not available");
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(32);
+  cfg.gridDim = dim3(C);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c->stream;
+  int maxc = 0;
+  e = cudaOccupancyMaxActiveClusters(&maxc, k_tri_cluster_w, &cfg);
+  if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
+  const int ncl = std::min(a.nsys, maxc);
+  cfg.gridDim = dim3(ncl * C);
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "propagate_f64", &ev);
+  e = cudaLaunchKernelEx(&cfg, k_tri_cluster_w, a);
+  timer_end(c, "propagate_f64", ev);
+  if (e) return cuda_err(c, e, "k_tri_cluster_w launch");
+  return LRP_OK;
+}
+
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (nsys <= 0) return LRP_OK;
@@ -578,6 +781,10 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
   a.lpcr = b[1].ptr;
   a.spk = b[2].ptr;
   a.sup = b[3].ptr;
+  if (pl->warp) {
+    if (f || spt != 1) return set_err(c, LRP_EINVAL, "warp cluster kernel is FP64, one system per thread");
+    return launch_cl_w(c, pl, a);
+  }
   if (pl->m == 8) {
     if (spt == 2) return f ? launch_cl<float, 8, 2>(c, pl, a) : launch_cl<double, 8, 2>(c, pl, a);
     return f ? launch_cl<float, 8, 1>(c, pl, a) : launch_cl<double, 8, 1>(c, pl, a);

@@ -309,3 +309,34 @@ def test_sweep_slicing_does_not_change_the_iterates(ctx, orc):
     oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
     res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, P.g, P.c, K=3)
     assert rel(u, res.iterates[-1]) <= 1e-10
+
+
+@pytest.mark.parametrize("n,nvec,Q", [(3000, 7, 2), (1025, 9, 0), (4096, 40, 1)])
+def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, Q):
+    """FP64 small batches with n <= 4096 run on the one-warp-per-CTA cluster
+    kernel (2..16 CTAs of 32 chunks); it agrees with the block kernel
+    (tri_warp = 1) to rounding and with the oracle, with and without a
+    source term, forward and adjoint."""
+    lo, di, up = W.adr1d_op(n)
+    dt, M = 1.0 / 16384, 9
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    rng = np.random.default_rng(n)
+    X = rng.standard_normal((nvec, n))
+    g = rng.standard_normal((Q, n)) if Q else None
+    c = rng.standard_normal((nvec, M, Q)) if Q else None
+    oop = orc.Tridiag(lo, di, up)
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    for adjoint in (False, True):
+        if adjoint and Q:
+            continue
+        got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c)
+        try:
+            ctx.set_param("tri_warp", 1)
+            blk = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c)
+        finally:
+            ctx.set_param("tri_warp", 0)
+        want = orc.propagate(oop, dt, M, X, adjoint=adjoint, g=g, cvals=c)
+        for v in range(nvec):
+            assert rel(got[v], want[v]) <= tol
+            assert rel(got[v], blk[v]) <= tol
