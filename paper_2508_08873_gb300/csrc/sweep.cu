@@ -34,6 +34,7 @@ constexpr int CSW_THREADS = 256;
 constexpr int CSW_MAXROWS = 2048;    // rows per slice (upper limit)
 constexpr int CSW_MAXR = 64;
 constexpr int CSW_KBUF = 32 * 1024;  // bytes of K staged per chunk of the recurrence
+constexpr int CSW_MAXN = 8192;       // intervals + 1 (norms staged in shared memory)
 
 // Workspace of one problem (doubles): a-partials [N][nsl][R], coefficients
 // [N][R], norm partials [N+1][nsl][2].
@@ -103,20 +104,24 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
   if (!csw_last_cta(&a.cnt[0], gridDim.x * gridDim.y)) return;
   // ---- the recurrence (this CTA only) ---------------------------------------
   double* coef = a.cw + csw_coef(N, nsl, R);
-  // a_j summed over the slices in a fixed order, for j in [start, N)
-  for (int k = threadIdx.x; k < (N - start) * R; k += blockDim.x) {
-    const int jj = start + k / R, r = k % R;
-    double s = 0.0;
+  // a_j is the fixed-order sum of its slice partials (summed where staged)
+  auto a_sum = [&](int jj, int r) {
+    double sum = 0.0;
     if (jj > start || a.initial)
-      for (int q = 0; q < nsl; ++q) s += __ldcg(&apart[((size_t)jj * nsl + q) * R + r]);
-    coef[(size_t)jj * R + r] = s;
+      for (int q = 0; q < nsl; ++q) sum += __ldcg(&apart[((size_t)jj * nsl + q) * R + r]);
+    return sum;
+  };
+  // c_start = a_start (initial: V_0^T u0) or 0; c_j = a_j + K_{j-1} c_{j-1}.
+  // K_{j-1} and a_j of a chunk of steps are staged in shared memory, so the
+  // sequential steps touch no global memory.
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const double c0 = a_sum(start, r);
+    cbuf[0][r] = c0;
+    coef[(size_t)start * R + r] = c0;
   }
-  __threadfence_block();
-  __syncthreads();
-  // c_start = a_start (initial: V_0^T u0) or 0; c_j = a_j + K_{j-1} c_{j-1}
-  for (int r = threadIdx.x; r < R; r += blockDim.x) cbuf[0][r] = coef[(size_t)start * R + r];
   double* sK = reinterpret_cast<double*>(csw_smem);
-  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(double) * R * R));
+  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(double) * (R * R + R)));
+  double* sA = sK + (size_t)kchunk * R * R;
   const int t = threadIdx.x, rr = t >> 2, part = t & 3;
   int cb = 0;
   for (int j0 = start + 1; j0 < N; j0 += kchunk) {
@@ -124,6 +129,7 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
     __syncthreads();
     const double* Kg = a.K + (size_t)(j0 - 1) * R * R;
     for (int k = threadIdx.x; k < nk * R * R; k += blockDim.x) sK[k] = __ldcg(&Kg[k]);
+    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) sA[k] = a_sum(j0 + k / R, k % R);
     __syncthreads();
     for (int jj = 0; jj < nk; ++jj) {
       const double* Kj = sK + (size_t)jj * R * R;
@@ -137,14 +143,15 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (r < R && part == 0) {
-          const double cv = coef[(size_t)(j0 + jj) * R + r] + acc;
+          const double cv = sA[(size_t)jj * R + r] + acc;
           cbuf[cb ^ 1][r] = cv;
-          coef[(size_t)(j0 + jj) * R + r] = cv;
+          sA[(size_t)jj * R + r] = cv;
         }
       }
       cb ^= 1;
       __syncthreads();
     }
+    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) coef[(size_t)j0 * R + k] = sA[k];
   }
 }
 
@@ -204,28 +211,43 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_apply(const SweepArgs* __re
   }
   if (!csw_last_cta(&a.cnt[1], gridDim.x * gridDim.y)) return;
   // ---- norms, bound recurrence and summary (this CTA only) -------------------
+  extern __shared__ double csw_nrm[];          // [2][N + 1]: ||Delta_m||, ||u_m||
+  double* sdu = csw_nrm;
+  double* sun = csw_nrm + (N + 1);
+  double umax_t = 0.0;
   for (int m = threadIdx.x; m <= N; m += blockDim.x) {
+    double dm = 0.0, um;
     if (m >= start) {
       double sd = 0.0, su = 0.0;
       for (int q = 0; q < nsl; ++q) {
         sd += __ldcg(&npart[((size_t)m * nsl + q) * 2 + 0]);
         su += __ldcg(&npart[((size_t)m * nsl + q) * 2 + 1]);
       }
-      a.du[m] = sqrt(sd);
-      a.unorm[m] = sqrt(su);
+      dm = sqrt(sd);
+      um = sqrt(su);
+      a.unorm[m] = um;
     } else {
-      a.du[m] = 0.0;                        // u^k_m = u^{k-1}_m for m < k
+      um = __ldcg(&a.unorm[m]);              // u^k_m = u^{k-1}_m for m < k
     }
+    a.du[m] = dm;
+    sdu[m] = dm;
+    sun[m] = um;
+    umax_t = fmax(umax_t, um);
   }
-  __threadfence_block();
+  umax_t = fmax(umax_t, __shfl_xor_sync(0xffffffffu, umax_t, 16));
+  umax_t = fmax(umax_t, __shfl_xor_sync(0xffffffffu, umax_t, 8));
+  umax_t = fmax(umax_t, __shfl_xor_sync(0xffffffffu, umax_t, 4));
+  umax_t = fmax(umax_t, __shfl_xor_sync(0xffffffffu, umax_t, 2));
+  umax_t = fmax(umax_t, __shfl_xor_sync(0xffffffffu, umax_t, 1));
+  if (lane == 0) red[w][1] = umax_t;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double B = 0.0, bmax = 0.0, umax = 0.0;
-    for (int m = 0; m <= N; ++m) umax = fmax(umax, a.unorm[m]);
+    double umax = 0.0, B = 0.0, bmax = 0.0;
+    for (int k = 0; k < nw; ++k) umax = fmax(umax, red[k][1]);
     if (a.bound) {
       a.bound[0] = 0.0;
       for (int m = 1; m <= N; ++m) {
-        B = a.delta * B + a.eps * a.du[m - 1];
+        B = a.delta * B + a.eps * sdu[m - 1];
         a.bound[m] = B;
         bmax = fmax(bmax, B);
       }
@@ -255,12 +277,15 @@ lrp_status coarse_sweep(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob
                 : (void (*)(const SweepArgs*))k_csw_project<double>;
   auto ka = f32 ? (void (*)(const SweepArgs*))k_csw_apply<float>
                 : (void (*)(const SweepArgs*))k_csw_apply<double>;
+  if (N + 1 > CSW_MAXN) return set_err(c, LRP_EINVAL, "too many intervals for the coarse sweep");
   e = cudaFuncSetAttribute(kp, cudaFuncAttributeMaxDynamicSharedMemorySize, CSW_KBUF);
+  if (!e) e = cudaFuncSetAttribute(ka, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)(sizeof(double) * 2 * CSW_MAXN));
   if (e) return cuda_err(c, e, "sweep smem attribute");
   cudaEvent_t ev = nullptr;
   timer_begin(c, "sweep", &ev);
   kp<<<dim3(nsl, N, nprob), CSW_THREADS, CSW_KBUF, c->stream>>>(d_args);
-  ka<<<dim3(nsl, N + 1, nprob), CSW_THREADS, 0, c->stream>>>(d_args);
+  ka<<<dim3(nsl, N + 1, nprob), CSW_THREADS, sizeof(double) * 2 * (N + 1), c->stream>>>(d_args);
   timer_end(c, "sweep", ev);
   e = cudaGetLastError();
   if (e) return cuda_err(c, e, "coarse sweep launch");

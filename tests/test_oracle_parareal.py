@@ -3,6 +3,7 @@
 representation for invariant projections (Theorem 2 and its self-adjoint
 corollary), the cost count (Eq. (num_F_eval)) and Remark (rem:affine_g_n)."""
 import math
+import pathlib
 
 import numpy as np
 import pytest
@@ -151,3 +152,35 @@ def test_tol_stopping(orc, heat_small):
     if res.k_done > 1:
         assert res.bounds[-2].max() > 1e-9 * np.max(np.linalg.norm(res.iterates[-2], axis=1))
     assert orc.rel_err(res.iterates[-1], ref) <= 1e-9 * 1.0001
+
+
+def _exp4_table():
+    rows = []
+    path = pathlib.Path(__file__).parent / "golden" / "exp4_fine_evaluations.txt"
+    for line in path.read_text().splitlines():
+        if line.strip() and not line.startswith("#"):
+            rows.append([int(v) for v in line.split()])
+    return rows
+
+
+def test_fine_evaluation_count_matches_experiment4_table(orc):
+    """The oracle's evaluation counters (sketch propagations of the build,
+    plus b_n and one fine solve per Parareal iteration) reproduce the counts
+    printed in the paper's Experiment 4 table, K_{F,n} + 1 of Eq. num_F_eval,
+    for every (p, r) and k = 0..4.  Tiny full-rank problem, so no sketch
+    direction is deflated."""
+    n, N, M, dt = 12, 5, 3, 0.05
+    lo = np.full(n, -1.0); di = np.full(n, 2.5); up = np.full(n, -1.2)
+    op = orc.Tridiag(lo, di, up)
+    g = np.linspace(0.5, 1.5, n)[None, :]
+    c = np.ones((N * M, 1))
+    u0 = np.sin(np.arange(n))
+    for p, r, setup, *per_k in _exp4_table():
+        co = orc.build_coarse(op, dt, M, N, r, p, 0)
+        build = co.intervals[0].fine_evals
+        assert all(iv.fine_evals == build for iv in co.intervals)
+        assert build + 1 == setup                       # sketches + b_n
+        for k, want in enumerate(per_k):
+            res = orc.parareal(op, dt, M, N, co, u0, g, c, K=k)
+            assert res.k_done == k
+            assert build + res.fine_evals + 1 == want, (p, r, k)
