@@ -91,7 +91,10 @@ long lrp_launch_count(lrp_ctx* ctx);
  *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
  *                    kernel (1..16, at most 512 threads per CTA);
  *   "queue_cluster": CTAs per cluster of the batched 2D work queue (1..16,
- *                    a power of two).
+ *                    a power of two);
+ *   "krylov_cluster": CTAs per cluster of the 2D propagator (1..16, a power
+ *                    of two; default: the most CTAs in flight whose Krylov
+ *                    workspaces fit in 96 MB).
  * Results do not depend on these settings beyond rounding. */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);
 lrp_status lrp_get_param(lrp_ctx* ctx, const char* name, int* value);

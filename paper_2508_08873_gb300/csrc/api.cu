@@ -287,6 +287,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
     c->p_tri_group = value;
+  } else if (k == "krylov_cluster") {
+    if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
+    c->p_krylov_cluster = value;
   } else if (k == "queue_cluster") {
     if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
     c->p_queue_cluster = value;
@@ -302,6 +305,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   if (k == "sweep_rows") *value = c->p_sweep_rows;
   else if (k == "tri_cluster") *value = c->p_tri_cluster;
   else if (k == "queue_cluster") *value = c->p_queue_cluster;
+  else if (k == "krylov_cluster") *value = c->p_krylov_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
   else if (k == "tri_warp") *value = c->p_tri_warp;
   else if (k == "tri_chunk") *value = c->p_tri_chunk;

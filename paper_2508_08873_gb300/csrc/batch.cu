@@ -82,7 +82,7 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     Operator* op = ops[p];
     if ((s = stencil_plan(c, op, dt, 0, &pf[p]))) return s;
     if ((s = stencil_plan(c, op, dt, 1, &pa[p]))) return s;
-    maxn = std::max(maxn, op->n);
+    maxn = std::max(maxn, op->n + 2 * op->mx);
     bicg |= op->symmetric ? 0 : 1;
     co[p] = std::make_unique<lrp_coarse>();
     Coarse* q = co[p].get();
@@ -146,10 +146,10 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     a.iters = reinterpret_cast<unsigned long long*>(d_stat.ptr);
     a.status = reinterpret_cast<int*>(static_cast<char*>(d_stat.ptr) + 8);
     KryArgs b = a;
-    a.B = f32 ? pf[p]->b32.ptr : pf[p]->b64.ptr;
+    a.B = stencil_B(pf[p], op, f32);
     a.in.gen = 1; a.in.seed = seed; a.in.ncol = ell; a.in.interval0 = 0;
     a.out.y = sc[p].Y.ptr; a.out.y_f64 = !f32; a.out.ldy = op->n;
-    b.B = f32 ? pa[p]->b32.ptr : pa[p]->b64.ptr;
+    b.B = stencil_B(pa[p], op, f32);
     b.in.x = sc[p].Y.ptr; b.in.x_f64 = !f32; b.in.ldx = op->n;
     b.out.y = sc[p].Z.ptr; b.out.y_f64 = !f32; b.out.ldy = op->n;
     hf[p] = a;
@@ -263,7 +263,7 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
         cos[p]->op->kind != 1 || cos[p]->R != cos[0]->R || cos[p]->prec != cos[0]->prec)
       return set_err(c, LRP_EINVAL, "batched solves need 2D coarse handles with equal N, M, R, precision");
     bicg |= cos[p]->op->symmetric ? 0 : 1;
-    maxn = std::max(maxn, cos[p]->op->n);
+    maxn = std::max(maxn, cos[p]->op->n + 2 * cos[p]->op->mx);
   }
   const int K = std::min(K_max, N);
   lrp_status s;
@@ -302,7 +302,7 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
     a.mx = op->mx; a.my = op->my; a.n = op->n; a.M = M; a.nsys = N;
     a.bicg = op->symmetric ? 0 : 1;
     a.dt = q->dt; a.rtol = op->rtol64; a.max_iter = op->max_iter; a.nvec = (int)nvec;
-    a.B = pf[p]->b64.ptr;
+    a.B = stencil_B(pf[p], op, 0);
     a.in.x = q->ws_u.ptr; a.in.x_f64 = 1; a.in.ldx = op->n;
     a.out.y = q->ws_F.ptr; a.out.y_f64 = 1; a.out.ldy = op->n;
     a.iters = reinterpret_cast<unsigned long long*>(d_stat.ptr);

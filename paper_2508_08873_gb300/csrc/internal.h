@@ -52,6 +52,7 @@ struct Ctx {
   int p_tri_cluster = 0;     // CTAs per tridiagonal system for small batches (1..8)
   int p_tri_warp = 0;        // one-warp cluster kernel for FP64 small batches (0 auto, 1 off)
   int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
+  int p_krylov_cluster = 0;  // CTAs per cluster of the 2D propagator (1..16)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
@@ -95,8 +96,9 @@ struct ClPlan {
   DevBuf status;
 };
 
-// B = I + dt*A (or its transpose) of a 5-point operator: [6][n] = centre,
-// west, east, south, north couplings and 1/centre, FP64 and FP32 copies.
+// B = I + dt*A (or its transpose) of a 5-point operator: [6][n + 2 mx] =
+// centre, west, east, south, north couplings and 1/centre, each with a zero
+// pad of mx entries on both sides; FP64 and FP32 copies.
 struct StencilPlan {
   double dt = 0.0;
   int adjoint = 0;
@@ -218,8 +220,9 @@ struct KryArgs {
   int mx, my, n, M, nsys, bicg;
   double dt, rtol;
   int max_iter;
-  const void* B;            // [6][n]: c, w, e, s, n, dinv (type T)
-  void* ws;                 // per cluster slot: nvec * n values of type T
+  const void* B;            // [6][n + 2 mx] from element 0 of array 0 (after the pad):
+                            // c, w, e, s, n, dinv (type T), zero pads of mx per side
+  void* ws;                 // per cluster slot: nvec padded vectors of n + 2 mx values
   int nvec;
   PropIn in;
   PropOut out;
@@ -229,6 +232,8 @@ struct KryArgs {
 };
 lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out);
 size_t krylov_queue_nvec(int bicg);
+// Device pointer of the stencil coefficients for KryArgs::B (past the pad).
+const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec);
 int krylov_queue_clusters(Ctx* c, int prec, int cs);
 lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const int* d_items,
                                int nitems, unsigned int* d_counter, void* ws, size_t ws_stride,

@@ -30,12 +30,15 @@ constexpr int KRY_MAXCS = 16;
 constexpr int KRY_MAXNV = 4;
 
 // B = I + dt*A (adjoint: its transpose) with the couplings that leave the
-// grid removed; dinv = 1 / diag.
+// grid removed; dinv = 1 / diag.  Each of the 6 arrays has a zero pad of mx
+// entries on both sides (row stride n + 2 mx), so that the stencil reads its
+// four neighbours without bounds tests: couplings across the boundary are 0.
 __global__ void k_stencil_plan(int mx, int my, double dt, int adj, const double* __restrict__ C,
                                const double* __restrict__ W, const double* __restrict__ E,
                                const double* __restrict__ S, const double* __restrict__ N,
                                double* __restrict__ b64, float* __restrict__ b32) {
   const int n = mx * my;
+  const size_t ld = (size_t)n + 2 * mx;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
   int ix = p % mx, iy = p / mx;
@@ -53,70 +56,92 @@ __global__ void k_stencil_plan(int mx, int my, double dt, int adj, const double*
   }
   double v[6] = {c, w, e, s, nn, 1.0 / c};
   for (int k = 0; k < 6; ++k) {
-    b64[(size_t)k * n + p] = v[k];
-    b32[(size_t)k * n + p] = (float)v[k];
+    b64[(size_t)k * ld + mx + p] = v[k];
+    b32[(size_t)k * ld + mx + p] = (float)v[k];
   }
 }
 
-
-
+// Cluster-wide reductions: per-warp sums in the working precision, per-CTA
+// sums in FP64 pushed into every CTA's shared memory before the cluster
+// barrier (remote stores), then one fixed-order sum over the CTAs per value.
 struct ClRed {
-  double part[2][KRY_MAXNV];
   double red[KRY_THREADS / 32][KRY_MAXNV];
-  double gath[KRY_MAXCS][KRY_MAXNV];
-  const double* rpart[KRY_MAXCS];   // part[][] of every CTA of the cluster (DSMEM), mapped once
+  double part[2][KRY_MAXCS][KRY_MAXNV];
+  double tot[KRY_MAXNV];
+  double* rpart[KRY_MAXCS];   // part[][][] of every CTA of the cluster (DSMEM), mapped once
 };
 
-// Map the partial-sum arrays of all CTAs of the cluster once per kernel.
 __device__ __forceinline__ void cl_map(cg::cluster_group& cl, ClRed& sh) {
   for (int q = threadIdx.x; q < (int)cl.num_blocks(); q += blockDim.x)
-    sh.rpart[q] = cl.map_shared_rank(&sh.part[0][0], q);
+    sh.rpart[q] = cl.map_shared_rank(&sh.part[0][0][0], q);
   __syncthreads();
 }
 
-// Cluster-wide sum of nv values (deterministic order); also a cluster barrier.
-template <int NV>
-__device__ __forceinline__ void cl_sum(cg::cluster_group& cl, double (&v)[NV], ClRed& sh, int& buf) {
+// Sum of NV values over the cluster (deterministic order); also a cluster
+// barrier.  v: per-thread partials in T on entry, cluster totals on exit.
+template <typename T, int NV>
+__device__ __forceinline__ void cl_sum(cg::cluster_group& cl, const T (&v)[NV], double (&out)[NV],
+                                       ClRed& sh, int& buf) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-  for (int i = 0; i < NV; ++i) v[i] = warp_sum(v[i]);
-  if (lane == 0)
-#pragma unroll
-    for (int i = 0; i < NV; ++i) sh.red[w][i] = v[i];
-  __syncthreads();
-  if (threadIdx.x < NV) {
-    double s = 0.0;
-    for (int k = 0; k < nw; ++k) s += sh.red[k][threadIdx.x];
-    sh.part[buf][threadIdx.x] = s;
-  }
-  cl.sync();
-  const int cs = (int)cl.num_blocks();
-  for (int k = threadIdx.x; k < cs * NV; k += blockDim.x)
-    sh.gath[k / NV][k % NV] = sh.rpart[k / NV][buf * KRY_MAXNV + k % NV];
-  __syncthreads();
+  const int cs = (int)cl.num_blocks(), crank = (int)cl.block_rank();
 #pragma unroll
   for (int i = 0; i < NV; ++i) {
-    double s = 0.0;
-    for (int q = 0; q < cs; ++q) s += sh.gath[q][i];
-    v[i] = s;
+    const T s = warp_sum<T>(v[i]);
+    if (lane == 0) sh.red[w][i] = (double)s;
   }
+  __syncthreads();
+  if (threadIdx.x < NV * cs) {
+    const int i = threadIdx.x % NV, q = threadIdx.x / NV;
+    double s = 0.0;
+    for (int k = 0; k < nw; ++k) s += sh.red[k][i];
+    sh.rpart[q][(buf * KRY_MAXCS + crank) * KRY_MAXNV + i] = s;
+  }
+  cl.sync();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int q = 0; q < cs; ++q) s += sh.part[buf][q][threadIdx.x];
+    sh.tot[threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < NV; ++i) out[i] = sh.tot[i];
   buf ^= 1;
 }
 
+// (B v)_k for the padded layouts: no bounds tests, boundary couplings are 0
+// and the pads of v are 0.
 template <typename T>
-__device__ __forceinline__ T stencil_apply(const T* __restrict__ B, int n, int mx, int k,
+__device__ __forceinline__ T stencil_apply(const T* __restrict__ B, size_t ldb, int mx, int k,
                                            const T* __restrict__ v) {
-  int ix = k % mx;
   T acc = B[k] * v[k];
-  if (ix > 0) acc += B[(size_t)n + k] * v[k - 1];
-  if (ix < mx - 1) acc += B[(size_t)2 * n + k] * v[k + 1];
-  if (k >= mx) acc += B[(size_t)3 * n + k] * v[k - mx];
-  if (k + mx < n) acc += B[(size_t)4 * n + k] * v[k + mx];
+  acc += B[ldb + k] * v[k - 1];
+  acc += B[2 * ldb + k] * v[k + 1];
+  acc += B[3 * ldb + k] * v[k - mx];
+  acc += B[4 * ldb + k] * v[k + mx];
   return acc;
 }
 
+// Loop over this CTA's points k in [k0, k1), KRY_UNROLL points per thread and
+// round: the loads of all of them are issued before any of their arithmetic
+// and stores (the passes only store to vectors they do not load at other
+// points), so each thread keeps several L2 requests in flight.
+constexpr int KRY_UNROLL = 4;
+template <typename Regs, typename Load, typename Comp>
+__device__ __forceinline__ void for_points(int k0, int k1, Load load, Comp comp) {
+  const int bd = blockDim.x;
+  int kb = k0 + threadIdx.x;
+  for (; kb + (KRY_UNROLL - 1) * bd < k1; kb += KRY_UNROLL * bd) {
+    Regs g0 = load(kb), g1 = load(kb + bd), g2 = load(kb + 2 * bd), g3 = load(kb + 3 * bd);
+    comp(kb, g0);
+    comp(kb + bd, g1);
+    comp(kb + 2 * bd, g2);
+    comp(kb + 3 * bd, g3);
+  }
+  for (; kb < k1; kb += bd) comp(kb, load(kb));
+}
+
 // One system (vector `sys` of the problem described by `a`) on this cluster,
-// using the workspace `ws` (a.nvec vectors of a.n values).
+// using the workspace `ws` (a.nvec padded vectors of n + 2 mx values).
 template <typename T>
 __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_group& cl, ClRed& sh,
                                               int& buf, int sys, T* ws,
@@ -124,177 +149,221 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   const int cs = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   const int n = a.n, mx = a.mx;
+  const size_t ldv = (size_t)n + 2 * mx;
+  const size_t ldb = ldv;
   const int rows_per = (a.my + cs - 1) / cs;
   const int k0 = min(a.n, crank * rows_per * mx), k1 = min(a.n, (crank + 1) * rows_per * mx);
-  const T* B = static_cast<const T*>(a.B);
-  const T* Bd = B + (size_t)5 * n;                         // 1 / diag
-  T* x = ws;
-  T* r = ws + (size_t)n;
-  T* p = ws + (size_t)2 * n;          // CG: p; BiCG: p
-  T* q = ws + (size_t)3 * n;          // CG: q = B p; BiCG: v
-  T* rh = ws + (size_t)4 * n;         // BiCG: r-hat
-  T* ph = ws + (size_t)5 * n;         // BiCG: D^-1 p
-  T* sv = ws + (size_t)6 * n;         // BiCG: s
-  T* shh = ws + (size_t)7 * n;        // BiCG: D^-1 s
-  T* tv = ws + (size_t)8 * n;         // BiCG: t = B D^-1 s
+  const T* __restrict__ B = static_cast<const T*>(a.B);
+  const T* __restrict__ Bd = B + 5 * ldb;             // 1 / diag (0 on the pads)
+  auto vec = [&](int v) { return ws + (size_t)v * ldv + mx; };
+  T* x = vec(0);
+  T* r = vec(1);
+  T* p = vec(2);            // CG: p; BiCG: p
+  T* q = vec(3);            // CG: q = B p; BiCG: v
+  T* rh = vec(4);           // BiCG: r-hat
+  T* ph = vec(5);           // BiCG: D^-1 p
+  T* sv = vec(6);           // BiCG: s
+  T* shh = vec(7);          // BiCG: D^-1 s
+  T* tv = vec(8);           // BiCG: t = B D^-1 s
   const T dt = (T)a.dt;
-    // ---- initial vector ----------------------------------------------------
+  struct St { T c0, c1, c2, c3, c4, v0, v1, v2, v3, v4; };   // stencil operands
+  auto st_load = [&](int k, const T* v) {
+    return St{B[k], B[ldb + k], B[2 * ldb + k], B[3 * ldb + k], B[4 * ldb + k],
+              v[k], v[k - 1], v[k + 1], v[k - mx], v[k + mx]};
+  };
+  auto st_eval = [](const St& g) {
+    T acc = g.c0 * g.v0;
+    acc += g.c1 * g.v1;
+    acc += g.c2 * g.v2;
+    acc += g.c3 * g.v3;
+    acc += g.c4 * g.v4;
+    return acc;
+  };
+  // zero pads of every workspace vector (the stencil reads them)
+  for (int e = crank * blockDim.x + threadIdx.x; e < a.nvec * 2 * mx; e += cs * blockDim.x) {
+    const int v = e / (2 * mx), o = e % (2 * mx);
+    T* base = ws + (size_t)v * ldv;
+    base[o < mx ? o : n + o] = T(0);       // [0, mx) and [n + mx, n + 2 mx)
+  }
+  // ---- initial vector ------------------------------------------------------
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    T v = T(0);
+    if (a.in.gen)
+      v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                   (uint32_t)(sys % a.in.ncol), (uint32_t)k);
+    else if (a.in.x == nullptr)
+      v = T(0);
+    else if (a.in.x_f64)
+      v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
+    else
+      v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
+    x[k] = v;
+  }
+  cl.sync();
+  const double* csys = a.src.Q > 0
+      ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+  const double* gsys = (a.src.Q > 0 && a.src.map)
+      ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
+  for (int j = 0; j < a.M; ++j) {
+    // ---- right-hand side d = x + dt f, residual r = d - B x --------------
+    T red3t[3] = {T(0), T(0), T(0)};    // d.d, r.r, rho
     for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      T v = T(0);
-      if (a.in.gen)
-        v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
-                     (uint32_t)(sys % a.in.ncol), (uint32_t)k);
-      else if (a.in.x == nullptr)
-        v = T(0);
-      else if (a.in.x_f64)
-        v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
-      else
-        v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
-      x[k] = v;
-    }
-    cl.sync();
-    const double* csys = a.src.Q > 0
-        ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
-    const double* gsys = (a.src.Q > 0 && a.src.map)
-        ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
-    for (int j = 0; j < a.M; ++j) {
-      // ---- right-hand side d = x + dt f, residual r = d - B x --------------
-      T red3t[3] = {T(0), T(0), T(0)};    // d.d, r.r, rho (per-thread partials in T)
-      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-        T d = x[k];
-        if (csys)
-          for (int qq = 0; qq < a.src.Q; ++qq)
-            d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
-        T rk = d - stencil_apply(B, n, mx, k, x);
-        r[k] = rk;
-        red3t[0] += d * d;
-        red3t[1] += rk * rk;
-        if (a.bicg) {
-          rh[k] = rk;
-          p[k] = rk;
-          red3t[2] += rk * rk;
-        } else {
-          T z = rk * Bd[k];
-          p[k] = z;
-          red3t[2] += rk * z;
-        }
-      }
-      double red3[3] = {(double)red3t[0], (double)red3t[1], (double)red3t[2]};
-      cl_sum<3>(cl, red3, sh, buf);
-      const double tol2 = a.rtol * a.rtol * red3[0];
-      double rr = red3[1], rho = red3[2];
-      int it = 0;
-      if (!a.bicg) {
-        // ---- preconditioned conjugate gradients ----------------------------
-        while (rr > tol2 && it < a.max_iter) {
-          T pqt = T(0);
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            T qk = stencil_apply(B, n, mx, k, p);
-            q[k] = qk;
-            pqt += p[k] * qk;
-          }
-          double pq[1] = {(double)pqt};
-          cl_sum<1>(cl, pq, sh, buf);
-          if (!(pq[0] > 0.0)) { my_status |= 2; break; }
-          const T alpha = (T)(rho / pq[0]);
-          T rz0 = T(0), rz1 = T(0);
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            x[k] += alpha * p[k];
-            T rk = r[k] - alpha * q[k];
-            r[k] = rk;
-            rz0 += rk * (rk * Bd[k]);
-            rz1 += rk * rk;
-          }
-          double rz[2] = {(double)rz0, (double)rz1};
-          cl_sum<2>(cl, rz, sh, buf);
-          const T beta = (T)(rz[0] / rho);
-          rho = rz[0];
-          rr = rz[1];
-          ++it;
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) p[k] = r[k] * Bd[k] + beta * p[k];
-          cl.sync();
-        }
+      T d = x[k];
+      if (csys)
+        for (int qq = 0; qq < a.src.Q; ++qq)
+          d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
+      T rk = d - stencil_apply(B, ldb, mx, k, x);
+      r[k] = rk;
+      red3t[0] += d * d;
+      red3t[1] += rk * rk;
+      if (a.bicg) {
+        rh[k] = rk;
+        p[k] = rk;
+        red3t[2] += rk * rk;
       } else {
-        // ---- BiCGStab with Jacobi right preconditioning ---------------------
-        double rho_prev = rho;
-        T alpha = T(1), omega = T(1);
-        bool first = true;
-        while (rr > tol2 && it < a.max_iter) {
-          if (!first) {
-            const T beta = (T)((rho / rho_prev) * ((double)alpha / (double)omega));
-            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
-              p[k] = r[k] + beta * (p[k] - omega * q[k]);
-          }
-          first = false;
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) ph[k] = p[k] * Bd[k];
-          cl.sync();
-          T rvt = T(0);
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            T vk = stencil_apply(B, n, mx, k, ph);
-            q[k] = vk;
-            rvt += rh[k] * vk;
-          }
-          double rv[1] = {(double)rvt};
-          cl_sum<1>(cl, rv, sh, buf);
-          if (rv[0] == 0.0 || !isfinite(rv[0])) { my_status |= 2; break; }
-          alpha = (T)(rho / rv[0]);
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            T s = r[k] - alpha * q[k];
-            sv[k] = s;
-            shh[k] = s * Bd[k];
-          }
-          cl.sync();
-          T ts0 = T(0), ts1 = T(0);
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            T t = stencil_apply(B, n, mx, k, shh);
-            tv[k] = t;
-            ts0 += t * sv[k];
-            ts1 += t * t;
-          }
-          double ts[2] = {(double)ts0, (double)ts1};
-          cl_sum<2>(cl, ts, sh, buf);
-          omega = ts[1] > 0.0 ? (T)(ts[0] / ts[1]) : T(0);
-          T rr0 = T(0), rr1 = T(0);
-          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-            x[k] += alpha * ph[k] + omega * shh[k];
-            T rk = sv[k] - omega * tv[k];
-            r[k] = rk;
-            rr0 += rh[k] * rk;
-            rr1 += rk * rk;
-          }
-          double rr2[2] = {(double)rr0, (double)rr1};
-          cl_sum<2>(cl, rr2, sh, buf);
-          rho_prev = rho;
-          rho = rr2[0];
-          rr = rr2[1];
-          ++it;
-          if (rr > tol2 && (omega == T(0) || rho == 0.0)) { my_status |= 2; break; }
-        }
+        const T z = rk * Bd[k];
+        p[k] = z;
+        red3t[2] += rk * z;
       }
-      if (rr > tol2) my_status |= 1;
-      my_iters += it;
-      cl.sync();
     }
-    // ---- store ---------------------------------------------------------------
-    const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
-    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
-      if (a.out.y_f64)
-        static_cast<double*>(a.out.y)[oy + k] = (double)x[k];
-      else
-        static_cast<float*>(a.out.y)[oy + k] = (float)x[k];
+    double red3[3];
+    cl_sum<T, 3>(cl, red3t, red3, sh, buf);
+    const double tol2 = a.rtol * a.rtol * red3[0];
+    double rr = red3[1], rho = red3[2];
+    int it = 0;
+    if (!a.bicg) {
+      // ---- preconditioned conjugate gradients ------------------------------
+      while (rr > tol2 && it < a.max_iter) {
+        T pqt[1] = {T(0)};
+        for_points<St>(k0, k1, [&](int k) { return st_load(k, p); },
+                       [&](int k, const St& g) {
+                         const T qk = st_eval(g);
+                         q[k] = qk;
+                         pqt[0] += g.v0 * qk;
+                       });
+        double pq[1];
+        cl_sum<T, 1>(cl, pqt, pq, sh, buf);
+        if (!(pq[0] > 0.0)) { my_status |= 2; break; }
+        const T alpha = (T)(rho / pq[0]);
+        T rz[2] = {T(0), T(0)};
+        struct Up { T x, p, r, q, d; };
+        for_points<Up>(k0, k1,
+                       [&](int k) { return Up{x[k], p[k], r[k], q[k], Bd[k]}; },
+                       [&](int k, const Up& g) {
+                         x[k] = g.x + alpha * g.p;
+                         const T rk = g.r - alpha * g.q;
+                         r[k] = rk;
+                         rz[0] += rk * (rk * g.d);
+                         rz[1] += rk * rk;
+                       });
+        double rzd[2];
+        cl_sum<T, 2>(cl, rz, rzd, sh, buf);
+        const T beta = (T)(rzd[0] / rho);
+        rho = rzd[0];
+        rr = rzd[1];
+        ++it;
+        struct Pu { T r, d, p; };
+        for_points<Pu>(k0, k1, [&](int k) { return Pu{r[k], Bd[k], p[k]}; },
+                       [&](int k, const Pu& g) { p[k] = g.r * g.d + beta * g.p; });
+        cl.sync();
+      }
+    } else {
+      // ---- BiCGStab with Jacobi right preconditioning ---------------------
+      double rho_prev = rho;
+      T alpha = T(1), omega = T(1);
+      bool first = true;
+      while (rr > tol2 && it < a.max_iter) {
+        struct Pb { T r, p, q, d; };
+        if (!first) {
+          const T beta = (T)((rho / rho_prev) * ((double)alpha / (double)omega));
+          for_points<Pb>(k0, k1, [&](int k) { return Pb{r[k], p[k], q[k], Bd[k]}; },
+                         [&](int k, const Pb& g) {
+                           const T pk = g.r + beta * (g.p - omega * g.q);
+                           p[k] = pk;
+                           ph[k] = pk * g.d;
+                         });
+        } else {
+          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) ph[k] = p[k] * Bd[k];
+        }
+        first = false;
+        cl.sync();
+        T rvt[1] = {T(0)};
+        struct Sv { St s; T rh; };
+        for_points<Sv>(k0, k1, [&](int k) { return Sv{st_load(k, ph), rh[k]}; },
+                       [&](int k, const Sv& g) {
+                         const T vk = st_eval(g.s);
+                         q[k] = vk;
+                         rvt[0] += g.rh * vk;
+                       });
+        double rv[1];
+        cl_sum<T, 1>(cl, rvt, rv, sh, buf);
+        if (rv[0] == 0.0 || !isfinite(rv[0])) { my_status |= 2; break; }
+        alpha = (T)(rho / rv[0]);
+        struct Ss { T r, q, d; };
+        for_points<Ss>(k0, k1, [&](int k) { return Ss{r[k], q[k], Bd[k]}; },
+                       [&](int k, const Ss& g) {
+                         const T s = g.r - alpha * g.q;
+                         sv[k] = s;
+                         shh[k] = s * g.d;
+                       });
+        cl.sync();
+        T tst[2] = {T(0), T(0)};
+        struct Tv { St s; T sv; };
+        for_points<Tv>(k0, k1, [&](int k) { return Tv{st_load(k, shh), sv[k]}; },
+                       [&](int k, const Tv& g) {
+                         const T t = st_eval(g.s);
+                         tv[k] = t;
+                         tst[0] += t * g.sv;
+                         tst[1] += t * t;
+                       });
+        double ts[2];
+        cl_sum<T, 2>(cl, tst, ts, sh, buf);
+        omega = ts[1] > 0.0 ? (T)(ts[0] / ts[1]) : T(0);
+        T rrt[2] = {T(0), T(0)};
+        struct Xu { T x, ph, shh, sv, tv, rh; };
+        for_points<Xu>(k0, k1,
+                       [&](int k) { return Xu{x[k], ph[k], shh[k], sv[k], tv[k], rh[k]}; },
+                       [&](int k, const Xu& g) {
+                         x[k] = g.x + alpha * g.ph + omega * g.shh;
+                         const T rk = g.sv - omega * g.tv;
+                         r[k] = rk;
+                         rrt[0] += g.rh * rk;
+                         rrt[1] += rk * rk;
+                       });
+        double rr2[2];
+        cl_sum<T, 2>(cl, rrt, rr2, sh, buf);
+        rho_prev = rho;
+        rho = rr2[0];
+        rr = rr2[1];
+        ++it;
+        if (rr > tol2 && (omega == T(0) || rho == 0.0)) { my_status |= 2; break; }
+      }
     }
+    if (rr > tol2) my_status |= 1;
+    my_iters += it;
     cl.sync();
+  }
+  // ---- store -----------------------------------------------------------------
+  const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    if (a.out.y_f64)
+      static_cast<double*>(a.out.y)[oy + k] = (double)x[k];
+    else
+      static_cast<float*>(a.out.y)[oy + k] = (float)x[k];
+  }
+  cl.sync();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
+__global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   __shared__ ClRed sh;
   const int cs = (int)cl.num_blocks();
   const int crank = (int)cl.block_rank();
   const int slot = blockIdx.x / cs, nslots = gridDim.x / cs;
-  T* ws = static_cast<T*>(a.ws) + (size_t)slot * a.nvec * a.n;
+  T* ws = static_cast<T*>(a.ws) + (size_t)slot * a.nvec * ((size_t)a.n + 2 * a.mx);
   cl_map(cl, sh);
+  cl.sync();   // every CTA runs before remote stores into its shared memory
   int buf = 0;
   unsigned long long my_iters = 0;
   int my_status = 0;
@@ -311,7 +380,7 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov(KryArgs a) {
 // cluster takes the next item from a global counter (rank 0 draws it and
 // the other CTAs read it through distributed shared memory).
 template <typename T>
-__global__ void __launch_bounds__(KRY_THREADS) k_krylov_queue(const KryArgs* __restrict__ probs,
+__global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov_queue(const KryArgs* __restrict__ probs,
                                                                const int* __restrict__ items,
                                                                int nitems,
                                                                unsigned int* __restrict__ counter,
@@ -324,6 +393,7 @@ __global__ void __launch_bounds__(KRY_THREADS) k_krylov_queue(const KryArgs* __r
   const int slot = blockIdx.x / cs;
   T* ws = reinterpret_cast<T*>(static_cast<char*>(ws_all) + (size_t)slot * ws_stride);
   cl_map(cl, sh);
+  cl.sync();   // every CTA runs before remote stores into its shared memory
   int buf = 0;
   unsigned long long my_iters = 0;
   int my_status = 0;
@@ -355,8 +425,11 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
   pl->dt = dt;
   pl->adjoint = adjoint;
   lrp_status s;
-  if ((s = dev_alloc(op->ctx, pl->b64, sizeof(double) * 6 * (size_t)op->n))) return s;
-  if ((s = dev_alloc(op->ctx, pl->b32, sizeof(float) * 6 * (size_t)op->n))) return s;
+  const size_t ld = (size_t)op->n + 2 * op->mx;
+  if ((s = dev_alloc(op->ctx, pl->b64, sizeof(double) * 6 * ld))) return s;
+  if ((s = dev_alloc(op->ctx, pl->b32, sizeof(float) * 6 * ld))) return s;
+  cudaMemsetAsync(pl->b64.ptr, 0, pl->b64.bytes, c->stream);
+  cudaMemsetAsync(pl->b32.ptr, 0, pl->b32.bytes, c->stream);
   k_stencil_plan<<<(op->n + 255) / 256, 256, 0, c->stream>>>(
       op->mx, op->my, dt, adjoint, op->a64[0].as<double>(), op->a64[1].as<double>(),
       op->a64[2].as<double>(), op->a64[3].as<double>(), op->a64[4].as<double>(),
@@ -382,30 +455,47 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   StencilPlan* plan = nullptr;
   lrp_status s = stencil_plan(c, op, dt, adjoint, &plan);
   if (s) return s;
-  const int cs = cluster_size_for(op->mx, op->my);
   const int bicg = op->symmetric ? 0 : 1;
-  const int nvec = bicg ? 9 : 4;
+  const int nvec = (int)krylov_queue_nvec(bicg);
   auto kern = prec == 0 ? (void (*)(KryArgs))k_krylov<double> : (void (*)(KryArgs))k_krylov<float>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e) return cuda_err(c, e, "krylov cluster attribute");
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = cs;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   cfg.blockDim = dim3(KRY_THREADS);
-  cfg.gridDim = dim3(cs);
   cfg.stream = c->stream;
-  int max_clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&max_clusters, kern, &cfg);
-  if (e || max_clusters < 1) { cudaGetLastError(); max_clusters = std::max(1, c->num_sms / cs); }
-  const int nclusters = std::min(nsys, max_clusters);
+  // cluster size: the largest (fewest points per CTA, shortest iteration) among
+  // those that keep the most CTAs in flight for this batch; clusters of 16 fit
+  // once per GPC, smaller ones pack the GPCs more densely
+  // The workspaces of the clusters in flight stay within 96 MB so that the
+  // Krylov vectors remain L2-resident (129 MB L2).
+  const int cs_max = cluster_size_for(op->mx, op->my);
+  const size_t es_ = prec == 0 ? 8 : 4;
+  const size_t ws_one = (size_t)(bicg ? 9 : 4) * ((size_t)op->n + 2 * op->mx) * es_;
+  const int ws_cap = (int)std::max<size_t>(1, ((size_t)96 << 20) / ws_one);
+  int cs = cs_max, nclusters = 1;
+  long best = -1;
+  for (int cc = cs_max; cc >= 1 && cc >= cs_max / 4; cc /= 2) {
+    if (c->p_krylov_cluster > 0 && cc != std::min(c->p_krylov_cluster, cs_max)) continue;
+    if ((op->my + cc - 1) / cc * (cc - 1) >= op->my && cc > 1) continue;   // every CTA owns rows
+    attr[0].val.clusterDim.x = cc;
+    cfg.gridDim = dim3(cc);
+    int maxc = 0;
+    e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+    if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / cc); }
+    const int ncl = std::min(std::min(nsys, maxc), ws_cap);
+    const long ctas = (long)ncl * cc;
+    if (ctas > best) { best = ctas; cs = cc; nclusters = ncl; }
+  }
+  attr[0].val.clusterDim.x = cs;
   cfg.gridDim = dim3(nclusters * cs);
   const size_t es = prec == 0 ? 8 : 4;
-  const size_t need = (size_t)nclusters * nvec * op->n * es;
+  const size_t need = (size_t)nclusters * nvec * ((size_t)op->n + 2 * op->mx) * es;
   if (op->kws.bytes < need)
     if ((s = dev_alloc(c, op->kws, need))) return s;
   if (!op->kstat.ptr)
@@ -421,7 +511,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   a.dt = dt;
   a.rtol = prec == 0 ? op->rtol64 : op->rtol32;
   a.max_iter = op->max_iter;
-  a.B = prec == 0 ? plan->b64.ptr : plan->b32.ptr;
+  a.B = stencil_B(plan, op, prec);
   a.ws = op->kws.ptr;
   a.nvec = nvec;
   a.in = in;
@@ -448,6 +538,11 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
 
 // ---- work-queue launches (batched problems of uneven size) -----------------
 size_t krylov_queue_nvec(int bicg) { return bicg ? 9 : 4; }
+
+const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec) {
+  return prec == 0 ? (const void*)(pl->b64.as<double>() + op->mx)
+                   : (const void*)(pl->b32.as<float>() + op->mx);
+}
 
 int krylov_queue_clusters(Ctx* c, int prec, int cs) {
   auto kern = prec == 0 ? (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<double>
