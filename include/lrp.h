@@ -86,7 +86,8 @@ long lrp_launch_count(lrp_ctx* ctx);
  *   "tri_cluster":   CTAs per tridiagonal system for small batches (1..8);
  *   "tri_chunk":     rows per chunk of the cluster tridiagonal kernel (8, 16);
  *   "tri_warp":      1 disables the one-warp-per-CTA FP64 cluster kernel that
- *                    small batches with n <= 4096 use by default;
+ *                    small batches with n <= 4096 use by default, 2 uses it
+ *                    for every FP64 batch with n <= 4096;
  *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);
  *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
  *                    kernel (1..16, at most 512 threads per CTA);

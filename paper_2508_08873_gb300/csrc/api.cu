@@ -276,7 +276,7 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
     if (value < 0 || value > 8) return LRP_EINVAL;
     c->p_tri_cluster = value;
   } else if (k == "tri_warp") {
-    if (value != 0 && value != 1) return LRP_EINVAL;
+    if (value < 0 || value > 2) return LRP_EINVAL;
     c->p_tri_warp = value;
   } else if (k == "tri_spt") {
     if (value != 0 && value != 1 && value != 2) return LRP_EINVAL;
@@ -455,10 +455,15 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       if (C > 1 && !fits(C, m)) { C = 1; }
     }
     // FP64 small batches with n <= 4096: the one-warp-per-CTA cluster kernel
-    // (factors in registers, no block barrier; 32 chunks of 8 rows per CTA)
-    if (C > 1 && prec == 0 && c->p_tri_warp == 0 && c->p_tri_cluster == 0 && c->p_tri_chunk == 0 &&
-        c->p_tri_spt == 0) {
-      const int Cw = ((op->n + 7) / 8 + 31) / 32;
+    // (factors in registers, no block barrier; 32 chunks of 8 rows per CTA).
+    // Its step is shorter, but it executes more FP64 instructions per row than
+    // the block kernel: measured on GB300 (n = 4095, 256 steps) it is faster
+    // up to about 57 systems (0.79 ms at 4, 0.96 at 38, 1.27 at 57) and slower
+    // beyond (1.39 ms against 1.26-1.29 at 64).
+    const int Cw = ((op->n + 7) / 8 + 31) / 32;
+    const bool warp_ok = (long)nsys * Cw <= 57L * 16;
+    if (((C > 1 && c->p_tri_warp == 0 && warp_ok) || c->p_tri_warp == 2) && prec == 0 &&
+        c->p_tri_cluster == 0 && c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       if (Cw >= 2 && Cw <= 16) {
         ClPlan* cp = nullptr;
         lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, 8, &cp, 1);
