@@ -51,9 +51,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the cpu_baseline sample")
-    ap.add_argument("--mode", default="solve", choices=["solve", "serve"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "serve", "krylov"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
-                         "coarse solvers (p50/p99 latency per offered rate)")
+                         "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
+                         "of the 2D Krylov fine propagator (HBM GB/s fraction)")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="arrival window per rate (at most 2000 requests)")
@@ -244,11 +245,83 @@ def run_serve(args):
     srv.close()
 
 
+HBM_PEAK_GBS_FALLBACK = 6800.0
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of the GB300s (generated file),
+    else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+            if k in d:
+                v = d[k]
+                return float(v["value"] if isinstance(v, dict) else v), "measured"
+    except Exception:
+        pass
+    return HBM_PEAK_GBS_FALLBACK, "fallback"
+
+
+def run_krylov(args):
+    """The 2D fine propagator's bandwidth (the 'HBM GB/s frac' part of the
+    metric): diff2d (511^2, kappa checkerboard, dt = 1/4096), Jacobi-PCG per
+    backward-Euler step, FP32 sketch propagations (rtol 1e-6, 64 vectors, one
+    step) and FP64 fine propagations (rtol 1e-12, 16 vectors, one step).
+    Algorithmic traffic of a CG iteration: x, r, p read and written (6 words
+    per grid point); achieved = that x iterations / kernel time."""
+    import torch
+    from paper_2508_08873_gb300 import api, workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
+    P = W.diff2d()
+    op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+    op.set_krylov(1e-12, 1e-6, 20000)
+    peak, peak_src = hbm_peak_gbs()
+    rng = np.random.default_rng(0)
+    out = {}
+    for prec, nsys in (("mixed", 64), ("f64", 16)):
+        X = rng.standard_normal((nsys, P.n))
+        for _ in range(max(1, args.warmup)):
+            api.propagate(ctx, op, P.dt, 1, X, prec=prec)
+        fam = "propagate_f64" if prec == "f64" else "propagate_f32"
+        it0 = op.krylov_iterations()
+        ctx.set_kernel_timing(True)
+        ctx.reset_kernel_time()
+        for _ in range(args.steps):
+            api.propagate(ctx, op, P.dt, 1, X, prec=prec)
+        nl, ms = ctx.kernel_time(fam)
+        ctx.set_kernel_timing(False)
+        its = op.krylov_iterations() - it0
+        es = 8 if prec == "f64" else 4
+        gbs = its * 6 * P.n * es / (ms * 1e-3) / 1e9
+        out[prec] = {"systems": nsys, "cg_iterations_per_step": its / (nsys * args.steps),
+                     "us_per_iteration_and_system": ms * 1e3 / its, "achieved_gbs": gbs,
+                     "frac": gbs / peak, "launches": nl}
+    line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
+            "value": out["mixed"]["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
+            "higher_is_better": True, "mode": "krylov", "steps": args.steps,
+            "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "diff2d 511^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, "
+                                   "one backward-Euler step per system"},
+            "roofline": {"bound": "hbm", "achieved": out["mixed"]["achieved_gbs"], "peak": peak,
+                         "unit": "GB/s", "frac": out["mixed"]["achieved_gbs"] / peak,
+                         "peak_source": peak_src, "traffic": None,
+                         "note": "Krylov vectors are L2-resident; algorithmic bytes (x, r, p "
+                                 "read + written per CG iteration) over kernel time"},
+            "precisions": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.mode == "serve":
         run_serve(args)
+        return
+    if args.mode == "krylov":
+        run_krylov(args)
         return
     from paper_2508_08873_gb300 import workloads as W
     P = W.adr1d()
@@ -331,6 +404,19 @@ def main():
     a1.record(stream)
     torch.cuda.synchronize()
     amort = 1000.0 * args.steps / a0.elapsed_time(a1)
+    # comparison: classical Parareal (one backward-Euler coarse step per
+    # interval), same fine solver, stopped on its increment at the same tol
+    cls_out = torch.empty_like(out_d)
+    api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, u0_d, K=P.N, tol=TOL, out=cls_out)
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    _, cls_info = api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, u0_d, K=P.N, tol=TOL,
+                                               out=cls_out)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    cls_ms = c0.elapsed_time(c1)
     # ---- e2e: host buffers through the C ABI ---------------------------------
     u0_h = torch.tensor(P.u0, dtype=torch.float64).pin_memory()
     out_h = torch.empty((P.N + 1, P.n), dtype=torch.float64).pin_memory()
@@ -346,11 +432,12 @@ def main():
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
     # ---- accuracy of the timed solve vs the oracle's sequential fine solution -
-    err = None
+    err = cls_err = None
     if rank == 0:
         from oracle import oracle as orc
         ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0)
         err = orc.rel_err(out_d.cpu().numpy(), ref)
+        cls_err = orc.rel_err(cls_out.cpu().numpy(), ref)
     # ---- roofline of the dominant kernel ---------------------------------------
     fam = max(("propagate_f64", "propagate_f32"), key=lambda f: kern[f][1])
     nl, tot = kern[fam]
@@ -389,6 +476,11 @@ def main():
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
                 "iterations": k_list[-1], "rel_err_vs_oracle": err,
                 "amortised_solves_per_s": amort * world,
+                "classical_parareal": {"iterations": cls_info["k_done"],
+                                       "solves_per_s": 1000.0 / cls_ms,
+                                       "rel_err_vs_oracle": cls_err,
+                                       "note": "one backward-Euler coarse step per interval, "
+                                               "stopped on its increment at the same tol"},
                 "e2e": {"value": e2e_val, "unit": UNIT,
                         "h2d_bytes_per_step": 8 * (P.n + 3 * P.n),
                         "d2h_bytes_per_step": 8 * (P.N + 1) * P.n},

@@ -93,6 +93,8 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    kernel (1..16, at most 512 threads per CTA);
  *   "queue_cluster": CTAs per cluster of the batched 2D work queue (1..16,
  *                    a power of two);
+ *   "orth_cluster":  CTAs per interval of the shared-memory CGS2 kernel (a power
+ *                    of two up to 16; -1 selects the one-CTA kernel);
  *   "krylov_cluster": CTAs per cluster of the 2D propagator (1..16, a power
  *                    of two; default: the most CTAs in flight whose Krylov
  *                    workspaces fit in 96 MB).
@@ -243,6 +245,23 @@ lrp_status lrp_parareal_solve(lrp_ctx* ctx, const lrp_coarse* co, const double* 
                               const double* g, const double* c, int K_max, double tol,
                               double* u_out, double* bound_out, int* k_done,
                               lrp_solve_stats* stats);
+
+/* Classical Parareal for comparison (the method of the dashed curves in the
+ * paper's numerical experiments, Sec. 4): Eq. def_Parareal with the coarse
+ * solver G_i = one backward-Euler step of size M*dt over interval i, the
+ * source sampled at the interval's end t_{i+1}; the same fine solver as
+ * lrp_parareal_solve (M steps of size dt).  No coarse factors are built.
+ * Stops after K_max iterations (clamped to N) or, when tol > 0, at the first
+ * k >= 1 with max_n ||u^k_n - u^{k-1}_n|| <= tol * max_n ||u^k_n|| (the
+ * classical coarse solver has no a posteriori bound).  u0 (n), g (Q x n),
+ * c ((N*M) x Q) host or device; u_out ((N+1) x n) the last iterate;
+ * incr_out (K_max, may be NULL): the relative increment of every iteration.
+ * Workspace is allocated per call on the context.  Returns LRP_ENOTCONV when
+ * tol > 0 was not met (outputs valid). */
+lrp_status lrp_parareal_solve_classical(lrp_ctx* ctx, const lrp_operator* op, double dt, int M,
+                                        int N, const double* u0, int Q, const double* g,
+                                        const double* c, int K_max, double tol, double* u_out,
+                                        double* incr_out, int* k_done, lrp_solve_stats* stats);
 
 /* The sequential fine solution u_{i+1} = F_i u_i (Sec. 2), (N+1) x n, with the
  * same propagator: the fixed point Parareal converges to. */

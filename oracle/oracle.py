@@ -463,3 +463,53 @@ def rel_err(iterate: np.ndarray, ref: np.ndarray) -> float:
     normalised)."""
     return float(np.max(np.linalg.norm(iterate - ref, axis=1)) /
                  np.max(np.linalg.norm(ref, axis=1)))
+
+
+# ----------------------------------------------------------------------------
+# Classical Parareal: a single backward-Euler step as coarse solver (the
+# comparison method of Sec. 4, dashed lines of Experiments 1-4)
+# ----------------------------------------------------------------------------
+def coarse_be(op, dt, M, v, i, g=None, c=None) -> np.ndarray:
+    """G_i v for the classical coarse solver: one backward-Euler step of size
+    M*dt over interval i, the source sampled at the interval's end t_{i+1}
+    (the step end, as in the fine solver)."""
+    if g is None:
+        return propagate(op, M * dt, 1, v)
+    return propagate(op, M * dt, 1, v, g=g, cvals=interval_cvals(c, i, M)[-1:])
+
+
+def parareal_classical(op, dt, M, N, u0, g=None, c=None, K: Optional[int] = None,
+                       tol: Optional[float] = None) -> PararealResult:
+    """Parareal (Eq. def_Parareal, literal form) with G_i = coarse_be.
+
+    Stops after K iterations (clamped to N), or at the first k >= 1 with
+    max_n ||u^k_n - u^{k-1}_n|| <= tol * max_n ||u^k_n|| (the classical
+    coarse solver has no a posteriori bound of Eq. apost_bound).  `bounds`
+    holds the increments ||u^k_n - u^{k-1}_n|| per iteration."""
+    u0 = _f64(u0)
+    n = u0.shape[0]
+    Kmax = N if K is None else min(int(K), N)
+    u = np.zeros((N + 1, n))
+    u[0] = u0
+    for i in range(N):
+        u[i + 1] = coarse_be(op, dt, M, u[i], i, g, c)
+    iterates = [u]
+    incs = []
+    k, evals = 0, 0
+    while k < Kmax:
+        prev = iterates[-1]
+        Fprev = np.stack([fine_solve(op, dt, M, prev[i], i, g, c) for i in range(N)])
+        evals += 1
+        new = np.zeros_like(prev)
+        new[0] = u0
+        for i in range(N):
+            new[i + 1] = Fprev[i] + coarse_be(op, dt, M, new[i], i, g, c) \
+                - coarse_be(op, dt, M, prev[i], i, g, c)
+        k += 1
+        iterates.append(new)
+        du = np.linalg.norm(new - prev, axis=1)
+        incs.append(du)
+        if tol is not None and tol > 0:
+            if np.max(du) <= tol * np.max(np.linalg.norm(new, axis=1)):
+                break
+    return PararealResult(iterates, incs, np.zeros((N, n)), k, evals)

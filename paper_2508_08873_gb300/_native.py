@@ -102,6 +102,8 @@ SIGNATURES = [
     ("lrp_parareal_solve", _I, [_P, _P, _P, _I, _P, _P, _I, _D, _P, _P, _PI,
                                 ctypes.POINTER(SolveStats)]),
     ("lrp_fine_solution", _I, [_P, _P, _D, _I, _I, _P, _I, _P, _P, _P]),
+    ("lrp_parareal_solve_classical", _I, [_P, _P, _D, _I, _I, _P, _I, _P, _P, _I, _D, _P, _P, _PI,
+                                          ctypes.POINTER(SolveStats)]),
     ("lrp_build_coarse_batch", _I, [_P, _I, _P, _D, _I, _I, _I, _I, _U64, _I, _P]),
     ("lrp_parareal_solve_batch", _I, [_P, _I, _P, _P, _I, _D, _P, _P]),
     ("lrp_server_create", _I, [_P, _I, _I, _S, _PP]),

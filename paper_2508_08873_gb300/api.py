@@ -325,6 +325,34 @@ def parareal_solve(ctx: Context, co: Coarse, u0, g=None, c=None, K: Optional[int
     return out, info
 
 
+def parareal_solve_classical(ctx: Context, op: Operator, dt: float, M: int, N: int, u0, g=None,
+                             c=None, K: Optional[int] = None, tol: float = 0.0, out=None,
+                             allow_notconv: bool = True):
+    """Classical Parareal with one backward-Euler coarse step per interval
+    (lrp_parareal_solve_classical).  Returns (u (N+1, n), info)."""
+    n = op.n
+    Kmax = N if K is None else int(K)
+    u0 = _as_c(u0)
+    Q = 0
+    if g is not None:
+        g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
+        Q = g.shape[0]
+        c = _as_c(c)
+    if out is None:
+        out = np.empty((N + 1, n))
+    inc = np.zeros(max(Kmax, 1))
+    kd = ctypes.c_int()
+    stats = nat.SolveStats()
+    ok = (nat.LRP_OK, nat.LRP_ENOTCONV) if allow_notconv else (nat.LRP_OK,)
+    st = check(ctx.lib.lrp_parareal_solve_classical(ctx.h, op.h, float(dt), int(M), int(N), ptr(u0), Q,
+                                                    ptr(g), ptr(c), Kmax, float(tol), ptr(out),
+                                                    inc.ctypes.data, ctypes.byref(kd),
+                                                    ctypes.byref(stats)), ctx.h, ok)
+    info = dict(k_done=kd.value, fine_evals=stats.fine_evals, converged=bool(stats.converged),
+                increments=inc[:kd.value], device_ms=stats.device_ms, status=st)
+    return out, info
+
+
 def fine_solution(ctx: Context, op: Operator, dt: float, M: int, N: int, u0, g=None, c=None,
                   out=None):
     """Sequential fine solution u_{i+1} = F_i u_i on the device, (N+1, n)."""

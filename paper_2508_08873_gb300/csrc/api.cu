@@ -287,6 +287,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
     c->p_tri_group = value;
+  } else if (k == "orth_cluster") {
+    if (value < -1 || value > 16 || (value > 0 && (value & (value - 1)))) return LRP_EINVAL;
+    c->p_orth_cluster = value;
   } else if (k == "krylov_cluster") {
     if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
     c->p_krylov_cluster = value;
@@ -306,6 +309,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_cluster") *value = c->p_tri_cluster;
   else if (k == "queue_cluster") *value = c->p_queue_cluster;
   else if (k == "krylov_cluster") *value = c->p_krylov_cluster;
+  else if (k == "orth_cluster") *value = c->p_orth_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
   else if (k == "tri_warp") *value = c->p_tri_warp;
   else if (k == "tri_chunk") *value = c->p_tri_chunk;
@@ -969,6 +973,173 @@ lrp_status lrp_fine_solution(lrp_ctx* c, const lrp_operator* opc, double dt, int
     if ((s = propagate_any(c, op, dt, M, 0, 1, 0, in, o, src))) return s;
   }
   return from_device(c, u_out, u.ptr, sizeof(double) * (size_t)(N + 1) * n);
+}
+
+
+// ===========================================================================
+// Classical Parareal: one backward-Euler step of size M*dt as the coarse
+// solver (the comparison method of the paper's numerical experiments)
+// ===========================================================================
+// u^k_{i+1} = F_i u^{k-1}_i + G_i'(u^k_i - u^{k-1}_i); the increment is stored
+// for the next interval's coarse step and for the norms.
+__global__ static void k_cls_update(const double* __restrict__ F, const double* __restrict__ y,
+                                    double* __restrict__ u_next, double* __restrict__ d_out, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double nv = y ? F[k] + y[k] : F[k];
+  d_out[k] = nv - u_next[k];
+  u_next[k] = nv;
+}
+
+// Per interval m = 0..N: ||u_m||^2 and ||u^k_m - u^{k-1}_m||^2 (the increment
+// of m >= first + 1 is in D[m - 1]), one CTA per interval, fixed-order sums.
+__global__ static void k_cls_norms(const double* __restrict__ u, const double* __restrict__ D, int n,
+                                   int first, double* __restrict__ out) {
+  __shared__ double red[2][8];
+  const int m = blockIdx.x;
+  const bool hasd = m >= first + 1;
+  double su = 0.0, sd = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) {
+    const double v = u[(size_t)m * n + k];
+    su += v * v;
+    if (hasd) {
+      const double d = D[(size_t)(m - 1) * n + k];
+      sd += d * d;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    su += __shfl_xor_sync(0xffffffffu, su, o);
+    sd += __shfl_xor_sync(0xffffffffu, sd, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) { red[0][w] = su; red[1][w] = sd; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0, b = 0.0;
+    for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { a += red[0][q]; b += red[1][q]; }
+    out[2 * m] = sqrt(a);
+    out[2 * m + 1] = sqrt(b);
+  }
+}
+
+lrp_status lrp_parareal_solve_classical(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int N,
+                                        const double* u0, int Q, const double* g, const double* cv,
+                                        int K_max, double tol, double* u_out, double* incr_out,
+                                        int* k_done, lrp_solve_stats* stats) {
+  if (!c || !opc || !u0 || !u_out || N < 1 || M < 1 || !(dt > 0) || Q < 0 || K_max < 0)
+    return LRP_EINVAL;
+  if (Q > 0 && (!g || !cv)) return LRP_EINVAL;
+  cudaSetDevice(c->device);
+  Operator* op = const_cast<lrp_operator*>(opc);
+  const int n = op->n;
+  const int K = std::min(K_max, N);
+  const double DT = dt * M;
+  DevBuf u, F, D, y, nrm;
+  lrp_status s;
+  if ((s = dev_alloc(c, u, sizeof(double) * (size_t)(N + 1) * n))) return s;
+  if ((s = dev_alloc(c, F, sizeof(double) * (size_t)N * n))) return s;
+  if ((s = dev_alloc(c, D, sizeof(double) * (size_t)N * n))) return s;
+  if ((s = dev_alloc(c, y, sizeof(double) * (size_t)n))) return s;
+  if ((s = dev_alloc(c, nrm, sizeof(double) * 2 * (size_t)(N + 1)))) return s;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, c->stream);
+  if ((s = to_device(c, u.ptr, u0, sizeof(double) * n))) return s;
+  DevView gv, cvv;
+  if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * Q, cvv))) return s;
+  // initial coarse sweep u^0_{i+1} = G_i u^0_i: one step of size M*dt, the
+  // source sampled at the interval's end t_{i+1}
+  for (int i = 0; i < N; ++i) {
+    PropIn in;
+    in.x = u.as<double>() + (size_t)i * n;
+    in.ldx = n;
+    PropOut o;
+    o.y = u.as<double>() + (size_t)(i + 1) * n;
+    o.ldy = n;
+    PropSrc src;
+    src.Q = Q;
+    src.g = (const double*)gv.p;
+    src.c = Q > 0 ? (const double*)cvv.p + ((size_t)(i + 1) * M - 1) * Q : nullptr;
+    src.cstride = Q;
+    if ((s = propagate_any(c, op, DT, 1, 0, 1, 0, in, o, src))) return s;
+  }
+  PropSrc srcf;
+  srcf.Q = Q;
+  srcf.g = (const double*)gv.p;
+  srcf.c = (const double*)cvv.p;
+  srcf.cstride = (long)M * Q;
+  int k = 0, converged = 0;
+  double last_inc = 0.0;
+  std::vector<double> hn(2 * (size_t)(N + 1));
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  while (k < K) {
+    const int first = k;
+    PropIn in;
+    in.x = u.as<double>() + (size_t)first * n;
+    in.ldx = n;
+    PropOut o;
+    o.y = F.as<double>() + (size_t)first * n;
+    o.ldy = n;
+    PropSrc sk = srcf;
+    if (Q > 0) sk.c = srcf.c + (size_t)first * M * Q;
+    if ((s = propagate_any(c, op, dt, M, 0, N - first, 0, in, o, sk))) return s;
+    // sequential correction; the increment at `first` is 0
+    for (int i = first; i < N; ++i) {
+      const double* yi = nullptr;
+      if (i > first) {
+        PropIn gin;
+        gin.x = D.as<double>() + (size_t)(i - 1) * n;
+        gin.ldx = n;
+        PropOut go;
+        go.y = y.ptr;
+        go.ldy = n;
+        PropSrc none;
+        if ((s = propagate_any(c, op, DT, 1, 0, 1, 0, gin, go, none))) return s;
+        yi = y.as<double>();
+      }
+      k_cls_update<<<nb, 256, 0, c->stream>>>(F.as<double>() + (size_t)i * n, yi,
+                                              u.as<double>() + (size_t)(i + 1) * n,
+                                              D.as<double>() + (size_t)i * n, n);
+      c->launches += 1;
+    }
+    k_cls_norms<<<N + 1, 256, 0, c->stream>>>(u.as<double>(), D.as<double>(), n, first, nrm.as<double>());
+    c->launches += 1;
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaMemcpyAsync(hn.data(), nrm.ptr, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost,
+                                c->stream);
+    if (!e) e = cudaStreamSynchronize(c->stream);
+    if (e) return cuda_err(c, e, "classical parareal iteration");
+    ++k;
+    double umax = 0.0, dmax = 0.0;
+    for (int m = 0; m <= N; ++m) {
+      umax = std::max(umax, hn[2 * m]);
+      dmax = std::max(dmax, hn[2 * m + 1]);
+    }
+    last_inc = umax > 0.0 ? dmax / umax : dmax;
+    if (incr_out) incr_out[k - 1] = last_inc;
+    if (tol > 0 && last_inc <= tol) { converged = 1; break; }
+  }
+  if ((s = from_device(c, u_out, u.ptr, sizeof(double) * (size_t)(N + 1) * n))) return s;
+  cudaEventRecord(e1, c->stream);
+  cudaError_t e = cudaEventSynchronize(e1);
+  if (e) return cuda_err(c, e, "classical parareal");
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (k_done) *k_done = k;
+  if (stats) {
+    stats->k_done = k;
+    stats->fine_evals = k;
+    stats->converged = converged;
+    stats->final_bound = last_inc;
+    stats->scale = 1.0;
+    stats->device_ms = ms;
+  }
+  if (tol > 0 && !converged) return set_err(c, LRP_ENOTCONV, "tolerance not met within K_max");
+  return LRP_OK;
 }
 
 }  // extern "C"

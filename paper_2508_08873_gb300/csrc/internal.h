@@ -53,6 +53,7 @@ struct Ctx {
   int p_tri_warp = 0;        // one-warp cluster kernel for FP64 small batches (0 auto, 1 off)
   int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
   int p_krylov_cluster = 0;  // CTAs per cluster of the 2D propagator (1..16)
+  int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)

@@ -10,8 +10,12 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "common.cuh"
 #include "internal.h"
+
+namespace cg = cooperative_groups;
 
 namespace lrp {
 
@@ -94,9 +98,183 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_cgs2(int ell, int n, T* __rest
   if (threadIdx.x == 0) rank[blockIdx.x] = r;
 }
 
+// ---------------------------------------------------------------------------
+// The same CGS2 with one interval per thread-block cluster and the interval's
+// block held in shared memory: CTA q of the cluster keeps rows
+// [q*per, (q+1)*per) of all ell vectors, dot products are summed over the
+// cluster (per-CTA FP64 partials pushed into every CTA's shared memory before
+// the cluster barrier, then added in a fixed order), and the update and
+// normalisation touch only shared memory.  Three cluster sums per vector:
+// ||y_j||^2 together with the first projection, the second projection, the
+// norm after it.
+// ---------------------------------------------------------------------------
+constexpr int ORTHC_MAXC = 16;
+constexpr int ORTHC_MAXV = 65;      // ell + 1 values per cluster sum
+
+struct OrthRed {
+  double red[ORTH_THREADS / 32];
+  double part[2][ORTHC_MAXC][ORTHC_MAXV];
+  double tot[ORTHC_MAXV];
+  double* rpart[ORTHC_MAXC];
+};
+
+template <typename T>
+__global__ void __launch_bounds__(ORTH_THREADS) k_cgs2_cl(int ell, int n, T* __restrict__ X,
+                                                           double tau, double* __restrict__ Rcoef,
+                                                           int* __restrict__ rank) {
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ __align__(16) unsigned char orth_smem[];
+  __shared__ OrthRed sh;
+  __shared__ T hT[ORTHC_MAXV];
+  const int C = (int)cl.num_blocks(), q = (int)cl.block_rank();
+  const int iv = blockIdx.x / C;
+  const int per = (n + C - 1) / C;
+  const int lo = min(n, q * per), rows = min(n, lo + per) - lo;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T* sB = reinterpret_cast<T*>(orth_smem);           // [ell][per]
+  T* B = X + (size_t)iv * ell * n;
+  double* Rc = Rcoef + (size_t)iv * ell * ell;
+  for (int k = threadIdx.x; k < ell * per; k += blockDim.x) {
+    const int j = k / per, i = k % per;
+    sB[k] = i < rows ? B[(size_t)j * n + lo + i] : T(0);
+  }
+  if (q == 0)
+    for (int k = threadIdx.x; k < ell * ell; k += blockDim.x) Rc[k] = 0.0;
+  for (int k = threadIdx.x; k < C; k += blockDim.x) sh.rpart[k] = cl.map_shared_rank(&sh.part[0][0][0], k);
+  cl.sync();     // every CTA runs before remote stores into its shared memory
+  int buf = 0;
+  // cluster sum of nv values; vals[v] is set for v < nv by the caller's warps
+  // through `partial` (lane 0 of a warp, or the block sum for slot `bslot`)
+  auto push_and_sum = [&](int nv) {
+    for (int k = threadIdx.x; k < nv * C; k += blockDim.x) {
+      const int v = k % nv, dst = k / nv;
+      sh.rpart[dst][(buf * ORTHC_MAXC + q) * ORTHC_MAXV + v] = sh.tot[v];
+    }
+    cl.sync();
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x < nv) {
+      for (int k = 0; k < C; ++k) out += sh.part[buf][k][threadIdx.x];
+    }
+    __syncthreads();
+    if (threadIdx.x < nv) sh.tot[threadIdx.x] = out;
+    __syncthreads();
+    buf ^= 1;
+  };
+  // per-CTA dots of v with basis vectors 0..r-1 into sh.tot[0..r-1] and,
+  // when with_norm, ||v||^2 of this CTA's rows into sh.tot[r]
+  auto local_dots = [&](const T* v, int r, bool with_norm) {
+    for (int c = w; c < r; c += nw) {
+      const T* qc = sB + (size_t)c * per;
+      T pc = T(0);
+      for (int i = lane; i < rows; i += 32) pc += qc[i] * v[i];
+      pc = warp_sum<T>(pc);
+      if (lane == 0) sh.tot[c] = (double)pc;
+    }
+    if (with_norm) {
+      T a = T(0);
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) a += v[i] * v[i];
+      a = warp_sum<T>(a);
+      if (lane == 0) sh.red[w] = (double)a;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int k = 0; k < nw; ++k) s += sh.red[k];
+        sh.tot[r] = s;
+      }
+    }
+    __syncthreads();
+  };
+  auto subtract = [&](T* v, int r) {
+    for (int c = threadIdx.x; c < r; c += blockDim.x) hT[c] = (T)sh.tot[c];
+    __syncthreads();
+    for (int i = threadIdx.x; i < rows; i += blockDim.x) {
+      T s = v[i];
+      for (int c = 0; c < r; ++c) s -= hT[c] * sB[(size_t)c * per + i];
+      v[i] = s;
+    }
+    __syncthreads();
+  };
+  int r = 0;
+  for (int j = 0; j < ell; ++j) {
+    T* v = sB + (size_t)j * per;
+    // ||y_j||^2 and the first projection in one cluster sum
+    local_dots(v, r, true);
+    push_and_sum(r + 1);
+    const double nrm0 = sqrt(sh.tot[r]);
+    if (q == 0)
+      for (int c = threadIdx.x; c < r; c += blockDim.x) Rc[c * ell + j] += sh.tot[c];
+    subtract(v, r);
+    // second projection
+    if (r > 0) {
+      local_dots(v, r, false);
+      push_and_sum(r);
+      if (q == 0)
+        for (int c = threadIdx.x; c < r; c += blockDim.x) Rc[c * ell + j] += sh.tot[c];
+      subtract(v, r);
+    }
+    // norm after the projections
+    local_dots(v, 0, true);
+    push_and_sum(1);
+    const double nrm = sqrt(sh.tot[0]);
+    if (nrm0 > 0.0 && nrm > tau * nrm0) {
+      const T inv = (T)(1.0 / nrm);
+      T* qn = sB + (size_t)r * per;
+      for (int i = threadIdx.x; i < rows; i += blockDim.x) qn[i] = v[i] * inv;
+      if (q == 0 && threadIdx.x == 0) Rc[r * ell + j] = nrm;
+      ++r;
+    }
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < ell * per; k += blockDim.x) {
+    const int j = k / per, i = k % per;
+    if (i < rows) B[(size_t)j * n + lo + i] = j < r ? sB[k] : T(0);
+  }
+  if (q == 0 && threadIdx.x == 0) rank[iv] = r;
+  cl.sync();     // no CTA leaves while others may still store into its shared memory
+}
+
 lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau,
                      double* Rcoef, int* rank) {
   if (N <= 0) return LRP_OK;
+  // shared-memory cluster variant when the interval's block fits in at most
+  // 16 CTAs of 200 KB (1D problems); the one-CTA kernel otherwise
+  const size_t es = x_f64 ? 8 : 4;
+  int C = 2;
+  while (C <= ORTHC_MAXC && (size_t)ell * ((n + C - 1) / C) * es > 100 * 1024) C *= 2;
+  if (c->p_orth_cluster > 0) C = c->p_orth_cluster;
+  if (ell + 1 <= ORTHC_MAXV && C <= ORTHC_MAXC && c->p_orth_cluster >= 0 && n >= 64 * C) {
+    const size_t smem = (size_t)ell * ((n + C - 1) / C) * es;
+    cudaError_t e;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(N * C);
+    cfg.blockDim = dim3(ORTH_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaEvent_t ev = nullptr;
+    if (x_f64) {
+      e = cudaFuncSetAttribute(k_cgs2_cl<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (!e && C > 8) e = cudaFuncSetAttribute(k_cgs2_cl<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e) return cuda_err(c, e, "cgs2 cluster attributes");
+      timer_begin(c, "orth", &ev);
+      e = cudaLaunchKernelEx(&cfg, k_cgs2_cl<double>, ell, n, (double*)X, tau, Rcoef, rank);
+    } else {
+      e = cudaFuncSetAttribute(k_cgs2_cl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (!e && C > 8) e = cudaFuncSetAttribute(k_cgs2_cl<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e) return cuda_err(c, e, "cgs2 cluster attributes");
+      timer_begin(c, "orth", &ev);
+      e = cudaLaunchKernelEx(&cfg, k_cgs2_cl<float>, ell, n, (float*)X, tau, Rcoef, rank);
+    }
+    timer_end(c, "orth", ev);
+    return e ? cuda_err(c, e, "k_cgs2_cl") : LRP_OK;
+  }
   const int nw = ORTH_THREADS / 32;
   size_t smem = sizeof(double) * ((size_t)ell + nw);
   cudaEvent_t ev = nullptr;
@@ -115,7 +293,7 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
 // Column pairs are rotated in round-robin order, one warp per pair, until a
 // full sweep performs no rotation (|a_p.a_q| <= eps sqrt(|a_p|^2 |a_q|^2)).
 // ---------------------------------------------------------------------------
-constexpr int SVD_THREADS = 256;
+constexpr int SVD_THREADS = 1024;   // launch: one warp per column pair of a round
 constexpr int SVD_MAX_SWEEPS = 60;
 
 __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* __restrict__ Rz,
@@ -231,7 +409,8 @@ lrp_status small_svd(Ctx* c, int N, int ell, const double* Rz, const int* rank_v
   if (e) return cuda_err(c, e, "jacobi smem");
   cudaEvent_t ev = nullptr;
   timer_begin(c, "svd", &ev);
-  k_jacobi<<<N, SVD_THREADS, smem, c->stream>>>(ell, Rz, rank_v, s, Psi, Phi, status);
+  const int threads = std::min(SVD_THREADS, 32 * std::max(1, (ell + 1) / 2));
+  k_jacobi<<<N, threads, smem, c->stream>>>(ell, Rz, rank_v, s, Psi, Phi, status);
   e = cudaGetLastError();
   timer_end(c, "svd", ev);
   return e ? cuda_err(c, e, "k_jacobi") : LRP_OK;

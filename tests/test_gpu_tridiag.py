@@ -340,3 +340,46 @@ def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, 
         for v in range(nvec):
             assert rel(got[v], want[v]) <= tol
             assert rel(got[v], blk[v]) <= tol
+
+
+# ---------------------------------------------------------------------------
+# classical Parareal (backward-Euler coarse step), the comparison method
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("K", [0, 1, 3])
+def test_classical_parareal_matches_oracle(ctx, orc, K):
+    P = W.heat1d(n=255, N=8, M=16)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    u, info = api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, P.u0, P.g, P.c, K=K)
+    res = orc.parareal_classical(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0, P.g, P.c, K=K)
+    assert info["k_done"] == res.k_done == K
+    assert rel(u, res.iterates[-1]) <= 1e-10
+    for k in range(1, K + 1):
+        d = res.bounds[k - 1]
+        want = np.max(d) / np.max(np.linalg.norm(res.iterates[k], axis=1))
+        assert abs(info["increments"][k - 1] - want) <= 1e-8 * want
+
+
+def test_classical_parareal_adr1d_K_equals_N(ctx, orc):
+    """Full adr1d size: K = N reproduces the sequential fine solution."""
+    P = W.adr1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+    u, info = api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, P.u0, K=P.N)
+    assert info["k_done"] == P.N
+    assert orc.rel_err(u, ref) <= 1e-10
+
+
+def test_low_rank_beats_classical_on_heat(ctx, orc):
+    """Experiment 1's comparison on the heat configuration (n=255, N=16,
+    M=64, R=8, p=4): after the same number of iterations the low-rank coarse
+    solvers are far more accurate than one backward-Euler coarse step."""
+    P = W.heat1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0, P.g, P.c)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    for K in (1, 2):
+        uc, _ = api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, P.u0, P.g, P.c, K=K)
+        ul, _ = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=K)
+        e_cl, e_lr = orc.rel_err(uc, ref), orc.rel_err(ul, ref)
+        assert e_lr < 1e-3 * e_cl, (K, e_lr, e_cl)

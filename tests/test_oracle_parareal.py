@@ -184,3 +184,51 @@ def test_fine_evaluation_count_matches_experiment4_table(orc):
             res = orc.parareal(op, dt, M, N, co, u0, g, c, K=k)
             assert res.k_done == k
             assert build + res.fine_evals + 1 == want, (p, r, k)
+
+
+# ---------------------------------------------------------------------------
+# classical Parareal (backward-Euler coarse solver), the comparison method
+# ---------------------------------------------------------------------------
+def test_classical_parareal_scalar_closed_form(orc):
+    """For a scalar linear problem Parareal's iterates have the closed form
+    u^k_n = sum_{j<=k} binom(n, j) (F - G)^j G^(n-j) u0 (Gander and Vandewalle,
+    SIAM J. Sci. Comput. 29 (2007), the linear analysis of Parareal), with
+    F = (1 + dt lam)^-M and G = (1 + M dt lam)^-1."""
+    lam, dt, M, N = 3.0, 0.02, 5, 9
+    op = orc.Tridiag(np.zeros(1), np.array([lam]), np.zeros(1))
+    F = (1.0 + dt * lam) ** (-M)
+    G = 1.0 / (1.0 + M * dt * lam)
+    u0 = np.array([1.7])
+    for K in range(0, N + 1):
+        res = orc.parareal_classical(op, dt, M, N, u0, K=K)
+        want = [sum(math.comb(nn, j) * (F - G) ** j * G ** (nn - j) for j in range(0, min(K, nn) + 1)) * u0[0]
+                for nn in range(N + 1)]
+        np.testing.assert_allclose(res.iterates[-1][:, 0], want, rtol=1e-13, atol=0)
+
+
+def test_classical_parareal_K_equals_N_and_exact_coarse(orc):
+    P = W.heat1d(n=63, N=6, M=8)
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    ref = orc.sequential_fine(op, P.dt, P.M, P.N, P.u0, P.g, P.c)
+    res = orc.parareal_classical(op, P.dt, P.M, P.N, P.u0, P.g, P.c, K=P.N)
+    assert orc.rel_err(res.iterates[-1], ref) <= 1e-13
+    for k, it in enumerate(res.iterates):              # u^k_n exact for n <= k
+        assert orc.rel_err(it[:k + 1], ref[:k + 1]) <= 1e-13
+    # M = 1: the coarse step is the fine step, so u^0 is already the fine solution
+    ref1 = orc.sequential_fine(op, P.dt * P.M, 1, P.N, P.u0, P.g, P.c[P.M - 1::P.M])
+    res1 = orc.parareal_classical(op, P.dt * P.M, 1, P.N, P.u0, P.g, P.c[P.M - 1::P.M], K=0)
+    assert orc.rel_err(res1.iterates[0], ref1) <= 1e-14
+
+
+def test_low_rank_coarse_beats_classical_on_heat(orc):
+    """The paper's comparison (Experiment 1): with rank-R coarse solvers the
+    error after k iterations is far below the classical one."""
+    P = W.heat1d()
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    ref = orc.sequential_fine(op, P.dt, P.M, P.N, P.u0, P.g, P.c)
+    co = orc.build_coarse(op, P.dt, P.M, P.N, 4, 2, 0)
+    lr = orc.parareal(op, P.dt, P.M, P.N, co, P.u0, P.g, P.c, K=2)
+    cl = orc.parareal_classical(op, P.dt, P.M, P.N, P.u0, P.g, P.c, K=2)
+    e_lr = orc.rel_err(lr.iterates[-1], ref)
+    e_cl = orc.rel_err(cl.iterates[-1], ref)
+    assert e_lr < 1e-3 * e_cl, (e_lr, e_cl)
