@@ -291,7 +291,7 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
 // ---------------------------------------------------------------------------
 // One-sided Jacobi SVD of M (ell rows x kv columns), M[i][c] = Rz[c][i].
 // Column pairs are rotated in round-robin order, one warp per pair, until a
-// full sweep performs no rotation (|a_p.a_q| <= eps sqrt(|a_p|^2 |a_q|^2)).
+// full sweep performs no rotation (|a_p.a_q| <= m eps sqrt(|a_p|^2 |a_q|^2)).
 // ---------------------------------------------------------------------------
 constexpr int SVD_THREADS = 1024;   // launch: one warp per column pair of a round
 constexpr int SVD_MAX_SWEEPS = 60;
@@ -321,7 +321,9 @@ __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* _
   __syncthreads();
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int kp = kv + (kv & 1);       // players, padded to even
-  const double eps = 2.220446049250313e-16;
+  // convergence: every pair's cosine below m * eps (the usual one-sided
+  // Jacobi threshold); a stricter eps keeps rotating on rounding noise
+  const double eps = 2.220446049250313e-16 * m;
   int sweep = 0, done = (kv < 2);
   while (!done && sweep < SVD_MAX_SWEEPS) {
     if (threadIdx.x == 0) rotated = 0;
