@@ -193,6 +193,21 @@ lrp_status lrp_propagate_noalloc(int device, void* stream, int n, const double* 
 lrp_status lrp_build_coarse(lrp_ctx* ctx, const lrp_operator* op, double dt, int M, int N,
                             int rank, int oversample, uint64_t seed, lrp_precision prec,
                             lrp_coarse** out);
+
+/* Build variants (flags of lrp_build_coarse_ex). */
+enum { LRP_BUILD_INDEPENDENT_ADJOINT = 1 };
+/* lrp_build_coarse with flags.  LRP_BUILD_INDEPENDENT_ADJOINT: the variant
+ * mentioned in Sec. 2.2 that evaluates F_i'^* on an independent set of
+ * 2 (rank + oversample) Gaussian vectors Psi (Philox stream 3) instead of on
+ * the basis W, so that the forward and adjoint sketches have no dependence
+ * (one sequential round instead of two) at some cost in accuracy: with
+ * Y = F'Omega, Z = F'^* Psi, Q = orth(Y), the core X = (Psi^T Q)^+ Psi^T F'
+ * is a least-squares estimate of Q^T F', and the factors are those of the
+ * SVD of Q X.  Other arguments, outputs and errors as lrp_build_coarse;
+ * LRP_EBREAKDOWN when Psi^T Q is rank deficient. */
+lrp_status lrp_build_coarse_ex(lrp_ctx* ctx, const lrp_operator* op, double dt, int M, int N,
+                               int rank, int oversample, uint64_t seed, lrp_precision prec,
+                               int flags, lrp_coarse** out);
 void lrp_coarse_free(lrp_coarse* co);
 /* R_i (kept rank), the dimensions of the deflated bases of steps 2 and 4, all
  * singular values of the small matrix of step 5 (N x (rank+oversample),

@@ -331,6 +331,52 @@ def build_coarse(op, dt, M, N, R, p, seed) -> Coarse:
     return Coarse([rsvd_interval(op, dt, M, i, R, p, seed) for i in range(N)], R, p)
 
 
+# ----------------------------------------------------------------------------
+# Variant of Sec. 2.2: F'^* evaluated on an independent set of random vectors
+# (a two-sided sketch) instead of on the basis w, so that both sketches are
+# independent and run in one round, at some cost in accuracy.
+# ----------------------------------------------------------------------------
+STREAM_PSI = 3
+
+
+def rsvd_interval_indep(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval:
+    """Two-sided randomized SVD of F_i': Y = F' Omega (l = R + p columns),
+    Z = F'^* Psi (2 l independent columns, Philox stream 3), Q = orth(Y),
+    X = argmin ||(Psi^T Q) X - Psi^T F'|| (least squares, Psi^T F' = Z^T), so
+    F' ~ Q X; the SVD of X (its row space orthonormalised, then the small
+    SVD) gives U = Q^T Psi_s, S, V = Vh^T Phi_s.  Accuracy: exact when the
+    sketches span the whole space (checked by brute force); otherwise below
+    the two-pass variant.  Parity unpinned beyond that and the closed-form
+    spectrum of the heat operator at a loose tolerance."""
+    n = op.n
+    ell = R + p
+    ell2 = 2 * ell
+    omega = gauss_block(seed, i, n, ell)
+    psi = gauss_block(seed, i, n, ell2, stream=STREAM_PSI)
+    Y = propagate(op, dt, M, omega)                              # rows F' omega_j
+    Z = propagate(op, dt, M, psi, adjoint=True)                  # rows F'^T psi_a
+    Q, _ = mgs2(Y, tau)                                          # rows q_c
+    k = Q.shape[0]
+    if k == 0:
+        return CoarseInterval(np.zeros((n, 0)), np.zeros(0), np.zeros((n, 0)), np.zeros(0),
+                              0, 0, 0.0, ell + ell2)
+    B = psi @ Q.T                                                # (2l, k): (psi_a, q_c)
+    X = np.linalg.lstsq(B, Z, rcond=None)[0]                     # (k, n): F' ~ Q^T X
+    Vh, _ = mgs2(X, tau)                                         # row space of X
+    Xs = X @ Vh.T                                                # (k, k'): X = Xs Vh
+    Psi_s, s, Phi_s = jacobi_svd(Xs)
+    Ri = min(R, s.shape[0])
+    U = Q.T @ Psi_s[:, :Ri]
+    V = Vh.T @ Phi_s[:, :Ri]
+    sig_next = float(s[Ri]) if s.shape[0] > Ri else tau * float(s[0])
+    return CoarseInterval(U, s[:Ri].copy(), V, s, k, Vh.shape[0], sig_next, ell + ell2)
+
+
+def build_coarse_indep(op, dt, M, N, R, p, seed) -> Coarse:
+    """Coarse solvers from the two-sided sketch (rsvd_interval_indep)."""
+    return Coarse([rsvd_interval_indep(op, dt, M, i, R, p, seed) for i in range(N)], R, p)
+
+
 def exact_coarse(op, dt, M, N, R) -> Coarse:
     """Truncated SVD of the dense F' (small n only): the exact G_n of
     Eq. (spectral_G), used by tests as a comparison coarse solver."""

@@ -63,6 +63,7 @@ class ServerStats(ctypes.Structure):
 
 
 LRP_PENDING = 8
+LRP_BUILD_INDEPENDENT_ADJOINT = 1   # flags of lrp_build_coarse_ex
 
 # (name, restype, argtypes)
 _P, _I, _D, _S, _U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64
@@ -94,6 +95,7 @@ SIGNATURES = [
     ("lrp_propagate_noalloc", _I, [_I, _P, _I, _P, _P, _P, _D, _I, _I, _I, _P, _P, _I, _P, _P, _I]),
     ("lrp_gaussian", _I, [_P, _U64, _I, _I, _I, _I, _P]),
     ("lrp_build_coarse", _I, [_P, _P, _D, _I, _I, _I, _I, _U64, _I, _PP]),
+    ("lrp_build_coarse_ex", _I, [_P, _P, _D, _I, _I, _I, _I, _U64, _I, _I, _PP]),
     ("lrp_coarse_free", None, [_P]),
     ("lrp_coarse_info", _I, [_P, _P, _P, _P, _P, _P, _P]),
     ("lrp_coarse_factors", _I, [_P, _I, _P, _P, _P]),

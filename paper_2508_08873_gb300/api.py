@@ -177,14 +177,17 @@ class Coarse:
     """Low-rank coarse solvers G_i' = U_i diag(S_i) V_i^T of all intervals."""
 
     def __init__(self, ctx: Context, op: Operator, dt: float, M: int, N: int, rank: int,
-                 oversample: int, seed: int = 0, prec="f64"):
+                 oversample: int, seed: int = 0, prec="f64", independent_adjoint: bool = False):
+        """independent_adjoint: the two-sided sketch variant (F'^* on independent
+        random vectors; lrp_build_coarse_ex with LRP_BUILD_INDEPENDENT_ADJOINT)."""
         self.ctx, self.op = ctx, op
         self.dt, self.M, self.N, self.R, self.p = dt, M, N, rank, oversample
         self.prec = _prec(prec)
         h = ctypes.c_void_p()
-        check(ctx.lib.lrp_build_coarse(ctx.h, op.h, float(dt), int(M), int(N), int(rank),
-                                       int(oversample), int(seed), self.prec, ctypes.byref(h)),
-              ctx.h)
+        flags = nat.LRP_BUILD_INDEPENDENT_ADJOINT if independent_adjoint else 0
+        check(ctx.lib.lrp_build_coarse_ex(ctx.h, op.h, float(dt), int(M), int(N), int(rank),
+                                          int(oversample), int(seed), self.prec, flags,
+                                          ctypes.byref(h)), ctx.h)
         self.h = h
 
     def info(self) -> dict:

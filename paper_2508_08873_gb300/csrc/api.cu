@@ -567,8 +567,16 @@ lrp_status lrp_gaussian(lrp_ctx* c, uint64_t seed, int interval, int ncol, int n
 lrp_status lrp_build_coarse(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int N,
                             int rank, int oversample, uint64_t seed, lrp_precision prec,
                             lrp_coarse** out) {
-  if (!c || !opc || !out || !(dt > 0) || M < 1 || N < 1 || rank < 0 || oversample < 0)
+  return lrp_build_coarse_ex(c, opc, dt, M, N, rank, oversample, seed, prec, 0, out);
+}
+
+lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int N,
+                               int rank, int oversample, uint64_t seed, lrp_precision prec,
+                               int flags, lrp_coarse** out) {
+  if (!c || !opc || !out || !(dt > 0) || M < 1 || N < 1 || rank < 0 || oversample < 0 ||
+      (flags & ~LRP_BUILD_INDEPENDENT_ADJOINT))
     return LRP_EINVAL;
+  const bool two_sided = (flags & LRP_BUILD_INDEPENDENT_ADJOINT) != 0;
   const int ell = rank + oversample;
   if (ell < 1) return set_err(c, LRP_EINVAL, "rank + oversample must be >= 1");
   if (rank > 64 || ell > 128) return set_err(c, LRP_EINVAL, "rank <= 64 and rank+oversample <= 128");
@@ -617,8 +625,35 @@ lrp_status lrp_build_coarse(lrp_ctx* c, const lrp_operator* opc, double dt, int 
   o.ldy = n;
   PropSrc nosrc;
   if ((s = propagate_any(c, op, dt, M, 0, N * ell, f32, in, o, nosrc))) return s;
-  // step 2: W = orth(Y), in place
   const double tau = f32 ? 2e-5 : 1e-13;
+  if (two_sided) {
+    // F'^* on 2 l independent random vectors psi (Philox stream 3), with no
+    // dependence on the forward sketch; Q = orth(Y); X^T = Z (Psi^T Q)^+T;
+    // Vh = orth(X^T) with X = Rz^T Vh, so the small SVD below is that of X.
+    const int ell2 = 2 * ell;
+    DevBuf Z2, Bb, Cb;
+    if ((s = dev_alloc(c, Z2, (size_t)N * ell2 * n * es))) return s;
+    if ((s = dev_alloc(c, Bb, sizeof(double) * (size_t)N * ell2 * ell))) return s;
+    if ((s = dev_alloc(c, Cb, sizeof(double) * (size_t)N * ell2 * ell))) return s;
+    PropIn ina;
+    ina.gen = 1;
+    ina.seed = seed;
+    ina.stream = 3;
+    ina.ncol = ell2;
+    ina.interval0 = 0;
+    PropOut oa;
+    oa.y = Z2.ptr;
+    oa.y_f64 = !f32;
+    oa.ldy = n;
+    if ((s = propagate_any(c, op, dt, M, 1, N * ell2, f32, ina, oa, nosrc))) return s;
+    if ((s = orth_cgs2(c, N, ell, n, Y.ptr, !f32, tau, Rw.as<double>(), rw.as<int>()))) return s;
+    if ((s = two_sided_core(c, N, ell, ell2, n, seed, f32, Y.ptr, rw.as<int>(), Z2.ptr, Z.ptr,
+                            Bb.as<double>(), Cb.as<double>(), st.as<int>())))
+      return s;
+    if ((s = orth_cgs2(c, N, ell, n, Z.ptr, !f32, tau, Rz.as<double>(), rv.as<int>()))) return s;
+    cudaStreamSynchronize(c->stream);    // Z2, Bb, Cb are released here
+  } else {
+  // step 2: W = orth(Y), in place
   if ((s = orth_cgs2(c, N, ell, n, Y.ptr, !f32, tau, Rw.as<double>(), rw.as<int>()))) return s;
   // step 3: Z = F'^* W
   PropIn in2;
@@ -632,6 +667,7 @@ lrp_status lrp_build_coarse(lrp_ctx* c, const lrp_operator* opc, double dt, int 
   if ((s = propagate_any(c, op, dt, M, 1, N * ell, f32, in2, o2, nosrc))) return s;
   // step 4: Vh = orth(Z) in place; M_ij = (z_i, v_j) = Rz[j][i]
   if ((s = orth_cgs2(c, N, ell, n, Z.ptr, !f32, tau, Rz.as<double>(), rv.as<int>()))) return s;
+  }
   // step 5: SVD of M
   if ((s = small_svd(c, N, ell, Rz.as<double>(), rv.as<int>(), sv.as<double>(), Psi.as<double>(),
                      Phi.as<double>(), st.as<int>())))
@@ -647,6 +683,7 @@ lrp_status lrp_build_coarse(lrp_ctx* c, const lrp_operator* opc, double dt, int 
   cudaMemcpyAsync(&svd_status, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "build_coarse");
+  if (svd_status & 2) return set_err(c, LRP_EBREAKDOWN, "rank-deficient two-sided sketch core");
   if (svd_status) return set_err(c, LRP_ENOTCONV, "Jacobi SVD did not converge");
   co->Ri.resize(N);
   co->delta = 0.0;

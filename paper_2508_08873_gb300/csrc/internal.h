@@ -172,6 +172,7 @@ struct PropIn {
   long slot_stride = 0;
   int gen = 0;              // 1: generate N(0,1) entries instead of reading x
   uint64_t seed = 0;
+  uint32_t stream = 0;      // Philox stream of the generated entries (0: Omega, 3: Psi)
   int ncol = 1;
   int interval0 = 0;        // interval of system 0 (generated input)
 };
@@ -245,6 +246,11 @@ lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const i
 // place.  Kept vectors are compacted to the front, dropped rows zeroed.
 // Rcoef [N][ell][ell] (FP64): Rcoef[c][j] = coefficient of basis vector c in
 // input vector j.  rank[N] (device int).
+// Two-sided sketch core: B = Psi^T Q, C = B (B^T B)^-1, X^T = Z C into XT
+// ([N][ell][n], sketch precision); status bit 1 set when B^T B is singular.
+lrp_status two_sided_core(Ctx* c, int N, int ell, int ell2, int n, uint64_t seed, int f32,
+                          const void* Q, const int* rank_w, const void* Z, void* XT, double* Bbuf,
+                          double* Cbuf, int* status);
 lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau,
                      double* Rcoef, int* rank);
 // One-sided Jacobi SVD of M_i = Rz_i^T (ell x ell) for every interval.

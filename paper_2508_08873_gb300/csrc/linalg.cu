@@ -476,6 +476,169 @@ lrp_status lift(Ctx* c, int N, int ell, int R, int n, const void* W, const void*
   return e ? cuda_err(c, e, "k_lift") : LRP_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Two-sided sketch (F'^* on independent random vectors psi_a, Philox stream 3):
+//   B = Psi^T Q (2l x k), C = B (B^T B)^-1 (the least-squares solution map),
+//   X^T = Z C (n x k), Z the adjoint sketch (2l x n, rows F'^T psi_a).
+// ---------------------------------------------------------------------------
+constexpr uint32_t PSI_STREAM = 3;
+
+// B[iv][a][c] = (psi_a, q_c) for c < k = rank_w[iv] (0 beyond); psi_a
+// regenerated in the sketch precision T, exactly as the adjoint propagation
+// drew it.  grid (ell2, N).
+template <typename T>
+__global__ void __launch_bounds__(256) k_psi_dots(int ell2, int ell, int n, uint64_t seed,
+                                                   const T* __restrict__ Q,
+                                                   const int* __restrict__ rank_w,
+                                                   double* __restrict__ B) {
+  __shared__ double red[8][16];
+  const int a = blockIdx.x, iv = blockIdx.y;
+  const int k = rank_w[iv];
+  const T* Qi = Q + (size_t)iv * ell * n;
+  double* Bi = B + ((size_t)iv * ell2 + a) * ell;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int c0 = 0; c0 < ell; c0 += 16) {
+    T acc[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc[t] = T(0);
+    if (c0 < k) {
+      for (int x = threadIdx.x; x < n; x += blockDim.x) {
+        const T ps = gauss<T>(seed, PSI_STREAM, (uint32_t)iv, (uint32_t)a, (uint32_t)x);
+#pragma unroll
+        for (int t = 0; t < 16; ++t)
+          if (c0 + t < k) acc[t] += ps * Qi[(size_t)(c0 + t) * n + x];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const T v = warp_sum<T>(acc[t]);
+      if (lane == 0) red[w][t] = (double)v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 16 && c0 + (int)threadIdx.x < ell) {
+      double sum = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); ++q) sum += red[q][threadIdx.x];
+      Bi[c0 + threadIdx.x] = (c0 + (int)threadIdx.x < k) ? sum : 0.0;
+    }
+    __syncthreads();
+  }
+}
+
+// C = B (B^T B)^-1 per interval (FP64, one CTA): Gram, Cholesky factor
+// (right-looking, in shared memory), then two triangular solves per row of B.
+__global__ void __launch_bounds__(256) k_lsq(int ell2, int ell, const double* __restrict__ B,
+                                             const int* __restrict__ rank_w, double* __restrict__ Cm,
+                                             int* __restrict__ status) {
+  extern __shared__ double lsq_sm[];
+  double* G = lsq_sm;                  // [ell][ell]
+  const int iv = blockIdx.x, k = rank_w[iv];
+  const double* Bi = B + (size_t)iv * ell2 * ell;
+  double* Ci = Cm + (size_t)iv * ell2 * ell;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, j = e % k;
+    double sum = 0.0;
+    for (int a = 0; a < ell2; ++a) sum += Bi[(size_t)a * ell + i] * Bi[(size_t)a * ell + j];
+    G[i * ell + j] = sum;
+  }
+  __syncthreads();
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = G[j * ell + j];
+      if (!(d > 0.0) || !isfinite(d)) bad = 1;
+      G[j * ell + j] = sqrt(fabs(d) > 0.0 ? fabs(d) : 1.0);
+    }
+    __syncthreads();
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) G[i * ell + j] /= G[j * ell + j];
+    __syncthreads();
+    for (int e = threadIdx.x; e < (k - j - 1) * (k - j - 1); e += blockDim.x) {
+      const int i = j + 1 + e / (k - j - 1), l = j + 1 + e % (k - j - 1);
+      if (l <= i) G[i * ell + l] -= G[i * ell + j] * G[l * ell + j];
+    }
+    __syncthreads();
+  }
+  // row a of C: solve (L L^T) c = B[a]^T
+  for (int a = threadIdx.x; a < ell2; a += blockDim.x) {
+    double y[128];
+    for (int i = 0; i < k; ++i) {
+      double v = Bi[(size_t)a * ell + i];
+      for (int l = 0; l < i; ++l) v -= G[i * ell + l] * y[l];
+      y[i] = v / G[i * ell + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {
+      double v = y[i];
+      for (int l = i + 1; l < k; ++l) v -= G[l * ell + i] * y[l];
+      y[i] = v / G[i * ell + i];
+    }
+    for (int i = 0; i < ell; ++i) Ci[(size_t)a * ell + i] = i < k ? y[i] : 0.0;
+  }
+  if (threadIdx.x == 0 && bad) atomicOr(status, 2);
+}
+
+// X^T = Z C: out[iv][c][x] = sum_a C[iv][a][c] Z[iv][a][x], c < ell (rows
+// beyond the rank are 0 because C's columns are).  grid (row blocks, N).
+template <typename T>
+__global__ void __launch_bounds__(256) k_combine(int ell2, int ell, int n, const T* __restrict__ Z,
+                                                 const double* __restrict__ Cm, T* __restrict__ out) {
+  extern __shared__ double cmb_sm[];
+  T* sC = reinterpret_cast<T*>(cmb_sm);            // [ell2][ell]
+  const int iv = blockIdx.y;
+  for (int e = threadIdx.x; e < ell2 * ell; e += blockDim.x) sC[e] = (T)Cm[(size_t)iv * ell2 * ell + e];
+  __syncthreads();
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const T* Zi = Z + (size_t)iv * ell2 * n;
+  for (int c0 = 0; c0 < ell; c0 += 16) {
+    T acc[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) acc[t] = T(0);
+    for (int a = 0; a < ell2; ++a) {
+      const T z = Zi[(size_t)a * n + x];
+#pragma unroll
+      for (int t = 0; t < 16; ++t)
+        if (c0 + t < ell) acc[t] += sC[a * ell + c0 + t] * z;
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+      if (c0 + t < ell) out[((size_t)iv * ell + c0 + t) * n + x] = acc[t];
+  }
+}
+
+lrp_status two_sided_core(Ctx* c, int N, int ell, int ell2, int n, uint64_t seed, int f32,
+                          const void* Q, const int* rank_w, const void* Z, void* XT, double* Bbuf,
+                          double* Cbuf, int* status) {
+  if (ell > 128 || ell2 > 256) return set_err(c, LRP_EINVAL, "two-sided sketch too wide");
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "orth", &ev);
+  const size_t smem_l = sizeof(double) * (size_t)ell * ell;
+  cudaError_t e = cudaFuncSetAttribute(k_lsq, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_l);
+  const size_t smem_c = (f32 ? 4 : 8) * (size_t)ell2 * ell;
+  if (!e) {
+    if (f32) {
+      e = cudaFuncSetAttribute(k_combine<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+      if (!e) {
+        k_psi_dots<float><<<dim3(ell2, N), 256, 0, c->stream>>>(ell2, ell, n, seed, (const float*)Q, rank_w, Bbuf);
+        k_lsq<<<N, 256, smem_l, c->stream>>>(ell2, ell, Bbuf, rank_w, Cbuf, status);
+        k_combine<float><<<dim3((n + 255) / 256, N), 256, smem_c, c->stream>>>(ell2, ell, n, (const float*)Z,
+                                                                              Cbuf, (float*)XT);
+      }
+    } else {
+      e = cudaFuncSetAttribute(k_combine<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_c);
+      if (!e) {
+        k_psi_dots<double><<<dim3(ell2, N), 256, 0, c->stream>>>(ell2, ell, n, seed, (const double*)Q, rank_w, Bbuf);
+        k_lsq<<<N, 256, smem_l, c->stream>>>(ell2, ell, Bbuf, rank_w, Cbuf, status);
+        k_combine<double><<<dim3((n + 255) / 256, N), 256, smem_c, c->stream>>>(ell2, ell, n, (const double*)Z,
+                                                                               Cbuf, (double*)XT);
+      }
+    }
+  }
+  timer_end(c, "orth", ev);
+  c->launches += 2;
+  if (!e) e = cudaGetLastError();
+  return e ? cuda_err(c, e, "two-sided sketch core") : LRP_OK;
+}
+
 // Sketch vectors of one interval, written as doubles.
 template <typename T>
 __global__ void k_gaussian(uint64_t seed, int interval, int ncol, int n, double* out) {

@@ -189,7 +189,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
     T v = T(0);
     if (a.in.gen)
-      v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+      v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                    (uint32_t)(sys % a.in.ncol), (uint32_t)k);
     else if (a.in.x == nullptr)
       v = T(0);

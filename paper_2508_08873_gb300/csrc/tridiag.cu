@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
       T v = T(0);
       if (active && r < n) {
         if (a.in.gen) {
-          v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+          v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                        (uint32_t)(sys % a.in.ncol), (uint32_t)r);
         } else if (a.in.x == nullptr) {
           v = T(0);                                   // zero initial value (b_i = F_i 0)
@@ -321,7 +321,7 @@ __global__ void __launch_bounds__(256) k_tri_propagate_rc(TriKArgs a) {
         T v = T(0);
         if (active && r < n) {
           if (a.in.gen)
-            v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+            v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                          (uint32_t)(sys % a.in.ncol), (uint32_t)r);
           else if (a.in.x == nullptr)
             v = T(0);

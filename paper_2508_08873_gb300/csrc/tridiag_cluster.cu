@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
         T v = T(0);
         if (act && r < n) {
           if (a.in.gen)
-            v = gauss<T>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+            v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                          (uint32_t)(sys % a.in.ncol), (uint32_t)r);
           else if (a.in.x == nullptr)
             v = T(0);
@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
       double v = 0.0;
       if (r < n) {
         if (a.in.gen)
-          v = gauss<double>(a.in.seed, 0u, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+          v = gauss<double>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                             (uint32_t)(sys % a.in.ncol), (uint32_t)r);
         else if (a.in.x == nullptr)
           v = 0.0;

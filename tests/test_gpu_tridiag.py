@@ -383,3 +383,44 @@ def test_low_rank_beats_classical_on_heat(ctx, orc):
         ul, _ = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=K)
         e_cl, e_lr = orc.rel_err(uc, ref), orc.rel_err(ul, ref)
         assert e_lr < 1e-3 * e_cl, (K, e_lr, e_cl)
+
+
+# ---------------------------------------------------------------------------
+# two-sided sketch variant (F'^* on independent random vectors, Sec. 2.2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("which", ["heat", "adr"])
+def test_build_two_sided_matches_oracle(ctx, orc, which):
+    if which == "heat":
+        P = W.heat1d(n=255, N=6, M=32, R=6, p=3)
+    else:
+        P = W.adr1d(n=1023, N=4, M=64, R=8, p=4)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64", independent_adjoint=True)
+    info = co.info()
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    probes = np.random.default_rng(11).standard_normal((3, P.n))
+    for i in range(P.N):
+        oc = orc.rsvd_interval_indep(oop, P.dt, P.M, i, P.R, P.p, P.seed)
+        s1 = oc.sigma[0]
+        assert info["R"][i] == oc.S.shape[0]
+        assert np.max(np.abs(info["sigma"][i, :oc.S.shape[0]] - oc.S)) <= 1e-9 * s1
+        U, S, V = co.factors(i)
+        assert _operator_diff(oc, U, S, V, probes) <= 1e-9 * s1
+    # the coarse solvers drive Parareal to the fine solution
+    u, pinfo = api.parareal_solve(ctx, co, P.u0, P.g, P.c, K=P.N)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0, P.g, P.c)
+    assert orc.rel_err(u, ref) <= 1e-10
+
+
+def test_build_two_sided_mixed_close_to_two_pass(ctx, orc):
+    """Mixed precision, heat: the two-sided coarse operators agree with the
+    closed-form leading singular values to the FP32 sketch accuracy."""
+    P = W.heat1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed", independent_adjoint=True)
+    info = co.info()
+    h = 1.0 / (P.n + 1)
+    lam = 4.0 / h ** 2 * np.sin(np.arange(1, P.n + 1) * np.pi * h / 2) ** 2
+    sig = (1.0 + P.dt * lam) ** (-P.M)
+    for i in range(P.N):
+        assert np.max(np.abs(info["sigma"][i, :4] - sig[:4])) <= 1e-4 * sig[0]

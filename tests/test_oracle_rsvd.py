@@ -72,3 +72,38 @@ def test_rsvd_independent_intervals_and_seed(orc):
     # different sketches, same operator: same leading singular values
     np.testing.assert_allclose(a.S[:3], b.S[:3], rtol=1e-9)
     assert a.fine_evals == 2 * (P.R + P.p)
+
+
+# ---------------------------------------------------------------------------
+# two-sided variant (F'^* on independent random vectors, Sec. 2.2)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("maker", ["heat", "adr"])
+def test_rsvd_indep_exact_when_sketches_span_space(orc, maker):
+    """With l >= n the forward sketch spans the space, Q is a complete basis
+    and the least-squares core is exact: the two-sided rSVD equals the
+    truncated dense SVD (brute force)."""
+    n, dt, M = 12, 1e-3, 5
+    lo, di, up = W.heat1d_op(n) if maker == "heat" else W.adr1d_op(n, nu=0.05)
+    op = orc.Tridiag(lo, di, up)
+    Fp = orc.propagate(op, dt, M, np.eye(n)).T
+    Uf, sf, Vft = np.linalg.svd(Fp)
+    R = 5
+    c = orc.rsvd_interval_indep(op, dt, M, 0, R, n - R + 2, seed=3)
+    np.testing.assert_allclose(c.S, sf[:R], rtol=0, atol=1e-11 * sf[0])
+    G = c.U @ np.diag(c.S) @ c.V.T
+    Gex = Uf[:, :R] @ np.diag(sf[:R]) @ Vft[:R]
+    np.testing.assert_allclose(G, Gex, atol=1e-10 * sf[0])
+    assert c.fine_evals == 3 * (n + 2)
+
+
+def test_rsvd_indep_heat_spectrum_and_orientation(orc):
+    """Heat configuration: the leading singular values follow the closed-form
+    DST spectrum (to 1e-7 sigma_1: the two-sided core is a least-squares
+    estimate), and F' phi_r ~ sigma_r psi_r."""
+    P = W.heat1d()
+    op = orc.Tridiag(P.lo, P.di, P.up)
+    c = orc.rsvd_interval_indep(op, P.dt, P.M, 3, P.R, P.p, P.seed)
+    sig, _ = _heat_closed_form(P.n, P.dt, P.M)
+    assert np.max(np.abs(c.S[:6] - sig[:6])) <= 1e-7 * sig[0]
+    FV = orc.propagate(op, P.dt, P.M, c.V[:, :4].T).T
+    np.testing.assert_allclose(FV, c.U[:, :4] * c.S[:4], atol=1e-7 * c.S[0])
