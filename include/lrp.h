@@ -261,6 +261,22 @@ lrp_status lrp_parareal_solve(lrp_ctx* ctx, const lrp_coarse* co, const double* 
                               double* u_out, double* bound_out, int* k_done,
                               lrp_solve_stats* stats);
 
+/* Fine time stepper of an operator's propagations (all of lrp_propagate,
+ * the sketches of lrp_build_coarse, the fine solves of lrp_parareal_solve and
+ * lrp_fine_solution): backward Euler (the default), or the two-stage SDIRK
+ * methods of Sec. 4 (effect of the time discretisation), SDIRK2 (gamma = 1,
+ * a21 = -1, b = (1/2, 1/2); not L-stable) and SDIRK2-L (gamma = (2-sqrt 2)/2,
+ * a21 = 1 - gamma, b = (1 - gamma, gamma); L-stable), each step two solves
+ * with I + gamma dt A.  SDIRK steppers: tridiagonal operators with n <= 4096
+ * and f = 0 only (LRP_EINVAL otherwise); coarse handles must be built with the stepper their
+ * solves use.  The allocation-free entry point always uses backward Euler. */
+typedef enum {
+  LRP_STEP_BACKWARD_EULER = 0,
+  LRP_STEP_SDIRK2 = 1,
+  LRP_STEP_SDIRK2_L = 2
+} lrp_stepper;
+lrp_status lrp_operator_set_stepper(lrp_operator* op, int stepper);
+
 /* Classical Parareal for comparison (the method of the dashed curves in the
  * paper's numerical experiments, Sec. 4): Eq. def_Parareal with the coarse
  * solver G_i = one backward-Euler step of size M*dt over interval i, the

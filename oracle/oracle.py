@@ -83,10 +83,25 @@ def num_threads() -> int:
 # ----------------------------------------------------------------------------
 @dataclass
 class Tridiag:
-    """Tridiagonal A: row i is lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1]."""
+    """Tridiagonal A: row i is lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1].
+    stepper: the fine time stepper of `propagate` ("be" backward Euler,
+    "sdirk2", "sdirk2l": the SDIRK methods of Sec. 4)."""
     lo: np.ndarray
     di: np.ndarray
     up: np.ndarray
+    stepper: str = "be"
+
+    def matvec(self, X: np.ndarray, adjoint: bool = False) -> np.ndarray:
+        """A x (or A^T x) for every row x of X (nvec, n)."""
+        lo, di, up = _f64(self.lo), _f64(self.di), _f64(self.up)
+        Y = X * di
+        if not adjoint:
+            Y[:, 1:] += lo[1:] * X[:, :-1]
+            Y[:, :-1] += up[:-1] * X[:, 1:]
+        else:
+            Y[:, 1:] += up[:-1] * X[:, :-1]
+            Y[:, :-1] += lo[1:] * X[:, 1:]
+        return Y
 
     @property
     def n(self) -> int:
@@ -170,6 +185,9 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
     nvec, n = X.shape
     if nvec == 0:
         return X
+    if isinstance(op, Tridiag) and op.stepper != "be":
+        assert g is None, "the SDIRK steppers are used without source"
+        return propagate_sdirk(op, dt, M, X, op.stepper, adjoint)
     Q = 0
     gp = cp = None
     cstride = 0
@@ -197,6 +215,36 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
     if rc != 0:
         raise RuntimeError("oracle propagation failed (zero pivot)")
     return X
+
+
+def sdirk_tableau(scheme: str):
+    """Butcher tableaus (c, A, b) of the two SDIRK methods of Sec. 4 (effect of
+    the time discretisation)."""
+    if scheme == "sdirk2":
+        return np.array([1.0, 0.0]), np.array([[1.0, 0.0], [-1.0, 1.0]]), np.array([0.5, 0.5])
+    if scheme == "sdirk2l":
+        g = (2.0 - math.sqrt(2.0)) / 2.0
+        return np.array([g, 1.0]), np.array([[g, 0.0], [1.0 - g, g]]), np.array([1.0 - g, g])
+    raise ValueError(scheme)
+
+
+def propagate_sdirk(op: Tridiag, dt: float, M: int, X: np.ndarray, scheme: str,
+                    adjoint: bool = False) -> np.ndarray:
+    """M steps of a two-stage SDIRK method for u' = -A u on every row of X:
+    (I + a_ii dt A) K_i = -A (u + dt sum_{j<i} a_ij K_j),  u <- u + dt sum_i b_i K_i.
+    The step map is R(-dt A) (R the stability function), so the adjoint is the
+    same scheme with A^T."""
+    _, At, b = sdirk_tableau(scheme)
+    be = Tridiag(op.lo, op.di, op.up)
+    U = np.array(X, dtype=np.float64, copy=True)
+    for _ in range(M):
+        K = []
+        for i in range(2):
+            arg = U + dt * sum(At[i, j] * K[j] for j in range(i))
+            rhs = -op.matvec(arg, adjoint)
+            K.append(propagate(be, At[i, i] * dt, 1, rhs, adjoint))
+        U = U + dt * (b[0] * K[0] + b[1] * K[1])
+    return U
 
 
 def interval_cvals(c: Optional[np.ndarray], i: int, M: int) -> Optional[np.ndarray]:

@@ -64,6 +64,7 @@ class ServerStats(ctypes.Structure):
 
 LRP_PENDING = 8
 LRP_BUILD_INDEPENDENT_ADJOINT = 1   # flags of lrp_build_coarse_ex
+STEPPERS = {"be": 0, "sdirk2": 1, "sdirk2l": 2}   # lrp_stepper
 
 # (name, restype, argtypes)
 _P, _I, _D, _S, _U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_uint64
@@ -104,6 +105,7 @@ SIGNATURES = [
     ("lrp_parareal_solve", _I, [_P, _P, _P, _I, _P, _P, _I, _D, _P, _P, _PI,
                                 ctypes.POINTER(SolveStats)]),
     ("lrp_fine_solution", _I, [_P, _P, _D, _I, _I, _P, _I, _P, _P, _P]),
+    ("lrp_operator_set_stepper", _I, [_P, _I]),
     ("lrp_parareal_solve_classical", _I, [_P, _P, _D, _I, _I, _P, _I, _P, _P, _I, _D, _P, _P, _PI,
                                           ctypes.POINTER(SolveStats)]),
     ("lrp_build_coarse_batch", _I, [_P, _I, _P, _D, _I, _I, _I, _I, _U64, _I, _P]),

@@ -114,6 +114,10 @@ class Operator:
             return cls.tridiag(ctx, P.lo, P.di, P.up)
         return cls.stencil5(ctx, P.mx, P.my, P.st)
 
+    def set_stepper(self, stepper: str = "be"):
+        """Fine time stepper: "be" (backward Euler), "sdirk2", "sdirk2l"."""
+        check(self.ctx.lib.lrp_operator_set_stepper(self.h, nat.STEPPERS[stepper]), self.ctx.h)
+
     def krylov_iterations(self) -> int:
         return int(self.ctx.lib.lrp_operator_krylov_iterations(self.h))
 

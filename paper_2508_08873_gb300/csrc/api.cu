@@ -415,8 +415,52 @@ namespace lrp {
 lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
                              int prec, const PropIn& in, const PropOut& out, const PropSrc& src);
 
+StepCoef step_coefficients(int stepper) {
+  // Butcher tableaus of the two SDIRK methods of Sec. 4 (effect of the time
+  // discretisation): SDIRK2 with gamma = 1, a21 = -1, b = (1/2, 1/2);
+  // SDIRK2-L with gamma = (2 - sqrt 2)/2, a21 = 1 - gamma, b = (1 - gamma, gamma)
+  double g = 1.0, a21 = -1.0, b1 = 0.5, b2 = 0.5;
+  if (stepper == LRP_STEP_SDIRK2_L) {
+    g = (2.0 - std::sqrt(2.0)) / 2.0;
+    a21 = 1.0 - g;
+    b1 = 1.0 - g;
+    b2 = g;
+  }
+  StepCoef sc;
+  sc.gamma = g;
+  sc.su = 1.0 - a21 / g;
+  sc.s1 = a21 / g;
+  sc.bu = 1.0 - b1 / g - b2 / g + b2 * a21 / (g * g);
+  sc.b1 = b1 / g - b2 * a21 / (g * g);
+  sc.b2 = b2 / g;
+  return sc;
+}
+
 lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src) {
+  if (op->kind == 0 && op->stepper != 0) {
+    // SDIRK fine steps: two solves with B = I + gamma dt A per step on the
+    // one-CTA-per-system kernel (sources are not supported by these steppers)
+    if (src.Q > 0) return set_err(c, LRP_EINVAL, "SDIRK steppers support f = 0 only");
+    const double dtg = dt * step_coefficients(op->stepper).gamma;
+    // chunks of at most 8 rows (three chunk states in registers); one CTA per
+    // system while its factors fit in shared memory, else a 4-CTA cluster
+    const int m = op->n >= 32 ? 8 : 4;
+    const int P = (op->n + m - 1) / m;
+    int L = 0;
+    while ((1 << L) < P) ++L;
+    const size_t one_cta = (size_t)(prec == 0 ? 8 : 4) * ((size_t)5 * m * P + (size_t)(2 * L + 1) * P + 3 * P);
+    if (one_cta > 200 * 1024 && m == 8 && (P + 3) / 4 >= 32 && (P + 3) / 4 <= 256) {
+      ClPlan* cp = nullptr;
+      lrp_status s = tri_get_cluster_plan(c, op, dtg, adjoint, 4, 8, &cp);
+      if (s) return s;
+      return tri_propagate_cluster(c, cp, M, nsys, prec, 1, in, out, src, op->stepper);
+    }
+    TriPlan* plan = nullptr;
+    lrp_status s = tri_get_plan(c, op, dtg, adjoint, &plan, m);
+    if (s) return s;
+    return tri_propagate(c, op, plan, M, nsys, prec, in, out, src);
+  }
   if (op->kind == 0) {
     // Small batches of long systems: spread every system over a cluster of
     // C CTAs (chunks of m rows, spt systems per thread) so that more SMs take
@@ -1057,6 +1101,15 @@ __global__ static void k_cls_norms(const double* __restrict__ u, const double* _
     out[2 * m] = sqrt(a);
     out[2 * m + 1] = sqrt(b);
   }
+}
+
+lrp_status lrp_operator_set_stepper(lrp_operator* opc, int stepper) {
+  if (!opc || stepper < LRP_STEP_BACKWARD_EULER || stepper > LRP_STEP_SDIRK2_L) return LRP_EINVAL;
+  Operator* op = opc;
+  if (op->kind != 0 && stepper != LRP_STEP_BACKWARD_EULER)
+    return set_err(op->ctx, LRP_EINVAL, "SDIRK steppers are available for tridiagonal operators");
+  op->stepper = stepper;
+  return LRP_OK;
 }
 
 lrp_status lrp_parareal_solve_classical(lrp_ctx* c, const lrp_operator* opc, double dt, int M, int N,

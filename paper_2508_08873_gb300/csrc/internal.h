@@ -116,6 +116,7 @@ struct Operator {
   double rtol64 = 1e-12, rtol32 = 1e-6;
   int max_iter = 20000;
   bool symmetric = false;  // 5-point: CG when symmetric, else BiCGStab
+  int stepper = 0;         // fine time stepper: lrp_stepper (tridiagonal operators)
   std::mutex plan_mu;      // plan lookup/creation (a server thread may propagate too)
   std::vector<std::unique_ptr<TriPlan>> plans;
   std::vector<std::unique_ptr<ClPlan>> cplans;
@@ -151,6 +152,17 @@ lrp_status dev_alloc(Ctx* c, DevBuf& b, size_t bytes);
 bool is_device_ptr(const void* p);
 void timer_begin(Ctx* c, const char* fam, cudaEvent_t* ev);
 void timer_end(Ctx* c, const char* fam, cudaEvent_t ev);
+
+// ---- time steppers ----------------------------------------------------------
+// Two-stage SDIRK in stage-value form for u' = -A u (Butcher tableau
+// (gamma, a21, b1, b2), a11 = a22 = gamma): with B = I + gamma dt A,
+//   U1 = B^-1 u,  U2 = B^-1 (su u + s1 U1),  u_new = bu u + b1 U1 + b2 U2,
+// su = 1 - a21/gamma, s1 = a21/gamma (from dt K1 = (U1 - u)/gamma), and the
+// update u + dt (b1 K1 + b2 K2) written through U1, U2 likewise.
+struct StepCoef {
+  double gamma, su, s1, bu, b1, b2;
+};
+StepCoef step_coefficients(int stepper);
 
 // ---- tridiagonal propagator (tridiag.cu) -----------------------------------
 // m_req = 0: the default chunk size for n; else the requested rows per chunk.
@@ -207,7 +219,8 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
 lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, int m,
                                 ClPlan** out, int warp = 0);
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
-                                 const PropIn& in, const PropOut& out, const PropSrc& src);
+                                 const PropIn& in, const PropOut& out, const PropSrc& src,
+                                 int stepper = 0);
 
 // Allocation-free variant: factorisation into caller-provided scratch.
 size_t tri_raw_scratch_bytes(int n);

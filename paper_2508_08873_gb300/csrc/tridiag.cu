@@ -153,6 +153,10 @@ __global__ void __launch_bounds__(1024) k_tri_factor(const double* __restrict__ 
 struct TriKArgs {
   int n, P, L, G, M, nsys;
   double dt;
+  // two-stage SDIRK step (stepper != 0): with B = I + gamma dt A (the plan's
+  // matrix), U1 = B^-1 u, U2 = B^-1 (su u + s1 U1), u_new = bu u + b1 U1 + b2 U2
+  int stepper;
+  double su, s1, bu, b1, b2;
   const void* coef;
   const void* pcr;
   PropIn in;
@@ -162,7 +166,7 @@ struct TriKArgs {
 
 // At most 512 threads per CTA, so that up to 128 registers per thread keep the
 // whole chunk state (MM values) in registers.
-template <typename T, int MM>
+template <typename T, int MM, bool SDIRK = false>
 __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_coef = reinterpret_cast<T*>(smem_raw);                 // [5][MM][P]
@@ -215,19 +219,8 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
         ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
     const double* gsys = (active && a.src.Q > 0 && a.src.map)
         ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
-    // ---- M implicit-Euler steps ------------------------------------------
-    for (int j = 0; j < a.M; ++j) {
-      if (csys) {
-        for (int q = 0; q < a.src.Q; ++q) {
-          T cq_ = dt * (T)csys[(size_t)j * a.src.Q + q];
-          const double* gq = gsys + (size_t)q * n;
-#pragma unroll
-          for (int i = 0; i < MM; ++i) {
-            int r = r0 + i;
-            if (r < n) x[i] += cq_ * (T)gq[r];
-          }
-        }
-      }
+    // one solve with B = I + dt A (the plan's matrix), in place on x
+    auto solve = [&](T (&x)[MM]) {
       // interior forward elimination and back substitution: x[0..MM-2] := g
 #pragma unroll
       for (int i = 1; i < MM - 1; ++i) x[i] -= cl[i * P + t] * x[i - 1];
@@ -257,6 +250,38 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
 #pragma unroll
       for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - cp[i * P + t] * yl - cq[i * P + t] * y;
       x[MM - 1] = y;
+    };
+    // ---- M time steps ------------------------------------------------------
+    for (int j = 0; j < a.M; ++j) {
+      if constexpr (!SDIRK) {
+        // backward Euler with the source sampled at the step end
+        if (csys) {
+          for (int q = 0; q < a.src.Q; ++q) {
+            T cq_ = dt * (T)csys[(size_t)j * a.src.Q + q];
+            const double* gq = gsys + (size_t)q * n;
+#pragma unroll
+            for (int i = 0; i < MM; ++i) {
+              int r = r0 + i;
+              if (r < n) x[i] += cq_ * (T)gq[r];
+            }
+          }
+        }
+        solve(x);
+      } else {
+        // two-stage SDIRK, both stages with the same matrix (no source)
+        T u[MM], u1[MM];
+#pragma unroll
+        for (int i = 0; i < MM; ++i) u[i] = x[i];
+        solve(x);
+#pragma unroll
+        for (int i = 0; i < MM; ++i) {
+          u1[i] = x[i];
+          x[i] = (T)a.su * u[i] + (T)a.s1 * x[i];
+        }
+        solve(x);
+#pragma unroll
+        for (int i = 0; i < MM; ++i) x[i] = (T)a.bu * u[i] + (T)a.b1 * u1[i] + (T)a.b2 * x[i];
+      }
     }
     // ---- store -------------------------------------------------------------
     if (active) {
@@ -475,7 +500,7 @@ lrp_status tri_get_plan(Ctx* c, Operator* op, double dt, int adjoint, TriPlan** 
 }
 
 template <typename T, int MM>
-static lrp_status launch_tri(Ctx* c, TriPlan* plan, TriKArgs& a) {
+static lrp_status launch_tri(Ctx* c, TriPlan* plan, TriKArgs& a, bool sdirk = false) {
   const int P = a.P;
   // up to 256 threads per CTA: two CTAs share an SM, so one CTA's barriers
   // overlap the other's arithmetic (c->p_tri_group overrides, tuning)
@@ -485,7 +510,9 @@ static lrp_status launch_tri(Ctx* c, TriPlan* plan, TriKArgs& a) {
   int G = std::max(1, std::min(Gmax, a.nsys / std::max(1, c->num_sms)));
   a.G = G;
   size_t smem = sizeof(T) * ((size_t)5 * MM * P + (size_t)(2 * a.L + 1) * P + (size_t)G * 3 * P);
-  auto kern = k_tri_propagate<T, MM>;
+  // SDIRK instantiations only for chunks of up to 8 rows (three chunk states
+  // in registers); the backward-Euler kernels are unchanged
+  auto kern = (sdirk && MM <= 8) ? k_tri_propagate<T, (MM <= 8 ? MM : 8), true> : k_tri_propagate<T, MM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return cuda_err(c, e, "tri smem attribute");
   int per_sm = 0;
@@ -531,6 +558,13 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
                          const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (nsys <= 0) return LRP_OK;
   TriKArgs a{};
+  a.stepper = op->stepper;
+  if (op->stepper) {
+    if (plan->m > 8) return set_err(c, LRP_EINVAL, "SDIRK propagation needs a plan of 8-row chunks");
+    const StepCoef sc = step_coefficients(op->stepper);
+    a.su = sc.su; a.s1 = sc.s1; a.bu = sc.bu; a.b1 = sc.b1; a.b2 = sc.b2;
+  }
+  const bool sd = a.stepper != 0;
   a.n = plan->n;
   a.P = plan->P;
   a.L = plan->levels;
@@ -544,23 +578,23 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
     a.coef = plan->coef64.ptr;
     a.pcr = plan->pcr64.ptr;
     switch (plan->m) {
-      case 4: return launch_tri<double, 4>(c, plan, a);
-      case 8: return launch_tri<double, 8>(c, plan, a);
+      case 4: return launch_tri<double, 4>(c, plan, a, sd);
+      case 8: return launch_tri<double, 8>(c, plan, a, sd);
       case 16: return launch_tri<double, 16>(c, plan, a);
       default: return launch_tri<double, 32>(c, plan, a);
     }
   }
   a.coef = plan->coef32.ptr;
   a.pcr = plan->pcr32.ptr;
-  if (plan->m == 16 && plan->P <= 256 && plan->levels <= 8) {
+  if (plan->m == 16 && plan->P <= 256 && plan->levels <= 8 && a.stepper == 0) {
     // enough systems to fill the SMs with 4 per CTA, else 2 or 1
     if (nsys >= 4 * c->num_sms) return launch_tri_rc<float, 16, 8, 4>(c, a);
     if (nsys >= 2 * c->num_sms) return launch_tri_rc<float, 16, 8, 2>(c, a);
     return launch_tri_rc<float, 16, 8, 1>(c, a);
   }
   switch (plan->m) {
-    case 4: return launch_tri<float, 4>(c, plan, a);
-    case 8: return launch_tri<float, 8>(c, plan, a);
+    case 4: return launch_tri<float, 4>(c, plan, a, sd);
+    case 8: return launch_tri<float, 8>(c, plan, a, sd);
     case 16: return launch_tri<float, 16>(c, plan, a);
     default: return launch_tri<float, 32>(c, plan, a);
   }

@@ -243,6 +243,7 @@ __global__ void k_to_f32(const double* __restrict__ a, float* __restrict__ b, si
 struct ClKArgs {
   int n, Pc, C, L, M, nsys;
   double dt;
+  double su, s1, bu, b1, b2;   // two-stage SDIRK coefficients (see StepCoef)
   const void* coef;
   const void* lpcr;
   const void* spk;
@@ -256,7 +257,7 @@ struct ClKArgs {
 // lockstep, so that every thread has SPT independent dependency chains (FP64
 // latency is exposed with one warp per scheduler) and the factors read from
 // shared memory serve SPT systems.
-template <typename T, int MM, int SPT>
+template <typename T, int MM, int SPT, bool SDIRK = false>
 __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -327,19 +328,8 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
       gsys[s] = (act && a.src.Q > 0 && a.src.map)
           ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
     }
-    for (int j = 0; j < a.M; ++j) {
-#pragma unroll
-      for (int s = 0; s < SPT; ++s) {
-        if (csys[s]) {
-          for (int q = 0; q < a.src.Q; ++q) {
-            T cq_ = dt * (T)csys[s][(size_t)j * a.src.Q + q];
-            const double* gq = gsys[s] + (size_t)q * n;
-#pragma unroll
-            for (int i = 0; i < MM; ++i)
-              if (r0 + i < n) x[s][i] += cq_ * (T)gq[r0 + i];
-          }
-        }
-      }
+    // one solve with the plan's matrix, in place on x (one cluster barrier)
+    auto solve = [&](T (&x)[SPT][MM]) {
       // interior forward elimination and back substitution (SPT chains)
 #pragma unroll
       for (int i = 1; i < MM - 1; ++i) {
@@ -442,6 +432,44 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
         x[s][MM - 1] = y[s];
       }
       pb ^= 1;
+    };
+    for (int j = 0; j < a.M; ++j) {
+      if constexpr (!SDIRK) {
+#pragma unroll
+        for (int s = 0; s < SPT; ++s) {
+          if (csys[s]) {
+            for (int q = 0; q < a.src.Q; ++q) {
+              T cq_ = dt * (T)csys[s][(size_t)j * a.src.Q + q];
+              const double* gq = gsys[s] + (size_t)q * n;
+#pragma unroll
+              for (int i = 0; i < MM; ++i)
+                if (r0 + i < n) x[s][i] += cq_ * (T)gq[r0 + i];
+            }
+          }
+        }
+        solve(x);
+      } else {
+        // two-stage SDIRK, both stages with the same matrix (no source)
+        T u[SPT][MM], u1[SPT][MM];
+#pragma unroll
+        for (int s = 0; s < SPT; ++s)
+#pragma unroll
+          for (int i = 0; i < MM; ++i) u[s][i] = x[s][i];
+        solve(x);
+#pragma unroll
+        for (int s = 0; s < SPT; ++s)
+#pragma unroll
+          for (int i = 0; i < MM; ++i) {
+            u1[s][i] = x[s][i];
+            x[s][i] = (T)a.su * u[s][i] + (T)a.s1 * x[s][i];
+          }
+        solve(x);
+#pragma unroll
+        for (int s = 0; s < SPT; ++s)
+#pragma unroll
+          for (int i = 0; i < MM; ++i)
+            x[s][i] = (T)a.bu * u[s][i] + (T)a.b1 * u1[s][i] + (T)a.b2 * x[s][i];
+      }
     }
 #pragma unroll
     for (int s = 0; s < SPT; ++s) {
@@ -693,13 +721,13 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
   return LRP_OK;
 }
 
-template <typename T, int MM, int SPT>
+template <typename T, int MM, int SPT, bool SDIRK = false>
 static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   const int Pc = pl->Pc, L = pl->L, C = pl->C;
   size_t smem = sizeof(T) * ((size_t)5 * MM * Pc + (size_t)(2 * L + 1) * Pc + 2 * Pc +
                              6 * CL_MAXC + CL_MAXC * CL_MAXC + (size_t)SPT * 3 * Pc +
                              (size_t)SPT * CL_MAXC);
-  auto kern = k_tri_cluster<T, MM, SPT>;
+  auto kern = k_tri_cluster<T, MM, SPT, SDIRK>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e) return cuda_err(c, e, "cluster tri smem attribute");
   cudaLaunchConfig_t cfg = {};
@@ -762,7 +790,8 @@ static lrp_status launch_cl_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
 }
 
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
-                                 const PropIn& in, const PropOut& out, const PropSrc& src) {
+                                 const PropIn& in, const PropOut& out, const PropSrc& src,
+                                 int stepper) {
   if (nsys <= 0) return LRP_OK;
   ClKArgs a{};
   a.n = pl->n;
@@ -781,6 +810,12 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
   a.lpcr = b[1].ptr;
   a.spk = b[2].ptr;
   a.sup = b[3].ptr;
+  if (stepper) {
+    if (pl->warp || pl->m != 8) return set_err(c, LRP_EINVAL, "SDIRK cluster propagation needs 8-row chunks");
+    const StepCoef sc = step_coefficients(stepper);
+    a.su = sc.su; a.s1 = sc.s1; a.bu = sc.bu; a.b1 = sc.b1; a.b2 = sc.b2;
+    return f ? launch_cl<float, 8, 1, true>(c, pl, a) : launch_cl<double, 8, 1, true>(c, pl, a);
+  }
   if (pl->warp) {
     if (f || spt != 1) return set_err(c, LRP_EINVAL, "warp cluster kernel is FP64, one system per thread");
     return launch_cl_w(c, pl, a);

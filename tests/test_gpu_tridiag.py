@@ -9,7 +9,7 @@ the FP32 paths state theirs per test.
 import numpy as np
 import pytest
 
-from paper_2508_08873_gb300 import api, workloads as W
+from paper_2508_08873_gb300 import _native, api, workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -424,3 +424,49 @@ def test_build_two_sided_mixed_close_to_two_pass(ctx, orc):
     sig = (1.0 + P.dt * lam) ** (-P.M)
     for i in range(P.N):
         assert np.max(np.abs(info["sigma"][i, :4] - sig[:4])) <= 1e-4 * sig[0]
+
+
+# ---------------------------------------------------------------------------
+# SDIRK fine steppers (Sec. 4, effect of the time discretisation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+@pytest.mark.parametrize("n", [255, 4095])
+def test_sdirk_propagate_parity(ctx, orc, scheme, n):
+    lo, di, up = W.adr1d_op(n)
+    dt, M = 1.0 / 16384, 9
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    op.set_stepper(scheme)
+    oop = orc.Tridiag(lo, di, up, stepper=scheme)
+    X = np.random.default_rng(n).standard_normal((5, n))
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 8 * M * cond * 2.2e-16)
+    for adjoint in (False, True):
+        got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+        want = orc.propagate(oop, dt, M, X, adjoint=adjoint)
+        assert max(rel(got[v], want[v]) for v in range(5)) <= tol
+        got32 = api.propagate(ctx, op, dt, M, X[:2], adjoint=adjoint, prec="mixed")
+        assert max(rel(got32[v], want[v]) for v in range(2)) <= 5e-5
+    # the steppers take no source
+    with pytest.raises(_native.LrpError):
+        api.propagate(ctx, op, dt, M, X[:1], g=np.ones((1, n)), c=np.ones((M, 1)))
+
+
+def test_sdirk2l_build_and_parareal(ctx, orc):
+    """Low-rank Parareal with an SDIRK2-L fine solver: the build matches the
+    oracle's, and K = N reproduces the oracle's sequential SDIRK2-L solution."""
+    P = W.heat1d(n=127, N=6, M=16, R=5, p=3)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    op.set_stepper("sdirk2l")
+    oop = orc.Tridiag(P.lo, P.di, P.up, stepper="sdirk2l")
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    info = co.info()
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    for i in range(P.N):
+        oc = oco.intervals[i]
+        assert np.max(np.abs(info["sigma"][i, :oc.S.shape[0]] - oc.S)) <= 1e-9 * oc.sigma[0]
+    u, _ = api.parareal_solve(ctx, co, P.u0, K=P.N)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+    assert orc.rel_err(u, ref) <= 1e-10
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, K=2)
+    u2, _ = api.parareal_solve(ctx, co, P.u0, K=2)
+    assert rel(u2, res.iterates[-1]) <= 1e-10

@@ -153,3 +153,57 @@ def test_diff2d_constant_kappa_modes(orc):
         lam = kappa * 4 / h ** 2 * (np.sin(kx * np.pi * h / 2) ** 2 + np.sin(ky * np.pi * h / 2) ** 2) + 1.0
         out = orc.propagate(op, dt, M, v)
         np.testing.assert_allclose(out, (1 + dt * lam) ** (-M) * v, rtol=0, atol=1e-13 * np.abs(v).max())
+
+
+# ---------------------------------------------------------------------------
+# SDIRK fine steppers (Sec. 4, effect of the time discretisation)
+# ---------------------------------------------------------------------------
+def _stability(scheme, z, orc):
+    """R(z) = 1 + z b^T (I - z A)^-1 1 from the Butcher tableau."""
+    _, A, b = orc.sdirk_tableau(scheme)
+    return 1.0 + z * b @ np.linalg.solve(np.eye(2) - z * A, np.ones(2))
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_step_is_the_stability_function(orc, scheme):
+    """Scalar problem u' = -lam u: one step multiplies by R(-dt lam); the
+    limits at infinite stiffness are -1/2 (SDIRK2, not L-stable) and 0
+    (SDIRK2-L, L-stable)."""
+    for lam in (0.3, 7.0, 250.0, 1e6):
+        op = orc.Tridiag(np.zeros(1), np.array([lam]), np.zeros(1), stepper=scheme)
+        for dt in (0.01, 0.2):
+            got = orc.propagate(op, dt, 1, np.array([[1.0]]))[0, 0]
+            want = _stability(scheme, -dt * lam, orc)
+            assert abs(got - want) <= 1e-14 * max(1.0, abs(want))
+    op = orc.Tridiag(np.zeros(1), np.array([1e12]), np.zeros(1), stepper=scheme)
+    r_inf = orc.propagate(op, 1.0, 1, np.array([[1.0]]))[0, 0]
+    assert abs(r_inf - (-0.5 if scheme == "sdirk2" else 0.0)) <= 1e-9
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_second_order_on_heat(orc, scheme):
+    """Heat equation, one DST mode: the error of M steps against the exact
+    decay exp(-lam T) falls by ~4 when dt halves (second order), against ~2
+    for backward Euler."""
+    n = 63
+    lo, di, up = W.heat1d_op(n)
+    h = 1.0 / (n + 1)
+    x = np.arange(1, n + 1) * h
+    mode = np.sin(3 * np.pi * x)
+    lam = 4.0 / h ** 2 * np.sin(3 * np.pi * h / 2) ** 2
+    T = 0.01
+    errs = []
+    for M in (16, 32, 64):
+        op = orc.Tridiag(lo, di, up, stepper=scheme)
+        u = orc.propagate(op, T / M, M, mode)
+        errs.append(np.linalg.norm(u - np.exp(-lam * T) * mode) / np.linalg.norm(mode))
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_adjoint_is_transpose(orc, scheme):
+    n, dt, M = 30, 0.01, 3
+    op = orc.Tridiag(*W.adr1d_op(n, nu=0.05), stepper=scheme)
+    F = orc.propagate(op, dt, M, np.eye(n)).T
+    Ft = orc.propagate(op, dt, M, np.eye(n), adjoint=True).T
+    np.testing.assert_allclose(Ft, F.T, atol=1e-14 * np.abs(F).max())
