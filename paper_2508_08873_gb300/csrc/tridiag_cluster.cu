@@ -30,6 +30,7 @@ namespace cg = cooperative_groups;
 namespace lrp {
 
 constexpr int CL_MAXC = 16;
+static_assert(CL_MAXC == 16, "the one-warp kernel splits the warp into two halves of CL_MAXC lanes");
 
 // index helpers for the per-CTA layouts
 __host__ __device__ __forceinline__ size_t cl_coef(int c, int k, int i, int tl, int m, int Pc) {
@@ -537,14 +538,17 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
   }
   const double dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] : 0.0;
   const double p2 = gsp[tl], q2 = gsp[32 + tl];
-  // super system: row `tl` (lanes < C) and the inverse rows of CTAs c-1, c
-  const int q = tl;
+  // super system: both half-warps form row q = tl mod 16 (q < C); the lower
+  // half holds column q of inverse row c, the upper half column q of inverse
+  // row c-1, so one product and four butterfly levels give Y_c and Y_{c-1}
+  const int q = tl & (CL_MAXC - 1);
   const double sa = q < C ? gsu[6 * q + 0] : 0.0;
   const double sc1 = q < C ? gsu[6 * q + 1] : 0.0;
   const double sc2 = q < C ? gsu[6 * q + 2] : 0.0;
   const double* minv = gsu + 6 * CL_MAXC;
-  const double mc = q < C ? minv[c * CL_MAXC + q] : 0.0;
-  const double mcl = (q < C && c > 0) ? minv[(c - 1) * CL_MAXC + q] : 0.0;
+  const double msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
+                                            : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : 0.0))
+                            : 0.0;
   if (tl < C) rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
   __syncwarp();
   cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
@@ -618,18 +622,16 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
       double rhs = 0.0;
       if (q < C) {
         const double* pq = &pubg[pb][q][0];
-        rhs = pq[2] - sa * pq[1];
+        rhs = fma(-sa, pq[1], pq[2]);
         if (q + 1 < C) {
           const double* pn = &pubg[pb][q + 1][0];
-          rhs -= sc2 * pn[3] + sc1 * pn[0];
+          rhs = fma(-sc2, pn[3], fma(-sc1, pn[0], rhs));
         }
       }
-      double Yc = mc * rhs, Yl = mcl * rhs;
+      double Ys = msel * rhs;
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        Yc += __shfl_xor_sync(FULL, Yc, o);
-        Yl += __shfl_xor_sync(FULL, Yl, o);
-      }
+      for (int o = CL_MAXC / 2; o > 0; o >>= 1) Ys += __shfl_xor_sync(FULL, Ys, o);
+      const double Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
       const double y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
       double yl = __shfl_up_sync(FULL, y, 1);
       if (tl == 0) yl = Yl;
