@@ -86,8 +86,11 @@ long lrp_launch_count(lrp_ctx* ctx);
  *   "tri_cluster":   CTAs per tridiagonal system for small batches (1..8);
  *   "tri_chunk":     rows per chunk of the cluster tridiagonal kernel (8, 16);
  *   "tri_warp":      1 disables the one-warp-per-CTA FP64 cluster kernel that
- *                    small batches with n <= 4096 use by default, 2 uses it
- *                    for every FP64 batch with n <= 4096;
+ *                    FP64 batches with 2048 <= n <= 4096 and up to about 3.5
+ *                    warps per SM sub-partition use by default, 2 uses it for
+ *                    every FP64 batch with n <= 4096;
+ *   "tri_wchunk":    rows per chunk of the one-warp FP64 cluster kernel (8, 10,
+ *                    12 or 16; 0 = automatic);
  *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);
  *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
  *                    kernel (1..16, at most 512 threads per CTA);

@@ -2,7 +2,8 @@
 
 For a given coarse handle it times a short Parareal solve under each candidate
 setting of the tridiagonal cluster split (CTAs per system, rows per chunk,
-systems per thread) and of the coarse-sweep slice (rows per CTA), using the library's
+systems per thread, rows per chunk of the one-warp kernel) and of the
+coarse-sweep slice (rows per CTA), using the library's
 per-kernel CUDA-event timers, and leaves the fastest setting applied to the
 context.  Results are cached in memory per (n, N, precision, device name).
 Every candidate computes the same solution up to rounding; the tuner only
@@ -16,7 +17,9 @@ from . import api
 
 _CACHE: Dict[Tuple, Dict[str, int]] = {}
 
-TRI_CANDIDATES = ((0, 0, 0), (2, 16, 1), (2, 8, 2), (4, 8, 2), (4, 8, 1), (1, 16, 1))
+# (tri_cluster, tri_chunk, tri_spt, tri_wchunk); all zeros = the library's own rule
+TRI_CANDIDATES = ((0, 0, 0, 0), (0, 0, 0, 8), (0, 0, 0, 12), (0, 0, 0, 16), (2, 16, 1, 0),
+                  (2, 8, 2, 0), (4, 8, 2, 0), (4, 8, 1, 0), (1, 16, 1, 0))
 SWEEP_CANDIDATES = (0, 256, 2048)
 
 
@@ -43,9 +46,10 @@ def tune_solve(ctx: api.Context, co: api.Coarse, u0, K: int = 6,
         _apply(ctx, _CACHE[key])
         return dict(_CACHE[key])
     best: Optional[Tuple[float, Dict[str, int]]] = None
-    for (tc, m, spt) in tri:
+    for (tc, m, spt, wm) in tri:
         for sc in sweep:
-            params = {"tri_cluster": tc, "tri_chunk": m, "tri_spt": spt, "sweep_rows": sc}
+            params = {"tri_cluster": tc, "tri_chunk": m, "tri_spt": spt, "tri_wchunk": wm,
+                      "sweep_rows": sc}
             try:
                 _apply(ctx, params)
                 api.parareal_solve(ctx, co, u0, K=2, bounds=False)        # plans, warm-up
@@ -62,7 +66,7 @@ def tune_solve(ctx: api.Context, co: api.Coarse, u0, K: int = 6,
             if best is None or t < best[0]:
                 best = (t, params)
     if best is None:
-        params = {"tri_cluster": 0, "tri_chunk": 0, "tri_spt": 0, "sweep_rows": 0}
+        params = {"tri_cluster": 0, "tri_chunk": 0, "tri_spt": 0, "tri_wchunk": 0, "sweep_rows": 0}
     else:
         params = best[1]
     _apply(ctx, params)

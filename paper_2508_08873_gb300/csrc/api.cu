@@ -284,6 +284,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_chunk") {
     if (value != 0 && value != 8 && value != 16) return LRP_EINVAL;
     c->p_tri_chunk = value;
+  } else if (k == "tri_wchunk") {
+    if (value != 0 && value != 8 && value != 10 && value != 12 && value != 16) return LRP_EINVAL;
+    c->p_tri_wchunk = value;
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
     c->p_tri_group = value;
@@ -314,6 +317,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_warp") *value = c->p_tri_warp;
   else if (k == "tri_chunk") *value = c->p_tri_chunk;
   else if (k == "tri_group") *value = c->p_tri_group;
+  else if (k == "tri_wchunk") *value = c->p_tri_wchunk;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
 }
@@ -502,19 +506,35 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       if (c->p_tri_spt) spt = c->p_tri_spt;
       if (C > 1 && !fits(C, m)) { C = 1; }
     }
-    // FP64 small batches with n <= 4096: the one-warp-per-CTA cluster kernel
-    // (factors in registers, no block barrier; 32 chunks of 8 rows per CTA).
-    // Its step is shorter, but it executes more FP64 instructions per row than
-    // the block kernel: measured on GB300 (n = 4095, 256 steps) it is faster
-    // up to about 57 systems (0.79 ms at 4, 0.96 at 38, 1.27 at 57) and slower
-    // beyond (1.39 ms against 1.26-1.29 at 64).
-    const int Cw = ((op->n + 7) / 8 + 31) / 32;
-    const bool warp_ok = (long)nsys * Cw <= 57L * 16;
-    if (((C > 1 && c->p_tri_warp == 0 && warp_ok) || c->p_tri_warp == 2) && prec == 0 &&
-        c->p_tri_cluster == 0 && c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
+    // FP64 batches of up to ~3.5 warps per SM sub-partition with 2048 <= n <=
+    // 4096: the one-warp-per-CTA cluster kernel (factors in registers, no
+    // block barrier, 32 chunks per CTA).  Its time per step is the FP64 issue
+    // of one warp per sub-partition (64 cycles per FP64 warp instruction on
+    // GB300), so the chunk length trades the number of warps against the
+    // interface work per row.  Measured on GB300 (n = 4095, 256 steps, ms):
+    //   systems   8-row   10-row  12-row  16-row  one-CTA/4-CTA block
+    //   16        0.76    0.82    0.89    1.01    1.01
+    //   40        0.88    0.90    0.94    1.03    1.30
+    //   48        0.99    0.98    0.97    1.07    1.30
+    //   56        1.12    1.07    1.01    1.06    1.30
+    //   64        1.25    1.16    1.08    1.08    1.30
+    //   96        2.05    2.19    1.45    1.33    1.92
+    //   128       2.37    2.30    2.42    1.65    1.92
+    const int Cw8 = ((op->n + 7) / 8 + 31) / 32;
+    const double wpp = (double)nsys * Cw8 / (4.0 * c->num_sms);   // warps per sub-partition, 8-row chunks
+    const bool warp_auto = c->p_tri_warp == 0 && op->n >= 2048 && Cw8 <= 16 && wpp <= 3.5;
+    if ((warp_auto || c->p_tri_warp == 2) && prec == 0 && c->p_tri_cluster == 0 &&
+        c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
+      int mw = c->p_tri_wchunk;
+      if (!mw) mw = wpp <= 1.1 ? 8 : wpp <= 1.24 ? 10 : wpp <= 1.53 ? 12 : 16;
+      int Cw = ((op->n + mw - 1) / mw + 31) / 32;
+      if (Cw < 2 && c->p_tri_wchunk == 0) {
+        mw = 8;
+        Cw = Cw8;
+      }
       if (Cw >= 2 && Cw <= 16) {
         ClPlan* cp = nullptr;
-        lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, 8, &cp, 1);
+        lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, mw, &cp, 1);
         if (s) return s;
         return tri_propagate_cluster(c, cp, M, nsys, prec, 1, in, out, src);
       }

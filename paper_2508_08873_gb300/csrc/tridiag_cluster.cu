@@ -499,14 +499,13 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
 // interface system of a CTA is then solved by parallel cyclic reduction with
 // warp shuffles and the C x C super system by two warp sums, so a step needs
 // no block barrier at all: only the cluster barrier that publishes the four
-// values of every CTA.  (FP64, 8-row chunks.)
+// values of every CTA.  (FP64, chunks of MM = 8, 10, 12 or 16 rows.)
 // ---------------------------------------------------------------------------
-constexpr int CLW_MM = 8;
 constexpr int CLW_L = 5;    // PCR levels over the 31 local interface unknowns
 
+template <int MM>
 __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
   cg::cluster_group cl = cg::this_cluster();
-  constexpr int MM = CLW_MM;
   __shared__ double pubg[2][CL_MAXC][4];
   __shared__ double* rpub[CL_MAXC];
   const int C = a.C;
@@ -679,7 +678,8 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
   if (warp) {
     // one warp per CTA: exactly 32 chunks of 8 rows per CTA (padding chunks
     // are identity rows)
-    if (CL_M != CLW_MM || P > 32 * C) return set_err(c, LRP_EINVAL, "warp cluster plan out of range");
+    if ((CL_M != 8 && CL_M != 10 && CL_M != 12 && CL_M != 16) || P > 32 * C)
+      return set_err(c, LRP_EINVAL, "warp cluster plan out of range");
     P = 32 * C;
   }
   pl->P = P;
@@ -759,11 +759,13 @@ static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   return LRP_OK;
 }
 
+template <int MM>
 static lrp_status launch_cl_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
   const int C = pl->C;
+  auto kern = k_tri_cluster_w<MM>;
   cudaError_t e;
   if (C > 8) {
-    e = cudaFuncSetAttribute(k_tri_cluster_w, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e) return cuda_err(c, e, "cluster size 16 not available");
   }
   cudaLaunchConfig_t cfg = {};
@@ -779,13 +781,13 @@ static lrp_status launch_cl_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
   cfg.dynamicSmemBytes = 0;
   cfg.stream = c->stream;
   int maxc = 0;
-  e = cudaOccupancyMaxActiveClusters(&maxc, k_tri_cluster_w, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
   if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
   const int ncl = std::min(a.nsys, maxc);
   cfg.gridDim = dim3(ncl * C);
   cudaEvent_t ev = nullptr;
   timer_begin(c, "propagate_f64", &ev);
-  e = cudaLaunchKernelEx(&cfg, k_tri_cluster_w, a);
+  e = cudaLaunchKernelEx(&cfg, kern, a);
   timer_end(c, "propagate_f64", ev);
   if (e) return cuda_err(c, e, "k_tri_cluster_w launch");
   return LRP_OK;
@@ -820,7 +822,12 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
   }
   if (pl->warp) {
     if (f || spt != 1) return set_err(c, LRP_EINVAL, "warp cluster kernel is FP64, one system per thread");
-    return launch_cl_w(c, pl, a);
+    switch (pl->m) {
+      case 16: return launch_cl_w<16>(c, pl, a);
+      case 12: return launch_cl_w<12>(c, pl, a);
+      case 10: return launch_cl_w<10>(c, pl, a);
+      default: return launch_cl_w<8>(c, pl, a);
+    }
   }
   if (pl->m == 8) {
     if (spt == 2) return f ? launch_cl<float, 8, 2>(c, pl, a) : launch_cl<double, 8, 2>(c, pl, a);

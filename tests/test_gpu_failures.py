@@ -59,7 +59,7 @@ def test_autotune_picks_valid_parameters():
     co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, 0, prec="f64")
     ref, _ = api.parareal_solve(ctx, co, P.u0, K=3)
     best = autotune.tune_solve(ctx, co, P.u0, K=2)
-    assert set(best) == {"tri_cluster", "tri_chunk", "tri_spt", "sweep_rows"}
+    assert set(best) == {"tri_cluster", "tri_chunk", "tri_spt", "tri_wchunk", "sweep_rows"}
     for k, v in best.items():
         assert ctx.get_param(k) == v
     u, _ = api.parareal_solve(ctx, co, P.u0, K=3)

@@ -311,12 +311,13 @@ def test_sweep_slicing_does_not_change_the_iterates(ctx, orc):
     assert rel(u, res.iterates[-1]) <= 1e-10
 
 
+@pytest.mark.parametrize("wchunk", [0, 10, 12, 16])
 @pytest.mark.parametrize("n,nvec,Q", [(3000, 7, 2), (1025, 9, 0), (4096, 40, 1)])
-def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, Q):
-    """FP64 small batches with n <= 4096 run on the one-warp-per-CTA cluster
-    kernel (2..16 CTAs of 32 chunks); it agrees with the block kernel
-    (tri_warp = 1) to rounding and with the oracle, with and without a
-    source term, forward and adjoint."""
+def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, Q, wchunk):
+    """FP64 batches with n <= 4096 run on the one-warp-per-CTA cluster kernel
+    (2..16 CTAs of 32 chunks of 8, 10, 12 or 16 rows); it agrees with the
+    block kernel (tri_warp = 1) to rounding and with the oracle, with and
+    without a source term, forward and adjoint."""
     lo, di, up = W.adr1d_op(n)
     dt, M = 1.0 / 16384, 9
     op = api.Operator.tridiag(ctx, lo, di, up)
@@ -330,7 +331,13 @@ def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, 
     for adjoint in (False, True):
         if adjoint and Q:
             continue
-        got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c)
+        try:
+            ctx.set_param("tri_warp", 2)
+            ctx.set_param("tri_wchunk", wchunk)
+            got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c)
+        finally:
+            ctx.set_param("tri_warp", 0)
+            ctx.set_param("tri_wchunk", 0)
         try:
             ctx.set_param("tri_warp", 1)
             blk = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c)
