@@ -218,6 +218,14 @@ void lrp_coarse_free(lrp_coarse* co);
  * (Eq. bounds_delta_eps).  Any output pointer may be NULL. Host outputs. */
 lrp_status lrp_coarse_info(const lrp_coarse* co, int* R_i, int* rank_w, int* rank_v,
                            double* sigma, double* delta, double* eps);
+/* How the bases of rSVD steps 2 and 4 (Sec. 2.1, orthonormal bases of the
+ * sketches) were computed: tc_w / tc_v = number of intervals whose basis W /
+ * V^ came from CholeskyQR2 with the Gram products and triangular applies on
+ * the tensor cores (TF32 operands split into two terms, FP32 accumulation;
+ * mixed precision, sketch width <= 64, well-conditioned sketches); the other
+ * intervals used Gram-Schmidt applied twice with deflation.  Host outputs,
+ * either may be NULL. */
+lrp_status lrp_coarse_orth_method(const lrp_coarse* co, int* tc_w, int* tc_v);
 /* Copy the factors of interval i: U and V are R_i x n (row r = psi_r / phi_r),
  * S has R_i entries (host or device outputs). */
 lrp_status lrp_coarse_factors(const lrp_coarse* co, int interval, double* U, double* S,

@@ -99,6 +99,7 @@ SIGNATURES = [
     ("lrp_build_coarse_ex", _I, [_P, _P, _D, _I, _I, _I, _I, _U64, _I, _I, _PP]),
     ("lrp_coarse_free", None, [_P]),
     ("lrp_coarse_info", _I, [_P, _P, _P, _P, _P, _P, _P]),
+    ("lrp_coarse_orth_method", _I, [_P, _P, _P]),
     ("lrp_coarse_factors", _I, [_P, _I, _P, _P, _P]),
     ("lrp_coarse_export", _I, [_P, _P, _P, ctypes.POINTER(ctypes.c_uint64), _P, _P, _P, _P, _P, _P, _P]),
     ("lrp_coarse_import", _I, [_P, _P, _P, _P, _U64, _P, _P, _P, _P, _P, _P, _P, _PP]),

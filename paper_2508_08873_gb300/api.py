@@ -207,6 +207,15 @@ class Coarse:
                                            ctypes.addressof(e)), self.ctx.h)
         return dict(R=Ri, rank_w=rw, rank_v=rv, sigma=sig, delta=d.value, eps=e.value)
 
+    def orth_method(self) -> dict:
+        """Intervals whose bases (rSVD steps 2 and 4) came from CholeskyQR2
+        on the tensor cores; the rest used Gram-Schmidt twice."""
+        w = ctypes.c_int()
+        v = ctypes.c_int()
+        check(self.ctx.lib.lrp_coarse_orth_method(self.h, ctypes.addressof(w), ctypes.addressof(v)),
+              self.ctx.h)
+        return dict(tc_w=w.value, tc_v=v.value)
+
     def factors(self, i: int):
         Ri = int(self.info()["R"][i])
         U = np.zeros((Ri, self.op.n))

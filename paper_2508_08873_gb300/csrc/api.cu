@@ -284,6 +284,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_chunk") {
     if (value != 0 && value != 8 && value != 16) return LRP_EINVAL;
     c->p_tri_chunk = value;
+  } else if (k == "orth_tc") {
+    if (value != 0 && value != 1) return LRP_EINVAL;
+    c->p_orth_tc = value;
   } else if (k == "tri_wchunk") {
     if (value != 0 && value != 8 && value != 10 && value != 12 && value != 16) return LRP_EINVAL;
     c->p_tri_wchunk = value;
@@ -318,6 +321,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_chunk") *value = c->p_tri_chunk;
   else if (k == "tri_group") *value = c->p_tri_group;
   else if (k == "tri_wchunk") *value = c->p_tri_wchunk;
+  else if (k == "orth_tc") *value = c->p_orth_tc;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
 }
@@ -677,6 +681,17 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   if ((s = dev_alloc(c, st, sizeof(int)))) return s;
   if ((s = dev_alloc(c, Rid, sizeof(int) * N))) return s;
   cudaMemsetAsync(st.ptr, 0, sizeof(int), c->stream);
+  const double tau = f32 ? 2e-5 : 1e-13;
+  // workspace of the tensor-core orthonormalisation (FP32 sketches)
+  DevBuf ows, tcc;
+  if ((s = dev_alloc(c, tcc, 2 * sizeof(int)))) return s;
+  cudaMemsetAsync(tcc.ptr, 0, 2 * sizeof(int), c->stream);
+  if (orth_tc_applies(c, ell, !f32))
+    if ((s = dev_alloc(c, ows, orth_tc_workspace(c, N, ell, n)))) return s;
+  auto orth = [&](void* X, double* Rc, int* rk, int which) {
+    return orth_auto(c, N, ell, n, X, !f32, tau, Rc, rk, ows.ptr, ows.bytes, st.as<int>(),
+                     tcc.as<int>() + which);
+  };
   // step 1: Y = F' Omega, Omega generated in the kernel (N*ell systems)
   PropIn in;
   in.gen = 1;
@@ -689,7 +704,6 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   o.ldy = n;
   PropSrc nosrc;
   if ((s = propagate_any(c, op, dt, M, 0, N * ell, f32, in, o, nosrc))) return s;
-  const double tau = f32 ? 2e-5 : 1e-13;
   if (two_sided) {
     // F'^* on 2 l independent random vectors psi (Philox stream 3), with no
     // dependence on the forward sketch; Q = orth(Y); X^T = Z (Psi^T Q)^+T;
@@ -710,15 +724,15 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
     oa.y_f64 = !f32;
     oa.ldy = n;
     if ((s = propagate_any(c, op, dt, M, 1, N * ell2, f32, ina, oa, nosrc))) return s;
-    if ((s = orth_cgs2(c, N, ell, n, Y.ptr, !f32, tau, Rw.as<double>(), rw.as<int>()))) return s;
+    if ((s = orth(Y.ptr, Rw.as<double>(), rw.as<int>(), 0))) return s;
     if ((s = two_sided_core(c, N, ell, ell2, n, seed, f32, Y.ptr, rw.as<int>(), Z2.ptr, Z.ptr,
                             Bb.as<double>(), Cb.as<double>(), st.as<int>())))
       return s;
-    if ((s = orth_cgs2(c, N, ell, n, Z.ptr, !f32, tau, Rz.as<double>(), rv.as<int>()))) return s;
+    if ((s = orth(Z.ptr, Rz.as<double>(), rv.as<int>(), 1))) return s;
     cudaStreamSynchronize(c->stream);    // Z2, Bb, Cb are released here
   } else {
   // step 2: W = orth(Y), in place
-  if ((s = orth_cgs2(c, N, ell, n, Y.ptr, !f32, tau, Rw.as<double>(), rw.as<int>()))) return s;
+  if ((s = orth(Y.ptr, Rw.as<double>(), rw.as<int>(), 0))) return s;
   // step 3: Z = F'^* W
   PropIn in2;
   in2.x = Y.ptr;
@@ -730,7 +744,7 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   o2.ldy = n;
   if ((s = propagate_any(c, op, dt, M, 1, N * ell, f32, in2, o2, nosrc))) return s;
   // step 4: Vh = orth(Z) in place; M_ij = (z_i, v_j) = Rz[j][i]
-  if ((s = orth_cgs2(c, N, ell, n, Z.ptr, !f32, tau, Rz.as<double>(), rv.as<int>()))) return s;
+  if ((s = orth(Z.ptr, Rz.as<double>(), rv.as<int>(), 1))) return s;
   }
   // step 5: SVD of M
   if ((s = small_svd(c, N, ell, Rz.as<double>(), rv.as<int>(), sv.as<double>(), Psi.as<double>(),
@@ -745,8 +759,13 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   cudaMemcpyAsync(co->rank_v.data(), rv.ptr, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream);
   cudaMemcpyAsync(co->sigma.data(), sv.ptr, sizeof(double) * N * ell, cudaMemcpyDeviceToHost, c->stream);
   cudaMemcpyAsync(&svd_status, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  int tc_counts[2] = {0, 0};
+  cudaMemcpyAsync(tc_counts, tcc.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
+  co->orth_tc_w = tc_counts[0];
+  co->orth_tc_v = tc_counts[1];
   if (e) return cuda_err(c, e, "build_coarse");
+  if (svd_status & 4) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation failed");
   if (svd_status & 2) return set_err(c, LRP_EBREAKDOWN, "rank-deficient two-sided sketch core");
   if (svd_status) return set_err(c, LRP_ENOTCONV, "Jacobi SVD did not converge");
   co->Ri.resize(N);
@@ -803,6 +822,13 @@ void lrp_coarse_free(lrp_coarse* co) {
   cudaSetDevice(co->ctx->device);
   cudaStreamSynchronize(co->ctx->stream);
   delete co;
+}
+
+lrp_status lrp_coarse_orth_method(const lrp_coarse* co, int* tc_w, int* tc_v) {
+  if (!co) return LRP_EINVAL;
+  if (tc_w) *tc_w = co->orth_tc_w;
+  if (tc_v) *tc_v = co->orth_tc_v;
+  return LRP_OK;
 }
 
 lrp_status lrp_coarse_info(const lrp_coarse* co, int* R_i, int* rank_w, int* rank_v,

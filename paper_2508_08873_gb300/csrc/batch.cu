@@ -51,6 +51,7 @@ namespace {
 
 struct BuildScratch {
   DevBuf Y, Z, Rw, Rz, rw, rv, sv, Psi, Phi, st, Rid;
+  DevBuf ows, ost;    // tensor-core orthonormalisation workspace; status, counts of W, V^ intervals
 };
 
 }  // namespace
@@ -104,6 +105,10 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     if ((s = dev_alloc(c, b.Phi, 8 * (size_t)N * ell * ell))) return s;
     if ((s = dev_alloc(c, b.st, 4))) return s;
     if ((s = dev_alloc(c, b.Rid, 4 * (size_t)N))) return s;
+    if ((s = dev_alloc(c, b.ost, 3 * sizeof(int)))) return s;
+    cudaMemsetAsync(b.ost.ptr, 0, 3 * sizeof(int), c->stream);
+    if (orth_tc_applies(c, ell, !f32))
+      if ((s = dev_alloc(c, b.ows, orth_tc_workspace(c, N, ell, (int)n)))) return s;
     if ((s = dev_alloc(c, q->U, 8 * N * Rm * n))) return s;
     if ((s = dev_alloc(c, q->V, 8 * N * Rm * n))) return s;
     if ((s = dev_alloc(c, q->S, 8 * N * Rm))) return s;
@@ -175,15 +180,17 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
                                  d_cnt.as<unsigned int>(), ws.ptr, ws_stride, cs, nclu)))
       return r;
     for (int p = 0; p < count; ++p)
-      if ((r = orth_cgs2(c, N, ell, ops[p]->n, sc[p].Y.ptr, !f32, tau, sc[p].Rw.as<double>(),
-                         sc[p].rw.as<int>())))
+      if ((r = orth_auto(c, N, ell, ops[p]->n, sc[p].Y.ptr, !f32, tau, sc[p].Rw.as<double>(),
+                         sc[p].rw.as<int>(), sc[p].ows.ptr, sc[p].ows.bytes, sc[p].ost.as<int>(),
+                         sc[p].ost.as<int>() + 1)))
         return r;
     if ((r = krylov_queue_launch(c, f32, d_adj.as<KryArgs>(), d_items.as<int>(), nitems,
                                  d_cnt.as<unsigned int>() + 1, ws.ptr, ws_stride, cs, nclu)))
       return r;
     for (int p = 0; p < count; ++p) {
-      if ((r = orth_cgs2(c, N, ell, ops[p]->n, sc[p].Z.ptr, !f32, tau, sc[p].Rz.as<double>(),
-                         sc[p].rv.as<int>())))
+      if ((r = orth_auto(c, N, ell, ops[p]->n, sc[p].Z.ptr, !f32, tau, sc[p].Rz.as<double>(),
+                         sc[p].rv.as<int>(), sc[p].ows.ptr, sc[p].ows.bytes, sc[p].ost.as<int>(),
+                         sc[p].ost.as<int>() + 2)))
         return r;
       cudaMemsetAsync(sc[p].st.ptr, 0, 4, c->stream);
       if ((r = small_svd(c, N, ell, sc[p].Rz.as<double>(), sc[p].rv.as<int>(), sc[p].sv.as<double>(),
@@ -231,7 +238,12 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     cudaMemcpy(q->rank_v.data(), sc[p].rv.ptr, 4 * N, cudaMemcpyDeviceToHost);
     cudaMemcpy(q->sigma.data(), sc[p].sv.ptr, 8 * (size_t)N * ell, cudaMemcpyDeviceToHost);
     cudaMemcpy(q->Ri.data(), sc[p].Rid.ptr, 4 * N, cudaMemcpyDeviceToHost);
+    int orth_st[3] = {0, 0, 0};
     cudaMemcpy(&svd_st, sc[p].st.ptr, 4, cudaMemcpyDeviceToHost);
+    cudaMemcpy(orth_st, sc[p].ost.ptr, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (orth_st[0]) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation failed");
+    q->orth_tc_w = orth_st[1];
+    q->orth_tc_v = orth_st[2];
     if (svd_st) return set_err(c, LRP_ENOTCONV, "Jacobi SVD did not converge");
     q->delta = q->eps = 0.0;
     for (int i = 0; i < N; ++i) {

@@ -56,6 +56,7 @@ struct Ctx {
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
+  int p_orth_tc = 1;         // CholeskyQR2 on the tensor cores for FP32 sketches (1 on, 0 off)
   int p_tri_wchunk = 0;      // rows per chunk of the one-warp cluster kernel (0 auto, 8, 16)
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
   // Caching allocator: released buffers are kept (up to pool_cap bytes) and
@@ -139,6 +140,7 @@ struct Coarse {
   std::vector<int> Ri, rank_w, rank_v;
   std::vector<double> sigma;  // N x ell
   double delta = 0.0, eps = 0.0;
+  int orth_tc_w = 0, orth_tc_v = 0;   // intervals orthonormalised on the tensor cores (steps 2, 4)
   // solve workspace (allocated on first use)
   DevBuf Kc;               // [N-1][R][R] chain matrices of the coarse sweep
   DevBuf ws_u, ws_F, ws_b, ws_norm, ws_d, ws_g, ws_c;
@@ -265,8 +267,24 @@ lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const i
 lrp_status two_sided_core(Ctx* c, int N, int ell, int ell2, int n, uint64_t seed, int f32,
                           const void* Q, const int* rank_w, const void* Z, void* XT, double* Bbuf,
                           double* Cbuf, int* status);
+// skip: optional [N] flags; intervals with skip[i] != 0 are left untouched.
 lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau,
-                     double* Rcoef, int* rank);
+                     double* Rcoef, int* rank, const int* skip = nullptr);
+// CholeskyQR2 with the Gram products and triangular applies on the tensor
+// cores (orth_tc.cu) for FP32 blocks with ell <= 64; same outputs as
+// orth_cgs2.  Intervals whose scaled Gram is too ill-conditioned fall back to
+// CGS2.  ws: orth_tc_workspace() bytes of device memory (allocated by the
+// caller, so that the call can be captured in a graph); status: device int,
+// bit 4 set when a tensor-core step failed (an mbarrier wait gave up or the
+// second pass broke down); tc_count (device int, optional) is incremented
+// once per interval orthonormalised on the tensor cores.
+bool orth_tc_applies(Ctx* c, int ell, int x_f64);
+size_t orth_tc_workspace(Ctx* c, int N, int ell, int n);
+lrp_status orth_tc(Ctx* c, int N, int ell, int n, float* X, double tau, double* Rcoef, int* rank,
+                   void* ws, size_t ws_bytes, int* status, int* tc_count = nullptr);
+// orth_tc when it applies and ws is large enough, else orth_cgs2.
+lrp_status orth_auto(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau, double* Rcoef,
+                     int* rank, void* ws, size_t ws_bytes, int* status, int* tc_count = nullptr);
 // One-sided Jacobi SVD of M_i = Rz_i^T (ell x ell) for every interval.
 // Outputs: s [N][ell] descending, Psi [N][ell][ell] (column r = left vector r,
 // stored Psi[i*ell + r]), Phi [N][ell][ell] likewise; status (int) 0/1.

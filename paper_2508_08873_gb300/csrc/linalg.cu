@@ -44,7 +44,9 @@ __device__ double block_sum(T v, double* red) {
 template <typename T>
 __global__ void __launch_bounds__(ORTH_THREADS) k_cgs2(int ell, int n, T* __restrict__ X,
                                                         double tau, double* __restrict__ Rcoef,
-                                                        int* __restrict__ rank) {
+                                                        int* __restrict__ rank,
+                                                        const int* __restrict__ skip) {
+  if (skip && skip[blockIdx.x]) return;
   extern __shared__ double sm[];
   const int nw = blockDim.x >> 5;
   double* red1 = sm;                // [nw] block-sum scratch
@@ -121,8 +123,12 @@ struct OrthRed {
 template <typename T>
 __global__ void __launch_bounds__(ORTH_THREADS) k_cgs2_cl(int ell, int n, T* __restrict__ X,
                                                            double tau, double* __restrict__ Rcoef,
-                                                           int* __restrict__ rank) {
+                                                           int* __restrict__ rank,
+                                                           const int* __restrict__ skip) {
   cg::cluster_group cl = cg::this_cluster();
+  // every CTA of a cluster serves the same interval, so a skipped interval
+  // leaves the kernel before any cluster barrier
+  if (skip && skip[blockIdx.x / cl.num_blocks()]) return;
   extern __shared__ __align__(16) unsigned char orth_smem[];
   __shared__ OrthRed sh;
   __shared__ T hT[ORTHC_MAXV];
@@ -235,7 +241,7 @@ __global__ void __launch_bounds__(ORTH_THREADS) k_cgs2_cl(int ell, int n, T* __r
 }
 
 lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau,
-                     double* Rcoef, int* rank) {
+                     double* Rcoef, int* rank, const int* skip) {
   if (N <= 0) return LRP_OK;
   // shared-memory cluster variant when the interval's block fits in at most
   // 16 CTAs of 200 KB (1D problems); the one-CTA kernel otherwise
@@ -264,13 +270,13 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
       if (!e && C > 8) e = cudaFuncSetAttribute(k_cgs2_cl<double>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e) return cuda_err(c, e, "cgs2 cluster attributes");
       timer_begin(c, "orth", &ev);
-      e = cudaLaunchKernelEx(&cfg, k_cgs2_cl<double>, ell, n, (double*)X, tau, Rcoef, rank);
+      e = cudaLaunchKernelEx(&cfg, k_cgs2_cl<double>, ell, n, (double*)X, tau, Rcoef, rank, skip);
     } else {
       e = cudaFuncSetAttribute(k_cgs2_cl<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (!e && C > 8) e = cudaFuncSetAttribute(k_cgs2_cl<float>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
       if (e) return cuda_err(c, e, "cgs2 cluster attributes");
       timer_begin(c, "orth", &ev);
-      e = cudaLaunchKernelEx(&cfg, k_cgs2_cl<float>, ell, n, (float*)X, tau, Rcoef, rank);
+      e = cudaLaunchKernelEx(&cfg, k_cgs2_cl<float>, ell, n, (float*)X, tau, Rcoef, rank, skip);
     }
     timer_end(c, "orth", ev);
     return e ? cuda_err(c, e, "k_cgs2_cl") : LRP_OK;
@@ -280,9 +286,9 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
   cudaEvent_t ev = nullptr;
   timer_begin(c, "orth", &ev);
   if (x_f64)
-    k_cgs2<double><<<N, ORTH_THREADS, smem, c->stream>>>(ell, n, (double*)X, tau, Rcoef, rank);
+    k_cgs2<double><<<N, ORTH_THREADS, smem, c->stream>>>(ell, n, (double*)X, tau, Rcoef, rank, skip);
   else
-    k_cgs2<float><<<N, ORTH_THREADS, smem, c->stream>>>(ell, n, (float*)X, tau, Rcoef, rank);
+    k_cgs2<float><<<N, ORTH_THREADS, smem, c->stream>>>(ell, n, (float*)X, tau, Rcoef, rank, skip);
   cudaError_t e = cudaGetLastError();
   timer_end(c, "orth", ev);
   return e ? cuda_err(c, e, "k_cgs2") : LRP_OK;

@@ -1,0 +1,95 @@
+"""Tensor-core orthonormalisation (rSVD steps 2 and 4, Sec. 2.1) of the mixed
+mode: CholeskyQR2 with tcgen05 Gram products and triangular applies in
+error-corrected TF32, and its fall-back to Gram-Schmidt applied twice for
+ill-conditioned sketches.  Checked against the FP64 oracle's randomized SVD
+(the coarse operators G_n' on probe vectors, as for the other mixed builds)
+and against the same build with the tensor-core path switched off."""
+import numpy as np
+import pytest
+
+from paper_2508_08873_gb300 import api, workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = api.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def orc():
+    from oracle import oracle
+    return oracle
+
+
+def _operator(U, S, V):
+    return U.T @ np.diag(S) @ V
+
+
+def _build(ctx, op, P, tc):
+    try:
+        ctx.set_param("orth_tc", tc)
+        return api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed")
+    finally:
+        ctx.set_param("orth_tc", 1)
+
+
+@pytest.mark.parametrize("R,p,n,N,M", [(8, 4, 1023, 16, 64), (32, 10, 1023, 128, 8),
+                                        (16, 8, 4095, 64, 256)])
+def test_tensor_core_orth_matches_oracle_and_cgs2(ctx, orc, R, p, n, N, M):
+    """Sketch widths 12, 42 (two K blocks of the apply) and 24 (the full
+    advection-diffusion-reaction configuration), with spectra that decay
+    slowly enough for CholeskyQR2: every interval takes the tensor-core path,
+    and on sampled intervals its coarse operators are within 1e-4 sigma_1 of
+    the FP64 oracle's and within 2e-5 sigma_1 of the Gram-Schmidt build."""
+    P = W.adr1d(n=n, N=N, M=M, R=R, p=p)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = _build(ctx, op, P, 1)
+    ref = _build(ctx, op, P, 0)
+    assert co.orth_method() == {"tc_w": P.N, "tc_v": P.N}
+    assert ref.orth_method() == {"tc_w": 0, "tc_v": 0}
+    inf, rinf = co.info(), ref.info()
+    assert np.all(inf["rank_w"] == R + p) and np.all(inf["rank_v"] == R + p)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    probes = np.random.default_rng(3).standard_normal((3, P.n))
+    for i in sorted({0, 1, P.N // 2, P.N - 1}):
+        oc = orc.rsvd_interval(oop, P.dt, P.M, i, P.R, P.p, P.seed)
+        s1 = oc.sigma[0]
+        G = _operator(*co.factors(i))
+        Go = oc.U @ np.diag(oc.S) @ oc.V.T
+        Gr = _operator(*ref.factors(i))
+        for x in probes:
+            assert np.linalg.norm((G - Go) @ x) <= 1e-4 * s1 * np.linalg.norm(x)
+            assert np.linalg.norm((G - Gr) @ x) <= 2e-5 * s1 * np.linalg.norm(x)
+        assert np.max(np.abs(inf["sigma"][i] - oc.sigma)) <= 1e-4 * s1
+        assert np.max(np.abs(inf["sigma"][i] - rinf["sigma"][i])) <= 2e-5 * s1
+
+
+def test_tensor_core_orth_falls_back_on_rank_deficient_sketches(ctx):
+    """heat1d: sigma_9 / sigma_1 ~ 1e-16, so the sketches are numerically rank
+    deficient; the conditioning test sends every interval to Gram-Schmidt
+    with deflation and the build equals the one with the path switched off."""
+    P = W.heat1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = _build(ctx, op, P, 1)
+    ref = _build(ctx, op, P, 0)
+    assert co.orth_method() == {"tc_w": 0, "tc_v": 0}
+    a, b = co.info(), ref.info()
+    assert np.array_equal(a["rank_w"], b["rank_w"]) and np.array_equal(a["rank_v"], b["rank_v"])
+    np.testing.assert_array_equal(a["sigma"], b["sigma"])
+
+
+def test_tensor_core_orth_parareal_to_tolerance(ctx, orc):
+    """A mixed-mode Parareal solve on coarse solvers built on the tensor cores
+    reaches the oracle's sequential FP64 fine solution to 1e-8."""
+    P = W.adr1d(n=1023, N=16, M=64, R=8, p=4)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = _build(ctx, op, P, 1)
+    assert co.orth_method()["tc_w"] == P.N
+    u, info = api.parareal_solve(ctx, co, P.u0, K=P.N, tol=1e-9)
+    ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0)
+    assert info["converged"]
+    assert orc.rel_err(u, ref) <= 1e-8
