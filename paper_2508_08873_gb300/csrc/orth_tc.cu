@@ -175,26 +175,38 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(const float* __restrict_
   const float* Xi = X + (size_t)iv * ell * n;
   const uint32_t idesc = idesc_tf32(TILE_ROWS, NB);
   // commit j (the MMAs of block j) arrives on mbar[j & 1], completing its
-  // phase (j >> 1) & 1; thread 0 waits for the commits in issue order
+  // phase (j >> 1) & 1; thread 0 waits for the commits in issue order.
+  // Thread t loads column k = t mod 32 of rows t/32, t/32 + 4, ...; the
+  // values of the next two blocks are in flight in registers while a block
+  // is staged and multiplied.
+  const int kc = tid & 31, rg = tid >> 5;
+  const int nrow = (ell - rg + 3) / 4;            // rows of this thread (<= 16)
+  auto load = [&](float* v, int b) {
+    const int col = k0 + b * 32 + kc;
+    const bool in = b < nb && col < k1;
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = (in && j < nrow) ? Xi[(size_t)(rg + 4 * j) * n + col] : 0.f;
+  };
   int issued = 0, waited = 0;
-  for (int b = 0; b < nb; ++b) {
+  auto stage = [&](const float* v, int b) -> bool {
     const int s = b & 1;
     if (b >= 2) {
       // the MMAs of block b-2 read this stage
       if (tid == 0 && !mbar_wait(saddr(&mbar[s]), (uint32_t)(((b - 2) >> 1) & 1))) sfail = 1;
       waited = b - 1;
       __syncthreads();
-      if (sfail) break;
+      if (sfail) return false;
     }
     unsigned char* hi = base + s * 2 * TILE_BYTES;
     unsigned char* lo = hi + TILE_BYTES;
-    const int kb = k0 + b * 32;
-    for (int idx = tid; idx < ell * 32; idx += TC_THREADS) {
-      const int r = idx >> 5, k = idx & 31;
-      const float v = (kb + k < k1) ? Xi[(size_t)r * n + kb + k] : 0.f;
-      const float h = tf32_hi(v);
-      *reinterpret_cast<float*>(hi + sw128(r, k)) = h;
-      *reinterpret_cast<float*>(lo + sw128(r, k)) = v - h;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      if (j < nrow) {
+        const float h = tf32_hi(v[j]);
+        *reinterpret_cast<float*>(hi + sw128(rg + 4 * j, kc)) = h;
+        *reinterpret_cast<float*>(lo + sw128(rg + 4 * j, kc)) = v[j] - h;
+      }
     }
     fence_async_smem();
     __syncthreads();
@@ -211,6 +223,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_gram_tc(const float* __restrict_
       mma_commit(saddr(&mbar[s]));
     }
     issued = b + 1;
+    return true;
+  };
+  float va[16], vb[16];
+  load(va, 0);
+  load(vb, 1);
+  for (int b = 0; b < nb; b += 2) {
+    if (!stage(va, b)) break;
+    load(va, b + 2);
+    if (b + 1 < nb) {
+      if (!stage(vb, b + 1)) break;
+      load(vb, b + 3);
+    }
   }
   // every commit still outstanding (also after a failed wait: the tensor
   // memory is released only once the MMAs that write it are done)
@@ -274,13 +298,20 @@ __global__ void __launch_bounds__(TC_THREADS) k_apply_tc(float* __restrict__ X, 
   if (warp == 0) tmem_alloc(saddr(&tslot));
   float* Xi = X + (size_t)iv * ell * n;
   const int gi = i0 + tid;                                  // this thread's row of A
-#pragma unroll 4
-  for (int k = 0; k < KB * 32; ++k) {
-    const float v = (k < ell && gi < n) ? Xi[(size_t)k * n + gi] : 0.f;
-    const float h = tf32_hi(v);
-    unsigned char* t = A + (k >> 5) * 2 * TILE_BYTES;
-    *reinterpret_cast<float*>(t + sw128(tid, k & 31)) = h;
-    *reinterpret_cast<float*>(t + TILE_BYTES + sw128(tid, k & 31)) = v - h;
+#pragma unroll
+  for (int k0 = 0; k0 < KB * 32; k0 += 16) {
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = (k0 + j < ell && gi < n) ? Xi[(size_t)(k0 + j) * n + gi] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = k0 + j;
+      const float h = tf32_hi(v[j]);
+      unsigned char* t = A + (k >> 5) * 2 * TILE_BYTES;
+      *reinterpret_cast<float*>(t + sw128(tid, k & 31)) = h;
+      *reinterpret_cast<float*>(t + TILE_BYTES + sw128(tid, k & 31)) = v[j] - h;
+    }
   }
   const int KP = KB * 32;
   const float* Ti = Tb + (size_t)iv * 2 * NB * KP;
@@ -359,6 +390,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_cholqr_small(int ell, int S, int
   double* A = small_smem;                 // [ell][ell + 1]
   double* Li = A + (size_t)ell * ld;      // [ell][ell + 1]
   __shared__ double dsc[TC_MAXL];
+  __shared__ double rinv[TC_MAXL];           // 1 / L_jj
   __shared__ double red[SM_THREADS / 32];
   __shared__ int sok;
   __shared__ double anorm;
@@ -412,10 +444,12 @@ __global__ void __launch_bounds__(SM_THREADS) k_cholqr_small(int ell, int S, int
         sok = 0;
         p = 1.0;
       }
-      A[(size_t)(j) * ld + (j)] = sqrt(p);
+      const double l = sqrt(p);
+      A[(size_t)(j) * ld + (j)] = l;
+      rinv[j] = 1.0 / l;
     }
     __syncthreads();
-    const double rl = 1.0 / A[(size_t)(j) * ld + (j)];
+    const double rl = rinv[j];
     for (int i = j + 1 + tid; i < ell; i += SM_THREADS) A[(size_t)(i) * ld + (j)] *= rl;
     __syncthreads();
     const int m = ell - j - 1;
@@ -430,7 +464,7 @@ __global__ void __launch_bounds__(SM_THREADS) k_cholqr_small(int ell, int S, int
     double x0 = lane == c ? 1.0 : 0.0, x1 = lane + 32 == c ? 1.0 : 0.0;
     for (int k = c; k < ell; ++k) {
       double xk = k < 32 ? __shfl_sync(FULL, x0, k) : __shfl_sync(FULL, x1, k - 32);
-      xk /= A[(size_t)(k) * ld + (k)];
+      xk *= rinv[k];
       if (lane == (k & 31)) {
         if (k < 32) x0 = xk; else x1 = xk;
       }
@@ -567,6 +601,7 @@ lrp_status orth_tc(Ctx* c, int N, int ell, int n, float* X, double tau, double* 
   }
   e = cudaGetLastError();
   timer_end(c, "orth", ev);
+  c->launches += 5;    // six launches above, one counted by timer_end
   if (e) return cuda_err(c, e, "tensor-core orthonormalisation");
   // intervals the test sent back: CGS2 with deflation on their untouched blocks
   return orth_cgs2(c, N, ell, n, X, 0, tau, Rcoef, rank, act);
