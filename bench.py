@@ -38,6 +38,7 @@ import numpy as np  # noqa: E402
 METRIC = "Parareal solves/s at 1e-8 rel err vs FP64 oracle"
 UNIT = "solves/s"
 TOL = 1e-8
+F64_DRAM_BYTES_PER_SYSTEM = 2.26e6 / 61
 WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
 
 
@@ -49,6 +50,10 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--prec", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="time only the headline step (no amortised, classical, two-sided or "
+                         "host-buffer legs): the launch list of a profiler then holds the "
+                         "warm-up and timed steps alone")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the cpu_baseline sample")
     ap.add_argument("--mode", default="solve", choices=["solve", "serve", "krylov"],
@@ -314,6 +319,84 @@ def run_krylov(args):
     print(json.dumps(line), flush=True)
 
 
+def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
+    """The legs beside the headline: solves on prebuilt coarse solvers, the
+    classical comparator, the two-sided sketch build and the host-buffer (e2e)
+    timing through the C ABI."""
+    import torch
+    from paper_2508_08873_gb300 import api
+    # amortised (serving view): solves only, coarse solvers built once
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=args.prec)
+    torch.cuda.synchronize()
+    a0 = torch.cuda.Event(enable_timing=True)
+    a1 = torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    for _ in range(args.steps):
+        api.parareal_solve(ctx, co, u0_d, K=P.N, tol=TOL, out=out_d, bounds=False)
+    a1.record(stream)
+    torch.cuda.synchronize()
+    amort = 1000.0 * args.steps / a0.elapsed_time(a1)
+    # comparison: classical Parareal (one backward-Euler coarse step per
+    # interval), same fine solver, stopped on its increment at the same tol
+    cls_out = torch.empty_like(out_d)
+    api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, u0_d, K=P.N, tol=TOL, out=cls_out)
+    torch.cuda.synchronize()
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    _, cls_info = api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, u0_d, K=P.N, tol=TOL,
+                                               out=cls_out)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    cls_ms = c0.elapsed_time(c1)
+    # variant of Sec. 2.2: adjoint sketch on independent random vectors
+    ts_out = torch.empty_like(out_d)
+
+    def step_two_sided():
+        co2 = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=args.prec,
+                         independent_adjoint=True)
+        u2, inf2 = api.parareal_solve(ctx, co2, u0_d, K=P.N, tol=TOL, out=ts_out, bounds=False)
+        co2.close()
+        return inf2
+    step_two_sided()
+    torch.cuda.synchronize()
+    d0 = torch.cuda.Event(enable_timing=True)
+    d1 = torch.cuda.Event(enable_timing=True)
+    d0.record(stream)
+    ts_info = step_two_sided()
+    d1.record(stream)
+    torch.cuda.synchronize()
+    ts_ms = d0.elapsed_time(d1)
+    # ---- e2e: host buffers through the C ABI ---------------------------------
+    u0_h = torch.tensor(P.u0, dtype=torch.float64).pin_memory()
+    out_h = torch.empty((P.N + 1, P.n), dtype=torch.float64).pin_memory()
+    lo_h, di_h, up_h = (torch.tensor(a, dtype=torch.float64).pin_memory() for a in (P.lo, P.di, P.up))
+    e2e_ms = []
+    for s in range(max(2, args.steps // 2)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        op_h = api.Operator.tridiag(ctx, lo_h.numpy(), di_h.numpy(), up_h.numpy())
+        info_h = step(op_h, u0_h.numpy(), out_h.numpy())
+        op_h.close()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+    return {"amortised_solves_per_s": amort * world,
+            "two_sided_sketch": {"iterations": ts_info["k_done"], "solves_per_s": 1000.0 / ts_ms,
+                                 "rel_err_vs_oracle": None,
+                                 "note": "build_coarse with F'^* on 2(R+p) independent random "
+                                         "vectors (Sec. 2.2 variant) + the same solve"},
+            "classical_parareal": {"iterations": cls_info["k_done"],
+                                   "solves_per_s": 1000.0 / cls_ms,
+                                   "rel_err_vs_oracle": None,
+                                   "note": "one backward-Euler coarse step per interval, "
+                                           "stopped on its increment at the same tol"},
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (P.n + 3 * P.n),
+                    "d2h_bytes_per_step": 8 * (P.N + 1) * P.n},
+            "cls_out": cls_out, "ts_out": ts_out}
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -393,70 +476,21 @@ def main():
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms_step = float(t.item())
     value = world * 1000.0 / ms_step
-    # amortised (serving view): solves only, coarse solvers built once
-    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=args.prec)
-    torch.cuda.synchronize()
-    a0 = torch.cuda.Event(enable_timing=True)
-    a1 = torch.cuda.Event(enable_timing=True)
-    a0.record(stream)
-    for _ in range(args.steps):
-        api.parareal_solve(ctx, co, u0_d, K=P.N, tol=TOL, out=out_d, bounds=False)
-    a1.record(stream)
-    torch.cuda.synchronize()
-    amort = 1000.0 * args.steps / a0.elapsed_time(a1)
-    # comparison: classical Parareal (one backward-Euler coarse step per
-    # interval), same fine solver, stopped on its increment at the same tol
-    cls_out = torch.empty_like(out_d)
-    api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, u0_d, K=P.N, tol=TOL, out=cls_out)
-    torch.cuda.synchronize()
-    c0 = torch.cuda.Event(enable_timing=True)
-    c1 = torch.cuda.Event(enable_timing=True)
-    c0.record(stream)
-    _, cls_info = api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, u0_d, K=P.N, tol=TOL,
-                                               out=cls_out)
-    c1.record(stream)
-    torch.cuda.synchronize()
-    cls_ms = c0.elapsed_time(c1)
-    # variant of Sec. 2.2: adjoint sketch on independent random vectors
-    ts_out = torch.empty_like(out_d)
-
-    def step_two_sided():
-        co2 = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec=args.prec,
-                         independent_adjoint=True)
-        u2, inf2 = api.parareal_solve(ctx, co2, u0_d, K=P.N, tol=TOL, out=ts_out, bounds=False)
-        co2.close()
-        return inf2
-    step_two_sided()
-    torch.cuda.synchronize()
-    d0 = torch.cuda.Event(enable_timing=True)
-    d1 = torch.cuda.Event(enable_timing=True)
-    d0.record(stream)
-    ts_info = step_two_sided()
-    d1.record(stream)
-    torch.cuda.synchronize()
-    ts_ms = d0.elapsed_time(d1)
-    # ---- e2e: host buffers through the C ABI ---------------------------------
-    u0_h = torch.tensor(P.u0, dtype=torch.float64).pin_memory()
-    out_h = torch.empty((P.N + 1, P.n), dtype=torch.float64).pin_memory()
-    lo_h, di_h, up_h = (torch.tensor(a, dtype=torch.float64).pin_memory() for a in (P.lo, P.di, P.up))
-    e2e_ms = []
-    for s in range(max(2, args.steps // 2)):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        op_h = api.Operator.tridiag(ctx, lo_h.numpy(), di_h.numpy(), up_h.numpy())
-        info_h = step(op_h, u0_h.numpy(), out_h.numpy())
-        op_h.close()
-        e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+    if args.headline_only:
+        extras = None
+    else:
+        extras = run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world)
     # ---- accuracy of the timed solve vs the oracle's sequential fine solution -
-    err = cls_err = ts_err = None
+    err = None
     if rank == 0:
         from oracle import oracle as orc
         ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0)
         err = orc.rel_err(out_d.cpu().numpy(), ref)
-        cls_err = orc.rel_err(cls_out.cpu().numpy(), ref)
-        ts_err = orc.rel_err(ts_out.cpu().numpy(), ref)
+        if extras is not None:
+            extras["classical_parareal"]["rel_err_vs_oracle"] = orc.rel_err(
+                extras.pop("cls_out").cpu().numpy(), ref)
+            extras["two_sided_sketch"]["rel_err_vs_oracle"] = orc.rel_err(
+                extras.pop("ts_out").cpu().numpy(), ref)
     # ---- roofline of the dominant kernel ---------------------------------------
     fam = max(("propagate_f64", "propagate_f32"), key=lambda f: kern[f][1])
     nl, tot = kern[fam]
@@ -469,8 +503,16 @@ def main():
     launches_per_step = nl / args.steps
     achieved = flops_step / (tot / args.steps) / 1e6 if tot > 0 else 0.0   # GFLOP/s
     peak = FP64_PEAK_GFLOPS if fam == "propagate_f64" else FP32_PEAK_GFLOPS
+    # DRAM traffic of the FP64 fine-solve kernel, from one ncu capture on GB300
+    # (dram__bytes_read.sum + dram__bytes_write.sum of a 61-system launch of
+    # the 16-row-chunk variant: 2.26 MB read, nothing written back within the
+    # launch), per propagated system, times this run's systems per launch
+    traffic = None
+    if fam == "propagate_f64" and launches_per_step > 0:
+        traffic = F64_DRAM_BYTES_PER_SYSTEM * systems_per_step / launches_per_step
     roof = {"bound": "alu", "kernel": fam, "achieved": achieved / 1e3, "peak": peak / 1e3,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "algorithmic_bytes": 16.0 * P.n * systems_per_step / max(launches_per_step, 1),
             "launches_per_step": launches_per_step,
             "share_of_step": (tot / args.steps) / ms_step,
             "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe: 1.195 TFLOP/s); "
@@ -494,19 +536,7 @@ def main():
                            "l2": "flushed (256 MB write) between timed steps",
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
                 "iterations": k_list[-1], "rel_err_vs_oracle": err,
-                "amortised_solves_per_s": amort * world,
-                "two_sided_sketch": {"iterations": ts_info["k_done"], "solves_per_s": 1000.0 / ts_ms,
-                                     "rel_err_vs_oracle": ts_err,
-                                     "note": "build_coarse with F'^* on 2(R+p) independent random "
-                                             "vectors (Sec. 2.2 variant) + the same solve"},
-                "classical_parareal": {"iterations": cls_info["k_done"],
-                                       "solves_per_s": 1000.0 / cls_ms,
-                                       "rel_err_vs_oracle": cls_err,
-                                       "note": "one backward-Euler coarse step per interval, "
-                                               "stopped on its increment at the same tol"},
-                "e2e": {"value": e2e_val, "unit": UNIT,
-                        "h2d_bytes_per_step": 8 * (P.n + 3 * P.n),
-                        "d2h_bytes_per_step": 8 * (P.N + 1) * P.n},
+                **(extras or {"e2e": None}),
                 "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
                 "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu,
                 "wall_s_timed": t_wall}

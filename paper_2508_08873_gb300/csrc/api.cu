@@ -797,10 +797,17 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   cudaMemsetAsync(co->U32.ptr, 0, co->U32.bytes, c->stream);
   cudaMemsetAsync(co->V32.ptr, 0, co->V32.bytes, c->stream);
   if ((s = to_device(c, Rid.ptr, co->Ri.data(), sizeof(int) * N))) return s;
-  if ((s = lift(c, N, ell, rank, n, Y.ptr, Z.ptr, !f32, Psi.as<double>(), Phi.as<double>(),
-                Rid.as<int>(), co->U.as<double>(), co->V.as<double>(), co->U32.as<float>(),
-                co->V32.as<float>())))
+  const bool ltc = lift_tc_applies(c, ell, rank, !f32);
+  if (ltc) {
+    if ((s = lift_tc(c, N, ell, rank, n, Y.as<float>(), Z.as<float>(), Psi.as<double>(),
+                     Phi.as<double>(), Rid.as<int>(), co->U.as<double>(), co->V.as<double>(),
+                     co->U32.as<float>(), co->V32.as<float>(), st.as<int>())))
+      return s;
+  } else if ((s = lift(c, N, ell, rank, n, Y.ptr, Z.ptr, !f32, Psi.as<double>(), Phi.as<double>(),
+                       Rid.as<int>(), co->U.as<double>(), co->V.as<double>(), co->U32.as<float>(),
+                       co->V32.as<float>()))) {
     return s;
+  }
   std::vector<double> S64((size_t)N * Rm, 0.0);
   std::vector<float> S32f((size_t)N * Rm, 0.f);
   for (int i = 0; i < N; ++i)
@@ -811,8 +818,10 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   if ((s = to_device(c, co->S.ptr, S64.data(), S64.size() * 8))) return s;
   if ((s = to_device(c, co->S32.ptr, S32f.data(), S32f.size() * 4))) return s;
   if ((s = coarse_chain(c, co.get()))) return s;
+  if (ltc) cudaMemcpyAsync(&svd_status, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "build_coarse");
+  if (ltc && (svd_status & 4)) return set_err(c, LRP_EBREAKDOWN, "tensor-core lift failed");
   *out = co.release();
   return LRP_OK;
 }

@@ -202,10 +202,18 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
           sc[p].Rid.as<int>(), q->S.as<double>(), q->S32.as<float>());
       cudaMemsetAsync(q->U.ptr, 0, q->U.bytes, c->stream);
       cudaMemsetAsync(q->V.ptr, 0, q->V.bytes, c->stream);
-      if ((r = lift(c, N, ell, rank, ops[p]->n, sc[p].Y.ptr, sc[p].Z.ptr, !f32, sc[p].Psi.as<double>(),
-                    sc[p].Phi.as<double>(), sc[p].Rid.as<int>(), q->U.as<double>(), q->V.as<double>(),
-                    q->U32.as<float>(), q->V32.as<float>())))
+      if (lift_tc_applies(c, ell, rank, !f32)) {
+        if ((r = lift_tc(c, N, ell, rank, ops[p]->n, sc[p].Y.as<float>(), sc[p].Z.as<float>(),
+                         sc[p].Psi.as<double>(), sc[p].Phi.as<double>(), sc[p].Rid.as<int>(),
+                         q->U.as<double>(), q->V.as<double>(), q->U32.as<float>(),
+                         q->V32.as<float>(), sc[p].ost.as<int>())))
+          return r;
+      } else if ((r = lift(c, N, ell, rank, ops[p]->n, sc[p].Y.ptr, sc[p].Z.ptr, !f32,
+                           sc[p].Psi.as<double>(), sc[p].Phi.as<double>(), sc[p].Rid.as<int>(),
+                           q->U.as<double>(), q->V.as<double>(), q->U32.as<float>(),
+                           q->V32.as<float>()))) {
         return r;
+      }
     }
     return LRP_OK;
   };
@@ -241,7 +249,7 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     int orth_st[3] = {0, 0, 0};
     cudaMemcpy(&svd_st, sc[p].st.ptr, 4, cudaMemcpyDeviceToHost);
     cudaMemcpy(orth_st, sc[p].ost.ptr, 3 * sizeof(int), cudaMemcpyDeviceToHost);
-    if (orth_st[0]) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation failed");
+    if (orth_st[0]) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation or lift failed");
     q->orth_tc_w = orth_st[1];
     q->orth_tc_v = orth_st[2];
     if (svd_st) return set_err(c, LRP_ENOTCONV, "Jacobi SVD did not converge");

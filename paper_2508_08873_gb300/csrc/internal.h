@@ -56,7 +56,7 @@ struct Ctx {
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
-  int p_orth_tc = 1;         // CholeskyQR2 on the tensor cores for FP32 sketches (1 on, 0 off)
+  int p_orth_tc = 1;         // tensor-core CholeskyQR2 and lift for FP32 sketches (1 on, 0 off)
   int p_tri_wchunk = 0;      // rows per chunk of the one-warp cluster kernel (0 auto, 8, 16)
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
   // Caching allocator: released buffers are kept (up to pool_cap bytes) and
@@ -282,6 +282,12 @@ bool orth_tc_applies(Ctx* c, int ell, int x_f64);
 size_t orth_tc_workspace(Ctx* c, int N, int ell, int n);
 lrp_status orth_tc(Ctx* c, int N, int ell, int n, float* X, double tau, double* Rcoef, int* rank,
                    void* ws, size_t ws_bytes, int* status, int* tc_count = nullptr);
+// Lift of step 6 on the tensor cores (FP32 bases, ell <= 64, R <= 64); same
+// outputs as lift(); status bit 4 on a failed mbarrier wait.
+bool lift_tc_applies(Ctx* c, int ell, int R, int b_f64);
+lrp_status lift_tc(Ctx* c, int N, int ell, int R, int n, const float* W, const float* Vh,
+                   const double* Psi, const double* Phi, const int* Ri, double* U, double* V,
+                   float* U32, float* V32, int* status);
 // orth_tc when it applies and ws is large enough, else orth_cgs2.
 lrp_status orth_auto(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau, double* Rcoef,
                      int* rank, void* ws, size_t ws_bytes, int* status, int* tc_count = nullptr);

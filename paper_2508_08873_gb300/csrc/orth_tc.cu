@@ -24,9 +24,12 @@
 // TC_KAPPA_MAX (rank-deficient sketches of quickly decaying spectra) is left
 // untouched here and orthonormalised by CGS2 with deflation instead.
 //
+// The lift of step 6 (U = W Psi, V = V^ Phi restricted to the leading R
+// singular vectors) is the same contraction and runs on the same path.
+//
 // Shared-memory operands are K-major tiles of 32 FP32 values (128 bytes) per
 // row with the 128-byte swizzle; every MMA is M = 128 (rows beyond the data
-// are zero), N = the padded sketch width, K = 8.
+// are zero), N = the padded sketch width or rank, K = 8.
 #include <algorithm>
 #include <cmath>
 
@@ -368,6 +371,117 @@ __global__ void __launch_bounds__(TC_THREADS) k_apply_tc(float* __restrict__ X, 
 }
 
 // ---------------------------------------------------------------------------
+// Lift of rSVD step 6 on the tensor cores: for the 128 columns i0.. of
+// interval iv, out[c][i] = sum_k X[k][i] Bsrc[c][k] for c < R (Bsrc = Psi or
+// Phi, FP64 rows of length ell, split into TF32 (hi, lo) pairs here), written
+// in FP64 and FP32; rows c >= Ri[iv] are zero.  blockIdx.z = 0: U from W and
+// Psi, 1: V from V^ and Phi.
+// ---------------------------------------------------------------------------
+template <int KB>
+__global__ void __launch_bounds__(TC_THREADS) k_lift_tc(int ell, int R, int n, int NB,
+                                                        const float* __restrict__ W,
+                                                        const float* __restrict__ Vh,
+                                                        const double* __restrict__ Psi,
+                                                        const double* __restrict__ Phi,
+                                                        const int* __restrict__ Ri,
+                                                        double* __restrict__ U, double* __restrict__ V,
+                                                        float* __restrict__ U32, float* __restrict__ V32,
+                                                        int* __restrict__ status) {
+  extern __shared__ unsigned char tc_smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ int sfail;
+  const int iv = blockIdx.y, i0 = blockIdx.x * TILE_ROWS, z = blockIdx.z;
+  const float* X = (z ? Vh : W) + (size_t)iv * ell * n;
+  const double* Bs = (z ? Phi : Psi) + (size_t)iv * ell * ell;
+  double* out = (z ? V : U) + (size_t)iv * R * n;
+  float* out32 = (z ? V32 : U32) + (size_t)iv * R * n;
+  const int rk = min(R, Ri[iv]);
+  unsigned char* base = align1024(tc_smem);
+  unsigned char* A = base;                                  // [KB][hi, lo] x TILE_BYTES
+  unsigned char* B = base + KB * 2 * TILE_BYTES;            // [KB][hi, lo] x NB * 128
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (tid == 0) {
+    mbar_init(saddr(&mbar));
+    sfail = 0;
+  }
+  if (warp == 0) tmem_alloc(saddr(&tslot));
+  const int gi = i0 + tid;
+#pragma unroll
+  for (int k0 = 0; k0 < KB * 32; k0 += 16) {
+    float v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+      v[j] = (k0 + j < ell && gi < n) ? X[(size_t)(k0 + j) * n + gi] : 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int k = k0 + j;
+      const float h = tf32_hi(v[j]);
+      unsigned char* t = A + (k >> 5) * 2 * TILE_BYTES;
+      *reinterpret_cast<float*>(t + sw128(tid, k & 31)) = h;
+      *reinterpret_cast<float*>(t + TILE_BYTES + sw128(tid, k & 31)) = v[j] - h;
+    }
+  }
+  const int KP = KB * 32;
+  for (int idx = tid; idx < NB * KP; idx += TC_THREADS) {
+    const int cc = idx / KP, k = idx % KP;
+    const float b = (cc < rk && k < ell) ? (float)Bs[(size_t)cc * ell + k] : 0.f;
+    const float h = tf32_hi(b);
+    unsigned char* t = B + (k >> 5) * 2 * (NB * 128);
+    *reinterpret_cast<float*>(t + sw128(cc, k & 31)) = h;
+    *reinterpret_cast<float*>(t + NB * 128 + sw128(cc, k & 31)) = b - h;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_tf32(TILE_ROWS, NB);
+#pragma unroll
+    for (int kb = 0; kb < KB; ++kb) {
+      const uint32_t ah = saddr(A + kb * 2 * TILE_BYTES), al = ah + TILE_BYTES;
+      const uint32_t bh = saddr(B + kb * 2 * NB * 128), bl = bh + NB * 128;
+#pragma unroll
+      for (int kk = 0; kk < 4; ++kk) {
+        mma_tf32(tmem, sdesc(ah + kk * 32), sdesc(bh + kk * 32), idesc, (kb | kk) != 0);
+        mma_tf32(tmem, sdesc(ah + kk * 32), sdesc(bl + kk * 32), idesc, 1u);
+        mma_tf32(tmem, sdesc(al + kk * 32), sdesc(bh + kk * 32), idesc, 1u);
+      }
+    }
+    mma_commit(saddr(&mbar));
+    if (!mbar_wait(saddr(&mbar), 0)) {
+      sfail = 1;
+      mbar_wait(saddr(&mbar), 0);
+    }
+  }
+  __syncthreads();
+  tc_fence_after();
+  if (!sfail) {
+    for (int cb = 0; cb < NB / 16; ++cb) {
+      float v[16];
+      tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(cb * 16), v);
+      if (gi < n) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int cc = cb * 16 + j;
+          if (cc < R) {
+            const float val = cc < rk ? v[j] : 0.f;
+            out[(size_t)cc * n + gi] = (double)val;
+            out32[(size_t)cc * n + gi] = val;
+          }
+        }
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(status, 4);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_free(tmem);
+}
+
+// ---------------------------------------------------------------------------
 // Per interval, FP64: sum of the Gram partials, diagonal scaling, Cholesky,
 // L^-1, the condition test and the factors.  pass 1: active[iv] <- test,
 // R1 = L^T D^-1, Tb = D L^-T; pass 2 (intervals with active = 1):
@@ -605,6 +719,35 @@ lrp_status orth_tc(Ctx* c, int N, int ell, int n, float* X, double tau, double* 
   if (e) return cuda_err(c, e, "tensor-core orthonormalisation");
   // intervals the test sent back: CGS2 with deflation on their untouched blocks
   return orth_cgs2(c, N, ell, n, X, 0, tau, Rcoef, rank, act);
+}
+
+bool lift_tc_applies(Ctx* c, int ell, int R, int b_f64) {
+  return !b_f64 && ell >= 1 && ell <= TC_MAXL && R >= 1 && R <= TC_MAXL && c->p_orth_tc != 0;
+}
+
+lrp_status lift_tc(Ctx* c, int N, int ell, int R, int n, const float* W, const float* Vh,
+                   const double* Psi, const double* Phi, const int* Ri, double* U, double* V,
+                   float* U32, float* V32, int* status) {
+  if (N <= 0 || R <= 0) return LRP_OK;
+  if (ell > TC_MAXL || R > TC_MAXL) return set_err(c, LRP_EINVAL, "tensor-core lift: width above 64");
+  const int NB = (R + 15) / 16 * 16, KB = (ell + 31) / 32;
+  const size_t smem = (size_t)KB * 2 * TILE_BYTES + (size_t)KB * 2 * NB * 128 + 1024;
+  cudaError_t e = KB == 1
+      ? cudaFuncSetAttribute(k_lift_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+      : cudaFuncSetAttribute(k_lift_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e) return cuda_err(c, e, "tensor-core lift attributes");
+  const dim3 grid((n + TILE_ROWS - 1) / TILE_ROWS, N, 2);
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "lift", &ev);
+  if (KB == 1)
+    k_lift_tc<1><<<grid, TC_THREADS, smem, c->stream>>>(ell, R, n, NB, W, Vh, Psi, Phi, Ri, U, V, U32,
+                                                        V32, status);
+  else
+    k_lift_tc<2><<<grid, TC_THREADS, smem, c->stream>>>(ell, R, n, NB, W, Vh, Psi, Phi, Ri, U, V, U32,
+                                                        V32, status);
+  e = cudaGetLastError();
+  timer_end(c, "lift", ev);
+  return e ? cuda_err(c, e, "k_lift_tc") : LRP_OK;
 }
 
 lrp_status orth_auto(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau, double* Rcoef,
