@@ -296,10 +296,17 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
 
 // ---------------------------------------------------------------------------
 // One-sided Jacobi SVD of M (ell rows x kv columns), M[i][c] = Rz[c][i].
-// Column pairs are rotated in round-robin order, one warp per pair, until a
-// full sweep performs no rotation (|a_p.a_q| <= m eps sqrt(|a_p|^2 |a_q|^2)).
+// Column pairs are rotated in round-robin order until a full sweep performs
+// no rotation (|a_p.a_q| <= m eps sqrt(|a_p|^2 |a_q|^2)).  Eight lanes serve
+// one pair, four pairs per warp: an FP64 warp instruction costs the same
+// issue time on GB300 whatever the number of active lanes, so the rotation
+// parameters (divisions and square roots) are computed once per eight lanes
+// rather than once per warp.  The squared column norms are carried through
+// the rotations (|a_p'|^2 = |a_p|^2 - t a_p.a_q, |a_q'|^2 = |a_q|^2 +
+// t a_p.a_q) and recomputed from the columns at the start of every sweep,
+// so a round needs one dot product per pair.
 // ---------------------------------------------------------------------------
-constexpr int SVD_THREADS = 1024;   // launch: one warp per column pair of a round
+constexpr int SVD_THREADS = 512;    // launch: 32 * ceil(pairs / 4) threads
 constexpr int SVD_MAX_SWEEPS = 60;
 
 __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* __restrict__ Rz,
@@ -325,7 +332,11 @@ __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* _
   for (int k = threadIdx.x; k < ell * ell; k += blockDim.x)
     Vw[k] = ((k / ell) == (k % ell)) ? 1.0 : 0.0;
   __syncthreads();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int l8 = lane & 7;                        // lane within the pair's group
+  const int slot = w * 4 + (lane >> 3);           // pair slot of this group
+  const unsigned gmask = 0xffu << (lane & 24);    // the group's lanes
+  const int nslots = (blockDim.x >> 5) * 4;
   const int kp = kv + (kv & 1);       // players, padded to even
   // convergence: every pair's cosine below m * eps (the usual one-sided
   // Jacobi threshold); a stricter eps keeps rotating on rounding noise
@@ -333,9 +344,14 @@ __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* _
   int sweep = 0, done = (kv < 2);
   while (!done && sweep < SVD_MAX_SWEEPS) {
     if (threadIdx.x == 0) rotated = 0;
+    for (int c = threadIdx.x; c < kv; c += blockDim.x) {
+      double t = 0.0;
+      for (int i = 0; i < m; ++i) t = fma(A[(size_t)c * m + i], A[(size_t)c * m + i], t);
+      nrm[c] = t;
+    }
     __syncthreads();
     for (int rd = 0; rd < kp - 1; ++rd) {
-      for (int pi = w; pi < kp / 2; pi += nw) {
+      for (int pi = slot; pi < kp / 2; pi += nslots) {
         int p, q;
         if (pi == 0) { p = kp - 1; q = rd; }
         else { p = (rd + pi) % (kp - 1); q = (rd - pi + (kp - 1)) % (kp - 1); }
@@ -343,31 +359,34 @@ __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* _
         if (q >= kv) continue;
         double* ap = A + (size_t)p * m;
         double* aq = A + (size_t)q * m;
-        double al = 0, be = 0, ga = 0;
-        for (int i = lane; i < m; i += 32) {
-          al += ap[i] * ap[i];
-          be += aq[i] * aq[i];
-          ga += ap[i] * aq[i];
-        }
-        al = warp_sum(al); be = warp_sum(be); ga = warp_sum(ga);
+        double ga = 0.0;
+        for (int i = l8; i < m; i += 8) ga = fma(ap[i], aq[i], ga);
+        ga += __shfl_xor_sync(gmask, ga, 4);
+        ga += __shfl_xor_sync(gmask, ga, 2);
+        ga += __shfl_xor_sync(gmask, ga, 1);
+        const double al = nrm[p], be = nrm[q];
         if (ga == 0.0 || fabs(ga) <= eps * sqrt(al * be)) continue;
-        double zeta = (be - al) / (2.0 * ga);
-        double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        double cs = 1.0 / sqrt(1.0 + tt * tt);
-        double sn = cs * tt;
-        for (int i = lane; i < m; i += 32) {
-          double x = ap[i], y = aq[i];
+        const double zeta = (be - al) / (2.0 * ga);
+        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        const double cs = rsqrt(fma(tt, tt, 1.0));
+        const double sn = cs * tt;
+        for (int i = l8; i < m; i += 8) {
+          const double x = ap[i], y = aq[i];
           ap[i] = cs * x - sn * y;
           aq[i] = sn * x + cs * y;
         }
         double* vp = Vw + (size_t)p * ell;
         double* vq = Vw + (size_t)q * ell;
-        for (int i = lane; i < kv; i += 32) {
-          double x = vp[i], y = vq[i];
+        for (int i = l8; i < kv; i += 8) {
+          const double x = vp[i], y = vq[i];
           vp[i] = cs * x - sn * y;
           vq[i] = sn * x + cs * y;
         }
-        if (lane == 0) rotated = 1;
+        if (l8 == 0) {
+          nrm[p] = fma(-tt, ga, al);
+          nrm[q] = fma(tt, ga, be);
+          rotated = 1;
+        }
       }
       __syncthreads();
     }
@@ -417,7 +436,8 @@ lrp_status small_svd(Ctx* c, int N, int ell, const double* Rz, const int* rank_v
   if (e) return cuda_err(c, e, "jacobi smem");
   cudaEvent_t ev = nullptr;
   timer_begin(c, "svd", &ev);
-  const int threads = std::min(SVD_THREADS, 32 * std::max(1, (ell + 1) / 2));
+  const int pairs = std::max(1, (ell + 1) / 2);
+  const int threads = std::min(SVD_THREADS, 32 * ((pairs + 3) / 4));
   k_jacobi<<<N, threads, smem, c->stream>>>(ell, Rz, rank_v, s, Psi, Phi, status);
   e = cudaGetLastError();
   timer_end(c, "svd", ev);
