@@ -14,7 +14,8 @@
 // handle.  The sequential dependence of the sweep is then an R-dimensional
 // recurrence; everything of size n runs in parallel over all intervals:
 //   1. project:  a_{i+1} = V_{i+1}^T r_i for every interval (all SMs);
-//   2. recur:    c_{i+1} = a_{i+1} + K_i c_i (one CTA, FP64, R x R steps);
+//   2. recur:    c_{i+1} = a_{i+1} + K_i c_i (one CTA, R x R steps, in the
+//                precision of the coarse apply);
 //   3. apply:    u^k_{i+1} = F_i u^{k-1}_i + U_i (S_i * c_i) for every
 //                interval, with the norms; then the bound recurrence.
 // Steps 1+2 and 3+bound are one launch each: the CTA that finishes a launch's
@@ -33,7 +34,7 @@ namespace lrp {
 constexpr int CSW_THREADS = 256;
 constexpr int CSW_MAXROWS = 2048;    // rows per slice (upper limit)
 constexpr int CSW_MAXR = 64;
-constexpr int CSW_KBUF = 32 * 1024;  // bytes of K staged per chunk of the recurrence
+constexpr int CSW_KBUF = 96 * 1024;  // bytes of K staged per chunk of the recurrence
 constexpr int CSW_MAXN = 8192;       // intervals + 1 (norms staged in shared memory)
 
 // Workspace of one problem (doubles): a-partials [N][nsl][R], coefficients
@@ -71,7 +72,7 @@ template <typename TF>
 __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __restrict__ args) {
   extern __shared__ __align__(16) unsigned char csw_smem[];
   __shared__ TF vs[CSW_MAXROWS];
-  __shared__ double cbuf[2][CSW_MAXR];
+  __shared__ TF cbuf[2][CSW_MAXR];
   const SweepArgs& a = args[blockIdx.z];
   const int j = blockIdx.y, sl = blockIdx.x;
   const int N = a.N, n = a.n, R = a.R, nsl = a.nsl;
@@ -114,36 +115,38 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
   // c_start = a_start (initial: V_0^T u0) or 0; c_j = a_j + K_{j-1} c_{j-1}.
   // K_{j-1} and a_j of a chunk of steps are staged in shared memory, so the
   // sequential steps touch no global memory.
+  // The recurrence runs in the precision of the coarse apply (TF: FP32 in
+  // the mixed mode, where G' is applied in FP32; FP64 otherwise).
   for (int r = threadIdx.x; r < R; r += blockDim.x) {
-    const double c0 = a_sum(start, r);
+    const TF c0 = (TF)a_sum(start, r);
     cbuf[0][r] = c0;
-    coef[(size_t)start * R + r] = c0;
+    coef[(size_t)start * R + r] = (double)c0;
   }
-  double* sK = reinterpret_cast<double*>(csw_smem);
-  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(double) * (R * R + R)));
-  double* sA = sK + (size_t)kchunk * R * R;
+  TF* sK = reinterpret_cast<TF*>(csw_smem);
+  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(TF) * (R * R + R)));
+  TF* sA = sK + (size_t)kchunk * R * R;
   const int t = threadIdx.x, rr = t >> 2, part = t & 3;
   int cb = 0;
   for (int j0 = start + 1; j0 < N; j0 += kchunk) {
     const int nk = min(kchunk, N - j0);
     __syncthreads();
     const double* Kg = a.K + (size_t)(j0 - 1) * R * R;
-    for (int k = threadIdx.x; k < nk * R * R; k += blockDim.x) sK[k] = __ldcg(&Kg[k]);
-    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) sA[k] = a_sum(j0 + k / R, k % R);
+    for (int k = threadIdx.x; k < nk * R * R; k += blockDim.x) sK[k] = (TF)__ldcg(&Kg[k]);
+    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) sA[k] = (TF)a_sum(j0 + k / R, k % R);
     __syncthreads();
     for (int jj = 0; jj < nk; ++jj) {
-      const double* Kj = sK + (size_t)jj * R * R;
+      const TF* Kj = sK + (size_t)jj * R * R;
       // rows rr = 0..R-1 of K c, four threads per row (interleaved columns),
       // combined by shuffles in a fixed order
       for (int rb = 0; rb < R; rb += CSW_THREADS / 4) {
         const int r = rb + rr;
-        double acc = 0.0;
+        TF acc = TF(0);
         if (r < R)
           for (int q = part; q < R; q += 4) acc = fma(Kj[r * R + q], cbuf[cb][q], acc);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (r < R && part == 0) {
-          const double cv = sA[(size_t)jj * R + r] + acc;
+          const TF cv = sA[(size_t)jj * R + r] + acc;
           cbuf[cb ^ 1][r] = cv;
           sA[(size_t)jj * R + r] = cv;
         }
@@ -151,7 +154,7 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
       cb ^= 1;
       __syncthreads();
     }
-    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) coef[(size_t)j0 * R + k] = sA[k];
+    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) coef[(size_t)j0 * R + k] = (double)sA[k];
   }
 }
 
