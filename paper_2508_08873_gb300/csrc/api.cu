@@ -510,7 +510,7 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       if (c->p_tri_spt) spt = c->p_tri_spt;
       if (C > 1 && !fits(C, m)) { C = 1; }
     }
-    // FP64 batches of up to ~3.5 warps per SM sub-partition with 2048 <= n <=
+    // FP64 batches of up to ~7 warps per SM sub-partition with 2048 <= n <=
     // 4096: the one-warp-per-CTA cluster kernel (factors in registers, no
     // block barrier, 32 chunks per CTA).  Its time per step is the FP64 issue
     // of one warp per sub-partition (64 cycles per FP64 warp instruction on
@@ -524,9 +524,13 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     //   64        1.25    1.16    1.08    1.08    1.30
     //   96        2.05    2.19    1.45    1.33    1.92
     //   128       2.37    2.30    2.42    1.65    1.92
+    //   192       -       -       2.83    2.84    3.81
+    //   256       -       -       3.96    3.17    3.80
+    //   512       -       -       7.46    6.51    5.94
+    //   1024      -       -       14.9    12.6    11.9
     const int Cw8 = ((op->n + 7) / 8 + 31) / 32;
     const double wpp = (double)nsys * Cw8 / (4.0 * c->num_sms);   // warps per sub-partition, 8-row chunks
-    const bool warp_auto = c->p_tri_warp == 0 && op->n >= 2048 && Cw8 <= 16 && wpp <= 3.5;
+    const bool warp_auto = c->p_tri_warp == 0 && op->n >= 2048 && Cw8 <= 16 && wpp <= 7.0;
     if ((warp_auto || c->p_tri_warp == 2) && prec == 0 && c->p_tri_cluster == 0 &&
         c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       int mw = c->p_tri_wchunk;
