@@ -67,8 +67,9 @@ Operator::~Operator() {
 Coarse::~Coarse() {
   Ctx* c = ctx;
   for (DevBuf* b : {&U, &S, &V, &U32, &S32, &V32, &Kc, &ws_u, &ws_F, &ws_b, &ws_norm, &ws_d, &ws_g,
-                     &ws_c, &ws_cw, &ws_cnt, &ws_args})
+                     &ws_c, &ws_cw, &ws_cnt, &ws_args, &ws_flag, &ws_bh, &ws_argv})
     b->release();
+  if (h_stat) cudaFreeHost(h_stat);
   ctx_release(c);
 }
 
@@ -970,6 +971,16 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
     if ((s = dev_alloc(c, co->ws_b, sizeof(double) * (size_t)N * n))) return s;
     if ((s = dev_alloc(c, co->ws_norm, sizeof(double) * (size_t)(3 * (N + 1) + 2)))) return s;
   }
+  // (the batched solver allocates the buffers above for its handles, not these)
+  if (!co->ws_flag.ptr) {
+    if ((s = dev_alloc(c, co->ws_flag, 2 * sizeof(int)))) return s;
+    if ((s = dev_alloc(c, co->ws_bh, sizeof(double) * (size_t)(N + 1) * (N + 1)))) return s;
+    if ((s = dev_alloc(c, co->ws_argv, sizeof(SweepArgs) * (size_t)(N + 1)))) return s;
+  }
+  if (!co->h_stat) {
+    cudaError_t eh = cudaMallocHost(&co->h_stat, 2 * 32);
+    if (eh) return cuda_err(c, eh, "pinned status slots");
+  }
   double* du = co->ws_norm.as<double>();
   double* unorm = du + (N + 1);
   double* bnd = unorm + (N + 1);
@@ -1031,37 +1042,81 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
   a.bound = nullptr;
   SweepArgs* dargs = co->ws_args.as<SweepArgs>();
   if ((s = coarse_sweep(c, &a, dargs, 1))) return s;
-  int k = 0, converged = 0;
+  // Iterations are enqueued in batches without waiting for the stopping test:
+  // the sweep of iteration k sets a device flag when the tolerance is met and
+  // every later kernel of the solve then returns at once.  The host reads the
+  // flag of batch j only after batch j + 1 is enqueued, so the GPU does not
+  // idle between iterations.
+  int* dflag = co->ws_flag.as<int>();        // [0] stop, [1] k_done
+  cudaMemsetAsync(dflag, 0, 2 * sizeof(int), c->stream);
+  struct HostStat { double sum[2]; int flag[2]; };
+  HostStat* hst = static_cast<HostStat*>(co->h_stat);
+  cudaEvent_t bev[2];
+  cudaEventCreateWithFlags(&bev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&bev[1], cudaEventDisableTiming);
+  int k = 0, converged = 0, k_run = 0, slot = 0, pending = 0;
   double hsum[2] = {0.0, 0.0};
   a.initial = 0;
   a.F = co->ws_F.as<double>();
-  a.bound = bnd;
-  while (k < K) {
-    const int first = k;            // F u^k_i for i < k equals the previous value
-    PropIn in;
-    in.x = co->ws_u.as<double>() + (size_t)first * n;
-    in.x_f64 = 1;
-    in.ldx = n;
-    PropOut o;
-    o.y = co->ws_F.as<double>() + (size_t)first * n;
-    o.y_f64 = 1;
-    o.ldy = n;
-    PropSrc sk = src;
-    if (Q > 0) sk.c = src.c + (size_t)first * M * Q;
-    if ((s = propagate_any(c, op, co->dt, M, 0, N - first, 0, in, o, sk))) return s;
-    a.first = first;
-    if ((s = coarse_sweep(c, &a, dargs, 1))) return s;
-    ++k;
-    ++evals;
-    if (bound_out) {
-      if ((s = from_device(c, bound_out + (size_t)(k - 1) * (N + 1), bnd, sizeof(double) * (N + 1))))
-        return s;
-    }
-    cudaError_t e = cudaMemcpyAsync(hsum, summ, sizeof(hsum), cudaMemcpyDeviceToHost, c->stream);
-    if (!e) e = cudaStreamSynchronize(c->stream);
-    if (e) return cuda_err(c, e, "parareal iteration");
-    if (tol > 0 && hsum[0] <= tol * hsum[1]) { converged = 1; break; }
+  a.stop = dflag;
+  a.k_done = dflag + 1;
+  a.tol = tol;
+  auto read_slot = [&](int sl) -> lrp_status {
+    cudaError_t ee = cudaEventSynchronize(bev[sl]);
+    if (ee) return cuda_err(c, ee, "parareal iteration");
+    hsum[0] = hst[sl].sum[0];
+    hsum[1] = hst[sl].sum[1];
+    k_run = hst[sl].flag[1];
+    if (hst[sl].flag[0]) converged = 1;
+    return LRP_OK;
+  };
+  // the sweep arguments of every iteration, uploaded once
+  std::vector<SweepArgs> hv((size_t)std::max(K, 1));
+  for (int kk = 0; kk < K; ++kk) {
+    hv[kk] = a;
+    hv[kk].first = kk;
+    hv[kk].iter = kk + 1;
+    hv[kk].bound = co->ws_bh.as<double>() + (size_t)kk * (N + 1);
   }
+  SweepArgs* dv = co->ws_argv.as<SweepArgs>();
+  if (K > 0) {
+    cudaError_t eu = cudaMemcpyAsync(dv, hv.data(), sizeof(SweepArgs) * K, cudaMemcpyHostToDevice,
+                                     c->stream);
+    if (eu) return cuda_err(c, eu, "sweep arguments");
+  }
+  const int batch = 4;
+  while (k < K && !converged) {
+    const int kb = std::min(K, k + batch);
+    for (; k < kb; ++k) {
+      const int first = k;          // F u^k_i for i < k equals the previous value
+      PropIn in;
+      in.x = co->ws_u.as<double>() + (size_t)first * n;
+      in.x_f64 = 1;
+      in.ldx = n;
+      in.stop = dflag;
+      PropOut o;
+      o.y = co->ws_F.as<double>() + (size_t)first * n;
+      o.y_f64 = 1;
+      o.ldy = n;
+      PropSrc sk = src;
+      if (Q > 0) sk.c = src.c + (size_t)first * M * Q;
+      if ((s = propagate_any(c, op, co->dt, M, 0, N - first, 0, in, o, sk))) return s;
+      if ((s = coarse_sweep_ex(c, &hv[k], dv + k, 1, 0))) return s;
+    }
+    cudaMemcpyAsync(hst[slot].sum, summ, 2 * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaMemcpyAsync(hst[slot].flag, dflag, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    cudaEventRecord(bev[slot], c->stream);
+    if (pending && (s = read_slot(slot ^ 1))) return s;
+    pending = 1;
+    slot ^= 1;
+  }
+  if (pending && (s = read_slot(slot ^ 1))) return s;
+  cudaEventDestroy(bev[0]);
+  cudaEventDestroy(bev[1]);
+  k = k_run;
+  evals += k;
+  if (bound_out && k > 0)
+    if ((s = from_device(c, bound_out, co->ws_bh.ptr, sizeof(double) * (size_t)k * (N + 1)))) return s;
   if ((s = from_device(c, u_out, co->ws_u.ptr, sizeof(double) * (size_t)(N + 1) * n))) return s;
   cudaEventRecord(e1, c->stream);
   cudaError_t e = cudaEventSynchronize(e1);

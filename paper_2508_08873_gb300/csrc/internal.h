@@ -145,6 +145,9 @@ struct Coarse {
   DevBuf Kc;               // [N-1][R][R] chain matrices of the coarse sweep
   DevBuf ws_u, ws_F, ws_b, ws_norm, ws_d, ws_g, ws_c;
   DevBuf ws_cw, ws_cnt, ws_args;   // coarse-sweep workspace
+  DevBuf ws_flag, ws_bh;           // stop flag + k_done; a posteriori bounds of every iteration
+  DevBuf ws_argv;                  // sweep arguments of every iteration (N + 1)
+  void* h_stat = nullptr;          // pinned host slots for the batched convergence checks
   size_t ws_gc_bytes = 0;
 };
 
@@ -190,6 +193,7 @@ struct PropIn {
   uint32_t stream = 0;      // Philox stream of the generated entries (0: Omega, 3: Psi)
   int ncol = 1;
   int interval0 = 0;        // interval of system 0 (generated input)
+  const int* stop = nullptr; // optional device flag: nonzero at launch -> the kernel does nothing
 };
 struct PropOut {
   void* y = nullptr;        // nsys x n (row stride ldy)
@@ -323,11 +327,21 @@ struct SweepArgs {
   int rows = 0, nsl = 0;          // rows per slice, slices = ceil(n / rows)
   double* cw = nullptr;           // workspace, sweep_ws_doubles(N, nsl, R) doubles
   unsigned* cnt = nullptr;        // 2 completion counters, zero between launches
+  // device-side stopping (single-problem solves): when stop != nullptr the
+  // kernels do nothing while *stop != 0, and the apply's last CTA records
+  // k_done[0] = iter and sets *stop when tol > 0 and max bound <= tol max ||u||
+  int* stop = nullptr;
+  int* k_done = nullptr;
+  int iter = 0;
+  double tol = 0.0;
 };
 // Coarse sweep of nprob problems of equal N and precision in two launches;
 // h is uploaded to d_args (nprob entries) on the stream and must stay alive
 // until the stream has passed the upload.
 lrp_status coarse_sweep(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob);
+// The same with upload = 0: d_args already holds h (uploaded earlier on the
+// stream), so nothing is copied before the launches.
+lrp_status coarse_sweep_ex(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob, int upload);
 size_t sweep_ws_doubles(int N, int nsl, int R);
 int sweep_rows(Ctx* c);
 // K_i of a coarse handle (Coarse::Kc), formed from the factors its apply uses.

@@ -356,6 +356,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
 
 template <typename T>
 __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   cg::cluster_group cl = cg::this_cluster();
   __shared__ ClRed sh;
   const int cs = (int)cl.num_blocks();

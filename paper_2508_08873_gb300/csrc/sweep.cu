@@ -74,6 +74,7 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
   __shared__ TF vs[CSW_MAXROWS];
   __shared__ TF cbuf[2][CSW_MAXR];
   const SweepArgs& a = args[blockIdx.z];
+  if (a.stop && *a.stop) return;             // the iteration has stopped on the device
   const int j = blockIdx.y, sl = blockIdx.x;
   const int N = a.N, n = a.n, R = a.R, nsl = a.nsl;
   const int start = a.initial ? 0 : a.first;
@@ -168,6 +169,7 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_apply(const SweepArgs* __re
   __shared__ TF sc[CSW_MAXR];
   __shared__ double red[CSW_THREADS / 32][2];
   const SweepArgs& a = args[blockIdx.z];
+  if (a.stop && *a.stop) return;             // the iteration has stopped on the device
   const int j = (int)blockIdx.y - 1, sl = blockIdx.x;
   const int N = a.N, n = a.n, R = a.R, nsl = a.nsl;
   const int start = a.initial ? 0 : a.first;
@@ -257,10 +259,16 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_apply(const SweepArgs* __re
     }
     a.summary[0] = bmax;
     a.summary[1] = umax;
+    if (a.k_done) *a.k_done = a.iter;
+    if (a.stop && a.tol > 0.0 && bmax <= a.tol * umax) *a.stop = 1;
   }
 }
 
 lrp_status coarse_sweep(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob) {
+  return coarse_sweep_ex(c, h, d_args, nprob, 1);
+}
+
+lrp_status coarse_sweep_ex(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob, int upload) {
   if (nprob <= 0) return LRP_OK;
   const int f32 = h[0].f32, N = h[0].N;
   int nsl = 0;
@@ -273,8 +281,9 @@ lrp_status coarse_sweep(Ctx* c, const SweepArgs* h, SweepArgs* d_args, int nprob
     if (!a.cw || !a.cnt || (N > 1 && !a.K)) return set_err(c, LRP_EINVAL, "sweep workspace missing");
     nsl = std::max(nsl, a.nsl);
   }
-  cudaError_t e = cudaMemcpyAsync(d_args, h, sizeof(SweepArgs) * nprob, cudaMemcpyHostToDevice,
-                                  c->stream);
+  cudaError_t e = upload ? cudaMemcpyAsync(d_args, h, sizeof(SweepArgs) * nprob,
+                                           cudaMemcpyHostToDevice, c->stream)
+                         : cudaSuccess;
   if (e) return cuda_err(c, e, "sweep arguments");
   auto kp = f32 ? (void (*)(const SweepArgs*))k_csw_project<float>
                 : (void (*)(const SweepArgs*))k_csw_project<double>;

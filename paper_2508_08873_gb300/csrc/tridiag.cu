@@ -168,6 +168,7 @@ struct TriKArgs {
 // whole chunk state (MM values) in registers.
 template <typename T, int MM, bool SDIRK = false>
 __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* s_coef = reinterpret_cast<T*>(smem_raw);                 // [5][MM][P]
   const int P = a.P, L = a.L, G = a.G;
@@ -308,6 +309,7 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
 // row-step) and one set of barriers serves SPT systems.  FP32, MM = 16.
 template <typename T, int MM, int LMAX, int SPT>
 __global__ void __launch_bounds__(256) k_tri_propagate_rc(TriKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int P = a.P, L = a.L;
   T* xb = reinterpret_cast<T*>(smem_raw);                  // [SPT][3][P]

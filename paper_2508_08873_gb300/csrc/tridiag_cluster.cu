@@ -260,6 +260,7 @@ struct ClKArgs {
 // shared memory serve SPT systems.
 template <typename T, int MM, int SPT, bool SDIRK = false>
 __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   cg::cluster_group cl = cg::this_cluster();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int Pc = a.Pc, L = a.L, C = a.C, Pl = Pc - 1;
@@ -505,6 +506,7 @@ constexpr int CLW_L = 5;    // PCR levels over the 31 local interface unknowns
 
 template <int MM>
 __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   cg::cluster_group cl = cg::this_cluster();
   __shared__ double pubg[2][CL_MAXC][4];
   __shared__ double* rpub[CL_MAXC];

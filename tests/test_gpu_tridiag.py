@@ -194,6 +194,28 @@ def test_parareal_f64_iterates_match_oracle(ctx, orc, K):
         np.testing.assert_allclose(info["bounds"][k - 1], res.bounds[k - 1], rtol=1e-8, atol=1e-14)
 
 
+@pytest.mark.parametrize("tol", [1e-2, 1e-4, 1e-6])
+def test_parareal_device_stopping_matches_oracle(ctx, orc, tol):
+    """The tolerance test runs on the device (the sweep sets a stop flag and
+    the kernels of later iterations return at once) while the host enqueues
+    iterations four at a time; the solve stops at the same iteration as the
+    oracle's literal Parareal (here 6, 9 and 13: inside a batch), with the
+    same iterate and the same a posteriori bounds."""
+    P = W.adr1d(n=511, N=16, M=32, R=8, p=4)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    u, info = api.parareal_solve(ctx, co, P.u0, K=P.N, tol=tol)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, K=P.N, tol=tol)
+    assert info["converged"] and info["k_done"] == res.k_done
+    assert res.k_done % 4 != 0
+    assert rel(u, res.iterates[-1]) <= 1e-10
+    assert info["bounds"].shape[0] == res.k_done
+    for k in range(res.k_done):
+        np.testing.assert_allclose(info["bounds"][k], res.bounds[k], rtol=1e-8, atol=1e-14)
+
+
 def test_parareal_heat1d_full_K_equals_N(ctx, orc):
     """Config: n=255, N=16, M=64, R=8, p=4, source sin(2 pi t) exp(-100(x-1/2)^2)."""
     P = W.heat1d()
