@@ -93,3 +93,59 @@ def test_tensor_core_orth_parareal_to_tolerance(ctx, orc):
     ref = orc.sequential_fine(orc.Tridiag(P.lo, P.di, P.up), P.dt, P.M, P.N, P.u0)
     assert info["converged"]
     assert orc.rel_err(u, ref) <= 1e-8
+
+
+def _adv2d_ops(ctx, Ps):
+    ops = []
+    for P in Ps:
+        op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+        op.set_krylov(1e-14, 1e-6, 20000)
+        ops.append(op)
+    return ops
+
+
+def test_tensor_core_orth_2d_mixed_matches_oracle(ctx, orc):
+    """2D advection-diffusion (31^2 grid, dt = 1/2048, R = 8, p = 4, FP32
+    Jacobi-BiCGStab sketches to rtol 1e-6): every interval's bases come from
+    the tensor-core CholeskyQR2, and the coarse operators of sampled
+    intervals are within 1e-4 sigma_1 of the FP64 oracle's."""
+    P = W.adv2d(0, m=31, N=32, M=64, R=8, p=4)
+    op, = _adv2d_ops(ctx, [P])
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed")
+    assert co.orth_method() == {"tc_w": P.N, "tc_v": P.N}
+    oop = orc.Stencil5(P.mx, P.my, P.st["C"], P.st["W"], P.st["E"], P.st["S"], P.st["N"])
+    probes = np.random.default_rng(5).standard_normal((3, P.n))
+    inf = co.info()
+    for i in (0, 13, P.N - 1):
+        oc = orc.rsvd_interval(oop, P.dt, P.M, i, P.R, P.p, P.seed)
+        s1 = oc.sigma[0]
+        G = _operator(*co.factors(i))
+        Go = oc.U @ np.diag(oc.S) @ oc.V.T
+        for x in probes:
+            assert np.linalg.norm((G - Go) @ x) <= 1e-4 * s1 * np.linalg.norm(x)
+        assert np.max(np.abs(inf["sigma"][i] - oc.sigma)) <= 1e-4 * s1
+
+
+def test_tensor_core_orth_in_captured_batch_build(ctx):
+    """The batched build of uneven 2D problems captures its whole build,
+    tensor-core orthonormalisation and lift included, in one CUDA graph; each
+    problem's coarse solver equals its separate mixed build to FP32 accuracy
+    and used the tensor-core path for every interval."""
+    grids = (31, 23, 31)
+    Ps = [W.adv2d(i, m=m, N=32, M=64, R=8, p=4) for i, m in enumerate(grids)]
+    ops = _adv2d_ops(ctx, Ps)
+    P0 = Ps[0]
+    cos = api.build_coarse_batch(ctx, ops, P0.dt, P0.M, P0.N, P0.R, P0.p, 0, prec="mixed")
+    probes = np.random.default_rng(9).standard_normal((2, max(P.n for P in Ps)))
+    for P, op, co in zip(Ps, ops, cos):
+        single = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, 0, prec="mixed")
+        assert co.orth_method() == {"tc_w": P.N, "tc_v": P.N}
+        assert single.orth_method() == {"tc_w": P.N, "tc_v": P.N}
+        a, b = co.info(), single.info()
+        s1 = b["sigma"].max()
+        np.testing.assert_allclose(a["sigma"], b["sigma"], rtol=0, atol=1e-5 * s1)
+        for i in (0, P.N - 1):
+            G, Gs = _operator(*co.factors(i)), _operator(*single.factors(i))
+            for x in probes:
+                xx = x[:P.n]
+                assert np.linalg.norm((G - Gs) @ xx) <= 1e-5 * s1 * np.linalg.norm(xx)
