@@ -96,6 +96,11 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    kernel (1..16, at most 512 threads per CTA);
  *   "queue_cluster": CTAs per cluster of the batched 2D work queue (1..16,
  *                    a power of two);
+ *   "orth_tc":       1 (default) orthonormalises the FP32 sketches of the mixed
+ *                    mode by CholeskyQR2 on the tensor cores and lifts the
+ *                    singular vectors there (sketch width <= 64, intervals
+ *                    whose Gram passes the conditioning test); 0 uses
+ *                    Gram-Schmidt and the SIMT lift throughout;
  *   "orth_cluster":  CTAs per interval of the shared-memory CGS2 kernel (a power
  *                    of two up to 16; -1 selects the one-CTA kernel);
  *   "krylov_cluster": CTAs per cluster of the 2D propagator (1..16, a power
