@@ -38,13 +38,16 @@ def _build(ctx, op, P, tc):
 
 
 @pytest.mark.parametrize("R,p,n,N,M", [(8, 4, 1023, 16, 64), (32, 10, 1023, 128, 8),
-                                        (16, 8, 4095, 64, 256)])
+                                        (16, 8, 4095, 64, 256), (48, 16, 1023, 256, 4),
+                                        (1, 1, 1023, 16, 64), (1, 0, 511, 8, 32)])
 def test_tensor_core_orth_matches_oracle_and_cgs2(ctx, orc, R, p, n, N, M):
-    """Sketch widths 12, 42 (two K blocks of the apply) and 24 (the full
-    advection-diffusion-reaction configuration), with spectra that decay
-    slowly enough for CholeskyQR2: every interval takes the tensor-core path,
-    and on sampled intervals its coarse operators are within 1e-4 sigma_1 of
-    the FP64 oracle's and within 2e-5 sigma_1 of the Gram-Schmidt build."""
+    """Sketch widths 12, 42 (two K blocks of the apply), 24 (the full
+    advection-diffusion-reaction configuration), 64 (the widest: N = 64 of
+    the MMAs, two K blocks) and the degenerate widths 2 and 1, with spectra
+    that decay slowly enough for CholeskyQR2: every interval takes the
+    tensor-core path, and on sampled intervals its coarse operators are
+    within 1e-4 sigma_1 of the FP64 oracle's and within 2e-5 sigma_1 of the
+    Gram-Schmidt build."""
     P = W.adr1d(n=n, N=N, M=M, R=R, p=p)
     op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
     co = _build(ctx, op, P, 1)
