@@ -89,8 +89,8 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    FP64 batches with 2048 <= n <= 4096 and up to about 7
  *                    warps per SM sub-partition use by default, 2 uses it for
  *                    every FP64 batch with n <= 4096;
- *   "tri_wchunk":    rows per chunk of the one-warp FP64 cluster kernel (8, 10,
- *                    12 or 16; 0 = automatic);
+ *   "tri_wchunk":    rows per chunk of the one-warp FP64 cluster kernel (8 to
+ *                    16; 0 = automatic);
  *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);
  *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
  *                    kernel (1..16, at most 512 threads per CTA);

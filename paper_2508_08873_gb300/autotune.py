@@ -18,7 +18,8 @@ from . import api
 _CACHE: Dict[Tuple, Dict[str, int]] = {}
 
 # (tri_cluster, tri_chunk, tri_spt, tri_wchunk); all zeros = the library's own rule
-TRI_CANDIDATES = ((0, 0, 0, 0), (0, 0, 0, 8), (0, 0, 0, 12), (0, 0, 0, 16), (2, 16, 1, 0),
+TRI_CANDIDATES = ((0, 0, 0, 0), (0, 0, 0, 8), (0, 0, 0, 11), (0, 0, 0, 13), (0, 0, 0, 16),
+                  (2, 16, 1, 0),
                   (2, 8, 2, 0), (4, 8, 2, 0), (4, 8, 1, 0), (1, 16, 1, 0))
 SWEEP_CANDIDATES = (0, 256, 2048)
 

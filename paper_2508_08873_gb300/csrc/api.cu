@@ -289,7 +289,7 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
     if (value != 0 && value != 1) return LRP_EINVAL;
     c->p_orth_tc = value;
   } else if (k == "tri_wchunk") {
-    if (value != 0 && value != 8 && value != 10 && value != 12 && value != 16) return LRP_EINVAL;
+    if (value != 0 && (value < 8 || value > 16)) return LRP_EINVAL;
     c->p_tri_wchunk = value;
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
@@ -514,28 +514,35 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     // FP64 batches of up to ~7 warps per SM sub-partition with 2048 <= n <=
     // 4096: the one-warp-per-CTA cluster kernel (factors in registers, no
     // block barrier, 32 chunks per CTA).  Its time per step is the FP64 issue
-    // of one warp per sub-partition (64 cycles per FP64 warp instruction on
-    // GB300), so the chunk length trades the number of warps against the
-    // interface work per row.  Measured on GB300 (n = 4095, 256 steps, ms):
-    //   systems   8-row   10-row  12-row  16-row  one-CTA/4-CTA block
-    //   16        0.76    0.82    0.89    1.01    1.01
-    //   40        0.88    0.90    0.94    1.03    1.30
-    //   48        0.99    0.98    0.97    1.07    1.30
-    //   56        1.12    1.07    1.01    1.06    1.30
-    //   64        1.25    1.16    1.08    1.08    1.30
-    //   96        2.05    2.19    1.45    1.33    1.92
-    //   128       2.37    2.30    2.42    1.65    1.92
-    //   192       -       -       2.83    2.84    3.81
-    //   256       -       -       3.96    3.17    3.80
-    //   512       -       -       7.46    6.51    5.94
-    //   1024      -       -       14.9    12.6    11.9
+    // of the warps sharing a sub-partition (~80 cycles per FP64 warp
+    // instruction on GB300), so the chunk length MM (8..16 rows) trades the
+    // number of warps, n / (32 MM) per system, against the interface work
+    // per row.  Measured on GB300 (n = 4095, 256 steps, ms; wpp8 = warps per
+    // sub-partition with 8-row chunks):
+    //   systems  wpp8   MM=8   9      10     11     12     13     14     15     16
+    //   32       0.84   0.852  0.849  0.873  0.896  0.925  0.940  0.983  1.010  1.021
+    //   40       1.05   0.880  0.897  0.895  0.913  0.938  0.949  0.990  1.009  1.028
+    //   44       1.16   0.930  1.028  0.922  0.912  0.940  0.949  0.989  1.022  1.029
+    //   52       1.37   1.023  1.042  1.009  0.987  1.008  1.005  1.044  1.031  1.068
+    //   56       1.47   1.121  1.139  1.066  1.019  1.010  1.005  1.043  1.067  1.059
+    //   60       1.58   1.133  1.141  1.068  1.074  1.077  1.058  1.104  1.067  1.078
+    //   64       1.68   1.254  1.275  1.164  1.077  1.079  1.078  1.130  1.131  1.080
+    //   96       2.53   2.064  2.119  2.182  1.449  1.447  1.364  1.435  1.319  1.329
+    //   128      3.37   2.371  2.409  2.301  2.310  2.425  2.442  2.565  2.608  1.651
+    //   160      4.21   3.303  3.347  2.774  2.512  2.523  2.506  2.626  2.725  2.817
+    //   192      5.05   3.601  3.673  3.608  2.889  2.852  2.694  2.840  2.885  2.848
+    //   256      6.74   4.735  4.825  4.939  3.952  4.006  4.028  4.234  4.388  3.181
+    // (the block kernel takes 1.30 ms from 40 to 64 systems and the one-CTA
+    // kernel 3.80 ms at 192 and 256; beyond ~7 warps per sub-partition the
+    // one-CTA kernel is faster: 5.94 against 6.51 ms at 512 systems).
     const int Cw8 = ((op->n + 7) / 8 + 31) / 32;
     const double wpp = (double)nsys * Cw8 / (4.0 * c->num_sms);   // warps per sub-partition, 8-row chunks
     const bool warp_auto = c->p_tri_warp == 0 && op->n >= 2048 && Cw8 <= 16 && wpp <= 7.0;
     if ((warp_auto || c->p_tri_warp == 2) && prec == 0 && c->p_tri_cluster == 0 &&
         c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       int mw = c->p_tri_wchunk;
-      if (!mw) mw = wpp <= 1.1 ? 8 : wpp <= 1.24 ? 10 : wpp <= 1.53 ? 12 : 16;
+      if (!mw)
+        mw = wpp <= 1.06 ? 8 : wpp <= 1.43 ? 11 : wpp <= 1.64 ? 13 : wpp <= 3.8 ? 16 : wpp <= 5.5 ? 13 : 16;
       int Cw = ((op->n + mw - 1) / mw + 31) / 32;
       if (Cw < 2 && c->p_tri_wchunk == 0) {
         mw = 8;

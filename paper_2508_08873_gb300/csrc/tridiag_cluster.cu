@@ -500,7 +500,7 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
 // interface system of a CTA is then solved by parallel cyclic reduction with
 // warp shuffles and the C x C super system by two warp sums, so a step needs
 // no block barrier at all: only the cluster barrier that publishes the four
-// values of every CTA.  (FP64, chunks of MM = 8, 10, 12 or 16 rows.)
+// values of every CTA.  (FP64, chunks of MM = 8..16 rows.)
 // ---------------------------------------------------------------------------
 constexpr int CLW_L = 5;    // PCR levels over the 31 local interface unknowns
 
@@ -680,7 +680,7 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
   if (warp) {
     // one warp per CTA: exactly 32 chunks of 8 rows per CTA (padding chunks
     // are identity rows)
-    if ((CL_M != 8 && CL_M != 10 && CL_M != 12 && CL_M != 16) || P > 32 * C)
+    if (CL_M < 8 || CL_M > 16 || P > 32 * C)
       return set_err(c, LRP_EINVAL, "warp cluster plan out of range");
     P = 32 * C;
   }
@@ -826,8 +826,13 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
     if (f || spt != 1) return set_err(c, LRP_EINVAL, "warp cluster kernel is FP64, one system per thread");
     switch (pl->m) {
       case 16: return launch_cl_w<16>(c, pl, a);
+      case 15: return launch_cl_w<15>(c, pl, a);
+      case 14: return launch_cl_w<14>(c, pl, a);
+      case 13: return launch_cl_w<13>(c, pl, a);
       case 12: return launch_cl_w<12>(c, pl, a);
+      case 11: return launch_cl_w<11>(c, pl, a);
       case 10: return launch_cl_w<10>(c, pl, a);
+      case 9: return launch_cl_w<9>(c, pl, a);
       default: return launch_cl_w<8>(c, pl, a);
     }
   }
