@@ -1,11 +1,14 @@
 """Autotuner for the launch parameters of the library (lrp_set_param).
 
-For a given coarse handle it times a short Parareal solve under each candidate
+tune_solve: for a given coarse handle it times a short Parareal solve under each candidate
 setting of the tridiagonal cluster split (CTAs per system, rows per chunk,
 systems per thread, rows per chunk of the one-warp kernel) and of the
 coarse-sweep slice (rows per CTA), using the library's
 per-kernel CUDA-event timers, and leaves the fastest setting applied to the
 context.  Results are cached in memory per (n, N, precision, device name).
+tune_krylov: for a 2D (5-point stencil) operator it times one batched
+backward-Euler step of the Krylov propagator under each CTA count per cluster
+(the CG/BiCGStab block shape), in the precision the build will use.
 Every candidate computes the same solution up to rounding; the tuner only
 picks launch shapes.
 """
@@ -70,6 +73,46 @@ def tune_solve(ctx: api.Context, co: api.Coarse, u0, K: int = 6,
         params = {"tri_cluster": 0, "tri_chunk": 0, "tri_spt": 0, "tri_wchunk": 0, "sweep_rows": 0}
     else:
         params = best[1]
+    _apply(ctx, params)
+    _CACHE[key] = dict(params)
+    return dict(params)
+
+
+KRYLOV_CANDIDATES = (0, 16, 8, 4)
+
+
+def tune_krylov(ctx: api.Context, op: api.Operator, dt: float, nsys: int = 32, prec: str = "mixed",
+                candidates: Iterable = KRYLOV_CANDIDATES, verbose: bool = False) -> Dict[str, int]:
+    """Pick the CTAs per cluster of the 2D Krylov propagator (krylov_cluster)
+    minimising the device time per Krylov iteration of one backward-Euler
+    step of nsys seeded vectors; leaves the choice applied to the context."""
+    import numpy as np
+    key = ("krylov", op.n, nsys, prec, _device_name(ctx))
+    if key in _CACHE:
+        _apply(ctx, _CACHE[key])
+        return dict(_CACHE[key])
+    X = np.random.default_rng(0).standard_normal((nsys, op.n))
+    fam = "propagate_f64" if prec == "f64" else "propagate_f32"
+    best: Optional[Tuple[float, Dict[str, int]]] = None
+    for cs in candidates:
+        params = {"krylov_cluster": cs}
+        try:
+            _apply(ctx, params)
+            api.propagate(ctx, op, dt, 1, X, prec=prec)                   # plans, warm-up
+            it0 = op.krylov_iterations()
+            ctx.set_kernel_timing(True)
+            ctx.reset_kernel_time()
+            api.propagate(ctx, op, dt, 1, X, prec=prec)
+            t = ctx.kernel_time(fam)[1] / max(1, op.krylov_iterations() - it0)
+        except Exception:
+            continue
+        finally:
+            ctx.set_kernel_timing(False)
+        if verbose:
+            print("autotune", params, "%.3f us per iteration" % (t * 1e3))
+        if best is None or t < best[0]:
+            best = (t, params)
+    params = {"krylov_cluster": 0} if best is None else best[1]
     _apply(ctx, params)
     _CACHE[key] = dict(params)
     return dict(params)

@@ -65,3 +65,22 @@ def test_autotune_picks_valid_parameters():
     u, _ = api.parareal_solve(ctx, co, P.u0, K=3)
     # launch shapes change only the rounding (FP64 path)
     assert np.linalg.norm(u - ref) <= 1e-12 * np.linalg.norm(ref)
+
+
+def test_autotune_krylov_picks_a_valid_cluster_size():
+    """The 2D tuner times the Krylov propagator under each CTA count per
+    cluster and leaves the fastest applied; every choice gives the same step
+    to the Krylov tolerance."""
+    from paper_2508_08873_gb300 import autotune
+    ctx = api.Context(0)
+    P = W.diff2d(m=63, N=4, M=4, R=4, p=2)
+    op = api.Operator.stencil5(ctx, 63, 63, P.st)
+    op.set_krylov(1e-12, 1e-6, 20000)
+    X = np.random.default_rng(1).standard_normal((4, P.n))
+    ref = api.propagate(ctx, op, P.dt, 2, X)
+    best = autotune.tune_krylov(ctx, op, P.dt, nsys=8, prec="f64")
+    assert set(best) == {"krylov_cluster"} and best["krylov_cluster"] in autotune.KRYLOV_CANDIDATES
+    assert ctx.get_param("krylov_cluster") == best["krylov_cluster"]
+    got = api.propagate(ctx, op, P.dt, 2, X)
+    assert np.linalg.norm(got - ref) <= 1e-10 * np.linalg.norm(ref)
+    ctx.set_param("krylov_cluster", 0)
