@@ -132,8 +132,36 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
     const int nk = min(kchunk, N - j0);
     __syncthreads();
     const double* Kg = a.K + (size_t)(j0 - 1) * R * R;
-    for (int k = threadIdx.x; k < nk * R * R; k += blockDim.x) sK[k] = (TF)__ldcg(&Kg[k]);
-    for (int k = threadIdx.x; k < nk * R; k += blockDim.x) sA[k] = (TF)a_sum(j0 + k / R, k % R);
+    // eight loads in flight per thread (this CTA stages alone while the
+    // other CTAs of the launch have finished)
+    const int nkr = nk * R * R;
+    for (int k0 = threadIdx.x; k0 < nkr; k0 += 8 * blockDim.x) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u * blockDim.x;
+        v[u] = k < nkr ? __ldcg(&Kg[k]) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int k = k0 + u * blockDim.x;
+        if (k < nkr) sK[k] = (TF)v[u];
+      }
+    }
+    const int na = nk * R;
+    for (int k0 = threadIdx.x; k0 < na; k0 += 4 * blockDim.x) {
+      double v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * blockDim.x;
+        v[u] = k < na ? a_sum(j0 + k / R, k % R) : 0.0;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + u * blockDim.x;
+        if (k < na) sA[k] = (TF)v[u];
+      }
+    }
     __syncthreads();
     for (int jj = 0; jj < nk; ++jj) {
       const TF* Kj = sK + (size_t)jj * R * R;
@@ -246,16 +274,57 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_apply(const SweepArgs* __re
   umax_t = fmax(umax_t, __shfl_xor_sync(0xffffffffu, umax_t, 1));
   if (lane == 0) red[w][1] = umax_t;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double umax = 0.0, B = 0.0, bmax = 0.0;
-    for (int k = 0; k < nw; ++k) umax = fmax(umax, red[k][1]);
-    if (a.bound) {
-      a.bound[0] = 0.0;
-      for (int m = 1; m <= N; ++m) {
-        B = a.delta * B + a.eps * sdu[m - 1];
-        a.bound[m] = B;
-        bmax = fmax(bmax, B);
+  // a posteriori bound B_m = delta B_{m-1} + eps ||Delta_{m-1}||, B_0 = 0, as
+  // a scan over m in chunks of blockDim.x (Hillis-Steele within a chunk:
+  // B_m += delta^d B_{m-d}), the carry delta^(m - m0 + 1) B_{m0-1} added
+  // from the previous chunk; then the maximum over m
+  double bmax_t = 0.0;
+  if (a.bound) {
+    double* sb = sun;                            // reused ([N + 1]): the scan buffer
+    __syncthreads();
+    double carry = 0.0;                          // B_{m0 - 1}
+    for (int m0 = 1; m0 <= N; m0 += blockDim.x) {
+      const int m = m0 + threadIdx.x;
+      double v = m <= N ? a.eps * sdu[m - 1] : 0.0;
+      __syncthreads();
+      double dp = a.delta;                       // delta^d
+      for (int d = 1; d < (int)blockDim.x; d <<= 1) {
+        if (m <= N) sb[m] = v;
+        __syncthreads();
+        if (m <= N && threadIdx.x >= d) v = fma(dp, sb[m - d], v);
+        __syncthreads();
+        dp *= dp;
       }
+      // add the carry: delta^(m - m0 + 1) B_{m0 - 1}
+      double cp = 1.0, base = a.delta;
+      for (int e = threadIdx.x + 1; e > 0; e >>= 1) {
+        if (e & 1) cp *= base;
+        base *= base;
+      }
+      v = fma(cp, carry, v);
+      if (m <= N) {
+        a.bound[m] = v;
+        bmax_t = fmax(bmax_t, v);
+        sb[m] = v;
+      }
+      __syncthreads();
+      carry = sb[min(N, m0 + (int)blockDim.x - 1)];
+    }
+    if (threadIdx.x == 0) a.bound[0] = 0.0;
+  }
+  bmax_t = fmax(bmax_t, __shfl_xor_sync(0xffffffffu, bmax_t, 16));
+  bmax_t = fmax(bmax_t, __shfl_xor_sync(0xffffffffu, bmax_t, 8));
+  bmax_t = fmax(bmax_t, __shfl_xor_sync(0xffffffffu, bmax_t, 4));
+  bmax_t = fmax(bmax_t, __shfl_xor_sync(0xffffffffu, bmax_t, 2));
+  bmax_t = fmax(bmax_t, __shfl_xor_sync(0xffffffffu, bmax_t, 1));
+  __syncthreads();
+  if (lane == 0) red[w][0] = bmax_t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double umax = 0.0, bmax = 0.0;
+    for (int k = 0; k < nw; ++k) {
+      umax = fmax(umax, red[k][1]);
+      bmax = fmax(bmax, red[k][0]);
     }
     a.summary[0] = bmax;
     a.summary[1] = umax;
