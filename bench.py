@@ -381,7 +381,46 @@ def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
         op_h.close()
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_val = world * 1000.0 / statistics.mean(e2e_ms)
+    # the 1D heat configuration of Experiment 1 (n=255, N=16, M=64, R=8, p=4,
+    # source sin(2 pi t) exp(-100 (x - 1/2)^2)): latency-bound, reported in us
+    # per solve (to tol 1e-10), with and without the coarse build
+    from paper_2508_08873_gb300 import workloads as W
+    H = W.heat1d()
+    op_h = api.Operator.tridiag(ctx, H.lo, H.di, H.up)
+    g_d = torch.tensor(H.g, dtype=torch.float64, device=u0_d.device)
+    c_d = torch.tensor(H.c, dtype=torch.float64, device=u0_d.device)
+    hu0 = torch.tensor(H.u0, dtype=torch.float64, device=u0_d.device)
+    hout = torch.empty((H.N + 1, H.n), dtype=torch.float64, device=u0_d.device)
+
+    def heat_step(build):
+        co_h = api.Coarse(ctx, op_h, H.dt, H.M, H.N, H.R, H.p, H.seed, prec=args.prec) \
+            if build else heat_step.co
+        _, inf_h = api.parareal_solve(ctx, co_h, hu0, g_d, c_d, K=H.N, tol=1e-10, out=hout,
+                                      bounds=False)
+        if build:
+            co_h.close()
+        return inf_h
+    heat_step.co = api.Coarse(ctx, op_h, H.dt, H.M, H.N, H.R, H.p, H.seed, prec=args.prec)
+    heat = {}
+    for build in (True, False):
+        for _ in range(2):
+            heat_step(build)
+        torch.cuda.synchronize()
+        h0 = torch.cuda.Event(enable_timing=True)
+        h1 = torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        reps = 10
+        for _ in range(reps):
+            inf_h = heat_step(build)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        heat["us_per_solve_with_build" if build else "us_per_solve"] = \
+            1000.0 * h0.elapsed_time(h1) / reps
+    heat["iterations"] = inf_h["k_done"]
+    heat["workload"] = "heat1d n=255 N=16 M=64 R=8 p=4 tol=1e-10"
+    heat_step.co.close()
     return {"amortised_solves_per_s": amort * world,
+            "heat1d": heat,
             "two_sided_sketch": {"iterations": ts_info["k_done"], "solves_per_s": 1000.0 / ts_ms,
                                  "rel_err_vs_oracle": None,
                                  "note": "build_coarse with F'^* on 2(R+p) independent random "

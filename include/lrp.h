@@ -86,7 +86,7 @@ long lrp_launch_count(lrp_ctx* ctx);
  *   "tri_cluster":   CTAs per tridiagonal system for small batches (1..8);
  *   "tri_chunk":     rows per chunk of the cluster tridiagonal kernel (8, 16);
  *   "tri_warp":      1 disables the one-warp-per-CTA FP64 cluster kernel that
- *                    FP64 batches with 2048 <= n <= 4096 and up to about 7
+ *                    FP64 batches with 256 < n <= 4096 and up to about 7
  *                    warps per SM sub-partition use by default, 2 uses it for
  *                    every FP64 batch with n <= 4096;
  *   "tri_wchunk":    rows per chunk of the one-warp FP64 cluster kernel (8 to

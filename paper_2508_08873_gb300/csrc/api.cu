@@ -511,7 +511,7 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       if (c->p_tri_spt) spt = c->p_tri_spt;
       if (C > 1 && !fits(C, m)) { C = 1; }
     }
-    // FP64 batches of up to ~7 warps per SM sub-partition with 2048 <= n <=
+    // FP64 batches of up to ~7 warps per SM sub-partition with 256 < n <=
     // 4096: the one-warp-per-CTA cluster kernel (factors in registers, no
     // block barrier, 32 chunks per CTA).  Its time per step is the FP64 issue
     // of the warps sharing a sub-partition (~80 cycles per FP64 warp
@@ -537,7 +537,9 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     // one-CTA kernel is faster: 5.94 against 6.51 ms at 512 systems).
     const int Cw8 = ((op->n + 7) / 8 + 31) / 32;
     const double wpp = (double)nsys * Cw8 / (4.0 * c->num_sms);   // warps per sub-partition, 8-row chunks
-    const bool warp_auto = c->p_tri_warp == 0 && op->n >= 2048 && Cw8 <= 16 && wpp <= 7.0;
+    // (n = 511 and 1023, 16 systems, 64 steps: 0.162 / 0.167 ms against 0.254 /
+    // 0.267 ms for the one-CTA kernel; n = 255, one CTA: 0.160 against 0.146)
+    const bool warp_auto = c->p_tri_warp == 0 && Cw8 >= 2 && Cw8 <= 16 && wpp <= 7.0;
     if ((warp_auto || c->p_tri_warp == 2) && prec == 0 && c->p_tri_cluster == 0 &&
         c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       int mw = c->p_tri_wchunk;
@@ -548,7 +550,7 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
         mw = 8;
         Cw = Cw8;
       }
-      if (Cw >= 2 && Cw <= 16) {
+      if (Cw >= 1 && Cw <= 16) {
         ClPlan* cp = nullptr;
         lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, mw, &cp, 1);
         if (s) return s;

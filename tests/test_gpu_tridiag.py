@@ -334,10 +334,10 @@ def test_sweep_slicing_does_not_change_the_iterates(ctx, orc):
 
 
 @pytest.mark.parametrize("wchunk", [0, 9, 10, 11, 12, 13, 14, 15, 16])
-@pytest.mark.parametrize("n,nvec,Q", [(3000, 7, 2), (1025, 9, 0), (4096, 40, 1)])
+@pytest.mark.parametrize("n,nvec,Q", [(3000, 7, 2), (1025, 9, 0), (4096, 40, 1), (200, 3, 1)])
 def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, Q, wchunk):
     """FP64 batches with n <= 4096 run on the one-warp-per-CTA cluster kernel
-    (2..16 CTAs of 32 chunks of 8 to 16 rows); it agrees with the
+    (1..16 CTAs of 32 chunks of 8 to 16 rows); it agrees with the
     block kernel (tri_warp = 1) to rounding and with the oracle, with and
     without a source term, forward and adjoint."""
     lo, di, up = W.adr1d_op(n)
