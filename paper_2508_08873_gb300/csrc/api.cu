@@ -1093,9 +1093,12 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
                                      c->stream);
     if (eu) return cuda_err(c, eu, "sweep arguments");
   }
-  const int batch = 4;
+  // batches of 1, 2, then 4 iterations: a solve that converges after one or
+  // two iterations runs few no-op launches, a long one keeps 4 in flight
+  int batch = 1;
   while (k < K && !converged) {
     const int kb = std::min(K, k + batch);
+    batch = std::min(4, 2 * batch);
     for (; k < kb; ++k) {
       const int first = k;          // F u^k_i for i < k equals the previous value
       PropIn in;
