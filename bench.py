@@ -546,13 +546,20 @@ def main():
     # (dram__bytes_read.sum + dram__bytes_write.sum of a 61-system launch of
     # the 16-row-chunk variant: 2.26 MB read, nothing written back within the
     # launch), per propagated system, times this run's systems per launch
+    # per-launch figures over the launches that propagate (one per Parareal
+    # iteration; the launches enqueued after the device-side stop return at
+    # once and are counted apart)
+    real_launches = k_mean if fam == "propagate_f64" else launches_per_step
+    systems_per_launch = systems_per_step / max(real_launches, 1)
     traffic = None
-    if fam == "propagate_f64" and launches_per_step > 0:
-        traffic = F64_DRAM_BYTES_PER_SYSTEM * systems_per_step / launches_per_step
+    if fam == "propagate_f64":
+        traffic = F64_DRAM_BYTES_PER_SYSTEM * systems_per_launch
     roof = {"bound": "alu", "kernel": fam, "achieved": achieved / 1e3, "peak": peak / 1e3,
             "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-            "algorithmic_bytes": 16.0 * P.n * systems_per_step / max(launches_per_step, 1),
+            "algorithmic_bytes": 16.0 * P.n * systems_per_launch,
+            "systems_per_launch": systems_per_launch,
             "launches_per_step": launches_per_step,
+            "noop_launches_per_step": launches_per_step - real_launches,
             "share_of_step": (tot / args.steps) / ms_step,
             "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe: 1.195 TFLOP/s); "
                          "FP32: 128 FMA/clk/SM"}
