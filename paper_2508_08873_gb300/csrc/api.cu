@@ -520,18 +520,19 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     // per row.  Measured on GB300 (n = 4095, 256 steps, ms; wpp8 = warps per
     // sub-partition with 8-row chunks):
     //   systems  wpp8   MM=8   9      10     11     12     13     14     15     16
-    //   32       0.84   0.852  0.849  0.873  0.896  0.925  0.940  0.983  1.010  1.021
-    //   40       1.05   0.880  0.897  0.895  0.913  0.938  0.949  0.990  1.009  1.028
-    //   44       1.16   0.930  1.028  0.922  0.912  0.940  0.949  0.989  1.022  1.029
-    //   52       1.37   1.023  1.042  1.009  0.987  1.008  1.005  1.044  1.031  1.068
-    //   56       1.47   1.121  1.139  1.066  1.019  1.010  1.005  1.043  1.067  1.059
-    //   60       1.58   1.133  1.141  1.068  1.074  1.077  1.058  1.104  1.067  1.078
-    //   64       1.68   1.254  1.275  1.164  1.077  1.079  1.078  1.130  1.131  1.080
-    //   96       2.53   2.064  2.119  2.182  1.449  1.447  1.364  1.435  1.319  1.329
-    //   128      3.37   2.371  2.409  2.301  2.310  2.425  2.442  2.565  2.608  1.651
-    //   160      4.21   3.303  3.347  2.774  2.512  2.523  2.506  2.626  2.725  2.817
-    //   192      5.05   3.601  3.673  3.608  2.889  2.852  2.694  2.840  2.885  2.848
-    //   256      6.74   4.735  4.825  4.939  3.952  4.006  4.028  4.234  4.388  3.181
+    //   32       0.84   0.753  0.765  0.778  0.808  0.827  0.857  0.909  0.939  0.975
+    //   40       1.05   0.802  0.827  0.797  0.814  0.842  0.856  0.896  0.947  0.983
+    //   44       1.16   0.859  0.909  0.881  0.814  0.838  0.869  0.911  0.945  0.984
+    //   48       1.26   0.958  0.907  0.907  0.891  0.859  0.880  0.921  0.985  0.987
+    //   52       1.37   0.970  0.935  0.931  0.902  0.924  0.891  0.930  0.979  1.013
+    //   56       1.47   1.048  1.028  0.954  0.938  0.925  0.897  0.945  0.985  1.018
+    //   60       1.58   1.086  1.040  0.969  1.015  0.947  0.962  1.011  0.990  1.025
+    //   64       1.68   1.132  1.141  1.087  1.014  0.959  0.967  1.010  1.071  1.025
+    //   96       2.53   1.843  1.863  1.958  1.313  1.322  1.288  1.353  1.237  1.283
+    //   128      3.37   2.200  2.163  2.087  2.107  2.175  2.234  2.346  2.468  1.647
+    //   160      4.21   2.949  2.983  2.453  2.306  2.284  2.249  2.365  2.485  2.606
+    //   192      5.05   3.255  3.266  3.193  2.632  2.581  2.466  2.611  2.612  2.613
+    //   256      6.74   4.317  4.301  4.387  3.619  3.556  3.618  3.805  4.020  2.925
     // (the block kernel takes 1.30 ms from 40 to 64 systems and the one-CTA
     // kernel 3.80 ms at 192 and 256; beyond ~7 warps per sub-partition the
     // one-CTA kernel is faster: 5.94 against 6.51 ms at 512 systems).
@@ -544,7 +545,9 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
         c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       int mw = c->p_tri_wchunk;
       if (!mw)
-        mw = wpp <= 1.06 ? 8 : wpp <= 1.43 ? 11 : wpp <= 1.64 ? 13 : wpp <= 3.8 ? 16 : wpp <= 5.5 ? 13 : 16;
+        mw = wpp <= 1.0 ? 8 : wpp <= 1.1 ? 10 : wpp <= 1.2 ? 11 : wpp <= 1.3 ? 12
+           : wpp <= 1.5 ? 13 : wpp <= 1.75 ? 12 : wpp <= 2.8 ? 15 : wpp <= 3.8 ? 16
+           : wpp <= 5.5 ? 13 : 16;
       int Cw = ((op->n + mw - 1) / mw + 31) / 32;
       if (Cw < 2 && c->p_tri_wchunk == 0) {
         mw = 8;

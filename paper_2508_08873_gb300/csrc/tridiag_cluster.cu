@@ -522,15 +522,30 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
   const double* gpc = static_cast<const double*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
   const double* gsp = static_cast<const double*>(a.spk) + (size_t)c * 2 * 32;
   const double* gsu = static_cast<const double*>(a.sup);
-  double fl[MM], fi[MM], fu[MM], fp[MM], fq[MM];
+  // Factors in registers.  pP, pQ hold T fp and T fq, the chunk-interior
+  // solve T applied to the two spike vectors: the step's correction
+  // x <- x - yl fp - y fq is deferred into the next step, whose interior
+  // solve is then T x_local - yl T fp - y T fq (T is linear), so that this
+  // solve runs while the cluster barrier of the step completes.
+  double fl[MM], fi[MM], fu[MM], pP[MM], pQ[MM];
 #pragma unroll
   for (int i = 0; i < MM; ++i) {
     fl[i] = gco[(0 * MM + i) * 32 + tl];
     fi[i] = gco[(1 * MM + i) * 32 + tl];
     fu[i] = gco[(2 * MM + i) * 32 + tl];
-    fp[i] = gco[(3 * MM + i) * 32 + tl];
-    fq[i] = gco[(4 * MM + i) * 32 + tl];
+    pP[i] = gco[(3 * MM + i) * 32 + tl];
+    pQ[i] = gco[(4 * MM + i) * 32 + tl];
   }
+  // the chunk-interior solve (rows 0..MM-2; row MM-1 is the interface row)
+  auto interior_solve = [&](double* v) {
+#pragma unroll
+    for (int i = 1; i < MM - 1; ++i) v[i] -= fl[i] * v[i - 1];
+    v[MM - 2] *= fi[MM - 2];
+#pragma unroll
+    for (int i = MM - 3; i >= 0; --i) v[i] = v[i] * fi[i] - fu[i] * v[i + 1];
+  };
+  interior_solve(pP);
+  interior_solve(pQ);
   double k1[CLW_L], k2[CLW_L];
 #pragma unroll
   for (int l = 0; l < CLW_L; ++l) {
@@ -579,22 +594,30 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
         ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
     const double* gsys = (a.src.Q > 0 && a.src.map)
         ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
-    for (int j = 0; j < a.M; ++j) {
-      if (csys) {
-        for (int qq = 0; qq < a.src.Q; ++qq) {
-          const double cq_ = dt * csys[(size_t)j * a.src.Q + qq];
-          const double* gq = gsys + (size_t)qq * n;
+    // dt f(t_{j+1}) added to the right-hand side of step j on the interior
+    // rows; the interface row's term is returned
+    auto add_source = [&](int j) -> double {
+      double sI = 0.0;
+      if (!csys) return sI;
+      for (int qq = 0; qq < a.src.Q; ++qq) {
+        const double cq_ = dt * csys[(size_t)j * a.src.Q + qq];
+        const double* gq = gsys + (size_t)qq * n;
 #pragma unroll
-          for (int i = 0; i < MM; ++i)
-            if (r0 + i < n) x[i] += cq_ * gq[r0 + i];
-        }
+        for (int i = 0; i < MM - 1; ++i)
+          if (r0 + i < n) x[i] += cq_ * gq[r0 + i];
+        if (r0 + MM - 1 < n) sI += cq_ * gq[r0 + MM - 1];
       }
-      // chunk interior: forward elimination and back substitution
-#pragma unroll
-      for (int i = 1; i < MM - 1; ++i) x[i] -= fl[i] * x[i - 1];
-      x[MM - 2] *= fi[MM - 2];
-#pragma unroll
-      for (int i = MM - 3; i >= 0; --i) x[i] = x[i] * fi[i] - fu[i] * x[i + 1];
+      return sI;
+    };
+    // x[0..MM-2]: the interior solution of the current step (spike
+    // corrections of the previous step included); x[MM-1]: the right-hand
+    // side of the interface row
+    if (a.M > 0) {
+      x[MM - 1] += add_source(0);
+      interior_solve(x);
+    }
+    double y = 0.0, yl = 0.0;
+    for (int j = 0; j < a.M; ++j) {
       // interface row of the chunk
       double gnext = __shfl_down_sync(FULL, x[0], 1);
       if (tl == 31) gnext = 0.0;
@@ -617,7 +640,16 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
         double* dst = rpub[tl] + (pb * CL_MAXC + c) * 4;
         dst[0] = v0; dst[1] = v1; dst[2] = v2; dst[3] = v3;
       }
-      cl.sync();
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      // while the barrier completes: the next step's interior solve on the
+      // uncorrected interior values (its right-hand side x + dt f)
+      double sI = 0.0;                       // source of the interface row
+      const bool more = j + 1 < a.M;
+      if (more) {
+        sI = add_source(j + 1);
+        interior_solve(x);
+      }
+      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
       // super system: lane q forms the right-hand side of unknown q; Y_c and
       // Y_{c-1} are rows of the precomputed inverse applied by warp sums
       double rhs = 0.0;
@@ -633,13 +665,23 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
 #pragma unroll
       for (int o = CL_MAXC / 2; o > 0; o >>= 1) Ys += __shfl_xor_sync(FULL, Ys, o);
       const double Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
-      const double y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
-      double yl = __shfl_up_sync(FULL, y, 1);
+      y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
+      yl = __shfl_up_sync(FULL, y, 1);
       if (tl == 0) yl = Yl;
+      if (more) {
+        // the deferred correction, through the next step's interior solve
 #pragma unroll
-      for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - fp[i] * yl - fq[i] * y;
-      x[MM - 1] = y;
+        for (int i = 0; i < MM - 1; ++i) x[i] = x[i] - pP[i] * yl - pQ[i] * y;
+        x[MM - 1] = y + sI;
+      }
       pb ^= 1;
+    }
+    if (a.M > 0) {
+      // the last step's spike corrections (with fp, fq themselves)
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i)
+        x[i] = x[i] - gco[(3 * MM + i) * 32 + tl] * yl - gco[(4 * MM + i) * 32 + tl] * y;
+      x[MM - 1] = y;
     }
     const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
 #pragma unroll
