@@ -38,7 +38,7 @@ import numpy as np  # noqa: E402
 METRIC = "Parareal solves/s at 1e-8 rel err vs FP64 oracle"
 UNIT = "solves/s"
 TOL = 1e-8
-F64_DRAM_BYTES_PER_SYSTEM = 1.91e6 / 50
+F64_DRAM_BYTES_PER_SYSTEM = 2.31e6 / 62
 WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
 
 
@@ -543,8 +543,8 @@ def main():
     achieved = flops_step / (tot / args.steps) / 1e6 if tot > 0 else 0.0   # GFLOP/s
     peak = FP64_PEAK_GFLOPS if fam == "propagate_f64" else FP32_PEAK_GFLOPS
     # DRAM traffic of the FP64 fine-solve kernel, from one ncu capture on GB300
-    # (dram__bytes_read.sum + dram__bytes_write.sum of a 50-system launch of
-    # the 11-row-chunk variant: 1.91 MB read, nothing written back within the
+    # (dram__bytes_read.sum + dram__bytes_write.sum of a 62-system launch of
+    # the 12-row-chunk variant: 2.31 MB read, nothing written back within the
     # launch), per propagated system, times this run's systems per launch
     # per-launch figures over the launches that propagate (one per Parareal
     # iteration; the launches enqueued after the device-side stop return at
