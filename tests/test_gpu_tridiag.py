@@ -371,6 +371,37 @@ def test_warp_cluster_kernel_matches_block_kernel_and_oracle(ctx, orc, n, nvec, 
             assert rel(got[v], blk[v]) <= tol
 
 
+@pytest.mark.parametrize("M", [0, 1, 2, 3])
+def test_warp_cluster_kernel_few_steps(ctx, orc, M):
+    """The one-warp kernel defers each step's spike correction into the next
+    step's interior solve and applies the last one with the spike vectors
+    themselves: with 0 steps the input comes back unchanged, and 1, 2 and 3
+    steps (no deferred correction, one, two) match the oracle, with a source
+    term."""
+    n, nvec, Q = 2049, 5, 2
+    lo, di, up = W.adr1d_op(n)
+    dt = 1.0 / 4096
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    rng = np.random.default_rng(M)
+    X = rng.standard_normal((nvec, n))
+    g = rng.standard_normal((Q, n))
+    c = rng.standard_normal((nvec, max(M, 1), Q))[:, :M, :]
+    try:
+        ctx.set_param("tri_warp", 2)
+        if M == 0:
+            got = api.propagate(ctx, op, dt, M, X)
+        else:
+            got = api.propagate(ctx, op, dt, M, X, g=g, c=np.ascontiguousarray(c))
+    finally:
+        ctx.set_param("tri_warp", 0)
+    if M == 0:
+        np.testing.assert_array_equal(got, X)
+        return
+    want = orc.propagate(orc.Tridiag(lo, di, up), dt, M, X, g=g, cvals=c)
+    for v in range(nvec):
+        assert rel(got[v], want[v]) <= 1e-12
+
+
 # ---------------------------------------------------------------------------
 # classical Parareal (backward-Euler coarse step), the comparison method
 # ---------------------------------------------------------------------------
