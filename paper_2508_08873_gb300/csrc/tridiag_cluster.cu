@@ -1,5 +1,5 @@
 // Tridiagonal backward-Euler propagation with one system spread over a
-// thread-block cluster of C CTAs (2 <= C <= 8), for batches too small to fill
+// thread-block cluster of C CTAs (up to 16), for batches too small to fill
 // the GPU with one CTA per system (the Parareal fine solves: one system per
 // coarse interval, FP64).
 //
@@ -500,7 +500,10 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
 // interface system of a CTA is then solved by parallel cyclic reduction with
 // warp shuffles and the C x C super system by two warp sums, so a step needs
 // no block barrier at all: only the cluster barrier that publishes the four
-// values of every CTA.  (FP64, chunks of MM = 8..16 rows.)
+// values of every CTA.  That barrier is split into arrive and wait, and the
+// next step's interior solve runs between the two: the step's spike
+// correction is deferred into it (see below).  (FP64, chunks of MM = 8..16
+// rows; C = 1..16.)
 // ---------------------------------------------------------------------------
 constexpr int CLW_L = 5;    // PCR levels over the 31 local interface unknowns
 
