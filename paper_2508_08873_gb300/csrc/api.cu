@@ -767,24 +767,57 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   if ((s = small_svd(c, N, ell, Rz.as<double>(), rv.as<int>(), sv.as<double>(), Psi.as<double>(),
                      Phi.as<double>(), st.as<int>())))
     return s;
-  // ranks and singular values to the host: R_i, sigma_{R_i+1}, delta, eps
+  // R_i and S on the device, then the lift (step 6) and the chain matrices
+  // of the sweep; the host reads ranks, singular values and statuses once,
+  // at the end
+  const int Rm = std::max(rank, 1);
+  if ((s = dev_alloc(c, co->U, sizeof(double) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->V, sizeof(double) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->S, sizeof(double) * N * Rm))) return s;
+  if ((s = dev_alloc(c, co->U32, sizeof(float) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->V32, sizeof(float) * N * Rm * (size_t)n))) return s;
+  if ((s = dev_alloc(c, co->S32, sizeof(float) * N * Rm))) return s;
+  const bool ltc = lift_tc_applies(c, ell, rank, !f32);
+  if (!ltc) {
+    // the SIMT lift writes the rows below R_i only
+    cudaMemsetAsync(co->U.ptr, 0, co->U.bytes, c->stream);
+    cudaMemsetAsync(co->V.ptr, 0, co->V.bytes, c->stream);
+    cudaMemsetAsync(co->U32.ptr, 0, co->U32.bytes, c->stream);
+    cudaMemsetAsync(co->V32.ptr, 0, co->V32.bytes, c->stream);
+  }
+  k_finish_ranks<<<(N + 127) / 128, 128, 0, c->stream>>>(N, rank, ell, rw.as<int>(), rv.as<int>(),
+                                                         sv.as<double>(), Rid.as<int>(),
+                                                         co->S.as<double>(), co->S32.as<float>());
+  ++c->launches;
+  if (ltc) {
+    if ((s = lift_tc(c, N, ell, rank, n, Y.as<float>(), Z.as<float>(), Psi.as<double>(),
+                     Phi.as<double>(), Rid.as<int>(), co->U.as<double>(), co->V.as<double>(),
+                     co->U32.as<float>(), co->V32.as<float>(), st.as<int>())))
+      return s;
+  } else if ((s = lift(c, N, ell, rank, n, Y.ptr, Z.ptr, !f32, Psi.as<double>(), Phi.as<double>(),
+                       Rid.as<int>(), co->U.as<double>(), co->V.as<double>(), co->U32.as<float>(),
+                       co->V32.as<float>()))) {
+    return s;
+  }
+  if ((s = coarse_chain(c, co.get()))) return s;
   co->rank_w.resize(N);
   co->rank_v.resize(N);
   co->sigma.resize((size_t)N * ell);
   int svd_status = 0;
+  int tc_counts[2] = {0, 0};
   cudaMemcpyAsync(co->rank_w.data(), rw.ptr, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream);
   cudaMemcpyAsync(co->rank_v.data(), rv.ptr, sizeof(int) * N, cudaMemcpyDeviceToHost, c->stream);
   cudaMemcpyAsync(co->sigma.data(), sv.ptr, sizeof(double) * N * ell, cudaMemcpyDeviceToHost, c->stream);
   cudaMemcpyAsync(&svd_status, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  int tc_counts[2] = {0, 0};
   cudaMemcpyAsync(tc_counts, tcc.ptr, 2 * sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "build_coarse");
   co->orth_tc_w = tc_counts[0];
   co->orth_tc_v = tc_counts[1];
-  if (e) return cuda_err(c, e, "build_coarse");
-  if (svd_status & 4) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation failed");
+  if (svd_status & 4) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation or lift failed");
   if (svd_status & 2) return set_err(c, LRP_EBREAKDOWN, "rank-deficient two-sided sketch core");
   if (svd_status) return set_err(c, LRP_ENOTCONV, "Jacobi SVD did not converge");
+  // R_i, sigma_{R_i+1}, delta, eps (as k_finish_ranks)
   co->Ri.resize(N);
   co->delta = 0.0;
   co->eps = 0.0;
@@ -801,44 +834,6 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
     co->delta = std::max(co->delta, s1);
     co->eps = std::max(co->eps, sn);
   }
-  // step 6: lift the leading R_i singular vectors
-  const int Rm = std::max(rank, 1);
-  if ((s = dev_alloc(c, co->U, sizeof(double) * N * Rm * (size_t)n))) return s;
-  if ((s = dev_alloc(c, co->V, sizeof(double) * N * Rm * (size_t)n))) return s;
-  if ((s = dev_alloc(c, co->S, sizeof(double) * N * Rm))) return s;
-  if ((s = dev_alloc(c, co->U32, sizeof(float) * N * Rm * (size_t)n))) return s;
-  if ((s = dev_alloc(c, co->V32, sizeof(float) * N * Rm * (size_t)n))) return s;
-  if ((s = dev_alloc(c, co->S32, sizeof(float) * N * Rm))) return s;
-  cudaMemsetAsync(co->U.ptr, 0, co->U.bytes, c->stream);
-  cudaMemsetAsync(co->V.ptr, 0, co->V.bytes, c->stream);
-  cudaMemsetAsync(co->U32.ptr, 0, co->U32.bytes, c->stream);
-  cudaMemsetAsync(co->V32.ptr, 0, co->V32.bytes, c->stream);
-  if ((s = to_device(c, Rid.ptr, co->Ri.data(), sizeof(int) * N))) return s;
-  const bool ltc = lift_tc_applies(c, ell, rank, !f32);
-  if (ltc) {
-    if ((s = lift_tc(c, N, ell, rank, n, Y.as<float>(), Z.as<float>(), Psi.as<double>(),
-                     Phi.as<double>(), Rid.as<int>(), co->U.as<double>(), co->V.as<double>(),
-                     co->U32.as<float>(), co->V32.as<float>(), st.as<int>())))
-      return s;
-  } else if ((s = lift(c, N, ell, rank, n, Y.ptr, Z.ptr, !f32, Psi.as<double>(), Phi.as<double>(),
-                       Rid.as<int>(), co->U.as<double>(), co->V.as<double>(), co->U32.as<float>(),
-                       co->V32.as<float>()))) {
-    return s;
-  }
-  std::vector<double> S64((size_t)N * Rm, 0.0);
-  std::vector<float> S32f((size_t)N * Rm, 0.f);
-  for (int i = 0; i < N; ++i)
-    for (int r = 0; r < co->Ri[i]; ++r) {
-      S64[(size_t)i * Rm + r] = co->sigma[(size_t)i * ell + r];
-      S32f[(size_t)i * Rm + r] = (float)co->sigma[(size_t)i * ell + r];
-    }
-  if ((s = to_device(c, co->S.ptr, S64.data(), S64.size() * 8))) return s;
-  if ((s = to_device(c, co->S32.ptr, S32f.data(), S32f.size() * 4))) return s;
-  if ((s = coarse_chain(c, co.get()))) return s;
-  if (ltc) cudaMemcpyAsync(&svd_status, st.ptr, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
-  e = cudaStreamSynchronize(c->stream);
-  if (e) return cuda_err(c, e, "build_coarse");
-  if (ltc && (svd_status & 4)) return set_err(c, LRP_EBREAKDOWN, "tensor-core lift failed");
   *out = co.release();
   return LRP_OK;
 }

@@ -292,6 +292,11 @@ bool lift_tc_applies(Ctx* c, int ell, int R, int b_f64);
 lrp_status lift_tc(Ctx* c, int N, int ell, int R, int n, const float* W, const float* Vh,
                    const double* Psi, const double* Phi, const int* Ri, double* U, double* V,
                    float* U32, float* V32, int* status);
+// R_i = min(R, rank_w, rank_v) and S (FP64, FP32; zero beyond R_i) of every
+// interval from the ranks and singular values of the build (batch.cu).
+__global__ void k_finish_ranks(int N, int R, int ell, const int* __restrict__ rw,
+                               const int* __restrict__ rv, const double* __restrict__ sv,
+                               int* __restrict__ Ri, double* __restrict__ S, float* __restrict__ S32);
 // orth_tc when it applies and ws is large enough, else orth_cgs2.
 lrp_status orth_auto(Ctx* c, int N, int ell, int n, void* X, int x_f64, double tau, double* Rcoef,
                      int* rank, void* ws, size_t ws_bytes, int* status, int* tc_count = nullptr);
