@@ -304,7 +304,9 @@ lrp_status orth_cgs2(Ctx* c, int N, int ell, int n, void* X, int x_f64, double t
 // rather than once per warp.  The squared column norms are carried through
 // the rotations (|a_p'|^2 = |a_p|^2 - t a_p.a_q, |a_q'|^2 = |a_q|^2 +
 // t a_p.a_q) and recomputed from the columns at the start of every sweep,
-// so a round needs one dot product per pair.
+// so a round needs one dot product per pair.  The angle's tangent is formed
+// in FP32 (its divisions and square root cost FP64 issue slots otherwise);
+// cos and sin are formed from it in FP64.
 // ---------------------------------------------------------------------------
 constexpr int SVD_THREADS = 512;    // launch: 32 * ceil(pairs / 4) threads
 constexpr int SVD_MAX_SWEEPS = 60;
@@ -341,6 +343,7 @@ __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* _
   // convergence: every pair's cosine below m * eps (the usual one-sided
   // Jacobi threshold); a stricter eps keeps rotating on rounding noise
   const double eps = 2.220446049250313e-16 * m;
+  const double eps2 = eps * eps;
   int sweep = 0, done = (kv < 2);
   while (!done && sweep < SVD_MAX_SWEEPS) {
     if (threadIdx.x == 0) rotated = 0;
@@ -365,9 +368,20 @@ __global__ void __launch_bounds__(SVD_THREADS) k_jacobi(int ell, const double* _
         ga += __shfl_xor_sync(gmask, ga, 2);
         ga += __shfl_xor_sync(gmask, ga, 1);
         const double al = nrm[p], be = nrm[q];
-        if (ga == 0.0 || fabs(ga) <= eps * sqrt(al * be)) continue;
+        if (ga == 0.0 || ga * ga <= eps2 * (al * be)) continue;
+        // zeta (dimensionless) in FP64, the tangent of the rotation angle
+        // from it in FP32, cos and sin from the tangent in FP64: the rotation
+        // is orthogonal to FP64 accuracy whatever the angle's accuracy, which
+        // only sets how far a_p.a_q drops (a relative 1e-7 instead of 1e-16;
+        // the sweeps go on until every pair passes the FP64 test)
         const double zeta = (be - al) / (2.0 * ga);
-        const double tt = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0)));
+        double tt;
+        if (fabs(zeta) < 1e15) {
+          const float z = (float)zeta;
+          tt = (double)(copysignf(1.0f, z) / (fabsf(z) + sqrtf(fmaf(z, z, 1.0f))));
+        } else {
+          tt = 0.5 / zeta;
+        }
         const double cs = rsqrt(fma(tt, tt, 1.0));
         const double sn = cs * tt;
         for (int i = l8; i < m; i += 8) {
