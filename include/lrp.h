@@ -91,6 +91,10 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    every FP64 batch with n <= 4096;
  *   "tri_wchunk":    rows per chunk of the one-warp FP64 cluster kernel (8 to
  *                    16; 0 = automatic);
+ *   "tri_wsplit":    where the one-warp kernel runs the chunk-interior solve
+ *                    of the next step: 0 = all of it between the cluster
+ *                    barrier's arrive and wait, 1 (default) = its last third
+ *                    of backward rows after the wait, beside the super system;
  *   "tri_spt":       systems per thread of the cluster tridiagonal kernel (1, 2);
  *   "tri_group":     systems per CTA of the one-CTA-per-system tridiagonal
  *                    kernel (1..16, at most 512 threads per CTA);

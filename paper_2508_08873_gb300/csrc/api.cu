@@ -291,6 +291,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_wchunk") {
     if (value != 0 && (value < 8 || value > 16)) return LRP_EINVAL;
     c->p_tri_wchunk = value;
+  } else if (k == "tri_wsplit") {
+    if (value < 0 || value > 1) return LRP_EINVAL;
+    c->p_tri_wsplit = value;
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
     c->p_tri_group = value;
@@ -322,6 +325,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_chunk") *value = c->p_tri_chunk;
   else if (k == "tri_group") *value = c->p_tri_group;
   else if (k == "tri_wchunk") *value = c->p_tri_wchunk;
+  else if (k == "tri_wsplit") *value = c->p_tri_wsplit;
   else if (k == "orth_tc") *value = c->p_orth_tc;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
@@ -520,19 +524,22 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     // per row.  Measured on GB300 (n = 4095, 256 steps, ms; wpp8 = warps per
     // sub-partition with 8-row chunks):
     //   systems  wpp8   MM=8   9      10     11     12     13     14     15     16
-    //   32       0.84   0.753  0.765  0.778  0.808  0.827  0.857  0.909  0.939  0.975
-    //   40       1.05   0.802  0.827  0.797  0.814  0.842  0.856  0.896  0.947  0.983
-    //   44       1.16   0.859  0.909  0.881  0.814  0.838  0.869  0.911  0.945  0.984
-    //   48       1.26   0.958  0.907  0.907  0.891  0.859  0.880  0.921  0.985  0.987
-    //   52       1.37   0.970  0.935  0.931  0.902  0.924  0.891  0.930  0.979  1.013
-    //   56       1.47   1.048  1.028  0.954  0.938  0.925  0.897  0.945  0.985  1.018
-    //   60       1.58   1.086  1.040  0.969  1.015  0.947  0.962  1.011  0.990  1.025
-    //   64       1.68   1.132  1.141  1.087  1.014  0.959  0.967  1.010  1.071  1.025
-    //   96       2.53   1.843  1.863  1.958  1.313  1.322  1.288  1.353  1.237  1.283
-    //   128      3.37   2.200  2.163  2.087  2.107  2.175  2.234  2.346  2.468  1.647
-    //   160      4.21   2.949  2.983  2.453  2.306  2.284  2.249  2.365  2.485  2.606
-    //   192      5.05   3.255  3.266  3.193  2.632  2.581  2.466  2.611  2.612  2.613
-    //   256      6.74   4.317  4.301  4.387  3.619  3.556  3.618  3.805  4.020  2.925
+    //   16       0.42   0.653  0.661  0.718  0.743  0.808  0.813  0.852  0.922  0.972
+    //   24       0.63   0.686  0.674  0.722  0.743  0.823  0.814  0.852  0.929  0.979
+    //   32       0.84   0.697  0.692  0.735  0.749  0.827  0.815  0.855  0.934  0.982
+    //   40       1.05   0.742  0.768  0.747  0.767  0.830  0.815  0.854  0.941  0.987
+    //   44       1.16   0.813  0.845  0.814  0.766  0.827  0.843  0.883  0.941  0.984
+    //   48       1.26   0.897  0.845  0.892  0.852  0.852  0.845  0.886  0.976  0.987
+    //   52       1.37   0.916  0.877  0.896  0.856  0.915  0.844  0.886  0.976  1.010
+    //   56       1.47   1.028  0.951  0.908  0.856  0.917  0.845  0.886  0.976  1.016
+    //   60       1.58   1.029  0.971  0.914  0.956  0.926  0.961  1.021  0.976  1.027
+    //   64       1.68   1.079  1.102  1.031  0.957  0.938  0.964  1.023  1.096  1.027
+    //   80       2.11   1.706  1.742  1.177  1.088  1.166  1.076  1.140  1.097  1.160
+    //   96       2.53   1.754  1.773  1.869  1.272  1.327  1.215  1.287  1.231  1.274
+    //   128      3.37   2.100  2.060  1.977  2.011  2.170  2.178  2.300  2.445  1.634
+    //   160      4.21   2.825  2.842  2.355  2.218  2.281  2.190  2.316  2.459  2.596
+    //   192      5.05   3.160  3.129  3.040  2.499  2.569  2.435  2.580  2.618  2.599
+    //   256      6.74   4.110  4.136  4.194  3.440  3.575  3.544  3.749  3.962  2.904
     // (the block kernel takes 1.30 ms from 40 to 64 systems and the one-CTA
     // kernel 3.80 ms at 192 and 256; beyond ~7 warps per sub-partition the
     // one-CTA kernel is faster: 5.94 against 6.51 ms at 512 systems).
@@ -545,9 +552,8 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
         c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       int mw = c->p_tri_wchunk;
       if (!mw)
-        mw = wpp <= 1.0 ? 8 : wpp <= 1.1 ? 10 : wpp <= 1.2 ? 11 : wpp <= 1.3 ? 12
-           : wpp <= 1.5 ? 13 : wpp <= 1.75 ? 12 : wpp <= 2.8 ? 15 : wpp <= 3.8 ? 16
-           : wpp <= 5.5 ? 13 : 16;
+        mw = wpp <= 1.1 ? 8 : wpp <= 1.2 ? 11 : wpp <= 1.5 ? 13 : wpp <= 1.75 ? 12
+           : wpp <= 2.8 ? 13 : wpp <= 3.8 ? 16 : wpp <= 5.5 ? 13 : 16;
       int Cw = ((op->n + mw - 1) / mw + 31) / 32;
       if (Cw < 2 && c->p_tri_wchunk == 0) {
         mw = 8;

@@ -57,7 +57,8 @@ struct Ctx {
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
   int p_orth_tc = 1;         // tensor-core CholeskyQR2 and lift for FP32 sketches (1 on, 0 off)
-  int p_tri_wchunk = 0;      // rows per chunk of the one-warp cluster kernel (0 auto, 8, 16)
+  int p_tri_wchunk = 0;      // rows per chunk of the one-warp cluster kernel (0 auto, 8..16)
+  int p_tri_wsplit = 1;      // backward rows of the one-warp kernel after the barrier wait (0 none, 1 a third)
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
   // Caching allocator: released buffers are kept (up to pool_cap bytes) and
   // reused by later allocations of a similar size, so repeated builds and

@@ -1,0 +1,344 @@
+// Shared by the cluster tridiagonal propagators: the kernel arguments and the
+// one-warp cluster kernel (instantiated in tridiag_warp.cu and tridiag_warp_nosplit.cu).
+#pragma once
+#include <cooperative_groups.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrp {
+
+constexpr int CL_MAXC = 16;
+static_assert(CL_MAXC == 16, "the one-warp kernel splits the warp into two halves of CL_MAXC lanes");
+constexpr int CLW_L = 5;    // PCR levels over the 31 local interface unknowns of a one-warp CTA
+
+// Arguments of the cluster propagation kernels: cluster of C CTAs per system,
+// blockDim = Pc (one chunk per thread).  Clusters loop over systems.
+struct ClKArgs {
+  int n, Pc, C, L, M, nsys;
+  double dt;
+  double su, s1, bu, b1, b2;   // two-stage SDIRK coefficients (see StepCoef)
+  const void* coef;
+  const void* lpcr;
+  const void* spk;
+  const void* sup;
+  PropIn in;
+  PropOut out;
+  PropSrc src;
+};
+
+// One-warp cluster propagation, FP64 (chunks of 8..16 rows); S selects how
+// the chunk-interior solve is split around the cluster barrier: S = 0 runs
+// all of it between arrive and wait, S = 1 leaves its last (MM-2)/3
+// backward rows after the wait (see the kernel).  Returns LRP_EINVAL for an
+// unsupported plan.
+template <int S>
+lrp_status tri_launch_warp(Ctx* c, ClPlan* pl, ClKArgs& a);
+
+#ifdef LRP_TRI_WARP_KERNEL
+namespace cg = cooperative_groups;
+
+// ---------------------------------------------------------------------------
+// One-warp variant: every CTA of the cluster is a single warp of 32 chunks
+// (Pc = 32), with its slice of the factorisation held in registers.  The local
+// interface system of a CTA is then solved by parallel cyclic reduction with
+// warp shuffles and the C x C super system by two warp sums, so a step needs
+// no block barrier at all: only the cluster barrier that publishes the four
+// values of every CTA.  (FP64, chunks of MM = 8..16 rows; C = 1..16.)
+//
+// Per step j the work splits into
+//   * a chain through the cluster: interface row, PCR, publish, barrier,
+//     super system, and the spike correction of rows 0 and MM-2 that the
+//     next step's interface row reads;
+//   * work off that chain: the chunk-interior solve of the next step and the
+//     correction of the other rows.
+// The spike correction x <- x - yl fp - y fq of a step is deferred into the
+// next step, whose interior solve is then T x_local - yl T fp - y T fq (T is
+// linear), so the interior solve does not wait for the barrier.  The loop is
+// rotated so that the super system, the correction and the next step's PCR
+// form one straight block (no branch between them: the compiler interleaves
+// the independent FMAs of the correction with the PCR's shuffle chains), and
+// the interior solve sits between the barrier's arrive and wait, except its
+// last HLO backward rows, which follow the wait and run beside the super
+// system's warp sums.
+// ---------------------------------------------------------------------------
+template <int MM, bool SRC, int HLO>
+__global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
+  static_assert(HLO >= 0 && HLO <= MM - 2, "split row out of range");
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double pubg[2][CL_MAXC][4];
+  __shared__ double* rpub[CL_MAXC];
+  const int C = a.C;
+  const int c = (int)cl.block_rank();
+  const int tl = threadIdx.x;
+  const int t = c * 32 + tl;
+  const int n = a.n;
+  const int r0 = t * MM;
+  const unsigned FULL = 0xffffffffu;
+  // ---- this thread's factors, in registers ---------------------------------
+  const double* gco = static_cast<const double*>(a.coef) + (size_t)c * 5 * MM * 32;
+  const double* gpc = static_cast<const double*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
+  const double* gsp = static_cast<const double*>(a.spk) + (size_t)c * 2 * 32;
+  const double* gsu = static_cast<const double*>(a.sup);
+  // pP, pQ hold T fp and T fq, the chunk-interior solve T applied to the two
+  // spike vectors (the deferred correction)
+  double fl[MM], fi[MM], fu[MM], pP[MM], pQ[MM];
+#pragma unroll
+  for (int i = 0; i < MM; ++i) {
+    fl[i] = gco[(0 * MM + i) * 32 + tl];
+    fi[i] = gco[(1 * MM + i) * 32 + tl];
+    fu[i] = gco[(2 * MM + i) * 32 + tl];
+    pP[i] = gco[(3 * MM + i) * 32 + tl];
+    pQ[i] = gco[(4 * MM + i) * 32 + tl];
+  }
+  // the chunk-interior solve (rows 0..MM-2; row MM-1 is the interface row):
+  // forward sweep, then the backward sweep in two parts, rows MM-3..HLO and
+  // HLO-1..0; each backward row is one FMA on the chain (the scaling by the
+  // inverse pivot is off it)
+  auto fwd = [&](double* v) {
+#pragma unroll
+    for (int i = 1; i < MM - 1; ++i) v[i] = fma(-fl[i], v[i - 1], v[i]);
+    v[MM - 2] *= fi[MM - 2];
+  };
+  auto bwd_hi = [&](double* v) {
+#pragma unroll
+    for (int i = MM - 3; i >= HLO; --i) v[i] = fma(-fu[i], v[i + 1], v[i] * fi[i]);
+  };
+  auto bwd_lo = [&](double* v) {
+#pragma unroll
+    for (int i = HLO - 1; i >= 0; --i) v[i] = fma(-fu[i], v[i + 1], v[i] * fi[i]);
+  };
+  fwd(pP); bwd_hi(pP); bwd_lo(pP);
+  fwd(pQ); bwd_hi(pQ); bwd_lo(pQ);
+  double k1[CLW_L], k2[CLW_L];
+#pragma unroll
+  for (int l = 0; l < CLW_L; ++l) {
+    k1[l] = gpc[l * 32 + tl];
+    k2[l] = gpc[(CLW_L + l) * 32 + tl];
+  }
+  const double dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] : 0.0;
+  const double p2 = gsp[tl], q2 = gsp[32 + tl];
+  // super system: both half-warps form row q = tl mod 16 (q < C); the lower
+  // half holds column q of inverse row c, the upper half column q of inverse
+  // row c-1, so one product and four butterfly levels give Y_c and Y_{c-1}
+  const int q = tl & (CL_MAXC - 1);
+  const double sa = q < C ? gsu[6 * q + 0] : 0.0;
+  const double sc1 = q < C ? gsu[6 * q + 1] : 0.0;
+  const double sc2 = q < C ? gsu[6 * q + 2] : 0.0;
+  const double* minv = gsu + 6 * CL_MAXC;
+  const double msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
+                                            : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : 0.0))
+                            : 0.0;
+  if (tl < C) rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
+  __syncwarp();
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
+  const double dt = a.dt;
+  const int nclu = gridDim.x / C;
+  int pb = 0;
+  for (int sys = blockIdx.x / C; sys < a.nsys; sys += nclu) {
+    double x[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      const int r = r0 + i;
+      double v = 0.0;
+      if (r < n) {
+        if (a.in.gen)
+          v = gauss<double>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                            (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+        else if (a.in.x == nullptr)
+          v = 0.0;
+        else if (a.in.x_f64)
+          v = static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+        else
+          v = (double)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+      }
+      x[i] = v;
+    }
+    if (a.M <= 0) {
+      // no step: the output is the input
+    } else {
+      const double* csys = nullptr;
+      const double* gsys = nullptr;
+      if (SRC) {
+        csys = a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys);
+        gsys = a.src.map ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
+      }
+      // dt f(t_{j+1}) added to the right-hand side of step j on the interior
+      // rows; the interface row's term is returned
+      auto add_source = [&](int j) -> double {
+        double sI = 0.0;
+        for (int qq = 0; qq < a.src.Q; ++qq) {
+          const double cq_ = dt * csys[(size_t)j * a.src.Q + qq];
+          const double* gq = gsys + (size_t)qq * n;
+#pragma unroll
+          for (int i = 0; i < MM - 1; ++i)
+            if (r0 + i < n) x[i] += cq_ * gq[r0 + i];
+          if (r0 + MM - 1 < n) sI += cq_ * gq[r0 + MM - 1];
+        }
+        return sI;
+      };
+      double z0 = 0.0, y = 0.0, yl = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      // interface row and local PCR; reads x[0] (of the next lane), x[MM-2]
+      // and x[MM-1]
+      auto pcr = [&]() {
+        double gnext = __shfl_down_sync(FULL, x[0], 1);
+        if (tl == 31) gnext = 0.0;
+        double r = x[MM - 1] - fl[MM - 1] * x[MM - 2] - fu[MM - 1] * gnext;
+        // local PCR over lanes 0..30 (lane 31 is the CTA's super unknown)
+#pragma unroll
+        for (int l = 0; l < CLW_L; ++l) {
+          const double rm = __shfl_up_sync(FULL, r, 1 << l);
+          const double rp = __shfl_down_sync(FULL, r, 1 << l);
+          if (tl < 31) r = r - k1[l] * rm - k2[l] * rp;
+        }
+        z0 = r * dv;                           // 0 on lane 31 (dv = 0)
+        // z0 of the first and last local unknown, the super row's r, the
+        // first row of the first chunk
+        v0 = __shfl_sync(FULL, z0, 0);
+        v1 = __shfl_sync(FULL, z0, 30);
+        v2 = __shfl_sync(FULL, r, 31);
+        v3 = __shfl_sync(FULL, x[0], 0);
+      };
+      // publication of the CTA's four values: lane q stores into CTA q
+      auto publish = [&]() {
+        if (tl < C) {
+          double* dst = rpub[tl] + (pb * CL_MAXC + c) * 4;
+          dst[0] = v0; dst[1] = v1; dst[2] = v2; dst[3] = v3;
+        }
+      };
+      // super system: lane q forms the right-hand side of unknown q; Y_c and
+      // Y_{c-1} are rows of the precomputed inverse applied by warp sums
+      auto super_solve = [&]() {
+        double rhs = 0.0;
+        if (q < C) {
+          const double* pq = &pubg[pb][q][0];
+          rhs = fma(-sa, pq[1], pq[2]);
+          if (q + 1 < C) {
+            const double* pn = &pubg[pb][q + 1][0];
+            rhs = fma(-sc2, pn[3], fma(-sc1, pn[0], rhs));
+          }
+        }
+        double Ys = msel * rhs;
+#pragma unroll
+        for (int o = CL_MAXC / 2; o > 0; o >>= 1) Ys += __shfl_xor_sync(FULL, Ys, o);
+        const double Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
+        y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
+        yl = __shfl_up_sync(FULL, y, 1);
+        if (tl == 0) yl = Yl;
+      };
+      // x[0..MM-2]: the interior solution of the current step (spike
+      // corrections of the previous step included); x[MM-1]: the right-hand
+      // side of the interface row
+      if (SRC) x[MM - 1] += add_source(0);
+      fwd(x); bwd_hi(x); bwd_lo(x);
+      pcr();
+      publish();
+      for (int j = 0; j + 1 < a.M; ++j) {
+        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        // while the barrier completes: the next step's interior solve on the
+        // uncorrected interior values (its right-hand side x + dt f)
+        double sI = 0.0;                     // source of the interface row
+        if (SRC) sI = add_source(j + 1);
+        fwd(x);
+        bwd_hi(x);
+        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        super_solve();
+        bwd_lo(x);
+        // the deferred correction, through the next step's interior solve
+        // (rows 0 and MM-2 feed the next interface row)
+        x[0] = fma(-pP[0], yl, fma(-pQ[0], y, x[0]));
+        x[MM - 2] = fma(-pP[MM - 2], yl, fma(-pQ[MM - 2], y, x[MM - 2]));
+        x[MM - 1] = SRC ? y + sI : y;
+        pb ^= 1;
+        pcr();
+#pragma unroll
+        for (int i = 1; i < MM - 2; ++i) x[i] = fma(-pP[i], yl, fma(-pQ[i], y, x[i]));
+        publish();
+      }
+      // the last step: its spike corrections with fp, fq themselves
+      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+      super_solve();
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i)
+        x[i] = x[i] - gco[(3 * MM + i) * 32 + tl] * yl - gco[(4 * MM + i) * 32 + tl] * y;
+      x[MM - 1] = y;
+      pb ^= 1;
+    }
+    const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      const int r = r0 + i;
+      if (r < n) {
+        if (a.out.y_f64)
+          static_cast<double*>(a.out.y)[oy + r] = x[i];
+        else
+          static_cast<float*>(a.out.y)[oy + r] = (float)x[i];
+      }
+    }
+  }
+  cl.sync();  // no CTA leaves while others may still store into its shared memory
+}
+
+template <int MM, bool SRC, int HLO>
+static lrp_status launch_cl_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  const int C = pl->C;
+  auto kern = k_tri_cluster_w<MM, SRC, HLO>;
+  cudaError_t e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e) return cuda_err(c, e, "cluster size 16 not available");
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(32);
+  cfg.gridDim = dim3(C);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c->stream;
+  int maxc = 0;
+  e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+  if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
+  const int ncl = std::min(a.nsys, maxc);
+  cfg.gridDim = dim3(ncl * C);
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "propagate_f64", &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  timer_end(c, "propagate_f64", ev);
+  if (e) return cuda_err(c, e, "k_tri_cluster_w launch");
+  return LRP_OK;
+}
+
+template <int MM, int S>
+static lrp_status launch_cl_w_src(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  constexpr int HLO = S == 0 ? 0 : (MM - 2) / 3;
+  if (a.src.Q > 0) return launch_cl_w<MM, true, HLO>(c, pl, a);
+  return launch_cl_w<MM, false, HLO>(c, pl, a);
+}
+
+template <int S>
+lrp_status tri_launch_warp(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  switch (pl->m) {
+    case 16: return launch_cl_w_src<16, S>(c, pl, a);
+    case 15: return launch_cl_w_src<15, S>(c, pl, a);
+    case 14: return launch_cl_w_src<14, S>(c, pl, a);
+    case 13: return launch_cl_w_src<13, S>(c, pl, a);
+    case 12: return launch_cl_w_src<12, S>(c, pl, a);
+    case 11: return launch_cl_w_src<11, S>(c, pl, a);
+    case 10: return launch_cl_w_src<10, S>(c, pl, a);
+    case 9: return launch_cl_w_src<9, S>(c, pl, a);
+    case 8: return launch_cl_w_src<8, S>(c, pl, a);
+    default: return set_err(c, LRP_EINVAL, "warp cluster chunk length out of range");
+  }
+}
+#endif  // LRP_TRI_WARP_KERNEL
+
+}  // namespace lrp

@@ -402,6 +402,39 @@ def test_warp_cluster_kernel_few_steps(ctx, orc, M):
         assert rel(got[v], want[v]) <= 1e-12
 
 
+@pytest.mark.parametrize("wsplit", [0, 1])
+@pytest.mark.parametrize("wchunk", [8, 12, 16])
+@pytest.mark.parametrize("n,nvec,Q,M", [(3000, 7, 2, 9), (1025, 9, 0, 9), (2049, 5, 2, 1),
+                                        (2049, 5, 0, 2)])
+def test_warp_cluster_kernel_split_variants(ctx, orc, n, nvec, Q, M, wchunk, wsplit):
+    """The split of the chunk-interior solve around the cluster barrier
+    (tri_wsplit 0: all of it before the wait; 1, the default: its last
+    backward rows after it) changes only the order of independent work: both
+    variants match the oracle, with and without a source, for 1, 2 and 9
+    steps."""
+    lo, di, up = W.adr1d_op(n)
+    dt = 1.0 / 16384
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    rng = np.random.default_rng(n + M)
+    X = rng.standard_normal((nvec, n))
+    g = rng.standard_normal((Q, n)) if Q else None
+    c = rng.standard_normal((nvec, M, Q)) if Q else None
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    try:
+        ctx.set_param("tri_warp", 2)
+        ctx.set_param("tri_wchunk", wchunk)
+        ctx.set_param("tri_wsplit", wsplit)
+        got = api.propagate(ctx, op, dt, M, X, g=g, c=c)
+    finally:
+        ctx.set_param("tri_warp", 0)
+        ctx.set_param("tri_wchunk", 0)
+        ctx.set_param("tri_wsplit", 1)
+    want = orc.propagate(orc.Tridiag(lo, di, up), dt, M, X, g=g, cvals=c)
+    for v in range(nvec):
+        assert rel(got[v], want[v]) <= tol
+
+
 # ---------------------------------------------------------------------------
 # classical Parareal (backward-Euler coarse step), the comparison method
 # ---------------------------------------------------------------------------
