@@ -38,7 +38,9 @@ import numpy as np  # noqa: E402
 METRIC = "Parareal solves/s at 1e-8 rel err vs FP64 oracle"
 UNIT = "solves/s"
 TOL = 1e-8
-F64_DRAM_BYTES_PER_SYSTEM = 2.31e6 / 62
+# DRAM bytes per system of the FP64 fine-solve kernel, from one ncu capture of
+# k_tri_cluster_w<12, false, 3> (62 systems: 2.3086 MB read, 0 written)
+F64_DRAM_BYTES_PER_SYSTEM = 2.3086e6 / 62
 WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
 
 
@@ -561,8 +563,8 @@ def main():
             "launches_per_step": launches_per_step,
             "noop_launches_per_step": launches_per_step - real_launches,
             "share_of_step": (tot / args.steps) / ms_step,
-            "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz (probe: 1.195 TFLOP/s); "
-                         "FP32: 128 FMA/clk/SM"}
+            "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz nominal (a throughput probe "
+                         "reaches 1.6 FMA/clk/SM = 1.007 TFLOP/s); FP32: 128 FMA/clk/SM"}
     kernels = {f: {"launches": v[0], "ms_total": v[1]} for f, v in kern.items()}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
