@@ -91,6 +91,10 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    every FP64 batch with n <= 4096;
  *   "tri_wchunk":    rows per chunk of the one-warp FP64 cluster kernel (8 to
  *                    16; 0 = automatic);
+ *   "tri_wblock":    one system per CTA of C warps (the one-warp kernel's
+ *                    steps with the exchange in shared memory): 0 = automatic
+ *                    (FP32 batches that do not take a cluster), 1 = always
+ *                    (FP64: at most 8 warps, else LRP_EINVAL), 2 = never;
  *   "tri_wsplit":    where the one-warp kernel runs the chunk-interior solve
  *                    of the next step: 0 = all of it between the cluster
  *                    barrier's arrive and wait, 1 (default) = its last third

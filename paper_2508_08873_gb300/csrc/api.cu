@@ -294,6 +294,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_wsplit") {
     if (value < 0 || value > 1) return LRP_EINVAL;
     c->p_tri_wsplit = value;
+  } else if (k == "tri_wblock") {
+    if (value < 0 || value > 2) return LRP_EINVAL;
+    c->p_tri_wblock = value;
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
     c->p_tri_group = value;
@@ -326,6 +329,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_group") *value = c->p_tri_group;
   else if (k == "tri_wchunk") *value = c->p_tri_wchunk;
   else if (k == "tri_wsplit") *value = c->p_tri_wsplit;
+  else if (k == "tri_wblock") *value = c->p_tri_wblock;
   else if (k == "orth_tc") *value = c->p_orth_tc;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
@@ -548,7 +552,7 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     // (n = 511 and 1023, 16 systems, 64 steps: 0.162 / 0.167 ms against 0.254 /
     // 0.267 ms for the one-CTA kernel; n = 255, one CTA: 0.160 against 0.146)
     const bool warp_auto = c->p_tri_warp == 0 && Cw8 >= 2 && Cw8 <= 16 && wpp <= 7.0;
-    if ((warp_auto || c->p_tri_warp == 2) && prec == 0 && c->p_tri_cluster == 0 &&
+    if ((warp_auto || c->p_tri_warp == 2) && prec == 0 && c->p_tri_wblock != 1 && c->p_tri_cluster == 0 &&
         c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
       int mw = c->p_tri_wchunk;
       if (!mw)
@@ -564,6 +568,28 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
         lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, mw, &cp, 1);
         if (s) return s;
         return tri_propagate_cluster(c, cp, M, nsys, prec, 1, in, out, src);
+      }
+    }
+    // FP32 batches (the sketches), and FP64 on request: one system per CTA
+    // of C warps (k_tri_block_w), the one-warp kernel's steps with the
+    // exchange through shared memory; chunks of 8, 12 or 16 rows.  Measured
+    // on GB300 (FP32, 256 steps, ms per launch; the register-chunk kernel
+    // k_tri_propagate_rc in brackets): n = 4095, 1536 systems: 16-row chunks
+    // 0.731, 12-row 1.265, 8-row 1.255 (1.012); 192 systems: 0.143 (0.289);
+    // n = 255, 64 steps, 1536 systems: 8-row 0.032, 16-row 0.035 (0.062).
+    // In FP64 it does not beat the one-CTA kernel (n = 4095, 1536 systems:
+    // 17.86 against 17.78 ms) and runs only on request.
+    {
+      const int wc = c->p_tri_wchunk;
+      const int mb = (wc == 8 || wc == 12 || wc == 16) ? wc : op->n >= 1024 ? 16 : 8;
+      const int Cb = ((op->n + mb - 1) / mb + 31) / 32;
+      const bool blk_auto = c->p_tri_wblock == 0 && prec == 1 && C == 1 && c->p_tri_cluster == 0 &&
+                            c->p_tri_chunk == 0 && c->p_tri_spt == 0;
+      if ((blk_auto || c->p_tri_wblock == 1) && Cb >= 1 && Cb <= 16) {
+        ClPlan* cp = nullptr;
+        lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cb, mb, &cp, 1);
+        if (s) return s;
+        return tri_propagate_warp_block(c, cp, M, nsys, prec, in, out, src);
       }
     }
     if (C > 1) {

@@ -59,6 +59,7 @@ struct Ctx {
   int p_orth_tc = 1;         // tensor-core CholeskyQR2 and lift for FP32 sketches (1 on, 0 off)
   int p_tri_wchunk = 0;      // rows per chunk of the one-warp cluster kernel (0 auto, 8..16)
   int p_tri_wsplit = 1;      // backward rows of the one-warp kernel after the barrier wait (0 none, 1 a third)
+  int p_tri_wblock = 0;      // one-CTA-per-system warp kernel: 0 auto (FP32), 1 always, 2 never
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
   // Caching allocator: released buffers are kept (up to pool_cap bytes) and
   // reused by later allocations of a similar size, so repeated builds and
@@ -226,6 +227,10 @@ lrp_status tri_propagate(Ctx* c, Operator* op, TriPlan* plan, int M, int nsys, i
 // warp = 1: the one-warp-per-CTA FP64 kernel (8-row chunks, 32 chunks per CTA)
 lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, int C, int m,
                                 ClPlan** out, int warp = 0);
+// one system per CTA of C warps, with the factorisation of a warp plan
+// (tri_get_cluster_plan with warp = 1); prec 0 = FP64, 1 = FP32
+lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int prec,
+                                    const PropIn& in, const PropOut& out, const PropSrc& src);
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src,
                                  int stepper = 0);

@@ -37,16 +37,26 @@ struct ClKArgs {
 template <int S>
 lrp_status tri_launch_warp(Ctx* c, ClPlan* pl, ClKArgs& a);
 
+// One system per CTA of C warps (T = float or double; chunks of 8, 12 or 16
+// rows), coefficients from a warp cluster plan (ClPlan with warp = 1) in T.
+template <typename T>
+lrp_status tri_launch_warp_block(Ctx* c, ClPlan* pl, ClKArgs& a);
+
 #ifdef LRP_TRI_WARP_KERNEL
 namespace cg = cooperative_groups;
 
+__device__ __forceinline__ double fmaT(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmaT(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
 // ---------------------------------------------------------------------------
-// One-warp variant: every CTA of the cluster is a single warp of 32 chunks
-// (Pc = 32), with its slice of the factorisation held in registers.  The local
-// interface system of a CTA is then solved by parallel cyclic reduction with
-// warp shuffles and the C x C super system by two warp sums, so a step needs
-// no block barrier at all: only the cluster barrier that publishes the four
-// values of every CTA.  (FP64, chunks of MM = 8..16 rows; C = 1..16.)
+// The steps of a system split over C units of one warp each (32 chunks per
+// warp), each unit with its slice of the factorisation held in registers:
+// the units are the one-warp CTAs of a cluster (k_tri_cluster_w, FP64: the
+// Parareal fine solves) or the warps of one CTA (k_tri_block_w, FP32 or
+// FP64: the sketches).  The local interface system of a unit is solved by
+// parallel cyclic reduction with warp shuffles and the C x C super system by
+// two warp sums, so a step needs one exchange of four values per unit and
+// one barrier (cluster or block).  (Chunks of MM = 8..16 rows; C = 1..16.)
 //
 // Per step j the work splits into
 //   * a chain through the cluster: interface row, PCR, publish, barrier,
@@ -64,28 +74,23 @@ namespace cg = cooperative_groups;
 // last HLO backward rows, which follow the wait and run beside the super
 // system's warp sums.
 // ---------------------------------------------------------------------------
-template <int MM, bool SRC, int HLO>
-__global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
+template <typename T, int MM, bool SRC, int HLO, class X>
+__device__ __forceinline__ void warp_steps(const ClKArgs& a, X& xch, int c, int tl, int sys0,
+                                           int dsys) {
   static_assert(HLO >= 0 && HLO <= MM - 2, "split row out of range");
-  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
-  cg::cluster_group cl = cg::this_cluster();
-  __shared__ double pubg[2][CL_MAXC][4];
-  __shared__ double* rpub[CL_MAXC];
   const int C = a.C;
-  const int c = (int)cl.block_rank();
-  const int tl = threadIdx.x;
   const int t = c * 32 + tl;
   const int n = a.n;
   const int r0 = t * MM;
   const unsigned FULL = 0xffffffffu;
   // ---- this thread's factors, in registers ---------------------------------
-  const double* gco = static_cast<const double*>(a.coef) + (size_t)c * 5 * MM * 32;
-  const double* gpc = static_cast<const double*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
-  const double* gsp = static_cast<const double*>(a.spk) + (size_t)c * 2 * 32;
-  const double* gsu = static_cast<const double*>(a.sup);
+  const T* gco = static_cast<const T*>(a.coef) + (size_t)c * 5 * MM * 32;
+  const T* gpc = static_cast<const T*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
+  const T* gsp = static_cast<const T*>(a.spk) + (size_t)c * 2 * 32;
+  const T* gsu = static_cast<const T*>(a.sup);
   // pP, pQ hold T fp and T fq, the chunk-interior solve T applied to the two
   // spike vectors (the deferred correction)
-  double fl[MM], fi[MM], fu[MM], pP[MM], pQ[MM];
+  T fl[MM], fi[MM], fu[MM], pP[MM], pQ[MM];
 #pragma unroll
   for (int i = 0; i < MM; ++i) {
     fl[i] = gco[(0 * MM + i) * 32 + tl];
@@ -98,62 +103,58 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
   // forward sweep, then the backward sweep in two parts, rows MM-3..HLO and
   // HLO-1..0; each backward row is one FMA on the chain (the scaling by the
   // inverse pivot is off it)
-  auto fwd = [&](double* v) {
+  auto fwd = [&](T* v) {
 #pragma unroll
-    for (int i = 1; i < MM - 1; ++i) v[i] = fma(-fl[i], v[i - 1], v[i]);
+    for (int i = 1; i < MM - 1; ++i) v[i] = fmaT(-fl[i], v[i - 1], v[i]);
     v[MM - 2] *= fi[MM - 2];
   };
-  auto bwd_hi = [&](double* v) {
+  auto bwd_hi = [&](T* v) {
 #pragma unroll
-    for (int i = MM - 3; i >= HLO; --i) v[i] = fma(-fu[i], v[i + 1], v[i] * fi[i]);
+    for (int i = MM - 3; i >= HLO; --i) v[i] = fmaT(-fu[i], v[i + 1], v[i] * fi[i]);
   };
-  auto bwd_lo = [&](double* v) {
+  auto bwd_lo = [&](T* v) {
 #pragma unroll
-    for (int i = HLO - 1; i >= 0; --i) v[i] = fma(-fu[i], v[i + 1], v[i] * fi[i]);
+    for (int i = HLO - 1; i >= 0; --i) v[i] = fmaT(-fu[i], v[i + 1], v[i] * fi[i]);
   };
   fwd(pP); bwd_hi(pP); bwd_lo(pP);
   fwd(pQ); bwd_hi(pQ); bwd_lo(pQ);
-  double k1[CLW_L], k2[CLW_L];
+  T k1[CLW_L], k2[CLW_L];
 #pragma unroll
   for (int l = 0; l < CLW_L; ++l) {
     k1[l] = gpc[l * 32 + tl];
     k2[l] = gpc[(CLW_L + l) * 32 + tl];
   }
-  const double dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] : 0.0;
-  const double p2 = gsp[tl], q2 = gsp[32 + tl];
+  const T dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] : T(0);
+  const T p2 = gsp[tl], q2 = gsp[32 + tl];
   // super system: both half-warps form row q = tl mod 16 (q < C); the lower
   // half holds column q of inverse row c, the upper half column q of inverse
   // row c-1, so one product and four butterfly levels give Y_c and Y_{c-1}
   const int q = tl & (CL_MAXC - 1);
-  const double sa = q < C ? gsu[6 * q + 0] : 0.0;
-  const double sc1 = q < C ? gsu[6 * q + 1] : 0.0;
-  const double sc2 = q < C ? gsu[6 * q + 2] : 0.0;
-  const double* minv = gsu + 6 * CL_MAXC;
-  const double msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
-                                            : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : 0.0))
-                            : 0.0;
-  if (tl < C) rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
-  __syncwarp();
-  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
-  const double dt = a.dt;
-  const int nclu = gridDim.x / C;
+  const T sa = q < C ? gsu[6 * q + 0] : T(0);
+  const T sc1 = q < C ? gsu[6 * q + 1] : T(0);
+  const T sc2 = q < C ? gsu[6 * q + 2] : T(0);
+  const T* minv = gsu + 6 * CL_MAXC;
+  const T msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
+                                       : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : T(0)))
+                       : T(0);
+  const T dt = (T)a.dt;
   int pb = 0;
-  for (int sys = blockIdx.x / C; sys < a.nsys; sys += nclu) {
-    double x[MM];
+  for (int sys = sys0; sys < a.nsys; sys += dsys) {
+    T x[MM];
 #pragma unroll
     for (int i = 0; i < MM; ++i) {
       const int r = r0 + i;
-      double v = 0.0;
+      T v = T(0);
       if (r < n) {
         if (a.in.gen)
-          v = gauss<double>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+          v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                             (uint32_t)(sys % a.in.ncol), (uint32_t)r);
         else if (a.in.x == nullptr)
-          v = 0.0;
+          v = T(0);
         else if (a.in.x_f64)
-          v = static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+          v = (T)static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
         else
-          v = (double)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+          v = (T)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
       }
       x[i] = v;
     }
@@ -168,30 +169,30 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
       }
       // dt f(t_{j+1}) added to the right-hand side of step j on the interior
       // rows; the interface row's term is returned
-      auto add_source = [&](int j) -> double {
-        double sI = 0.0;
+      auto add_source = [&](int j) -> T {
+        T sI = T(0);
         for (int qq = 0; qq < a.src.Q; ++qq) {
-          const double cq_ = dt * csys[(size_t)j * a.src.Q + qq];
+          const T cq_ = dt * (T)csys[(size_t)j * a.src.Q + qq];
           const double* gq = gsys + (size_t)qq * n;
 #pragma unroll
           for (int i = 0; i < MM - 1; ++i)
-            if (r0 + i < n) x[i] += cq_ * gq[r0 + i];
-          if (r0 + MM - 1 < n) sI += cq_ * gq[r0 + MM - 1];
+            if (r0 + i < n) x[i] += cq_ * (T)gq[r0 + i];
+          if (r0 + MM - 1 < n) sI += cq_ * (T)gq[r0 + MM - 1];
         }
         return sI;
       };
-      double z0 = 0.0, y = 0.0, yl = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      T z0 = T(0), y = T(0), yl = T(0), v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0);
       // interface row and local PCR; reads x[0] (of the next lane), x[MM-2]
       // and x[MM-1]
       auto pcr = [&]() {
-        double gnext = __shfl_down_sync(FULL, x[0], 1);
-        if (tl == 31) gnext = 0.0;
-        double r = x[MM - 1] - fl[MM - 1] * x[MM - 2] - fu[MM - 1] * gnext;
+        T gnext = __shfl_down_sync(FULL, x[0], 1);
+        if (tl == 31) gnext = T(0);
+        T r = x[MM - 1] - fl[MM - 1] * x[MM - 2] - fu[MM - 1] * gnext;
         // local PCR over lanes 0..30 (lane 31 is the CTA's super unknown)
 #pragma unroll
         for (int l = 0; l < CLW_L; ++l) {
-          const double rm = __shfl_up_sync(FULL, r, 1 << l);
-          const double rp = __shfl_down_sync(FULL, r, 1 << l);
+          const T rm = __shfl_up_sync(FULL, r, 1 << l);
+          const T rp = __shfl_down_sync(FULL, r, 1 << l);
           if (tl < 31) r = r - k1[l] * rm - k2[l] * rp;
         }
         z0 = r * dv;                           // 0 on lane 31 (dv = 0)
@@ -204,27 +205,24 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
       };
       // publication of the CTA's four values: lane q stores into CTA q
       auto publish = [&]() {
-        if (tl < C) {
-          double* dst = rpub[tl] + (pb * CL_MAXC + c) * 4;
-          dst[0] = v0; dst[1] = v1; dst[2] = v2; dst[3] = v3;
-        }
+        xch.publish(pb, c, tl, C, v0, v1, v2, v3);
       };
       // super system: lane q forms the right-hand side of unknown q; Y_c and
       // Y_{c-1} are rows of the precomputed inverse applied by warp sums
       auto super_solve = [&]() {
-        double rhs = 0.0;
+        T rhs = T(0);
         if (q < C) {
-          const double* pq = &pubg[pb][q][0];
-          rhs = fma(-sa, pq[1], pq[2]);
+          const T* pq = xch.slot(pb, q);
+          rhs = fmaT(-sa, pq[1], pq[2]);
           if (q + 1 < C) {
-            const double* pn = &pubg[pb][q + 1][0];
-            rhs = fma(-sc2, pn[3], fma(-sc1, pn[0], rhs));
+            const T* pn = xch.slot(pb, q + 1);
+            rhs = fmaT(-sc2, pn[3], fmaT(-sc1, pn[0], rhs));
           }
         }
-        double Ys = msel * rhs;
+        T Ys = msel * rhs;
 #pragma unroll
         for (int o = CL_MAXC / 2; o > 0; o >>= 1) Ys += __shfl_xor_sync(FULL, Ys, o);
-        const double Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
+        const T Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
         y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
         yl = __shfl_up_sync(FULL, y, 1);
         if (tl == 0) yl = Yl;
@@ -237,30 +235,30 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
       pcr();
       publish();
       for (int j = 0; j + 1 < a.M; ++j) {
-        asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+        xch.arrive();
         // while the barrier completes: the next step's interior solve on the
         // uncorrected interior values (its right-hand side x + dt f)
-        double sI = 0.0;                     // source of the interface row
+        T sI = T(0);                         // source of the interface row
         if (SRC) sI = add_source(j + 1);
         fwd(x);
         bwd_hi(x);
-        asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+        xch.wait();
         super_solve();
         bwd_lo(x);
         // the deferred correction, through the next step's interior solve
         // (rows 0 and MM-2 feed the next interface row)
-        x[0] = fma(-pP[0], yl, fma(-pQ[0], y, x[0]));
-        x[MM - 2] = fma(-pP[MM - 2], yl, fma(-pQ[MM - 2], y, x[MM - 2]));
+        x[0] = fmaT(-pP[0], yl, fmaT(-pQ[0], y, x[0]));
+        x[MM - 2] = fmaT(-pP[MM - 2], yl, fmaT(-pQ[MM - 2], y, x[MM - 2]));
         x[MM - 1] = SRC ? y + sI : y;
         pb ^= 1;
         pcr();
 #pragma unroll
-        for (int i = 1; i < MM - 2; ++i) x[i] = fma(-pP[i], yl, fma(-pQ[i], y, x[i]));
+        for (int i = 1; i < MM - 2; ++i) x[i] = fmaT(-pP[i], yl, fmaT(-pQ[i], y, x[i]));
         publish();
       }
       // the last step: its spike corrections with fp, fq themselves
-      asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
-      asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+      xch.arrive();
+      xch.wait();
       super_solve();
 #pragma unroll
       for (int i = 0; i < MM - 1; ++i)
@@ -274,13 +272,84 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
       const int r = r0 + i;
       if (r < n) {
         if (a.out.y_f64)
-          static_cast<double*>(a.out.y)[oy + r] = x[i];
+          static_cast<double*>(a.out.y)[oy + r] = (double)x[i];
         else
           static_cast<float*>(a.out.y)[oy + r] = (float)x[i];
       }
     }
   }
+}
+
+// Exchange of the four published values per unit, between the one-warp CTAs
+// of a cluster: lane q pushes into CTA q's shared memory; one cluster
+// barrier (split into arrive and wait) per step
+struct XchCluster {
+  double (*pubg)[CL_MAXC][4];   // this CTA's receive buffers
+  double* const* rpub;          // the receive buffers of the cluster's CTAs
+  __device__ __forceinline__ void publish(int pb, int c, int tl, int C, double v0, double v1,
+                                          double v2, double v3) {
+    if (tl < C) {
+      double* dst = rpub[tl] + (pb * CL_MAXC + c) * 4;
+      dst[0] = v0; dst[1] = v1; dst[2] = v2; dst[3] = v3;
+    }
+  }
+  __device__ __forceinline__ const double* slot(int pb, int q) const { return &pubg[pb][q][0]; }
+  __device__ __forceinline__ void arrive() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+  }
+  __device__ __forceinline__ void wait() {
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+};
+
+// Exchange between the warps of one CTA: lane 0 of each warp writes its
+// values into the CTA's buffer; one block barrier per step
+template <typename T>
+struct XchBlock {
+  T (*pubg)[CL_MAXC][4];
+  __device__ __forceinline__ void publish(int pb, int c, int tl, int, T v0, T v1, T v2, T v3) {
+    if (tl == 0) {
+      T* dst = &pubg[pb][c][0];
+      dst[0] = v0; dst[1] = v1; dst[2] = v2; dst[3] = v3;
+    }
+  }
+  __device__ __forceinline__ const T* slot(int pb, int q) const { return &pubg[pb][q][0]; }
+  __device__ __forceinline__ void arrive() {}
+  __device__ __forceinline__ void wait() { __syncthreads(); }
+};
+
+// FP64, one system per cluster of C one-warp CTAs (the Parareal fine solves)
+template <int MM, bool SRC, int HLO>
+__global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double pubg[2][CL_MAXC][4];
+  __shared__ double* rpub[CL_MAXC];
+  const int C = a.C;
+  const int c = (int)cl.block_rank();
+  const int tl = threadIdx.x;
+  if (tl < C) rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
+  __syncwarp();
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
+  XchCluster xch{pubg, rpub};
+  warp_steps<double, MM, SRC, HLO>(a, xch, c, tl, (int)blockIdx.x / C, (int)gridDim.x / C);
   cl.sync();  // no CTA leaves while others may still store into its shared memory
+}
+
+// FP32 or FP64, one system per CTA of C warps (32 C chunks; C <= 16 in FP32,
+// <= 8 in FP64): the same steps with the exchange through the CTA's shared
+// memory and a block barrier, for batches large enough to fill the GPU with
+// CTAs (the sketches)
+template <typename T>
+constexpr int blk_w_threads() { return sizeof(T) == 8 ? 256 : 512; }   // FP64: factors need > 128 registers
+
+template <typename T, int MM, bool SRC, int HLO>
+__global__ void __launch_bounds__(blk_w_threads<T>()) k_tri_block_w(ClKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  __shared__ T pubg[2][CL_MAXC][4];
+  XchBlock<T> xch{pubg};
+  warp_steps<T, MM, SRC, HLO>(a, xch, (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31),
+                              (int)blockIdx.x, (int)gridDim.x);
 }
 
 template <int MM, bool SRC, int HLO>
@@ -315,6 +384,37 @@ static lrp_status launch_cl_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
   timer_end(c, "propagate_f64", ev);
   if (e) return cuda_err(c, e, "k_tri_cluster_w launch");
   return LRP_OK;
+}
+
+template <typename T, int MM, bool SRC, int HLO>
+static lrp_status launch_blk_w(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  auto kern = k_tri_block_w<T, MM, SRC, HLO>;
+  const int threads = 32 * pl->C;
+  if (threads > blk_w_threads<T>())
+    return set_err(c, LRP_EINVAL, "block warp kernel: too many warps per system for this precision");
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e || per_sm < 1) { cudaGetLastError(); per_sm = 1; }
+  const int grid = std::min(a.nsys, per_sm * c->num_sms);
+  const char* fam = sizeof(T) == 8 ? "propagate_f64" : "propagate_f32";
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, fam, &ev);
+  kern<<<grid, threads, 0, c->stream>>>(a);
+  e = cudaGetLastError();
+  timer_end(c, fam, ev);
+  if (e) return cuda_err(c, e, "k_tri_block_w launch");
+  return LRP_OK;
+}
+
+template <typename T>
+lrp_status tri_launch_warp_block(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  const bool src = a.src.Q > 0;
+  switch (pl->m) {
+    case 16: return src ? launch_blk_w<T, 16, true, 4>(c, pl, a) : launch_blk_w<T, 16, false, 4>(c, pl, a);
+    case 12: return src ? launch_blk_w<T, 12, true, 3>(c, pl, a) : launch_blk_w<T, 12, false, 3>(c, pl, a);
+    case 8: return src ? launch_blk_w<T, 8, true, 2>(c, pl, a) : launch_blk_w<T, 8, false, 2>(c, pl, a);
+    default: return set_err(c, LRP_EINVAL, "block warp kernel: chunk length 8, 12 or 16");
+  }
 }
 
 template <int MM, int S>

@@ -586,6 +586,29 @@ static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
   return LRP_OK;
 }
 
+lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int prec,
+                                    const PropIn& in, const PropOut& out, const PropSrc& src) {
+  if (nsys <= 0) return LRP_OK;
+  if (!pl->warp) return set_err(c, LRP_EINVAL, "block warp kernel needs a warp plan");
+  ClKArgs a{};
+  a.n = pl->n;
+  a.Pc = pl->Pc;
+  a.C = pl->C;
+  a.L = pl->L;
+  a.M = M;
+  a.nsys = nsys;
+  a.dt = pl->dt;
+  a.in = in;
+  a.out = out;
+  a.src = src;
+  DevBuf* b = prec == 0 ? pl->b64 : pl->b32;
+  a.coef = b[0].ptr;
+  a.lpcr = b[1].ptr;
+  a.spk = b[2].ptr;
+  a.sup = b[3].ptr;
+  return prec == 0 ? tri_launch_warp_block<double>(c, pl, a) : tri_launch_warp_block<float>(c, pl, a);
+}
+
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src,
                                  int stepper) {

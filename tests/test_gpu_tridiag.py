@@ -435,6 +435,48 @@ def test_warp_cluster_kernel_split_variants(ctx, orc, n, nvec, Q, M, wchunk, wsp
         assert rel(got[v], want[v]) <= tol
 
 
+@pytest.mark.parametrize("prec", ["mixed", "f64"])
+@pytest.mark.parametrize("wchunk", [8, 12, 16])
+@pytest.mark.parametrize("n,nvec,Q,M", [(4095, 200, 0, 37), (1000, 3, 2, 9), (255, 9, 1, 5),
+                                        (100, 5, 0, 1), (2049, 4, 0, 0)])
+def test_block_warp_kernel_matches_oracle(ctx, orc, n, nvec, Q, M, wchunk, prec):
+    """One system per CTA of C warps (tri_wblock = 1; the FP32 sketches take
+    it by default): forward and adjoint, with and without a source, against
+    the oracle (FP32 to 2e-5, FP64 to rounding).  FP64 takes at most 8 warps
+    per CTA: longer systems are refused with LRP_EINVAL."""
+    lo, di, up = W.adr1d_op(n)
+    dt = 1.0 / 16384
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    rng = np.random.default_rng(n + nvec + M)
+    X = rng.standard_normal((nvec, n))
+    g = rng.standard_normal((Q, n)) if Q else None
+    c = rng.standard_normal((nvec, M, Q)) if Q else None
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = 2e-5 if prec == "mixed" else max(1e-12, 4 * max(M, 1) * cond * 2.2e-16)
+    units = ((n + wchunk - 1) // wchunk + 31) // 32
+    oop = orc.Tridiag(lo, di, up)
+    for adjoint in (False, True):
+        if adjoint and Q:
+            continue
+        try:
+            ctx.set_param("tri_wblock", 1)
+            ctx.set_param("tri_wchunk", wchunk)
+            if prec == "f64" and units > 8:
+                with pytest.raises(_native.LrpError):
+                    api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c, prec=prec)
+                continue
+            got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, g=g, c=c, prec=prec)
+        finally:
+            ctx.set_param("tri_wblock", 0)
+            ctx.set_param("tri_wchunk", 0)
+        if M == 0:
+            np.testing.assert_allclose(got, X, rtol=0, atol=1e-6 if prec == "mixed" else 0)
+            continue
+        want = orc.propagate(oop, dt, M, X, adjoint=adjoint, g=g, cvals=c)
+        for v in range(nvec):
+            assert rel(got[v], want[v]) <= tol
+
+
 # ---------------------------------------------------------------------------
 # classical Parareal (backward-Euler coarse step), the comparison method
 # ---------------------------------------------------------------------------
