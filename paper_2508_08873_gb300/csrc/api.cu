@@ -297,6 +297,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_wblock") {
     if (value < 0 || value > 2) return LRP_EINVAL;
     c->p_tri_wblock = value;
+  } else if (k == "tri_wtoep") {
+    if (value < 0 || value > 2) return LRP_EINVAL;
+    c->p_tri_wtoep = value;
   } else if (k == "tri_group") {
     if (value < 0 || value > 16) return LRP_EINVAL;
     c->p_tri_group = value;
@@ -330,6 +333,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_wchunk") *value = c->p_tri_wchunk;
   else if (k == "tri_wsplit") *value = c->p_tri_wsplit;
   else if (k == "tri_wblock") *value = c->p_tri_wblock;
+  else if (k == "tri_wtoep") *value = c->p_tri_wtoep;
   else if (k == "orth_tc") *value = c->p_orth_tc;
   else return set_err(c, LRP_EINVAL, "unknown parameter");
   return LRP_OK;
@@ -397,6 +401,24 @@ lrp_status lrp_operator_tridiag(lrp_ctx* c, int n, const double* lo, const doubl
   }
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "operator upload");
+  // constant coefficients (lo[1..n-1], di, up[0..n-2] each one value): the
+  // one-warp kernel has a variant for them
+  {
+    std::vector<double> h(3 * (size_t)n);
+    for (int k = 0; k < 3; ++k) {
+      e = cudaMemcpy(h.data() + (size_t)k * n, op->a64[k].ptr, sizeof(double) * n, cudaMemcpyDeviceToHost);
+      if (e) return cuda_err(c, e, "operator read-back");
+    }
+    const double* hl = h.data();
+    const double* hd = hl + n;
+    const double* hu = hd + n;
+    bool toep = true;
+    for (int i = 1; i < n && toep; ++i) toep = hl[i] == hl[1] && hd[i] == hd[0] && hu[i - 1] == hu[0];
+    op->toeplitz = toep;
+    op->tlo = hl[1];
+    op->tdi = hd[0];
+    op->tup = hu[0];
+  }
   *out = op.release();
   return LRP_OK;
 }
@@ -563,11 +585,45 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
         mw = 8;
         Cw = Cw8;
       }
+      // constant-coefficient operators without a source: the Toeplitz
+      // variant (two FP64 instructions per row for the chunk solve instead of
+      // three), on the chunk length nearest the rule's (the larger on a tie)
+      // for which n mod MM is 0 or MM - 1
+      // Measured on GB300 (n = 4095, 256 steps, ms per launch, general kernel
+      // in brackets; chunk lengths 8, 9, 13, 15, 16 are the ones with n mod
+      // MM in {0, MM - 1}): 16 systems MM = 8 0.664 (0.662); 40 systems
+      // MM = 9 0.723 (MM = 8 0.739); 48-56 systems MM = 13 0.765 (0.814-0.843);
+      // 60 systems MM = 15 0.826 (MM = 12 0.950); 64 systems MM = 13 0.863
+      // (0.954); 96 systems MM = 15 1.041 (1.217); 128 systems MM = 16 1.412
+      // (1.633).
+      ToepCoef tz{};
+      if (op->toeplitz && src.Q == 0 && c->p_tri_wtoep != 2) {
+        if (!c->p_tri_wchunk)
+          mw = wpp <= 0.55 ? 8 : wpp <= 1.1 ? 9 : wpp <= 1.5 ? 13 : wpp <= 1.6 ? 15
+             : wpp <= 1.75 ? 13 : wpp <= 2.8 ? 15 : wpp <= 3.8 ? 16 : wpp <= 5.5 ? 13 : 16;
+        int best = 0;
+        for (int d = 0; d <= 8 && !best; ++d) {
+          const int cands[2] = {mw + d, mw - d};
+          for (int cand : cands)
+            if (!best && cand >= 8 && cand <= 16 && (op->n % cand == 0 || (op->n + 1) % cand == 0) &&
+                (c->p_tri_wchunk == 0 || cand == mw))
+              best = cand;
+        }
+        if (best) {
+          const int Cb = ((op->n + best - 1) / best + 31) / 32;
+          if (Cb >= 1 && Cb <= 16) {
+            tri_toeplitz_coef(op, dt, adjoint, M, best, &tz);
+            if (tz.on) { mw = best; Cw = Cb; }
+          }
+        }
+      }
+      if (c->p_tri_wtoep == 1 && !tz.on)
+        return set_err(c, LRP_EINVAL, "constant-coefficient kernel not applicable");
       if (Cw >= 1 && Cw <= 16) {
         ClPlan* cp = nullptr;
         lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Cw, mw, &cp, 1);
         if (s) return s;
-        return tri_propagate_cluster(c, cp, M, nsys, prec, 1, in, out, src);
+        return tri_propagate_cluster(c, cp, M, nsys, prec, 1, in, out, src, 0, tz.on ? &tz : nullptr);
       }
     }
     // FP32 batches (the sketches), and FP64 on request: one system per CTA

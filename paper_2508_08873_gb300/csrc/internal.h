@@ -60,6 +60,7 @@ struct Ctx {
   int p_tri_wchunk = 0;      // rows per chunk of the one-warp cluster kernel (0 auto, 8..16)
   int p_tri_wsplit = 1;      // backward rows of the one-warp kernel after the barrier wait (0 none, 1 a third)
   int p_tri_wblock = 0;      // one-CTA-per-system warp kernel: 0 auto (FP32), 1 always, 2 never
+  int p_tri_wtoep = 0;       // constant-coefficient one-warp kernel: 0 auto, 1 always (else EINVAL), 2 never
   int p_tri_group = 0;       // systems per CTA of the one-CTA-per-system kernel (1..16)
   // Caching allocator: released buffers are kept (up to pool_cap bytes) and
   // reused by later allocations of a similar size, so repeated builds and
@@ -110,11 +111,28 @@ struct StencilPlan {
   DevBuf b64, b32;
 };
 
+// Constant-coefficient (Toeplitz) data of a tridiagonal step matrix
+// B = I + dt A for the one-warp kernel (see tri_warp.cuh): lower a, diagonal
+// d, upper c; the steady pivot dinf of its LU factorisation (the larger root
+// of p = d - a c / p) with l = a / dinf, u = c / dinf; the state is carried
+// scaled by dinf per step and rescaled by rho = dinf^-P every P steps; fin
+// undoes the scaling left after the last step.
+struct ToepCoef {
+  int on = 0;
+  int P = 1;
+  double a = 0.0, d = 1.0, c = 0.0, dinf = 1.0, idinf = 1.0, l = 0.0, u = 0.0;
+  double rho = 1.0, fin = 1.0;
+};
+
 struct Operator {
   Ctx* ctx = nullptr;
   ~Operator();
   int kind = 0;            // 0 tridiagonal, 1 5-point stencil
   int n = 0, mx = 0, my = 0;
+  // tridiagonal with constant coefficients (lo[1..n-1], di, up[0..n-2] each
+  // one value): tlo, tdi, tup
+  bool toeplitz = false;
+  double tlo = 0.0, tdi = 0.0, tup = 0.0;
   DevBuf a64[5];           // tridiagonal: lo, di, up; stencil: C, W, E, S, N
   DevBuf a32[5];
   double rtol64 = 1e-12, rtol32 = 1e-6;
@@ -233,7 +251,12 @@ lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int pre
                                     const PropIn& in, const PropOut& out, const PropSrc& src);
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src,
-                                 int stepper = 0);
+                                 int stepper = 0, const ToepCoef* tz = nullptr);
+// The constant-coefficient data of B = I + dt A (or its transpose) for M
+// steps on chunks of m rows, if the operator is Toeplitz, its step matrix has
+// a steady pivot, and n mod m is 0 or m - 1 (so that no chunk interior mixes
+// rows of the system with padding rows); tz->on = 0 otherwise.
+void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m, ToepCoef* tz);
 
 // Allocation-free variant: factorisation into caller-provided scratch.
 size_t tri_raw_scratch_bytes(int n);

@@ -27,6 +27,7 @@ struct ClKArgs {
   PropIn in;
   PropOut out;
   PropSrc src;
+  ToepCoef tz;                 // constant-coefficient one-warp kernel
 };
 
 // One-warp cluster propagation, FP64 (chunks of 8..16 rows); S selects how
@@ -36,6 +37,10 @@ struct ClKArgs {
 // unsupported plan.
 template <int S>
 lrp_status tri_launch_warp(Ctx* c, ClPlan* pl, ClKArgs& a);
+
+// The constant-coefficient variant of the cluster kernel (a.tz.on, no
+// source term, FP64).
+lrp_status tri_launch_warp_toep(Ctx* c, ClPlan* pl, ClKArgs& a);
 
 // One system per CTA of C warps (T = float or double; chunks of 8, 12 or 16
 // rows), coefficients from a warp cluster plan (ClPlan with warp = 1) in T.
@@ -280,6 +285,233 @@ __device__ __forceinline__ void warp_steps(const ClKArgs& a, X& xch, int c, int 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Constant-coefficient variant (FP64, no source; one system per cluster of
+// one-warp CTAs).  Every chunk interior is the Toeplitz matrix T (lower a,
+// diagonal d, upper c) of m = MM - 1 rows, or identity padding rows.  With
+// the steady pivot dinf of the LU factorisation of tridiag(a, d, c),
+//   T = L U + (d - dinf) e_0 e_0^T,  L = I + l E^T,  U = dinf (I + u E),
+// so with S = dinf (L U)^{-1} (one forward and one backward sweep of one FMA
+// per row: no division by a pivot) and phi = (L U)^{-1} e_0,
+//   T^{-1} v = (L U)^{-1} v - kappa ((L U)^{-1} v)_0 phi,
+//   kappa = (d - dinf) / (1 + (d - dinf) phi_0)        (Sherman-Morrison),
+// and the left spike fp = T^{-1}(a_left e_0) = beta phi, beta = a_left (1 -
+// kappa phi_0).  A step's interior solution is then
+//   x = w - (kappa w_0 + beta yl) phi - y fq,   w = (L U)^{-1} b,
+// two FMAs per row beside the two of the sweeps (the general kernel needs
+// three for the solve).  The state is carried scaled: step j's quantities are
+// dinf^(j+1) times the true ones, so that S replaces (L U)^{-1}; the
+// interface row, PCR and super system take the scaling in their constants
+// (the interface residual is formed divided by dinf), and every P steps the
+// state is multiplied by rho = dinf^-P.  The step loop and its split around
+// the cluster barrier are those of warp_steps; the correction is deferred
+// into the next step's sweeps through S phi and S fq.
+// ---------------------------------------------------------------------------
+template <int MM, int HLO, class X>
+__device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c, int tl, int sys0,
+                                                int dsys) {
+  static_assert(HLO >= 0 && HLO <= MM - 2, "split row out of range");
+  const int C = a.C;
+  const int t = c * 32 + tl;
+  const int n = a.n;
+  const int r0 = t * MM;
+  const unsigned FULL = 0xffffffffu;
+  const ToepCoef& z = a.tz;
+  const double* gco = static_cast<const double*>(a.coef) + (size_t)c * 5 * MM * 32;
+  const double* gpc = static_cast<const double*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
+  const double* gsp = static_cast<const double*>(a.spk) + (size_t)c * 2 * 32;
+  const double* gsu = static_cast<const double*>(a.sup);
+  // this lane's chunk: Toeplitz interior rows, or identity padding rows
+  const bool real = r0 < n;
+  const double l = real ? z.l : 0.0, u = real ? z.u : 0.0;
+  auto s_fwd = [&](double* v) {
+#pragma unroll
+    for (int i = 1; i < MM - 1; ++i) v[i] = fmaT(-l, v[i - 1], v[i]);
+  };
+  auto s_bwd_hi = [&](double* v) {
+#pragma unroll
+    for (int i = MM - 3; i >= HLO; --i) v[i] = fmaT(-u, v[i + 1], v[i]);
+  };
+  auto s_bwd_lo = [&](double* v) {
+#pragma unroll
+    for (int i = HLO - 1; i >= 0; --i) v[i] = fmaT(-u, v[i + 1], v[i]);
+  };
+  // phi = (L U)^{-1} e_0 of a Toeplitz chunk (the same in every lane;
+  // formed again for the last step rather than kept in registers)
+  auto make_phi = [&](double* phi) {
+#pragma unroll
+    for (int i = 0; i < MM; ++i) phi[i] = i == 0 ? 1.0 : 0.0;
+#pragma unroll
+    for (int i = 1; i < MM - 1; ++i) phi[i] = fmaT(-z.l, phi[i - 1], phi[i]);
+#pragma unroll
+    for (int i = MM - 3; i >= 0; --i) phi[i] = fmaT(-z.u, phi[i + 1], phi[i]);
+#pragma unroll
+    for (int i = 0; i < MM - 1; ++i) phi[i] *= z.idinf;
+  };
+  double phi[MM], sphi[MM], sq[MM];
+  make_phi(phi);
+  const double delta = z.d - z.dinf;
+  const double kap_sys = delta / (1.0 + delta * phi[0]);
+  const double kap = real ? kap_sys : 0.0;
+  const double beta = (real && r0 > 0) ? z.a * (1.0 - kap_sys * phi[0]) : 0.0;
+  // S phi and S fq: the deferred correction
+#pragma unroll
+  for (int i = 0; i < MM - 1; ++i) {
+    sphi[i] = phi[i];
+    sq[i] = gco[(4 * MM + i) * 32 + tl];
+  }
+  s_fwd(sphi); s_bwd_hi(sphi); s_bwd_lo(sphi);
+  s_fwd(sq); s_bwd_hi(sq); s_bwd_lo(sq);
+  // interface row (couplings aE to row MM-2 and cE to the next chunk's row
+  // 0), divided by dinf, in terms of w: X_{MM-2} = w_{MM-2} - kappa phi_{MM-2}
+  // w_0 and X'_0 = (1 - kappa phi_0) w'_0
+  const double aE = gco[(0 * MM + MM - 1) * 32 + tl];
+  const double cE = gco[(2 * MM + MM - 1) * 32 + tl];
+  const double cA = aE * z.idinf;
+  const double cK = aE * kap * phi[MM - 2] * z.idinf;
+  const double cB = cE * (1.0 - kap_sys * phi[0]) * z.idinf;
+  double k1[CLW_L], k2[CLW_L];
+#pragma unroll
+  for (int lv = 0; lv < CLW_L; ++lv) {
+    k1[lv] = gpc[lv * 32 + tl];
+    k2[lv] = gpc[(CLW_L + lv) * 32 + tl];
+  }
+  const double dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] * z.dinf : 0.0;
+  const double p2 = gsp[tl], q2 = gsp[32 + tl];
+  const int q = tl & (CL_MAXC - 1);
+  const double sa = q < C ? gsu[6 * q + 0] * z.idinf : 0.0;
+  const double sc1 = q < C ? gsu[6 * q + 1] * z.idinf : 0.0;
+  const double sc2 = q < C ? gsu[6 * q + 2] * (1.0 - kap_sys * phi[0]) * z.idinf : 0.0;
+  const double* minv = gsu + 6 * CL_MAXC;
+  const double msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
+                                            : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : 0.0)) * z.dinf
+                            : 0.0;
+  int pb = 0;
+  for (int sys = sys0; sys < a.nsys; sys += dsys) {
+    double x[MM];
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      const int r = r0 + i;
+      double v = 0.0;
+      if (r < n) {
+        if (a.in.gen)
+          v = gauss<double>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                            (uint32_t)(sys % a.in.ncol), (uint32_t)r);
+        else if (a.in.x == nullptr)
+          v = 0.0;
+        else if (a.in.x_f64)
+          v = static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+        else
+          v = (double)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+      }
+      x[i] = v;
+    }
+    if (a.M > 0) {
+      double z0 = 0.0, y = 0.0, yl = 0.0, w0 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      auto pcr = [&]() {
+        double gnext = __shfl_down_sync(FULL, x[0], 1);
+        if (tl == 31) gnext = 0.0;
+        double r = fmaT(-cB, gnext, fmaT(cK, x[0], fmaT(-cA, x[MM - 2], x[MM - 1])));
+#pragma unroll
+        for (int lv = 0; lv < CLW_L; ++lv) {
+          const double rm = __shfl_up_sync(FULL, r, 1 << lv);
+          const double rp = __shfl_down_sync(FULL, r, 1 << lv);
+          if (tl < 31) r = r - k1[lv] * rm - k2[lv] * rp;
+        }
+        z0 = r * dv;
+        v0 = __shfl_sync(FULL, z0, 0);
+        v1 = __shfl_sync(FULL, z0, 30);
+        v2 = __shfl_sync(FULL, r, 31);
+        v3 = __shfl_sync(FULL, x[0], 0);
+      };
+      auto super_solve = [&]() {
+        double rhs = 0.0;
+        if (q < C) {
+          const double* pq = xch.slot(pb, q);
+          rhs = fmaT(-sa, pq[1], pq[2]);
+          if (q + 1 < C) {
+            const double* pn = xch.slot(pb, q + 1);
+            rhs = fmaT(-sc2, pn[3], fmaT(-sc1, pn[0], rhs));
+          }
+        }
+        double Ys = msel * rhs;
+#pragma unroll
+        for (int o = CL_MAXC / 2; o > 0; o >>= 1) Ys += __shfl_xor_sync(FULL, Ys, o);
+        const double Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
+        y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
+        yl = __shfl_up_sync(FULL, y, 1);
+        if (tl == 0) yl = Yl;
+      };
+      // one step of the loop: the barrier of step j, the sweeps of step j+1,
+      // the super system of step j and the deferred correction, the PCR of
+      // step j+1; with resc, the state is rescaled by rho after the super
+      // system
+      auto body = [&](bool resc) {
+        xch.arrive();
+        w0 = x[0];
+        s_fwd(x);
+        s_bwd_hi(x);
+        xch.wait();
+        super_solve();
+        s_bwd_lo(x);
+        if (resc) {
+          y *= z.rho;
+          yl *= z.rho;
+          w0 *= z.rho;
+#pragma unroll
+          for (int i = 0; i < MM - 1; ++i) x[i] *= z.rho;
+        }
+        const double sc = fmaT(kap, w0, beta * yl);
+        x[0] = fmaT(-sc, sphi[0], fmaT(-sq[0], y, x[0]));
+        x[MM - 2] = fmaT(-sc, sphi[MM - 2], fmaT(-sq[MM - 2], y, x[MM - 2]));
+        x[MM - 1] = y;
+        pb ^= 1;
+        pcr();
+#pragma unroll
+        for (int i = 1; i < MM - 2; ++i) x[i] = fmaT(-sc, sphi[i], fmaT(-sq[i], y, x[i]));
+        xch.publish(pb, c, tl, C, v0, v1, v2, v3);
+      };
+      s_fwd(x); s_bwd_hi(x); s_bwd_lo(x);
+      pcr();
+      xch.publish(pb, c, tl, C, v0, v1, v2, v3);
+      // bodies j = 0 .. M-2; the one with (j + 1) % P == 0 rescales
+      int j = 0;
+      while (true) {
+        const int jr = ((j + z.P) / z.P) * z.P - 1;
+        const int jlim = min(jr, a.M - 1);
+        for (; j < jlim; ++j) body(false);
+        if (j >= a.M - 1) break;
+        body(true);
+        ++j;
+      }
+      // the last step: its correction with phi and fq themselves, then the
+      // remaining scaling undone
+      xch.arrive();
+      xch.wait();
+      super_solve();
+      const double sc = fmaT(kap, x[0], beta * yl);
+      double phl[MM];
+      make_phi(phl);
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i)
+        x[i] = (x[i] - sc * phl[i] - gco[(4 * MM + i) * 32 + tl] * y) * z.fin;
+      x[MM - 1] = y * z.fin;
+      pb ^= 1;
+    }
+    const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
+#pragma unroll
+    for (int i = 0; i < MM; ++i) {
+      const int r = r0 + i;
+      if (r < n) {
+        if (a.out.y_f64)
+          static_cast<double*>(a.out.y)[oy + r] = x[i];
+        else
+          static_cast<float*>(a.out.y)[oy + r] = (float)x[i];
+      }
+    }
+  }
+}
+
 // Exchange of the four published values per unit, between the one-warp CTAs
 // of a cluster: lane q pushes into CTA q's shared memory; one cluster
 // barrier (split into arrive and wait) per step
@@ -333,6 +565,24 @@ __global__ void __launch_bounds__(32) k_tri_cluster_w(ClKArgs a) {
   cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
   XchCluster xch{pubg, rpub};
   warp_steps<double, MM, SRC, HLO>(a, xch, c, tl, (int)blockIdx.x / C, (int)gridDim.x / C);
+  cl.sync();  // no CTA leaves while others may still store into its shared memory
+}
+
+// FP64 constant-coefficient variant, one system per cluster of C one-warp CTAs
+template <int MM, int HLO>
+__global__ void __launch_bounds__(32) k_tri_cluster_wt(ClKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ double pubg[2][CL_MAXC][4];
+  __shared__ double* rpub[CL_MAXC];
+  const int C = a.C;
+  const int c = (int)cl.block_rank();
+  const int tl = threadIdx.x;
+  if (tl < C) rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
+  __syncwarp();
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
+  XchCluster xch{pubg, rpub};
+  warp_steps_toep<MM, HLO>(a, xch, c, tl, (int)blockIdx.x / C, (int)gridDim.x / C);
   cl.sync();  // no CTA leaves while others may still store into its shared memory
 }
 
@@ -415,6 +665,40 @@ lrp_status tri_launch_warp_block(Ctx* c, ClPlan* pl, ClKArgs& a) {
     case 8: return src ? launch_blk_w<T, 8, true, 2>(c, pl, a) : launch_blk_w<T, 8, false, 2>(c, pl, a);
     default: return set_err(c, LRP_EINVAL, "block warp kernel: chunk length 8, 12 or 16");
   }
+}
+
+template <int MM>
+static lrp_status launch_cl_wt(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  const int C = pl->C;
+  auto kern = k_tri_cluster_wt<MM, (MM - 2) / 3>;
+  cudaError_t e;
+  if (C > 8) {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e) return cuda_err(c, e, "cluster size 16 not available");
+  }
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(32);
+  cfg.gridDim = dim3(C);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c->stream;
+  int maxc = 0;
+  e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+  if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
+  const int ncl = std::min(a.nsys, maxc);
+  cfg.gridDim = dim3(ncl * C);
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "propagate_f64", &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  timer_end(c, "propagate_f64", ev);
+  if (e) return cuda_err(c, e, "k_tri_cluster_wt launch");
+  return LRP_OK;
 }
 
 template <int MM, int S>

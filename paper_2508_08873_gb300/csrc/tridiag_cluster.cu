@@ -611,7 +611,7 @@ lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int pre
 
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src,
-                                 int stepper) {
+                                 int stepper, const ToepCoef* tz) {
   if (nsys <= 0) return LRP_OK;
   ClKArgs a{};
   a.n = pl->n;
@@ -638,6 +638,10 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
   }
   if (pl->warp) {
     if (f || spt != 1) return set_err(c, LRP_EINVAL, "warp cluster kernel is FP64, one system per thread");
+    if (tz && tz->on) {
+      a.tz = *tz;
+      return tri_launch_warp_toep(c, pl, a);
+    }
     return c->p_tri_wsplit ? tri_launch_warp<1>(c, pl, a) : tri_launch_warp<0>(c, pl, a);
   }
   if (pl->m == 8) {

@@ -1,0 +1,65 @@
+// Instantiation of the constant-coefficient one-warp cluster tridiagonal
+// propagator (tri_warp.cuh), and the host side of its coefficients.
+#define LRP_TRI_WARP_KERNEL
+#include "tri_warp.cuh"
+
+#include <cmath>
+
+namespace lrp {
+
+lrp_status tri_launch_warp_toep(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  if (!a.tz.on || a.src.Q > 0) return set_err(c, LRP_EINVAL, "constant-coefficient kernel: no data or a source");
+  switch (pl->m) {
+    case 16: return launch_cl_wt<16>(c, pl, a);
+    case 15: return launch_cl_wt<15>(c, pl, a);
+    case 14: return launch_cl_wt<14>(c, pl, a);
+    case 13: return launch_cl_wt<13>(c, pl, a);
+    case 12: return launch_cl_wt<12>(c, pl, a);
+    case 11: return launch_cl_wt<11>(c, pl, a);
+    case 10: return launch_cl_wt<10>(c, pl, a);
+    case 9: return launch_cl_wt<9>(c, pl, a);
+    case 8: return launch_cl_wt<8>(c, pl, a);
+    default: return set_err(c, LRP_EINVAL, "warp cluster chunk length out of range");
+  }
+}
+
+void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m, ToepCoef* tz) {
+  *tz = ToepCoef{};
+  if (!op->toeplitz || m < 3) return;
+  const int n = op->n;
+  if (n % m != 0 && (n + 1) % m != 0) return;
+  const double a = dt * (adjoint ? op->tup : op->tlo);
+  const double c = dt * (adjoint ? op->tlo : op->tup);
+  const double d = 1.0 + dt * op->tdi;
+  const double disc = d * d - 4.0 * a * c;
+  if (!(d > 0.0) || !(disc > 0.0) || !std::isfinite(disc)) return;
+  const double dinf = 0.5 * (d + std::sqrt(disc));
+  if (!(dinf > 0.0)) return;
+  // the Sherman-Morrison denominator 1 + (d - dinf) phi_0 of a chunk
+  const double l = a / dinf, u = c / dinf;
+  double phi[32];
+  const int mi = m - 1;
+  for (int i = 0; i < mi; ++i) phi[i] = i == 0 ? 1.0 : 0.0;
+  for (int i = 1; i < mi; ++i) phi[i] -= l * phi[i - 1];
+  for (int i = mi - 2; i >= 0; --i) phi[i] -= u * phi[i + 1];
+  const double den = 1.0 + (d - dinf) * phi[0] / dinf;
+  if (!(std::fabs(den) > 1e-3)) return;
+  // rescale period: dinf^P within 1e150 either way
+  const double lg = std::fabs(std::log10(dinf));
+  int P = lg > 1e-3 ? (int)std::floor(150.0 / lg) : (1 << 30);
+  P = std::max(1, std::min(P, 1 << 30));
+  tz->on = 1;
+  tz->P = P;
+  tz->a = a;
+  tz->d = d;
+  tz->c = c;
+  tz->dinf = dinf;
+  tz->idinf = 1.0 / dinf;
+  tz->l = l;
+  tz->u = u;
+  tz->rho = P < (1 << 30) ? std::pow(dinf, -(double)P) : 1.0;
+  const long e = M >= 1 ? (long)M - (long)P * ((M - 1) / P) : 0;
+  tz->fin = std::pow(dinf, -(double)e);
+}
+
+}  // namespace lrp

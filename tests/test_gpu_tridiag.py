@@ -477,6 +477,79 @@ def test_block_warp_kernel_matches_oracle(ctx, orc, n, nvec, Q, M, wchunk, prec)
             assert rel(got[v], want[v]) <= tol
 
 
+@pytest.mark.parametrize("n,wchunk", [(4095, 8), (4095, 9), (4095, 13), (4095, 15), (4095, 16),
+                                      (3000, 12), (1023, 11), (2048, 16), (300, 10)])
+@pytest.mark.parametrize("M", [1, 2, 3, 37, 700])
+def test_toeplitz_warp_kernel_matches_oracle(ctx, orc, n, wchunk, M):
+    """Constant-coefficient operators take the Toeplitz variant of the
+    one-warp kernel (steady LU factors, a Sherman-Morrison term for the first
+    row of each chunk, the state carried scaled by the steady pivot and
+    rescaled every P steps: 700 steps cross several rescales).  Forward and
+    adjoint against the oracle, for chunk lengths with n mod MM = 0 or MM - 1
+    (padding rows only in chunks of their own)."""
+    lo, di, up = W.adr1d_op(n)
+    dt = 1.0 / 16384
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    X = np.random.default_rng(n + M).standard_normal((6, n))
+    oop = orc.Tridiag(lo, di, up)
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    for adjoint in (False, True):
+        try:
+            ctx.set_param("tri_warp", 2)
+            ctx.set_param("tri_wchunk", wchunk)
+            ctx.set_param("tri_wtoep", 1)
+            got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+        finally:
+            ctx.set_param("tri_warp", 0)
+            ctx.set_param("tri_wchunk", 0)
+            ctx.set_param("tri_wtoep", 0)
+        want = orc.propagate(oop, dt, M, X, adjoint=adjoint)
+        for v in range(X.shape[0]):
+            assert rel(got[v], want[v]) <= tol, (adjoint, v, rel(got[v], want[v]), tol)
+
+
+def test_toeplitz_warp_kernel_heat_and_eligibility(ctx, orc):
+    """The heat operator (symmetric, diffusion only) on the Toeplitz variant
+    matches the oracle; a variable-coefficient operator, a source term or a
+    chunk length with n mod MM not in {0, MM - 1} are refused when the
+    variant is forced, and fall back to the general kernel otherwise."""
+    n, M, dt = 4095, 64, 1.0 / 1024
+    lo, di, up = W.heat1d_op(n)
+    X = np.random.default_rng(1).standard_normal((5, n))
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    want = orc.propagate(orc.Tridiag(lo, di, up), dt, M, X)
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    try:
+        ctx.set_param("tri_warp", 2)
+        ctx.set_param("tri_wtoep", 1)
+        got = api.propagate(ctx, op, dt, M, X)
+        for v in range(5):
+            assert rel(got[v], want[v]) <= tol
+        g = np.ones((1, n))
+        c = np.ones((M, 1))
+        with pytest.raises(_native.LrpError):
+            api.propagate(ctx, op, dt, M, X, g=g, c=c)
+        ctx.set_param("tri_wchunk", 12)            # 4095 mod 12 = 3
+        with pytest.raises(_native.LrpError):
+            api.propagate(ctx, op, dt, M, X)
+        ctx.set_param("tri_wchunk", 0)
+        lo2 = lo * (1.0 + 0.01 * np.sin(np.arange(n)))
+        op2 = api.Operator.tridiag(ctx, lo2, di, up)
+        with pytest.raises(_native.LrpError):
+            api.propagate(ctx, op2, dt, M, X)
+        ctx.set_param("tri_wtoep", 0)
+        got2 = api.propagate(ctx, op2, dt, M, X)
+        want2 = orc.propagate(orc.Tridiag(lo2, di, up), dt, M, X)
+        for v in range(5):
+            assert rel(got2[v], want2[v]) <= tol
+    finally:
+        ctx.set_param("tri_warp", 0)
+        ctx.set_param("tri_wchunk", 0)
+        ctx.set_param("tri_wtoep", 0)
+
+
 # ---------------------------------------------------------------------------
 # classical Parareal (backward-Euler coarse step), the comparison method
 # ---------------------------------------------------------------------------
