@@ -39,8 +39,8 @@ METRIC = "Parareal solves/s at 1e-8 rel err vs FP64 oracle"
 UNIT = "solves/s"
 TOL = 1e-8
 # DRAM bytes per system of the FP64 fine-solve kernel, from one ncu capture of
-# k_tri_cluster_w<12, false, 3> (62 systems: 2.3086 MB read, 0 written)
-F64_DRAM_BYTES_PER_SYSTEM = 2.3086e6 / 62
+# k_tri_cluster_wt<13, 3> (62 systems: 2.1978 MB read, 0 written)
+F64_DRAM_BYTES_PER_SYSTEM = 2.1978e6 / 62
 WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
 
 
