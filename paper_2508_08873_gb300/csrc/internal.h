@@ -248,7 +248,8 @@ lrp_status tri_get_cluster_plan(Ctx* c, Operator* op, double dt, int adjoint, in
 // one system per CTA of C warps, with the factorisation of a warp plan
 // (tri_get_cluster_plan with warp = 1); prec 0 = FP64, 1 = FP32
 lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int prec,
-                                    const PropIn& in, const PropOut& out, const PropSrc& src);
+                                    const PropIn& in, const PropOut& out, const PropSrc& src,
+                                    const ToepCoef* tz = nullptr);
 lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, int spt,
                                  const PropIn& in, const PropOut& out, const PropSrc& src,
                                  int stepper = 0, const ToepCoef* tz = nullptr);

@@ -39,8 +39,9 @@ template <int S>
 lrp_status tri_launch_warp(Ctx* c, ClPlan* pl, ClKArgs& a);
 
 // The constant-coefficient variant of the cluster kernel (a.tz.on, no
-// source term, FP64).
+// source term, FP64), and of the one-CTA-per-system kernel (C <= 8).
 lrp_status tri_launch_warp_toep(Ctx* c, ClPlan* pl, ClKArgs& a);
+lrp_status tri_launch_warp_block_toep(Ctx* c, ClPlan* pl, ClKArgs& a);
 
 // One system per CTA of C warps (T = float or double; chunks of 8, 12 or 16
 // rows), coefficients from a warp cluster plan (ClPlan with warp = 1) in T.
@@ -600,6 +601,34 @@ __global__ void __launch_bounds__(blk_w_threads<T>()) k_tri_block_w(ClKArgs a) {
   XchBlock<T> xch{pubg};
   warp_steps<T, MM, SRC, HLO>(a, xch, (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31),
                               (int)blockIdx.x, (int)gridDim.x);
+}
+
+// FP64 constant-coefficient variant, one system per CTA of C warps (C <= 8)
+template <int MM, int HLO>
+__global__ void __launch_bounds__(256) k_tri_block_wt(ClKArgs a) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  __shared__ double pubg[2][CL_MAXC][4];
+  XchBlock<double> xch{pubg};
+  warp_steps_toep<MM, HLO>(a, xch, (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31),
+                           (int)blockIdx.x, (int)gridDim.x);
+}
+
+template <int MM>
+static lrp_status launch_blk_wt(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  auto kern = k_tri_block_wt<MM, (MM - 2) / 3>;
+  const int threads = 32 * pl->C;
+  if (threads > 256) return set_err(c, LRP_EINVAL, "block warp kernel: at most 8 warps per system in FP64");
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
+  if (e || per_sm < 1) { cudaGetLastError(); per_sm = 1; }
+  const int grid = std::min(a.nsys, per_sm * c->num_sms);
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "propagate_f64", &ev);
+  kern<<<grid, threads, 0, c->stream>>>(a);
+  e = cudaGetLastError();
+  timer_end(c, "propagate_f64", ev);
+  if (e) return cuda_err(c, e, "k_tri_block_wt launch");
+  return LRP_OK;
 }
 
 template <int MM, bool SRC, int HLO>

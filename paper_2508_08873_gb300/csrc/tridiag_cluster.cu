@@ -587,7 +587,8 @@ static lrp_status launch_cl(Ctx* c, ClPlan* pl, ClKArgs& a) {
 }
 
 lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int prec,
-                                    const PropIn& in, const PropOut& out, const PropSrc& src) {
+                                    const PropIn& in, const PropOut& out, const PropSrc& src,
+                                    const ToepCoef* tz) {
   if (nsys <= 0) return LRP_OK;
   if (!pl->warp) return set_err(c, LRP_EINVAL, "block warp kernel needs a warp plan");
   ClKArgs a{};
@@ -606,6 +607,11 @@ lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int pre
   a.lpcr = b[1].ptr;
   a.spk = b[2].ptr;
   a.sup = b[3].ptr;
+  if (tz && tz->on) {
+    if (prec != 0) return set_err(c, LRP_EINVAL, "constant-coefficient kernel is FP64");
+    a.tz = *tz;
+    return tri_launch_warp_block_toep(c, pl, a);
+  }
   return prec == 0 ? tri_launch_warp_block<double>(c, pl, a) : tri_launch_warp_block<float>(c, pl, a);
 }
 

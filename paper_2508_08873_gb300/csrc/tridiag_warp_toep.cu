@@ -23,6 +23,22 @@ lrp_status tri_launch_warp_toep(Ctx* c, ClPlan* pl, ClKArgs& a) {
   }
 }
 
+lrp_status tri_launch_warp_block_toep(Ctx* c, ClPlan* pl, ClKArgs& a) {
+  if (!a.tz.on || a.src.Q > 0) return set_err(c, LRP_EINVAL, "constant-coefficient kernel: no data or a source");
+  switch (pl->m) {
+    case 16: return launch_blk_wt<16>(c, pl, a);
+    case 15: return launch_blk_wt<15>(c, pl, a);
+    case 14: return launch_blk_wt<14>(c, pl, a);
+    case 13: return launch_blk_wt<13>(c, pl, a);
+    case 12: return launch_blk_wt<12>(c, pl, a);
+    case 11: return launch_blk_wt<11>(c, pl, a);
+    case 10: return launch_blk_wt<10>(c, pl, a);
+    case 9: return launch_blk_wt<9>(c, pl, a);
+    case 8: return launch_blk_wt<8>(c, pl, a);
+    default: return set_err(c, LRP_EINVAL, "warp chunk length out of range");
+  }
+}
+
 void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m, ToepCoef* tz) {
   *tz = ToepCoef{};
   if (!op->toeplitz || m < 3) return;

@@ -550,6 +550,36 @@ def test_toeplitz_warp_kernel_heat_and_eligibility(ctx, orc):
         ctx.set_param("tri_wtoep", 0)
 
 
+@pytest.mark.parametrize("n,nvec,M", [(4095, 300, 37), (511, 20, 700), (1023, 400, 3), (2048, 290, 1),
+                                    (255, 9, 5)])
+def test_toeplitz_block_kernel_matches_oracle(ctx, orc, n, nvec, M):
+    """FP64 batches too large for the cluster kernels (or systems too short
+    for them) with constant coefficients run the block variant of the
+    constant-coefficient kernel (one system per CTA of 2 to 8 warps; n = 255
+    stays on the general path): forward and adjoint against the oracle and
+    against the general path (tri_wtoep = 2)."""
+    lo, di, up = W.adr1d_op(n)
+    dt = 1.0 / 16384
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    X = np.random.default_rng(n + M).standard_normal((nvec, n))
+    oop = orc.Tridiag(lo, di, up)
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * cond * 2.2e-16)
+    for adjoint in (False, True):
+        got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+        try:
+            ctx.set_param("tri_wtoep", 2)
+            gen = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+        finally:
+            ctx.set_param("tri_wtoep", 0)
+        rows = range(0, nvec, max(1, nvec // 7))
+        want = orc.propagate(oop, dt, M, X[list(rows)], adjoint=adjoint)
+        for k, v in enumerate(rows):
+            assert rel(got[v], want[k]) <= tol
+        for v in range(nvec):
+            assert rel(got[v], gen[v]) <= tol
+
+
 # ---------------------------------------------------------------------------
 # classical Parareal (backward-Euler coarse step), the comparison method
 # ---------------------------------------------------------------------------
