@@ -566,12 +566,14 @@ def test_toeplitz_block_kernel_matches_oracle(ctx, orc, n, nvec, M):
     cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
     tol = max(1e-12, 4 * M * cond * 2.2e-16)
     for adjoint in (False, True):
-        got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
         try:
+            ctx.set_param("tri_warp", 1)             # not the cluster kernels
+            got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
             ctx.set_param("tri_wtoep", 2)
             gen = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
         finally:
             ctx.set_param("tri_wtoep", 0)
+            ctx.set_param("tri_warp", 0)
         rows = range(0, nvec, max(1, nvec // 7))
         want = orc.propagate(oop, dt, M, X[list(rows)], adjoint=adjoint)
         for k, v in enumerate(rows):
