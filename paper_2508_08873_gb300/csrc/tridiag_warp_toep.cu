@@ -62,8 +62,8 @@ void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m,
   if (!(std::fabs(den) > 1e-3)) return;
   // rescale period: dinf^P within 1e150 either way
   const double lg = std::fabs(std::log10(dinf));
-  int P = lg > 1e-3 ? (int)std::floor(150.0 / lg) : (1 << 30);
-  P = std::max(1, std::min(P, 1 << 30));
+  const double Pd = lg > 0.0 ? std::floor(150.0 / lg) : (double)(1 << 30);
+  const int P = (int)std::max(1.0, std::min(Pd, (double)(1 << 30)));
   tz->on = 1;
   tz->P = P;
   tz->a = a;

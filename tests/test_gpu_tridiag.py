@@ -509,6 +509,33 @@ def test_toeplitz_warp_kernel_matches_oracle(ctx, orc, n, wchunk, M):
             assert rel(got[v], want[v]) <= tol, (adjoint, v, rel(got[v], want[v]), tol)
 
 
+@pytest.mark.parametrize("dt,M,nvec", [(1.0, 100, 4), (1e-9, 50, 4), (1.0 / 16384, 5, 200)])
+def test_toeplitz_warp_kernel_stiff_mild_and_many(ctx, orc, dt, M, nvec):
+    """The constant-coefficient kernel with a stiff step (steady pivot
+    ~1.7e5: rescaled every 28 steps), an almost-identity step (pivot
+    ~1 + 3.4e-4: no rescale) and more systems than resident clusters (each
+    cluster loops over systems)."""
+    n = 4095
+    lo, di, up = W.adr1d_op(n)
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    X = np.random.default_rng(nvec + M).standard_normal((nvec, n))
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 4 * M * min(cond, 1e4) * 2.2e-16)
+    try:
+        ctx.set_param("tri_warp", 2)
+        ctx.set_param("tri_wchunk", 13)
+        ctx.set_param("tri_wtoep", 1)
+        got = api.propagate(ctx, op, dt, M, X)
+    finally:
+        ctx.set_param("tri_warp", 0)
+        ctx.set_param("tri_wchunk", 0)
+        ctx.set_param("tri_wtoep", 0)
+    rows = list(range(0, nvec, max(1, nvec // 5)))
+    want = orc.propagate(orc.Tridiag(lo, di, up), dt, M, X[rows])
+    for k, v in enumerate(rows):
+        assert rel(got[v], want[k]) <= tol, (v, rel(got[v], want[k]), tol)
+
+
 def test_toeplitz_warp_kernel_heat_and_eligibility(ctx, orc):
     """The heat operator (symmetric, diffusion only) on the Toeplitz variant
     matches the oracle; a variable-coefficient operator, a source term or a
