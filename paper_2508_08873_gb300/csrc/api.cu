@@ -641,23 +641,24 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
       const int Cb = ((op->n + mb - 1) / mb + 31) / 32;
       const bool blk_auto = c->p_tri_wblock == 0 && prec == 1 && C == 1 && c->p_tri_cluster == 0 &&
                             c->p_tri_chunk == 0 && c->p_tri_spt == 0;
-      // FP64 constant-coefficient batches without a source: the block
-      // variant of the constant-coefficient kernel, on the longest chunk
+      // Constant-coefficient batches without a source (FP64, and the FP32
+      // ones that take no cluster): the block variant of the
+      // constant-coefficient kernel, on the longest chunk
       // length with n mod MM in {0, MM - 1}, 2 to 8 warps per system and the
       // warps at least three quarters full.  Measured on GB300 (ms per
       // launch, the one-CTA-per-system kernel in brackets): n = 4095, 256
       // steps: 300 systems 2.81 (3.80), 1536 systems 15.35 (17.74), 3072
       // systems 29.3 (32.5); n = 1023, 64 steps, 512 systems: 0.326 (0.372);
       // a single half-full warp per system (n = 255) is slower: 0.213 (0.144).
-      if (prec == 0 && op->toeplitz && src.Q == 0 && c->p_tri_wtoep != 2 && c->p_tri_wblock != 2 &&
-          c->p_tri_cluster == 0 && c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
+      if ((prec == 0 || C == 1) && op->toeplitz && src.Q == 0 && c->p_tri_wtoep != 2 &&
+          c->p_tri_wblock != 2 && c->p_tri_cluster == 0 && c->p_tri_chunk == 0 && c->p_tri_spt == 0) {
         for (int mm = 16; mm >= 8; --mm) {
           if ((wc && mm != wc) || (op->n % mm != 0 && (op->n + 1) % mm != 0)) continue;
           const int chunks = (op->n + mm - 1) / mm;
           const int Ct = (chunks + 31) / 32;
           if (Ct < 2 || Ct > 8 || 4 * chunks < 3 * 32 * Ct) continue;
           ToepCoef tzb{};
-          tri_toeplitz_coef(op, dt, adjoint, M, mm, &tzb);
+          tri_toeplitz_coef(op, dt, adjoint, M, mm, &tzb, prec);
           if (!tzb.on) continue;
           ClPlan* cp = nullptr;
           lrp_status s = tri_get_cluster_plan(c, op, dt, adjoint, Ct, mm, &cp, 1);

@@ -257,7 +257,8 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
 // steps on chunks of m rows, if the operator is Toeplitz, its step matrix has
 // a steady pivot, and n mod m is 0 or m - 1 (so that no chunk interior mixes
 // rows of the system with padding rows); tz->on = 0 otherwise.
-void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m, ToepCoef* tz);
+void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m, ToepCoef* tz,
+                       int prec = 0);
 
 // Allocation-free variant: factorisation into caller-provided scratch.
 size_t tri_raw_scratch_bytes(int n);

@@ -39,8 +39,10 @@ template <int S>
 lrp_status tri_launch_warp(Ctx* c, ClPlan* pl, ClKArgs& a);
 
 // The constant-coefficient variant of the cluster kernel (a.tz.on, no
-// source term, FP64), and of the one-CTA-per-system kernel (C <= 8).
+// source term, FP64), and of the one-CTA-per-system kernel (C <= 8; T =
+// float or double).
 lrp_status tri_launch_warp_toep(Ctx* c, ClPlan* pl, ClKArgs& a);
+template <typename T>
 lrp_status tri_launch_warp_block_toep(Ctx* c, ClPlan* pl, ClKArgs& a);
 
 // One system per CTA of C warps (T = float or double; chunks of 8, 12 or 16
@@ -308,9 +310,9 @@ __device__ __forceinline__ void warp_steps(const ClKArgs& a, X& xch, int c, int 
 // the cluster barrier are those of warp_steps; the correction is deferred
 // into the next step's sweeps through S phi and S fq.
 // ---------------------------------------------------------------------------
-template <int MM, int HLO, class X>
+template <typename T, int MM, int HLO, class X>
 __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c, int tl, int sys0,
-                                                int dsys) {
+                                                int dsys, T* shc = nullptr) {
   static_assert(HLO >= 0 && HLO <= MM - 2, "split row out of range");
   const int C = a.C;
   const int t = c * 32 + tl;
@@ -318,105 +320,136 @@ __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c,
   const int r0 = t * MM;
   const unsigned FULL = 0xffffffffu;
   const ToepCoef& z = a.tz;
-  const double* gco = static_cast<const double*>(a.coef) + (size_t)c * 5 * MM * 32;
-  const double* gpc = static_cast<const double*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
-  const double* gsp = static_cast<const double*>(a.spk) + (size_t)c * 2 * 32;
-  const double* gsu = static_cast<const double*>(a.sup);
+  const T* gco = static_cast<const T*>(a.coef) + (size_t)c * 5 * MM * 32;
+  const T* gpc = static_cast<const T*>(a.lpcr) + (size_t)c * (2 * CLW_L + 1) * 32;
+  const T* gsp = static_cast<const T*>(a.spk) + (size_t)c * 2 * 32;
+  const T* gsu = static_cast<const T*>(a.sup);
   // this lane's chunk: Toeplitz interior rows, or identity padding rows
   const bool real = r0 < n;
-  const double l = real ? z.l : 0.0, u = real ? z.u : 0.0;
-  auto s_fwd = [&](double* v) {
+  const T l = real ? (T)z.l : T(0), u = real ? (T)z.u : T(0);
+  auto s_fwd = [&](T* v) {
 #pragma unroll
     for (int i = 1; i < MM - 1; ++i) v[i] = fmaT(-l, v[i - 1], v[i]);
   };
-  auto s_bwd_hi = [&](double* v) {
+  auto s_bwd_hi = [&](T* v) {
 #pragma unroll
     for (int i = MM - 3; i >= HLO; --i) v[i] = fmaT(-u, v[i + 1], v[i]);
   };
-  auto s_bwd_lo = [&](double* v) {
+  auto s_bwd_lo = [&](T* v) {
 #pragma unroll
     for (int i = HLO - 1; i >= 0; --i) v[i] = fmaT(-u, v[i + 1], v[i]);
   };
   // phi = (L U)^{-1} e_0 of a Toeplitz chunk (the same in every lane;
   // formed again for the last step rather than kept in registers)
-  auto make_phi = [&](double* phi) {
+  auto make_phi = [&](T* phi) {
 #pragma unroll
-    for (int i = 0; i < MM; ++i) phi[i] = i == 0 ? 1.0 : 0.0;
+    for (int i = 0; i < MM; ++i) phi[i] = i == 0 ? T(1) : T(0);
 #pragma unroll
-    for (int i = 1; i < MM - 1; ++i) phi[i] = fmaT(-z.l, phi[i - 1], phi[i]);
+    for (int i = 1; i < MM - 1; ++i) phi[i] = fmaT(-(T)z.l, phi[i - 1], phi[i]);
 #pragma unroll
-    for (int i = MM - 3; i >= 0; --i) phi[i] = fmaT(-z.u, phi[i + 1], phi[i]);
+    for (int i = MM - 3; i >= 0; --i) phi[i] = fmaT(-(T)z.u, phi[i + 1], phi[i]);
 #pragma unroll
-    for (int i = 0; i < MM - 1; ++i) phi[i] *= z.idinf;
+    for (int i = 0; i < MM - 1; ++i) phi[i] *= (T)z.idinf;
   };
-  double phi[MM], sphi[MM], sq[MM];
+  T phi[MM], sphi[MM], sq[MM];
   make_phi(phi);
-  const double delta = z.d - z.dinf;
-  const double kap_sys = delta / (1.0 + delta * phi[0]);
-  const double kap = real ? kap_sys : 0.0;
-  const double beta = (real && r0 > 0) ? z.a * (1.0 - kap_sys * phi[0]) : 0.0;
-  // S phi and S fq: the deferred correction
+  const T delta = (T)(z.d - z.dinf);
+  const T kap_sys = delta / (T(1) + delta * phi[0]);
+  const T kap = real ? kap_sys : T(0);
+  const T beta = (real && r0 > 0) ? (T)z.a * (T(1) - kap_sys * phi[0]) : T(0);
+  // S phi and S fq: the deferred correction.  With shc (the block kernel),
+  // both live in shared memory: S phi is the same in every lane, and S fq
+  // too, times qs = 0 for the lanes without a right coupling (padding, or
+  // an interface row past the system); fq is then the fq of chunk 0
+  // (identical in every chunk with a right coupling).
+  const T qs = (real && r0 + MM - 1 < n) ? T(1) : T(0);
+  const T* gq0 = static_cast<const T*>(a.coef) + 4 * MM * 32;   // chunk 0's fq
 #pragma unroll
   for (int i = 0; i < MM - 1; ++i) {
     sphi[i] = phi[i];
-    sq[i] = gco[(4 * MM + i) * 32 + tl];
+    sq[i] = shc ? gq0[i * 32] : gco[(4 * MM + i) * 32 + tl];
   }
-  s_fwd(sphi); s_bwd_hi(sphi); s_bwd_lo(sphi);
-  s_fwd(sq); s_bwd_hi(sq); s_bwd_lo(sq);
+  if (shc) {
+    const T lr = (T)z.l, ur = (T)z.u;
+#pragma unroll
+    for (int i = 1; i < MM - 1; ++i) {
+      sphi[i] = fmaT(-lr, sphi[i - 1], sphi[i]);
+      sq[i] = fmaT(-lr, sq[i - 1], sq[i]);
+    }
+#pragma unroll
+    for (int i = MM - 3; i >= 0; --i) {
+      sphi[i] = fmaT(-ur, sphi[i + 1], sphi[i]);
+      sq[i] = fmaT(-ur, sq[i + 1], sq[i]);
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int i = 0; i < MM - 1; ++i) {
+        shc[i] = sphi[i];
+        shc[MM + i] = sq[i];
+      }
+    __syncthreads();
+  } else {
+    s_fwd(sphi); s_bwd_hi(sphi); s_bwd_lo(sphi);
+    s_fwd(sq); s_bwd_hi(sq); s_bwd_lo(sq);
+  }
+  // the correction vectors of row i
+  auto cphi = [&](int i) -> T { return shc ? shc[i] : sphi[i]; };
+  auto cq = [&](int i) -> T { return shc ? shc[MM + i] : sq[i]; };
   // interface row (couplings aE to row MM-2 and cE to the next chunk's row
   // 0), divided by dinf, in terms of w: X_{MM-2} = w_{MM-2} - kappa phi_{MM-2}
   // w_0 and X'_0 = (1 - kappa phi_0) w'_0
-  const double aE = gco[(0 * MM + MM - 1) * 32 + tl];
-  const double cE = gco[(2 * MM + MM - 1) * 32 + tl];
-  const double cA = aE * z.idinf;
-  const double cK = aE * kap * phi[MM - 2] * z.idinf;
-  const double cB = cE * (1.0 - kap_sys * phi[0]) * z.idinf;
-  double k1[CLW_L], k2[CLW_L];
+  const T idinf = (T)z.idinf, dinf = (T)z.dinf;
+  const T aE = gco[(0 * MM + MM - 1) * 32 + tl];
+  const T cE = gco[(2 * MM + MM - 1) * 32 + tl];
+  const T cA = aE * idinf;
+  const T cK = aE * kap * phi[MM - 2] * idinf;
+  const T cB = cE * (T(1) - kap_sys * phi[0]) * idinf;
+  T k1[CLW_L], k2[CLW_L];
 #pragma unroll
   for (int lv = 0; lv < CLW_L; ++lv) {
     k1[lv] = gpc[lv * 32 + tl];
     k2[lv] = gpc[(CLW_L + lv) * 32 + tl];
   }
-  const double dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] * z.dinf : 0.0;
-  const double p2 = gsp[tl], q2 = gsp[32 + tl];
+  const T dv = tl < 31 ? gpc[2 * CLW_L * 32 + tl] * dinf : T(0);
+  const T p2 = gsp[tl], q2 = gsp[32 + tl];
   const int q = tl & (CL_MAXC - 1);
-  const double sa = q < C ? gsu[6 * q + 0] * z.idinf : 0.0;
-  const double sc1 = q < C ? gsu[6 * q + 1] * z.idinf : 0.0;
-  const double sc2 = q < C ? gsu[6 * q + 2] * (1.0 - kap_sys * phi[0]) * z.idinf : 0.0;
-  const double* minv = gsu + 6 * CL_MAXC;
-  const double msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
-                                            : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : 0.0)) * z.dinf
-                            : 0.0;
+  const T sa = q < C ? gsu[6 * q + 0] * idinf : T(0);
+  const T sc1 = q < C ? gsu[6 * q + 1] * idinf : T(0);
+  const T sc2 = q < C ? gsu[6 * q + 2] * (T(1) - kap_sys * phi[0]) * idinf : T(0);
+  const T* minv = gsu + 6 * CL_MAXC;
+  const T msel = q < C ? (tl < CL_MAXC ? minv[c * CL_MAXC + q]
+                                       : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : T(0))) * dinf
+                       : T(0);
   int pb = 0;
   for (int sys = sys0; sys < a.nsys; sys += dsys) {
-    double x[MM];
+    T x[MM];
 #pragma unroll
     for (int i = 0; i < MM; ++i) {
       const int r = r0 + i;
-      double v = 0.0;
+      T v = T(0);
       if (r < n) {
         if (a.in.gen)
-          v = gauss<double>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+          v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
                             (uint32_t)(sys % a.in.ncol), (uint32_t)r);
         else if (a.in.x == nullptr)
-          v = 0.0;
+          v = T(0);
         else if (a.in.x_f64)
-          v = static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+          v = (T)static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
         else
-          v = (double)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
+          v = (T)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + r];
       }
       x[i] = v;
     }
     if (a.M > 0) {
-      double z0 = 0.0, y = 0.0, yl = 0.0, w0 = 0.0, v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+      T z0 = T(0), y = T(0), yl = T(0), w0 = T(0), v0 = T(0), v1 = T(0), v2 = T(0), v3 = T(0);
       auto pcr = [&]() {
-        double gnext = __shfl_down_sync(FULL, x[0], 1);
-        if (tl == 31) gnext = 0.0;
-        double r = fmaT(-cB, gnext, fmaT(cK, x[0], fmaT(-cA, x[MM - 2], x[MM - 1])));
+        T gnext = __shfl_down_sync(FULL, x[0], 1);
+        if (tl == 31) gnext = T(0);
+        T r = fmaT(-cB, gnext, fmaT(cK, x[0], fmaT(-cA, x[MM - 2], x[MM - 1])));
 #pragma unroll
         for (int lv = 0; lv < CLW_L; ++lv) {
-          const double rm = __shfl_up_sync(FULL, r, 1 << lv);
-          const double rp = __shfl_down_sync(FULL, r, 1 << lv);
+          const T rm = __shfl_up_sync(FULL, r, 1 << lv);
+          const T rp = __shfl_down_sync(FULL, r, 1 << lv);
           if (tl < 31) r = r - k1[lv] * rm - k2[lv] * rp;
         }
         z0 = r * dv;
@@ -426,19 +459,19 @@ __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c,
         v3 = __shfl_sync(FULL, x[0], 0);
       };
       auto super_solve = [&]() {
-        double rhs = 0.0;
+        T rhs = T(0);
         if (q < C) {
-          const double* pq = xch.slot(pb, q);
+          const T* pq = xch.slot(pb, q);
           rhs = fmaT(-sa, pq[1], pq[2]);
           if (q + 1 < C) {
-            const double* pn = xch.slot(pb, q + 1);
+            const T* pn = xch.slot(pb, q + 1);
             rhs = fmaT(-sc2, pn[3], fmaT(-sc1, pn[0], rhs));
           }
         }
-        double Ys = msel * rhs;
+        T Ys = msel * rhs;
 #pragma unroll
         for (int o = CL_MAXC / 2; o > 0; o >>= 1) Ys += __shfl_xor_sync(FULL, Ys, o);
-        const double Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
+        const T Yc = __shfl_sync(FULL, Ys, 0), Yl = __shfl_sync(FULL, Ys, CL_MAXC);
         y = (tl < 31) ? z0 - p2 * Yl - q2 * Yc : Yc;
         yl = __shfl_up_sync(FULL, y, 1);
         if (tl == 0) yl = Yl;
@@ -456,20 +489,22 @@ __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c,
         super_solve();
         s_bwd_lo(x);
         if (resc) {
-          y *= z.rho;
-          yl *= z.rho;
-          w0 *= z.rho;
+          const T rho = (T)z.rho;
+          y *= rho;
+          yl *= rho;
+          w0 *= rho;
 #pragma unroll
-          for (int i = 0; i < MM - 1; ++i) x[i] *= z.rho;
+          for (int i = 0; i < MM - 1; ++i) x[i] *= rho;
         }
-        const double sc = fmaT(kap, w0, beta * yl);
-        x[0] = fmaT(-sc, sphi[0], fmaT(-sq[0], y, x[0]));
-        x[MM - 2] = fmaT(-sc, sphi[MM - 2], fmaT(-sq[MM - 2], y, x[MM - 2]));
+        const T sc = fmaT(kap, w0, beta * yl);
+        const T yq = shc ? qs * y : y;
+        x[0] = fmaT(-sc, cphi(0), fmaT(-cq(0), yq, x[0]));
+        x[MM - 2] = fmaT(-sc, cphi(MM - 2), fmaT(-cq(MM - 2), yq, x[MM - 2]));
         x[MM - 1] = y;
         pb ^= 1;
         pcr();
 #pragma unroll
-        for (int i = 1; i < MM - 2; ++i) x[i] = fmaT(-sc, sphi[i], fmaT(-sq[i], y, x[i]));
+        for (int i = 1; i < MM - 2; ++i) x[i] = fmaT(-sc, cphi(i), fmaT(-cq(i), yq, x[i]));
         xch.publish(pb, c, tl, C, v0, v1, v2, v3);
       };
       s_fwd(x); s_bwd_hi(x); s_bwd_lo(x);
@@ -490,13 +525,14 @@ __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c,
       xch.arrive();
       xch.wait();
       super_solve();
-      const double sc = fmaT(kap, x[0], beta * yl);
-      double phl[MM];
+      const T sc = fmaT(kap, x[0], beta * yl);
+      const T fin = (T)z.fin;
+      T phl[MM];
       make_phi(phl);
 #pragma unroll
       for (int i = 0; i < MM - 1; ++i)
-        x[i] = (x[i] - sc * phl[i] - gco[(4 * MM + i) * 32 + tl] * y) * z.fin;
-      x[MM - 1] = y * z.fin;
+        x[i] = (x[i] - sc * phl[i] - gco[(4 * MM + i) * 32 + tl] * y) * fin;
+      x[MM - 1] = y * fin;
       pb ^= 1;
     }
     const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
@@ -505,7 +541,7 @@ __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c,
       const int r = r0 + i;
       if (r < n) {
         if (a.out.y_f64)
-          static_cast<double*>(a.out.y)[oy + r] = x[i];
+          static_cast<double*>(a.out.y)[oy + r] = (double)x[i];
         else
           static_cast<float*>(a.out.y)[oy + r] = (float)x[i];
       }
@@ -583,7 +619,7 @@ __global__ void __launch_bounds__(32) k_tri_cluster_wt(ClKArgs a) {
   __syncwarp();
   cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
   XchCluster xch{pubg, rpub};
-  warp_steps_toep<MM, HLO>(a, xch, c, tl, (int)blockIdx.x / C, (int)gridDim.x / C);
+  warp_steps_toep<double, MM, HLO>(a, xch, c, tl, (int)blockIdx.x / C, (int)gridDim.x / C);
   cl.sync();  // no CTA leaves while others may still store into its shared memory
 }
 
@@ -603,30 +639,36 @@ __global__ void __launch_bounds__(blk_w_threads<T>()) k_tri_block_w(ClKArgs a) {
                               (int)blockIdx.x, (int)gridDim.x);
 }
 
-// FP64 constant-coefficient variant, one system per CTA of C warps (C <= 8)
-template <int MM, int HLO>
-__global__ void __launch_bounds__(256) k_tri_block_wt(ClKArgs a) {
+// Constant-coefficient variant, one system per CTA of C warps (C <= 8):
+// FP64, or FP32 at three CTAs per SM
+template <typename T>
+constexpr int blk_wt_min_ctas() { return sizeof(T) == 8 ? 1 : 3; }
+
+template <typename T, int MM, int HLO>
+__global__ void __launch_bounds__(256, blk_wt_min_ctas<T>()) k_tri_block_wt(ClKArgs a) {
   if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
-  __shared__ double pubg[2][CL_MAXC][4];
-  XchBlock<double> xch{pubg};
-  warp_steps_toep<MM, HLO>(a, xch, (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31),
-                           (int)blockIdx.x, (int)gridDim.x);
+  __shared__ T pubg[2][CL_MAXC][4];
+  __shared__ T shc[2 * MM];
+  XchBlock<T> xch{pubg};
+  warp_steps_toep<T, MM, HLO>(a, xch, (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31),
+                              (int)blockIdx.x, (int)gridDim.x, sizeof(T) == 4 ? shc : nullptr);
 }
 
-template <int MM>
+template <typename T, int MM>
 static lrp_status launch_blk_wt(Ctx* c, ClPlan* pl, ClKArgs& a) {
-  auto kern = k_tri_block_wt<MM, (MM - 2) / 3>;
+  auto kern = k_tri_block_wt<T, MM, (MM - 2) / 3>;
   const int threads = 32 * pl->C;
-  if (threads > 256) return set_err(c, LRP_EINVAL, "block warp kernel: at most 8 warps per system in FP64");
+  if (threads > 256) return set_err(c, LRP_EINVAL, "block warp kernel: at most 8 warps per system");
   int per_sm = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0);
   if (e || per_sm < 1) { cudaGetLastError(); per_sm = 1; }
   const int grid = std::min(a.nsys, per_sm * c->num_sms);
+  const char* fam = sizeof(T) == 8 ? "propagate_f64" : "propagate_f32";
   cudaEvent_t ev = nullptr;
-  timer_begin(c, "propagate_f64", &ev);
+  timer_begin(c, fam, &ev);
   kern<<<grid, threads, 0, c->stream>>>(a);
   e = cudaGetLastError();
-  timer_end(c, "propagate_f64", ev);
+  timer_end(c, fam, ev);
   if (e) return cuda_err(c, e, "k_tri_block_wt launch");
   return LRP_OK;
 }

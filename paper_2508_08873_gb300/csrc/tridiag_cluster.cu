@@ -608,9 +608,9 @@ lrp_status tri_propagate_warp_block(Ctx* c, ClPlan* pl, int M, int nsys, int pre
   a.spk = b[2].ptr;
   a.sup = b[3].ptr;
   if (tz && tz->on) {
-    if (prec != 0) return set_err(c, LRP_EINVAL, "constant-coefficient kernel is FP64");
     a.tz = *tz;
-    return tri_launch_warp_block_toep(c, pl, a);
+    return prec == 0 ? tri_launch_warp_block_toep<double>(c, pl, a)
+                     : tri_launch_warp_block_toep<float>(c, pl, a);
   }
   return prec == 0 ? tri_launch_warp_block<double>(c, pl, a) : tri_launch_warp_block<float>(c, pl, a);
 }

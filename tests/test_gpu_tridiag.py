@@ -536,6 +536,33 @@ def test_toeplitz_warp_kernel_stiff_mild_and_many(ctx, orc, dt, M, nvec):
         assert rel(got[v], want[k]) <= tol, (v, rel(got[v], want[k]), tol)
 
 
+@pytest.mark.parametrize("M", [1, 37, 300])
+def test_toeplitz_block_kernel_f32(ctx, orc, M):
+    """FP32 batches of a constant-coefficient operator (the sketches) run the
+    FP32 block variant (S phi and S fq in shared memory, three CTAs per SM,
+    rescaled every 13 steps): forward and adjoint against the oracle to FP32
+    accuracy, and against the general FP32 block kernel."""
+    n, nvec = 4095, 300
+    lo, di, up = W.adr1d_op(n)
+    dt = 1.0 / 16384
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    X = np.random.default_rng(M).standard_normal((nvec, n))
+    oop = orc.Tridiag(lo, di, up)
+    for adjoint in (False, True):
+        got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, prec="mixed")
+        try:
+            ctx.set_param("tri_wtoep", 2)
+            gen = api.propagate(ctx, op, dt, M, X, adjoint=adjoint, prec="mixed")
+        finally:
+            ctx.set_param("tri_wtoep", 0)
+        rows = list(range(0, nvec, 50))
+        want = orc.propagate(oop, dt, M, X[rows], adjoint=adjoint)
+        for k, v in enumerate(rows):
+            assert rel(got[v], want[k]) <= 2e-5
+        for v in range(nvec):
+            assert rel(got[v], gen[v]) <= 4e-5
+
+
 def test_toeplitz_warp_kernel_heat_and_eligibility(ctx, orc):
     """The heat operator (symmetric, diffusion only) on the Toeplitz variant
     matches the oracle; a variable-coefficient operator, a source term or a
