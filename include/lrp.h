@@ -93,8 +93,15 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    16; 0 = automatic);
  *   "tri_wblock":    one system per CTA of C warps (the one-warp kernel's
  *                    steps with the exchange in shared memory): 0 = automatic
- *                    (FP32 batches that do not take a cluster), 1 = always
- *                    (FP64: at most 8 warps, else LRP_EINVAL), 2 = never;
+ *                    (FP32 batches that do not take a cluster, and FP64
+ *                    constant-coefficient batches beyond the cluster kernels'
+ *                    range), 1 = always (FP64: at most 8 warps, else
+ *                    LRP_EINVAL), 2 = never;
+ *   "tri_wtoep":     the constant-coefficient variant of the one-warp kernels
+ *                    (operators whose lo[1..n-1], di and up[0..n-2] are each
+ *                    one value, no source term, n mod MM in {0, MM - 1}):
+ *                    0 = automatic, 1 = always (LRP_EINVAL where it does not
+ *                    apply), 2 = never;
  *   "tri_wsplit":    where the one-warp kernel runs the chunk-interior solve
  *                    of the next step: 0 = all of it between the cluster
  *                    barrier's arrive and wait, 1 (default) = its last third
@@ -131,7 +138,9 @@ lrp_status lrp_reset_kernel_time(lrp_ctx* ctx);
 
 /* Tridiagonal A, row i: lo[i] x[i-1] + di[i] x[i] + up[i] x[i+1] (lo[0] and
  * up[n-1] are ignored).  I + dt*A must be diagonally dominant: the
- * propagator eliminates without pivoting.  2 <= n <= 16384. */
+ * propagator eliminates without pivoting.  2 <= n <= 16384.  The call reads
+ * the arrays back once to note whether the coefficients are constant (the
+ * propagator has faster kernels for that case; "tri_wtoep"). */
 lrp_status lrp_operator_tridiag(lrp_ctx* ctx, int n, const double* lo, const double* di,
                                 const double* up, lrp_operator** out);
 /* 5-point A on an mx x my grid of interior nodes, node p = iy*mx + ix:
