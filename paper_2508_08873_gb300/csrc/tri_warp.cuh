@@ -289,8 +289,9 @@ __device__ __forceinline__ void warp_steps(const ClKArgs& a, X& xch, int c, int 
 }
 
 // ---------------------------------------------------------------------------
-// Constant-coefficient variant (FP64, no source; one system per cluster of
-// one-warp CTAs).  Every chunk interior is the Toeplitz matrix T (lower a,
+// Constant-coefficient variant (no source; FP64 on a cluster of one-warp
+// CTAs per system, FP64 or FP32 on one CTA of warps per system).  Every
+// chunk interior is the Toeplitz matrix T (lower a,
 // diagonal d, upper c) of m = MM - 1 rows, or identity padding rows.  With
 // the steady pivot dinf of the LU factorisation of tridiag(a, d, c),
 //   T = L U + (d - dinf) e_0 e_0^T,  L = I + l E^T,  U = dinf (I + u E),
@@ -307,8 +308,10 @@ __device__ __forceinline__ void warp_steps(const ClKArgs& a, X& xch, int c, int 
 // interface row, PCR and super system take the scaling in their constants
 // (the interface residual is formed divided by dinf), and every P steps the
 // state is multiplied by rho = dinf^-P.  The step loop and its split around
-// the cluster barrier are those of warp_steps; the correction is deferred
-// into the next step's sweeps through S phi and S fq.
+// the barrier are those of warp_steps; the correction is deferred into the
+// next step's sweeps through S phi and S fq.  (In FP32 the host sets dinf so
+// that the swept matrix keeps the smallest eigenvalue of tridiag(a, d, c)
+// exactly; see tri_toeplitz_coef.)
 // ---------------------------------------------------------------------------
 template <typename T, int MM, int HLO, class X>
 __device__ __forceinline__ void warp_steps_toep(const ClKArgs& a, X& xch, int c, int tl, int sys0,
