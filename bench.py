@@ -75,6 +75,20 @@ def dist_env():
     return rank, world, local
 
 
+def aggregate_over_ranks(ms_step: float, world: int, device=None):
+    """Whole-job throughput of `world` independent replicas (one solve per rank
+    and step): the step time is the slowest rank's (max over ranks, through
+    the initialised process group), and value = world * 1000 / that time.
+    Returns (ms_step, solves per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    return ms_step, world * 1000.0 / ms_step
+
+
 # ---------------------------------------------------------------------------
 # clocks during the timed region
 # ---------------------------------------------------------------------------
@@ -511,12 +525,7 @@ def main():
                                             "svd", "lift")}
     ctx.set_kernel_timing(False)
     clk = clocks.stop()
-    ms_step = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
-    value = world * 1000.0 / ms_step
+    ms_step, value = aggregate_over_ranks(statistics.mean(ms), world, dev)
     if args.headline_only:
         extras = None
     else:
