@@ -36,6 +36,7 @@ constexpr int CSW_MAXROWS = 2048;    // rows per slice (upper limit)
 constexpr int CSW_MAXR = 64;
 constexpr int CSW_KBUF = 96 * 1024;  // bytes of K staged per chunk of the recurrence
 constexpr int CSW_MAXN = 8192;       // intervals + 1 (norms staged in shared memory)
+constexpr int CSW_RPT = 4;           // rows per thread in flight in the apply
 
 // Workspace of one problem (doubles): a-partials [N][nsl][R], coefficients
 // [N][R], norm partials [N+1][nsl][2].
@@ -132,37 +133,65 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
     const int nk = min(kchunk, N - j0);
     __syncthreads();
     const double* Kg = a.K + (size_t)(j0 - 1) * R * R;
-    // eight loads in flight per thread (this CTA stages alone while the
+    // sixteen loads in flight per thread (this CTA stages alone while the
     // other CTAs of the launch have finished)
     const int nkr = nk * R * R;
-    for (int k0 = threadIdx.x; k0 < nkr; k0 += 8 * blockDim.x) {
-      double v[8];
+    for (int k0 = threadIdx.x; k0 < nkr; k0 += 16 * blockDim.x) {
+      double v[16];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int k = k0 + u * blockDim.x;
         v[u] = k < nkr ? __ldcg(&Kg[k]) : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
+      for (int u = 0; u < 16; ++u) {
         const int k = k0 + u * blockDim.x;
         if (k < nkr) sK[k] = (TF)v[u];
       }
     }
     const int na = nk * R;
-    for (int k0 = threadIdx.x; k0 < na; k0 += 4 * blockDim.x) {
-      double v[4];
+    for (int k0 = threadIdx.x; k0 < na; k0 += 8 * blockDim.x) {
+      double v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int k = k0 + u * blockDim.x;
         v[u] = k < na ? a_sum(j0 + k / R, k % R) : 0.0;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int k = k0 + u * blockDim.x;
         if (k < na) sA[k] = (TF)v[u];
       }
     }
     __syncthreads();
+    if (R <= 16) {
+      // one warp, no block barrier: row r of K c on the two lanes r and
+      // r + 16, lane group g taking columns q = g, g + 2, ...; c_q comes from
+      // lane q by a shuffle; the two partial sums are added by one butterfly
+      if (threadIdx.x < 32) {
+        const int r = lane & 15, g = lane >> 4;
+        TF cr = r < R ? cbuf[cb][r] : TF(0);
+        for (int jj = 0; jj < nk; ++jj) {
+          const TF* Kj = sK + (size_t)jj * R * R + r * R;
+          TF cq[8], kq[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int q = 2 * t + g;
+            cq[t] = __shfl_sync(0xffffffffu, cr, q);
+            kq[t] = (r < R && q < R) ? Kj[q] : TF(0);
+          }
+          TF acc = TF(0);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) acc = fma(kq[t], cq[t], acc);
+          acc += __shfl_xor_sync(0xffffffffu, acc, 16);
+          if (r < R) cr = sA[(size_t)jj * R + r] + acc;
+          __syncwarp();
+          if (r < R && g == 0) sA[(size_t)jj * R + r] = cr;
+        }
+        if (r < R && g == 0) cbuf[cb][r] = cr;
+      }
+      __syncthreads();
+    } else
     for (int jj = 0; jj < nk; ++jj) {
       const TF* Kj = sK + (size_t)jj * R * R;
       // rows rr = 0..R-1 of K c, four threads per row (interleaved columns),
@@ -221,15 +250,37 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_apply(const SweepArgs* __re
       const TF* Uj = static_cast<const TF*>(a.U) + (size_t)j * R * n + lo;
       const double* Fj = a.F + (size_t)j * n + lo;
       double* un = a.u + (size_t)(j + 1) * n + lo;
-      for (int i = threadIdx.x; i < rows; i += blockDim.x) {
-        TF g = TF(0);
-        for (int r = 0; r < R; ++r) g += Uj[(size_t)r * n + i] * sc[r];
-        const double nv = Fj[i] + (double)g;
-        const double old = a.initial ? 0.0 : un[i];
-        un[i] = nv;
-        const TF d = (TF)(nv - old), u = (TF)nv;
-        accd += d * d;
-        accu += u * u;
+      // CSW_RPT rows per thread at once, so that all their loads are in flight
+      for (int i0 = threadIdx.x; i0 < rows; i0 += CSW_RPT * blockDim.x) {
+        TF g[CSW_RPT];
+        double fv[CSW_RPT], ov[CSW_RPT];
+#pragma unroll
+        for (int k = 0; k < CSW_RPT; ++k) {
+          const int i = i0 + k * blockDim.x;
+          g[k] = TF(0);
+          fv[k] = i < rows ? Fj[i] : 0.0;
+          ov[k] = (i < rows && !a.initial) ? un[i] : 0.0;
+        }
+        for (int r = 0; r < R; ++r) {
+          const TF sr = sc[r];
+          const TF* ur = Uj + (size_t)r * n;
+#pragma unroll
+          for (int k = 0; k < CSW_RPT; ++k) {
+            const int i = i0 + k * blockDim.x;
+            if (i < rows) g[k] += ur[i] * sr;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < CSW_RPT; ++k) {
+          const int i = i0 + k * blockDim.x;
+          if (i < rows) {
+            const double nv = fv[k] + (double)g[k];
+            un[i] = nv;
+            const TF d = (TF)(nv - ov[k]), u = (TF)nv;
+            accd += d * d;
+            accu += u * u;
+          }
+        }
       }
     }
     accd = warp_sum<TF>(accd);
