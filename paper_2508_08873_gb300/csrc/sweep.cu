@@ -125,8 +125,11 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
     coef[(size_t)start * R + r] = (double)c0;
   }
   TF* sK = reinterpret_cast<TF*>(csw_smem);
-  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(TF) * (R * R + R)));
-  TF* sA = sK + (size_t)kchunk * R * R;
+  // K_j staged with row stride R + 1 (the one-warp recurrence reads a column
+  // of K_j per FMA: rows r = 0..15 then fall in distinct banks)
+  const int KS = R * (R + 1);
+  const int kchunk = max(1, CSW_KBUF / (int)(sizeof(TF) * (KS + R)));
+  TF* sA = sK + (size_t)kchunk * KS;
   const int t = threadIdx.x, rr = t >> 2, part = t & 3;
   int cb = 0;
   for (int j0 = start + 1; j0 < N; j0 += kchunk) {
@@ -146,7 +149,7 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
 #pragma unroll
       for (int u = 0; u < 16; ++u) {
         const int k = k0 + u * blockDim.x;
-        if (k < nkr) sK[k] = (TF)v[u];
+        if (k < nkr) sK[(k / R) * (R + 1) + k % R] = (TF)v[u];
       }
     }
     const int na = nk * R;
@@ -172,7 +175,7 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
         const int r = lane & 15, g = lane >> 4;
         TF cr = r < R ? cbuf[cb][r] : TF(0);
         for (int jj = 0; jj < nk; ++jj) {
-          const TF* Kj = sK + (size_t)jj * R * R + r * R;
+          const TF* Kj = sK + (size_t)jj * KS + r * (R + 1);
           TF cq[8], kq[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
@@ -193,14 +196,14 @@ __global__ void __launch_bounds__(CSW_THREADS) k_csw_project(const SweepArgs* __
       __syncthreads();
     } else
     for (int jj = 0; jj < nk; ++jj) {
-      const TF* Kj = sK + (size_t)jj * R * R;
+      const TF* Kj = sK + (size_t)jj * KS;
       // rows rr = 0..R-1 of K c, four threads per row (interleaved columns),
       // combined by shuffles in a fixed order
       for (int rb = 0; rb < R; rb += CSW_THREADS / 4) {
         const int r = rb + rr;
         TF acc = TF(0);
         if (r < R)
-          for (int q = part; q < R; q += 4) acc = fma(Kj[r * R + q], cbuf[cb][q], acc);
+          for (int q = part; q < R; q += 4) acc = fma(Kj[r * (R + 1) + q], cbuf[cb][q], acc);
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);
         acc += __shfl_xor_sync(0xffffffffu, acc, 2);
         if (r < R && part == 0) {

@@ -194,6 +194,22 @@ def test_parareal_f64_iterates_match_oracle(ctx, orc, K):
         np.testing.assert_allclose(info["bounds"][k - 1], res.bounds[k - 1], rtol=1e-8, atol=1e-14)
 
 
+@pytest.mark.parametrize("R,p", [(20, 4), (16, 4), (5, 2)])
+def test_parareal_sweep_ranks_match_oracle(ctx, orc, R, p):
+    """The sweep's R x R recurrence runs on one warp for R <= 16 and on the
+    whole CTA above; both, and a rank that is not a power of two, give the
+    oracle's iterates and bounds."""
+    P = W.adr1d(n=511, N=8, M=32, R=R, p=p)
+    op, co, u, info = _run_both(ctx, orc, P, K=3)
+    oop = orc.Tridiag(P.lo, P.di, P.up)
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, K=3)
+    assert info["k_done"] == res.k_done == 3
+    assert rel(u, res.iterates[-1]) <= 1e-10
+    for k in range(1, 4):
+        np.testing.assert_allclose(info["bounds"][k - 1], res.bounds[k - 1], rtol=1e-8, atol=1e-14)
+
+
 @pytest.mark.parametrize("tol", [1e-2, 1e-4, 1e-6])
 def test_parareal_device_stopping_matches_oracle(ctx, orc, tol):
     """The tolerance test runs on the device (the sweep sets a stop flag and
