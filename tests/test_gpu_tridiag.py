@@ -421,7 +421,7 @@ def test_warp_cluster_kernel_few_steps(ctx, orc, M):
 @pytest.mark.parametrize("wsplit", [0, 1])
 @pytest.mark.parametrize("wchunk", [8, 12, 16])
 @pytest.mark.parametrize("n,nvec,Q,M", [(3000, 7, 2, 9), (1025, 9, 0, 9), (2049, 5, 2, 1),
-                                        (2049, 5, 0, 2)])
+                                        (2049, 5, 0, 2), (8192, 3, 1, 3)])
 def test_warp_cluster_kernel_split_variants(ctx, orc, n, nvec, Q, M, wchunk, wsplit):
     """The split of the chunk-interior solve around the cluster barrier
     (tri_wsplit 0: all of it before the wait; 1, the default: its last
@@ -494,7 +494,8 @@ def test_block_warp_kernel_matches_oracle(ctx, orc, n, nvec, Q, M, wchunk, prec)
 
 
 @pytest.mark.parametrize("n,wchunk", [(4095, 8), (4095, 9), (4095, 13), (4095, 15), (4095, 16),
-                                      (3000, 12), (1023, 11), (2048, 16), (300, 10)])
+                                      (3000, 12), (1023, 11), (2048, 16), (300, 10), (8191, 16),
+                                      (8192, 16)])
 @pytest.mark.parametrize("M", [1, 2, 3, 37, 700])
 def test_toeplitz_warp_kernel_matches_oracle(ctx, orc, n, wchunk, M):
     """Constant-coefficient operators take the Toeplitz variant of the
