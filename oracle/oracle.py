@@ -395,7 +395,8 @@ def rsvd_interval_indep(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval
     SVD) gives U = Q^T Psi_s, S, V = Vh^T Phi_s.  Accuracy: exact when the
     sketches span the whole space (checked by brute force); otherwise below
     the two-pass variant.  Parity unpinned beyond that and the closed-form
-    spectrum of the heat operator at a loose tolerance."""
+    spectrum of the heat operator at a loose tolerance.  The least-squares
+    step is lstsq_mgs (Gram-Schmidt QR and back substitution, no LAPACK)."""
     n = op.n
     ell = R + p
     ell2 = 2 * ell
@@ -409,7 +410,7 @@ def rsvd_interval_indep(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval
         return CoarseInterval(np.zeros((n, 0)), np.zeros(0), np.zeros((n, 0)), np.zeros(0),
                               0, 0, 0.0, ell + ell2)
     B = psi @ Q.T                                                # (2l, k): (psi_a, q_c)
-    X = np.linalg.lstsq(B, Z, rcond=None)[0]                     # (k, n): F' ~ Q^T X
+    X = lstsq_mgs(B, Z, tau)                                     # (k, n): F' ~ Q^T X
     Vh, _ = mgs2(X, tau)                                         # row space of X
     Xs = X @ Vh.T                                                # (k, k'): X = Xs Vh
     Psi_s, s, Phi_s = jacobi_svd(Xs)
@@ -418,6 +419,28 @@ def rsvd_interval_indep(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval
     V = Vh.T @ Phi_s[:, :Ri]
     sig_next = float(s[Ri]) if s.shape[0] > Ri else tau * float(s[0])
     return CoarseInterval(U, s[:Ri].copy(), V, s, k, Vh.shape[0], sig_next, ell + ell2)
+
+
+def lstsq_mgs(B: np.ndarray, Z: np.ndarray, tau: float = MGS_TAU) -> np.ndarray:
+    """Least-squares solution X of min ||B X - Z||_F for B (m, k) of full
+    column rank k <= m, through a thin QR factorisation of B by the oracle's
+    own Gram-Schmidt (mgs2 on the columns of B): B = Qb^T Rb with Qb (k, m)
+    orthonormal rows and Rb = Qb B upper triangular, then Rb X = Qb Z by
+    back substitution.  Raises when a column of B is deflated (B rank
+    deficient), where the least-squares solution is not unique."""
+    B = _f64(B)
+    Z = _f64(Z)
+    m, k = B.shape
+    Qb, keep = mgs2(B.T, tau)
+    if Qb.shape[0] != k:
+        raise RuntimeError("lstsq_mgs: B is rank deficient (%d of %d columns kept)"
+                           % (Qb.shape[0], k))
+    Rb = Qb @ B                                                  # (k, k), upper triangular
+    rhs = Qb @ Z                                                 # (k, n)
+    X = np.zeros((k, Z.shape[1]))
+    for j in range(k - 1, -1, -1):                               # back substitution
+        X[j] = (rhs[j] - Rb[j, j + 1:] @ X[j + 1:]) / Rb[j, j]
+    return X
 
 
 def build_coarse_indep(op, dt, M, N, R, p, seed) -> Coarse:
@@ -430,8 +453,8 @@ def exact_coarse(op, dt, M, N, R) -> Coarse:
     Eq. (spectral_G), used by tests as a comparison coarse solver."""
     n = op.n
     Fp = propagate(op, dt, M, np.eye(n)).T           # column j = F' e_j
-    Uf, s, Vt = np.linalg.svd(Fp)
-    ci = CoarseInterval(Uf[:, :R].copy(), s[:R].copy(), Vt[:R].T.copy(), s.copy(), n, n,
+    Uf, s, Vf = jacobi_svd(Fp)
+    ci = CoarseInterval(Uf[:, :R].copy(), s[:R].copy(), Vf[:, :R].copy(), s.copy(), n, n,
                         float(s[R]) if R < n else 0.0, 0)
     return Coarse([ci] * N, R, 0)
 

@@ -57,3 +57,27 @@ def test_jacobi_svd_degenerate(orc):
     np.testing.assert_allclose(U @ np.diag(s) @ V.T, A, atol=1e-15)
     U, s, V = orc.jacobi_svd(np.zeros((3, 3)))
     assert np.all(s == 0)
+
+
+def test_lstsq_mgs_normal_equations_and_consistent_systems(orc):
+    """lstsq_mgs (the least-squares step of the two-sided sketch): on a
+    consistent system B X0 = Z it returns X0; on an inconsistent one the
+    residual is orthogonal to the range of B (the normal equations
+    B^T (B X - Z) = 0 that define the least-squares solution); a rank-deficient
+    B is refused."""
+    rng = np.random.default_rng(5)
+    for m, k, n in [(6, 3, 4), (48, 24, 100), (10, 10, 3), (2, 1, 5)]:
+        B = rng.standard_normal((m, k))
+        X0 = rng.standard_normal((k, n))
+        np.testing.assert_allclose(orc.lstsq_mgs(B, B @ X0), X0, rtol=0, atol=1e-11)
+        Z = rng.standard_normal((m, n))
+        X = orc.lstsq_mgs(B, Z)
+        res = B @ X - Z
+        assert np.abs(B.T @ res).max() <= 1e-12 * np.abs(B).max() * np.abs(Z).max() * m
+        # any other candidate has a residual at least as large
+        Xp = X + 1e-3 * rng.standard_normal(X.shape)
+        assert np.linalg.norm(B @ Xp - Z) >= np.linalg.norm(res)
+    B = rng.standard_normal((8, 3))
+    B[:, 2] = B[:, 0] - 2 * B[:, 1]
+    with pytest.raises(RuntimeError):
+        orc.lstsq_mgs(B, rng.standard_normal((8, 2)))

@@ -232,3 +232,114 @@ def test_low_rank_coarse_beats_classical_on_heat(orc):
     e_lr = orc.rel_err(lr.iterates[-1], ref)
     e_cl = orc.rel_err(cl.iterates[-1], ref)
     assert e_lr < 1e-3 * e_cl, (e_lr, e_cl)
+
+
+# ---------------------------------------------------------------------------
+# the bound functions pinned by value
+# ---------------------------------------------------------------------------
+def _hand_values():
+    """Rows of tests/golden/bound_hand_values.txt: name -> list of Fractions."""
+    from fractions import Fraction
+    out = {}
+    path = pathlib.Path(__file__).parent / "golden" / "bound_hand_values.txt"
+    for line in path.read_text().splitlines():
+        if not line.strip() or line.startswith("#"):
+            continue
+        name, _, vals = [s.strip() for s in line.split("|")]
+        out[name] = [Fraction(v) for v in vals.split()]
+    return out
+
+
+def test_bound_functions_match_hand_evaluated_values(orc):
+    """apriori_initial (Eq. error_bound_initial), apriori_k
+    (Eq. error_bound_eps_delta2), apriori_from_e0 (Eq. error_bound_eps_delta),
+    apost_bound (Eq. apost_bound) and efficiency (Eq. def_efficiency) on the
+    hand-worked example of tests/golden/bound_hand_values.txt (delta = 1/2,
+    eps = 3/8, exact rationals)."""
+    hv = _hand_values()
+    d, e = 0.5, 0.375
+    b = np.array([1.0, 2.0, 4.0])
+    e0 = np.array([0.0, 1.0, 3.0, 5.0])
+    du = np.array([7.0, 1.0, 2.0, 4.0, 8.0])
+
+    def chk(got, name):
+        want = np.array([float(v) for v in hv[name]])
+        np.testing.assert_allclose(got, want, rtol=1e-15, atol=0, err_msg=name)
+
+    chk(orc.apriori_initial(d, e, b), "apriori_initial")
+    for k in (1, 2, 3):
+        chk(orc.apriori_k(d, e, b, k), "apriori_k k=%d" % k)
+    for k in (1, 2):
+        chk(orc.apriori_from_e0(d, e, e0, k), "apriori_from_e0 k=%d" % k)
+    ab = orc.apost_bound(d, e, du)
+    chk(ab, "apost_bound")
+    assert orc.efficiency(0.5, ab) == pytest.approx(float(hv["efficiency"][0]), rel=1e-15)
+    # the printed range 1 <= n < N gives the other value (reading G11 takes n <= N)
+    assert 0.5 / ab[1:-1].max() == pytest.approx(float(hv["efficiency_printed_range"][0]), rel=1e-15)
+
+
+def _scalar_problem(orc, N=7, M=3, dt=0.1, lam=2.0):
+    """Scalar u' = -lam u + f(t) with f > 0 and u0 > 0 (one degree of freedom)."""
+    op = orc.Tridiag(np.zeros(1), np.array([lam]), np.zeros(1))
+    g = np.ones((1, 1))
+    t = dt * np.arange(1, N * M + 1)
+    c = (1.0 + 0.5 * np.sin(3.0 * t))[:, None]          # positive source values
+    u0 = np.array([1.3])
+    return op, g, c, u0
+
+
+def test_apost_bound_is_exact_on_scalar_rank0(orc):
+    """A case where the a posteriori bound is attained.  For one degree of
+    freedom and rank R = 0, G_n' = 0 and delta = eps = f := (1 + dt lam)^-M
+    (sigma_1 of the scalar F'); with u0 > 0 and b_n > 0 every Parareal
+    increment u^k_m - u^{k-1}_m = f^k b_{m-k} is positive, so the triangle
+    inequality in the proof of Eq. apost_bound holds with equality and the
+    bound equals ||e^k_n|| for every n and k.  An off-by-one in the sum, a
+    wrong power of delta or a missing factor eps fails this.  The efficiency
+    of Eq. def_efficiency is then exactly 1."""
+    N, M, dt, lam = 7, 3, 0.1, 2.0
+    op, g, c, u0 = _scalar_problem(orc, N, M, dt, lam)
+    f = (1.0 + dt * lam) ** (-M)
+    co = orc.build_coarse(op, dt, M, N, 0, 1, 0)
+    assert co.delta == pytest.approx(f, rel=1e-14) and co.eps == pytest.approx(f, rel=1e-14)
+    ref = orc.sequential_fine(op, dt, M, N, u0, g, c)
+    res = orc.parareal(op, dt, M, N, co, u0, g, c, K=N)
+    assert np.all(res.b[:, 0] > 0)
+    for k in range(1, N):
+        err = np.abs(res.iterates[k][:, 0] - ref[:, 0])
+        inc = res.iterates[k][:, 0] - res.iterates[k - 1][:, 0]
+        assert np.all(inc[k:] > 0) and np.all(inc[:k] == 0)
+        # n <= k: both vanish (the iterate is exact up to the rounding of
+        # F u + b - b); n > k: the bound equals the error
+        assert np.all(res.bounds[k - 1][:k + 1] == 0)
+        assert np.all(err[:k + 1] <= 1e-15 * np.abs(ref).max())
+        np.testing.assert_allclose(res.bounds[k - 1][k + 1:], err[k + 1:], rtol=1e-12, atol=0)
+        assert np.all(err[k + 1:] > 0)
+        assert orc.efficiency(err.max(), res.bounds[k - 1]) == pytest.approx(1.0, rel=1e-12)
+
+
+def test_initial_and_apriori_bounds_on_scalar_rank0(orc):
+    """Same scalar rank-0 problem: e^0_n = -sum_{m<n} f^{n-m} b_m and
+    e^k_n = f^k e^0_{n-k} (the error identity with G' = 0), so the
+    m = n-1 term of Eq. error_bound_initial (min = eps) is attained while
+    the others take 2 delta: bound_n = 2 ||e^0_n|| - f ||b_{n-1}||.  In
+    Eq. error_bound_eps_delta the m = n-k term, binom(k, k-1) = k, carries
+    e^k_n itself: bound_n = k ||e^k_n|| + (terms m < n-k) for delta = eps."""
+    N, M, dt, lam = 6, 4, 0.05, 3.0
+    op, g, c, u0 = _scalar_problem(orc, N, M, dt, lam)
+    f = (1.0 + dt * lam) ** (-M)
+    co = orc.build_coarse(op, dt, M, N, 0, 1, 0)
+    ref = orc.sequential_fine(op, dt, M, N, u0, g, c)
+    res = orc.parareal(op, dt, M, N, co, u0, g, c, K=N)
+    bn = np.concatenate([[abs(u0[0])], np.abs(res.b[:-1, 0])])
+    e0 = np.abs(res.iterates[0][:, 0] - ref[:, 0])
+    bnd0 = orc.apriori_initial(co.delta, co.eps, bn)
+    for n in range(1, N + 1):
+        assert bnd0[n] == pytest.approx(2 * e0[n] - f * bn[n - 1], rel=1e-12)
+    for k in range(1, N):
+        ek = np.abs(res.iterates[k][:, 0] - ref[:, 0])
+        np.testing.assert_allclose(ek[k + 1:], f ** k * e0[1:N - k + 1], rtol=1e-12)
+        bk = orc.apriori_from_e0(co.delta, co.eps, e0, k)
+        tail = np.array([sum(math.comb(n - m, k - 1) * f ** (n - m) * e0[m] for m in range(1, n - k))
+                         for n in range(N + 1)])
+        np.testing.assert_allclose(bk[k + 1:], k * ek[k + 1:] + tail[k + 1:], rtol=1e-12)
