@@ -62,6 +62,13 @@ def parse():
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
                          "of the 2D Krylov fine propagator (HBM GB/s fraction)")
+    ap.add_argument("--krylov-precs", default="mixed,f64",
+                    help="krylov mode: precisions to time (mixed = FP32 sketch settings)")
+    ap.add_argument("--krylov-systems", default="64,16",
+                    help="krylov mode: systems per launch for each precision")
+    ap.add_argument("--krylov-onchip", type=int, default=0, choices=[0, 2],
+                    help="krylov mode: 0 the on-chip CG where it applies, 2 the kernel with "
+                         "its Krylov vectors in global memory")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="arrival window per rate (at most 2000 requests)")
@@ -299,10 +306,13 @@ def run_krylov(args):
     P = W.diff2d()
     op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
     op.set_krylov(1e-12, 1e-6, 20000)
+    ctx.set_param("krylov_onchip", args.krylov_onchip)
     peak, peak_src = hbm_peak_gbs()
     rng = np.random.default_rng(0)
     out = {}
-    for prec, nsys in (("mixed", 64), ("f64", 16)):
+    precs = args.krylov_precs.split(",")
+    nsyss = [int(v) for v in args.krylov_systems.split(",")]
+    for prec, nsys in zip(precs, nsyss):
         X = rng.standard_normal((nsys, P.n))
         for _ in range(max(1, args.warmup)):
             api.propagate(ctx, op, P.dt, 1, X, prec=prec)
@@ -319,15 +329,21 @@ def run_krylov(args):
         gbs = its * 6 * P.n * es / (ms * 1e-3) / 1e9
         out[prec] = {"systems": nsys, "cg_iterations_per_step": its / (nsys * args.steps),
                      "us_per_iteration_and_system": ms * 1e3 / its, "achieved_gbs": gbs,
-                     "frac": gbs / peak, "launches": nl}
+                     "frac": gbs / peak, "launches": nl,
+                     "kernel": "k_cg_onchip" if ctx.get_param("krylov_onchip_rows") else "k_krylov",
+                     "onchip_shape": {"rows_per_thread": ctx.get_param("krylov_onchip_rows"),
+                                      "ctas_per_cluster": ctx.get_param("krylov_onchip_cs"),
+                                      "clusters": ctx.get_param("krylov_onchip_clusters")}}
+        ctx.set_param("krylov_onchip", args.krylov_onchip)
+    head = out[precs[0]]
     line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
-            "value": out["mixed"]["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
+            "value": head["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "mode": "krylov", "steps": args.steps,
             "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "diff2d 511^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, "
                                    "one backward-Euler step per system"},
-            "roofline": {"bound": "hbm", "achieved": out["mixed"]["achieved_gbs"], "peak": peak,
-                         "unit": "GB/s", "frac": out["mixed"]["achieved_gbs"] / peak,
+            "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": peak,
+                         "unit": "GB/s", "frac": head["achieved_gbs"] / peak,
                          "peak_source": peak_src, "traffic": None,
                          "note": "Krylov vectors are L2-resident; algorithmic bytes (x, r, p "
                                  "read + written per CG iteration) over kernel time"},

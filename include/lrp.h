@@ -120,9 +120,20 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    of two up to 16; -1 selects the one-CTA kernel);
  *   "krylov_cluster": CTAs per cluster of the 2D propagator (1..16, a power
  *                    of two; default: the most CTAs in flight whose Krylov
- *                    workspaces fit in 96 MB).
+ *                    workspaces fit in 96 MB);
+ *   "krylov_onchip": 0 (default) runs the conjugate gradients of symmetric
+ *                    5-point operators with every Krylov vector on chip
+ *                    (registers and shared memory of one thread-block
+ *                    cluster per system) where the grid allows it (at most
+ *                    512 columns and 512 rows in FP32, 256 rows in FP64);
+ *                    2 always uses the kernel with its Krylov vectors in
+ *                    global memory.
  * Results do not depend on these settings beyond rounding. */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);
+/* lrp_get_param reads the parameters above and, read-only, the launch shape
+ * of the last on-chip CG launch of the context: "krylov_onchip_rows" (grid
+ * rows per thread), "krylov_onchip_cs" (CTAs per cluster) and
+ * "krylov_onchip_clusters" (clusters in flight); 0 before the first one. */
 lrp_status lrp_get_param(lrp_ctx* ctx, const char* name, int* value);
 
 /* Per-kernel timing with CUDA events recorded around every launch of the

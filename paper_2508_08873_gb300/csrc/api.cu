@@ -312,6 +312,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "queue_cluster") {
     if (value < 0 || value > 16 || (value & (value - 1))) return LRP_EINVAL;
     c->p_queue_cluster = value;
+  } else if (k == "krylov_onchip") {
+    if (value != 0 && value != 2) return LRP_EINVAL;
+    c->p_krylov_onchip = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -325,6 +328,10 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "tri_cluster") *value = c->p_tri_cluster;
   else if (k == "queue_cluster") *value = c->p_queue_cluster;
   else if (k == "krylov_cluster") *value = c->p_krylov_cluster;
+  else if (k == "krylov_onchip") *value = c->p_krylov_onchip;
+  else if (k == "krylov_onchip_rows") *value = c->oc_last[0];
+  else if (k == "krylov_onchip_cs") *value = c->oc_last[1];
+  else if (k == "krylov_onchip_clusters") *value = c->oc_last[2];
   else if (k == "orth_cluster") *value = c->p_orth_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
   else if (k == "tri_warp") *value = c->p_tri_warp;

@@ -53,6 +53,8 @@ struct Ctx {
   int p_tri_warp = 0;        // one-warp cluster kernel for FP64 small batches (0 auto, 1 off)
   int p_queue_cluster = 0;   // CTAs per cluster of the batched 2D work queue (1..16)
   int p_krylov_cluster = 0;  // CTAs per cluster of the 2D propagator (1..16)
+  int p_krylov_onchip = 0;   // on-chip CG for symmetric 2D operators: 0 auto, 2 never
+  int oc_last[3] = {0, 0, 0};  // last on-chip CG launch: rows per thread, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
@@ -109,6 +111,8 @@ struct StencilPlan {
   double dt = 0.0;
   int adjoint = 0;
   DevBuf b64, b32;
+  DevBuf oc64, oc32;   // scaled couplings and scales of the on-chip CG kernel (stencil_onchip.cu)
+  int oc_rows[2] = {0, 0};   // padded grid rows those were laid out for (FP64, FP32)
 };
 
 // Constant-coefficient (Toeplitz) data of a tridiagonal step matrix
@@ -284,6 +288,14 @@ struct KryArgs {
   int* status;                 // bit 0: cap hit, bit 1: breakdown
 };
 lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out);
+// On-chip CG (stencil_onchip.cu): symmetric operators with at most 512 grid
+// columns and 16 x 32 (FP32) or 16 x 16 (FP64) rows; every Krylov vector in
+// registers and shared memory.  base: the arguments of k_krylov (ws unused).
+// Both CG kernels stop on the residual of the diagonally scaled system,
+// ||D^1/2 (d - B x)|| <= rtol ||D^1/2 d||, D = diag(B)^-1.
+bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys);
+lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
+                                    int prec, const KryArgs& base);
 size_t krylov_queue_nvec(int bicg);
 // Device pointer of the stencil coefficients for KryArgs::B (past the pad).
 const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec);

@@ -1,9 +1,13 @@
 // Batched backward-Euler propagator for 5-point stencil operators (2D): every
 // implicit-Euler step (I + dt A) x_{j+1} = x_j + dt f(t_{j+1}) is solved by a
 // Jacobi-preconditioned Krylov method warm-started from x_j -- conjugate
-// gradients when A is symmetric, BiCGStab otherwise -- to the relative
-// residual ||d - B x|| <= rtol ||d|| (d the step's right-hand side), with an
-// iteration cap per step that raises a status instead of looping on.
+// gradients when A is symmetric, BiCGStab otherwise -- to a relative
+// residual rtol (d the step's right-hand side, D = diag(B)^-1): for CG the
+// residual of the diagonally scaled system, ||D^1/2 (d - B x)|| <= rtol
+// ||D^1/2 d||, for BiCGStab ||d - B x|| <= rtol ||d||; an iteration cap per
+// step raises a status instead of looping on.  Symmetric operators whose
+// grid fits one thread-block cluster's registers and shared memory run on
+// the on-chip CG kernel instead (stencil_onchip.cuh).
 //
 // One system (one vector of one interval) runs on one thread-block cluster:
 // the CTAs of the cluster own contiguous blocks of grid rows, the vectors live
@@ -214,15 +218,19 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
           d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
       T rk = d - stencil_apply(B, ldb, mx, k, x);
       r[k] = rk;
-      red3t[0] += d * d;
-      red3t[1] += rk * rk;
       if (a.bicg) {
+        red3t[0] += d * d;
+        red3t[1] += rk * rk;
         rh[k] = rk;
         p[k] = rk;
         red3t[2] += rk * rk;
       } else {
+        // CG stops on the residual of the diagonally scaled system:
+        // ||D^1/2 r|| <= rtol ||D^1/2 d||, with ||D^1/2 r||^2 = r.z
         const T z = rk * Bd[k];
         p[k] = z;
+        red3t[0] += d * (d * Bd[k]);
+        red3t[1] += rk * z;
         red3t[2] += rk * z;
       }
     }
@@ -245,7 +253,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
         cl_sum<T, 1>(cl, pqt, pq, sh, buf);
         if (!(pq[0] > 0.0)) { my_status |= 2; break; }
         const T alpha = (T)(rho / pq[0]);
-        T rz[2] = {T(0), T(0)};
+        T rz[1] = {T(0)};
         struct Up { T x, p, r, q, d; };
         for_points<Up>(k0, k1,
                        [&](int k) { return Up{x[k], p[k], r[k], q[k], Bd[k]}; },
@@ -254,13 +262,12 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
                          const T rk = g.r - alpha * g.q;
                          r[k] = rk;
                          rz[0] += rk * (rk * g.d);
-                         rz[1] += rk * rk;
                        });
-        double rzd[2];
-        cl_sum<T, 2>(cl, rz, rzd, sh, buf);
+        double rzd[1];
+        cl_sum<T, 1>(cl, rz, rzd, sh, buf);
         const T beta = (T)(rzd[0] / rho);
         rho = rzd[0];
-        rr = rzd[1];
+        rr = rzd[0];
         ++it;
         struct Pu { T r, d, p; };
         for_points<Pu>(k0, k1, [&](int k) { return Pu{r[k], Bd[k], p[k]}; },
@@ -458,6 +465,8 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   if (s) return s;
   const int bicg = op->symmetric ? 0 : 1;
   const int nvec = (int)krylov_queue_nvec(bicg);
+  const bool onchip = stencil_onchip_applies(c, op, prec, nsys);
+  if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
   auto kern = prec == 0 ? (void (*)(KryArgs))k_krylov<double> : (void (*)(KryArgs))k_krylov<float>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e) return cuda_err(c, e, "krylov cluster attribute");
@@ -497,7 +506,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   cfg.gridDim = dim3(nclusters * cs);
   const size_t es = prec == 0 ? 8 : 4;
   const size_t need = (size_t)nclusters * nvec * ((size_t)op->n + 2 * op->mx) * es;
-  if (op->kws.bytes < need)
+  if (!onchip && op->kws.bytes < need)
     if ((s = dev_alloc(c, op->kws, need))) return s;
   if (!op->kstat.ptr)
     if ((s = dev_alloc(c, op->kstat, 16))) return s;
@@ -520,12 +529,16 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   a.src = src;
   a.iters = reinterpret_cast<unsigned long long*>(op->kstat.ptr);
   a.status = reinterpret_cast<int*>(static_cast<char*>(op->kstat.ptr) + 8);
-  const char* fam = prec == 0 ? "propagate_f64" : "propagate_f32";
-  cudaEvent_t ev = nullptr;
-  timer_begin(c, fam, &ev);
-  e = cudaLaunchKernelEx(&cfg, kern, a);
-  timer_end(c, fam, ev);
-  if (e) return cuda_err(c, e, "k_krylov launch");
+  if (onchip) {
+    if ((s = stencil_propagate_onchip(c, op, plan, M, nsys, prec, a))) return s;
+  } else {
+    const char* fam = prec == 0 ? "propagate_f64" : "propagate_f32";
+    cudaEvent_t ev = nullptr;
+    timer_begin(c, fam, &ev);
+    e = cudaLaunchKernelEx(&cfg, kern, a);
+    timer_end(c, fam, ev);
+    if (e) return cuda_err(c, e, "k_krylov launch");
+  }
   unsigned long long hs[2] = {0, 0};
   e = cudaMemcpyAsync(hs, op->kstat.ptr, 16, cudaMemcpyDeviceToHost, c->stream);
   if (!e) e = cudaStreamSynchronize(c->stream);
