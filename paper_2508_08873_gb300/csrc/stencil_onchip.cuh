@@ -102,6 +102,7 @@ struct Smem {
   typename V2<T>::t ring[KA][PITCH];// (e^, n^) rows in flight
   T pedge[RPT][NW + 2][2];          // p of lanes 0 and 31 of warp w at [w + 1]; zero pads
   T wco[RPT][NW];                   // e^ of the column left of each warp's lane 0
+  T junk[NW][32];                   // target of the edge-table stores of lanes 1..30
   T xedge[2][PITCH], redge[2][PITCH], qedge[2][PITCH];   // first and last row
   T red[4][NW];                     // per-warp partial sums
   T part[2][4][MAXCS];              // per-CTA partials of every CTA (pushed by each CTA)
@@ -176,6 +177,13 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
   const T s_first = cfc[-PITCH].y;    // n^ of the row above ours: south coupling of row 0
   cl.sync();   // every CTA runs before remote accesses to its shared memory
 
+  // where this lane's p of row i goes in the warp-edge table: lanes 0 and 31
+  // store into the table, the others into their scratch slot (one store per
+  // lane, no divergent branch)
+  auto edge_slot = [&](int i) -> T* {
+    return lane == 0 ? &sh.pedge[i][wid + 1][0]
+                     : lane == 31 ? &sh.pedge[i][wid + 1][1] : &sh.junk[wid][lane];
+  };
   auto up_ = [&](T (*e)[PITCH]) -> T { return *cl.map_shared_rank(&e[1][col], crank - 1); };
   auto dn_ = [&](T (*e)[PITCH]) -> T { return *cl.map_shared_rank(&e[0][col], crank + 1); };
   auto issue = [&](const T2* cb, int i, int slot) {   // row i of the couplings into ring slot
@@ -252,8 +260,7 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
           red2t[1] += rk * rk;
           if (i == 0) sh.redge[0][col] = rk;
           if (i == RPT - 1) sh.redge[1][col] = rk;
-          if (lane == 0) sh.pedge[i][wid + 1][0] = rk;
-          if (lane == 31) sh.pedge[i][wid + 1][1] = rk;
+          *edge_slot(i) = rk;
           return rk;
         };
         if constexpr (QSM) {
@@ -335,6 +342,14 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
           }
           cpa_commit();
         }
+        // every ring slot has been read: the next pass's first KA rows (the
+        // couplings are constant) go in flight now, under the reductions
+        consumed(hist[0] + hist[1] + hist[2]);
+#pragma unroll
+        for (int s = 0; s < KA; ++s) {
+          issue(cfc, s, s);
+          cpa_commit();
+        }
         cl_sum<T, 1>(cl, pq, sh, buf, [&](const T (&t)[1]) {
           if (t[0] > T(0)) sh.scal[2] = sh.scal[0] / t[0];
           else sh.flag[1] = 1;
@@ -367,16 +382,10 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
         for (int i = 0; i < RPT; ++i) {
           const T pk = fma_rn(beta, p[i], r[i]);
           p[i] = pk;
-          if (lane == 0) sh.pedge[i][wid + 1][0] = pk;
-          if (lane == 31) sh.pedge[i][wid + 1][1] = pk;
+          *edge_slot(i) = pk;
         }
         if (has_up) p_up = fma_rn(beta, p_up, r_up);
         if (has_dn) p_dn = fma_rn(beta, p_dn, r_dn);
-#pragma unroll
-        for (int s = 0; s < KA; ++s) {
-          issue(cfc, s, s);
-          cpa_commit();
-        }
         __syncthreads();
       }
       if (!sh.flag[1] && sh.scal[0] > sh.scal[1]) my_status |= 1;
