@@ -57,7 +57,8 @@ def parse():
                          "host-buffer legs): the launch list of a profiler then holds the "
                          "warm-up and timed steps alone")
     ap.add_argument("--cpu-budget", type=float, default=20.0,
-                    help="seconds of oracle work for the cpu_baseline sample")
+                    help="seconds of oracle work for the cpu_baseline samples (all cores, then "
+                         "one core)")
     ap.add_argument("--mode", default="solve", choices=["solve", "serve", "krylov"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
@@ -154,51 +155,78 @@ class ClockSampler:
 # ---------------------------------------------------------------------------
 # reference arm / cpu baseline: the FP64 oracle on a bounded sample
 # ---------------------------------------------------------------------------
-def oracle_sample(P, budget_s: float):
-    """Time the oracle on a bounded sample of the workload and extrapolate to one
-    solve: the rSVD of as many intervals as fit in 70% of the budget (scaled by
-    N / intervals done) plus one Parareal iteration (N fine solves and the
-    sweep), scaled by the iteration count of the solve."""
+def oracle_sample(P, budget_s: float, threads: int = 0, iters: int = 3):
+    """Time the FP64 oracle on a bounded sample of the workload and extrapolate
+    to one solve: the rSVD of as many intervals as fit in 60% of the budget
+    (at least one), scaled by N / intervals done, plus `iters` real Parareal
+    iterations over all N intervals (coarse solvers of the sampled intervals
+    reused for the others; the N fine solves of an iteration run as one
+    batched call), scaled by the iteration count of the solve.  threads:
+    the oracle's OpenMP threads (0: all host cores)."""
     from oracle import oracle as orc
-    oop = orc.Tridiag(P.lo, P.di, P.up)
-    t0 = time.perf_counter()
-    coarse = []
-    while len(coarse) < P.N:
-        coarse.append(orc.rsvd_interval(oop, P.dt, P.M, len(coarse), P.R, P.p, P.seed))
-        if time.perf_counter() - t0 > 0.7 * budget_s:
-            break
-    nb = len(coarse)
-    t_build = (time.perf_counter() - t0) * P.N / nb
-    co = orc.Coarse([coarse[i % nb] for i in range(P.N)], P.R, P.p)
-    t1 = time.perf_counter()
-    orc.parareal(oop, P.dt, P.M, P.N, co, P.u0, K=1)
-    t_iter = time.perf_counter() - t1
-    return t_build, t_iter, nb, 1, orc.num_threads()
+    orc.set_num_threads(threads)
+    try:
+        oop = orc.Tridiag(P.lo, P.di, P.up)
+        t0 = time.perf_counter()
+        coarse = []
+        while len(coarse) < P.N:
+            coarse.append(orc.rsvd_interval(oop, P.dt, P.M, len(coarse), P.R, P.p, P.seed))
+            if time.perf_counter() - t0 > 0.6 * budget_s:
+                break
+        nb = len(coarse)
+        t_build = (time.perf_counter() - t0) * P.N / nb
+        co = orc.Coarse([coarse[i % nb] for i in range(P.N)], P.R, P.p)
+        t1 = time.perf_counter()
+        orc.parareal(oop, P.dt, P.M, P.N, co, P.u0, K=iters)
+        t_iter = (time.perf_counter() - t1) / iters
+        cores = orc.num_threads()
+    finally:
+        orc.set_num_threads(0)
+    wall = time.perf_counter() - t0
+    return {"t_build": t_build, "t_iter": t_iter, "intervals": nb, "iters": iters,
+            "cores": cores, "wall_s": wall}
+
+
+def cpu_baseline_entry(P, budget_s: float, k_iters: int, threads: int) -> dict:
+    smp = oracle_sample(P, budget_s, threads)
+    est = smp["t_build"] + smp["t_iter"] * k_iters
+    return {"value": 1.0 / est, "unit": UNIT, "cores": smp["cores"], "kind": "oracle",
+            "sample": "rSVD of %d/%d intervals scaled to %d, plus %d real Parareal iterations "
+                      "(all %d intervals) scaled to the %d of the solve: %.1f s per solve "
+                      "(%.1f s of oracle work timed)"
+                      % (smp["intervals"], P.N, P.N, smp["iters"], P.N, k_iters, est,
+                         smp["wall_s"])}
 
 
 def run_reference(args, P, k_iters: int):
+    """The reference arm: the FP64 oracle as it stands on the host cores.  Each
+    step times one bounded sample (oracle_sample, about 4 s); value = the
+    solves/s that sample extrapolates to; ms_per_step = the measured time of
+    a step's sample."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    times = []
-    info = None
+    ests, walls = [], []
+    smp = None
+    budget = min(args.cpu_budget, 4.0)
     for s in range(args.warmup + args.steps):
-        tb, ti, nb, kd, cores = oracle_sample(P, budget_s=min(args.cpu_budget, 6.0))
-        est = tb + ti * k_iters
+        smp = oracle_sample(P, budget_s=budget)
         if s >= args.warmup:
-            times.append(est)
-        info = (nb, kd, cores)
-    sec = statistics.mean(times)
+            ests.append(smp["t_build"] + smp["t_iter"] * k_iters)
+            walls.append(smp["wall_s"])
+    sec = statistics.mean(ests)
     val = 1.0 / sec
-    nb, kd, cores = info
-    sample = ("oracle rSVD of %d of %d intervals scaled to %d, plus %d Parareal iterations "
-              "scaled to the %d the solve needs" % (nb, P.N, P.N, kd, k_iters))
+    sample = ("per step: oracle rSVD of %d of %d intervals scaled to %d, plus %d real Parareal "
+              "iterations (all intervals) scaled to the %d of the solve; %.1f s per solve "
+              "extrapolated, %.2f s measured per step"
+              % (smp["intervals"], P.N, P.N, smp["iters"], k_iters, sec, statistics.mean(walls)))
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT,
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "ms_per_step": statistics.mean(walls) * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "solve_estimate_s": sec,
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": smp["cores"], "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -212,16 +240,13 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.070      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.
 FP32_PEAK_GFLOPS = 152 * 256 * 2.070    # 128 FP32 FMA/clk/SM
 
 
-def run_serve(args):
+def serve_leg(ctx, rates, seconds: float, quiet: bool = False) -> dict:
     """Requests with new sources f = sum_{i<4} a_i sin(w_i t) exp(-(x-c_i)^2/w_i^2) and new
     u0 on coarse solvers prebuilt (mixed mode) for the 1D heat (n=255, N=16, M=64) and the
     1D advection-diffusion-reaction (n=4095, N=64, M=256) operators, 50/50, tol 1e-8,
-    Poisson arrivals; latency = submit -> result on the host."""
-    import torch
+    Poisson arrivals at each offered rate for `seconds` (at most 2000 requests);
+    latency = submit -> result on the host."""
     from paper_2508_08873_gb300 import api, workloads as W
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    ctx = api.Context(local)
     probs = [W.heat1d(), W.adr1d()]
     ops = [api.Operator.tridiag(ctx, P.lo, P.di, P.up) for P in probs]
     cos = [api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed")
@@ -238,8 +263,8 @@ def run_serve(args):
         _, u0, g, c = pool[j]
         srv.wait(srv.submit(cos[j], u0, g, c, K=probs[j].N, tol=TOL), timeout=600)
     results = []
-    for rate in [float(r) for r in args.rates.split(",")]:
-        nreq = int(min(2000, max(8, rate * args.serve_seconds)))
+    for rate in rates:
+        nreq = int(min(2000, max(8, rate * seconds)))
         gaps = rng.exponential(1.0 / rate, nreq)
         tickets = []
         t0 = time.perf_counter()
@@ -261,16 +286,36 @@ def run_serve(args):
                         "achieved_per_s": nreq / span,
                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                         "p50_ms_heat1d": float(np.percentile(lat_by[0], 50)),
+                        "p99_ms_heat1d": float(np.percentile(lat_by[0], 99)),
+                        "p50_ms_adr1d": float(np.percentile(lat_by[1], 50)),
                         "p99_ms_adr1d": float(np.percentile(lat_by[1], 99))})
-        print(json.dumps(results[-1]), flush=True)
-    sat = max((r["achieved_per_s"] for r in results), default=0.0)
-    line = {"metric": "served Parareal solves/s (continuous batching)", "value": sat,
-            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "mode": "serve",
-            "config": {"workload": "serve heat1d n=255 N=16 + adr1d n=4095 N=64, 50/50, "
-                                   "tol=1e-8, Poisson arrivals, mixed coarse solvers"},
-            "rates": results, "server": srv.stats()}
-    print(json.dumps(line), flush=True)
+        if not quiet:
+            print(json.dumps(results[-1]), flush=True)
+    stats = srv.stats()
     srv.close()
+    for co in cos:
+        co.close()
+    for op in ops:
+        op.close()
+    return {"workload": "heat1d n=255 N=16 + adr1d n=4095 N=64, 50/50, tol=1e-8, Poisson "
+                        "arrivals, mixed coarse solvers prebuilt",
+            "saturation_per_s": max((r["achieved_per_s"] for r in results), default=0.0),
+            "rates": results, "server": stats}
+
+
+def run_serve(args):
+    import torch
+    from paper_2508_08873_gb300 import api
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
+    res = serve_leg(ctx, [float(r) for r in args.rates.split(",")], args.serve_seconds)
+    line = {"metric": "served Parareal solves/s (continuous batching)",
+            "value": res["saturation_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "higher_is_better": True, "mode": "serve",
+            "config": {"workload": "serve " + res["workload"]},
+            "rates": res["rates"], "server": res["server"]}
+    print(json.dumps(line), flush=True)
 
 
 HBM_PEAK_GBS_FALLBACK = 6800.0
@@ -291,64 +336,125 @@ def hbm_peak_gbs():
     return HBM_PEAK_GBS_FALLBACK, "fallback"
 
 
-def run_krylov(args):
+# DRAM bytes of one on-chip CG launch on diff2d 511^2 (16 FP32 systems, one
+# step, 788 CG iterations each), from one ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum: 38.77 + 1.02 MB): the coefficients' and vectors'
+# first reads and the results' writes; the Krylov vectors stay on chip.
+ONCHIP_DRAM_BYTES_PER_SYSTEM = (38.77e6 + 1.02e6) / 16
+
+
+def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0) -> dict:
     """The 2D fine propagator's bandwidth (the 'HBM GB/s frac' part of the
     metric): diff2d (511^2, kappa checkerboard, dt = 1/4096), Jacobi-PCG per
-    backward-Euler step, FP32 sketch propagations (rtol 1e-6, 64 vectors, one
-    step) and FP64 fine propagations (rtol 1e-12, 16 vectors, one step).
-    Algorithmic traffic of a CG iteration: x, r, p read and written (6 words
-    per grid point); achieved = that x iterations / kernel time."""
-    import torch
+    backward-Euler step, FP32 sketch propagations (rtol 1e-6) and FP64 fine
+    propagations (rtol 1e-12), one step per system.  Algorithmic traffic of a
+    CG iteration: x, r, p read and written (6 words per grid point);
+    achieved = that x iterations / kernel time (CUDA events on the library's
+    stream)."""
     from paper_2508_08873_gb300 import api, workloads as W
-    rank, world, local = dist_env()
-    torch.cuda.set_device(local)
-    ctx = api.Context(local)
     P = W.diff2d()
     op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
     op.set_krylov(1e-12, 1e-6, 20000)
-    ctx.set_param("krylov_onchip", args.krylov_onchip)
+    ctx.set_param("krylov_onchip", onchip)
     peak, peak_src = hbm_peak_gbs()
     rng = np.random.default_rng(0)
     out = {}
+    try:
+        for prec, nsys in zip(precs, nsyss):
+            X = rng.standard_normal((nsys, P.n))
+            for _ in range(max(1, warmup)):
+                api.propagate(ctx, op, P.dt, 1, X, prec=prec)
+            fam = "propagate_f64" if prec == "f64" else "propagate_f32"
+            it0 = op.krylov_iterations()
+            ctx.set_kernel_timing(True)
+            ctx.reset_kernel_time()
+            for _ in range(steps):
+                api.propagate(ctx, op, P.dt, 1, X, prec=prec)
+            nl, ms = ctx.kernel_time(fam)
+            ctx.set_kernel_timing(False)
+            its = op.krylov_iterations() - it0
+            es = 8 if prec == "f64" else 4
+            gbs = its * 6 * P.n * es / (ms * 1e-3) / 1e9
+            onchip_used = ctx.get_param("krylov_onchip_rows") > 0
+            key = "f64" if prec == "f64" else "f32"
+            out[key] = {"systems": nsys, "cg_iterations_per_step": its / (nsys * steps),
+                        "us_per_iteration_and_system": ms * 1e3 / its, "achieved_gbs": gbs,
+                        "peak_gbs": peak, "frac": gbs / peak, "launches": nl,
+                        "rtol": 1e-12 if prec == "f64" else 1e-6,
+                        "kernel": "k_cg_onchip" if onchip_used else "k_krylov",
+                        "dram_traffic_per_launch": ONCHIP_DRAM_BYTES_PER_SYSTEM * nsys
+                        if onchip_used and key == "f32" else None,
+                        "onchip_shape": {"rows_per_cta": ctx.get_param("krylov_onchip_rows"),
+                                         "ctas_per_cluster": ctx.get_param("krylov_onchip_cs"),
+                                         "clusters": ctx.get_param("krylov_onchip_clusters")}}
+    finally:
+        ctx.set_param("krylov_onchip", 0)
+        op.close()
+    return {"workload": "diff2d 511^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, one "
+                        "backward-Euler step per system",
+            "peak_source": peak_src, "algorithmic_bytes": "6 words per grid point and CG "
+                                                          "iteration (x, r, p read + written)",
+            **out}
+
+
+def run_krylov(args):
+    import torch
+    from paper_2508_08873_gb300 import api
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
     precs = args.krylov_precs.split(",")
     nsyss = [int(v) for v in args.krylov_systems.split(",")]
-    for prec, nsys in zip(precs, nsyss):
-        X = rng.standard_normal((nsys, P.n))
-        for _ in range(max(1, args.warmup)):
-            api.propagate(ctx, op, P.dt, 1, X, prec=prec)
-        fam = "propagate_f64" if prec == "f64" else "propagate_f32"
-        it0 = op.krylov_iterations()
-        ctx.set_kernel_timing(True)
-        ctx.reset_kernel_time()
-        for _ in range(args.steps):
-            api.propagate(ctx, op, P.dt, 1, X, prec=prec)
-        nl, ms = ctx.kernel_time(fam)
-        ctx.set_kernel_timing(False)
-        its = op.krylov_iterations() - it0
-        es = 8 if prec == "f64" else 4
-        gbs = its * 6 * P.n * es / (ms * 1e-3) / 1e9
-        out[prec] = {"systems": nsys, "cg_iterations_per_step": its / (nsys * args.steps),
-                     "us_per_iteration_and_system": ms * 1e3 / its, "achieved_gbs": gbs,
-                     "frac": gbs / peak, "launches": nl,
-                     "kernel": "k_cg_onchip" if ctx.get_param("krylov_onchip_rows") else "k_krylov",
-                     "onchip_shape": {"rows_per_thread": ctx.get_param("krylov_onchip_rows"),
-                                      "ctas_per_cluster": ctx.get_param("krylov_onchip_cs"),
-                                      "clusters": ctx.get_param("krylov_onchip_clusters")}}
-        ctx.set_param("krylov_onchip", args.krylov_onchip)
-    head = out[precs[0]]
+    res = krylov_leg(ctx, precs, nsyss, args.steps, args.warmup, args.krylov_onchip)
+    head = res["f64" if precs[0] == "f64" else "f32"]
     line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
             "value": head["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
             "higher_is_better": True, "mode": "krylov", "steps": args.steps,
-            "warmup": args.warmup, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "diff2d 511^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, "
-                                   "one backward-Euler step per system"},
-            "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"], "peak": peak,
-                         "unit": "GB/s", "frac": head["achieved_gbs"] / peak,
-                         "peak_source": peak_src, "traffic": None,
-                         "note": "Krylov vectors are L2-resident; algorithmic bytes (x, r, p "
-                                 "read + written per CG iteration) over kernel time"},
-            "precisions": out}
+            "warmup": args.warmup, "dtype": "f64" if precs[0] == "f64" else "f32",
+            "data": "synthetic", "config": {"workload": res["workload"]},
+            "roofline": {"bound": "hbm", "achieved": head["achieved_gbs"],
+                         "peak": head["peak_gbs"], "unit": "GB/s", "frac": head["frac"],
+                         "peak_source": res["peak_source"],
+                         "traffic": head["dram_traffic_per_launch"],
+                         "note": "algorithmic bytes (x, r, p read + written per CG iteration) "
+                                 "over kernel time; the on-chip kernel keeps the Krylov vectors "
+                                 "in registers and shared memory"},
+            "precisions": res}
     print(json.dumps(line), flush=True)
+
+
+def all_fp64_leg(args, ctx, op, P, stream, flush) -> dict:
+    """The same step (build + solve to tol 1e-8) with every stage in FP64 (the
+    plain all-FP64 form the mixed one is compared with), device-timed like the
+    headline, L2 flushed between steps."""
+    import torch
+    from paper_2508_08873_gb300 import api
+    dev = flush.device
+    u0 = torch.tensor(P.u0, dtype=torch.float64, device=dev)
+    out = torch.empty((P.N + 1, P.n), dtype=torch.float64, device=dev)
+
+    def step():
+        co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+        _, info = api.parareal_solve(ctx, co, u0, K=P.N, tol=TOL, out=out, bounds=False)
+        co.close()
+        return info
+    step()
+    nsteps = max(3, args.steps // 3)
+    ms = []
+    for _ in range(nsteps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        info = step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return {"solves_per_s": 1000.0 / statistics.mean(ms), "ms_per_step": statistics.mean(ms),
+            "steps": nsteps, "iterations": info["k_done"], "rel_err_vs_oracle": None,
+            "note": "FP64 sketches, orthonormalisation, small SVD, coarse applies and fine "
+                    "solves; same workload and tolerance as the headline", "out": out}
 
 
 def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
@@ -546,6 +652,9 @@ def main():
         extras = None
     else:
         extras = run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world)
+        extras["all_fp64"] = all_fp64_leg(args, ctx, op, P, stream, flush)
+        extras["krylov_hbm_frac"] = krylov_leg(ctx, ["mixed", "f64"], [64, 16], 3, 1)
+        extras["serve"] = serve_leg(ctx, [10.0, 30.0, 100.0], 3.0, quiet=True)
     # ---- accuracy of the timed solve vs the oracle's sequential fine solution -
     err = None
     if rank == 0:
@@ -557,6 +666,8 @@ def main():
                 extras.pop("cls_out").cpu().numpy(), ref)
             extras["two_sided_sketch"]["rel_err_vs_oracle"] = orc.rel_err(
                 extras.pop("ts_out").cpu().numpy(), ref)
+            extras["all_fp64"]["rel_err_vs_oracle"] = orc.rel_err(
+                extras["all_fp64"].pop("out").cpu().numpy(), ref)
     # ---- roofline of the dominant kernel ---------------------------------------
     fam = max(("propagate_f64", "propagate_f32"), key=lambda f: kern[f][1])
     nl, tot = kern[fam]
@@ -593,11 +704,8 @@ def main():
     kernels = {f: {"launches": v[0], "ms_total": v[1]} for f, v in kern.items()}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        tb, ti, nb, kd, cores = oracle_sample(P, args.cpu_budget)
-        est = tb + ti * K_ITERS_REF
-        cpu = {"value": 1.0 / est, "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": "rSVD of %d/%d intervals + %d of %d Parareal iterations, "
-                         "extrapolated to one solve (%.1f s)" % (nb, P.N, kd, K_ITERS_REF, est)}
+        cpu = cpu_baseline_entry(P, 0.4 * args.cpu_budget, K_ITERS_REF, 0)
+        cpu["one_core"] = cpu_baseline_entry(P, 0.6 * args.cpu_budget, K_ITERS_REF, 1)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,

@@ -62,6 +62,8 @@ def lib():
         L.orc_jacobi_svd.restype = i
         L.orc_jacobi_svd.argtypes = [i, i, P, P, P, P]
         L.orc_num_threads.restype = i
+        L.orc_set_num_threads.restype = None
+        L.orc_set_num_threads.argtypes = [i]
         _lib = L
     return _lib
 
@@ -76,6 +78,12 @@ def _f64(a) -> np.ndarray:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the C primitives' loops over independent vectors (n <= 0:
+    all host cores).  Results do not depend on it."""
+    lib().orc_set_num_threads(int(n))
 
 
 # ----------------------------------------------------------------------------
@@ -259,6 +267,16 @@ def fine_solve(op, dt, M, v, i, g=None, c=None) -> np.ndarray:
     if g is None:
         return propagate(op, dt, M, v)
     return propagate(op, dt, M, v, g=g, cvals=interval_cvals(c, i, M))
+
+
+def fine_solve_all(op, dt, M, V, g=None, c=None) -> np.ndarray:
+    """F_i V[i] for every interval i = 0..N-1 at once (one call over the N
+    independent propagations, which the C primitives run in parallel); row
+    i is exactly fine_solve(op, dt, M, V[i], i, g, c)."""
+    N = V.shape[0]
+    if g is None:
+        return propagate(op, dt, M, V)
+    return propagate(op, dt, M, V, g=g, cvals=np.stack([interval_cvals(c, i, M) for i in range(N)]))
 
 
 def sequential_fine(op, dt, M, N, u0, g=None, c=None) -> np.ndarray:
@@ -514,7 +532,7 @@ def parareal(op, dt, M, N, coarse: Coarse, u0, g=None, c=None, K: Optional[int] 
     k = 0
     while k < Kmax:
         prev = iterates[-1]
-        Fprev = np.stack([fine_solve(op, dt, M, prev[i], i, g, c) for i in range(N)])
+        Fprev = fine_solve_all(op, dt, M, prev[:N], g, c)
         evals += 1
         new = np.zeros_like(prev)
         new[0] = u0
