@@ -71,6 +71,9 @@ def parse():
                     help="krylov mode: 0 the on-chip CG where it applies, 2 the kernel with "
                          "its Krylov vectors in global memory")
     ap.add_argument("--rates", default="10,30,100,300,1000")
+    ap.add_argument("--serve-targets", default="",
+                    help="serve mode: extra passes 'rate:adr1d_target_ms,...' with admission "
+                         "control on the adr1d handle")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="arrival window per rate (at most 2000 requests)")
     return ap.parse_args()
@@ -240,12 +243,15 @@ FP64_PEAK_GFLOPS = 152 * 4 * 2.070      # 152 SMs x 2 FP64 FMA/clk x 2 flop x 2.
 FP32_PEAK_GFLOPS = 152 * 256 * 2.070    # 128 FP32 FMA/clk/SM
 
 
-def serve_leg(ctx, rates, seconds: float, quiet: bool = False) -> dict:
+def serve_leg(ctx, rates, seconds: float, quiet: bool = False, targets=None) -> dict:
     """Requests with new sources f = sum_{i<4} a_i sin(w_i t) exp(-(x-c_i)^2/w_i^2) and new
     u0 on coarse solvers prebuilt (mixed mode) for the 1D heat (n=255, N=16, M=64) and the
     1D advection-diffusion-reaction (n=4095, N=64, M=256) operators, 50/50, tol 1e-8,
     Poisson arrivals at each offered rate for `seconds` (at most 2000 requests);
-    latency = submit -> result on the host."""
+    latency = submit -> result on the host.  targets: (rate, adr1d latency
+    target in ms) passes run after the plain ones, with requests turned away
+    (LRP_EBUSY) counted."""
+    from paper_2508_08873_gb300 import _native
     from paper_2508_08873_gb300 import api, workloads as W
     probs = [W.heat1d(), W.adr1d()]
     ops = [api.Operator.tridiag(ctx, P.lo, P.di, P.up) for P in probs]
@@ -263,10 +269,13 @@ def serve_leg(ctx, rates, seconds: float, quiet: bool = False) -> dict:
         _, u0, g, c = pool[j]
         srv.wait(srv.submit(cos[j], u0, g, c, K=probs[j].N, tol=TOL), timeout=600)
     results = []
-    for rate in rates:
+    passes = [(float(r), None) for r in rates] + [(float(r), float(t)) for r, t in (targets or [])]
+    for rate, target in passes:
+        srv.set_latency_target(cos[1], target or 0.0)
         nreq = int(min(2000, max(8, rate * seconds)))
         gaps = rng.exponential(1.0 / rate, nreq)
         tickets = []
+        rejected = [0, 0]
         t0 = time.perf_counter()
         t_next = t0
         for i in range(nreq):
@@ -274,7 +283,12 @@ def serve_leg(ctx, rates, seconds: float, quiet: bool = False) -> dict:
             while time.perf_counter() < t_next:
                 time.sleep(min(0.0005, max(0.0, t_next - time.perf_counter())))
             j, u0, g, c = pool[i % len(pool)]
-            tickets.append((j, srv.submit(cos[j], u0, g, c, K=probs[j].N, tol=TOL)))
+            try:
+                tickets.append((j, srv.submit(cos[j], u0, g, c, K=probs[j].N, tol=TOL)))
+            except _native.LrpError as e:
+                if e.status != _native.LRP_EBUSY:
+                    raise
+                rejected[j] += 1
         lat = []
         lat_by = {0: [], 1: []}
         for j, t in tickets:
@@ -282,15 +296,19 @@ def serve_leg(ctx, rates, seconds: float, quiet: bool = False) -> dict:
             lat.append(info["latency_ms"])
             lat_by[j].append(info["latency_ms"])
         span = time.perf_counter() - t0
+
+        def pct(v, q):
+            return float(np.percentile(v, q)) if v else None
         results.append({"offered_per_s": rate, "requests": nreq,
-                        "achieved_per_s": nreq / span,
-                        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                        "p50_ms_heat1d": float(np.percentile(lat_by[0], 50)),
-                        "p99_ms_heat1d": float(np.percentile(lat_by[0], 99)),
-                        "p50_ms_adr1d": float(np.percentile(lat_by[1], 50)),
-                        "p99_ms_adr1d": float(np.percentile(lat_by[1], 99))})
+                        "adr1d_latency_target_ms": target,
+                        "rejected_busy": {"heat1d": rejected[0], "adr1d": rejected[1]},
+                        "achieved_per_s": len(tickets) / span,
+                        "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99),
+                        "p50_ms_heat1d": pct(lat_by[0], 50), "p99_ms_heat1d": pct(lat_by[0], 99),
+                        "p50_ms_adr1d": pct(lat_by[1], 50), "p99_ms_adr1d": pct(lat_by[1], 99)})
         if not quiet:
             print(json.dumps(results[-1]), flush=True)
+    srv.set_latency_target(cos[1], 0.0)
     stats = srv.stats()
     srv.close()
     for co in cos:
@@ -309,7 +327,9 @@ def run_serve(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     ctx = api.Context(local)
-    res = serve_leg(ctx, [float(r) for r in args.rates.split(",")], args.serve_seconds)
+    tg = [tuple(float(x) for x in v.split(":")) for v in args.serve_targets.split(",") if v]
+    res = serve_leg(ctx, [float(r) for r in args.rates.split(",")], args.serve_seconds,
+                    targets=tg)
     line = {"metric": "served Parareal solves/s (continuous batching)",
             "value": res["saturation_per_s"], "unit": "solves/s", "n_gpus": 1,
             "higher_is_better": True, "mode": "serve",
@@ -654,7 +674,8 @@ def main():
         extras = run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world)
         extras["all_fp64"] = all_fp64_leg(args, ctx, op, P, stream, flush)
         extras["krylov_hbm_frac"] = krylov_leg(ctx, ["mixed", "f64"], [64, 16], 3, 1)
-        extras["serve"] = serve_leg(ctx, [10.0, 30.0, 100.0], 3.0, quiet=True)
+        extras["serve"] = serve_leg(ctx, [10.0, 30.0, 100.0], 3.0, quiet=True,
+                                    targets=[(100.0, 1000.0)])
     # ---- accuracy of the timed solve vs the oracle's sequential fine solution -
     err = None
     if rank == 0:

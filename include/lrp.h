@@ -370,11 +370,15 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* ctx, int count, lrp_coarse* const* 
 
 /* The coarse solvers depend on the operator and the time grid only (Sec. 2.1,
  * Remark rem:affine_g_n), so built handles serve a stream of solves with new
- * u0 and new sources.  A server owns a worker thread and its own context on
- * the device of `ctx`.  Requests are admitted into slots (device memory for
- * the iterate, F outputs, b_i and the source of one request; at most
- * max_slots per coarse handle and as many as half the free HBM -- and the
- * budget, if nonzero -- allow); waiting requests stay queued.  Each tick runs
+ * u0 and new sources.  A server works on the device of `ctx`; the requests
+ * of each coarse handle form a group with its own worker thread and its own
+ * stream, whose priority is higher the cheaper the handle's fine solves are
+ * (n N M row-steps: the highest up to 1e5, one level lower per factor of
+ * ten), so that short requests do not wait behind long ones of another
+ * handle.  Requests are admitted into slots (device memory for the iterate,
+ * F outputs, b_i and the source of one request; at most max_slots per
+ * coarse handle and as many as half the free HBM -- and the budget, if
+ * nonzero -- allow); waiting requests stay queued.  Each tick of a group runs
  * one Parareal iteration for every admitted request: the fine solves of all
  * their unconverged intervals in one launch and all their coarse sweeps in
  * one batched launch; requests arriving meanwhile join at the next tick.
@@ -401,8 +405,10 @@ lrp_status lrp_server_create(lrp_ctx* ctx, int max_slots, int max_terms,
  * the server.  Coarse handles in use must outlive the server. */
 void lrp_server_destroy(lrp_server* srv);
 /* Queue a solve with coarse solvers `co` (same arguments as
- * lrp_parareal_solve; host pointers; copied before the call returns).
- * Returns LRP_EBUSY when the queue is full. */
+ * lrp_parareal_solve; host pointers; copied before the call returns).  The
+ * first request of a handle creates its group (LRP_ENOMEM when not one slot
+ * fits).  Returns LRP_EBUSY when the queue is full, or when the handle has a
+ * latency target and the request's estimated latency exceeds it. */
 lrp_status lrp_server_submit(lrp_server* srv, const lrp_coarse* co, const double* u0, int Q,
                              const double* g, const double* c, int K_max, double tol,
                              uint64_t* ticket);
@@ -415,6 +421,18 @@ lrp_status lrp_server_poll(lrp_server* srv, uint64_t ticket, double* u_out,
 lrp_status lrp_server_wait(lrp_server* srv, uint64_t ticket, double timeout_s, double* u_out,
                            lrp_request_info* info);
 lrp_status lrp_server_stats_get(lrp_server* srv, lrp_server_stats* stats);
+/* Admission control: requests on `co` whose estimated latency (submit ->
+ * result) exceeds target_ms are turned away with LRP_EBUSY (0: no target,
+ * the default).  Estimate, with A the requests active or queued on `co`
+ * plus the new one: (ticks a request spends in a slot) x (tick time with
+ * min(A, slots) requests active) x ceil(A / slots), the first an average
+ * over finished requests, the second a line in the number of active
+ * requests fitted to the group's ticks with exponential forgetting; while
+ * the group has finished no request the estimate is 0 and requests are
+ * admitted. */
+lrp_status lrp_server_set_latency_target(lrp_server* srv, const lrp_coarse* co, double target_ms);
+/* The current latency estimate (ms) of a request on `co` (0 without history). */
+lrp_status lrp_server_estimate(lrp_server* srv, const lrp_coarse* co, double* latency_ms);
 
 #ifdef __cplusplus
 }

@@ -117,6 +117,8 @@ SIGNATURES = [
     ("lrp_server_poll", _I, [_P, ctypes.c_uint64, _P, ctypes.POINTER(RequestInfo)]),
     ("lrp_server_wait", _I, [_P, ctypes.c_uint64, _D, _P, ctypes.POINTER(RequestInfo)]),
     ("lrp_server_stats_get", _I, [_P, ctypes.POINTER(ServerStats)]),
+    ("lrp_server_set_latency_target", _I, [_P, _P, ctypes.c_double]),
+    ("lrp_server_estimate", _I, [_P, _P, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 

@@ -440,6 +440,16 @@ class Server:
             raise nat.LrpError(st, "served request failed")
         return u, self._info(inf, st)
 
+    def set_latency_target(self, co: Coarse, target_ms: float):
+        """Turn away (LrpError LRP_EBUSY at submit) requests on co whose estimated
+        latency exceeds target_ms (0: no target)."""
+        check(self.lib.lrp_server_set_latency_target(self.h, co.h, float(target_ms)))
+
+    def estimate_ms(self, co: Coarse) -> float:
+        v = ctypes.c_double()
+        check(self.lib.lrp_server_estimate(self.h, co.h, ctypes.byref(v)))
+        return v.value
+
     def stats(self) -> dict:
         s = nat.ServerStats()
         check(self.lib.lrp_server_stats_get(self.h, ctypes.byref(s)))

@@ -207,6 +207,23 @@ static lrp_status device_view(Ctx* c, const void* src, size_t bytes, DevView& v)
 // ===========================================================================
 // context
 // ===========================================================================
+namespace lrp {
+Ctx* ctx_create(int device, size_t hbm_budget_bytes, int priority) {
+  if (cudaSetDevice(device)) { cudaGetLastError(); return nullptr; }
+  auto* c = new lrp_ctx();
+  c->device = device;
+  c->budget = hbm_budget_bytes;
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (cudaStreamCreateWithPriority(&c->own_stream, cudaStreamNonBlocking, priority)) {
+    cudaGetLastError();
+    delete c;
+    return nullptr;
+  }
+  c->stream = c->own_stream;
+  return c;
+}
+}  // namespace lrp
+
 extern "C" {
 
 const char* lrp_status_string(lrp_status s) {

@@ -77,6 +77,9 @@ struct Ctx {
 };
 void ctx_retain(Ctx* c);
 void ctx_release(Ctx* c);
+// A context whose own stream has the given CUDA stream priority (lower
+// numbers run first); nullptr on failure.  Released with ctx_release.
+Ctx* ctx_create(int device, size_t hbm_budget_bytes, int priority);
 
 // Per-(dt, direction) factorisation of B = I + dt*A (or its transpose) for the
 // partitioned tridiagonal solve: P chunks of m rows, interior Thomas factors,

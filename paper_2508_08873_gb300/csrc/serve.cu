@@ -3,7 +3,15 @@
 // The low-rank coarse solvers depend only on the operator and the time grid,
 // not on the source term or the initial value (Sec. 2.1; Remark
 // rem:affine_g_n), so built coarse handles stay resident and serve a stream of
-// requests (new u0, new f).  A worker thread runs "ticks"; each tick
+// requests (new u0, new f).  Requests on one coarse handle form a group with
+// its own worker thread and its own stream, whose CUDA priority grows as the
+// group's requests get cheaper (fewer row-steps per fine solve), so that
+// short requests are not held behind long ones of another handle: the GPU
+// gives the higher-priority stream's blocks the SMs as the running blocks
+// retire.  An optional latency target per handle turns away (LRP_EBUSY)
+// requests whose estimated latency, from the group's measured service time
+// and completion rate, would exceed it.  A group's worker runs "ticks"; each
+// tick
 //   1. admits queued requests into free slots (slot memory is reserved per
 //      coarse handle up to the HBM budget; requests wait in the queue when no
 //      slot is free),
@@ -22,6 +30,7 @@
 // beyond the rounding of the launch configuration chosen for the batch size.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -50,6 +59,7 @@ struct Request {
   double tol = 0.0;
   Clock::time_point t_submit, t_admit, t_done;
   int slot = -1, k = 0;
+  unsigned long long tick_admit = 0;   // the group's tick count at admission
   bool admitted = false, done = false, fetched = false;
   int status = LRP_OK;
   double bound = 0.0, scale = 0.0;
@@ -58,43 +68,71 @@ struct Request {
 
 struct Group {
   Coarse* co = nullptr;
-  int n = 0, N = 0, M = 0, Qmax = 0, slots = 0;
+  Ctx* gctx = nullptr;                                 // own stream (priority) and memory
+  int n = 0, N = 0, M = 0, Qmax = 0, slots = 0, priority = 0;
   size_t su = 0, sF = 0, sg = 0, sc = 0, snorm = 0;   // per-slot strides (doubles)
   int rows = 0, nsl = 0;                               // coarse-sweep slices
   size_t scw = 0;                                      // per-slot sweep workspace (doubles)
   DevBuf u, F, b, g, c, norms, summ, dargs, dmap, cw, cnt;
   std::vector<int> free;
   std::vector<Request*> active;
+  // under the server mutex
+  std::deque<Request*> queue;
+  std::condition_variable cv;
+  std::thread worker;
+  double target_ms = 0.0;          // latency target (0: none)
+  // latency model: a request spends svc_ticks ticks in a slot (EWMA over
+  // finished requests, about its iteration count whatever the load); a tick
+  // with A requests active takes t0 + t1 A ms (least squares over the ticks,
+  // exponentially forgetting)
+  double svc_ticks = 0.0;
+  double sw = 0.0, sx = 0.0, sy = 0.0, sxx = 0.0, sxy = 0.0;
+  int n_est = 0;
+  unsigned long long ticks = 0, completed = 0;
+  double busy_ms = 0.0;
+  ~Group() {
+    for (DevBuf* d : {&u, &F, &b, &g, &c, &norms, &summ, &dargs, &dmap, &cw, &cnt}) d->release();
+    ctx_release(gctx);
+  }
 };
 
 }  // namespace
 
 struct lrp_server {
-  lrp_ctx* ctx = nullptr;           // the server's own context (stream, memory)
+  lrp_ctx* ctx = nullptr;           // the server's context (device)
   int max_slots = 64, Qmax = 4;
   size_t budget = 0;
-  std::thread worker;
   std::mutex mu;
-  std::condition_variable cv_work, cv_done;
-  std::deque<Request*> queue;
+  std::condition_variable cv_done;
   std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
   std::unordered_map<const Coarse*, std::unique_ptr<Group>> groups;
+  std::unordered_map<const Coarse*, double> targets;
   uint64_t next_ticket = 1;
   bool stop = false;
   int active_total = 0;
-  size_t queue_cap = 100000;
-  // statistics
-  unsigned long long completed = 0, ticks = 0, launches = 0;
-  double busy_ms = 0.0;
+  size_t queued_total = 0, queue_cap = 100000;
   lrp_status worker_error = LRP_OK;
   std::string worker_msg;
 };
 
 namespace {
 
+// CUDA stream priority of a group: the highest for requests of at most 1e5
+// row-steps per fine solve (n N M), one level lower per factor of ten.
+int group_priority(const Coarse* co) {
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest)) { cudaGetLastError(); return 0; }
+  const double cost = (double)co->op->n * co->N * co->M;
+  const int lvl = std::max(0, (int)std::floor(std::log10(std::max(cost, 1.0))) - 5);
+  return std::min(least, greatest + lvl);
+}
+
 lrp_status make_group(lrp_server* S, Coarse* co, Group** out) {
-  Ctx* c = S->ctx;
   auto G = std::make_unique<Group>();
+  G->priority = group_priority(co);
+  G->gctx = ctx_create(S->ctx->device, S->budget, G->priority);
+  if (!G->gctx) return set_err(S->ctx, LRP_ECUDA, "server group: stream creation failed");
+  Ctx* c = G->gctx;
   G->co = co;
   G->n = co->op->n;
   G->N = co->N;
@@ -117,7 +155,7 @@ lrp_status make_group(lrp_server* S, Coarse* co, Group** out) {
   size_t cap = freeb / 2;
   if (S->budget) cap = std::min(cap, S->budget);
   int slots = (int)std::min<size_t>((size_t)S->max_slots, cap / std::max<size_t>(per_slot, 1));
-  if (slots < 1) return set_err(c, LRP_ENOMEM, "no HBM for a single request slot");
+  if (slots < 1) return set_err(S->ctx, LRP_ENOMEM, "no HBM for a single request slot");
   G->slots = slots;
   lrp_status s;
   if ((s = dev_alloc(c, G->u, 8 * G->su * slots))) return s;
@@ -132,7 +170,10 @@ lrp_status make_group(lrp_server* S, Coarse* co, Group** out) {
   if ((s = dev_alloc(c, G->cw, 8 * G->scw * slots))) return s;
   if ((s = dev_alloc(c, G->cnt, 2 * sizeof(unsigned) * slots))) return s;
   cudaMemsetAsync(G->cnt.ptr, 0, G->cnt.bytes, c->stream);
+  if (cudaStreamSynchronize(c->stream)) return cuda_err(S->ctx, cudaGetLastError(), "server group");
   for (int i = slots - 1; i >= 0; --i) G->free.push_back(i);
+  auto t = S->targets.find(co);
+  if (t != S->targets.end()) G->target_ms = t->second;
   *out = G.get();
   S->groups[co] = std::move(G);
   return LRP_OK;
@@ -170,8 +211,9 @@ SweepArgs slot_args(Group* G, int slot, int first, int initial) {
 
 // One batched sweep launch for `list` (slot, first, initial) of group G.
 lrp_status batch_sweep(lrp_server* S, Group* G, const std::vector<Request*>& list, int initial) {
+  (void)S;
   if (list.empty()) return LRP_OK;
-  Ctx* c = S->ctx;
+  Ctx* c = G->gctx;
   std::vector<SweepArgs> h(list.size());
   for (size_t i = 0; i < list.size(); ++i)
     h[i] = slot_args(G, list[i]->slot, initial ? 0 : list[i]->k, initial);
@@ -182,7 +224,7 @@ lrp_status batch_sweep(lrp_server* S, Group* G, const std::vector<Request*>& lis
 }
 
 lrp_status tick_group(lrp_server* S, Group* G, std::vector<Request*>& fresh) {
-  Ctx* c = S->ctx;
+  Ctx* c = G->gctx;
   Coarse* co = G->co;
   Operator* op = const_cast<Operator*>(co->op);
   const int n = G->n, N = G->N, M = G->M;
@@ -274,104 +316,107 @@ lrp_status tick_group(lrp_server* S, Group* G, std::vector<Request*>& fresh) {
   return LRP_OK;
 }
 
-void worker_main(lrp_server* S) {
+// The worker of one group: admit from the group's queue into free slots,
+// run a tick, retire finished requests, update the estimates.
+void group_main(lrp_server* S, Group* G) {
   cudaSetDevice(S->ctx->device);
+  Ctx* c = G->gctx;
   std::vector<double> summ;
   while (true) {
-    std::unordered_map<Group*, std::vector<Request*>> fresh;
+    std::vector<Request*> fresh;
     {
       std::unique_lock<std::mutex> lk(S->mu);
-      S->cv_work.wait(lk, [&] { return S->stop || !S->queue.empty() || S->active_total > 0; });
+      G->cv.wait(lk, [&] { return S->stop || !G->queue.empty() || !G->active.empty(); });
       if (S->stop) break;
-      // admit FIFO into free slots
-      for (auto it = S->queue.begin(); it != S->queue.end();) {
-        Request* r = *it;
-        Group* G = nullptr;
-        auto gi = S->groups.find(r->co);
-        if (gi == S->groups.end()) {
-          lrp_status s = make_group(S, r->co, &G);
-          if (s) {
-            r->status = s;
-            r->done = true;
-            r->t_done = Clock::now();
-            it = S->queue.erase(it);
-            S->cv_done.notify_all();
-            continue;
-          }
-        } else {
-          G = gi->second.get();
-        }
-        if (G->free.empty()) { ++it; continue; }
+      while (!G->queue.empty() && !G->free.empty()) {
+        Request* r = G->queue.front();
+        G->queue.pop_front();
+        S->queued_total -= 1;
         r->slot = G->free.back();
         G->free.pop_back();
         r->admitted = true;
         r->t_admit = Clock::now();
+        r->tick_admit = G->ticks;
         G->active.push_back(r);
-        fresh[G].push_back(r);
+        fresh.push_back(r);
         S->active_total += 1;
-        it = S->queue.erase(it);
       }
     }
     auto t0 = Clock::now();
-    lrp_status st = LRP_OK;
-    std::vector<Group*> gl;
-    {
-      std::lock_guard<std::mutex> lk(S->mu);
-      for (auto& kv : S->groups)
-        if (!kv.second->active.empty()) gl.push_back(kv.second.get());
-    }
-    for (Group* G : gl) {
-      std::vector<Request*> fr = fresh[G];
-      if ((st = tick_group(S, G, fr))) break;
-    }
+    const double active_in_tick = (double)G->active.size();
+    lrp_status st = tick_group(S, G, fresh);
     // ---- read back bounds, retire converged requests -------------------------
-    std::vector<std::pair<Group*, Request*>> retire;
-    for (Group* G : gl) {
-      summ.resize(2 * (size_t)G->slots);
-      if (!st) {
-        cudaError_t e = cudaMemcpyAsync(summ.data(), G->summ.ptr, 16 * (size_t)G->slots,
-                                        cudaMemcpyDeviceToHost, S->ctx->stream);
-        if (!e) e = cudaStreamSynchronize(S->ctx->stream);
-        if (e) st = cuda_err(S->ctx, e, "server tick");
-      }
-      for (Request* r : G->active) {
-        if (st) { r->status = st; retire.push_back({G, r}); continue; }
-        r->bound = summ[2 * r->slot];
-        r->scale = summ[2 * r->slot + 1];
-        bool conv = r->k >= 1 && r->tol > 0 && r->bound <= r->tol * r->scale;
-        if (conv || r->k >= r->K) {
-          r->status = (r->tol > 0 && !conv) ? LRP_ENOTCONV : LRP_OK;
-          retire.push_back({G, r});
-        }
+    std::vector<Request*> retire;
+    summ.resize(2 * (size_t)G->slots);
+    if (!st) {
+      cudaError_t e = cudaMemcpyAsync(summ.data(), G->summ.ptr, 16 * (size_t)G->slots,
+                                      cudaMemcpyDeviceToHost, c->stream);
+      if (!e) e = cudaStreamSynchronize(c->stream);
+      if (e) st = cuda_err(c, e, "server tick");
+    }
+    for (Request* r : G->active) {
+      if (st) { r->status = st; retire.push_back(r); continue; }
+      r->bound = summ[2 * r->slot];
+      r->scale = summ[2 * r->slot + 1];
+      bool conv = r->k >= 1 && r->tol > 0 && r->bound <= r->tol * r->scale;
+      if (conv || r->k >= r->K) {
+        r->status = (r->tol > 0 && !conv) ? LRP_ENOTCONV : LRP_OK;
+        retire.push_back(r);
       }
     }
-    for (auto& gr : retire) {
-      Group* G = gr.first;
-      Request* r = gr.second;
+    for (Request* r : retire) {
       r->result.resize((size_t)G->su);
       if (!st)
         cudaMemcpyAsync(r->result.data(), G->u.as<double>() + (size_t)r->slot * G->su, 8 * G->su,
-                        cudaMemcpyDeviceToHost, S->ctx->stream);
+                        cudaMemcpyDeviceToHost, c->stream);
     }
-    if (!retire.empty()) cudaStreamSynchronize(S->ctx->stream);
+    if (!retire.empty()) cudaStreamSynchronize(c->stream);
     {
       std::lock_guard<std::mutex> lk(S->mu);
-      for (auto& gr : retire) {
-        Group* G = gr.first;
-        Request* r = gr.second;
+      const auto now = Clock::now();
+      const double tick = std::chrono::duration<double, std::milli>(now - t0).count();
+      for (Request* r : retire) {
         r->done = true;
-        r->t_done = Clock::now();
+        r->t_done = now;
         G->free.push_back(r->slot);
         G->active.erase(std::find(G->active.begin(), G->active.end(), r));
         S->active_total -= 1;
-        S->completed += 1;
+        G->completed += 1;
+        const double svc = (double)(G->ticks - r->tick_admit + 1);
+        G->svc_ticks = G->n_est ? 0.8 * G->svc_ticks + 0.2 * svc : svc;
+        G->n_est += 1;
       }
-      if (st) { S->worker_error = st; S->worker_msg = S->ctx->last_error; }
-      S->ticks += 1;
-      S->busy_ms += std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+      const double f = 0.97;   // forgetting factor of the tick-time fit
+      G->sw = f * G->sw + 1.0;
+      G->sx = f * G->sx + active_in_tick;
+      G->sy = f * G->sy + tick;
+      G->sxx = f * G->sxx + active_in_tick * active_in_tick;
+      G->sxy = f * G->sxy + active_in_tick * tick;
+      G->ticks += 1;
+      G->busy_ms += tick;
+      if (st && S->worker_error == LRP_OK) { S->worker_error = st; S->worker_msg = c->last_error; }
     }
-    if (!retire.empty()) S->cv_done.notify_all();
+    if (!retire.empty() || st) S->cv_done.notify_all();
   }
+}
+
+// Estimated latency (ms) of a request submitted to G now: with A = the
+// requests active or queued plus this one, the tick time at min(A, slots)
+// active requests from the fitted line, times the request's ticks in a slot,
+// times the waves of slots the queue needs; 0 while the group has no
+// finished request.
+double estimate_ms(const lrp_server* S, const Group* G) {
+  (void)S;
+  if (!G->n_est || G->sw <= 0.0) return 0.0;
+  const double mx = G->sx / G->sw, my = G->sy / G->sw;
+  const double var = G->sxx / G->sw - mx * mx;
+  double t1 = var > 1e-9 ? (G->sxy / G->sw - mx * my) / var : 0.0;
+  t1 = std::max(t1, 0.0);
+  const double t0 = std::max(my - t1 * mx, 0.0);
+  const long A = (long)G->queue.size() + (long)G->active.size() + 1;
+  const long running = std::min<long>(A, G->slots);
+  const long waves = (A + G->slots - 1) / G->slots;
+  return G->svc_ticks * (t0 + t1 * (double)running) * (double)waves;
 }
 
 }  // namespace
@@ -390,8 +435,6 @@ lrp_status lrp_server_create(lrp_ctx* ctx, int max_slots, int max_terms, size_t 
   S->max_slots = max_slots;
   S->Qmax = max_terms;
   S->budget = hbm_budget_bytes;
-  lrp_server* raw = S.get();
-  raw->worker = std::thread(worker_main, raw);
   *out = S.release();
   return LRP_OK;
 }
@@ -401,9 +444,10 @@ void lrp_server_destroy(lrp_server* S) {
   {
     std::lock_guard<std::mutex> lk(S->mu);
     S->stop = true;
+    for (auto& kv : S->groups) kv.second->cv.notify_all();
   }
-  S->cv_work.notify_all();
-  if (S->worker.joinable()) S->worker.join();
+  for (auto& kv : S->groups)
+    if (kv.second->worker.joinable()) kv.second->worker.join();
   S->groups.clear();
   lrp_ctx* c = S->ctx;
   S->reqs.clear();
@@ -434,15 +478,49 @@ lrp_status lrp_server_submit(lrp_server* S, const lrp_coarse* co, const double* 
       for (int q = 0; q < Q; ++q) r->c[j * Qm + q] = c[j * Q + q];
   }
   r->t_submit = Clock::now();
+  Group* G = nullptr;
   {
     std::lock_guard<std::mutex> lk(S->mu);
-    if (S->queue.size() >= S->queue_cap) return LRP_EBUSY;
+    if (S->stop) return LRP_EINVAL;
+    if (S->queued_total >= S->queue_cap) return LRP_EBUSY;
+    auto gi = S->groups.find(cc);
+    if (gi == S->groups.end()) {
+      cudaSetDevice(S->ctx->device);
+      lrp_status s = make_group(S, cc, &G);
+      if (s) {
+        S->groups.erase(cc);
+        return s;
+      }
+      G->worker = std::thread(group_main, S, G);
+    } else {
+      G = gi->second.get();
+    }
+    if (G->target_ms > 0.0 && estimate_ms(S, G) > G->target_ms) return LRP_EBUSY;
     r->ticket = S->next_ticket++;
     *ticket = r->ticket;
-    S->queue.push_back(r.get());
+    G->queue.push_back(r.get());
+    S->queued_total += 1;
     S->reqs[r->ticket] = std::move(r);
   }
-  S->cv_work.notify_one();
+  G->cv.notify_one();
+  return LRP_OK;
+}
+
+lrp_status lrp_server_set_latency_target(lrp_server* S, const lrp_coarse* co, double target_ms) {
+  if (!S || !co || !(target_ms >= 0.0)) return LRP_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const Coarse* cc = co;
+  S->targets[cc] = target_ms;
+  auto gi = S->groups.find(cc);
+  if (gi != S->groups.end()) gi->second->target_ms = target_ms;
+  return LRP_OK;
+}
+
+lrp_status lrp_server_estimate(lrp_server* S, const lrp_coarse* co, double* latency_ms) {
+  if (!S || !co || !latency_ms) return LRP_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto gi = S->groups.find(static_cast<const Coarse*>(co));
+  *latency_ms = gi == S->groups.end() ? 0.0 : estimate_ms(S, gi->second.get());
   return LRP_OK;
 }
 
@@ -492,13 +570,18 @@ lrp_status lrp_server_wait(lrp_server* S, uint64_t ticket, double timeout_s, dou
 lrp_status lrp_server_stats_get(lrp_server* S, lrp_server_stats* st) {
   if (!S || !st) return LRP_EINVAL;
   std::lock_guard<std::mutex> lk(S->mu);
-  st->completed = S->completed;
-  st->queued = S->queue.size();
-  st->active = S->active_total;
-  st->ticks = S->ticks;
-  st->busy_ms = S->busy_ms;
+  st->completed = 0;
+  st->ticks = 0;
+  st->busy_ms = 0.0;
   st->slots = 0;
-  for (auto& kv : S->groups) st->slots += kv.second->slots;
+  for (auto& kv : S->groups) {
+    st->completed += kv.second->completed;
+    st->ticks += kv.second->ticks;
+    st->busy_ms += kv.second->busy_ms;
+    st->slots += kv.second->slots;
+  }
+  st->queued = S->queued_total;
+  st->active = S->active_total;
   st->error = S->worker_error;
   return LRP_OK;
 }

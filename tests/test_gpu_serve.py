@@ -100,3 +100,53 @@ def test_concurrent_submitters(setup):
         x.join()
     assert len(out) == 6 and all(v[1]["converged"] for v in out.values())
     srv.close()
+
+
+def test_latency_target_turns_requests_away(setup):
+    """Admission control: with a latency target below the group's measured
+    service time a new request is turned away with LRP_EBUSY; without a
+    target (0) or with a generous one it is admitted."""
+    from paper_2508_08873_gb300 import _native
+    ctx, H, A = setup
+    P, op, co = A
+    srv = api.Server(ctx, max_slots=4, max_terms=4)
+    assert srv.estimate_ms(co) == 0.0                      # no history: admit
+    for k in range(3):
+        srv.wait(srv.submit(co, *_request(P, 300 + k), K=3, tol=0.0), timeout=120)
+    est = srv.estimate_ms(co)
+    assert est > 0.0
+    srv.set_latency_target(co, est * 1e-3)
+    with pytest.raises(_native.LrpError) as ei:
+        srv.submit(co, *_request(P, 310), K=3, tol=0.0)
+    assert ei.value.status == _native.LRP_EBUSY
+    srv.set_latency_target(co, 0.0)
+    u, info = srv.wait(srv.submit(co, *_request(P, 311), K=3, tol=0.0), timeout=120)
+    assert info["k_done"] == 3
+    srv.set_latency_target(co, 1e9)
+    u, info = srv.wait(srv.submit(co, *_request(P, 312), K=3, tol=0.0), timeout=120)
+    assert info["k_done"] == 3
+    srv.close()
+
+
+def test_short_requests_not_held_behind_long_ones(setup, orc):
+    """Each coarse handle is served by its own worker on its own stream (the
+    cheaper handle's at a higher priority): heat1d requests submitted behind
+    a burst of longer advection requests finish first and stay correct."""
+    ctx, H, A = setup
+    srv = api.Server(ctx, max_slots=64, max_terms=4)
+    Pa, opa, coa = A
+    Ph, oph, coh = H
+    long_t = [srv.submit(coa, *_request(Pa, 400 + k), K=Pa.N, tol=1e-12) for k in range(24)]
+    short = []
+    for k in range(6):
+        u0, g, c = _request(Ph, 500 + k)
+        short.append((srv.submit(coh, u0, g, c, K=Ph.N, tol=1e-10), u0, g, c))
+    short_lat = []
+    for t, u0, g, c in short:
+        u, info = srv.wait(t, timeout=120)
+        short_lat.append(info["latency_ms"])
+        direct, _ = api.parareal_solve(ctx, coh, u0, g, c, K=Ph.N, tol=1e-10)
+        assert np.linalg.norm(u - direct) <= 1e-12 * np.linalg.norm(direct)
+    long_lat = [srv.wait(t, timeout=300)[1]["latency_ms"] for t in long_t]
+    assert max(short_lat) < np.median(long_lat), (short_lat, np.median(long_lat))
+    srv.close()
