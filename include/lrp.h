@@ -213,8 +213,9 @@ lrp_status lrp_gaussian(lrp_ctx* ctx, uint64_t seed, int interval, int ncol, int
  * The first call on a device looks up that array's device address (a one-time
  * set-up per device).  Every call shares the array and overwrites the previous
  * call's factorisation: calls that overlap on the GPU (several streams or host
- * threads) race and must be serialised by the caller.  Returns LRP_EBREAKDOWN
- * on a zero pivot. */
+ * threads) race and must be serialised by the caller.  The calling thread's
+ * current device is the same after the call as before it.  Returns
+ * LRP_EBREAKDOWN on a zero pivot. */
 #define LRP_NOALLOC_MAX_N 4096
 lrp_status lrp_propagate_noalloc(int device, void* stream, int n, const double* lo,
                                  const double* di, const double* up, double dt, int M,

@@ -24,6 +24,21 @@ std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};   // device address of g_scratch, per device
 int g_sms[kMaxDevices] = {};
 
+// Makes `device` current for the call and gives the calling thread its
+// previous current device back on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) { cudaGetLastError(); prev = -1; }
+    ok = cudaSetDevice(device) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
 }  // namespace
 
 using namespace lrp;
@@ -40,7 +55,8 @@ extern "C" lrp_status lrp_propagate_noalloc(int device, void* stream, int n, con
   if (adjoint && Q > 0) return LRP_EINVAL;
   if (Q > 0 && (!g || !c)) return LRP_EINVAL;
   if (tri_raw_scratch_bytes(n) > kScratchBytes) return LRP_EINVAL;
-  if (cudaSetDevice(device) != cudaSuccess) return LRP_ECUDA;
+  DeviceGuard guard(device);
+  if (!guard.ok) return LRP_ECUDA;
   void* scratch = nullptr;
   int sms = 0;
   {
