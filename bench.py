@@ -59,7 +59,9 @@ def parse():
     ap.add_argument("--cpu-budget", type=float, default=20.0,
                     help="seconds of oracle work for the cpu_baseline samples (all cores, then "
                          "one core)")
-    ap.add_argument("--mode", default="solve", choices=["solve", "serve", "krylov"],
+    ap.add_argument("--batch-per-grid", type=int, default=2,
+                    help="batch mode: problems per grid size of the uneven 2D batch")
+    ap.add_argument("--mode", default="solve", choices=["solve", "serve", "krylov", "batch"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
                          "of the 2D Krylov fine propagator (HBM GB/s fraction)")
@@ -477,6 +479,66 @@ def all_fp64_leg(args, ctx, op, P, stream, flush) -> dict:
                     "solves; same workload and tolerance as the headline", "out": out}
 
 
+def run_batch(args):
+    """The uneven 2D batch (64 independent advection-diffusion problems
+    u_t = nu Lap u - b.grad u on grids drawn from {63^2, 127^2, 255^2, 511^2},
+    N = 32, M = 64, R = 24, p = 8, BiCGStab per step): a bounded subset with
+    args.batch_per_grid problems of every grid size, one step = the batched
+    graph-captured coarse build (mixed mode) plus the device-driven batched
+    Parareal solve to tol 1e-8; solves/s = problems per second of device time.
+    The full 64-problem batch is this subset scaled by its grid mix."""
+    import torch
+    from paper_2508_08873_gb300 import api, workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
+    stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
+    Ps = []
+    for m in W.ADV2D_GRIDS:
+        for j in range(args.batch_per_grid):
+            Ps.append(W.adv2d(len(Ps), m=m))
+    ops = [api.Operator.stencil5(ctx, P.mx, P.my, P.st) for P in Ps]
+    P0 = Ps[0]
+
+    def step():
+        ctx.set_kernel_timing(True)
+        ctx.reset_kernel_time()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e2 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        cos = api.build_coarse_batch(ctx, ops, P0.dt, P0.M, P0.N, P0.R, P0.p, 0, prec="mixed")
+        e1.record(stream)
+        outs, kd = api.parareal_solve_batch(ctx, cos, [P.u0 for P in Ps], K=P0.N, tol=TOL)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        kt = {f: ctx.kernel_time(f) for f in ("propagate_f32", "propagate_f64")}
+        ctx.set_kernel_timing(False)
+        for co in cos:
+            co.close()
+        return e0.elapsed_time(e1), e1.elapsed_time(e2), list(kd), outs, kt
+    for _ in range(max(1, args.warmup)):
+        step()
+    ms_b, ms_s = [], []
+    for _ in range(args.steps):
+        b, sv, kd, outs, kt = step()
+        ms_b.append(b)
+        ms_s.append(sv)
+    ms = statistics.mean(ms_b) + statistics.mean(ms_s)
+    line = {"metric": "uneven 2D batch: Parareal solves/s at tol 1e-8 (build + solve)",
+            "value": 1000.0 * len(Ps) / ms, "unit": "solves/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "mode": "batch",
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "adv2d uneven batch, %d problems (%d per grid of %s), N=32, M=64, "
+                                   "R=24, p=8, BiCGStab, tol=1e-8" % (len(Ps), args.batch_per_grid,
+                                                                       list(W.ADV2D_GRIDS))},
+            "build_ms": statistics.mean(ms_b), "solve_ms": statistics.mean(ms_s),
+            "iterations": [int(k) for k in kd], "grids": [P.mx for P in Ps],
+            "kernels": {f: {"launches": v[0], "ms_total": v[1]} for f, v in kt.items()}}
+    print(json.dumps(line), flush=True)
+
+
 def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
     """The legs beside the headline: solves on prebuilt coarse solvers, the
     classical comparator, the two-sided sketch build and the host-buffer (e2e)
@@ -602,6 +664,9 @@ def main():
         return
     if args.mode == "krylov":
         run_krylov(args)
+        return
+    if args.mode == "batch":
+        run_batch(args)
         return
     from paper_2508_08873_gb300 import workloads as W
     P = W.adr1d()

@@ -14,8 +14,10 @@
 // sweeps batched per grid size.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <memory>
+#include <string>
 #include <vector>
 
 #include "internal.h"
@@ -132,7 +134,7 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
   if ((s = dev_alloc(c, d_fwd, sizeof(KryArgs) * count))) return s;
   if ((s = dev_alloc(c, d_adj, sizeof(KryArgs) * count))) return s;
   if ((s = dev_alloc(c, d_cnt, 2 * sizeof(unsigned int)))) return s;
-  if ((s = dev_alloc(c, d_stat, 16))) return s;
+  if ((s = dev_alloc(c, d_stat, 16 * (size_t)count))) return s;   // per problem: iterations, status
   const int cs = c->p_queue_cluster > 0 ? c->p_queue_cluster : 4;
   const int nclu = krylov_queue_clusters(c, f32, cs);
   const size_t nvec = krylov_queue_nvec(bicg);
@@ -148,8 +150,8 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     a.rtol = f32 ? op->rtol32 : op->rtol64;
     a.max_iter = op->max_iter;
     a.nvec = (int)nvec;
-    a.iters = reinterpret_cast<unsigned long long*>(d_stat.ptr);
-    a.status = reinterpret_cast<int*>(static_cast<char*>(d_stat.ptr) + 8);
+    a.iters = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_stat.ptr) + 16 * p);
+    a.status = reinterpret_cast<int*>(static_cast<char*>(d_stat.ptr) + 16 * p + 8);
     KryArgs b = a;
     a.B = stencil_B(pf[p], op, f32);
     a.in.gen = 1; a.in.seed = seed; a.in.ncol = ell; a.in.interval0 = 0;
@@ -164,7 +166,7 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
                                   cudaMemcpyHostToDevice, c->stream);
   if (!e) e = cudaMemcpyAsync(d_fwd.ptr, hf.data(), sizeof(KryArgs) * count, cudaMemcpyHostToDevice, c->stream);
   if (!e) e = cudaMemcpyAsync(d_adj.ptr, ha.data(), sizeof(KryArgs) * count, cudaMemcpyHostToDevice, c->stream);
-  if (!e) e = cudaMemsetAsync(d_stat.ptr, 0, 16, c->stream);
+  if (!e) e = cudaMemsetAsync(d_stat.ptr, 0, d_stat.bytes, c->stream);
   if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "batch build setup");
   const double tau = f32 ? 2e-5 : 1e-13;
@@ -233,8 +235,9 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     if (r) return r;
   }
   // ---- ranks, singular values, status ------------------------------------------
-  unsigned long long hs[2] = {0, 0};
-  cudaMemcpy(hs, d_stat.ptr, 16, cudaMemcpyDeviceToHost);
+  std::vector<unsigned long long> hs(2 * (size_t)count, 0);
+  e = cudaMemcpy(hs.data(), d_stat.ptr, 16 * (size_t)count, cudaMemcpyDeviceToHost);
+  if (e) return cuda_err(c, e, "batch build status");
   for (int p = 0; p < count; ++p) {
     Coarse* q = co[p].get();
     q->rank_w.resize(N);
@@ -242,13 +245,14 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     q->sigma.resize((size_t)N * ell);
     q->Ri.resize(N);
     int svd_st = 0;
-    cudaMemcpy(q->rank_w.data(), sc[p].rw.ptr, 4 * N, cudaMemcpyDeviceToHost);
-    cudaMemcpy(q->rank_v.data(), sc[p].rv.ptr, 4 * N, cudaMemcpyDeviceToHost);
-    cudaMemcpy(q->sigma.data(), sc[p].sv.ptr, 8 * (size_t)N * ell, cudaMemcpyDeviceToHost);
-    cudaMemcpy(q->Ri.data(), sc[p].Rid.ptr, 4 * N, cudaMemcpyDeviceToHost);
     int orth_st[3] = {0, 0, 0};
-    cudaMemcpy(&svd_st, sc[p].st.ptr, 4, cudaMemcpyDeviceToHost);
-    cudaMemcpy(orth_st, sc[p].ost.ptr, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+    e = cudaMemcpy(q->rank_w.data(), sc[p].rw.ptr, 4 * N, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(q->rank_v.data(), sc[p].rv.ptr, 4 * N, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(q->sigma.data(), sc[p].sv.ptr, 8 * (size_t)N * ell, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(q->Ri.data(), sc[p].Rid.ptr, 4 * N, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(&svd_st, sc[p].st.ptr, 4, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(orth_st, sc[p].ost.ptr, 3 * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e) return cuda_err(c, e, "batch build results");
     if (orth_st[0]) return set_err(c, LRP_EBREAKDOWN, "tensor-core orthonormalisation or lift failed");
     q->orth_tc_w = orth_st[1];
     q->orth_tc_v = orth_st[2];
@@ -263,11 +267,19 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
       q->eps = std::max(q->eps, sn);
     }
   }
-  for (int p = 0; p < count; ++p) ops[p]->krylov_iters += hs[0] / count;
-  const int kst = (int)(hs[1] & 0xffffffffu);
+  int bad = -1, kbad = 0;
+  for (int p = 0; p < count; ++p) {
+    ops[p]->krylov_iters += hs[2 * p];
+    const int kst = (int)(hs[2 * p + 1] & 0xffffffffu);
+    if (kst && (bad < 0 || (kst & 2) > (kbad & 2))) { bad = p; kbad = kst; }
+  }
   for (int p = 0; p < count; ++p) out[p] = co[p].release();
-  if (kst & 2) return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in a batched build");
-  if (kst & 1) return set_err(c, LRP_ENOTCONV, "Krylov iteration cap reached in a batched build");
+  if (kbad & 2)
+    return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in a batched build (problem " +
+                                          std::to_string(bad) + ")");
+  if (kbad & 1)
+    return set_err(c, LRP_ENOTCONV, "Krylov iteration cap reached in a batched build (problem " +
+                                        std::to_string(bad) + ")");
   return LRP_OK;
 }
 
@@ -287,6 +299,7 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
   }
   const int K = std::min(K_max, N);
   lrp_status s;
+  cudaError_t e;
   std::vector<StencilPlan*> pf(count);
   for (int p = 0; p < count; ++p) {
     Coarse* q = cos[p];
@@ -300,20 +313,36 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
       if ((s = dev_alloc(c, q->ws_norm, 8 * (size_t)(3 * (N + 1) + 2)))) return s;
     }
     if ((s = coarse_sweep_workspace(c, q, sweep_rows(c)))) return s;
-    cudaMemcpyAsync(q->ws_u.ptr, u0[p], 8 * (size_t)n, cudaMemcpyDefault, c->stream);
-    cudaMemsetAsync(q->ws_b.ptr, 0, q->ws_b.bytes, c->stream);
+    e = cudaMemcpyAsync(q->ws_u.ptr, u0[p], 8 * (size_t)n, cudaMemcpyDefault, c->stream);
+    if (!e) e = cudaMemsetAsync(q->ws_b.ptr, 0, q->ws_b.bytes, c->stream);
+    if (e) return cuda_err(c, e, "batch solve input");
   }
   const int cs = c->p_queue_cluster > 0 ? c->p_queue_cluster : 4;
   const int nclu = krylov_queue_clusters(c, 0, cs);
   const size_t nvec = krylov_queue_nvec(bicg);
   const size_t ws_stride = ((nvec * maxn * 8 + 255) / 256) * 256;
-  DevBuf ws, d_items, d_probs, d_cnt, d_stat;
+  // Queue items interval-major, intervals N-1 down to 0 and within an
+  // interval the problems largest grid first: iteration k (intervals >= k)
+  // is the prefix of count (N - k) items.  Per problem: a stop flag and
+  // k_done (set by its sweeps, read by its queue items), and the Krylov
+  // iteration count and status.
+  std::vector<int> order(count);
+  for (int p = 0; p < count; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int a, int b) { return cos[a]->op->n > cos[b]->op->n; });
+  std::vector<int> items;
+  items.reserve(2 * (size_t)count * N);
+  for (int i = N - 1; i >= 0; --i)
+    for (int p : order) { items.push_back(p); items.push_back(i); }
+  DevBuf ws, d_items, d_probs, d_cnt, d_stat, d_flag, d_args;
   if ((s = dev_alloc(c, ws, ws_stride * nclu))) return s;
-  if ((s = dev_alloc(c, d_items, sizeof(int) * 2 * (size_t)count * N))) return s;
+  if ((s = dev_alloc(c, d_items, sizeof(int) * items.size()))) return s;
   if ((s = dev_alloc(c, d_probs, sizeof(KryArgs) * count))) return s;
-  if ((s = dev_alloc(c, d_cnt, sizeof(unsigned int)))) return s;
-  if ((s = dev_alloc(c, d_stat, 16))) return s;
-  cudaMemsetAsync(d_stat.ptr, 0, 16, c->stream);
+  if ((s = dev_alloc(c, d_cnt, sizeof(unsigned int) * (size_t)(K + 1)))) return s;
+  if ((s = dev_alloc(c, d_stat, 16 * (size_t)count))) return s;
+  if ((s = dev_alloc(c, d_flag, 2 * sizeof(int) * (size_t)count))) return s;
+  if ((s = dev_alloc(c, d_args, sizeof(SweepArgs) * (size_t)count * (K + 1)))) return s;
+  int* dflag = d_flag.as<int>();
   std::vector<KryArgs> hp(count);
   for (int p = 0; p < count; ++p) {
     Coarse* q = cos[p];
@@ -324,30 +353,23 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
     a.dt = q->dt; a.rtol = op->rtol64; a.max_iter = op->max_iter; a.nvec = (int)nvec;
     a.B = stencil_B(pf[p], op, 0);
     a.in.x = q->ws_u.ptr; a.in.x_f64 = 1; a.in.ldx = op->n;
+    a.in.stop = dflag + 2 * p;
     a.out.y = q->ws_F.ptr; a.out.y_f64 = 1; a.out.ldy = op->n;
-    a.iters = reinterpret_cast<unsigned long long*>(d_stat.ptr);
-    a.status = reinterpret_cast<int*>(static_cast<char*>(d_stat.ptr) + 8);
+    a.iters = reinterpret_cast<unsigned long long*>(static_cast<char*>(d_stat.ptr) + 16 * p);
+    a.status = reinterpret_cast<int*>(static_cast<char*>(d_stat.ptr) + 16 * p + 8);
     hp[p] = a;
   }
-  cudaError_t e = cudaMemcpyAsync(d_probs.ptr, hp.data(), sizeof(KryArgs) * count,
-                                  cudaMemcpyHostToDevice, c->stream);
-  if (e) return cuda_err(c, e, "batch solve setup");
-  // all problems' sweeps in one pair of launches (equal N and precision)
-  DevBuf d_args;
-  if ((s = dev_alloc(c, d_args, sizeof(SweepArgs) * count))) return s;
-  std::vector<int> kk(count, 0), active(count, 1);
-  std::vector<double> summ(2);
+  // sweep arguments: the initial sweep, then iteration k = 0..K-1
   const int rows = sweep_rows(c);
-  std::vector<SweepArgs> h;
-  auto sweeps = [&](int initial) -> lrp_status {
-    h.clear();
+  std::vector<SweepArgs> hv((size_t)count * (K + 1));
+  for (int k = -1; k < K; ++k)
     for (int p = 0; p < count; ++p) {
-      if (!initial && !active[p]) continue;
       Coarse* q = cos[p];
       const int f32 = q->prec == LRP_PREC_MIXED;
+      const bool initial = k < 0;
       SweepArgs a;
       a.N = N; a.n = q->op->n; a.R = std::max(q->R, 1);
-      a.first = initial ? 0 : kk[p];
+      a.first = initial ? 0 : k;
       a.initial = initial;
       a.u = q->ws_u.as<double>();
       a.F = initial ? q->ws_b.as<double>() : q->ws_F.as<double>();
@@ -364,49 +386,92 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
       a.nsl = (a.n + rows - 1) / rows;
       a.cw = q->ws_cw.as<double>();
       a.cnt = q->ws_cnt.as<unsigned>();
-      h.push_back(a);
+      if (!initial) {
+        a.stop = dflag + 2 * p;
+        a.k_done = dflag + 2 * p + 1;
+        a.iter = k + 1;
+        a.tol = tol;
+      }
+      hv[(size_t)(k + 1) * count + p] = a;
     }
-    if (h.empty()) return LRP_OK;
-    lrp_status r = coarse_sweep(c, h.data(), d_args.as<SweepArgs>(), (int)h.size());
-    cudaStreamSynchronize(c->stream);      // host args outlive their upload
-    return r;
-  };
-  if ((s = sweeps(1))) return s;
-  int it = 0;
-  while (it < K) {
-    std::vector<int> items;
+  e = cudaMemcpyAsync(d_items.ptr, items.data(), sizeof(int) * items.size(),
+                      cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaMemcpyAsync(d_probs.ptr, hp.data(), sizeof(KryArgs) * count,
+                              cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaMemcpyAsync(d_args.ptr, hv.data(), sizeof(SweepArgs) * hv.size(),
+                              cudaMemcpyHostToDevice, c->stream);
+  if (!e) e = cudaMemsetAsync(d_cnt.ptr, 0, d_cnt.bytes, c->stream);
+  if (!e) e = cudaMemsetAsync(d_stat.ptr, 0, d_stat.bytes, c->stream);
+  if (!e) e = cudaMemsetAsync(d_flag.ptr, 0, d_flag.bytes, c->stream);
+  if (e) return cuda_err(c, e, "batch solve setup");
+  SweepArgs* dargs = d_args.as<SweepArgs>();
+  if ((s = coarse_sweep_ex(c, hv.data(), dargs, count, 0))) return s;
+  // Iterations enqueued in batches of 1, 2, then 4 without waiting for the
+  // stopping test; the flags of batch j are read after batch j + 1 is queued.
+  int* hflag = nullptr;
+  e = cudaMallocHost(&hflag, 2 * 2 * sizeof(int) * (size_t)count);
+  if (e) return cuda_err(c, e, "pinned flags");
+  cudaEvent_t bev[2];
+  cudaEventCreateWithFlags(&bev[0], cudaEventDisableTiming);
+  cudaEventCreateWithFlags(&bev[1], cudaEventDisableTiming);
+  auto all_stopped = [&](int sl) {
     for (int p = 0; p < count; ++p)
-      if (active[p])
-        for (int i = kk[p]; i < N; ++i) { items.push_back(p); items.push_back(i); }
-    if (items.empty()) break;
-    e = cudaMemcpyAsync(d_items.ptr, items.data(), sizeof(int) * items.size(), cudaMemcpyHostToDevice,
-                        c->stream);
-    if (!e) e = cudaMemsetAsync(d_cnt.ptr, 0, sizeof(unsigned int), c->stream);
-    if (e) return cuda_err(c, e, "items");
-    if ((s = krylov_queue_launch(c, 0, d_probs.as<KryArgs>(), d_items.as<int>(), (int)items.size() / 2,
-                                 d_cnt.as<unsigned int>(), ws.ptr, ws_stride, cs, nclu)))
-      return s;
-    cudaStreamSynchronize(c->stream);
-    if ((s = sweeps(0))) return s;
-    ++it;
-    for (int p = 0; p < count; ++p) {
-      if (!active[p]) continue;
-      kk[p] += 1;
-      cudaMemcpy(summ.data(), cos[p]->ws_norm.as<double>() + 3 * (N + 1), 16, cudaMemcpyDeviceToHost);
-      bool conv = tol > 0 && summ[0] <= tol * summ[1];
-      if (conv || kk[p] >= K) active[p] = 0;
+      if (!hflag[(size_t)sl * 2 * count + 2 * p]) return false;
+    return true;
+  };
+  int k = 0, batch = 1, slot = 0, pending = 0;
+  bool done = false;
+  s = LRP_OK;
+  while (k < K && !done) {
+    const int kb = std::min(K, k + batch);
+    batch = std::min(4, 2 * batch);
+    for (; k < kb && !s; ++k) {
+      if ((s = krylov_queue_launch(c, 0, d_probs.as<KryArgs>(), d_items.as<int>(), count * (N - k),
+                                   d_cnt.as<unsigned int>() + k, ws.ptr, ws_stride, cs, nclu)))
+        break;
+      s = coarse_sweep_ex(c, &hv[(size_t)(k + 1) * count], dargs + (size_t)(k + 1) * count, count, 0);
     }
+    if (s) break;
+    e = cudaMemcpyAsync(hflag + (size_t)slot * 2 * count, dflag, 2 * sizeof(int) * count,
+                        cudaMemcpyDeviceToHost, c->stream);
+    if (!e) e = cudaEventRecord(bev[slot], c->stream);
+    if (e) { s = cuda_err(c, e, "batch solve flags"); break; }
+    if (pending) {
+      e = cudaEventSynchronize(bev[slot ^ 1]);
+      if (e) { s = cuda_err(c, e, "batch solve iteration"); break; }
+      done = tol > 0 && all_stopped(slot ^ 1);
+    }
+    pending = 1;
+    slot ^= 1;
   }
+  e = cudaStreamSynchronize(c->stream);
+  if (!s && e) s = cuda_err(c, e, "batch solve");
+  std::vector<int> fl(2 * (size_t)count, 0);
+  std::vector<unsigned long long> hs(2 * (size_t)count, 0);
+  if (!s) {
+    e = cudaMemcpy(fl.data(), dflag, 2 * sizeof(int) * count, cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(hs.data(), d_stat.ptr, 16 * (size_t)count, cudaMemcpyDeviceToHost);
+    if (e) s = cuda_err(c, e, "batch solve status");
+  }
+  cudaEventDestroy(bev[0]);
+  cudaEventDestroy(bev[1]);
+  cudaFreeHost(hflag);
+  if (s) return s;
+  int bad = -1, kbad = 0;
   for (int p = 0; p < count; ++p) {
     e = cudaMemcpy(u_out[p], cos[p]->ws_u.ptr, 8 * (size_t)(N + 1) * cos[p]->op->n, cudaMemcpyDefault);
     if (e) return cuda_err(c, e, "batch solve output");
-    if (k_done) k_done[p] = kk[p];
+    if (k_done) k_done[p] = K > 0 ? fl[2 * p + 1] : 0;
+    const_cast<Operator*>(cos[p]->op)->krylov_iters += hs[2 * p];
+    const int kst = (int)(hs[2 * p + 1] & 0xffffffffu);
+    if (kst && (bad < 0 || (kst & 2) > (kbad & 2))) { bad = p; kbad = kst; }
   }
-  unsigned long long hs[2] = {0, 0};
-  cudaMemcpy(hs, d_stat.ptr, 16, cudaMemcpyDeviceToHost);
-  const int kst = (int)(hs[1] & 0xffffffffu);
-  if (kst & 2) return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in a batched solve");
-  if (kst & 1) return set_err(c, LRP_ENOTCONV, "Krylov iteration cap reached in a batched solve");
+  if (kbad & 2)
+    return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in a batched solve (problem " +
+                                          std::to_string(bad) + ")");
+  if (kbad & 1)
+    return set_err(c, LRP_ENOTCONV, "Krylov iteration cap reached in a batched solve (problem " +
+                                        std::to_string(bad) + ")");
   return LRP_OK;
 }
 

@@ -386,7 +386,9 @@ __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
 // Many problems (different grids and operators) in one persistent launch: a
 // device work queue of items (problem, system), largest grids first; each
 // cluster takes the next item from a global counter (rank 0 draws it and
-// the other CTAs read it through distributed shared memory).
+// the other CTAs read it through distributed shared memory).  The Krylov
+// iterations and status of an item go to its own problem's counters; items
+// of a problem whose stop flag (in.stop) is set are skipped.
 template <typename T>
 __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov_queue(const KryArgs* __restrict__ probs,
                                                                const int* __restrict__ items,
@@ -403,9 +405,6 @@ __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov_queue(const KryArgs* 
   cl_map(cl, sh);
   cl.sync();   // every CTA runs before remote stores into its shared memory
   int buf = 0;
-  unsigned long long my_iters = 0;
-  int my_status = 0;
-  const KryArgs* last = nullptr;
   while (true) {
     if (crank == 0 && threadIdx.x == 0) next_item = (int)atomicAdd(counter, 1u);
     cl.sync();
@@ -413,12 +412,14 @@ __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov_queue(const KryArgs* 
     cl.sync();                        // rank 0 may overwrite next_item only after all read it
     if (it >= nitems) break;
     const KryArgs& a = probs[items[2 * it]];
-    last = &a;
+    if (a.in.stop && *a.in.stop) continue;   // the same flag for every CTA of the cluster
+    unsigned long long my_iters = 0;
+    int my_status = 0;
     krylov_system<T>(a, cl, sh, buf, items[2 * it + 1], ws, my_iters, my_status);
-  }
-  if (threadIdx.x == 0 && crank == 0 && last) {
-    if (my_iters) atomicAdd(last->iters, my_iters);
-    if (my_status) atomicOr(last->status, my_status);
+    if (threadIdx.x == 0 && crank == 0) {
+      if (my_iters) atomicAdd(a.iters, my_iters);
+      if (my_status) atomicOr(a.status, my_status);
+    }
   }
 }
 

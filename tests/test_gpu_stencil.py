@@ -156,3 +156,43 @@ def test_batched_uneven_build_and_solve(ctx, orc):
     for P, op, co, u in zip(Ps, ops, cos, outs2):
         uu, info = api.parareal_solve(ctx, co, P.u0, K=2)
         assert rel(u, uu) <= 1e-10
+
+
+def test_batched_uneven_at_config_sizes(ctx, orc):
+    """The uneven batch at its own sizes: one advection-diffusion problem on
+    each grid of {63^2, 127^2, 255^2, 511^2} (nu drawn as in the workload),
+    N = 32, M = 64, R = 24, p = 8, built in one graph-captured queue build
+    (mixed mode: FP32 sketches) and solved together with BiCGStab fine
+    solves (rtol 1e-14) through the device-driven batched solve.  At tol 1e-8
+    the 63^2 and 127^2 results are within 1e-7 of the oracle's sequential
+    fine solution, and at K = N they equal it (finite termination) to 1e-10;
+    every problem reports its own Krylov iteration count."""
+    grids = (511, 63, 255, 127)
+    Ps = [W.adv2d(i, N=32, M=64, R=24, p=8, m=m) for i, m in enumerate(grids)]
+    ops = []
+    for P in Ps:
+        op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+        op.set_krylov(1e-14, 1e-6, 20000)
+        ops.append(op)
+    P0 = Ps[0]
+    it0 = [op.krylov_iterations() for op in ops]
+    cos = api.build_coarse_batch(ctx, ops, P0.dt, P0.M, P0.N, P0.R, P0.p, 0, prec="mixed")
+    it1 = [op.krylov_iterations() for op in ops]
+    assert all(b > a for a, b in zip(it0, it1))
+    # larger grids need more Krylov iterations per system, so the counts differ
+    assert len(set(b - a for a, b in zip(it0, it1))) == len(ops)
+    refs = {}
+    for P in Ps:
+        if P.mx <= 127:
+            oop = orc.Stencil5(P.mx, P.my, P.st["C"], P.st["W"], P.st["E"], P.st["S"], P.st["N"])
+            refs[P.mx] = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+    outs, kd = api.parareal_solve_batch(ctx, cos, [P.u0 for P in Ps], K=P0.N, tol=1e-8)
+    assert all(1 <= k <= P0.N for k in kd)
+    for P, u in zip(Ps, outs):
+        if P.mx in refs:
+            assert orc.rel_err(u, refs[P.mx]) <= 1e-7, (P.mx, orc.rel_err(u, refs[P.mx]))
+    outs, kd = api.parareal_solve_batch(ctx, cos, [P.u0 for P in Ps], K=P0.N)
+    assert list(kd) == [P0.N] * len(Ps)
+    for P, u in zip(Ps, outs):
+        if P.mx in refs:
+            assert orc.rel_err(u, refs[P.mx]) <= 1e-10, (P.mx, orc.rel_err(u, refs[P.mx]))
