@@ -51,6 +51,8 @@ def lib():
         L.orc_thomas.argtypes = [i, P, P, P, P, P, P]
         L.orc_tridiag_propagate_many.restype = i
         L.orc_tridiag_propagate_many.argtypes = [i, P, P, P, d, i, i, i, P, P, L_, i, P]
+        L.orc_tridiag_td_propagate_many.restype = i
+        L.orc_tridiag_td_propagate_many.argtypes = [i, i, P, P, P, P, d, i, i, i, P, P, L_, i, P]
         L.orc_stencil_propagate_many.restype = i
         L.orc_stencil_propagate_many.argtypes = [i, i, P, P, P, P, P, d, i, i, i, P, P, L_, i, P]
         L.orc_stencil_dense.restype = i
@@ -124,6 +126,29 @@ class Tridiag:
 
 
 @dataclass
+class TridiagTD:
+    """Time-dependent tridiagonal A (Experiment 2 of Sec. 4): fine step J
+    (0-based over the whole time grid) uses A_J = A(t_{J+1}) with row i
+    lo_t[J, i] x[i-1] + di_t[J, i] x[i] + up_t[J, i] x[i+1].  The fine solver
+    of interval i runs steps i*M .. i*M + M - 1."""
+    lo_t: np.ndarray
+    di_t: np.ndarray
+    up_t: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return self.di_t.shape[1]
+
+    @property
+    def steps(self) -> int:
+        return self.di_t.shape[0]
+
+    def step(self, J: int) -> Tridiag:
+        """The time-invariant operator A_J."""
+        return Tridiag(self.lo_t[J], self.di_t[J], self.up_t[J])
+
+
+@dataclass
 class Stencil5:
     """5-point A on an mx x my grid, node p = iy*mx + ix:
     (A x)_p = C x_p + W x_{p-1} + E x_{p+1} + S x_{p-mx} + N x_{p+mx}."""
@@ -181,15 +206,20 @@ def philox_rows(seed: int, stream: int, interval: int, column: int, n: int) -> n
 # Fine propagators F_i, F_i' and F_i'^* (Sec. 4 backward Euler; Eq. (F_n_affine))
 # ----------------------------------------------------------------------------
 def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
-              g: Optional[np.ndarray] = None, cvals: Optional[np.ndarray] = None) -> np.ndarray:
+              g: Optional[np.ndarray] = None, cvals: Optional[np.ndarray] = None,
+              intervals=0) -> np.ndarray:
     """Apply M backward-Euler steps to every row of X (nvec, n).
 
     g: (Q, n) spatial source profiles or None (linear part F').
     cvals: (M, Q) shared by all rows, or (nvec, M, Q) per row: c_q at the end
-    of each step.  adjoint=True applies F'^* (no source allowed)."""
+    of each step.  adjoint=True applies F'^* (no source allowed).
+    intervals: for a time-dependent operator (TridiagTD), the interval of
+    every row (a scalar or nvec values): row v runs steps intervals[v]*M ..
+    intervals[v]*M + M - 1, and its adjoint the transposed solves of those
+    steps in reversed order."""
     X = np.array(X, dtype=np.float64, order="C", copy=True)
     if X.ndim == 1:
-        return propagate(op, dt, M, X[None, :], adjoint, g, cvals)[0]
+        return propagate(op, dt, M, X[None, :], adjoint, g, cvals, intervals)[0]
     nvec, n = X.shape
     if nvec == 0:
         return X
@@ -211,7 +241,15 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
             cstride = M * Q
         gp, cp = _p(g), _p(cvals)
     L = lib()
-    if isinstance(op, Tridiag):
+    if isinstance(op, TridiagTD):
+        j0s = np.ascontiguousarray(np.broadcast_to(np.asarray(intervals) * M, (nvec,)),
+                                   dtype=np.int32)
+        rc = L.orc_tridiag_td_propagate_many(n, op.steps, _p(_f64(op.lo_t)), _p(_f64(op.di_t)),
+                                             _p(_f64(op.up_t)), _p(j0s), float(dt), int(M),
+                                             int(adjoint), Q, gp, cp, cstride, nvec, _p(X))
+        if rc == -3:
+            raise ValueError("time-dependent operator: steps beyond its time grid")
+    elif isinstance(op, Tridiag):
         rc = L.orc_tridiag_propagate_many(n, _p(_f64(op.lo)), _p(_f64(op.di)), _p(_f64(op.up)),
                                           float(dt), int(M), int(adjoint), Q, gp, cp, cstride,
                                           nvec, _p(X))
@@ -265,8 +303,8 @@ def interval_cvals(c: Optional[np.ndarray], i: int, M: int) -> Optional[np.ndarr
 def fine_solve(op, dt, M, v, i, g=None, c=None) -> np.ndarray:
     """F_i v: the full (affine) fine solver of interval i."""
     if g is None:
-        return propagate(op, dt, M, v)
-    return propagate(op, dt, M, v, g=g, cvals=interval_cvals(c, i, M))
+        return propagate(op, dt, M, v, intervals=i)
+    return propagate(op, dt, M, v, g=g, cvals=interval_cvals(c, i, M), intervals=i)
 
 
 def fine_solve_all(op, dt, M, V, g=None, c=None) -> np.ndarray:
@@ -274,9 +312,11 @@ def fine_solve_all(op, dt, M, V, g=None, c=None) -> np.ndarray:
     independent propagations, which the C primitives run in parallel); row
     i is exactly fine_solve(op, dt, M, V[i], i, g, c)."""
     N = V.shape[0]
+    iv = np.arange(N)
     if g is None:
-        return propagate(op, dt, M, V)
-    return propagate(op, dt, M, V, g=g, cvals=np.stack([interval_cvals(c, i, M) for i in range(N)]))
+        return propagate(op, dt, M, V, intervals=iv)
+    return propagate(op, dt, M, V, g=g, cvals=np.stack([interval_cvals(c, i, M) for i in range(N)]),
+                     intervals=iv)
 
 
 def sequential_fine(op, dt, M, N, u0, g=None, c=None) -> np.ndarray:
@@ -350,9 +390,9 @@ def rsvd_interval(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval:
     n = op.n
     ell = R + p
     omega = gauss_block(seed, i, n, ell)                         # step 1
-    Y = propagate(op, dt, M, omega)                              # F' omega
+    Y = propagate(op, dt, M, omega, intervals=i)                 # F' omega
     W, _ = mgs2(Y, tau)                                          # step 2
-    Z = propagate(op, dt, M, W, adjoint=True)                    # step 3
+    Z = propagate(op, dt, M, W, adjoint=True, intervals=i)       # step 3
     Vb, _ = mgs2(Z, tau)                                         # step 4
     Mm = Z @ Vb.T                                                # step 5: M_ij = (F'^*w_i, v_j)
     if Mm.size == 0:
@@ -420,8 +460,8 @@ def rsvd_interval_indep(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval
     ell2 = 2 * ell
     omega = gauss_block(seed, i, n, ell)
     psi = gauss_block(seed, i, n, ell2, stream=STREAM_PSI)
-    Y = propagate(op, dt, M, omega)                              # rows F' omega_j
-    Z = propagate(op, dt, M, psi, adjoint=True)                  # rows F'^T psi_a
+    Y = propagate(op, dt, M, omega, intervals=i)                 # rows F' omega_j
+    Z = propagate(op, dt, M, psi, adjoint=True, intervals=i)     # rows F'^T psi_a
     Q, _ = mgs2(Y, tau)                                          # rows q_c
     k = Q.shape[0]
     if k == 0:
@@ -470,11 +510,15 @@ def exact_coarse(op, dt, M, N, R) -> Coarse:
     """Truncated SVD of the dense F' (small n only): the exact G_n of
     Eq. (spectral_G), used by tests as a comparison coarse solver."""
     n = op.n
-    Fp = propagate(op, dt, M, np.eye(n)).T           # column j = F' e_j
-    Uf, s, Vf = jacobi_svd(Fp)
-    ci = CoarseInterval(Uf[:, :R].copy(), s[:R].copy(), Vf[:, :R].copy(), s.copy(), n, n,
-                        float(s[R]) if R < n else 0.0, 0)
-    return Coarse([ci] * N, R, 0)
+
+    def one(i):
+        Fp = propagate(op, dt, M, np.eye(n), intervals=i).T      # column j = F_i' e_j
+        Uf, s, Vf = jacobi_svd(Fp)
+        return CoarseInterval(Uf[:, :R].copy(), s[:R].copy(), Vf[:, :R].copy(), s.copy(), n, n,
+                              float(s[R]) if R < n else 0.0, 0)
+    if isinstance(op, TridiagTD):
+        return Coarse([one(i) for i in range(N)], R, 0)
+    return Coarse([one(0)] * N, R, 0)
 
 
 # ----------------------------------------------------------------------------
@@ -608,6 +652,8 @@ def coarse_be(op, dt, M, v, i, g=None, c=None) -> np.ndarray:
     """G_i v for the classical coarse solver: one backward-Euler step of size
     M*dt over interval i, the source sampled at the interval's end t_{i+1}
     (the step end, as in the fine solver)."""
+    if isinstance(op, TridiagTD):
+        op = op.step(i * M + M - 1)          # A at the interval's end
     if g is None:
         return propagate(op, M * dt, 1, v)
     return propagate(op, M * dt, 1, v, g=g, cvals=interval_cvals(c, i, M)[-1:])

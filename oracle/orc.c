@@ -180,6 +180,67 @@ int orc_tridiag_propagate_many(int n, const double* lo, const double* di, const 
   return bad ? -1 : 0;
 }
 
+/* Backward-Euler propagation with a time-dependent tridiagonal operator
+ * (Experiment 2 of Sec. 4): fine step J (0-based over the whole time grid)
+ * uses A_J, whose coefficients are rows J of LO, DI, UP (each of size nJ x n,
+ * row J holding A(t_{J+1})).  The interval's first step is j0:
+ *   (I + dt*A_{j0+j}) x_{j+1} = x_j + dt * sum_q cvals[j*Q+q] g[q*n + .],
+ * j = 0..M-1, so F' = B_{j0+M-1}^{-1} ... B_{j0}^{-1} with B_J = I + dt A_J.
+ * adjoint != 0 applies F'^* = B_{j0}^{-T} ... B_{j0+M-1}^{-T}: the
+ * transposed solves in the reversed order of the steps (no source).
+ * Returns 0, -1 on a zero pivot, -3 when the steps run past row nJ - 1. */
+int orc_tridiag_td_propagate(int n, int nJ, const double* LO, const double* DI, const double* UP,
+                             int j0, double dt, int M, int adjoint, int Q, const double* g,
+                             const double* cvals, double* x) {
+  if (j0 < 0 || j0 + M > nJ) return -3;
+  double* bl = (double*)malloc(sizeof(double) * (size_t)n * 5);
+  if (!bl) return -2;
+  double* bd = bl + n;
+  double* bu = bd + n;
+  double* rhs = bu + n;
+  double* work = rhs + n;
+  int rc = 0;
+  for (int t = 0; t < M && rc == 0; ++t) {
+    const int J = adjoint ? j0 + M - 1 - t : j0 + t;
+    const double* lo = LO + (size_t)J * n;
+    const double* di = DI + (size_t)J * n;
+    const double* up = UP + (size_t)J * n;
+    for (int i = 0; i < n; ++i) {
+      double a_lo = adjoint ? (i > 0 ? up[i - 1] : 0.0) : lo[i];
+      double a_up = adjoint ? (i < n - 1 ? lo[i + 1] : 0.0) : up[i];
+      bl[i] = dt * a_lo;
+      bd[i] = 1.0 + dt * di[i];
+      bu[i] = dt * a_up;
+    }
+    for (int i = 0; i < n; ++i) {
+      double s = 0.0;
+      for (int q = 0; q < Q; ++q) s += cvals[(size_t)t * Q + q] * g[(size_t)q * n + i];
+      rhs[i] = x[i] + dt * s;
+    }
+    rc = orc_thomas(n, bl, bd, bu, rhs, x, work);
+  }
+  free(bl);
+  return rc;
+}
+
+/* orc_tridiag_td_propagate for nvec vectors, vector v starting at step
+ * j0s[v] (its interval times M); independent vectors run in parallel. */
+int orc_tridiag_td_propagate_many(int n, int nJ, const double* LO, const double* DI,
+                                  const double* UP, const int* j0s, double dt, int M, int adjoint,
+                                  int Q, const double* g, const double* cvals, long cstride,
+                                  int nvec, double* X) {
+  int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+  for (int v = 0; v < nvec; ++v) {
+    int rc = orc_tridiag_td_propagate(n, nJ, LO, DI, UP, j0s[v], dt, M, adjoint, Q, g,
+                                      cvals ? cvals + (size_t)v * cstride : NULL,
+                                      X + (size_t)v * n);
+    if (rc == -3) bad |= 2;
+    else if (rc) bad |= 1;
+  }
+  return (bad & 2) ? -3 : (bad ? -1 : 0);
+}
+
 /* ------------------------------------------------------------------------ */
 /* 5-point stencils on an mx x my grid of interior nodes, node p = iy*mx+ix. */
 /* A x at p = C[p] x_p + W[p] x_{p-1} + E[p] x_{p+1} + S[p] x_{p-mx}          */

@@ -14,7 +14,9 @@ The problems are finite-difference stand-ins for the paper's experiments
   * diff2d      u_t = div(kappa grad u) - u, kappa piecewise constant on an
                 8x8 checkerboard with values 10^U(0,2), 5-point stencil,
                 kappa evaluated at face midpoints;
-  * adv2d       u_t = nu Lap u - b.grad u, b = (-(y-1/2), x-1/2), upwind.
+  * adv2d       u_t = nu Lap u - b.grad u, b = (-(y-1/2), x-1/2), upwind;
+  * heat_td     u_t = d/dx[(1 + 0.9 sin(7 pi t + 2 pi x)) u_x] + f with Neumann
+                conditions (Experiment 2): a time-dependent tridiagonal A.
 Random problem data come from numpy's PCG64 seeded per problem; the Gaussian
 sketch vectors of the method are NOT drawn here.
 """
@@ -120,6 +122,45 @@ def adr1d(n: int = 4095, N: int = 64, M: int = 256, R: int = 16, p: int = 8, see
     rng = np.random.default_rng(data_seed)
     return Problem("adr1d", "tridiag", n, T / (N * M), M, N, R, p, seed, bumps1d(x, rng),
                    lo=lo, di=di, up=up)
+
+
+def heat_td_op(n: int, N: int, M: int, T: float = 1.0):
+    """Experiment 2's operator, -d/dx[(1 + 0.9 sin(7 pi t + 2 pi x)) du/dx] with
+    homogeneous Neumann conditions: n cells of width h = 1/n (unknowns at the
+    cell centres), the conductivity at the interior faces x = (i+1) h and at
+    the end t_{J+1} = (J+1) dt of every fine step J = 0..N*M-1 (fully implicit
+    backward Euler), no flux through the boundary faces.  Returns lo_t, di_t,
+    up_t, each (N*M, n): row J holds A(t_{J+1})."""
+    h = 1.0 / n
+    dt = T / (N * M)
+    t = fine_times(N, M, dt)
+    xf = h * np.arange(1, n)
+    kap = (1.0 + 0.9 * np.sin(7 * np.pi * t[:, None] + 2 * np.pi * xf[None, :])) / h ** 2
+    J = N * M
+    di = np.zeros((J, n))
+    di[:, :-1] += kap
+    di[:, 1:] += kap
+    lo = np.zeros((J, n))
+    lo[:, 1:] = -kap
+    up = np.zeros((J, n))
+    up[:, :-1] = -kap
+    return lo, di, up
+
+
+def heat_td(n: int = 100, N: int = 10, M: int = 10, R: int = 5, p: int = 1, seed: int = 0,
+            T: float = 1.0) -> Problem:
+    """Experiment 2 stand-in: heat equation with the space- and time-dependent
+    conductivity 1 + 0.9 sin(7 pi t + 2 pi x), Neumann conditions, n = 100
+    cells, N = 10 intervals of M = 10 steps on [0, 1] (the paper's mesh and
+    time grid), f = sin(2 pi t) exp(-100 (x-1/2)^2), u0 = x(1-x).  The
+    operator arrays (N*M, n) are in lo, di, up (kind "tridiag_td")."""
+    lo, di, up = heat_td_op(n, N, M, T)
+    x = (np.arange(n) + 0.5) / n
+    dt = T / (N * M)
+    g = np.exp(-100.0 * (x - 0.5) ** 2)[None, :]
+    c = np.sin(2 * np.pi * fine_times(N, M, dt))[:, None]
+    return Problem("heat_td", "tridiag_td", n, dt, M, N, R, p, seed, x * (1 - x),
+                   lo=lo, di=di, up=up, g=g, c=c)
 
 
 # ----------------------------------------------------------------------------
