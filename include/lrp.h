@@ -154,6 +154,18 @@ lrp_status lrp_reset_kernel_time(lrp_ctx* ctx);
  * propagator has faster kernels for that case; "tri_wtoep"). */
 lrp_status lrp_operator_tridiag(lrp_ctx* ctx, int n, const double* lo, const double* di,
                                 const double* up, lrp_operator** out);
+/* Time-dependent tridiagonal operator (Experiment 2 of Sec. 4: coefficients
+ * that vary in time, so that the fine solvers F_n of the intervals differ):
+ * lo, di, up are nJ x n (host or device), row J holding A(t_{J+1}) for fine
+ * step J = 0..nJ-1 of the whole time grid (backward Euler is fully implicit).
+ * Interval i of a coarse build or Parareal solve runs steps i M .. i M + M - 1
+ * (N M <= nJ, else LRP_EINVAL); its adjoint applies the transposed steps in
+ * reversed order.  lrp_propagate runs steps 0..M-1 on every vector.  n <= 1024
+ * (each step is solved by parallel cyclic reduction within one CTA).  The
+ * SDIRK steppers and the classical comparator take time-invariant operators
+ * only. */
+lrp_status lrp_operator_tridiag_td(lrp_ctx* ctx, int n, int nJ, const double* lo,
+                                   const double* di, const double* up, lrp_operator** out);
 /* 5-point A on an mx x my grid of interior nodes, node p = iy*mx + ix:
  * (A x)_p = C[p] x_p + W[p] x_{p-1} + E[p] x_{p+1} + S[p] x_{p-mx} + N[p] x_{p+mx};
  * coefficients that reach outside the grid are ignored (homogeneous Dirichlet). */

@@ -87,6 +87,7 @@ SIGNATURES = [
     ("lrp_kernel_time", _I, [_P, ctypes.c_char_p, _PI, _PD]),
     ("lrp_reset_kernel_time", _I, [_P]),
     ("lrp_operator_tridiag", _I, [_P, _I, _P, _P, _P, _PP]),
+    ("lrp_operator_tridiag_td", _I, [_P, _I, _I, _P, _P, _P, _PP]),
     ("lrp_operator_stencil5", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _PP]),
     ("lrp_operator_free", None, [_P]),
     ("lrp_operator_size", _I, [_P]),

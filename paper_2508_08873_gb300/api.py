@@ -101,6 +101,15 @@ class Operator:
         return cls(ctx, h, di.shape[0], "tridiag")
 
     @classmethod
+    def tridiag_td(cls, ctx: Context, lo_t, di_t, up_t) -> "Operator":
+        """Time-dependent tridiagonal operator: (nJ, n) arrays, row J = A(t_{J+1})."""
+        lo, di, up = (np.ascontiguousarray(a, dtype=np.float64) for a in (lo_t, di_t, up_t))
+        h = ctypes.c_void_p()
+        check(ctx.lib.lrp_operator_tridiag_td(ctx.h, di.shape[1], di.shape[0], ptr(lo), ptr(di),
+                                              ptr(up), ctypes.byref(h)), ctx.h)
+        return cls(ctx, h, di.shape[1], "tridiag_td")
+
+    @classmethod
     def stencil5(cls, ctx: Context, mx: int, my: int, st: dict) -> "Operator":
         arr = [np.ascontiguousarray(st[k], dtype=np.float64) for k in ("C", "W", "E", "S", "N")]
         h = ctypes.c_void_p()

@@ -501,6 +501,7 @@ StepCoef step_coefficients(int stepper) {
 
 lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src) {
+  if (op->kind == 2) return tri_td_propagate(c, op, dt, M, adjoint, nsys, prec, in, out, src);
   if (op->kind == 0 && op->stepper != 0) {
     // SDIRK fine steps: two solves with B = I + gamma dt A per step on the
     // one-CTA-per-system kernel (sources are not supported by these steppers)
@@ -744,6 +745,7 @@ lrp_status lrp_propagate(lrp_ctx* c, const lrp_operator* opc, double dt, int M, 
   in.x = xin.p;
   in.x_f64 = 1;
   in.ldx = n;
+  in.ncol = std::max(nvec, 1);   // time-dependent operators: every vector from t = 0
   PropOut o;
   o.y = dout;
   o.y_f64 = 1;
@@ -806,6 +808,8 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   Operator* op = const_cast<lrp_operator*>(opc);
   const int n = op->n;
   if (ell > n) return set_err(c, LRP_EINVAL, "rank + oversample exceeds the dimension");
+  if (op->kind == 2 && (long)N * M > op->nJ)
+    return set_err(c, LRP_EINVAL, "N * M exceeds the time grid of the operator");
   auto co = std::make_unique<lrp_coarse>();
   co->ctx = c;
   ctx_retain(c);
@@ -892,6 +896,7 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   in2.x = Y.ptr;
   in2.x_f64 = !f32;
   in2.ldx = n;
+  in2.ncol = ell;               // system s is column s % ell of interval s / ell
   PropOut o2;
   o2.y = Z.ptr;
   o2.y_f64 = !f32;
@@ -1241,6 +1246,7 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
       in.x_f64 = 1;
       in.ldx = n;
       in.stop = dflag;
+      in.interval0 = first;          // system s is interval first + s
       PropOut o;
       o.y = co->ws_F.as<double>() + (size_t)first * n;
       o.y_f64 = 1;
@@ -1300,10 +1306,13 @@ lrp_status lrp_fine_solution(lrp_ctx* c, const lrp_operator* opc, double dt, int
   DevView gv, cvv;
   if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
   if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * Q, cvv))) return s;
+  if (op->kind == 2 && (long)N * M > op->nJ)
+    return set_err(c, LRP_EINVAL, "N * M exceeds the time grid of the operator");
   for (int i = 0; i < N; ++i) {
     PropIn in;
     in.x = u.as<double>() + (size_t)i * n;
     in.ldx = n;
+    in.interval0 = i;
     PropOut o;
     o.y = u.as<double>() + (size_t)(i + 1) * n;
     o.ldy = n;
@@ -1382,6 +1391,8 @@ lrp_status lrp_parareal_solve_classical(lrp_ctx* c, const lrp_operator* opc, dou
   if (Q > 0 && (!g || !cv)) return LRP_EINVAL;
   cudaSetDevice(c->device);
   Operator* op = const_cast<lrp_operator*>(opc);
+  if (op->kind == 2)
+    return set_err(c, LRP_EINVAL, "the classical comparator takes time-invariant operators");
   const int n = op->n;
   const int K = std::min(K_max, N);
   const double DT = dt * M;

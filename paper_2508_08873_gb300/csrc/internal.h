@@ -134,8 +134,9 @@ struct ToepCoef {
 struct Operator {
   Ctx* ctx = nullptr;
   ~Operator();
-  int kind = 0;            // 0 tridiagonal, 1 5-point stencil
+  int kind = 0;            // 0 tridiagonal, 1 5-point stencil, 2 time-dependent tridiagonal
   int n = 0, mx = 0, my = 0;
+  int nJ = 0;              // kind 2: fine steps of the time grid (a64[0..2] are nJ x n)
   // tridiagonal with constant coefficients (lo[1..n-1], di, up[0..n-2] each
   // one value): tlo, tdi, tup
   bool toeplitz = false;
@@ -218,8 +219,8 @@ struct PropIn {
   int gen = 0;              // 1: generate N(0,1) entries instead of reading x
   uint64_t seed = 0;
   uint32_t stream = 0;      // Philox stream of the generated entries (0: Omega, 3: Psi)
-  int ncol = 1;
-  int interval0 = 0;        // interval of system 0 (generated input)
+  int ncol = 1;             // systems per interval (generated input; time-dependent operators)
+  int interval0 = 0;        // interval of system 0 (generated input; time-dependent operators)
   const int* stop = nullptr; // optional device flag: nonzero at launch -> the kernel does nothing
 };
 struct PropOut {
@@ -266,6 +267,12 @@ lrp_status tri_propagate_cluster(Ctx* c, ClPlan* pl, int M, int nsys, int prec, 
 // rows of the system with padding rows); tz->on = 0 otherwise.
 void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m, ToepCoef* tz,
                        int prec = 0);
+
+// Time-dependent tridiagonal operators (tridiag_td.cu): one CTA per system,
+// parallel cyclic reduction of every step's own matrix; system s runs the
+// steps of interval (map ? map[2s+1] : in.interval0 + s / in.ncol).
+lrp_status tri_td_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
+                            int prec, const PropIn& in, const PropOut& out, const PropSrc& src);
 
 // Allocation-free variant: factorisation into caller-provided scratch.
 size_t tri_raw_scratch_bytes(int n);
