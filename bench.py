@@ -61,7 +61,8 @@ def parse():
                          "one core)")
     ap.add_argument("--batch-per-grid", type=int, default=2,
                     help="batch mode: problems per grid size of the uneven 2D batch")
-    ap.add_argument("--mode", default="solve", choices=["solve", "serve", "krylov", "batch"],
+    ap.add_argument("--mode", default="solve",
+                    choices=["solve", "serve", "krylov", "batch", "cfg3"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
                          "of the 2D Krylov fine propagator (HBM GB/s fraction)")
@@ -539,6 +540,66 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cfg3(args):
+    """The 2D diffusion workload at its own size (511^2, kappa checkerboard,
+    N = 128, M = 32, R = 32, p = 10, Jacobi-PCG at rtol 1e-6 for the FP32
+    sketches and 1e-12 for the FP64 fine solves).  A full build (~10^4
+    propagations of 32 steps) and every Parareal iteration (128 FP64 fine
+    solves) take minutes, so the leg measures at full size, on the device:
+      * the CG rates of both precisions (us per iteration and system, CG
+        iterations per step) on full batches of one step;
+      * a complete build with M = 1 (all N intervals, the same sketches,
+        orthonormalisation, small SVDs and lift at n = 261121, l = 42): its
+        time less its propagation time is the dense part of the build;
+      * one Parareal iteration on that build (the coarse sweep's time);
+    and states the full-size figures they give:
+      T_build = dense + 2 N l M it32 t32,   T_iter = N M it64 t64 + sweep,
+      solves/s(k) = 1 / (T_build + k T_iter)."""
+    import torch
+    from paper_2508_08873_gb300 import api, workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
+    P = W.diff2d()
+    kr = krylov_leg(ctx, ["mixed", "f64"], [64, 128], 1, 1)
+    op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+    op.set_krylov(1e-12, 1e-6, 20000)
+    ell = P.R + P.p
+    api.Coarse(ctx, op, P.dt, 1, P.N, P.R, P.p, P.seed, prec="mixed").close()   # warm-up
+    ctx.set_kernel_timing(True)
+    ctx.reset_kernel_time()
+    t0 = time.perf_counter()
+    co = api.Coarse(ctx, op, P.dt, 1, P.N, P.R, P.p, P.seed, prec="mixed")
+    torch.cuda.synchronize()
+    t_b1 = time.perf_counter() - t0
+    kt = {f: ctx.kernel_time(f) for f in ("propagate_f32", "orth", "svd", "lift")}
+    ctx.reset_kernel_time()
+    u, info = api.parareal_solve(ctx, co, P.u0, K=1)
+    sweep = ctx.kernel_time("sweep")
+    ctx.set_kernel_timing(False)
+    dense = t_b1 - kt["propagate_f32"][1] * 1e-3
+    f32, f64 = kr["f32"], kr["f64"]
+    prop32 = 2 * P.N * ell * P.M * f32["cg_iterations_per_step"] * f32["us_per_iteration_and_system"] * 1e-6
+    t_build = dense + prop32
+    t_iter = P.N * P.M * f64["cg_iterations_per_step"] * f64["us_per_iteration_and_system"] * 1e-6 \
+        + sweep[1] * 1e-3
+    line = {"metric": "diff2d 511^2 Parareal: build and iteration times at full size (extrapolated "
+                      "from full-size measurements)",
+            "value": t_build, "unit": "s (build)", "mode": "cfg3", "n_gpus": 1,
+            "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "diff2d 511^2 kappa 8x8 checkerboard, N=128, M=32, R=32, p=10, "
+                                   "Jacobi-PCG rtol 1e-6 (FP32 sketches) / 1e-12 (FP64 fine)"},
+            "krylov": kr,
+            "build_M1_s": t_b1, "build_M1_kernels_ms": {f: v[1] for f, v in kt.items()},
+            "dense_part_s": dense, "sketch_propagation_s": prop32, "build_s": t_build,
+            "sweep_ms": sweep[1], "iteration_s": t_iter,
+            "solves_per_s": {str(k): 1.0 / (t_build + k * t_iter) for k in (1, 4, 16, P.N)},
+            "formula": "T_build = dense + 2 N l M it32 t32; T_iter = N M it64 t64 + sweep; "
+                       "solves/s(k) = 1 / (T_build + k T_iter)"}
+    co.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
     """The legs beside the headline: solves on prebuilt coarse solvers, the
     classical comparator, the two-sided sketch build and the host-buffer (e2e)
@@ -667,6 +728,9 @@ def main():
         return
     if args.mode == "batch":
         run_batch(args)
+        return
+    if args.mode == "cfg3":
+        run_cfg3(args)
         return
     from paper_2508_08873_gb300 import workloads as W
     P = W.adr1d()
