@@ -154,9 +154,11 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
     a.status = reinterpret_cast<int*>(static_cast<char*>(d_stat.ptr) + 16 * p + 8);
     KryArgs b = a;
     a.B = stencil_B(pf[p], op, f32);
+    a.Bs = stencil_Bs(pf[p], op, f32);
     a.in.gen = 1; a.in.seed = seed; a.in.ncol = ell; a.in.interval0 = 0;
     a.out.y = sc[p].Y.ptr; a.out.y_f64 = !f32; a.out.ldy = op->n;
     b.B = stencil_B(pa[p], op, f32);
+    b.Bs = stencil_Bs(pa[p], op, f32);
     b.in.x = sc[p].Y.ptr; b.in.x_f64 = !f32; b.in.ldx = op->n;
     b.out.y = sc[p].Z.ptr; b.out.y_f64 = !f32; b.out.ldy = op->n;
     hf[p] = a;
@@ -352,6 +354,7 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
     a.bicg = op->symmetric ? 0 : 1;
     a.dt = q->dt; a.rtol = op->rtol64; a.max_iter = op->max_iter; a.nvec = (int)nvec;
     a.B = stencil_B(pf[p], op, 0);
+    a.Bs = stencil_Bs(pf[p], op, 0);
     a.in.x = q->ws_u.ptr; a.in.x_f64 = 1; a.in.ldx = op->n;
     a.in.stop = dflag + 2 * p;
     a.out.y = q->ws_F.ptr; a.out.y_f64 = 1; a.out.ldy = op->n;

@@ -114,6 +114,7 @@ struct StencilPlan {
   double dt = 0.0;
   int adjoint = 0;
   DevBuf b64, b32;
+  DevBuf bs64, bs32;   // symmetric operators: the scaled matrix of CG (k_stencil_plan_scaled)
   DevBuf oc64, oc32;   // scaled couplings and scales of the on-chip CG kernel (stencil_onchip.cu)
   int oc_rows[2] = {0, 0};   // padded grid rows those were laid out for (FP64, FP32)
 };
@@ -289,6 +290,8 @@ struct KryArgs {
   int max_iter;
   const void* B;            // [6][n + 2 mx] from element 0 of array 0 (after the pad):
                             // c, w, e, s, n, dinv (type T), zero pads of mx per side
+  const void* Bs;           // CG (symmetric operators): [7][n + 2 mx], same layout: west,
+                            // east, south, north couplings of S^-1 B S^-1, 1/c, 1/sqrt(c), sqrt(c)
   void* ws;                 // per cluster slot: nvec padded vectors of n + 2 mx values
   int nvec;
   PropIn in;
@@ -309,6 +312,8 @@ lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int
 size_t krylov_queue_nvec(int bicg);
 // Device pointer of the stencil coefficients for KryArgs::B (past the pad).
 const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec);
+// The same for KryArgs::Bs (symmetric operators; nullptr otherwise).
+const void* stencil_Bs(const StencilPlan* pl, const Operator* op, int prec);
 int krylov_queue_clusters(Ctx* c, int prec, int cs);
 lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const int* d_items,
                                int nitems, unsigned int* d_counter, void* ws, size_t ws_stride,

@@ -65,6 +65,37 @@ __global__ void k_stencil_plan(int mx, int my, double dt, int adj, const double*
   }
 }
 
+// The diagonally scaled step matrix of a symmetric operator, B^ = S^-1 B S^-1
+// with S = diag(sqrt(c)), c the diagonal of B = I + dt A: [7][n + 2 mx] =
+// west, east, south, north couplings of B^ (its diagonal is 1), 1/c,
+// 1/sqrt(c), sqrt(c), with the layout and zero pads of the plan arrays.  The
+// coupling of p to q is b_pq / sqrt(c_p c_q) for both directions, so B^ is
+// symmetric bitwise when B is.
+__global__ void k_stencil_plan_scaled(int mx, int my, const double* __restrict__ b64,
+                                      double* __restrict__ s64, float* __restrict__ s32) {
+  const int n = mx * my;
+  const size_t ld = (size_t)n + 2 * mx;
+  int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= n) return;
+  const size_t q = (size_t)mx + p;
+  const double* c = b64;
+  const double cp = c[q];
+  const double w = b64[ld + q], e = b64[2 * ld + q], so = b64[3 * ld + q], no = b64[4 * ld + q];
+  const int ix = p % mx, iy = p / mx;
+  double v[7];
+  v[0] = ix > 0 ? w / sqrt(cp * c[q - 1]) : 0.0;
+  v[1] = ix < mx - 1 ? e / sqrt(cp * c[q + 1]) : 0.0;
+  v[2] = iy > 0 ? so / sqrt(cp * c[q - mx]) : 0.0;
+  v[3] = iy < my - 1 ? no / sqrt(cp * c[q + mx]) : 0.0;
+  v[4] = 1.0 / cp;
+  v[5] = 1.0 / sqrt(cp);
+  v[6] = sqrt(cp);
+  for (int k = 0; k < 7; ++k) {
+    s64[(size_t)k * ld + q] = v[k];
+    s32[(size_t)k * ld + q] = (float)v[k];
+  }
+}
+
 // Cluster-wide reductions: per-warp sums in the working precision, per-CTA
 // sums in FP64 pushed into every CTA's shared memory before the cluster
 // barrier (remote stores), then one fixed-order sum over the CTAs per value.
@@ -159,6 +190,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   const int k0 = min(a.n, crank * rows_per * mx), k1 = min(a.n, (crank + 1) * rows_per * mx);
   const T* __restrict__ B = static_cast<const T*>(a.B);
   const T* __restrict__ Bd = B + 5 * ldb;             // 1 / diag (0 on the pads)
+  const T* __restrict__ Bs = static_cast<const T*>(a.Bs);   // CG: scaled matrix (see KryArgs)
   auto vec = [&](int v) { return ws + (size_t)v * ldv + mx; };
   T* x = vec(0);
   T* r = vec(1);
@@ -201,6 +233,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
       v = (T) static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
     else
       v = (T) static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
+    if (!a.bicg && a.M > 0) v *= Bs[6 * ldb + k];   // CG iterates in x^ = S x
     x[k] = v;
   }
   cl.sync();
@@ -211,28 +244,37 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   for (int j = 0; j < a.M; ++j) {
     // ---- right-hand side d = x + dt f, residual r = d - B x --------------
     T red3t[3] = {T(0), T(0), T(0)};    // d.d, r.r, rho
-    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    for (int k = k0 + threadIdx.x; k < k1 && !a.bicg; k += blockDim.x) {
+      // CG: d^ = x^ / c + dt f / sqrt(c), r = p = d^ - B^ x^
+      T f = T(0);
+      if (csys)
+        for (int qq = 0; qq < a.src.Q; ++qq)
+          f += (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
+      const T d = Bs[4 * ldb + k] * x[k] + dt * Bs[5 * ldb + k] * f;
+      T bx = x[k];
+      bx += Bs[k] * x[k - 1];
+      bx += Bs[ldb + k] * x[k + 1];
+      bx += Bs[2 * ldb + k] * x[k - mx];
+      bx += Bs[3 * ldb + k] * x[k + mx];
+      const T rk = d - bx;
+      r[k] = rk;
+      p[k] = rk;
+      red3t[0] += d * d;
+      red3t[1] += rk * rk;
+      red3t[2] += rk * rk;
+    }
+    for (int k = k0 + threadIdx.x; k < k1 && a.bicg; k += blockDim.x) {
       T d = x[k];
       if (csys)
         for (int qq = 0; qq < a.src.Q; ++qq)
           d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
       T rk = d - stencil_apply(B, ldb, mx, k, x);
       r[k] = rk;
-      if (a.bicg) {
-        red3t[0] += d * d;
-        red3t[1] += rk * rk;
-        rh[k] = rk;
-        p[k] = rk;
-        red3t[2] += rk * rk;
-      } else {
-        // CG stops on the residual of the diagonally scaled system:
-        // ||D^1/2 r|| <= rtol ||D^1/2 d||, with ||D^1/2 r||^2 = r.z
-        const T z = rk * Bd[k];
-        p[k] = z;
-        red3t[0] += d * (d * Bd[k]);
-        red3t[1] += rk * z;
-        red3t[2] += rk * z;
-      }
+      red3t[0] += d * d;
+      red3t[1] += rk * rk;
+      rh[k] = rk;
+      p[k] = rk;
+      red3t[2] += rk * rk;
     }
     double red3[3];
     cl_sum<T, 3>(cl, red3t, red3, sh, buf);
@@ -240,12 +282,25 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
     double rr = red3[1], rho = red3[2];
     int it = 0;
     if (!a.bicg) {
-      // ---- preconditioned conjugate gradients ------------------------------
+      // ---- conjugate gradients on the diagonally scaled system ----------------
+      // (Jacobi-preconditioned CG on B x = d: the same Krylov spaces and
+      // scalars in exact arithmetic; B^ has a unit diagonal, so q = p + the
+      // four scaled couplings, and the residual r^ = S^-1 r is the quantity
+      // the stopping test measures: ||r^|| <= rtol ||d^||)
+      struct Sc { T w, e, s, nn, v0, v1, v2, v3, v4; };
       while (rr > tol2 && it < a.max_iter) {
         T pqt[1] = {T(0)};
-        for_points<St>(k0, k1, [&](int k) { return st_load(k, p); },
-                       [&](int k, const St& g) {
-                         const T qk = st_eval(g);
+        for_points<Sc>(k0, k1,
+                       [&](int k) {
+                         return Sc{Bs[k], Bs[ldb + k], Bs[2 * ldb + k], Bs[3 * ldb + k],
+                                   p[k], p[k - 1], p[k + 1], p[k - mx], p[k + mx]};
+                       },
+                       [&](int k, const Sc& g) {
+                         T qk = g.v0;
+                         qk += g.w * g.v1;
+                         qk += g.e * g.v2;
+                         qk += g.s * g.v3;
+                         qk += g.nn * g.v4;
                          q[k] = qk;
                          pqt[0] += g.v0 * qk;
                        });
@@ -254,14 +309,14 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
         if (!(pq[0] > 0.0)) { my_status |= 2; break; }
         const T alpha = (T)(rho / pq[0]);
         T rz[1] = {T(0)};
-        struct Up { T x, p, r, q, d; };
+        struct Up { T x, p, r, q; };
         for_points<Up>(k0, k1,
-                       [&](int k) { return Up{x[k], p[k], r[k], q[k], Bd[k]}; },
+                       [&](int k) { return Up{x[k], p[k], r[k], q[k]}; },
                        [&](int k, const Up& g) {
                          x[k] = g.x + alpha * g.p;
                          const T rk = g.r - alpha * g.q;
                          r[k] = rk;
-                         rz[0] += rk * (rk * g.d);
+                         rz[0] += rk * rk;
                        });
         double rzd[1];
         cl_sum<T, 1>(cl, rz, rzd, sh, buf);
@@ -269,9 +324,9 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
         rho = rzd[0];
         rr = rzd[0];
         ++it;
-        struct Pu { T r, d, p; };
-        for_points<Pu>(k0, k1, [&](int k) { return Pu{r[k], Bd[k], p[k]}; },
-                       [&](int k, const Pu& g) { p[k] = g.r * g.d + beta * g.p; });
+        struct Pu { T r, p; };
+        for_points<Pu>(k0, k1, [&](int k) { return Pu{r[k], p[k]}; },
+                       [&](int k, const Pu& g) { p[k] = g.r + beta * g.p; });
         cl.sync();
       }
     } else {
@@ -353,10 +408,11 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   // ---- store -----------------------------------------------------------------
   const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
   for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    const T v = !a.bicg && a.M > 0 ? x[k] * Bs[5 * ldb + k] : x[k];   // CG: x = S^-1 x^
     if (a.out.y_f64)
-      static_cast<double*>(a.out.y)[oy + k] = (double)x[k];
+      static_cast<double*>(a.out.y)[oy + k] = (double)v;
     else
-      static_cast<float*>(a.out.y)[oy + k] = (float)x[k];
+      static_cast<float*>(a.out.y)[oy + k] = (float)v;
   }
   cl.sync();
 }
@@ -445,6 +501,16 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
       pl->b64.as<double>(), pl->b32.as<float>());
   cudaError_t e = cudaGetLastError();
   if (e) return cuda_err(c, e, "k_stencil_plan");
+  if (op->symmetric) {
+    if ((s = dev_alloc(op->ctx, pl->bs64, sizeof(double) * 7 * ld))) return s;
+    if ((s = dev_alloc(op->ctx, pl->bs32, sizeof(float) * 7 * ld))) return s;
+    cudaMemsetAsync(pl->bs64.ptr, 0, pl->bs64.bytes, c->stream);
+    cudaMemsetAsync(pl->bs32.ptr, 0, pl->bs32.bytes, c->stream);
+    k_stencil_plan_scaled<<<(op->n + 255) / 256, 256, 0, c->stream>>>(
+        op->mx, op->my, pl->b64.as<double>(), pl->bs64.as<double>(), pl->bs32.as<float>());
+    e = cudaGetLastError();
+    if (e) return cuda_err(c, e, "k_stencil_plan_scaled");
+  }
   *out = pl.get();
   op->splans.push_back(std::move(pl));
   return LRP_OK;
@@ -523,6 +589,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   a.rtol = prec == 0 ? op->rtol64 : op->rtol32;
   a.max_iter = op->max_iter;
   a.B = stencil_B(plan, op, prec);
+  a.Bs = stencil_Bs(plan, op, prec);
   a.ws = op->kws.ptr;
   a.nvec = nvec;
   a.in = in;
@@ -557,6 +624,12 @@ size_t krylov_queue_nvec(int bicg) { return bicg ? 9 : 4; }
 const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec) {
   return prec == 0 ? (const void*)(pl->b64.as<double>() + op->mx)
                    : (const void*)(pl->b32.as<float>() + op->mx);
+}
+
+const void* stencil_Bs(const StencilPlan* pl, const Operator* op, int prec) {
+  if (!op->symmetric) return nullptr;
+  return prec == 0 ? (const void*)(pl->bs64.as<double>() + op->mx)
+                   : (const void*)(pl->bs32.as<float>() + op->mx);
 }
 
 int krylov_queue_clusters(Ctx* c, int prec, int cs) {
