@@ -70,6 +70,10 @@ def parse():
                     help="krylov mode: precisions to time (mixed = FP32 sketch settings)")
     ap.add_argument("--krylov-systems", default="64,16",
                     help="krylov mode: systems per launch for each precision")
+    ap.add_argument("--krylov-block", type=int, default=0, choices=[0, 4],
+                    help="--mode krylov: solve the systems four at a time by block CG")
+    ap.add_argument("--krylov-block-clusters", type=int, default=0,
+                    help="--mode krylov: clusters in flight of the block CG (0: automatic)")
     ap.add_argument("--krylov-onchip", type=int, default=0, choices=[0, 2],
                     help="krylov mode: 0 the on-chip CG where it applies, 2 the kernel with "
                          "its Krylov vectors in global memory")
@@ -366,19 +370,24 @@ def hbm_peak_gbs():
 ONCHIP_DRAM_BYTES_PER_SYSTEM = (38.77e6 + 1.02e6) / 16
 
 
-def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0) -> dict:
+def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, block: int = 0,
+               block_clusters: int = 0) -> dict:
     """The 2D fine propagator's bandwidth (the 'HBM GB/s frac' part of the
     metric): diff2d (511^2, kappa checkerboard, dt = 1/4096), Jacobi-PCG per
     backward-Euler step, FP32 sketch propagations (rtol 1e-6) and FP64 fine
     propagations (rtol 1e-12), one step per system.  Algorithmic traffic of a
     CG iteration: x, r, p read and written (6 words per grid point);
     achieved = that x iterations / kernel time (CUDA events on the library's
-    stream)."""
+    stream).  With block = 4 the systems are solved four at a time in one
+    block Krylov space (fewer iterations per system; `us_per_system_step`
+    compares the kernels per system and step)."""
     from paper_2508_08873_gb300 import api, workloads as W
     P = W.diff2d()
     op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
     op.set_krylov(1e-12, 1e-6, 20000)
     ctx.set_param("krylov_onchip", onchip)
+    ctx.set_param("krylov_block", block)
+    ctx.set_param("krylov_block_clusters", block_clusters)
     peak, peak_src = hbm_peak_gbs()
     rng = np.random.default_rng(0)
     out = {}
@@ -399,12 +408,18 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0) -> d
             es = 8 if prec == "f64" else 4
             gbs = its * 6 * P.n * es / (ms * 1e-3) / 1e9
             onchip_used = ctx.get_param("krylov_onchip_rows") > 0
+            block_used = ctx.get_param("krylov_block_last_systems") > 0
             key = "f64" if prec == "f64" else "f32"
             out[key] = {"systems": nsys, "cg_iterations_per_step": its / (nsys * steps),
-                        "us_per_iteration_and_system": ms * 1e3 / its, "achieved_gbs": gbs,
+                        "us_per_iteration_and_system": ms * 1e3 / its,
+                        "us_per_system_step": ms * 1e3 / (nsys * steps), "achieved_gbs": gbs,
                         "peak_gbs": peak, "frac": gbs / peak, "launches": nl,
                         "rtol": 1e-12 if prec == "f64" else 1e-6,
-                        "kernel": "k_cg_onchip" if onchip_used else "k_krylov",
+                        "kernel": "k_bcg" if block_used else "k_cg_onchip" if onchip_used
+                        else "k_krylov",
+                        "block_shape": {"systems_per_block": ctx.get_param("krylov_block_last_systems"),
+                                        "ctas_per_cluster": ctx.get_param("krylov_block_last_cs"),
+                                        "clusters": ctx.get_param("krylov_block_last_clusters")},
                         "dram_traffic_per_launch": ONCHIP_DRAM_BYTES_PER_SYSTEM * nsys
                         if onchip_used and key == "f32" else None,
                         "onchip_shape": {"rows_per_cta": ctx.get_param("krylov_onchip_rows"),
@@ -412,6 +427,8 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0) -> d
                                          "clusters": ctx.get_param("krylov_onchip_clusters")}}
     finally:
         ctx.set_param("krylov_onchip", 0)
+        ctx.set_param("krylov_block", 0)
+        ctx.set_param("krylov_block_clusters", 0)
         op.close()
     return {"workload": "diff2d 511^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, one "
                         "backward-Euler step per system",
@@ -428,7 +445,8 @@ def run_krylov(args):
     ctx = api.Context(local)
     precs = args.krylov_precs.split(",")
     nsyss = [int(v) for v in args.krylov_systems.split(",")]
-    res = krylov_leg(ctx, precs, nsyss, args.steps, args.warmup, args.krylov_onchip)
+    res = krylov_leg(ctx, precs, nsyss, args.steps, args.warmup, args.krylov_onchip,
+                     args.krylov_block, args.krylov_block_clusters)
     head = res["f64" if precs[0] == "f64" else "f32"]
     line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
             "value": head["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,

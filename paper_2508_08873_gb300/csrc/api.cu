@@ -332,6 +332,12 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "krylov_onchip") {
     if (value != 0 && value != 2) return LRP_EINVAL;
     c->p_krylov_onchip = value;
+  } else if (k == "krylov_block") {
+    if (value != 0 && value != 4) return LRP_EINVAL;
+    c->p_krylov_block = value;
+  } else if (k == "krylov_block_clusters") {
+    if (value < 0 || value > 1024) return LRP_EINVAL;
+    c->p_krylov_block_clusters = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -349,6 +355,11 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "krylov_onchip_rows") *value = c->oc_last[0];
   else if (k == "krylov_onchip_cs") *value = c->oc_last[1];
   else if (k == "krylov_onchip_clusters") *value = c->oc_last[2];
+  else if (k == "krylov_block") *value = c->p_krylov_block;
+  else if (k == "krylov_block_clusters") *value = c->p_krylov_block_clusters;
+  else if (k == "krylov_block_last_systems") *value = c->bk_last[0];
+  else if (k == "krylov_block_last_cs") *value = c->bk_last[1];
+  else if (k == "krylov_block_last_clusters") *value = c->bk_last[2];
   else if (k == "orth_cluster") *value = c->p_orth_cluster;
   else if (k == "tri_spt") *value = c->p_tri_spt;
   else if (k == "tri_warp") *value = c->p_tri_warp;

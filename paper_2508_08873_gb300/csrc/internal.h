@@ -55,6 +55,9 @@ struct Ctx {
   int p_krylov_cluster = 0;  // CTAs per cluster of the 2D propagator (1..16)
   int p_krylov_onchip = 0;   // on-chip CG for symmetric 2D operators: 0 auto, 2 never
   int oc_last[3] = {0, 0, 0};  // last on-chip CG launch: rows per thread, CTAs per cluster, clusters
+  int p_krylov_block = 0;    // block CG over this many systems for symmetric 2D operators (0 off, 4)
+  int p_krylov_block_clusters = 0;  // clusters in flight of the block CG (0: workspaces within 96 MB)
+  int bk_last[3] = {0, 0, 0};  // last block CG launch: systems per block, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
   int p_tri_chunk = 0;       // rows per chunk of the cluster tridiagonal kernel (8, 16)
@@ -117,6 +120,8 @@ struct StencilPlan {
   DevBuf bs64, bs32;   // symmetric operators: the scaled matrix of CG (k_stencil_plan_scaled)
   DevBuf oc64, oc32;   // scaled couplings and scales of the on-chip CG kernel (stencil_onchip.cu)
   int oc_rows[2] = {0, 0};   // padded grid rows those were laid out for (FP64, FP32)
+  DevBuf bk64, bk32;   // the same, laid out for the block CG kernel (stencil_block.cu)
+  int bk_rows[2] = {0, 0};
 };
 
 // Constant-coefficient (Toeplitz) data of a tridiagonal step matrix
@@ -153,6 +158,7 @@ struct Operator {
   std::vector<std::unique_ptr<ClPlan>> cplans;
   std::vector<std::unique_ptr<StencilPlan>> splans;
   DevBuf kws, kstat;       // Krylov workspace and status of 2D propagations
+  DevBuf bws;              // block CG workspace (stencil_block.cu)
   unsigned long long krylov_iters = 0;
 };
 
@@ -307,6 +313,17 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
 // Both CG kernels stop on the residual of the diagonally scaled system,
 // ||D^1/2 (d - B x)|| <= rtol ||D^1/2 d||, D = diag(B)^-1.
 bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys);
+// Scaled couplings (e^, n^) and scales (1/c, 1/sqrt(c), sqrt(c)) of the
+// step matrix laid out [rows + 2][pitch] from grid row -1, into buf
+// (allocated or grown as needed); T = double for prec 0, else float.
+lrp_status oc_coef_fill(Ctx* c, const Operator* op, const StencilPlan* plan, int prec, int pitch,
+                        int rows, DevBuf& buf);
+// Block CG (stencil_block.cu): symmetric operators, propagations without a
+// source, at least two systems; the systems are taken in blocks of
+// p_krylov_block consecutive ones, each block on one cluster.
+bool stencil_block_applies(Ctx* c, const Operator* op, int prec, int nsys, int M, int Q);
+lrp_status stencil_propagate_block(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
+                                   int prec, const KryArgs& base);
 lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
                                     int prec, const KryArgs& base);
 size_t krylov_queue_nvec(int bicg);

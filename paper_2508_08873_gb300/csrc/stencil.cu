@@ -532,7 +532,9 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   if (s) return s;
   const int bicg = op->symmetric ? 0 : 1;
   const int nvec = (int)krylov_queue_nvec(bicg);
-  const bool onchip = stencil_onchip_applies(c, op, prec, nsys);
+  const bool block = stencil_block_applies(c, op, prec, nsys, M, src.Q);
+  if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
+  const bool onchip = !block && stencil_onchip_applies(c, op, prec, nsys);
   if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
   auto kern = prec == 0 ? (void (*)(KryArgs))k_krylov<double> : (void (*)(KryArgs))k_krylov<float>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -573,7 +575,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   cfg.gridDim = dim3(nclusters * cs);
   const size_t es = prec == 0 ? 8 : 4;
   const size_t need = (size_t)nclusters * nvec * ((size_t)op->n + 2 * op->mx) * es;
-  if (!onchip && op->kws.bytes < need)
+  if (!onchip && !block && op->kws.bytes < need)
     if ((s = dev_alloc(c, op->kws, need))) return s;
   if (!op->kstat.ptr)
     if ((s = dev_alloc(c, op->kstat, 16))) return s;
@@ -597,7 +599,9 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   a.src = src;
   a.iters = reinterpret_cast<unsigned long long*>(op->kstat.ptr);
   a.status = reinterpret_cast<int*>(static_cast<char*>(op->kstat.ptr) + 8);
-  if (onchip) {
+  if (block) {
+    if ((s = stencil_propagate_block(c, op, plan, M, nsys, prec, a))) return s;
+  } else if (onchip) {
     if ((s = stencil_propagate_onchip(c, op, plan, M, nsys, prec, a))) return s;
   } else {
     const char* fam = prec == 0 ? "propagate_f64" : "propagate_f32";
@@ -613,6 +617,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   if (e) return cuda_err(c, e, "k_krylov");
   op->krylov_iters += hs[0];
   int st = (int)(hs[1] & 0xffffffffu);
+  if (st & 4) return set_err(c, LRP_ETIMEOUT, "a bounded wait of the 2D block propagator expired");
   if (st & 2) return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in a 2D propagation");
   if (st & 1) return set_err(c, LRP_ENOTCONV, "Krylov iteration cap reached in a 2D propagation");
   return LRP_OK;

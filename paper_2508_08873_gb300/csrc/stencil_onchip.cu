@@ -42,6 +42,27 @@ __global__ void k_oc_coef(int mx, int my, int pitch, int rows, const double* __r
   scl[2 * plane + t] = (T)s;
 }
 
+lrp_status oc_coef_fill(Ctx* c, const Operator* op, const StencilPlan* plan, int prec, int pitch,
+                        int rows, DevBuf& buf) {
+  const size_t es = prec == 0 ? 8 : 4;
+  const size_t tot = (size_t)(rows + 2) * pitch;
+  const size_t need = tot * es * 5;          // (e^, n^) pairs + three scale planes
+  lrp_status s;
+  if (buf.bytes < need && (s = dev_alloc(c, buf, need))) return s;
+  const int nb = (int)((tot + 255) / 256);
+  if (prec == 0)
+    k_oc_coef<double><<<nb, 256, 0, c->stream>>>(
+        op->mx, op->my, pitch, rows, plan->b64.as<double>(),
+        reinterpret_cast<double2*>(buf.ptr), static_cast<double*>(buf.ptr) + 2 * tot);
+  else
+    k_oc_coef<float><<<nb, 256, 0, c->stream>>>(
+        op->mx, op->my, pitch, rows, plan->b64.as<double>(),
+        reinterpret_cast<float2*>(buf.ptr), static_cast<float*>(buf.ptr) + 2 * tot);
+  cudaError_t e = cudaGetLastError();
+  if (e) return cuda_err(c, e, "k_oc_coef");
+  return LRP_OK;
+}
+
 static int oc_pitch(int mx) {
   for (int p : {64, 128, 256, 512})
     if (mx <= p) return p;
@@ -118,18 +139,7 @@ lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int
   const size_t need = tot * es * 5;          // (e^, n^) pairs + three scale planes
   lrp_status s;
   if (cfb.bytes < need || plan->oc_rows[prec ? 1 : 0] != rows) {
-    if (cfb.bytes < need && (s = dev_alloc(c, cfb, need))) return s;
-    const int nb = (int)((tot + 255) / 256);
-    if (prec == 0)
-      k_oc_coef<double><<<nb, 256, 0, c->stream>>>(
-          op->mx, op->my, pitch, rows, plan->b64.as<double>(),
-          reinterpret_cast<double2*>(cfb.ptr), static_cast<double*>(cfb.ptr) + 2 * tot);
-    else
-      k_oc_coef<float><<<nb, 256, 0, c->stream>>>(
-          op->mx, op->my, pitch, rows, plan->b64.as<double>(),
-          reinterpret_cast<float2*>(cfb.ptr), static_cast<float*>(cfb.ptr) + 2 * tot);
-    cudaError_t e = cudaGetLastError();
-    if (e) return cuda_err(c, e, "k_oc_coef");
+    if ((s = oc_coef_fill(c, op, plan, prec, pitch, rows, cfb))) return s;
     plan->oc_rows[prec ? 1 : 0] = rows;
   }
   c->oc_last[0] = rpt;
