@@ -22,7 +22,7 @@ Variant variant_f32(int pitch) {
     case 128: return make_variant<float, BS, 128, RBF>();
     case 256: return make_variant<float, BS, 256, RBF>();
     case 512: return make_variant<float, BS, 512, RBF>();
-    default: return Variant{nullptr, 0, 0, 0, 0};
+    default: return Variant{nullptr, 0, 0, 0, 0, 0};
   }
 }
 
@@ -36,7 +36,7 @@ static int bk_pitch(int mx, int prec) {
 
 static bk::Variant bk_variant(int prec, int mx) {
   const int pitch = bk_pitch(mx, prec);
-  if (!pitch) return bk::Variant{nullptr, 0, 0, 0, 0};
+  if (!pitch) return bk::Variant{nullptr, 0, 0, 0, 0, 0};
   return prec == 0 ? bk::variant_f64(pitch) : bk::variant_f32(pitch);
 }
 
@@ -74,7 +74,7 @@ lrp_status stencil_propagate_block(Ctx* c, Operator* op, StencilPlan* plan, int 
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  cfg.blockDim = dim3(v.pitch);
+  cfg.blockDim = dim3(v.threads);   // two grid columns per thread
   cfg.gridDim = dim3(cs);
   cfg.dynamicSmemBytes = v.smem;
   cfg.stream = c->stream;

@@ -28,22 +28,26 @@
 // iterates until all S have.
 //
 // One block runs on one thread-block cluster of cs CTAs: CTA c owns grid
-// rows [c RB, c RB + RB), thread t owns grid column t (PITCH >= mx threads).
-// The block vectors X^, R (old and new) and P (old and new) live in a
-// global-memory workspace of the cluster, laid out [row][s][PITCH] with two
-// zero rows above and below the grid, so that one grid row of one block
-// vector is S PITCH contiguous elements.  An iteration streams the rows of
-// P, R and X^ (and the coupling row) that the CTA needs through a ring of
-// DR shared-memory slots, each filled by one thread with bulk asynchronous
-// copies (cp.async.bulk, completion on an mbarrier of the slot) three rows
-// ahead of their use: row q of the old directions enters the stencil of row
-// q - 1, whose new residual and direction are computed and stored; the new
-// directions of the last four rows stay in shared memory for the stencil of
-// B^ P_new one row behind.  Every CTA also computes the new residual and
-// direction of the row just above and just below its own (from old values
-// that their owners do not change in the pass).  The S x S algebra runs on
-// one warp of every CTA on the reduced totals, which every CTA receives
-// bitwise equal, so that all CTAs take the same decisions.
+// rows [c RB, c RB + RB), thread t owns grid columns 2t and 2t + 1 (PITCH / 2
+// threads, PITCH >= mx), whose values it carries as pairs: in FP32 every
+// multiply-add of the two columns is one packed instruction (fma.rn.f32x2),
+// and a coefficient of the S x S algebra, stored twice side by side, is one
+// 64-bit shared-memory load for both.  The block vectors X^, R (old and new)
+// and P (old and new) live in a global-memory workspace of the cluster,
+// laid out [row][s][PITCH] with two zero rows above and below the grid, so
+// that one grid row of one block vector is S PITCH contiguous elements.  An
+// iteration streams the rows of P, R and X^ (and the coupling row) that the
+// CTA needs through a ring of DR shared-memory slots, each filled by the
+// CTA's first thread with bulk asynchronous copies (cp.async.bulk,
+// completion on an mbarrier of the slot) three rows ahead of their use: row
+// q of the old directions enters the stencil of row q - 1, whose new
+// residual and direction are computed and stored; the new directions of the
+// last four rows stay in shared memory for the stencil of B^ P_new one row
+// behind.  Every CTA also computes the new residual and direction of the
+// row just above and just below its own (from old values that their owners
+// do not change in the pass).  The S x S algebra runs on one warp of every
+// CTA on the reduced totals, which every CTA receives bitwise equal, so that
+// all CTAs take the same decisions.
 #pragma once
 #include <cooperative_groups.h>
 
@@ -64,6 +68,7 @@ template <typename T> struct V2;
 template <> struct V2<float> { using t = float2; };
 template <> struct V2<double> { using t = double2; };
 
+
 // Launch arguments.  cf: [rows + 2][PITCH] pairs (e^, n^) from grid row -1
 // (the layout of the on-chip CG kernel); scl: three planes [rows + 2][PITCH]
 // of 1/c, 1/sqrt(c), sqrt(c).  ws: per cluster slot, slot_elems elements:
@@ -81,11 +86,11 @@ struct Args {
 template <typename T, int S, int PITCH>
 struct Smem {
   using T2 = typename V2<T>::t;
-  static constexpr int NW = PITCH / 32;
+  static constexpr int NW = PITCH / 64;                      // warps (two columns per thread)
   static constexpr int NU = S * (S + 1) / 2;                 // upper triangle of a symmetric S x S
   static constexpr int NV = 2 * NU + 2 * S * S + S;          // G, ZZ, H, ZR, r.r
   static constexpr int OG = 0, OZZ = NU, OH = 2 * NU, OZR = 2 * NU + S * S, ORR = 2 * NU + 2 * S * S;
-  T ring[DR][3][S][PITCH];   // per slot: one row of P (old), R (old), X^
+  alignas(16) T ring[DR][3][S][PITCH];   // per slot: one row of P (old), R (old), X^
   T2 cfr[DR][PITCH];         // per slot: the coupling row
   T pb[4][S][PITCH];         // new directions of the last four rows (row m in pb[m & 3])
   T red[NV][NW];             // per-warp partial sums
@@ -94,6 +99,7 @@ struct Smem {
   T A[S][S];                 // Schur complements of the pivoted Cholesky
   T L[S][S];                 // its columns: L[i][k] = entry of original row i in column k
   T C1[S][S], C2[S][S], E[S][S];
+  T2 C1s[S][S], nC1s[S][S], nC2s[S][S];   // C1, -C1, -C2 with each entry twice (packed operands)
   T dinv[S];                 // 1 / L[piv[k]][k]
   T dd[S], rr[S];            // d^.d^ and r.r per system
   alignas(8) unsigned long long mbar[DR];
@@ -276,9 +282,11 @@ LRP_DEV void gplus_apply(const T* m, T (*out)[S], SM& sh) {
 }
 
 // Warp 0, on the totals of a pass: the pivoted factor of G, C1 = G+ H,
-// E = ZR - ZZ C1, C2 = G+ E; brk when no direction is left.
+// E = ZR - ZZ C1, C2 = G+ E, and C1, -C1, -C2 with each entry doubled for
+// packed operands; brk when no direction is left.
 template <typename T, int S, typename SM>
 LRP_DEV void block_coefficients(T thr, SM& sh) {
+  using T2 = typename SM::T2;
   const int lane = threadIdx.x & 31;
   pchol<T, S>(sh.tot + SM::OG, thr, sh);
   if (sh.rank == 0) {
@@ -298,46 +306,99 @@ LRP_DEV void block_coefficients(T thr, SM& sh) {
   }
   __syncwarp();
   gplus_apply<T, S>(&sh.E[0][0], sh.C2, sh);
+  if (lane < S) {
+#pragma unroll
+    for (int t = 0; t < S; ++t) {
+      sh.C1s[t][lane] = T2{sh.C1[t][lane], sh.C1[t][lane]};
+      sh.nC1s[t][lane] = T2{-sh.C1[t][lane], -sh.C1[t][lane]};
+      sh.nC2s[t][lane] = T2{-sh.C2[t][lane], -sh.C2[t][lane]};
+    }
+  }
+  __syncwarp();
 }
 
-template <typename T, int S, typename SM>
-LRP_DEV void add_grams(T (&acc)[SM::NV], const T (&p)[S], const T (&z)[S], const T (&r)[S]) {
+// ---- two adjacent columns as one value ----------------------------------------
+// a * b + c on both halves: one packed instruction in FP32, two in FP64.
+LRP_DEV float2 vfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{\n\t.reg .b64 pa, pb, pc, pd;\n\tmov.b64 pa, {%2, %3};\n\tmov.b64 pb, {%4, %5};\n\t"
+      "mov.b64 pc, {%6, %7};\n\tfma.rn.f32x2 pd, pa, pb, pc;\n\tmov.b64 {%0, %1}, pd;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+LRP_DEV double2 vfma(double2 a, double2 b, double2 c) {
+  return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+
+// (e^, n^) of columns c and c + 1 (c even) as (e^ pair, n^ pair)
+LRP_DEV void ld_cf_pair(const float2* p, float2& e, float2& n) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  e = make_float2(q.x, q.z);
+  n = make_float2(q.y, q.w);
+}
+LRP_DEV void ld_cf_pair(const double2* p, double2& e, double2& n) {
+  const double2 a = p[0], b = p[1];
+  e = make_double2(a.x, b.x);
+  n = make_double2(a.y, b.y);
+}
+
+// Gram accumulators: in FP32 one packed pair per entry (the two columns'
+// partial sums, added at the end), in FP64 one scalar per entry (registers).
+template <typename T> struct AccT;
+template <> struct AccT<float> { using t = float2; };
+template <> struct AccT<double> { using t = double; };
+LRP_DEV void acc_add(float2& a, float2 x, float2 y) { a = vfma(x, y, a); }
+LRP_DEV void acc_add(double& a, double2 x, double2 y) {
+  a = fma(x.x, y.x, a);
+  a = fma(x.y, y.y, a);
+}
+LRP_DEV float acc_val(float2 a) { return a.x + a.y; }
+LRP_DEV double acc_val(double a) { return a; }
+LRP_DEV void acc_zero(float2& a) { a = make_float2(0.f, 0.f); }
+LRP_DEV void acc_zero(double& a) { a = 0.0; }
+
+template <int S, typename SM, typename A, typename V>
+LRP_DEV void add_grams(A (&acc)[SM::NV], const V (&p)[S], const V (&z)[S], const V (&r)[S]) {
 #pragma unroll
   for (int t = 0; t < S; ++t) {
 #pragma unroll
     for (int s = t; s < S; ++s) {
-      acc[SM::OG + up_idx<S>(t, s)] += p[t] * z[s];
-      acc[SM::OZZ + up_idx<S>(t, s)] += z[t] * z[s];
+      acc_add(acc[SM::OG + up_idx<S>(t, s)], p[t], z[s]);
+      acc_add(acc[SM::OZZ + up_idx<S>(t, s)], z[t], z[s]);
     }
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      acc[SM::OH + t * S + s] += p[t] * r[s];
-      acc[SM::OZR + t * S + s] += z[t] * r[s];
+      acc_add(acc[SM::OH + t * S + s], p[t], r[s]);
+      acc_add(acc[SM::OZR + t * S + s], z[t], r[s]);
     }
   }
 #pragma unroll
-  for (int s = 0; s < S; ++s) acc[SM::ORR + s] += r[s] * r[s];
+  for (int s = 0; s < S; ++s) acc_add(acc[SM::ORR + s], r[s], r[s]);
 }
 
 template <typename T, int S, int PITCH, int RB>
-__global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
+__global__ void __launch_bounds__(PITCH / 2, 1) k_bcg(Args ba) {
   using SM = Smem<T, S, PITCH>;
-  using T2 = typename SM::T2;
+  using V = typename SM::T2;      // two columns (the same type as a coupling pair)
+  using A = typename AccT<T>::t;
   constexpr int NV = SM::NV;
   const KryArgs& a = ba.k;
   if (a.in.stop && *a.in.stop) return;
   cg::cluster_group cl = cg::this_cluster();
   const int cs = (int)cl.num_blocks(), crank = (int)cl.block_rank();
   const int mx = a.mx, my = a.my;
-  const int col = threadIdx.x, wid = col >> 5, lane = col & 31;
+  const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  const int c0 = 2 * tid;                       // this thread's columns c0, c0 + 1
+  const bool has_w = c0 > 0, has_e = c0 + 2 < PITCH;
   const int r0 = crank * RB;
   const int rows = ba.rows;
   const size_t plane = (size_t)(rows + 2) * PITCH;
   const size_t rowel = (size_t)S * PITCH;
   const size_t bstride = (size_t)(rows + 2 * PADR) * rowel;
-  const T2* const cf0 = static_cast<const T2*>(ba.cf) + PITCH;   // grid row 0, column 0
-  const T2* __restrict__ cfc = cf0 + col;
-  const T* __restrict__ sc = static_cast<const T*>(ba.scl) + PITCH + col;
+  const V* const cf0 = static_cast<const V*>(ba.cf) + PITCH;    // grid row 0, column 0
+  const V* __restrict__ cfc = cf0 + c0;
+  const T* __restrict__ sc = static_cast<const T*>(ba.scl) + PITCH + c0;
 
   extern __shared__ __align__(128) unsigned char bk_smem_raw[];
   SM& sh = *reinterpret_cast<SM*>(bk_smem_raw);
@@ -350,16 +411,21 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
   T* const P0g = ws + 3 * bstride;
   T* const P1g = ws + 4 * bstride;
   auto rowp = [&](T* b, int row) -> T* { return b + (size_t)(row + PADR) * rowel; };
-  auto el = [&](T* b, int row, int s) -> T& { return rowp(b, row)[(size_t)s * PITCH + col]; };
+  // the pair (c0, c0 + 1) of system s in row `row` of a block vector
+  auto gv = [&](T* b, int row, int s) -> V& {
+    return *reinterpret_cast<V*>(rowp(b, row) + (size_t)s * PITCH + c0);
+  };
+  auto sv = [&](T* p) -> V& { return *reinterpret_cast<V*>(p); };
   const T thr = (T)ba.thr;
   const T rtol2 = (T)(a.rtol * a.rtol);
   const int max_iter = a.max_iter;
+  const V vzero{T(0), T(0)};
   int buf = 0;
   unsigned long long my_iters = 0;
   int my_status = 0;
   uint32_t ph = 0;   // parity of the next phase of every ring slot (bit i), the same in all threads
 
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     for (int i = 0; i < DR; ++i) mbar_init(saddr(&sh.mbar[i]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -371,6 +437,25 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
     if (!mbar_wait(saddr(&sh.mbar[i]), par) && !mbar_wait(saddr(&sh.mbar[i]), par)) my_status |= 4;
     ph ^= 1u << i;
   };
+  auto reduce = [&](const A (&acc)[NV]) {
+    T v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) v[i] = acc_val(acc[i]);
+    cl_reduce<T, NV>(cl, v, sh, buf);
+  };
+  // 5-point product of the scaled matrix at one row: centre pair pc, its
+  // west and east neighbours (columns c0 - 1 and c0 + 2) pwv, pev, the rows
+  // above and below pn, ps; couplings e^ (ec), e^ of the column to the west
+  // (ew), n^ of the row (nc) and of the row below (ns)
+  auto stencil = [&](V pc, T pwv, T pev, V pn, V ps, V ec, V ew, V nc, V ns) -> V {
+    const V pe{pc.y, pev};
+    const V pw{pwv, pc.x};
+    V z = vfma(ec, pe, pc);
+    z = vfma(ew, pw, z);
+    z = vfma(nc, pn, z);
+    z = vfma(ns, ps, z);
+    return z;
+  };
 
   // ---- one iteration: X^ += P C1, R_new = R - (B^ P) C1, P_new = R_new - P C2,
   // B^ P_new and the Gram matrices of (P_new, B^ P_new, R_new), one reduction
@@ -380,7 +465,7 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
     T* const Rn = cur ? R0g : R1g;
     T* const Pn = cur ? P0g : P1g;
     const int q0 = r0 - 2, q1 = r0 + RB + 1;
-    const uint32_t rbytes = (uint32_t)(rowel * sizeof(T)), cbytes = (uint32_t)(PITCH * sizeof(T2));
+    const uint32_t rbytes = (uint32_t)(rowel * sizeof(T)), cbytes = (uint32_t)(PITCH * sizeof(V));
     // row q into its ring slot: the old directions always, the old residual
     // for rows r0 - 1 .. r0 + RB, X^ for own rows, the couplings inside -1 .. rows
     auto issue = [&](int q) {
@@ -395,101 +480,103 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
       if (hasX) bulk_g2s(&sh.ring[i][2][0][0], rowp(Xg, q), rbytes, mb);
       if (hasC) bulk_g2s(&sh.cfr[i][0], cf0 + (long)q * PITCH, cbytes, mb);
     };
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       fence_async_global();
       fence_async_shared();
       for (int q = q0; q <= q1 && q < q0 + DR; ++q) issue(q);
     }
-    T acc[NV];
+    A acc[NV];
 #pragma unroll
-    for (int v = 0; v < NV; ++v) acc[v] = T(0);
+    for (int v = 0; v < NV; ++v) acc_zero(acc[v]);
     wait_slot(0);
     wait_slot(1);
-    T ec_p = T(0), ew_p = T(0), nc_p = T(0), ns_p = T(0);   // couplings of the previous centre row
-    T rprev[S];                                             // its new residual
+    V ec_p = vzero, ew_p = vzero, nc_p = vzero, ns_p = vzero;   // couplings of the previous centre row
+    V rprev[S];                                                 // its new residual
 #pragma unroll
-    for (int s = 0; s < S; ++s) rprev[s] = T(0);
+    for (int s = 0; s < S; ++s) rprev[s] = vzero;
+    int is = 0, ic = 1, in = 2;   // ring slots of rows q - 2, q - 1, q
 #pragma unroll 1
     for (int q = r0; q <= q1; ++q) {
       const int c = q - 1;   // centre row: r0 - 1 .. r0 + RB
-      const int is = (q - 2 - q0) % DR, ic = (q - 1 - q0) % DR, in = (q - q0) % DR;
       wait_slot(in);
-      const T2 c2 = sh.cfr[ic][col];
-      const T ew = col > 0 ? sh.cfr[ic][col - 1].x : T(0);
-      const T ns = c - 1 >= -1 ? sh.cfr[is][col].y : T(0);
-      T pc[S], z[S], rn[S], pn[S];
+      V ec, nc, ew;
+      ld_cf_pair(&sh.cfr[ic][c0], ec, nc);
+      ew = V{has_w ? sh.cfr[ic][c0 - 1].x : T(0), ec.x};
+      V ns = vzero;
+      if (c - 1 >= -1) {
+        V e_s;
+        ld_cf_pair(&sh.cfr[is][c0], e_s, ns);
+      }
+      V pc[S], z[S], rn[S], pn[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        pc[s] = sh.ring[ic][0][s][col];
-        const T pe = col + 1 < PITCH ? sh.ring[ic][0][s][col + 1] : T(0);
-        const T pw = col > 0 ? sh.ring[ic][0][s][col - 1] : T(0);
-        T zz = pc[s];
-        zz += c2.x * pe;
-        zz += ew * pw;
-        zz += c2.y * sh.ring[in][0][s][col];
-        zz += ns * sh.ring[is][0][s][col];
-        z[s] = zz;
+        const T* pr = &sh.ring[ic][0][s][c0];
+        pc[s] = sv(const_cast<T*>(pr));
+        const T pwv = has_w ? pr[-1] : T(0);
+        const T pev = has_e ? pr[2] : T(0);
+        z[s] = stencil(pc[s], pwv, pev, sv(&sh.ring[in][0][s][c0]), sv(&sh.ring[is][0][s][c0]), ec,
+                       ew, nc, ns);
       }
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        T v = sh.ring[ic][1][s][col];
+        V v = sv(&sh.ring[ic][1][s][c0]);
 #pragma unroll
-        for (int t = 0; t < S; ++t) v -= z[t] * sh.C1[t][s];
+        for (int t = 0; t < S; ++t) v = vfma(z[t], sh.nC1s[t][s], v);
         rn[s] = v;
       }
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        T v = rn[s];
+        V v = rn[s];
 #pragma unroll
-        for (int t = 0; t < S; ++t) v -= pc[t] * sh.C2[t][s];
+        for (int t = 0; t < S; ++t) v = vfma(pc[t], sh.nC2s[t][s], v);
         pn[s] = v;
       }
       if (c >= r0 && c < r0 + RB) {
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          T xv = sh.ring[ic][2][s][col];
+          V xv = sv(&sh.ring[ic][2][s][c0]);
 #pragma unroll
-          for (int t = 0; t < S; ++t) xv += pc[t] * sh.C1[t][s];
-          el(Xg, c, s) = xv;
-          el(Rn, c, s) = rn[s];
-          el(Pn, c, s) = pn[s];
+          for (int t = 0; t < S; ++t) xv = vfma(pc[t], sh.C1s[t][s], xv);
+          gv(Xg, c, s) = xv;
+          gv(Rn, c, s) = rn[s];
+          gv(Pn, c, s) = pn[s];
         }
       }
 #pragma unroll
-      for (int s = 0; s < S; ++s) sh.pb[c & 3][s][col] = pn[s];
+      for (int s = 0; s < S; ++s) sv(&sh.pb[c & 3][s][c0]) = pn[s];
       __syncthreads();
       // the slot of row q - 3 is read by no thread any more: refill it
-      if (threadIdx.x == 0 && q - 3 >= q0 && q - 3 + DR <= q1) {
+      if (tid == 0 && q - 3 >= q0 && q - 3 + DR <= q1) {
         fence_async_shared();
         issue(q - 3 + DR);
       }
       // B^ P_new of the own row m = c - 1 (its neighbours' new directions are in pb)
       const int m = c - 1;
       if (m >= r0) {
-        T pm[S], zm[S];
+        V pm[S], zm[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          pm[s] = sh.pb[m & 3][s][col];
-          const T pe = col + 1 < PITCH ? sh.pb[m & 3][s][col + 1] : T(0);
-          const T pw = col > 0 ? sh.pb[m & 3][s][col - 1] : T(0);
-          T zz = pm[s];
-          zz += ec_p * pe;
-          zz += ew_p * pw;
-          zz += nc_p * sh.pb[c & 3][s][col];
-          zz += ns_p * sh.pb[(m - 1) & 3][s][col];
-          zm[s] = zz;
+          const T* pr = &sh.pb[m & 3][s][c0];
+          pm[s] = sv(const_cast<T*>(pr));
+          const T pwv = has_w ? pr[-1] : T(0);
+          const T pev = has_e ? pr[2] : T(0);
+          zm[s] = stencil(pm[s], pwv, pev, sv(&sh.pb[c & 3][s][c0]), sv(&sh.pb[(m - 1) & 3][s][c0]),
+                          ec_p, ew_p, nc_p, ns_p);
         }
-        add_grams<T, S, SM>(acc, pm, zm, rprev);
+        add_grams<S, SM>(acc, pm, zm, rprev);
       }
-      ec_p = c2.x;
+      ec_p = ec;
       ew_p = ew;
-      nc_p = c2.y;
+      nc_p = nc;
       ns_p = ns;
 #pragma unroll
       for (int s = 0; s < S; ++s) rprev[s] = rn[s];
+      is = ic;
+      ic = in;
+      in = in + 1 == DR ? 0 : in + 1;
     }
     fence_async_global();   // X^, R_new, P_new stores before the next pass's bulk copies
-    cl_reduce<T, NV>(cl, acc, sh, buf);
+    reduce(acc);
   };
 
   const int nblk = (a.nsys + S - 1) / S;
@@ -499,24 +586,28 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
     // ---- X^ = sqrt(c) x, own rows (systems beyond nsys: 0) --------------------
     for (int i = 0; i < RB; ++i) {
       const int row = r0 + i;
-      const bool in_grid = col < mx && row < my;
-      const T sq = in_grid ? sc[(long)row * PITCH + 2 * plane] : T(0);
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        T v = T(0);
-        if (in_grid && s < ncols) {
-          const int sys = sys0 + s, k = row * mx + col;
-          if (a.in.gen)
-            v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
-                         (uint32_t)(sys % a.in.ncol), (uint32_t)k);
-          else if (a.in.x != nullptr) {
-            const long ox = sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys);
-            v = a.in.x_f64 ? (T) static_cast<const double*>(a.in.x)[ox + k]
-                           : (T) static_cast<const float*>(a.in.x)[ox + k];
+        T v2[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = c0 + h;
+          T v = T(0);
+          if (col < mx && row < my && s < ncols) {
+            const int sys = sys0 + s, k = row * mx + col;
+            if (a.in.gen)
+              v = gauss<T>(a.in.seed, a.in.stream, (uint32_t)(a.in.interval0 + sys / a.in.ncol),
+                           (uint32_t)(sys % a.in.ncol), (uint32_t)k);
+            else if (a.in.x != nullptr) {
+              const long ox = sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys);
+              v = a.in.x_f64 ? (T) static_cast<const double*>(a.in.x)[ox + k]
+                             : (T) static_cast<const float*>(a.in.x)[ox + k];
+            }
+            v *= sc[(long)row * PITCH + 2 * plane + h];
           }
-          v *= sq;
+          v2[h] = v;
         }
-        el(Xg, row, s) = v;
+        gv(Xg, row, s) = V{v2[0], v2[1]};
       }
     }
     fence_async_global();
@@ -525,41 +616,40 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
     for (int j = 0; j < a.M; ++j) {
       // ---- d^ = X^ / c, R = d^ - B^ X^; d^.d^, r.r per system -----------------
       {
-        T acc[2 * S];
+        A acc[2 * S];
 #pragma unroll
-        for (int v = 0; v < 2 * S; ++v) acc[v] = T(0);
-        T xs[S], xc[S], xn[S];
+        for (int v = 0; v < 2 * S; ++v) acc_zero(acc[v]);
+        V xs[S], xc[S], xn[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          xs[s] = el(Xg, r0 - 1, s);
-          xc[s] = el(Xg, r0, s);
+          xs[s] = gv(Xg, r0 - 1, s);
+          xc[s] = gv(Xg, r0, s);
         }
-        T n_s = cfc[(long)(r0 - 1) * PITCH].y;
+        V ns, e_s;
+        ld_cf_pair(cfc + (long)(r0 - 1) * PITCH, e_s, ns);
+        T* const Rk = cur ? R1g : R0g;
 #pragma unroll 1
         for (int i = 0; i < RB; ++i) {
           const int row = r0 + i;
-          const T2 c2 = cfc[(long)row * PITCH];
-          const T ew = col > 0 ? cfc[(long)row * PITCH - 1].x : T(0);
-          const T ic = sc[(long)row * PITCH];
+          V ec, nc;
+          ld_cf_pair(cfc + (long)row * PITCH, ec, nc);
+          const V ew{has_w ? cfc[(long)row * PITCH - 1].x : T(0), ec.x};
+          const V ic{sc[(long)row * PITCH], sc[(long)row * PITCH + 1]};
 #pragma unroll
-          for (int s = 0; s < S; ++s) xn[s] = el(Xg, row + 1, s);
+          for (int s = 0; s < S; ++s) xn[s] = gv(Xg, row + 1, s);
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const T* xr = rowp(Xg, row) + (size_t)s * PITCH + col;
-            const T xw = col > 0 ? xr[-1] : T(0);
-            const T xe = col + 1 < PITCH ? xr[1] : T(0);
-            T bx = xc[s];
-            bx += c2.x * xe;
-            bx += ew * xw;
-            bx += c2.y * xn[s];
-            bx += n_s * xs[s];
-            const T d = ic * xc[s];
-            const T rk = d - bx;
-            el(cur ? R1g : R0g, row, s) = rk;
-            acc[s] += d * d;
-            acc[S + s] += rk * rk;
+            const T* xr = rowp(Xg, row) + (size_t)s * PITCH + c0;
+            const T xw = has_w ? xr[-1] : T(0);
+            const T xe = has_e ? xr[2] : T(0);
+            const V bx = stencil(xc[s], xw, xe, xn[s], xs[s], ec, ew, nc, ns);
+            const V d{ic.x * xc[s].x, ic.y * xc[s].y};
+            const V rk{d.x - bx.x, d.y - bx.y};
+            gv(Rk, row, s) = rk;
+            acc_add(acc[s], d, d);
+            acc_add(acc[S + s], rk, rk);
           }
-          n_s = c2.y;
+          ns = nc;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
             xs[s] = xc[s];
@@ -567,8 +657,11 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
           }
         }
         fence_async_global();
-        cl_reduce<T, 2 * S>(cl, acc, sh, buf);
-        if (threadIdx.x == 0) {
+        T v[2 * S];
+#pragma unroll
+        for (int i = 0; i < 2 * S; ++i) v[i] = acc_val(acc[i]);
+        cl_reduce<T, 2 * S>(cl, v, sh, buf);
+        if (tid == 0) {
           bool go = false;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
@@ -583,42 +676,39 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
       }
       int it = 0;
       if (sh.go) {
-        // ---- P = R; B^ P and the Gram matrices of (P, B^ P, R) -------------------
-        T acc[NV];
+        // ---- P = R; B^ P and the Gram matrices of (P, B^ P, R) --------------------
+        A acc[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) acc[v] = T(0);
+        for (int v = 0; v < NV; ++v) acc_zero(acc[v]);
         T* const Rk = cur ? R1g : R0g;
         T* const Pk = cur ? P1g : P0g;
-        T rs[S], rc[S], rnx[S];
+        V rs[S], rc[S], rnx[S];
 #pragma unroll
         for (int s = 0; s < S; ++s) {
-          rs[s] = el(Rk, r0 - 1, s);
-          rc[s] = el(Rk, r0, s);
+          rs[s] = gv(Rk, r0 - 1, s);
+          rc[s] = gv(Rk, r0, s);
         }
-        T n_s = cfc[(long)(r0 - 1) * PITCH].y;
+        V ns, e_s;
+        ld_cf_pair(cfc + (long)(r0 - 1) * PITCH, e_s, ns);
 #pragma unroll 1
         for (int i = 0; i < RB; ++i) {
           const int row = r0 + i;
-          const T2 c2 = cfc[(long)row * PITCH];
-          const T ew = col > 0 ? cfc[(long)row * PITCH - 1].x : T(0);
-          T z[S];
+          V ec, nc;
+          ld_cf_pair(cfc + (long)row * PITCH, ec, nc);
+          const V ew{has_w ? cfc[(long)row * PITCH - 1].x : T(0), ec.x};
+          V z[S];
 #pragma unroll
-          for (int s = 0; s < S; ++s) rnx[s] = el(Rk, row + 1, s);
+          for (int s = 0; s < S; ++s) rnx[s] = gv(Rk, row + 1, s);
 #pragma unroll
           for (int s = 0; s < S; ++s) {
-            const T* rr_ = rowp(Rk, row) + (size_t)s * PITCH + col;
-            const T rw = col > 0 ? rr_[-1] : T(0);
-            const T re = col + 1 < PITCH ? rr_[1] : T(0);
-            T zz = rc[s];
-            zz += c2.x * re;
-            zz += ew * rw;
-            zz += c2.y * rnx[s];
-            zz += n_s * rs[s];
-            z[s] = zz;
-            el(Pk, row, s) = rc[s];
+            const T* rr_ = rowp(Rk, row) + (size_t)s * PITCH + c0;
+            const T rw = has_w ? rr_[-1] : T(0);
+            const T re = has_e ? rr_[2] : T(0);
+            z[s] = stencil(rc[s], rw, re, rnx[s], rs[s], ec, ew, nc, ns);
+            gv(Pk, row, s) = rc[s];
           }
-          add_grams<T, S, SM>(acc, rc, z, rc);
-          n_s = c2.y;
+          add_grams<S, SM>(acc, rc, z, rc);
+          ns = nc;
 #pragma unroll
           for (int s = 0; s < S; ++s) {
             rs[s] = rc[s];
@@ -626,7 +716,7 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
           }
         }
         fence_async_global();
-        cl_reduce<T, NV>(cl, acc, sh, buf);
+        reduce(acc);
         if (wid == 0) block_coefficients<T, S>(thr, sh);
         __syncthreads();
       }
@@ -663,12 +753,16 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
     // ---- x = X^ / sqrt(c), own rows ---------------------------------------------------
     for (int i = 0; i < RB; ++i) {
       const int row = r0 + i;
-      if (col < mx && row < my) {
-        const int k = row * mx + col;
-        const T isq = sc[(long)row * PITCH + plane];
-        for (int s = 0; s < ncols; ++s) {
-          const T v = el(Xg, row, s) * isq;
-          const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys0 + s);
+      if (row >= my) continue;
+      for (int s = 0; s < ncols; ++s) {
+        const V xv = gv(Xg, row, s);
+        const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys0 + s);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int col = c0 + h;
+          if (col >= mx) continue;
+          const T v = (h ? xv.y : xv.x) * sc[(long)row * PITCH + plane + h];
+          const long k = (long)row * mx + col;
           if (a.out.y_f64)
             static_cast<double*>(a.out.y)[oy + k] = (double)v;
           else
@@ -678,23 +772,25 @@ __global__ void __launch_bounds__(PITCH, 1) k_bcg(Args ba) {
     }
     cl.sync();   // the neighbours' last reads of our rows are done before the next block
   }
-  if (threadIdx.x == 0 && crank == 0) {
+  if (tid == 0 && crank == 0) {
     if (my_iters) atomicAdd(a.iters, my_iters);
   }
-  if (threadIdx.x == 0 && my_status) atomicOr(a.status, my_status);
+  if (tid == 0 && my_status) atomicOr(a.status, my_status);
 }
 
 struct Variant {
   const void* fn;
   size_t smem;
   int S, pitch, rb;
+  int threads;   // pitch / 2: two grid columns per thread
 };
 Variant variant_f32(int pitch);
 Variant variant_f64(int pitch);
 
 template <typename T, int S, int PITCH, int RB>
 Variant make_variant() {
-  return Variant{(const void*)k_bcg<T, S, PITCH, RB>, sizeof(Smem<T, S, PITCH>), S, PITCH, RB};
+  return Variant{(const void*)k_bcg<T, S, PITCH, RB>, sizeof(Smem<T, S, PITCH>), S, PITCH, RB,
+                 PITCH / 2};
 }
 
 }  // namespace bk

@@ -10,7 +10,7 @@ Variant variant_f64(int pitch) {
     case 64: return make_variant<double, 4, 64, 32>();
     case 128: return make_variant<double, 4, 128, 32>();
     case 256: return make_variant<double, 4, 256, 32>();
-    default: return Variant{nullptr, 0, 0, 0, 0};
+    default: return Variant{nullptr, 0, 0, 0, 0, 0};
   }
 }
 
