@@ -127,13 +127,29 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    cluster per system) where the grid allows it (at most
  *                    512 columns and 512 rows in FP32, 256 rows in FP64);
  *                    2 always uses the kernel with its Krylov vectors in
- *                    global memory.
- * Results do not depend on these settings beyond rounding. */
+ *                    global memory;
+ *   "krylov_block":  0 (default) or 4: propagations of two or more systems
+ *                    without a source on symmetric 5-point operators (at
+ *                    most 512 columns in FP32, 256 in FP64, 512 rows) solve
+ *                    every step by block conjugate gradients over groups of
+ *                    four consecutive systems (the paper's Sec. 2.2 remark
+ *                    that the R + p sketch vectors can be propagated
+ *                    together; one block Krylov space per group, fewer
+ *                    iterations than four separate solves, block vectors in
+ *                    a device workspace of the operator);
+ *   "krylov_block_clusters": clusters in flight of the block CG (0 =
+ *                    automatic: workspaces within 96 MB).
+ * Results do not depend on these settings beyond rounding (the block
+ * solver stops every system on the same residual test as the others). */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);
 /* lrp_get_param reads the parameters above and, read-only, the launch shape
  * of the last on-chip CG launch of the context: "krylov_onchip_rows" (grid
  * rows per thread), "krylov_onchip_cs" (CTAs per cluster) and
- * "krylov_onchip_clusters" (clusters in flight); 0 before the first one. */
+ * "krylov_onchip_clusters" (clusters in flight); of the last 2D propagation,
+ * whether it ran on the block CG: "krylov_block_last_systems" (systems per
+ * block, 0 when it did not), "krylov_block_last_cs" (CTAs per cluster),
+ * "krylov_block_last_clusters" (clusters in flight); 0 before the first
+ * one.  A bounded wait of the block CG that expires returns LRP_ETIMEOUT. */
 lrp_status lrp_get_param(lrp_ctx* ctx, const char* name, int* value);
 
 /* Per-kernel timing with CUDA events recorded around every launch of the
