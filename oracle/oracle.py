@@ -212,7 +212,9 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
 
     g: (Q, n) spatial source profiles or None (linear part F').
     cvals: (M, Q) shared by all rows, or (nvec, M, Q) per row: c_q at the end
-    of each step.  adjoint=True applies F'^* (no source allowed).
+    of each step; for the SDIRK steppers (M, 2, Q) or (nvec, M, 2, Q): c_q at
+    the two stage times of each step.  adjoint=True applies F'^* (no source
+    allowed).
     intervals: for a time-dependent operator (TridiagTD), the interval of
     every row (a scalar or nvec values): row v runs steps intervals[v]*M ..
     intervals[v]*M + M - 1, and its adjoint the transposed solves of those
@@ -224,8 +226,7 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
     if nvec == 0:
         return X
     if isinstance(op, Tridiag) and op.stepper != "be":
-        assert g is None, "the SDIRK steppers are used without source"
-        return propagate_sdirk(op, dt, M, X, op.stepper, adjoint)
+        return propagate_sdirk(op, dt, M, X, op.stepper, adjoint, g, cvals)
     Q = 0
     gp = cp = None
     cstride = 0
@@ -275,26 +276,40 @@ def sdirk_tableau(scheme: str):
 
 
 def propagate_sdirk(op: Tridiag, dt: float, M: int, X: np.ndarray, scheme: str,
-                    adjoint: bool = False) -> np.ndarray:
-    """M steps of a two-stage SDIRK method for u' = -A u on every row of X:
-    (I + a_ii dt A) K_i = -A (u + dt sum_{j<i} a_ij K_j),  u <- u + dt sum_i b_i K_i.
-    The step map is R(-dt A) (R the stability function), so the adjoint is the
-    same scheme with A^T."""
+                    adjoint: bool = False, g: Optional[np.ndarray] = None,
+                    cvals: Optional[np.ndarray] = None) -> np.ndarray:
+    """M steps of a two-stage SDIRK method for u' = -A u + f(t) on every row of X:
+    (I + a_ii dt A) K_i = -A (u + dt sum_{j<i} a_ij K_j) + f_i,
+    u <- u + dt sum_i b_i K_i, with f_i = sum_q c_q(t + c_i dt) g_q the source
+    at the stage time (cvals[..., step, i, q]).  Without a source the step map
+    is R(-dt A) (R the stability function), so the adjoint is the same scheme
+    with A^T."""
     _, At, b = sdirk_tableau(scheme)
     be = Tridiag(op.lo, op.di, op.up)
     U = np.array(X, dtype=np.float64, copy=True)
-    for _ in range(M):
+    nvec = U.shape[0]
+    if g is not None:
+        assert not adjoint, "the adjoint acts on the linear part"
+        g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+        cv = np.asarray(cvals, dtype=np.float64)
+        if cv.ndim == 3:
+            cv = np.broadcast_to(cv, (nvec,) + cv.shape)
+        assert cv.shape == (nvec, M, 2, g.shape[0]), "SDIRK sources take (M, 2, Q) stage samples"
+    for step in range(M):
         K = []
         for i in range(2):
             arg = U + dt * sum(At[i, j] * K[j] for j in range(i))
             rhs = -op.matvec(arg, adjoint)
+            if g is not None:
+                rhs = rhs + cv[:, step, i, :] @ g
             K.append(propagate(be, At[i, i] * dt, 1, rhs, adjoint))
         U = U + dt * (b[0] * K[0] + b[1] * K[1])
     return U
 
 
 def interval_cvals(c: Optional[np.ndarray], i: int, M: int) -> Optional[np.ndarray]:
-    """Source coefficients of interval i: rows i*M .. i*M+M-1 of c (N*M, Q)."""
+    """Source coefficients of interval i: rows i*M .. i*M+M-1 of c (N*M, Q), or
+    of c (N*M, 2, Q) for the SDIRK steppers (the two stage samples of a step)."""
     if c is None:
         return None
     return c[i * M:(i + 1) * M]

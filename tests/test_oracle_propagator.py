@@ -208,3 +208,70 @@ def test_sdirk_adjoint_is_transpose(orc, scheme):
     F = orc.propagate(op, dt, M, np.eye(n)).T
     Ft = orc.propagate(op, dt, M, np.eye(n), adjoint=True).T
     np.testing.assert_allclose(Ft, F.T, atol=1e-14 * np.abs(F).max())
+
+
+# ---------------------------------------------------------------------------
+# SDIRK fine steppers with a source f(t) = sum_q c_q(t) g_q, sampled at the
+# stage times t + c_i dt of every step
+# ---------------------------------------------------------------------------
+def _stage_samples(orc, scheme, fun, dt, M, t0=0.0):
+    """(M, 2, 1) samples of fun at the stage times of M steps from t0."""
+    c, _, _ = orc.sdirk_tableau(scheme)
+    t = t0 + dt * np.arange(M)
+    return np.stack([fun(t + c[0] * dt), fun(t + c[1] * dt)], axis=1)[:, :, None]
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_source_is_exact_quadrature_for_linear_forcing(orc, scheme):
+    """A = 0: u' = f(t) g, and a second-order Runge-Kutta step is a quadrature
+    rule exact for f linear in t (sum b_i = 1, sum b_i c_i = 1/2), so M steps
+    give u0 + g (alpha T + beta T^2 / 2) to rounding.  A wrong stage time or
+    weight breaks the second condition."""
+    n, M, T = 5, 7, 0.9
+    dt = T / M
+    z = np.zeros(n)
+    op = orc.Tridiag(z, z, z, stepper=scheme)
+    g = np.random.default_rng(1).standard_normal((1, n))
+    u0 = np.random.default_rng(2).standard_normal(n)
+    alpha, beta = 0.7, -2.3
+    cv = _stage_samples(orc, scheme, lambda t: alpha + beta * t, dt, M)
+    got = orc.propagate(op, dt, M, u0, g=g, cvals=cv)
+    np.testing.assert_allclose(got, u0 + g[0] * (alpha * T + beta * T * T / 2), rtol=0, atol=1e-14)
+    # a quadratic forcing is not integrated exactly (second order only)
+    cv2 = _stage_samples(orc, scheme, lambda t: t * t, dt, M)
+    got2 = orc.propagate(op, dt, M, u0, g=g, cvals=cv2)
+    assert np.abs(got2 - (u0 + g[0] * T ** 3 / 3)).max() > 1e-6
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_source_steady_state_is_a_fixed_point(orc, scheme):
+    """A constant source: the steady state u* = A^-1 g makes every stage
+    derivative vanish, so the step map leaves it unchanged."""
+    n = 40
+    op = orc.Tridiag(*W.heat1d_op(n), stepper=scheme)
+    g = np.random.default_rng(3).standard_normal((1, n))
+    u_star = np.linalg.solve(op.dense(), g[0])
+    cv = np.ones((5, 2, 1))
+    got = orc.propagate(op, 0.01, 5, u_star, g=g, cvals=cv)
+    np.testing.assert_allclose(got, u_star, rtol=1e-12, atol=1e-12 * np.abs(u_star).max())
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_source_second_order(orc, scheme):
+    """Decoupled scalar problems u' = -lam u + sin(w t) (diagonal A): the error
+    against the closed-form solution falls by ~4 when dt halves."""
+    lam = np.array([0.5, 3.0, 20.0])
+    w, T, u0 = 9.0, 1.0, np.array([1.0, -0.5, 2.0])
+    z = np.zeros(3)
+    op = orc.Tridiag(z, lam, z, stepper=scheme)
+
+    def exact(t):
+        return (np.exp(-lam * t) * u0
+                + (lam * np.sin(w * t) - w * np.cos(w * t) + w * np.exp(-lam * t)) / (lam ** 2 + w ** 2))
+
+    errs = []
+    for M in (40, 80, 160):
+        cv = _stage_samples(orc, scheme, lambda t: np.sin(w * t), T / M, M)
+        got = orc.propagate(op, T / M, M, u0, g=np.ones((1, 3)), cvals=cv)
+        errs.append(np.abs(got - exact(T)).max())
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
