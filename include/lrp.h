@@ -15,7 +15,9 @@
  *    (vector v occupies [v*n, (v+1)*n)).
  *  - Sources are separable, f(t, x) = sum_{q<Q} c_q(t) g_q(x): g is Q x n,
  *    and c holds c_q at the end of every fine step, c[(J-1)*Q + q] at
- *    t = J*dt for J = 1..N*M (fully implicit Euler samples f at t_{j+1}).
+ *    t = J*dt for J = 1..N*M (fully implicit Euler samples f at t_{j+1});
+ *    operators with an SDIRK stepper take two samples per step, at its stage
+ *    times (lrp_operator_set_stepper).
  *  - Every pointer argument may be host memory or device memory of the
  *    context's device; the library detects which.  The caller owns all
  *    buffers it passes; the library owns the handles it returns and the device
@@ -341,8 +343,15 @@ lrp_status lrp_parareal_solve(lrp_ctx* ctx, const lrp_coarse* co, const double* 
  * a21 = -1, b = (1/2, 1/2); not L-stable) and SDIRK2-L (gamma = (2-sqrt 2)/2,
  * a21 = 1 - gamma, b = (1 - gamma, gamma); L-stable), each step two solves
  * with I + gamma dt A.  SDIRK steppers: tridiagonal operators with n <= 4096
- * and f = 0 only (LRP_EINVAL otherwise); coarse handles must be built with the stepper their
- * solves use.  The allocation-free entry point always uses backward Euler. */
+ * (LRP_EINVAL otherwise).  With a source f(t, x) = sum_q c_q(t) g_q(x) an
+ * SDIRK step takes two samples of every c_q, at its stage times t + c_1 dt
+ * and t + c_2 dt (c = (1, 0) for SDIRK2, (gamma, 1) for SDIRK2-L), so that
+ * the c arrays of lrp_propagate, lrp_parareal_solve and lrp_fine_solution
+ * hold 2 Q values per fine step, c[((J - 1) * 2 + i) * Q + q] for stage i of
+ * step J; the classical comparator and the server take sources with
+ * backward-Euler steps only.  Coarse handles must be built with the stepper
+ * their solves use.  The allocation-free entry point always uses backward
+ * Euler. */
 typedef enum {
   LRP_STEP_BACKWARD_EULER = 0,
   LRP_STEP_SDIRK2 = 1,

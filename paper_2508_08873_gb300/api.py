@@ -124,8 +124,11 @@ class Operator:
         return cls.stencil5(ctx, P.mx, P.my, P.st)
 
     def set_stepper(self, stepper: str = "be"):
-        """Fine time stepper: "be" (backward Euler), "sdirk2", "sdirk2l"."""
+        """Fine time stepper: "be" (backward Euler), "sdirk2", "sdirk2l".  With
+        an SDIRK stepper a source takes two samples per fine step (its stage
+        times): c arrays gain an axis of length 2 before the last."""
         check(self.ctx.lib.lrp_operator_set_stepper(self.h, nat.STEPPERS[stepper]), self.ctx.h)
+        self.stepper = stepper
 
     def krylov_iterations(self) -> int:
         return int(self.ctx.lib.lrp_operator_krylov_iterations(self.h))
@@ -153,10 +156,21 @@ def _as_c(a):
     return a
 
 
+def _source_samples(op) -> int:
+    """Source samples per fine step: two for the SDIRK steppers."""
+    return 1 if getattr(op, "stepper", "be") == "be" else 2
+
+
+def _check_source(c, count: int):
+    if isinstance(c, np.ndarray) and c.size != count:
+        raise ValueError("source coefficients: %d values given, %d expected" % (c.size, count))
+
+
 def propagate(ctx: Context, op: Operator, dt: float, M: int, X, adjoint: bool = False,
               g=None, c=None, prec="f64", out=None):
-    """M backward-Euler steps on each row of X (nvec, n) (lrp_propagate).
-    c: (nvec, M, Q) source samples per row, or (M, Q) shared."""
+    """M fine steps on each row of X (nvec, n) (lrp_propagate).
+    c: (nvec, M, Q) source samples per row, or (M, Q) shared; with an SDIRK
+    stepper (nvec, M, 2, Q) or (M, 2, Q), the stage samples of every step."""
     X = _as_c(X)
     squeeze = False
     if isinstance(X, np.ndarray) and X.ndim == 1:
@@ -168,8 +182,10 @@ def propagate(ctx: Context, op: Operator, dt: float, M: int, X, adjoint: bool = 
         g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
         Q = g.shape[0]
         c = _as_c(c)
-        if isinstance(c, np.ndarray) and c.ndim == 2:
+        sps = _source_samples(op)
+        if isinstance(c, np.ndarray) and c.ndim == (2 if sps == 1 else 3):
             c = np.ascontiguousarray(np.broadcast_to(c, (nvec,) + c.shape))
+        _check_source(c, nvec * M * sps * Q)
     if out is None:
         out = np.empty((nvec, op.n))
     check(ctx.lib.lrp_propagate(ctx.h, op.h, float(dt), int(M), int(adjoint), nvec, ptr(X),
@@ -334,6 +350,7 @@ def parareal_solve(ctx: Context, co: Coarse, u0, g=None, c=None, K: Optional[int
         g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
         Q = g.shape[0]
         c = _as_c(c)
+        _check_source(c, N * co.M * _source_samples(co.op) * Q)
     if out is None:
         out = np.empty((N + 1, n))
     bnd = np.zeros((max(Kmax, 1), N + 1)) if bounds else None
@@ -387,6 +404,7 @@ def fine_solution(ctx: Context, op: Operator, dt: float, M: int, N: int, u0, g=N
         g = np.ascontiguousarray(np.atleast_2d(g), dtype=np.float64) if isinstance(g, np.ndarray) else g
         Q = g.shape[0]
         c = _as_c(c)
+        _check_source(c, N * M * _source_samples(op) * Q)
     if out is None:
         out = np.empty((N + 1, op.n))
     check(ctx.lib.lrp_fine_solution(ctx.h, op.h, float(dt), int(M), int(N), ptr(u0), Q, ptr(g),

@@ -510,13 +510,17 @@ StepCoef step_coefficients(int stepper) {
   return sc;
 }
 
+// Source samples per fine step: the two stage times of an SDIRK step, else
+// the step end.
+int source_samples(const Operator* op) { return (op->kind == 0 && op->stepper != 0) ? 2 : 1; }
+
 lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (op->kind == 2) return tri_td_propagate(c, op, dt, M, adjoint, nsys, prec, in, out, src);
   if (op->kind == 0 && op->stepper != 0) {
     // SDIRK fine steps: two solves with B = I + gamma dt A per step on the
-    // one-CTA-per-system kernel (sources are not supported by these steppers)
-    if (src.Q > 0) return set_err(c, LRP_EINVAL, "SDIRK steppers support f = 0 only");
+    // one-CTA-per-system kernel; a source brings two samples per step (the
+    // stage times), src.cstride counts them
     const double dtg = dt * step_coefficients(op->stepper).gamma;
     // chunks of at most 8 rows (three chunk states in registers); one CTA per
     // system while its factors fit in shared memory, else a 4-CTA cluster
@@ -744,7 +748,8 @@ lrp_status lrp_propagate(lrp_ctx* c, const lrp_operator* opc, double dt, int M, 
   lrp_status s;
   if ((s = device_view(c, x_in, vb, xin))) return s;
   if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
-  if ((s = device_view(c, cv, sizeof(double) * (size_t)nvec * M * Q, cvv))) return s;
+  const int sps = source_samples(op);
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)nvec * M * sps * Q, cvv))) return s;
   bool out_dev = is_device_ptr(x_out);
   DevBuf tmp_out;
   void* dout = x_out;
@@ -765,7 +770,7 @@ lrp_status lrp_propagate(lrp_ctx* c, const lrp_operator* opc, double dt, int M, 
   src.Q = Q;
   src.g = (const double*)gv.p;
   src.c = (const double*)cvv.p;
-  src.cstride = (long)M * Q;
+  src.cstride = (long)M * sps * Q;
   if ((s = propagate_any(c, op, dt, M, adjoint, nvec, prec == LRP_PREC_MIXED ? 1 : 0, in, o, src)))
     return s;
   if (!out_dev) {
@@ -1153,14 +1158,15 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
   if ((s = to_device(c, co->ws_u.ptr, u0, sizeof(double) * n))) return s;
   DevView gv, cvv;
   if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
-  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * Q, cvv))) return s;
+  const int sps = source_samples(co->op);
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * sps * Q, cvv))) return s;
   const int f32 = co->prec == LRP_PREC_MIXED;
   // b_i = F_i 0 for all intervals in one launch (Eq. F_n_affine)
   PropSrc src;
   src.Q = Q;
   src.g = (const double*)gv.p;
   src.c = (const double*)cvv.p;
-  src.cstride = (long)M * Q;
+  src.cstride = (long)M * sps * Q;
   int evals = 0;
   if (Q > 0) {
     PropIn zin;               // zero initial values
@@ -1263,7 +1269,7 @@ lrp_status lrp_parareal_solve(lrp_ctx* c, const lrp_coarse* coc, const double* u
       o.y_f64 = 1;
       o.ldy = n;
       PropSrc sk = src;
-      if (Q > 0) sk.c = src.c + (size_t)first * M * Q;
+      if (Q > 0) sk.c = src.c + (size_t)first * M * sps * Q;
       if ((s = propagate_any(c, op, co->dt, M, 0, N - first, 0, in, o, sk))) return s;
       if ((s = coarse_sweep_ex(c, &hv[k], dv + k, 1, 0))) return s;
     }
@@ -1316,7 +1322,8 @@ lrp_status lrp_fine_solution(lrp_ctx* c, const lrp_operator* opc, double dt, int
   if ((s = to_device(c, u.ptr, u0, sizeof(double) * n))) return s;
   DevView gv, cvv;
   if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
-  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * Q, cvv))) return s;
+  const int sps = source_samples(op);
+  if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * sps * Q, cvv))) return s;
   if (op->kind == 2 && (long)N * M > op->nJ)
     return set_err(c, LRP_EINVAL, "N * M exceeds the time grid of the operator");
   for (int i = 0; i < N; ++i) {
@@ -1330,8 +1337,8 @@ lrp_status lrp_fine_solution(lrp_ctx* c, const lrp_operator* opc, double dt, int
     PropSrc src;
     src.Q = Q;
     src.g = (const double*)gv.p;
-    src.c = Q > 0 ? (const double*)cvv.p + (size_t)i * M * Q : nullptr;
-    src.cstride = (long)M * Q;
+    src.c = Q > 0 ? (const double*)cvv.p + (size_t)i * M * sps * Q : nullptr;
+    src.cstride = (long)M * sps * Q;
     if ((s = propagate_any(c, op, dt, M, 0, 1, 0, in, o, src))) return s;
   }
   return from_device(c, u_out, u.ptr, sizeof(double) * (size_t)(N + 1) * n);
@@ -1404,6 +1411,8 @@ lrp_status lrp_parareal_solve_classical(lrp_ctx* c, const lrp_operator* opc, dou
   Operator* op = const_cast<lrp_operator*>(opc);
   if (op->kind == 2)
     return set_err(c, LRP_EINVAL, "the classical comparator takes time-invariant operators");
+  if (Q > 0 && source_samples(op) != 1)
+    return set_err(c, LRP_EINVAL, "the classical comparator takes sources with backward-Euler fine steps");
   const int n = op->n;
   const int K = std::min(K_max, N);
   const double DT = dt * M;

@@ -204,6 +204,9 @@ struct StepCoef {
   double gamma, su, s1, bu, b1, b2;
 };
 StepCoef step_coefficients(int stepper);
+// Source samples per fine step of the operator: 2 for the SDIRK steppers
+// (the stage times), else 1 (the step end).
+int source_samples(const Operator* op);
 
 // ---- tridiagonal propagator (tridiag.cu) -----------------------------------
 // m_req = 0: the default chunk size for n; else the requested rows per chunk.

@@ -461,6 +461,8 @@ lrp_status lrp_server_submit(lrp_server* S, const lrp_coarse* co, const double* 
   if (!S || !co || !u0 || !ticket || Q < 0 || K_max < 0) return LRP_EINVAL;
   if (Q > S->Qmax) return LRP_EINVAL;
   if (Q > 0 && (!g || !c)) return LRP_EINVAL;
+  if (Q > 0 && source_samples(co->op) != 1)
+    return set_err(S->ctx, LRP_EINVAL, "served requests take sources with backward-Euler fine steps");
   if (co->op->ctx->device != S->ctx->device) return LRP_EINVAL;
   auto r = std::make_unique<Request>();
   Coarse* cc = const_cast<lrp_coarse*>(co);

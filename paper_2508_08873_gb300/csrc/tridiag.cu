@@ -269,16 +269,33 @@ __global__ void __launch_bounds__(512) k_tri_propagate(TriKArgs a) {
         }
         solve(x);
       } else {
-        // two-stage SDIRK, both stages with the same matrix (no source)
+        // two-stage SDIRK, both stages with the same matrix B = I + gamma dt A;
+        // the source of stage i, sampled at its stage time (two samples per
+        // step), enters its right-hand side as gamma dt f_i (dt here is the
+        // plan's gamma dt)
+        auto add_source = [&](int stage) {
+          if (!csys) return;
+          for (int q = 0; q < a.src.Q; ++q) {
+            T cq_ = dt * (T)csys[((size_t)j * 2 + stage) * a.src.Q + q];
+            const double* gq = gsys + (size_t)q * n;
+#pragma unroll
+            for (int i = 0; i < MM; ++i) {
+              int r = r0 + i;
+              if (r < n) x[i] += cq_ * (T)gq[r];
+            }
+          }
+        };
         T u[MM], u1[MM];
 #pragma unroll
         for (int i = 0; i < MM; ++i) u[i] = x[i];
+        add_source(0);
         solve(x);
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
           u1[i] = x[i];
           x[i] = (T)a.su * u[i] + (T)a.s1 * x[i];
         }
+        add_source(1);
         solve(x);
 #pragma unroll
         for (int i = 0; i < MM; ++i) x[i] = (T)a.bu * u[i] + (T)a.b1 * u1[i] + (T)a.b2 * x[i];

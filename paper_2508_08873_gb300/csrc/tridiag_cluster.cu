@@ -438,12 +438,29 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
         }
         solve(x);
       } else {
-        // two-stage SDIRK, both stages with the same matrix (no source)
+        // two-stage SDIRK, both stages with the same matrix B = I + gamma dt A;
+        // the source of stage i, sampled at its stage time (two samples per
+        // step), enters its right-hand side as gamma dt f_i (dt here is the
+        // plan's gamma dt)
+        auto add_source = [&](int stage) {
+#pragma unroll
+          for (int s = 0; s < SPT; ++s) {
+            if (!csys[s]) continue;
+            for (int q = 0; q < a.src.Q; ++q) {
+              T cq_ = dt * (T)csys[s][((size_t)j * 2 + stage) * a.src.Q + q];
+              const double* gq = gsys[s] + (size_t)q * n;
+#pragma unroll
+              for (int i = 0; i < MM; ++i)
+                if (r0 + i < n) x[s][i] += cq_ * (T)gq[r0 + i];
+            }
+          }
+        };
         T u[SPT][MM], u1[SPT][MM];
 #pragma unroll
         for (int s = 0; s < SPT; ++s)
 #pragma unroll
           for (int i = 0; i < MM; ++i) u[s][i] = x[s][i];
+        add_source(0);
         solve(x);
 #pragma unroll
         for (int s = 0; s < SPT; ++s)
@@ -452,6 +469,7 @@ __global__ void __launch_bounds__(256) k_tri_cluster(ClKArgs a) {
             u1[s][i] = x[s][i];
             x[s][i] = (T)a.su * u[s][i] + (T)a.s1 * x[s][i];
           }
+        add_source(1);
         solve(x);
 #pragma unroll
         for (int s = 0; s < SPT; ++s)

@@ -757,8 +757,8 @@ def test_sdirk_propagate_parity(ctx, orc, scheme, n):
         assert max(rel(got[v], want[v]) for v in range(5)) <= tol
         got32 = api.propagate(ctx, op, dt, M, X[:2], adjoint=adjoint, prec="mixed")
         assert max(rel(got32[v], want[v]) for v in range(2)) <= 5e-5
-    # the steppers take no source
-    with pytest.raises(_native.LrpError):
+    # a source takes two samples per step with these steppers
+    with pytest.raises(ValueError):
         api.propagate(ctx, op, dt, M, X[:1], g=np.ones((1, n)), c=np.ones((M, 1)))
 
 
@@ -781,3 +781,63 @@ def test_sdirk2l_build_and_parareal(ctx, orc):
     res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, K=2)
     u2, _ = api.parareal_solve(ctx, co, P.u0, K=2)
     assert rel(u2, res.iterates[-1]) <= 1e-10
+
+
+def _stage_samples(orc, scheme, fun, dt, J0, M):
+    """(M, 2, Q) samples of fun (returning Q values per time) at the stage times
+    of fine steps J0 .. J0 + M - 1."""
+    cst, _, _ = orc.sdirk_tableau(scheme)
+    t = dt * (J0 + np.arange(M))
+    return np.stack([fun(t + cst[0] * dt), fun(t + cst[1] * dt)], axis=1)
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+@pytest.mark.parametrize("n", [200, 4095])
+def test_sdirk_source_propagate_parity(ctx, orc, scheme, n):
+    """SDIRK steps with a source sampled at the stage times, per-row samples,
+    on the one-CTA-per-system kernel (n = 200) and the 4-CTA cluster kernel
+    (n = 4095), FP64 and FP32."""
+    lo, di, up = W.adr1d_op(n)
+    dt, M, Q = 1.0 / 16384, 9, 2
+    op = api.Operator.tridiag(ctx, lo, di, up)
+    op.set_stepper(scheme)
+    oop = orc.Tridiag(lo, di, up, stepper=scheme)
+    rng = np.random.default_rng(n + 5)
+    X = rng.standard_normal((4, n))
+    g = rng.standard_normal((Q, n))
+    c = np.stack([_stage_samples(orc, scheme, lambda t, k=k: np.stack(
+        [np.sin((3 + k) * 7 * t), np.cos((2 + k) * 5 * t)], axis=-1), dt, 11 * k, M) for k in range(4)])
+    cond = 1 + 2 * dt * np.max(np.abs(lo) + np.abs(di) + np.abs(up))
+    tol = max(1e-12, 8 * M * cond * 2.2e-16)
+    got = api.propagate(ctx, op, dt, M, X, g=g, c=c)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=c)
+    assert max(rel(got[v], want[v]) for v in range(4)) <= tol
+    got32 = api.propagate(ctx, op, dt, M, X[:2], g=g, c=c[:2], prec="mixed")
+    assert max(rel(got32[v], want[v]) for v in range(2)) <= 5e-5
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_source_parareal_matches_oracle(ctx, orc, scheme):
+    """Experiment 1's source on the heat1d operator with an SDIRK fine solver:
+    K = N reproduces the oracle's sequential solution, K = 2 the oracle's
+    Parareal iterate, and the fine solution equals the oracle's."""
+    P = W.heat1d(n=127, N=6, M=16, R=5, p=3)
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    op.set_stepper(scheme)
+    oop = orc.Tridiag(P.lo, P.di, P.up, stepper=scheme)
+    # f(t, x) = sin(2 pi t) g(x) (the heat1d source) at the stage times
+    c = _stage_samples(orc, scheme, lambda t: np.sin(2 * np.pi * t)[:, None], P.dt, 0, P.N * P.M)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0, P.g, c)
+    u, _ = api.parareal_solve(ctx, co, P.u0, P.g, c, K=P.N)
+    assert orc.rel_err(u, ref) <= 1e-10
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, P.g, c, K=2)
+    u2, _ = api.parareal_solve(ctx, co, P.u0, P.g, c, K=2)
+    assert rel(u2, res.iterates[-1]) <= 1e-10
+    uf = api.fine_solution(ctx, op, P.dt, P.M, P.N, P.u0, P.g, c)
+    assert orc.rel_err(uf, ref) <= 1e-11
+    # the comparator and the server take sources with backward Euler only
+    with pytest.raises(_native.LrpError) as ei:
+        api.parareal_solve_classical(ctx, op, P.dt, P.M, P.N, P.u0, P.g, P.c, K=1)
+    assert ei.value.status == _native.LRP_EINVAL
