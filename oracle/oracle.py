@@ -23,6 +23,7 @@ from __future__ import annotations
 import ctypes
 import math
 import os
+import dataclasses
 from dataclasses import dataclass, field
 from typing import List, Optional
 
@@ -151,7 +152,9 @@ class TridiagTD:
 @dataclass
 class Stencil5:
     """5-point A on an mx x my grid, node p = iy*mx + ix:
-    (A x)_p = C x_p + W x_{p-1} + E x_{p+1} + S x_{p-mx} + N x_{p+mx}."""
+    (A x)_p = C x_p + W x_{p-1} + E x_{p+1} + S x_{p-mx} + N x_{p+mx}, the
+    neighbours outside the grid absent (homogeneous Dirichlet).
+    stepper: the fine time stepper, as for Tridiag."""
     mx: int
     my: int
     C: np.ndarray
@@ -159,10 +162,31 @@ class Stencil5:
     E: np.ndarray
     S: np.ndarray
     N: np.ndarray
+    stepper: str = "be"
 
     @property
     def n(self) -> int:
         return self.mx * self.my
+
+    def matvec(self, X: np.ndarray, adjoint: bool = False) -> np.ndarray:
+        """A x (or A^T x) for every row x of X (nvec, n), written out from the
+        definition above on the (my, mx) grid."""
+        mx, my = self.mx, self.my
+        G = np.asarray(X, dtype=np.float64).reshape(-1, my, mx)
+        C, W, E, S, N = (_f64(a).reshape(my, mx) for a in (self.C, self.W, self.E, self.S, self.N))
+        Y = C * G
+        if not adjoint:
+            Y[:, :, 1:] += W[:, 1:] * G[:, :, :-1]      # west neighbour, ix > 0
+            Y[:, :, :-1] += E[:, :-1] * G[:, :, 1:]     # east neighbour, ix < mx - 1
+            Y[:, 1:, :] += S[1:, :] * G[:, :-1, :]      # south neighbour, iy > 0
+            Y[:, :-1, :] += N[:-1, :] * G[:, 1:, :]     # north neighbour, iy < my - 1
+        else:
+            # (A^T x)_p = sum_q A_qp x_q: node q = p + 1 reaches p through its W, ...
+            Y[:, :, :-1] += W[:, 1:] * G[:, :, 1:]
+            Y[:, :, 1:] += E[:, :-1] * G[:, :, :-1]
+            Y[:, :-1, :] += S[1:, :] * G[:, 1:, :]
+            Y[:, 1:, :] += N[:-1, :] * G[:, :-1, :]
+        return Y.reshape(np.asarray(X).shape)
 
     def dense_B(self, dt: float) -> np.ndarray:
         """Dense I + dt*A (tiny grids only)."""
@@ -225,7 +249,7 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
     nvec, n = X.shape
     if nvec == 0:
         return X
-    if isinstance(op, Tridiag) and op.stepper != "be":
+    if isinstance(op, (Tridiag, Stencil5)) and op.stepper != "be":
         return propagate_sdirk(op, dt, M, X, op.stepper, adjoint, g, cvals)
     Q = 0
     gp = cp = None
@@ -275,7 +299,7 @@ def sdirk_tableau(scheme: str):
     raise ValueError(scheme)
 
 
-def propagate_sdirk(op: Tridiag, dt: float, M: int, X: np.ndarray, scheme: str,
+def propagate_sdirk(op, dt: float, M: int, X: np.ndarray, scheme: str,
                     adjoint: bool = False, g: Optional[np.ndarray] = None,
                     cvals: Optional[np.ndarray] = None) -> np.ndarray:
     """M steps of a two-stage SDIRK method for u' = -A u + f(t) on every row of X:
@@ -285,7 +309,7 @@ def propagate_sdirk(op: Tridiag, dt: float, M: int, X: np.ndarray, scheme: str,
     is R(-dt A) (R the stability function), so the adjoint is the same scheme
     with A^T."""
     _, At, b = sdirk_tableau(scheme)
-    be = Tridiag(op.lo, op.di, op.up)
+    be = dataclasses.replace(op, stepper="be")   # the same A, backward-Euler solves
     U = np.array(X, dtype=np.float64, copy=True)
     nvec = U.shape[0]
     if g is not None:

@@ -275,3 +275,46 @@ def test_sdirk_source_second_order(orc, scheme):
         got = orc.propagate(op, T / M, M, u0, g=np.ones((1, 3)), cvals=cv)
         errs.append(np.abs(got - exact(T)).max())
     assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5, errs
+
+
+# ---------------------------------------------------------------------------
+# SDIRK steppers on 5-point operators (2D)
+# ---------------------------------------------------------------------------
+def _stencil(orc, st, m, scheme):
+    return orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"], stepper=scheme)
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_2d_step_is_the_stability_function(orc, scheme):
+    """Symmetric diffusion stencil A = V diag(lam) V^T: M steps apply
+    V R(-dt lam)^M V^T, R from the Butcher tableau alone."""
+    m, dt, M = 7, 0.02, 3
+    st = W.diff2d_op(m, 10.0 ** np.random.default_rng(1).uniform(0, 2, (8, 8)))
+    op = _stencil(orc, st, m, scheme)
+    A = op.dense_B(1.0) - np.eye(m * m)
+    lam, V = np.linalg.eigh(0.5 * (A + A.T))
+    R = np.array([_stability(scheme, -dt * l, orc) for l in lam])
+    F = (V * R ** M) @ V.T
+    X = np.random.default_rng(2).standard_normal((3, m * m))
+    np.testing.assert_allclose(orc.propagate(op, dt, M, X), X @ F.T, rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_2d_adjoint_is_transpose(orc, scheme):
+    """Nonsymmetric advection-diffusion stencil: F'^* = F'^T."""
+    m, dt, M = 6, 0.01, 2
+    op = _stencil(orc, W.adv2d_op(m, 0.01), m, scheme)
+    n = m * m
+    F = orc.propagate(op, dt, M, np.eye(n)).T
+    Ft = orc.propagate(op, dt, M, np.eye(n), adjoint=True).T
+    np.testing.assert_allclose(Ft, F.T, atol=1e-14 * np.abs(F).max())
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_2d_source_steady_state_is_a_fixed_point(orc, scheme):
+    m = 8
+    op = _stencil(orc, W.adv2d_op(m, 0.02), m, scheme)
+    g = np.random.default_rng(4).standard_normal((1, m * m))
+    u_star = np.linalg.solve(op.dense_B(1.0) - np.eye(m * m), g[0])
+    got = orc.propagate(op, 0.01, 4, u_star, g=g, cvals=np.ones((4, 2, 1)))
+    np.testing.assert_allclose(got, u_star, rtol=1e-12, atol=1e-12 * np.abs(u_star).max())
