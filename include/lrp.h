@@ -342,8 +342,10 @@ lrp_status lrp_parareal_solve(lrp_ctx* ctx, const lrp_coarse* co, const double* 
  * methods of Sec. 4 (effect of the time discretisation), SDIRK2 (gamma = 1,
  * a21 = -1, b = (1/2, 1/2); not L-stable) and SDIRK2-L (gamma = (2-sqrt 2)/2,
  * a21 = 1 - gamma, b = (1 - gamma, gamma); L-stable), each step two solves
- * with I + gamma dt A.  SDIRK steppers: tridiagonal operators with n <= 4096
- * (LRP_EINVAL otherwise).  With a source f(t, x) = sum_q c_q(t) g_q(x) an
+ * with I + gamma dt A.  SDIRK steppers: time-invariant tridiagonal operators
+ * with n <= 4096 and 5-point operators (their steps on the Krylov kernel with
+ * the vectors in global memory; not in batched builds); LRP_EINVAL
+ * otherwise.  With a source f(t, x) = sum_q c_q(t) g_q(x) an
  * SDIRK step takes two samples of every c_q, at its stage times t + c_1 dt
  * and t + c_2 dt (c = (1, 0) for SDIRK2, (gamma, 1) for SDIRK2-L), so that
  * the c arrays of lrp_propagate, lrp_parareal_solve and lrp_fine_solution

@@ -512,7 +512,7 @@ StepCoef step_coefficients(int stepper) {
 
 // Source samples per fine step: the two stage times of an SDIRK step, else
 // the step end.
-int source_samples(const Operator* op) { return (op->kind == 0 && op->stepper != 0) ? 2 : 1; }
+int source_samples(const Operator* op) { return op->stepper != 0 ? 2 : 1; }
 
 lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys, int prec,
                          const PropIn& in, const PropOut& out, const PropSrc& src) {
@@ -1394,8 +1394,9 @@ __global__ static void k_cls_norms(const double* __restrict__ u, const double* _
 lrp_status lrp_operator_set_stepper(lrp_operator* opc, int stepper) {
   if (!opc || stepper < LRP_STEP_BACKWARD_EULER || stepper > LRP_STEP_SDIRK2_L) return LRP_EINVAL;
   Operator* op = opc;
-  if (op->kind != 0 && stepper != LRP_STEP_BACKWARD_EULER)
-    return set_err(op->ctx, LRP_EINVAL, "SDIRK steppers are available for tridiagonal operators");
+  if (op->kind == 2 && stepper != LRP_STEP_BACKWARD_EULER)
+    return set_err(op->ctx, LRP_EINVAL,
+                   "SDIRK steppers are available for time-invariant tridiagonal and 5-point operators");
   op->stepper = stepper;
   return LRP_OK;
 }

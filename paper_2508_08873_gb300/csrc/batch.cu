@@ -73,6 +73,8 @@ lrp_status lrp_build_coarse_batch(lrp_ctx* c, int count, lrp_operator* const* op
   for (int p = 0; p < count; ++p) {
     out[p] = nullptr;
     if (!ops[p] || ops[p]->kind != 1) return set_err(c, LRP_EINVAL, "batched builds take 5-point operators");
+    if (ops[p]->stepper != 0)
+      return set_err(c, LRP_EINVAL, "batched builds take backward-Euler fine steps");
     if (ell > ops[p]->n) return set_err(c, LRP_EINVAL, "rank + oversample exceeds a dimension");
   }
   lrp_status s;

@@ -297,6 +297,11 @@ struct KryArgs {
   int mx, my, n, M, nsys, bicg;
   double dt, rtol;
   int max_iter;
+  // two-stage SDIRK steps (stepper != 0; dt is then gamma dt and B = I + gamma dt A):
+  // the combination coefficients of step_coefficients; the workspace holds two
+  // more vectors (the step's start state and first stage value)
+  int stepper;
+  double su, s1, bu, b1, b2;
   const void* B;            // [6][n + 2 mx] from element 0 of array 0 (after the pad):
                             // c, w, e, s, n, dinv (type T), zero pads of mx per side
   const void* Bs;           // CG (symmetric operators): [7][n + 2 mx], same layout: west,

@@ -177,7 +177,7 @@ __device__ __forceinline__ void for_points(int k0, int k1, Load load, Comp comp)
 
 // One system (vector `sys` of the problem described by `a`) on this cluster,
 // using the workspace `ws` (a.nvec padded vectors of n + 2 mx values).
-template <typename T>
+template <typename T, bool SD = false>   // SD: two-stage SDIRK steps
 __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_group& cl, ClRed& sh,
                                               int& buf, int sys, T* ws,
                                               unsigned long long& my_iters, int& my_status) {
@@ -201,6 +201,8 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   T* sv = vec(6);           // BiCG: s
   T* shh = vec(7);          // BiCG: D^-1 s
   T* tv = vec(8);           // BiCG: t = B D^-1 s
+  T* u0v = SD ? vec(a.bicg ? 9 : 4) : nullptr;    // SDIRK: the state at the step start
+  T* u1v = SD ? vec(a.bicg ? 10 : 5) : nullptr;   // SDIRK: the first stage value
   const T dt = (T)a.dt;
   struct St { T c0, c1, c2, c3, c4, v0, v1, v2, v3, v4; };   // stencil operands
   auto st_load = [&](int k, const T* v) {
@@ -241,16 +243,21 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
       ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
   const double* gsys = (a.src.Q > 0 && a.src.map)
       ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
-  for (int j = 0; j < a.M; ++j) {
-    // ---- right-hand side d = x + dt f, residual r = d - B x --------------
+  // one solve B x = d from the warm start x, d = au uv + a1 w1 + dt f (w1 may
+  // be null; f the source sample fj; CG: the scaled vectors of the same
+  // combination)
+  auto solve = [&](T au, const T* uv, T a1, const T* w1, int fj) {
+    // ---- right-hand side d, residual r = d - B x -------------------------
     T red3t[3] = {T(0), T(0), T(0)};    // d.d, r.r, rho
     for (int k = k0 + threadIdx.x; k < k1 && !a.bicg; k += blockDim.x) {
-      // CG: d^ = x^ / c + dt f / sqrt(c), r = p = d^ - B^ x^
+      // CG: d^ = (au u^ + a1 w1^) / c + dt f / sqrt(c), r = p = d^ - B^ x^
       T f = T(0);
       if (csys)
         for (int qq = 0; qq < a.src.Q; ++qq)
-          f += (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
-      const T d = Bs[4 * ldb + k] * x[k] + dt * Bs[5 * ldb + k] * f;
+          f += (T)csys[(size_t)fj * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
+      T dv = au * uv[k];
+      if (w1) dv += a1 * w1[k];
+      const T d = Bs[4 * ldb + k] * dv + dt * Bs[5 * ldb + k] * f;
       T bx = x[k];
       bx += Bs[k] * x[k - 1];
       bx += Bs[ldb + k] * x[k + 1];
@@ -264,10 +271,11 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
       red3t[2] += rk * rk;
     }
     for (int k = k0 + threadIdx.x; k < k1 && a.bicg; k += blockDim.x) {
-      T d = x[k];
+      T d = au * uv[k];
+      if (w1) d += a1 * w1[k];
       if (csys)
         for (int qq = 0; qq < a.src.Q; ++qq)
-          d += dt * (T)csys[(size_t)j * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
+          d += dt * (T)csys[(size_t)fj * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
       T rk = d - stencil_apply(B, ldb, mx, k, x);
       r[k] = rk;
       red3t[0] += d * d;
@@ -404,6 +412,24 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
     if (rr > tol2) my_status |= 1;
     my_iters += it;
     cl.sync();
+  };
+  for (int j = 0; j < a.M; ++j) {
+    if constexpr (!SD) {
+      solve(T(1), x, T(0), nullptr, j);        // backward Euler: d = x + dt f(t_{j+1})
+    } else {
+      // two-stage SDIRK with B = I + gamma dt A (dt here is gamma dt): stage
+      // values U1 = B^-1 (u + gamma dt f_1), U2 = B^-1 (su u + s1 U1 + gamma dt f_2),
+      // the new state bu u + b1 U1 + b2 U2 (the source at the stage times,
+      // samples 2j and 2j + 1); every point is handled by the same thread in
+      // these loops and in the right-hand side of the solves
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) u0v[k] = x[k];
+      solve(T(1), u0v, T(0), nullptr, 2 * j);
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) u1v[k] = x[k];
+      solve((T)a.su, u0v, (T)a.s1, u1v, 2 * j + 1);
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+        x[k] = (T)a.bu * u0v[k] + (T)a.b1 * u1v[k] + (T)a.b2 * x[k];
+      cl.sync();
+    }
   }
   // ---- store -----------------------------------------------------------------
   const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
@@ -417,7 +443,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   cl.sync();
 }
 
-template <typename T>
+template <typename T, bool SD = false>
 __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
   if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   cg::cluster_group cl = cg::this_cluster();
@@ -432,7 +458,7 @@ __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
   unsigned long long my_iters = 0;
   int my_status = 0;
   for (int sys = slot; sys < a.nsys; sys += nslots)
-    krylov_system<T>(a, cl, sh, buf, sys, ws, my_iters, my_status);
+    krylov_system<T, SD>(a, cl, sh, buf, sys, ws, my_iters, my_status);
   if (threadIdx.x == 0 && crank == 0) {
     if (my_iters) atomicAdd(a.iters, my_iters);
     if (my_status) atomicOr(a.status, my_status);
@@ -527,16 +553,23 @@ static int cluster_size_for(int mx, int my) {
 lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
                              int prec, const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (nsys <= 0) return LRP_OK;
+  // SDIRK steps solve with B = I + gamma dt A: the plan and the kernel's dt
+  // are gamma dt (the source of a stage enters as gamma dt f); they run on
+  // the kernel with its Krylov vectors in global memory
+  const bool sdirk = op->stepper != 0;
+  const StepCoef sc = sdirk ? step_coefficients(op->stepper) : StepCoef{1.0, 0, 0, 0, 0, 0};
+  const double dtp = sdirk ? dt * sc.gamma : dt;
   StencilPlan* plan = nullptr;
-  lrp_status s = stencil_plan(c, op, dt, adjoint, &plan);
+  lrp_status s = stencil_plan(c, op, dtp, adjoint, &plan);
   if (s) return s;
   const int bicg = op->symmetric ? 0 : 1;
-  const int nvec = (int)krylov_queue_nvec(bicg);
-  const bool block = stencil_block_applies(c, op, prec, nsys, M, src.Q);
+  const int nvec = (int)krylov_queue_nvec(bicg) + (sdirk ? 2 : 0);
+  const bool block = !sdirk && stencil_block_applies(c, op, prec, nsys, M, src.Q);
   if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
-  const bool onchip = !block && stencil_onchip_applies(c, op, prec, nsys);
+  const bool onchip = !sdirk && !block && stencil_onchip_applies(c, op, prec, nsys);
   if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
-  auto kern = prec == 0 ? (void (*)(KryArgs))k_krylov<double> : (void (*)(KryArgs))k_krylov<float>;
+  auto kern = prec == 0 ? (sdirk ? (void (*)(KryArgs))k_krylov<double, true> : (void (*)(KryArgs))k_krylov<double>)
+                        : (sdirk ? (void (*)(KryArgs))k_krylov<float, true> : (void (*)(KryArgs))k_krylov<float>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e) return cuda_err(c, e, "krylov cluster attribute");
   cudaLaunchConfig_t cfg = {};
@@ -555,7 +588,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   // Krylov vectors remain L2-resident (129 MB L2).
   const int cs_max = cluster_size_for(op->mx, op->my);
   const size_t es_ = prec == 0 ? 8 : 4;
-  const size_t ws_one = (size_t)(bicg ? 9 : 4) * ((size_t)op->n + 2 * op->mx) * es_;
+  const size_t ws_one = (size_t)nvec * ((size_t)op->n + 2 * op->mx) * es_;
   const int ws_cap = (int)std::max<size_t>(1, ((size_t)96 << 20) / ws_one);
   int cs = cs_max, nclusters = 1;
   long best = -1;
@@ -587,7 +620,13 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   a.M = M;
   a.nsys = nsys;
   a.bicg = bicg;
-  a.dt = dt;
+  a.dt = dtp;
+  a.stepper = op->stepper;
+  a.su = sc.su;
+  a.s1 = sc.s1;
+  a.bu = sc.bu;
+  a.b1 = sc.b1;
+  a.b2 = sc.b2;
   a.rtol = prec == 0 ? op->rtol64 : op->rtol32;
   a.max_iter = op->max_iter;
   a.B = stencil_B(plan, op, prec);

@@ -196,3 +196,74 @@ def test_batched_uneven_at_config_sizes(ctx, orc):
     for P, u in zip(Ps, outs):
         if P.mx in refs:
             assert orc.rel_err(u, refs[P.mx]) <= 1e-10, (P.mx, orc.rel_err(u, refs[P.mx]))
+
+
+# ---------------------------------------------------------------------------
+# SDIRK steppers on 5-point operators (two solves with I + gamma dt A per
+# step on the Krylov kernel with its vectors in global memory; the source at
+# the stage times)
+# ---------------------------------------------------------------------------
+def _stage_samples(orc, scheme, fun, dt, J0, M):
+    cst, _, _ = orc.sdirk_tableau(scheme)
+    t = dt * (J0 + np.arange(M))
+    return np.stack([fun(t + cst[0] * dt), fun(t + cst[1] * dt)], axis=1)
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+@pytest.mark.parametrize("kind,m", [("diff", 15), ("diff", 63), ("adv", 31), ("adv", 127)])
+def test_sdirk_2d_propagate_parity(ctx, orc, scheme, kind, m):
+    """CG (diffusion) and BiCGStab (advection-diffusion), one-CTA and cluster
+    systems, with a two-term source at the stage times and the adjoint,
+    FP64 at rtol 1e-14 within 1e-10 of the oracle; FP32 at the sketch
+    tolerance."""
+    op, oop = _ops(ctx, orc, kind, m)
+    op.set_stepper(scheme)
+    oop.stepper = scheme
+    dt, M, Q = 1.0 / 1024, 3, 2
+    rng = np.random.default_rng(3 * m + len(scheme))
+    X = rng.standard_normal((3, m * m))
+    g = rng.standard_normal((Q, m * m))
+    c = np.stack([_stage_samples(orc, scheme, lambda t, k=k: np.stack(
+        [np.sin((2 + k) * 9 * t), np.cos((1 + k) * 4 * t)], axis=-1), dt, 5 * k, M) for k in range(3)])
+    got = api.propagate(ctx, op, dt, M, X, g=g, c=c)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=c)
+    for v in range(3):
+        assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
+    gadj = api.propagate(ctx, op, dt, M, X, adjoint=True)
+    wadj = orc.propagate(oop, dt, M, X, adjoint=True)
+    for v in range(3):
+        assert rel(gadj[v], wadj[v]) <= 1e-10
+    g32 = api.propagate(ctx, op, dt, M, X[:2], g=g, c=c[:2], prec="mixed")
+    for v in range(2):
+        assert rel(g32[v], want[v]) <= 5e-4
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_sdirk_2d_build_and_parareal(ctx, orc, scheme):
+    """Low-rank Parareal with an SDIRK fine solver on the checkerboard
+    diffusion operator, with a source: the build matches the oracle's, K = 2
+    the oracle's iterate, K = N the oracle's sequential solution."""
+    P = W.diff2d(m=31, N=4, M=6, R=6, p=3)
+    op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+    op.set_krylov(1e-14, 1e-6, 20000)
+    op.set_stepper(scheme)
+    oop = orc.Stencil5(P.mx, P.my, P.st["C"], P.st["W"], P.st["E"], P.st["S"], P.st["N"],
+                       stepper=scheme)
+    g = np.exp(-20 * np.linspace(-1, 1, P.n) ** 2)[None, :]
+    c = _stage_samples(orc, scheme, lambda t: np.sin(5 * np.pi * t)[:, None], P.dt, 0, P.N * P.M)
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    info = co.info()
+    for i in range(P.N):
+        oc = oco.intervals[i]
+        assert np.max(np.abs(info["sigma"][i, :oc.S.shape[0]] - oc.S)) <= 1e-9 * oc.sigma[0]
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0, g, c)
+    u, _ = api.parareal_solve(ctx, co, P.u0, g, c, K=P.N)
+    assert orc.rel_err(u, ref) <= 1e-10
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, g, c, K=2)
+    u2, _ = api.parareal_solve(ctx, co, P.u0, g, c, K=2)
+    assert rel(u2, res.iterates[-1]) <= 1e-10
+    # batched builds keep backward-Euler steps
+    with pytest.raises(_native.LrpError) as ei:
+        api.build_coarse_batch(ctx, [op], P.dt, P.M, P.N, P.R, P.p, 0, prec="f64")
+    assert ei.value.status == _native.LRP_EINVAL
