@@ -199,6 +199,61 @@ class Stencil5:
         return out
 
 
+@dataclass
+class Stencil5TD:
+    """Time-dependent 5-point A (Experiment 3 of Sec. 4: a conductivity that
+    varies in time): fine step J (0-based over the whole time grid) uses A_J
+    with the coefficients C_t[J], W_t[J], E_t[J], S_t[J], N_t[J] (each
+    mx*my values, as in Stencil5).  The fine solver of interval i runs steps
+    i*M .. i*M + M - 1."""
+    mx: int
+    my: int
+    C_t: np.ndarray
+    W_t: np.ndarray
+    E_t: np.ndarray
+    S_t: np.ndarray
+    N_t: np.ndarray
+
+    @property
+    def n(self) -> int:
+        return self.mx * self.my
+
+    @property
+    def steps(self) -> int:
+        return self.C_t.shape[0]
+
+    def step(self, J: int) -> Stencil5:
+        """The time-invariant operator A_J."""
+        return Stencil5(self.mx, self.my, self.C_t[J], self.W_t[J], self.E_t[J], self.S_t[J],
+                        self.N_t[J])
+
+
+TIME_DEPENDENT = (TridiagTD, Stencil5TD)
+
+
+def _propagate_stencil_td(op: Stencil5TD, dt, M, X, adjoint, g, cvals, intervals):
+    """Backward-Euler steps with every step's own matrix, one banded solve per
+    step; the adjoint runs the transposed steps in reversed order."""
+    nvec = X.shape[0]
+    j0s = np.broadcast_to(np.asarray(intervals) * M, (nvec,))
+    if g is not None:
+        cv = _f64(cvals)
+        if cv.ndim == 2:
+            cv = np.broadcast_to(cv, (nvec,) + cv.shape)
+    for v in range(nvec):
+        J0 = int(j0s[v])
+        if J0 < 0 or J0 + M > op.steps:
+            raise ValueError("time-dependent operator: steps beyond its time grid")
+        order = range(M - 1, -1, -1) if adjoint else range(M)
+        for j in order:
+            A_J = op.step(J0 + j)
+            if g is None:
+                X[v] = propagate(A_J, dt, 1, X[v:v + 1], adjoint)[0]
+            else:
+                X[v] = propagate(A_J, dt, 1, X[v:v + 1], g=g, cvals=cv[v, j:j + 1])[0]
+    return X
+
+
 # ----------------------------------------------------------------------------
 # Random sketch vectors (rSVD step 1; generator: Philox4x32-10 + Box-Muller)
 # ----------------------------------------------------------------------------
@@ -239,7 +294,7 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
     of each step; for the SDIRK steppers (M, 2, Q) or (nvec, M, 2, Q): c_q at
     the two stage times of each step.  adjoint=True applies F'^* (no source
     allowed).
-    intervals: for a time-dependent operator (TridiagTD), the interval of
+    intervals: for a time-dependent operator (TridiagTD, Stencil5TD), the interval of
     every row (a scalar or nvec values): row v runs steps intervals[v]*M ..
     intervals[v]*M + M - 1, and its adjoint the transposed solves of those
     steps in reversed order."""
@@ -251,6 +306,9 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
         return X
     if isinstance(op, (Tridiag, Stencil5)) and op.stepper != "be":
         return propagate_sdirk(op, dt, M, X, op.stepper, adjoint, g, cvals)
+    if isinstance(op, Stencil5TD):
+        assert g is None or not adjoint, "the adjoint acts on the linear part only"
+        return _propagate_stencil_td(op, dt, M, X, adjoint, g, cvals, intervals)
     Q = 0
     gp = cp = None
     cstride = 0
@@ -555,7 +613,7 @@ def exact_coarse(op, dt, M, N, R) -> Coarse:
         Uf, s, Vf = jacobi_svd(Fp)
         return CoarseInterval(Uf[:, :R].copy(), s[:R].copy(), Vf[:, :R].copy(), s.copy(), n, n,
                               float(s[R]) if R < n else 0.0, 0)
-    if isinstance(op, TridiagTD):
+    if isinstance(op, TIME_DEPENDENT):
         return Coarse([one(i) for i in range(N)], R, 0)
     return Coarse([one(0)] * N, R, 0)
 
@@ -691,7 +749,7 @@ def coarse_be(op, dt, M, v, i, g=None, c=None) -> np.ndarray:
     """G_i v for the classical coarse solver: one backward-Euler step of size
     M*dt over interval i, the source sampled at the interval's end t_{i+1}
     (the step end, as in the fine solver)."""
-    if isinstance(op, TridiagTD):
+    if isinstance(op, TIME_DEPENDENT):
         op = op.step(i * M + M - 1)          # A at the interval's end
     if g is None:
         return propagate(op, M * dt, 1, v)

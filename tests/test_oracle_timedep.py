@@ -93,3 +93,75 @@ def test_parareal_time_dependent_K_N_full_rank_and_bounds(orc, small):
     full = orc.exact_coarse(op, P.dt, P.M, P.N, P.n)
     r1 = orc.parareal(op, P.dt, P.M, P.N, full, P.u0, P.g, P.c, K=1)
     assert orc.rel_err(r1.iterates[1], ref) <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Time-dependent 5-point operators (Experiment 3: the conductivity varies in time)
+# ---------------------------------------------------------------------------
+def _stencil_td(m, nJ, seed):
+    """A diffusion stencil whose face conductances oscillate in time, each
+    step its own coefficients (symmetric in space at every step)."""
+    rng = np.random.default_rng(seed)
+    table = 10.0 ** rng.uniform(0, 1, (8, 8))
+    out = {k: [] for k in "CWESN"}
+    for J in range(nJ):
+        st = W.diff2d_op(m, table * (1.0 + 0.5 * np.sin(0.7 * J + np.arange(64).reshape(8, 8))))
+        for k in "CWESN":
+            out[k].append(st[k])
+    return {k: np.array(v) for k, v in out.items()}
+
+
+def test_stencil_td_constant_rows_equal_time_invariant(orc):
+    m, N, M, dt = 5, 3, 2, 0.01
+    st = W.diff2d_op(m, 10.0 ** np.random.default_rng(1).uniform(0, 2, (8, 8)))
+    rep = lambda a: np.repeat(a[None, :], N * M, axis=0)
+    td = orc.Stencil5TD(m, m, *(rep(st[k]) for k in "CWESN"))
+    ti = orc.Stencil5(m, m, *(st[k] for k in "CWESN"))
+    X = np.random.default_rng(2).standard_normal((3, m * m))
+    for adj in (False, True):
+        a = orc.propagate(td, dt, M, X, adjoint=adj, intervals=[0, 1, 2])
+        b = orc.propagate(ti, dt, M, X, adjoint=adj)
+        np.testing.assert_allclose(a, b, rtol=1e-15, atol=0)
+
+
+def test_stencil_td_dense_products_and_reversed_adjoint(orc):
+    """F_i' = B_{j1}^-1 ... B_{j0}^-1 and F_i'^* = B_{j0}^-T ... B_{j1}^-T, the
+    transposed solves in reversed order (the forward order differs)."""
+    m, N, M, dt = 4, 3, 3, 0.05
+    c = _stencil_td(m, N * M, 3)
+    op = orc.Stencil5TD(m, m, c["C"], c["W"], c["E"], c["S"], c["N"])
+    n = m * m
+    X = np.random.default_rng(4).standard_normal((2, n))
+    for i in range(N):
+        Fd = np.eye(n)
+        Wd = np.eye(n)
+        for J in range(i * M, i * M + M):
+            B = op.step(J).dense_B(dt)
+            Fd = np.linalg.solve(B, Fd)
+            Wd = np.linalg.solve(B.T, Wd)
+        np.testing.assert_allclose(orc.propagate(op, dt, M, X, intervals=i), X @ Fd.T,
+                                   rtol=1e-12, atol=1e-14)
+        adj = orc.propagate(op, dt, M, X, adjoint=True, intervals=i)
+        np.testing.assert_allclose(adj, X @ Fd, rtol=1e-12, atol=1e-14)
+        assert np.abs(adj - X @ Wd.T).max() > 1e-8 * np.abs(adj).max()
+    with pytest.raises(ValueError):
+        orc.propagate(op, dt, M, X, intervals=N)
+
+
+def test_stencil_td_parareal_K_N_and_full_rank(orc):
+    m, N, M, dt = 5, 4, 3, 0.02
+    c = _stencil_td(m, N * M, 5)
+    op = orc.Stencil5TD(m, m, c["C"], c["W"], c["E"], c["S"], c["N"])
+    n = m * m
+    u0 = np.random.default_rng(6).standard_normal(n)
+    g = np.random.default_rng(7).standard_normal((1, n))
+    cv = np.sin(np.arange(N * M))[:, None]
+    ref = orc.sequential_fine(op, dt, M, N, u0, g, cv)
+    co = orc.build_coarse(op, dt, M, N, 4, 2, 0)
+    res = orc.parareal(op, dt, M, N, co, u0, g, cv, K=N)
+    scale = np.max(np.linalg.norm(ref, axis=1))
+    for k, it in enumerate(res.iterates):
+        assert np.all(np.linalg.norm(it - ref, axis=1)[:k + 1] <= 1e-13 * scale)
+    full = orc.exact_coarse(op, dt, M, N, n)
+    r1 = orc.parareal(op, dt, M, N, full, u0, g, cv, K=1)
+    assert orc.rel_err(r1.iterates[1], ref) <= 1e-12
