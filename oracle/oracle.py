@@ -131,10 +131,15 @@ class TridiagTD:
     """Time-dependent tridiagonal A (Experiment 2 of Sec. 4): fine step J
     (0-based over the whole time grid) uses A_J = A(t_{J+1}) with row i
     lo_t[J, i] x[i-1] + di_t[J, i] x[i] + up_t[J, i] x[i+1].  The fine solver
-    of interval i runs steps i*M .. i*M + M - 1."""
+    of interval i runs steps i*M .. i*M + M - 1.
+
+    stepper "sdirk2" / "sdirk2l": the rows are the operator at the two stage
+    times of every step, row 2J + s = A(t_J + c_s dt) (c from sdirk_tableau,
+    t_J = J dt the start of step J)."""
     lo_t: np.ndarray
     di_t: np.ndarray
     up_t: np.ndarray
+    stepper: str = "be"
 
     @property
     def n(self) -> int:
@@ -142,11 +147,16 @@ class TridiagTD:
 
     @property
     def steps(self) -> int:
-        return self.di_t.shape[0]
+        return self.di_t.shape[0] // (1 if self.stepper == "be" else 2)
 
     def step(self, J: int) -> Tridiag:
-        """The time-invariant operator A_J."""
+        """The time-invariant operator A_J (backward Euler)."""
         return Tridiag(self.lo_t[J], self.di_t[J], self.up_t[J])
+
+    def stage(self, J: int, s: int) -> Tridiag:
+        """A at stage time s of step J (SDIRK steppers)."""
+        r = 2 * J + s
+        return Tridiag(self.lo_t[r], self.di_t[r], self.up_t[r])
 
 
 @dataclass
@@ -213,6 +223,7 @@ class Stencil5TD:
     E_t: np.ndarray
     S_t: np.ndarray
     N_t: np.ndarray
+    stepper: str = "be"     # SDIRK: rows 2J + s = A(t_J + c_s dt), as for TridiagTD
 
     @property
     def n(self) -> int:
@@ -220,12 +231,18 @@ class Stencil5TD:
 
     @property
     def steps(self) -> int:
-        return self.C_t.shape[0]
+        return self.C_t.shape[0] // (1 if self.stepper == "be" else 2)
 
     def step(self, J: int) -> Stencil5:
-        """The time-invariant operator A_J."""
+        """The time-invariant operator A_J (backward Euler)."""
         return Stencil5(self.mx, self.my, self.C_t[J], self.W_t[J], self.E_t[J], self.S_t[J],
                         self.N_t[J])
+
+    def stage(self, J: int, s: int) -> Stencil5:
+        """A at stage time s of step J (SDIRK steppers)."""
+        r = 2 * J + s
+        return Stencil5(self.mx, self.my, self.C_t[r], self.W_t[r], self.E_t[r], self.S_t[r],
+                        self.N_t[r])
 
 
 TIME_DEPENDENT = (TridiagTD, Stencil5TD)
@@ -306,6 +323,8 @@ def propagate(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
         return X
     if isinstance(op, (Tridiag, Stencil5)) and op.stepper != "be":
         return propagate_sdirk(op, dt, M, X, op.stepper, adjoint, g, cvals)
+    if isinstance(op, TIME_DEPENDENT) and op.stepper != "be":
+        return propagate_sdirk_td(op, dt, M, X, adjoint, g, cvals, intervals)
     if isinstance(op, Stencil5TD):
         assert g is None or not adjoint, "the adjoint acts on the linear part only"
         return _propagate_stencil_td(op, dt, M, X, adjoint, g, cvals, intervals)
@@ -386,6 +405,61 @@ def propagate_sdirk(op, dt: float, M: int, X: np.ndarray, scheme: str,
                 rhs = rhs + cv[:, step, i, :] @ g
             K.append(propagate(be, At[i, i] * dt, 1, rhs, adjoint))
         U = U + dt * (b[0] * K[0] + b[1] * K[1])
+    return U
+
+
+def propagate_sdirk_td(op, dt: float, M: int, X: np.ndarray, adjoint: bool = False,
+                       g: Optional[np.ndarray] = None, cvals: Optional[np.ndarray] = None,
+                       intervals=0) -> np.ndarray:
+    """Two-stage SDIRK steps for u' = -A(t) u + f(t) with a time-dependent A
+    (TridiagTD / Stencil5TD with an SDIRK stepper): stage s of step J uses
+    A_s = A(t_J + c_s dt) and the source at the same time,
+      (I + a_ss dt A_s) K_s = -A_s (u + dt sum_{r<s} a_sr K_r) + f_s,
+      u <- u + dt (b_1 K_1 + b_2 K_2).
+    Row v runs steps intervals[v]*M .. intervals[v]*M + M - 1.  The adjoint
+    applies the transpose of every step map, S_J^T, in reversed step order:
+    with L_s = -(I + a_ss dt A_s)^-1 A_s (so that K_1 = L_1 u and
+    K_2 = L_2 (u + dt a_21 K_1)),
+      S_J^T v = v + dt b_2 w + L_1^T (dt b_1 v + dt^2 a_21 b_2 w),  w = L_2^T v,
+    where L_s^T x = -A_s^T (I + a_ss dt A_s)^-T x."""
+    _, At, b = sdirk_tableau(op.stepper)
+    U = np.array(X, dtype=np.float64, copy=True)
+    nvec = U.shape[0]
+    j0s = np.broadcast_to(np.asarray(intervals) * M, (nvec,))
+    if g is not None:
+        assert not adjoint, "the adjoint acts on the linear part"
+        g = np.atleast_2d(np.asarray(g, dtype=np.float64))
+        cv = np.asarray(cvals, dtype=np.float64)
+        if cv.ndim == 3:
+            cv = np.broadcast_to(cv, (nvec,) + cv.shape)
+        assert cv.shape == (nvec, M, 2, g.shape[0]), "SDIRK sources take (M, 2, Q) stage samples"
+
+    def solve(A_s, a, x, transposed):
+        return propagate(A_s, a * dt, 1, x[None, :], transposed)[0]
+
+    for v in range(nvec):
+        J0 = int(j0s[v])
+        if J0 < 0 or J0 + M > op.steps:
+            raise ValueError("time-dependent operator: steps beyond its time grid")
+        u = U[v]
+        for j in (range(M - 1, -1, -1) if adjoint else range(M)):
+            A1, A2 = op.stage(J0 + j, 0), op.stage(J0 + j, 1)
+            if not adjoint:
+                r1 = -A1.matvec(u[None, :])[0]
+                if g is not None:
+                    r1 = r1 + cv[v, j, 0] @ g
+                K1 = solve(A1, At[0, 0], r1, False)
+                r2 = -A2.matvec((u + dt * At[1, 0] * K1)[None, :])[0]
+                if g is not None:
+                    r2 = r2 + cv[v, j, 1] @ g
+                K2 = solve(A2, At[1, 1], r2, False)
+                u = u + dt * (b[0] * K1 + b[1] * K2)
+            else:
+                w = -A2.matvec(solve(A2, At[1, 1], u, True)[None, :], adjoint=True)[0]
+                z = dt * b[0] * u + dt * dt * At[1, 0] * b[1] * w
+                u = u + dt * b[1] * w - A1.matvec(solve(A1, At[0, 0], z, True)[None, :],
+                                                  adjoint=True)[0]
+        U[v] = u
     return U
 
 
