@@ -190,6 +190,23 @@ lrp_status lrp_operator_tridiag_td(lrp_ctx* ctx, int n, int nJ, const double* lo
 lrp_status lrp_operator_stencil5(lrp_ctx* ctx, int mx, int my, const double* C,
                                  const double* W, const double* E, const double* S,
                                  const double* N, lrp_operator** out);
+/* Time-dependent 5-point operator (Experiment 3 of Sec. 4: a conductivity
+ * that varies in time; Sec. 2: every interval its own F_n): C, W, E, S, N are
+ * nJ x (mx my) (host or device), row J holding the stencil of A(t_{J+1}) for
+ * fine step J = 0..nJ-1 of the whole time grid, each row as in
+ * lrp_operator_stencil5.  Interval i of a coarse build or Parareal solve runs
+ * steps i M .. i M + M - 1 (N M <= nJ, else LRP_EINVAL); its adjoint applies
+ * the transposed steps in reversed order.  lrp_propagate runs steps 0..M-1
+ * on every vector.  Every step is solved by Jacobi-preconditioned CG when
+ * every step's stencil is symmetric, else by BiCGStab, with the controls of
+ * lrp_operator_set_krylov.  The library keeps the step matrices of every
+ * (dt, adjoint) pair it has propagated with: 13 (n + 2 mx) nJ values in FP64
+ * and FP32 each.  nJ <= 65535 and mx my nJ <= 2^28.  The SDIRK steppers, the
+ * classical comparator and the batched builds take time-invariant operators
+ * only. */
+lrp_status lrp_operator_stencil5_td(lrp_ctx* ctx, int mx, int my, int nJ, const double* C,
+                                    const double* W, const double* E, const double* S,
+                                    const double* N, lrp_operator** out);
 void lrp_operator_free(lrp_operator* op);
 int lrp_operator_size(const lrp_operator* op);
 /* Krylov iterations spent so far by 2D propagations with this operator. */

@@ -118,6 +118,19 @@ class Operator:
         return cls(ctx, h, mx * my, "stencil5")
 
     @classmethod
+    def stencil5_td(cls, ctx: Context, mx: int, my: int, st_t: dict) -> "Operator":
+        """Time-dependent 5-point operator: st_t["C"], ... are (nJ, mx*my),
+        row J the stencil of A(t_{J+1})."""
+        arr = [np.ascontiguousarray(st_t[k], dtype=np.float64) for k in ("C", "W", "E", "S", "N")]
+        nJ = arr[0].shape[0]
+        if any(a.shape != (nJ, mx * my) for a in arr):
+            raise ValueError("stencil arrays must be (nJ, mx*my)")
+        h = ctypes.c_void_p()
+        check(ctx.lib.lrp_operator_stencil5_td(ctx.h, mx, my, nJ, *[ptr(a) for a in arr],
+                                               ctypes.byref(h)), ctx.h)
+        return cls(ctx, h, mx * my, "stencil5_td")
+
+    @classmethod
     def from_problem(cls, ctx: Context, P) -> "Operator":
         if P.kind == "tridiag":
             return cls.tridiag(ctx, P.lo, P.di, P.up)

@@ -824,7 +824,7 @@ lrp_status lrp_build_coarse_ex(lrp_ctx* c, const lrp_operator* opc, double dt, i
   Operator* op = const_cast<lrp_operator*>(opc);
   const int n = op->n;
   if (ell > n) return set_err(c, LRP_EINVAL, "rank + oversample exceeds the dimension");
-  if (op->kind == 2 && (long)N * M > op->nJ)
+  if ((op->kind == 2 || op->kind == 3) && (long)N * M > op->nJ)
     return set_err(c, LRP_EINVAL, "N * M exceeds the time grid of the operator");
   auto co = std::make_unique<lrp_coarse>();
   co->ctx = c;
@@ -1324,7 +1324,7 @@ lrp_status lrp_fine_solution(lrp_ctx* c, const lrp_operator* opc, double dt, int
   if ((s = device_view(c, g, sizeof(double) * (size_t)Q * n, gv))) return s;
   const int sps = source_samples(op);
   if ((s = device_view(c, cv, sizeof(double) * (size_t)N * M * sps * Q, cvv))) return s;
-  if (op->kind == 2 && (long)N * M > op->nJ)
+  if ((op->kind == 2 || op->kind == 3) && (long)N * M > op->nJ)
     return set_err(c, LRP_EINVAL, "N * M exceeds the time grid of the operator");
   for (int i = 0; i < N; ++i) {
     PropIn in;
@@ -1394,7 +1394,7 @@ __global__ static void k_cls_norms(const double* __restrict__ u, const double* _
 lrp_status lrp_operator_set_stepper(lrp_operator* opc, int stepper) {
   if (!opc || stepper < LRP_STEP_BACKWARD_EULER || stepper > LRP_STEP_SDIRK2_L) return LRP_EINVAL;
   Operator* op = opc;
-  if (op->kind == 2 && stepper != LRP_STEP_BACKWARD_EULER)
+  if ((op->kind == 2 || op->kind == 3) && stepper != LRP_STEP_BACKWARD_EULER)
     return set_err(op->ctx, LRP_EINVAL,
                    "SDIRK steppers are available for time-invariant tridiagonal and 5-point operators");
   op->stepper = stepper;
@@ -1410,7 +1410,7 @@ lrp_status lrp_parareal_solve_classical(lrp_ctx* c, const lrp_operator* opc, dou
   if (Q > 0 && (!g || !cv)) return LRP_EINVAL;
   cudaSetDevice(c->device);
   Operator* op = const_cast<lrp_operator*>(opc);
-  if (op->kind == 2)
+  if (op->kind == 2 || op->kind == 3)
     return set_err(c, LRP_EINVAL, "the classical comparator takes time-invariant operators");
   if (Q > 0 && source_samples(op) != 1)
     return set_err(c, LRP_EINVAL, "the classical comparator takes sources with backward-Euler fine steps");

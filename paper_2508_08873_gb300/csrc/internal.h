@@ -140,9 +140,10 @@ struct ToepCoef {
 struct Operator {
   Ctx* ctx = nullptr;
   ~Operator();
-  int kind = 0;            // 0 tridiagonal, 1 5-point stencil, 2 time-dependent tridiagonal
+  int kind = 0;            // 0 tridiagonal, 1 5-point stencil, 2 time-dependent tridiagonal,
+                           // 3 time-dependent 5-point stencil
   int n = 0, mx = 0, my = 0;
-  int nJ = 0;              // kind 2: fine steps of the time grid (a64[0..2] are nJ x n)
+  int nJ = 0;              // kinds 2, 3: fine steps of the time grid (a64[k] are nJ x n)
   // tridiagonal with constant coefficients (lo[1..n-1], di, up[0..n-2] each
   // one value): tlo, tdi, tup
   bool toeplitz = false;
@@ -302,6 +303,13 @@ struct KryArgs {
   // more vectors (the step's start state and first stage value)
   int stepper;
   double su, s1, bu, b1, b2;
+  // time-dependent operators (kind 3): the plans of the steps follow one another
+  // (B and Bs advance by b_step and bs_step elements per fine step); system s
+  // runs steps J0 .. J0 + M - 1 with J0 = interval * M (the interval from the
+  // call's system map, else interval0 + s / ncol of the input), the adjoint in
+  // reversed order
+  long b_step, bs_step;
+  int nJ, adj;
   const void* B;            // [6][n + 2 mx] from element 0 of array 0 (after the pad):
                             // c, w, e, s, n, dinv (type T), zero pads of mx per side
   const void* Bs;           // CG (symmetric operators): [7][n + 2 mx], same layout: west,

@@ -45,6 +45,11 @@ __global__ void k_stencil_plan(int mx, int my, double dt, int adj, const double*
   const size_t ld = (size_t)n + 2 * mx;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
+  // time-dependent operators: grid row J takes step J's coefficients and plan
+  const size_t J = blockIdx.y;
+  C += J * n; W += J * n; E += J * n; S += J * n; N += J * n;
+  b64 += J * 6 * ld;
+  b32 += J * 6 * ld;
   int ix = p % mx, iy = p / mx;
   double c = 1.0 + dt * C[p], w, e, s, nn;
   if (!adj) {
@@ -77,6 +82,10 @@ __global__ void k_stencil_plan_scaled(int mx, int my, const double* __restrict__
   const size_t ld = (size_t)n + 2 * mx;
   int p = blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= n) return;
+  const size_t J = blockIdx.y;   // time-dependent operators: step J
+  b64 += J * 6 * ld;
+  s64 += J * 7 * ld;
+  s32 += J * 7 * ld;
   const size_t q = (size_t)mx + p;
   const double* c = b64;
   const double cp = c[q];
@@ -177,7 +186,11 @@ __device__ __forceinline__ void for_points(int k0, int k1, Load load, Comp comp)
 
 // One system (vector `sys` of the problem described by `a`) on this cluster,
 // using the workspace `ws` (a.nvec padded vectors of n + 2 mx values).
-template <typename T, bool SD = false>   // SD: two-stage SDIRK steps
+// SD: two-stage SDIRK steps.  TD: a time-dependent operator, every fine step
+// its own plan (B, Bs advance by a.b_step, a.bs_step per step of the time
+// grid); the system runs steps J0 .. J0 + M - 1 of its interval, the
+// adjoint in reversed order.
+template <typename T, bool SD = false, bool TD = false>
 __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_group& cl, ClRed& sh,
                                               int& buf, int sys, T* ws,
                                               unsigned long long& my_iters, int& my_status) {
@@ -191,6 +204,23 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   const T* __restrict__ B = static_cast<const T*>(a.B);
   const T* __restrict__ Bd = B + 5 * ldb;             // 1 / diag (0 on the pads)
   const T* __restrict__ Bs = static_cast<const T*>(a.Bs);   // CG: scaled matrix (see KryArgs)
+  long J0 = 0;
+  if constexpr (TD) {
+    // the interval of the system (system map of the input, else of the
+    // output, else of the source; else interval0 + sys / ncol), its first step
+    const int* imap = a.in.map ? a.in.map : a.out.map ? a.out.map : a.src.map;
+    const int interval = imap ? imap[2 * sys + 1] : a.in.interval0 + sys / a.in.ncol;
+    J0 = (long)interval * a.M;
+    if (J0 < 0 || J0 + a.M > a.nJ) return;    // outside the time grid (checked on the host)
+  }
+  // TD: the plan of step j of the system (j in the order the steps run)
+  auto set_step = [&](int j) {
+    const long J = a.adj ? J0 + a.M - 1 - j : J0 + j;
+    B = static_cast<const T*>(a.B) + J * a.b_step;
+    Bd = B + 5 * ldb;
+    if (a.Bs) Bs = static_cast<const T*>(a.Bs) + J * a.bs_step;
+  };
+  if constexpr (TD) set_step(0);
   auto vec = [&](int v) { return ws + (size_t)v * ldv + mx; };
   T* x = vec(0);
   T* r = vec(1);
@@ -414,6 +444,18 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
     cl.sync();
   };
   for (int j = 0; j < a.M; ++j) {
+    if constexpr (TD) {
+      if (j > 0) {
+        // CG iterates in x^ = S_J x: rescale from the previous step's S
+        const T* Bp = Bs;
+        set_step(j);
+        if (!a.bicg) {
+          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+            x[k] = x[k] * Bp[5 * ldb + k] * Bs[6 * ldb + k];
+          cl.sync();                             // the stencil reads neighbours' points
+        }
+      }
+    }
     if constexpr (!SD) {
       solve(T(1), x, T(0), nullptr, j);        // backward Euler: d = x + dt f(t_{j+1})
     } else {
@@ -443,7 +485,7 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
   cl.sync();
 }
 
-template <typename T, bool SD = false>
+template <typename T, bool SD = false, bool TD = false>
 __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
   if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
   cg::cluster_group cl = cg::this_cluster();
@@ -458,7 +500,7 @@ __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
   unsigned long long my_iters = 0;
   int my_status = 0;
   for (int sys = slot; sys < a.nsys; sys += nslots)
-    krylov_system<T, SD>(a, cl, sh, buf, sys, ws, my_iters, my_status);
+    krylov_system<T, SD, TD>(a, cl, sh, buf, sys, ws, my_iters, my_status);
   if (threadIdx.x == 0 && crank == 0) {
     if (my_iters) atomicAdd(a.iters, my_iters);
     if (my_status) atomicOr(a.status, my_status);
@@ -517,22 +559,25 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
   pl->adjoint = adjoint;
   lrp_status s;
   const size_t ld = (size_t)op->n + 2 * op->mx;
-  if ((s = dev_alloc(op->ctx, pl->b64, sizeof(double) * 6 * ld))) return s;
-  if ((s = dev_alloc(op->ctx, pl->b32, sizeof(float) * 6 * ld))) return s;
+  // time-dependent operators: one plan per fine step of the time grid, back to back
+  const size_t steps = op->kind == 3 ? (size_t)op->nJ : 1;
+  if ((s = dev_alloc(op->ctx, pl->b64, sizeof(double) * 6 * ld * steps))) return s;
+  if ((s = dev_alloc(op->ctx, pl->b32, sizeof(float) * 6 * ld * steps))) return s;
   cudaMemsetAsync(pl->b64.ptr, 0, pl->b64.bytes, c->stream);
   cudaMemsetAsync(pl->b32.ptr, 0, pl->b32.bytes, c->stream);
-  k_stencil_plan<<<(op->n + 255) / 256, 256, 0, c->stream>>>(
+  const dim3 pgrid((op->n + 255) / 256, (unsigned)steps);
+  k_stencil_plan<<<pgrid, 256, 0, c->stream>>>(
       op->mx, op->my, dt, adjoint, op->a64[0].as<double>(), op->a64[1].as<double>(),
       op->a64[2].as<double>(), op->a64[3].as<double>(), op->a64[4].as<double>(),
       pl->b64.as<double>(), pl->b32.as<float>());
   cudaError_t e = cudaGetLastError();
   if (e) return cuda_err(c, e, "k_stencil_plan");
   if (op->symmetric) {
-    if ((s = dev_alloc(op->ctx, pl->bs64, sizeof(double) * 7 * ld))) return s;
-    if ((s = dev_alloc(op->ctx, pl->bs32, sizeof(float) * 7 * ld))) return s;
+    if ((s = dev_alloc(op->ctx, pl->bs64, sizeof(double) * 7 * ld * steps))) return s;
+    if ((s = dev_alloc(op->ctx, pl->bs32, sizeof(float) * 7 * ld * steps))) return s;
     cudaMemsetAsync(pl->bs64.ptr, 0, pl->bs64.bytes, c->stream);
     cudaMemsetAsync(pl->bs32.ptr, 0, pl->bs32.bytes, c->stream);
-    k_stencil_plan_scaled<<<(op->n + 255) / 256, 256, 0, c->stream>>>(
+    k_stencil_plan_scaled<<<pgrid, 256, 0, c->stream>>>(
         op->mx, op->my, pl->b64.as<double>(), pl->bs64.as<double>(), pl->bs32.as<float>());
     e = cudaGetLastError();
     if (e) return cuda_err(c, e, "k_stencil_plan_scaled");
@@ -564,12 +609,25 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   if (s) return s;
   const int bicg = op->symmetric ? 0 : 1;
   const int nvec = (int)krylov_queue_nvec(bicg) + (sdirk ? 2 : 0);
-  const bool block = !sdirk && stencil_block_applies(c, op, prec, nsys, M, src.Q);
+  // time-dependent operators (kind 3) run on the kernel with its vectors in
+  // global memory, every step on its own plan
+  const bool td = op->kind == 3;
+  if (td && adjoint && src.Q > 0) return set_err(c, LRP_EINVAL, "the adjoint acts on the linear part");
+  if (td && !in.map && !out.map && !src.map) {
+    const long last = (long)in.interval0 + (long)(nsys - 1) / std::max(in.ncol, 1);
+    if (in.interval0 < 0 || (last + 1) * M > op->nJ)
+      return set_err(c, LRP_EINVAL, "time-dependent operator: steps beyond its time grid");
+  }
+  const bool block = !sdirk && !td && stencil_block_applies(c, op, prec, nsys, M, src.Q);
   if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
-  const bool onchip = !sdirk && !block && stencil_onchip_applies(c, op, prec, nsys);
+  const bool onchip = !sdirk && !td && !block && stencil_onchip_applies(c, op, prec, nsys);
   if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
-  auto kern = prec == 0 ? (sdirk ? (void (*)(KryArgs))k_krylov<double, true> : (void (*)(KryArgs))k_krylov<double>)
-                        : (sdirk ? (void (*)(KryArgs))k_krylov<float, true> : (void (*)(KryArgs))k_krylov<float>);
+  auto kern = prec == 0 ? (sdirk ? (void (*)(KryArgs))k_krylov<double, true>
+                           : td ? (void (*)(KryArgs))k_krylov<double, false, true>
+                                : (void (*)(KryArgs))k_krylov<double>)
+                        : (sdirk ? (void (*)(KryArgs))k_krylov<float, true>
+                           : td ? (void (*)(KryArgs))k_krylov<float, false, true>
+                                : (void (*)(KryArgs))k_krylov<float>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e) return cuda_err(c, e, "krylov cluster attribute");
   cudaLaunchConfig_t cfg = {};
@@ -631,6 +689,12 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   a.max_iter = op->max_iter;
   a.B = stencil_B(plan, op, prec);
   a.Bs = stencil_Bs(plan, op, prec);
+  if (td) {
+    a.b_step = 6 * ((long)op->n + 2 * op->mx);
+    a.bs_step = 7 * ((long)op->n + 2 * op->mx);
+    a.nJ = op->nJ;
+    a.adj = adjoint;
+  }
   a.ws = op->kws.ptr;
   a.nvec = nvec;
   a.in = in;
@@ -764,6 +828,54 @@ extern "C" lrp_status lrp_operator_stencil5(lrp_ctx* cc, int mx, int my, const d
     int ix = p % mx, iy = p / mx;
     if (ix > 0 && h[1][p] != h[2][p - 1]) sym = false;
     if (iy > 0 && h[3][p] != h[4][p - mx]) sym = false;
+  }
+  op->symmetric = sym;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) { delete op; return cuda_err(c, e, "stencil upload"); }
+  *out = op;
+  return LRP_OK;
+}
+
+extern "C" lrp_status lrp_operator_stencil5_td(lrp_ctx* cc, int mx, int my, int nJ, const double* C,
+                                               const double* W, const double* E, const double* S,
+                                               const double* N, lrp_operator** out) {
+  Ctx* c = reinterpret_cast<Ctx*>(cc);
+  if (!c || !out || !C || !W || !E || !S || !N || mx < 1 || my < 1 || nJ < 1) return LRP_EINVAL;
+  if (nJ > 65535) return set_err(c, LRP_EINVAL, "time-dependent operators take at most 65535 steps");
+  if ((long)mx * my * nJ > (1L << 28))
+    return set_err(c, LRP_EINVAL, "time-dependent operator too large (mx my nJ > 2^28)");
+  cudaSetDevice(c->device);
+  const int n = mx * my;
+  auto* op = new lrp_operator();
+  op->ctx = c;
+  ctx_retain(c);
+  op->kind = 3;
+  op->mx = mx;
+  op->my = my;
+  op->n = n;
+  op->nJ = nJ;
+  const double* src[5] = {C, W, E, S, N};
+  const size_t cnt = (size_t)nJ * n;
+  std::vector<double> h[5];
+  for (int k = 0; k < 5; ++k) {
+    h[k].resize(cnt);
+    cudaError_t e = cudaMemcpy(h[k].data(), src[k], sizeof(double) * cnt, cudaMemcpyDefault);
+    if (e) { delete op; return cuda_err(c, e, "stencil read"); }
+    lrp_status s = dev_alloc(c, op->a64[k], sizeof(double) * cnt);
+    if (s) { delete op; return s; }
+    e = cudaMemcpyAsync(op->a64[k].ptr, h[k].data(), sizeof(double) * cnt, cudaMemcpyHostToDevice,
+                        c->stream);
+    if (e) { delete op; return cuda_err(c, e, "stencil upload"); }
+  }
+  // CG when every step's stencil is symmetric, else BiCGStab
+  bool sym = true;
+  for (size_t J = 0; J < (size_t)nJ && sym; ++J) {
+    const size_t o = J * n;
+    for (int p = 0; p < n && sym; ++p) {
+      int ix = p % mx, iy = p / mx;
+      if (ix > 0 && h[1][o + p] != h[2][o + p - 1]) sym = false;
+      if (iy > 0 && h[3][o + p] != h[4][o + p - mx]) sym = false;
+    }
   }
   op->symmetric = sym;
   cudaError_t e = cudaStreamSynchronize(c->stream);

@@ -16,7 +16,9 @@ The problems are finite-difference stand-ins for the paper's experiments
                 kappa evaluated at face midpoints;
   * adv2d       u_t = nu Lap u - b.grad u, b = (-(y-1/2), x-1/2), upwind;
   * heat_td     u_t = d/dx[(1 + 0.9 sin(7 pi t + 2 pi x)) u_x] + f with Neumann
-                conditions (Experiment 2): a time-dependent tridiagonal A.
+                conditions (Experiment 2): a time-dependent tridiagonal A;
+  * heat2d_td   u_t = div(d(x, y, t) grad u) + f on (0,1)^2 with Dirichlet
+                conditions (Experiment 3): a time-dependent 5-point A.
 Random problem data come from numpy's PCG64 seeded per problem; the Gaussian
 sketch vectors of the method are NOT drawn here.
 """
@@ -284,3 +286,56 @@ def serving_request(n: int, N: int, M: int, dt: float, index: int, data_seed: in
     c = np.stack([a[i] * np.sin(om[i] * t) for i in range(terms)], axis=1)
     u0 = bumps1d(x, rng)
     return u0, g, c
+
+
+def heat2d_td_op(m: int, N: int, M: int, T: float = 1.0) -> dict:
+    """Experiment 3's operator, -div(d grad u) with d(x, y, t) = 1 + 0.9
+    sin(7 pi t) on [0, 1/2]^2 + 0.9 cos(5 pi t) on [1/2, 1]^2 (closed
+    squares; 1 elsewhere), homogeneous Dirichlet, m x m interior nodes of
+    spacing h = 1/(m+1), d at the face midpoints and at the end t_{J+1} of
+    every fine step J = 0..N*M-1.  Returns C, W, E, S, N, each (N*M, m*m):
+    row J holds the stencil of A(t_{J+1})."""
+    h = 1.0 / (m + 1)
+    dt = T / (N * M)
+    t = fine_times(N, M, dt)
+    xn = (np.arange(m) + 1) * h
+    XN, YN = np.meshgrid(xn, xn, indexing="xy")
+    sw = lambda xx, yy: ((xx <= 0.5) & (yy <= 0.5)).astype(np.float64)
+    ne = lambda xx, yy: ((xx >= 0.5) & (yy >= 0.5)).astype(np.float64)
+    faces = dict(E=(XN + 0.5 * h, YN), W=(XN - 0.5 * h, YN), N=(XN, YN + 0.5 * h),
+                 S=(XN, YN - 0.5 * h))
+    ih2 = 1.0 / h ** 2
+    out = {}
+    for k, (xx, yy) in faces.items():
+        a = sw(xx, yy).ravel()
+        b = ne(xx, yy).ravel()
+        d = 1.0 + 0.9 * np.sin(7 * np.pi * t)[:, None] * a[None, :] + \
+            0.9 * np.cos(5 * np.pi * t)[:, None] * b[None, :]
+        out[k] = -d * ih2
+    ix = np.tile(np.arange(m), m)
+    iy = np.repeat(np.arange(m), m)
+    C = -(out["E"] + out["W"] + out["N"] + out["S"])
+    out["W"][:, ix == 0] = 0.0
+    out["E"][:, ix == m - 1] = 0.0
+    out["S"][:, iy == 0] = 0.0
+    out["N"][:, iy == m - 1] = 0.0
+    out["C"] = C
+    return {k: np.ascontiguousarray(out[k]) for k in ("C", "W", "E", "S", "N")}
+
+
+def heat2d_td(m: int = 99, N: int = 10, M: int = 10, R: int = 6, p: int = 1, seed: int = 0,
+              T: float = 1.0) -> Problem:
+    """Experiment 3 stand-in: 2D heat equation with the conductivity of
+    heat2d_td_op, f = 100 sin(5 pi t)(1 + cos(3 pi x))(1 + sin(4 pi y)) (one
+    separable term), u0 = 10 on [0.6, 0.8]^2 and 0 elsewhere; m = 99 (h =
+    0.01, the paper's 100 x 100 mesh), N = 10 intervals of M = 10 steps on
+    [0, 1], R = 6, p = 1.  The operator arrays (N*M, m*m) are in st_t
+    (kind "stencil5_td")."""
+    st_t = heat2d_td_op(m, N, M, T)
+    h, X, Y = _grid(m)
+    dt = T / (N * M)
+    g = (100.0 * (1.0 + np.cos(3 * np.pi * X)) * (1.0 + np.sin(4 * np.pi * Y)))[None, :]
+    c = np.sin(5 * np.pi * fine_times(N, M, dt))[:, None]
+    u0 = 10.0 * ((X >= 0.6) & (X <= 0.8) & (Y >= 0.6) & (Y <= 0.8)).astype(np.float64)
+    return Problem("heat2d_td", "stencil5_td", m * m, dt, M, N, R, p, seed, u0, mx=m, my=m,
+                   g=g, c=c, extra=dict(st_t=st_t))
