@@ -180,8 +180,8 @@ lrp_status lrp_operator_tridiag(lrp_ctx* ctx, int n, const double* lo, const dou
  * (N M <= nJ, else LRP_EINVAL); its adjoint applies the transposed steps in
  * reversed order.  lrp_propagate runs steps 0..M-1 on every vector.  n <= 1024
  * (each step is solved by parallel cyclic reduction within one CTA).  The
- * SDIRK steppers and the classical comparator take time-invariant operators
- * only. */
+ * classical comparator takes time-invariant operators only; SDIRK steps take
+ * the stage-sampled constructor lrp_operator_tridiag_td_sdirk. */
 lrp_status lrp_operator_tridiag_td(lrp_ctx* ctx, int n, int nJ, const double* lo,
                                    const double* di, const double* up, lrp_operator** out);
 /* 5-point A on an mx x my grid of interior nodes, node p = iy*mx + ix:
@@ -201,9 +201,10 @@ lrp_status lrp_operator_stencil5(lrp_ctx* ctx, int mx, int my, const double* C,
  * every step's stencil is symmetric, else by BiCGStab, with the controls of
  * lrp_operator_set_krylov.  The library keeps the step matrices of every
  * (dt, adjoint) pair it has propagated with: 13 (n + 2 mx) nJ values in FP64
- * and FP32 each.  nJ <= 65535 and mx my nJ <= 2^28.  The SDIRK steppers, the
- * classical comparator and the batched builds take time-invariant operators
- * only. */
+ * and FP32 each.  nJ <= 65535 and mx my nJ <= 2^28.  The classical
+ * comparator and the batched builds take time-invariant operators only;
+ * SDIRK steps take the stage-sampled constructor
+ * lrp_operator_stencil5_td_sdirk. */
 lrp_status lrp_operator_stencil5_td(lrp_ctx* ctx, int mx, int my, int nJ, const double* C,
                                     const double* W, const double* E, const double* S,
                                     const double* N, lrp_operator** out);
@@ -377,6 +378,26 @@ typedef enum {
   LRP_STEP_SDIRK2_L = 2
 } lrp_stepper;
 lrp_status lrp_operator_set_stepper(lrp_operator* op, int stepper);
+
+/* SDIRK steppers on time-dependent operators (Sec. 4, effect of the time
+ * discretisation, run on Experiment 3's time-dependent operator): every
+ * stage of a step solves with the operator at its own stage time, so the
+ * coefficient arrays hold two rows per fine step, 2 nJ rows in all: row
+ * 2J + s = A(t_J + c_s dt) for stage s = 0, 1 of step J (t_J = J dt the
+ * start of step J; c = (1, 0) for SDIRK2, (gamma, 1) for SDIRK2-L), each row
+ * laid out as in lrp_operator_tridiag_td / lrp_operator_stencil5_td.
+ * stepper: LRP_STEP_SDIRK2 or LRP_STEP_SDIRK2_L (LRP_EINVAL otherwise); the
+ * operator keeps it (lrp_operator_set_stepper accepts only the same one).
+ * Sources take two samples per step at the same stage times, as for
+ * time-invariant operators.  The adjoint propagation applies the transpose
+ * of every step map in reversed step order (stage-2 matrix first).  Limits
+ * as for the backward-Euler constructors, with 2 nJ rows in place of nJ. */
+lrp_status lrp_operator_tridiag_td_sdirk(lrp_ctx* ctx, int n, int nJ, int stepper,
+                                         const double* lo, const double* di, const double* up,
+                                         lrp_operator** out);
+lrp_status lrp_operator_stencil5_td_sdirk(lrp_ctx* ctx, int mx, int my, int nJ, int stepper,
+                                          const double* C, const double* W, const double* E,
+                                          const double* S, const double* N, lrp_operator** out);
 
 /* Classical Parareal for comparison (the method of the dashed curves in the
  * paper's numerical experiments, Sec. 4): Eq. def_Parareal with the coarse

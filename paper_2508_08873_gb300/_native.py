@@ -90,6 +90,8 @@ SIGNATURES = [
     ("lrp_operator_tridiag_td", _I, [_P, _I, _I, _P, _P, _P, _PP]),
     ("lrp_operator_stencil5", _I, [_P, _I, _I, _P, _P, _P, _P, _P, _PP]),
     ("lrp_operator_stencil5_td", _I, [_P, _I, _I, _I, _P, _P, _P, _P, _P, _PP]),
+    ("lrp_operator_tridiag_td_sdirk", _I, [_P, _I, _I, _I, _P, _P, _P, _PP]),
+    ("lrp_operator_stencil5_td_sdirk", _I, [_P, _I, _I, _I, _I, _P, _P, _P, _P, _P, _PP]),
     ("lrp_operator_free", None, [_P]),
     ("lrp_operator_size", _I, [_P]),
     ("lrp_operator_krylov_iterations", ctypes.c_ulonglong, [_P]),

@@ -101,13 +101,23 @@ class Operator:
         return cls(ctx, h, di.shape[0], "tridiag")
 
     @classmethod
-    def tridiag_td(cls, ctx: Context, lo_t, di_t, up_t) -> "Operator":
-        """Time-dependent tridiagonal operator: (nJ, n) arrays, row J = A(t_{J+1})."""
+    def tridiag_td(cls, ctx: Context, lo_t, di_t, up_t, stepper: str = "be") -> "Operator":
+        """Time-dependent tridiagonal operator: (nJ, n) arrays, row J = A(t_{J+1});
+        with an SDIRK stepper (2 nJ, n) arrays, row 2J + s = A(t_J + c_s dt)."""
         lo, di, up = (np.ascontiguousarray(a, dtype=np.float64) for a in (lo_t, di_t, up_t))
         h = ctypes.c_void_p()
-        check(ctx.lib.lrp_operator_tridiag_td(ctx.h, di.shape[1], di.shape[0], ptr(lo), ptr(di),
-                                              ptr(up), ctypes.byref(h)), ctx.h)
-        return cls(ctx, h, di.shape[1], "tridiag_td")
+        if stepper == "be":
+            check(ctx.lib.lrp_operator_tridiag_td(ctx.h, di.shape[1], di.shape[0], ptr(lo),
+                                                  ptr(di), ptr(up), ctypes.byref(h)), ctx.h)
+        else:
+            if di.shape[0] % 2:
+                raise ValueError("SDIRK operators take two coefficient rows per fine step")
+            check(ctx.lib.lrp_operator_tridiag_td_sdirk(ctx.h, di.shape[1], di.shape[0] // 2,
+                                                        nat.STEPPERS[stepper], ptr(lo), ptr(di),
+                                                        ptr(up), ctypes.byref(h)), ctx.h)
+        op = cls(ctx, h, di.shape[1], "tridiag_td")
+        op.stepper = stepper
+        return op
 
     @classmethod
     def stencil5(cls, ctx: Context, mx: int, my: int, st: dict) -> "Operator":
@@ -118,17 +128,29 @@ class Operator:
         return cls(ctx, h, mx * my, "stencil5")
 
     @classmethod
-    def stencil5_td(cls, ctx: Context, mx: int, my: int, st_t: dict) -> "Operator":
+    def stencil5_td(cls, ctx: Context, mx: int, my: int, st_t: dict,
+                    stepper: str = "be") -> "Operator":
         """Time-dependent 5-point operator: st_t["C"], ... are (nJ, mx*my),
-        row J the stencil of A(t_{J+1})."""
+        row J the stencil of A(t_{J+1}); with an SDIRK stepper (2 nJ, mx*my),
+        row 2J + s the stencil at stage time s of step J."""
         arr = [np.ascontiguousarray(st_t[k], dtype=np.float64) for k in ("C", "W", "E", "S", "N")]
-        nJ = arr[0].shape[0]
-        if any(a.shape != (nJ, mx * my) for a in arr):
-            raise ValueError("stencil arrays must be (nJ, mx*my)")
+        rows = arr[0].shape[0]
+        if any(a.shape != (rows, mx * my) for a in arr):
+            raise ValueError("stencil arrays must be (rows, mx*my)")
         h = ctypes.c_void_p()
-        check(ctx.lib.lrp_operator_stencil5_td(ctx.h, mx, my, nJ, *[ptr(a) for a in arr],
-                                               ctypes.byref(h)), ctx.h)
-        return cls(ctx, h, mx * my, "stencil5_td")
+        if stepper == "be":
+            check(ctx.lib.lrp_operator_stencil5_td(ctx.h, mx, my, rows, *[ptr(a) for a in arr],
+                                                   ctypes.byref(h)), ctx.h)
+        else:
+            if rows % 2:
+                raise ValueError("SDIRK operators take two coefficient rows per fine step")
+            check(ctx.lib.lrp_operator_stencil5_td_sdirk(ctx.h, mx, my, rows // 2,
+                                                         nat.STEPPERS[stepper],
+                                                         *[ptr(a) for a in arr],
+                                                         ctypes.byref(h)), ctx.h)
+        op = cls(ctx, h, mx * my, "stencil5_td")
+        op.stepper = stepper
+        return op
 
     @classmethod
     def from_problem(cls, ctx: Context, P) -> "Operator":

@@ -1394,9 +1394,9 @@ __global__ static void k_cls_norms(const double* __restrict__ u, const double* _
 lrp_status lrp_operator_set_stepper(lrp_operator* opc, int stepper) {
   if (!opc || stepper < LRP_STEP_BACKWARD_EULER || stepper > LRP_STEP_SDIRK2_L) return LRP_EINVAL;
   Operator* op = opc;
-  if ((op->kind == 2 || op->kind == 3) && stepper != LRP_STEP_BACKWARD_EULER)
+  if ((op->kind == 2 || op->kind == 3) && stepper != op->stepper)
     return set_err(op->ctx, LRP_EINVAL,
-                   "SDIRK steppers are available for time-invariant tridiagonal and 5-point operators");
+                   "a time-dependent operator keeps the stepper its coefficient rows were sampled for");
   op->stepper = stepper;
   return LRP_OK;
 }

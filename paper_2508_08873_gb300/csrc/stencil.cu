@@ -213,14 +213,18 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
     J0 = (long)interval * a.M;
     if (J0 < 0 || J0 + a.M > a.nJ) return;    // outside the time grid (checked on the host)
   }
-  // TD: the plan of step j of the system (j in the order the steps run)
-  auto set_step = [&](int j) {
+  // TD: the plan of solve st of step j of the system (j in the order the
+  // steps run): backward Euler: row J of the time grid; SDIRK: row 2J + s,
+  // the operator at stage time s, solved stage 1 then 2 forward and stage 2
+  // then 1 in the adjoint (the transposed step map)
+  auto set_step = [&](int j, int st) {
     const long J = a.adj ? J0 + a.M - 1 - j : J0 + j;
-    B = static_cast<const T*>(a.B) + J * a.b_step;
+    const long row = SD ? 2 * J + (a.adj ? 1 - st : st) : J;
+    B = static_cast<const T*>(a.B) + row * a.b_step;
     Bd = B + 5 * ldb;
-    if (a.Bs) Bs = static_cast<const T*>(a.Bs) + J * a.bs_step;
+    if (a.Bs) Bs = static_cast<const T*>(a.Bs) + row * a.bs_step;
   };
-  if constexpr (TD) set_step(0);
+  if constexpr (TD) set_step(0, 0);
   auto vec = [&](int v) { return ws + (size_t)v * ldv + mx; };
   T* x = vec(0);
   T* r = vec(1);
@@ -287,7 +291,10 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
           f += (T)csys[(size_t)fj * a.src.Q + qq] * (T)gsys[(size_t)qq * n + k];
       T dv = au * uv[k];
       if (w1) dv += a1 * w1[k];
-      const T d = Bs[4 * ldb + k] * dv + dt * Bs[5 * ldb + k] * f;
+      // SD + TD: the stage vectors are kept unscaled (the scaling changes
+      // with the stage's matrix), d^ = S^-1 (d + dt f)
+      const T d = (SD && TD) ? Bs[5 * ldb + k] * (dv + dt * f)
+                             : Bs[4 * ldb + k] * dv + dt * Bs[5 * ldb + k] * f;
       T bx = x[k];
       bx += Bs[k] * x[k - 1];
       bx += Bs[ldb + k] * x[k + 1];
@@ -444,11 +451,11 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
     cl.sync();
   };
   for (int j = 0; j < a.M; ++j) {
-    if constexpr (TD) {
+    if constexpr (TD && !SD) {
       if (j > 0) {
         // CG iterates in x^ = S_J x: rescale from the previous step's S
         const T* Bp = Bs;
-        set_step(j);
+        set_step(j, 0);
         if (!a.bicg) {
           for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
             x[k] = x[k] * Bp[5 * ldb + k] * Bs[6 * ldb + k];
@@ -458,6 +465,40 @@ __device__ __forceinline__ void krylov_system(const KryArgs& a, cg::cluster_grou
     }
     if constexpr (!SD) {
       solve(T(1), x, T(0), nullptr, j);        // backward Euler: d = x + dt f(t_{j+1})
+    } else if constexpr (TD) {
+      // SDIRK on a time-dependent operator: each stage solve on its own
+      // matrix; u0v, u1v hold unscaled vectors and x (the Krylov iterate) is
+      // rescaled to the diagonal of the matrix it is solved with (CG).  With
+      // the combination coefficients remapped by the host, the same body runs
+      // the adjoint: W2 = B2^-T v, W1 = B1^-T (b1 v + b2 s1 W2), v' = bu v +
+      // b2 su W2 + W1.
+      const bool cgs = !a.bicg;
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) u0v[k] = cgs ? x[k] * Bs[5 * ldb + k] : x[k];
+      {
+        const T* Bp = Bs;
+        set_step(j, 0);
+        if (cgs)
+          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+            x[k] = x[k] * Bp[5 * ldb + k] * Bs[6 * ldb + k];
+      }
+      cl.sync();
+      solve(T(1), u0v, T(0), nullptr, 2 * j);
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) u1v[k] = cgs ? x[k] * Bs[5 * ldb + k] : x[k];
+      {
+        const T* Bp = Bs;
+        set_step(j, 1);
+        if (cgs)
+          for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x)
+            x[k] = x[k] * Bp[5 * ldb + k] * Bs[6 * ldb + k];
+      }
+      cl.sync();
+      solve((T)a.su, u0v, (T)a.s1, u1v, 2 * j + 1);
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const T u2 = cgs ? x[k] * Bs[5 * ldb + k] : x[k];
+        const T v = (T)a.bu * u0v[k] + (T)a.b1 * u1v[k] + (T)a.b2 * u2;
+        x[k] = cgs ? v * Bs[6 * ldb + k] : v;
+      }
+      cl.sync();
     } else {
       // two-stage SDIRK with B = I + gamma dt A (dt here is gamma dt): stage
       // values U1 = B^-1 (u + gamma dt f_1), U2 = B^-1 (su u + s1 U1 + gamma dt f_2),
@@ -560,7 +601,7 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
   lrp_status s;
   const size_t ld = (size_t)op->n + 2 * op->mx;
   // time-dependent operators: one plan per fine step of the time grid, back to back
-  const size_t steps = op->kind == 3 ? (size_t)op->nJ : 1;
+  const size_t steps = op->kind == 3 ? (size_t)op->nJ * (op->stepper ? 2 : 1) : 1;
   if ((s = dev_alloc(op->ctx, pl->b64, sizeof(double) * 6 * ld * steps))) return s;
   if ((s = dev_alloc(op->ctx, pl->b32, sizeof(float) * 6 * ld * steps))) return s;
   cudaMemsetAsync(pl->b64.ptr, 0, pl->b64.bytes, c->stream);
@@ -622,12 +663,11 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
   const bool onchip = !sdirk && !td && !block && stencil_onchip_applies(c, op, prec, nsys);
   if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
-  auto kern = prec == 0 ? (sdirk ? (void (*)(KryArgs))k_krylov<double, true>
-                           : td ? (void (*)(KryArgs))k_krylov<double, false, true>
-                                : (void (*)(KryArgs))k_krylov<double>)
-                        : (sdirk ? (void (*)(KryArgs))k_krylov<float, true>
-                           : td ? (void (*)(KryArgs))k_krylov<float, false, true>
-                                : (void (*)(KryArgs))k_krylov<float>);
+  using KrK = void (*)(KryArgs);
+  auto kern = prec == 0 ? (sdirk ? (td ? (KrK)k_krylov<double, true, true> : (KrK)k_krylov<double, true>)
+                           : td ? (KrK)k_krylov<double, false, true> : (KrK)k_krylov<double>)
+                        : (sdirk ? (td ? (KrK)k_krylov<float, true, true> : (KrK)k_krylov<float, true>)
+                           : td ? (KrK)k_krylov<float, false, true> : (KrK)k_krylov<float>);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e) return cuda_err(c, e, "krylov cluster attribute");
   cudaLaunchConfig_t cfg = {};
@@ -694,6 +734,14 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
     a.bs_step = 7 * ((long)op->n + 2 * op->mx);
     a.nJ = op->nJ;
     a.adj = adjoint;
+    if (sdirk && adjoint) {
+      // the transposed step map: W2 = B2^-T v, W1 = B1^-T (b1 v + b2 s1 W2),
+      // v' = bu v + b2 su W2 + W1 (the kernel's stage body with these coefficients)
+      a.su = sc.b1;
+      a.s1 = sc.b2 * sc.s1;
+      a.b1 = sc.b2 * sc.su;
+      a.b2 = 1.0;
+    }
   }
   a.ws = op->kws.ptr;
   a.nvec = nvec;
@@ -836,14 +884,13 @@ extern "C" lrp_status lrp_operator_stencil5(lrp_ctx* cc, int mx, int my, const d
   return LRP_OK;
 }
 
-extern "C" lrp_status lrp_operator_stencil5_td(lrp_ctx* cc, int mx, int my, int nJ, const double* C,
-                                               const double* W, const double* E, const double* S,
-                                               const double* N, lrp_operator** out) {
-  Ctx* c = reinterpret_cast<Ctx*>(cc);
-  if (!c || !out || !C || !W || !E || !S || !N || mx < 1 || my < 1 || nJ < 1) return LRP_EINVAL;
-  if (nJ > 65535) return set_err(c, LRP_EINVAL, "time-dependent operators take at most 65535 steps");
-  if ((long)mx * my * nJ > (1L << 28))
-    return set_err(c, LRP_EINVAL, "time-dependent operator too large (mx my nJ > 2^28)");
+static lrp_status make_stencil5_td(Ctx* c, int mx, int my, int nJ, int stepper, const double* C,
+                                   const double* W, const double* E, const double* S,
+                                   const double* N, lrp_operator** out) {
+  const long rows = (long)nJ * (stepper ? 2 : 1);
+  if (rows > 65535) return set_err(c, LRP_EINVAL, "time-dependent operators take at most 65535 coefficient rows");
+  if ((long)mx * my * rows > (1L << 28))
+    return set_err(c, LRP_EINVAL, "time-dependent operator too large (mx my rows > 2^28)");
   cudaSetDevice(c->device);
   const int n = mx * my;
   auto* op = new lrp_operator();
@@ -854,8 +901,9 @@ extern "C" lrp_status lrp_operator_stencil5_td(lrp_ctx* cc, int mx, int my, int 
   op->my = my;
   op->n = n;
   op->nJ = nJ;
+  op->stepper = stepper;
   const double* src[5] = {C, W, E, S, N};
-  const size_t cnt = (size_t)nJ * n;
+  const size_t cnt = (size_t)rows * n;
   std::vector<double> h[5];
   for (int k = 0; k < 5; ++k) {
     h[k].resize(cnt);
@@ -867,9 +915,9 @@ extern "C" lrp_status lrp_operator_stencil5_td(lrp_ctx* cc, int mx, int my, int 
                         c->stream);
     if (e) { delete op; return cuda_err(c, e, "stencil upload"); }
   }
-  // CG when every step's stencil is symmetric, else BiCGStab
+  // CG when every row's stencil is symmetric, else BiCGStab
   bool sym = true;
-  for (size_t J = 0; J < (size_t)nJ && sym; ++J) {
+  for (size_t J = 0; J < (size_t)rows && sym; ++J) {
     const size_t o = J * n;
     for (int p = 0; p < n && sym; ++p) {
       int ix = p % mx, iy = p / mx;
@@ -882,4 +930,23 @@ extern "C" lrp_status lrp_operator_stencil5_td(lrp_ctx* cc, int mx, int my, int 
   if (e) { delete op; return cuda_err(c, e, "stencil upload"); }
   *out = op;
   return LRP_OK;
+}
+
+extern "C" lrp_status lrp_operator_stencil5_td(lrp_ctx* cc, int mx, int my, int nJ, const double* C,
+                                               const double* W, const double* E, const double* S,
+                                               const double* N, lrp_operator** out) {
+  Ctx* c = reinterpret_cast<Ctx*>(cc);
+  if (!c || !out || !C || !W || !E || !S || !N || mx < 1 || my < 1 || nJ < 1) return LRP_EINVAL;
+  return make_stencil5_td(c, mx, my, nJ, 0, C, W, E, S, N, out);
+}
+
+extern "C" lrp_status lrp_operator_stencil5_td_sdirk(lrp_ctx* cc, int mx, int my, int nJ,
+                                                     int stepper, const double* C, const double* W,
+                                                     const double* E, const double* S,
+                                                     const double* N, lrp_operator** out) {
+  Ctx* c = reinterpret_cast<Ctx*>(cc);
+  if (!c || !out || !C || !W || !E || !S || !N || mx < 1 || my < 1 || nJ < 1) return LRP_EINVAL;
+  if (stepper != LRP_STEP_SDIRK2 && stepper != LRP_STEP_SDIRK2_L)
+    return set_err(c, LRP_EINVAL, "stage-sampled operators take an SDIRK stepper");
+  return make_stencil5_td(c, mx, my, nJ, stepper, C, W, E, S, N, out);
 }

@@ -25,7 +25,8 @@ namespace lrp {
 
 struct TdArgs {
   int n, nJ, M, adjoint, nsys, P;
-  double dt;
+  double dt;                 // SDIRK: gamma dt
+  double su, s1, bu, b1, b2; // SDIRK: stage combination (see StepCoef; remapped for the adjoint)
   const double* lo;   // nJ x n: row J holds A(t_{J+1})
   const double* di;
   const double* up;
@@ -34,7 +35,12 @@ struct TdArgs {
   PropSrc src;
 };
 
-template <typename T>
+// SD: two-stage SDIRK steps; the coefficient rows are then 2 per step, row
+// 2J + s the operator at stage time s of step J.  The forward step solves
+// with the stage-1 matrix, then the stage-2 matrix; the adjoint step (the
+// transposed step map) solves with the transposed stage-2 matrix first, the
+// host remapping the combination coefficients.
+template <typename T, bool SD>
 __global__ void __launch_bounds__(1024) k_tri_td(TdArgs a) {
   if (a.in.stop && *a.in.stop) return;
   extern __shared__ __align__(16) unsigned char td_smem[];
@@ -64,23 +70,22 @@ __global__ void __launch_bounds__(1024) k_tri_td(TdArgs a) {
         ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
     const double* gsys = (a.src.Q > 0 && a.src.map)
         ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
-    for (int t = 0; t < a.M; ++t) {
-      const long J = a.adjoint ? j0 + a.M - 1 - t : j0 + t;
-      T av = T(0), bv = T(1), cv = T(0), dv = T(0);   // identity rows beyond n
+    // one PCR solve with row `row` of the coefficients: (I + dt A_row) y = d
+    // (or its transpose), thread i holding row i (identity rows beyond n)
+    auto pcr = [&](long row, T dv) -> T {
+      T av = T(0), bv = T(1), cv = T(0);
       if (i < n) {
-        const double* lo = a.lo + J * n;
-        const double* di = a.di + J * n;
-        const double* up = a.up + J * n;
-        // row i of B_J (or of its transpose): a x_{i-1} + b x_i + c x_{i+1}
+        const double* lo = a.lo + row * n;
+        const double* di = a.di + row * n;
+        const double* up = a.up + row * n;
+        // row i of B (or of its transpose): a x_{i-1} + b x_i + c x_{i+1}
         const double l = a.adjoint ? (i > 0 ? up[i - 1] : 0.0) : (i > 0 ? lo[i] : 0.0);
         const double u = a.adjoint ? (i + 1 < n ? lo[i + 1] : 0.0) : (i + 1 < n ? up[i] : 0.0);
         av = (T)(a.dt * l);
         bv = (T)(1.0 + a.dt * di[i]);
         cv = (T)(a.dt * u);
-        dv = x;
-        if (csys)
-          for (int q = 0; q < a.src.Q; ++q)
-            dv += dt * (T)csys[(size_t)t * a.src.Q + q] * (T)gsys[(size_t)q * n + i];
+      } else {
+        dv = T(0);
       }
       for (int s = 1; s < P; s <<= 1) {
         sa[i] = av;
@@ -107,7 +112,27 @@ __global__ void __launch_bounds__(1024) k_tri_td(TdArgs a) {
         dv = dv + al * dm + ga * dp;
         __syncthreads();
       }
-      x = dv / bv;
+      return dv / bv;
+    };
+    // dt f at source sample fj of this system (0 without a source)
+    auto src = [&](int fj) -> T {
+      T f = T(0);
+      if (csys && i < n)
+        for (int q = 0; q < a.src.Q; ++q)
+          f += dt * (T)csys[(size_t)fj * a.src.Q + q] * (T)gsys[(size_t)q * n + i];
+      return f;
+    };
+    for (int t = 0; t < a.M; ++t) {
+      const long J = a.adjoint ? j0 + a.M - 1 - t : j0 + t;
+      if constexpr (!SD) {
+        x = pcr(J, x + src(t));
+      } else {
+        const long r1 = a.adjoint ? 2 * J + 1 : 2 * J, r2 = a.adjoint ? 2 * J : 2 * J + 1;
+        const T u0 = x;
+        const T U1 = pcr(r1, u0 + src(2 * t));
+        const T U2 = pcr(r2, (T)a.su * u0 + (T)a.s1 * U1 + src(2 * t + 1));
+        x = (T)a.bu * u0 + (T)a.b1 * U1 + (T)a.b2 * U2;
+      }
     }
     if (i < n) {
       const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
@@ -129,6 +154,21 @@ lrp_status tri_td_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint,
       return set_err(c, LRP_EINVAL, "time-dependent operator: steps beyond its time grid");
   }
   TdArgs a;
+  const bool sd = op->stepper != 0;
+  const StepCoef sc = sd ? step_coefficients(op->stepper) : StepCoef{1.0, 0, 0, 0, 0, 0};
+  a.su = sc.su;
+  a.s1 = sc.s1;
+  a.bu = sc.bu;
+  a.b1 = sc.b1;
+  a.b2 = sc.b2;
+  if (sd && adjoint) {
+    // the transposed step map bu I + b1 B1^-T + b2 su B2^-T + b2 s1 B1^-T B2^-T:
+    // W2 = B2^-T v, W1 = B1^-T (b1 v + b2 s1 W2), v' = bu v + b2 su W2 + W1
+    a.su = sc.b1;
+    a.s1 = sc.b2 * sc.s1;
+    a.b1 = sc.b2 * sc.su;
+    a.b2 = 1.0;
+  }
   a.n = op->n;
   a.nJ = op->nJ;
   a.M = M;
@@ -137,7 +177,7 @@ lrp_status tri_td_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint,
   int P = 32;
   while (P < op->n) P <<= 1;
   a.P = P;
-  a.dt = dt;
+  a.dt = sd ? dt * sc.gamma : dt;
   a.lo = op->a64[0].as<double>();
   a.di = op->a64[1].as<double>();
   a.up = op->a64[2].as<double>();
@@ -150,9 +190,9 @@ lrp_status tri_td_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint,
   cudaEvent_t ev = nullptr;
   timer_begin(c, fam, &ev);
   if (prec == 0)
-    k_tri_td<double><<<grid, P, smem, c->stream>>>(a);
+    (sd ? k_tri_td<double, true> : k_tri_td<double, false>)<<<grid, P, smem, c->stream>>>(a);
   else
-    k_tri_td<float><<<grid, P, smem, c->stream>>>(a);
+    (sd ? k_tri_td<float, true> : k_tri_td<float, false>)<<<grid, P, smem, c->stream>>>(a);
   timer_end(c, fam, ev);
   cudaError_t e = cudaGetLastError();
   if (e) return cuda_err(c, e, "k_tri_td launch");
@@ -164,11 +204,9 @@ lrp_status tri_td_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint,
 using namespace lrp;
 struct lrp_operator : public Operator {};
 
-extern "C" lrp_status lrp_operator_tridiag_td(lrp_ctx* cc, int n, int nJ, const double* lo,
-                                              const double* di, const double* up,
-                                              lrp_operator** out) {
-  Ctx* c = reinterpret_cast<Ctx*>(cc);
-  if (!c || !out || !lo || !di || !up || n < 2 || nJ < 1) return LRP_EINVAL;
+// rows = nJ (backward Euler) or 2 nJ (SDIRK: the two stage times of every step)
+static lrp_status make_tridiag_td(Ctx* c, int n, int nJ, int stepper, const double* lo,
+                                  const double* di, const double* up, lrp_operator** out) {
   if (n > 1024) return set_err(c, LRP_EINVAL, "time-dependent operators take n <= 1024");
   cudaSetDevice(c->device);
   auto* op = new lrp_operator();
@@ -177,8 +215,9 @@ extern "C" lrp_status lrp_operator_tridiag_td(lrp_ctx* cc, int n, int nJ, const 
   op->kind = 2;
   op->n = n;
   op->nJ = nJ;
+  op->stepper = stepper;
   const double* src[3] = {lo, di, up};
-  const size_t bytes = sizeof(double) * (size_t)nJ * n;
+  const size_t bytes = sizeof(double) * (size_t)nJ * (stepper ? 2 : 1) * n;
   for (int k = 0; k < 3; ++k) {
     lrp_status s = dev_alloc(c, op->a64[k], bytes);
     if (s) { delete op; return s; }
@@ -189,4 +228,22 @@ extern "C" lrp_status lrp_operator_tridiag_td(lrp_ctx* cc, int n, int nJ, const 
   if (e) { delete op; return cuda_err(c, e, "time-dependent operator upload"); }
   *out = op;
   return LRP_OK;
+}
+
+extern "C" lrp_status lrp_operator_tridiag_td(lrp_ctx* cc, int n, int nJ, const double* lo,
+                                              const double* di, const double* up,
+                                              lrp_operator** out) {
+  Ctx* c = reinterpret_cast<Ctx*>(cc);
+  if (!c || !out || !lo || !di || !up || n < 2 || nJ < 1) return LRP_EINVAL;
+  return make_tridiag_td(c, n, nJ, 0, lo, di, up, out);
+}
+
+extern "C" lrp_status lrp_operator_tridiag_td_sdirk(lrp_ctx* cc, int n, int nJ, int stepper,
+                                                    const double* lo, const double* di,
+                                                    const double* up, lrp_operator** out) {
+  Ctx* c = reinterpret_cast<Ctx*>(cc);
+  if (!c || !out || !lo || !di || !up || n < 2 || nJ < 1) return LRP_EINVAL;
+  if (stepper != LRP_STEP_SDIRK2 && stepper != LRP_STEP_SDIRK2_L)
+    return set_err(c, LRP_EINVAL, "stage-sampled operators take an SDIRK stepper");
+  return make_tridiag_td(c, n, nJ, stepper, lo, di, up, out);
 }

@@ -133,12 +133,17 @@ def heat_td_op(n: int, N: int, M: int, T: float = 1.0):
     the end t_{J+1} = (J+1) dt of every fine step J = 0..N*M-1 (fully implicit
     backward Euler), no flux through the boundary faces.  Returns lo_t, di_t,
     up_t, each (N*M, n): row J holds A(t_{J+1})."""
+    return heat_td_at(n, fine_times(N, M, T / (N * M)))
+
+
+def heat_td_at(n: int, times) -> tuple:
+    """Experiment 2's operator (see heat_td_op) at the given times: lo, di,
+    up, each (len(times), n), row r holding A(times[r])."""
+    t = np.asarray(times, dtype=np.float64)
     h = 1.0 / n
-    dt = T / (N * M)
-    t = fine_times(N, M, dt)
     xf = h * np.arange(1, n)
     kap = (1.0 + 0.9 * np.sin(7 * np.pi * t[:, None] + 2 * np.pi * xf[None, :])) / h ** 2
-    J = N * M
+    J = t.shape[0]
     di = np.zeros((J, n))
     di[:, :-1] += kap
     di[:, 1:] += kap
@@ -295,9 +300,14 @@ def heat2d_td_op(m: int, N: int, M: int, T: float = 1.0) -> dict:
     spacing h = 1/(m+1), d at the face midpoints and at the end t_{J+1} of
     every fine step J = 0..N*M-1.  Returns C, W, E, S, N, each (N*M, m*m):
     row J holds the stencil of A(t_{J+1})."""
+    return heat2d_td_at(m, fine_times(N, M, T / (N * M)))
+
+
+def heat2d_td_at(m: int, times) -> dict:
+    """Experiment 3's operator (see heat2d_td_op) at the given times: C, W,
+    E, S, N, each (len(times), m*m), row r the stencil of A(times[r])."""
+    t = np.asarray(times, dtype=np.float64)
     h = 1.0 / (m + 1)
-    dt = T / (N * M)
-    t = fine_times(N, M, dt)
     xn = (np.arange(m) + 1) * h
     XN, YN = np.meshgrid(xn, xn, indexing="xy")
     sw = lambda xx, yy: ((xx <= 0.5) & (yy <= 0.5)).astype(np.float64)

@@ -116,3 +116,67 @@ def test_td_rejects_beyond_time_grid_and_classical(setup):
     with pytest.raises(_native.LrpError) as ei:
         api.Operator.tridiag_td(ctx, lo, lo + 1.0, lo)
     assert ei.value.status == _native.LRP_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# SDIRK steppers on the time-dependent operator: two coefficient rows per
+# step (the stage times), the adjoint as the transposed step map
+# ---------------------------------------------------------------------------
+def _stage_times(orc, scheme, dt, nJ):
+    c, _, _ = orc.sdirk_tableau(scheme)
+    return np.array([[(J + c[s]) * dt for s in range(2)] for J in range(nJ)]).ravel()
+
+
+@pytest.fixture(scope="module", params=["sdirk2", "sdirk2l"])
+def sdirk_td(request, orc):
+    scheme = request.param
+    ctx = api.Context(0)
+    P = W.heat_td(n=100, N=6, M=8, R=5, p=2)
+    lo, di, up = W.heat_td_at(P.n, _stage_times(orc, scheme, P.dt, P.N * P.M))
+    op = api.Operator.tridiag_td(ctx, lo, di, up, stepper=scheme)
+    oop = orc.TridiagTD(lo, di, up, stepper=scheme)
+    c = np.sin(2 * np.pi * _stage_times(orc, scheme, P.dt, P.N * P.M)).reshape(-1, 2, 1)
+    return ctx, P, op, oop, c, scheme
+
+
+def test_sdirk_td_propagate_matches_oracle(sdirk_td, orc):
+    ctx, P, op, oop, c, scheme = sdirk_td
+    rng = np.random.default_rng(11)
+    X = rng.standard_normal((5, P.n))
+    cv = rng.standard_normal((5, P.M, 2, 1))
+    got = api.propagate(ctx, op, P.dt, P.M, X, g=P.g, c=cv)
+    want = orc.propagate(oop, P.dt, P.M, X, g=P.g, cvals=cv, intervals=0)
+    for v in range(5):
+        assert rel(got[v], want[v]) <= 1e-12, (v, rel(got[v], want[v]))
+    adj = api.propagate(ctx, op, P.dt, P.M, X, adjoint=True)
+    wadj = orc.propagate(oop, P.dt, P.M, X, adjoint=True, intervals=0)
+    for v in range(5):
+        assert rel(adj[v], wadj[v]) <= 1e-12, (v, rel(adj[v], wadj[v]))
+    g32 = api.propagate(ctx, op, P.dt, P.M, X, adjoint=True, prec="mixed")
+    for v in range(5):
+        assert rel(g32[v], wadj[v]) <= 5e-5
+
+
+def test_sdirk_td_build_and_parareal_match_oracle(sdirk_td, orc):
+    ctx, P, op, oop, c, scheme = sdirk_td
+    co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="f64")
+    oco = orc.build_coarse(oop, P.dt, P.M, P.N, P.R, P.p, P.seed)
+    info = co.info()
+    probes = np.random.default_rng(12).standard_normal((3, P.n))
+    for i in range(P.N):
+        oc = oco.intervals[i]
+        U, S, V = co.factors(i)
+        Go = oc.U @ np.diag(oc.S) @ oc.V.T
+        Gg = U.T @ np.diag(S) @ V
+        assert max(np.linalg.norm((Gg - Go) @ x) / np.linalg.norm(x) for x in probes) <= 1e-9 * oc.sigma[0]
+    ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0, P.g, c)
+    u, _ = api.parareal_solve(ctx, co, P.u0, P.g, c, K=2)
+    res = orc.parareal(oop, P.dt, P.M, P.N, oco, P.u0, P.g, c, K=2)
+    assert rel(u, res.iterates[-1]) <= 1e-10
+    uf = api.fine_solution(ctx, op, P.dt, P.M, P.N, P.u0, P.g, c)
+    assert orc.rel_err(uf, ref) <= 1e-12
+    u, info = api.parareal_solve(ctx, co, P.u0, P.g, c, K=P.N)
+    assert orc.rel_err(u, ref) <= 1e-12
+    # the operator keeps its stepper; backward Euler needs the other constructor
+    with pytest.raises(_native.LrpError):
+        op.set_stepper("be")

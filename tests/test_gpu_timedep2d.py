@@ -191,3 +191,76 @@ def test_td2d_rejects(ctx, heat31):
     assert ei.value.status == _native.LRP_EINVAL
     with pytest.raises(ValueError):
         api.Operator.stencil5_td(ctx, P.mx, P.my, {k: np.zeros((3, P.n + 1)) for k in "CWESN"})
+
+
+# ---------------------------------------------------------------------------
+# SDIRK steppers on time-dependent 5-point operators (Sec. 4, effect of the
+# time discretisation on Experiment 3): the operator at both stage times of
+# every step, the adjoint as the transposed step map
+# ---------------------------------------------------------------------------
+def _stage_times(orc, scheme, dt, nJ):
+    c, _, _ = orc.sdirk_tableau(scheme)
+    return np.array([[(J + c[s]) * dt for s in range(2)] for J in range(nJ)]).ravel()
+
+
+def _sdirk_case(orc, kind, scheme, m, nJ):
+    if kind == "heat":
+        dt = 0.01
+        return W.heat2d_td_at(m, _stage_times(orc, scheme, dt, nJ)), dt
+    dt = 1.0 / 2048
+    per = [W.adv2d_op(m, 0.01 * (1.0 + 0.5 * np.sin(9.0 * t)))
+           for t in _stage_times(orc, scheme, dt, nJ)]
+    return {k: np.array([d[k] for d in per]) for k in "CWESN"}, dt
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+@pytest.mark.parametrize("kind", ["heat", "adv"])
+@pytest.mark.parametrize("m", [15, 63])
+def test_td2d_sdirk_propagate_parity(ctx, orc, scheme, kind, m):
+    M = 3
+    st, dt = _sdirk_case(orc, kind, scheme, m, 2 * M)
+    op = api.Operator.stencil5_td(ctx, m, m, st, stepper=scheme)
+    op.set_krylov(1e-14, 1e-6, 20000)
+    oop = orc.Stencil5TD(m, m, *(st[k] for k in "CWESN"), stepper=scheme)
+    rng = np.random.default_rng(20 + m)
+    X = rng.standard_normal((3, m * m))
+    g = rng.standard_normal((2, m * m))
+    cv = rng.standard_normal((3, M, 2, 2))
+    got = api.propagate(ctx, op, dt, M, X, g=g, c=cv)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=cv, intervals=0)
+    for v in range(3):
+        assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
+    adj = api.propagate(ctx, op, dt, M, X, adjoint=True)
+    wadj = orc.propagate(oop, dt, M, X, adjoint=True, intervals=0)
+    for v in range(3):
+        assert rel(adj[v], wadj[v]) <= 1e-10, (v, rel(adj[v], wadj[v]))
+    g32 = api.propagate(ctx, op, dt, M, X, g=g, c=cv, prec="mixed")
+    for v in range(3):
+        assert rel(g32[v], want[v]) <= 5e-4
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+def test_td2d_sdirk_build_and_parareal(ctx, orc, scheme):
+    """Experiment 3's operator and source on a 15^2 grid with the SDIRK
+    stepper: the build matches the oracle's, K = 2 the oracle's iterate and
+    K = N the oracle's sequential solution."""
+    m, N, M, dt = 15, 4, 5, 0.01
+    ts = _stage_times(orc, scheme, dt, N * M)
+    st = W.heat2d_td_at(m, ts)
+    op = api.Operator.stencil5_td(ctx, m, m, st, stepper=scheme)
+    op.set_krylov(1e-14, 1e-6, 20000)
+    oop = orc.Stencil5TD(m, m, *(st[k] for k in "CWESN"), stepper=scheme)
+    P = W.heat2d_td(m=m, N=N, M=M, T=N * M * dt)
+    c = np.sin(5 * np.pi * ts).reshape(N * M, 2, 1)
+    co = api.Coarse(ctx, op, dt, M, N, 4, 2, 0, prec="f64")
+    oco = orc.build_coarse(oop, dt, M, N, 4, 2, 0)
+    info = co.info()
+    for i in range(N):
+        oc = oco.intervals[i]
+        assert np.max(np.abs(info["sigma"][i, :oc.S.shape[0]] - oc.S)) <= 1e-9 * oc.sigma[0]
+    ref = orc.sequential_fine(oop, dt, M, N, P.u0, P.g, c)
+    u, _ = api.parareal_solve(ctx, co, P.u0, P.g, c, K=N)
+    assert orc.rel_err(u, ref) <= 1e-10
+    res = orc.parareal(oop, dt, M, N, oco, P.u0, P.g, c, K=2)
+    u2, _ = api.parareal_solve(ctx, co, P.u0, P.g, c, K=2)
+    assert rel(u2, res.iterates[-1]) <= 1e-10
