@@ -338,6 +338,12 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "krylov_block_clusters") {
     if (value < 0 || value > 1024) return LRP_EINVAL;
     c->p_krylov_block_clusters = value;
+  } else if (k == "krylov_refine") {
+    if (value < 0 || value > 2) return LRP_EINVAL;
+    c->p_krylov_refine = value;
+  } else if (k == "krylov_refine_digits") {
+    if (value < 0 || value > 7) return LRP_EINVAL;
+    c->p_krylov_refine_digits = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -357,6 +363,8 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "krylov_onchip_clusters") *value = c->oc_last[2];
   else if (k == "krylov_block") *value = c->p_krylov_block;
   else if (k == "krylov_block_clusters") *value = c->p_krylov_block_clusters;
+  else if (k == "krylov_refine") *value = c->p_krylov_refine;
+  else if (k == "krylov_refine_digits") *value = c->p_krylov_refine_digits;
   else if (k == "krylov_block_last_systems") *value = c->bk_last[0];
   else if (k == "krylov_block_last_cs") *value = c->bk_last[1];
   else if (k == "krylov_block_last_clusters") *value = c->bk_last[2];

@@ -57,6 +57,8 @@ struct Ctx {
   int oc_last[3] = {0, 0, 0};  // last on-chip CG launch: rows per thread, CTAs per cluster, clusters
   int p_krylov_block = 0;    // block CG over this many systems for symmetric 2D operators (0 off, 4)
   int p_krylov_block_clusters = 0;  // clusters in flight of the block CG (0: workspaces within 96 MB)
+  int p_krylov_refine = 0;   // FP64 2D steps by iterative refinement: 0 auto, 1 where it applies, 2 never
+  int p_krylov_refine_digits = 0;   // relative tolerance 10^-digits of its FP32 solves (0: 1e-4)
   int bk_last[3] = {0, 0, 0};  // last block CG launch: systems per block, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
@@ -160,6 +162,7 @@ struct Operator {
   std::vector<std::unique_ptr<StencilPlan>> splans;
   DevBuf kws, kstat;       // Krylov workspace and status of 2D propagations
   DevBuf bws;              // block CG workspace (stencil_block.cu)
+  DevBuf irws, irstat;     // iterative refinement workspace and inner-solve status (stencil_refine.cu)
   unsigned long long krylov_iters = 0;
 };
 
@@ -342,6 +345,13 @@ lrp_status stencil_propagate_block(Ctx* c, Operator* op, StencilPlan* plan, int 
                                    int prec, const KryArgs& base);
 lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
                                     int prec, const KryArgs& base);
+// FP64 steps of symmetric time-invariant 5-point operators by mixed-precision
+// iterative refinement (stencil_refine.cu): FP64 residuals, FP32 on-chip CG
+// corrections, the FP64 Krylov kernels' stopping test.  Applies (automatic
+// mode) where the FP32 on-chip kernel takes the grid and the FP64 one does not.
+bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys);
+lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
+                                    const PropIn& in, const PropOut& out, const PropSrc& src);
 size_t krylov_queue_nvec(int bicg);
 // Device pointer of the stencil coefficients for KryArgs::B (past the pad).
 const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec);

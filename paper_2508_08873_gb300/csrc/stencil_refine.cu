@@ -1,0 +1,309 @@
+// FP64 backward-Euler steps of symmetric 5-point operators by mixed-precision
+// iterative refinement: every step (I + dt A) x = d, d = x_j + dt f(t_{j+1}),
+// is solved to the FP64 tolerance by rounds of
+//   r = d - B x          (FP64, from the FP64 step matrix),
+//   B e = r              (FP32 conjugate gradients on the on-chip kernel, to a
+//                         looser relative tolerance, from e = 0),
+//   x <- x + e           (FP64),
+// until the residual of the diagonally scaled system meets the same test as
+// the FP64 Krylov kernels, ||D^1/2 (d - B x)|| <= rtol ||D^1/2 d||
+// (D = diag(B)^-1), evaluated in FP64, or reaches its rounding level,
+// ||D^1/2 (d - B x)|| <= IR_FLOOR u_64 ||D^1/2 (|d| + |B| |x|)|| (the residual
+// of the true solution rounded to FP64 is of that size, so no iterate can do
+// better; the Krylov kernels test their recursively updated residual, which
+// can fall below it).  The FP32 solves run with every Krylov
+// vector on chip, and GB300 executes FP32 at 64 times its FP64 rate, so the
+// FP64 work of a step shrinks to one residual per round.
+//
+// Each round gains a factor of about rtol_inner + kappa u_32 on the residual
+// (kappa the condition number of the scaled step matrix, u_32 the FP32 unit
+// roundoff: the FP32 solve is exact only for the rounded matrix); a system
+// stops as soon as its own residual passes, so that the rounds of a step only
+// run the systems still above the tolerance.  The iterate is warm-started
+// from x_j as in the FP64 kernels.  Systems are processed in batches of at
+// most IR_BATCH with FP64 workspaces of four vectors each.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace lrp {
+
+constexpr int IR_THREADS = 256;
+constexpr int IR_PTS = 8;          // grid points per thread in the residual kernel
+constexpr int IR_BATCH = 256;      // systems per batch (four FP64 vectors each)
+constexpr int IR_MAX_ROUNDS = 60;  // refinement rounds per step before LRP_ENOTCONV
+constexpr double IR_FLOOR = 8.0;   // rounding level of the residual, in units of u_64 (|d| + |B||x|)
+
+// input vector of systems s0 .. s0 + cnt - 1 into X (cnt x n)
+__global__ void k_ir_gather(PropIn in, int n, int s0, int cnt, double* __restrict__ X) {
+  const long tot = (long)cnt * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), k = (int)(e % n), sys = s0 + s;
+    double v = 0.0;
+    if (in.gen)
+      v = gauss<double>(in.seed, in.stream, (uint32_t)(in.interval0 + sys / in.ncol),
+                        (uint32_t)(sys % in.ncol), (uint32_t)k);
+    else if (in.x != nullptr) {
+      const long o = sys_offset(in.map, in.slot_stride, in.ldx, sys) + k;
+      v = in.x_f64 ? static_cast<const double*>(in.x)[o] : (double)static_cast<const float*>(in.x)[o];
+    }
+    X[e] = v;
+  }
+}
+
+__global__ void k_ir_scatter(PropOut out, int n, int s0, int cnt, const double* __restrict__ X) {
+  const long tot = (long)cnt * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), k = (int)(e % n);
+    const long o = sys_offset(out.map, out.slot_stride, out.ldy, s0 + s) + k;
+    if (out.y_f64)
+      static_cast<double*>(out.y)[o] = X[e];
+    else
+      static_cast<float*>(out.y)[o] = (float)X[e];
+  }
+}
+
+// right-hand side of step j: D = X + dt f(t_{j+1}) (source sample j)
+__global__ void k_ir_rhs(PropSrc src, int n, int s0, int cnt, int j, double dt,
+                         const double* __restrict__ X, double* __restrict__ D) {
+  const long tot = (long)cnt * n;
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(e / n), k = (int)(e % n), sys = s0 + s;
+    double f = 0.0;
+    if (src.Q > 0) {
+      const double* csys = src.c + sys_offset(src.map, src.c_slot_stride, src.cstride, sys);
+      const double* gsys = src.map ? src.g + (long)src.map[2 * sys] * src.g_slot_stride : src.g;
+      for (int q = 0; q < src.Q; ++q) f += csys[(size_t)j * src.Q + q] * gsys[(size_t)q * n + k];
+    }
+    D[e] = X[e] + dt * f;
+  }
+}
+
+// Residual of the listed systems (list[2 i] = system of the batch):
+// r = D - B X, G = r / dt (the source of the FP32 correction solve, whose
+// right-hand side is dt G), and per block the partial sums of r^T D r,
+// d^T D d and a^T D a, a = |d| + |B| |x| (D = 1 / diag(B)), in a fixed order.
+__global__ void __launch_bounds__(IR_THREADS) k_ir_resid(int mx, int my, double dt,
+                                                        const double* __restrict__ B, long ldb,
+                                                        const int* __restrict__ list,
+                                                        const double* __restrict__ X,
+                                                        const double* __restrict__ D,
+                                                        double* __restrict__ G,
+                                                        double* __restrict__ part) {
+  const int n = mx * my;
+  const int s = list[2 * blockIdx.y];
+  const long base = (long)s * n;
+  const int k0 = blockIdx.x * IR_THREADS * IR_PTS;
+  double rr = 0.0, dd = 0.0, aa = 0.0;
+#pragma unroll
+  for (int u = 0; u < IR_PTS; ++u) {
+    const int k = k0 + u * IR_THREADS + threadIdx.x;
+    if (k < n) {
+      const int ix = k % mx, iy = k / mx;
+      const double* x = X + base;
+      double bx = B[k] * x[k];
+      double ab = fabs(B[k] * x[k]);
+      if (ix > 0) { const double t = B[ldb + k] * x[k - 1]; bx += t; ab += fabs(t); }
+      if (ix < mx - 1) { const double t = B[2 * ldb + k] * x[k + 1]; bx += t; ab += fabs(t); }
+      if (iy > 0) { const double t = B[3 * ldb + k] * x[k - mx]; bx += t; ab += fabs(t); }
+      if (iy < my - 1) { const double t = B[4 * ldb + k] * x[k + mx]; bx += t; ab += fabs(t); }
+      const double d = D[base + k];
+      const double r = d - bx;
+      const double dinv = B[5 * ldb + k];
+      G[base + k] = r / dt;
+      rr += r * r * dinv;
+      dd += d * d * dinv;
+      ab += fabs(d);
+      aa += ab * ab * dinv;
+    }
+  }
+  __shared__ double sh[3][IR_THREADS / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    aa += __shfl_xor_sync(0xffffffffu, aa, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    sh[0][w] = rr;
+    sh[1][w] = dd;
+    sh[2][w] = aa;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double a = 0.0;
+    for (int i = 0; i < IR_THREADS / 32; ++i) a += sh[threadIdx.x][i];
+    part[((long)blockIdx.y * gridDim.x + blockIdx.x) * 3 + threadIdx.x] = a;
+  }
+}
+
+// One warp per listed system: the residual test from the partial sums (fixed
+// order); systems above both the tolerance and the rounding level go to the
+// next list (cnt[0] counts them; their order does not affect any result).
+__global__ void k_ir_reduce(int nblk, double rtol2, double floor2, const int* __restrict__ list,
+                            const double* __restrict__ part, int* __restrict__ next,
+                            int* __restrict__ cnt) {
+  const int i = blockIdx.x, lane = threadIdx.x;
+  double rr = 0.0, dd = 0.0, aa = 0.0;
+  for (int b = lane; b < nblk; b += 32) {
+    rr += part[((long)i * nblk + b) * 3];
+    dd += part[((long)i * nblk + b) * 3 + 1];
+    aa += part[((long)i * nblk + b) * 3 + 2];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    rr += __shfl_xor_sync(0xffffffffu, rr, o);
+    dd += __shfl_xor_sync(0xffffffffu, dd, o);
+    aa += __shfl_xor_sync(0xffffffffu, aa, o);
+  }
+  if (lane == 0 && rr > rtol2 * dd && rr > floor2 * aa) {
+    const int at = atomicAdd(cnt, 1);
+    next[2 * at] = list[2 * i];
+    next[2 * at + 1] = 0;
+  }
+}
+
+// X += E on the listed systems
+__global__ void k_ir_apply(int n, const int* __restrict__ list, double* __restrict__ X,
+                           const double* __restrict__ E) {
+  const long base = (long)list[2 * blockIdx.y] * n;
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    X[base + k] += E[base + k];
+}
+
+__global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restrict__ one) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < cnt) {
+    list[2 * i] = i;
+    list[2 * i + 1] = 0;
+  }
+  if (i == 0) *one = 1.0;
+}
+
+bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys) {
+  if (prec != 0 || op->kind != 1 || !op->symmetric || op->stepper != 0) return false;
+  if (c->p_krylov_refine == 2) return false;
+  if (c->p_krylov_refine == 0 && stencil_onchip_applies(c, op, 0, nsys)) return false;
+  return stencil_onchip_applies(c, op, 1, std::min(nsys, IR_BATCH));
+}
+
+lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
+                                    const PropIn& in, const PropOut& out, const PropSrc& src) {
+  const int n = op->n;
+  const int batch = std::min(nsys, IR_BATCH);
+  const size_t vec = (size_t)batch * n;
+  const int nblk = (n + IR_THREADS * IR_PTS - 1) / (IR_THREADS * IR_PTS);
+  // X, D, G, E (FP64), partial sums, two system lists, the counter, the constant 1
+  const size_t need = sizeof(double) * (4 * vec + (size_t)batch * nblk * 3 + 8) +
+                      sizeof(int) * (4 * (size_t)batch + 8);
+  lrp_status s;
+  if (op->irws.bytes < need)
+    if ((s = dev_alloc(c, op->irws, need))) return s;
+  if (!op->irstat.ptr)
+    if ((s = dev_alloc(c, op->irstat, 32))) return s;
+  double* X = op->irws.as<double>();
+  double* D = X + vec;
+  double* G = D + vec;
+  double* E = G + vec;
+  double* part = E + vec;
+  double* one = part + (size_t)batch * nblk * 3;
+  int* listA = reinterpret_cast<int*>(one + 8);
+  int* listB = listA + 2 * batch;
+  int* cnt = listB + 2 * batch;
+  cudaStream_t st = c->stream;
+  // the inner FP32 solves: their iterations and status words
+  unsigned long long* iters = reinterpret_cast<unsigned long long*>(op->irstat.ptr);
+  int* istat = reinterpret_cast<int*>(static_cast<char*>(op->irstat.ptr) + 8);
+  cudaMemsetAsync(op->irstat.ptr, 0, 32, st);
+  const double rtol2 = op->rtol64 * op->rtol64;
+  const double floor2 = (IR_FLOOR * 0x1p-53) * (IR_FLOOR * 0x1p-53);
+  const double rtol_in = c->p_krylov_refine_digits > 0 ? std::pow(10.0, -c->p_krylov_refine_digits)
+                                                       : 1e-4;
+  const long ldb = (long)n + 2 * op->mx;
+  const double* B64 = plan->b64.as<double>() + op->mx;
+  int* hcnt = nullptr;
+  cudaError_t e = cudaMallocHost(&hcnt, sizeof(int));
+  if (e) return cuda_err(c, e, "refinement counter");
+  struct HostFree { int* p; ~HostFree() { if (p) cudaFreeHost(p); } } hf{hcnt};
+  const int gsz = std::min<long>(4L * c->num_sms, ((long)vec + 255) / 256);
+  const char* fam = "propagate_f64";
+  bool notconv = false;
+  for (int s0 = 0; s0 < nsys; s0 += batch) {
+    const int cnt0 = std::min(batch, nsys - s0);
+    k_ir_gather<<<gsz, 256, 0, st>>>(in, n, s0, cnt0, X);
+    for (int j = 0; j < M; ++j) {
+      k_ir_rhs<<<gsz, 256, 0, st>>>(src, n, s0, cnt0, j, plan->dt, X, D);
+      k_ir_list_all<<<(cnt0 + 255) / 256, 256, 0, st>>>(cnt0, listA, one);
+      int nact = cnt0;
+      int* cur = listA;
+      int* nxt = listB;
+      for (int round = 0;; ++round) {
+        cudaEvent_t ev = nullptr;
+        timer_begin(c, fam, &ev);
+        k_ir_resid<<<dim3(nblk, nact), IR_THREADS, 0, st>>>(op->mx, op->my, plan->dt, B64, ldb, cur, X, D,
+                                                            G, part);
+        cudaMemsetAsync(cnt, 0, sizeof(int), st);
+        k_ir_reduce<<<nact, 32, 0, st>>>(nblk, rtol2, floor2, cur, part, nxt, cnt);
+        timer_end(c, fam, ev);
+        e = cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (!e) e = cudaStreamSynchronize(st);
+        if (!e) e = cudaGetLastError();
+        if (e) return cuda_err(c, e, "refinement residual");
+        nact = *hcnt;
+        if (nact == 0) break;
+        if (round == IR_MAX_ROUNDS || op->max_iter == 0) { notconv = true; break; }
+        // the correction of every system still above the tolerance: FP32
+        // CG on B e = dt G = r from e = 0 (zero input, the residual as the
+        // step's source), on chip
+        std::swap(cur, nxt);
+        KryArgs a{};
+        a.mx = op->mx;
+        a.my = op->my;
+        a.n = n;
+        a.M = 1;
+        a.nsys = nact;
+        a.bicg = 0;
+        a.dt = plan->dt;
+        a.rtol = rtol_in;
+        a.max_iter = op->max_iter;
+        a.B = stencil_B(plan, op, 1);
+        a.Bs = stencil_Bs(plan, op, 1);
+        a.in.x = nullptr;
+        a.in.ncol = 1;
+        a.out.y = E;
+        a.out.y_f64 = 1;
+        a.out.map = cur;
+        a.out.slot_stride = n;
+        a.out.ldy = 0;
+        a.src.Q = 1;
+        a.src.g = G;
+        a.src.c = one;
+        a.src.cstride = 0;
+        a.src.map = cur;
+        a.src.c_slot_stride = 0;
+        a.src.g_slot_stride = n;
+        a.iters = iters;
+        a.status = istat;
+        if ((s = stencil_propagate_onchip(c, op, plan, 1, nact, 1, a))) return s;
+        k_ir_apply<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, cur, X, E);
+      }
+      if (notconv) break;
+    }
+    k_ir_scatter<<<gsz, 256, 0, st>>>(out, n, s0, cnt0, X);
+    if (notconv) break;
+  }
+  unsigned long long hs[2] = {0, 0};
+  e = cudaMemcpyAsync(hs, op->irstat.ptr, 16, cudaMemcpyDeviceToHost, st);
+  if (!e) e = cudaStreamSynchronize(st);
+  if (!e) e = cudaGetLastError();
+  if (e) return cuda_err(c, e, "refinement");
+  op->krylov_iters += hs[0];
+  const int stw = (int)(hs[1] & 0xffffffffu);
+  if (stw & 2) return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in an FP32 correction solve");
+  if (notconv) return set_err(c, LRP_ENOTCONV, "iterative refinement did not reach the FP64 tolerance");
+  return LRP_OK;
+}
+
+}  // namespace lrp
