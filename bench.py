@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--batch-per-grid", type=int, default=2,
                     help="batch mode: problems per grid size of the uneven 2D batch")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "serve", "krylov", "batch", "cfg3"],
+                    choices=["solve", "serve", "krylov", "batch", "cfg3", "trisweep"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
                          "of the 2D Krylov fine propagator (HBM GB/s fraction)")
@@ -74,9 +74,21 @@ def parse():
                     help="--mode krylov: solve the systems four at a time by block CG")
     ap.add_argument("--krylov-block-clusters", type=int, default=0,
                     help="--mode krylov: clusters in flight of the block CG (0: automatic)")
+    ap.add_argument("--krylov-m", type=int, default=511,
+                    help="krylov mode: grid size m of the diff2d m x m operator")
+    ap.add_argument("--krylov-refine", type=int, default=0, choices=[0, 1],
+                    help="krylov mode: 1 forces the FP64 iterative refinement where the FP32 "
+                         "on-chip kernel takes the grid (0: the library's default)")
+    ap.add_argument("--refine-digits", default="",
+                    help="krylov mode: also time the FP64 iterative refinement with these inner "
+                         "FP32 tolerances 10^-d (comma list)")
     ap.add_argument("--krylov-onchip", type=int, default=0, choices=[0, 2],
                     help="krylov mode: 0 the on-chip CG where it applies, 2 the kernel with "
                          "its Krylov vectors in global memory")
+    ap.add_argument("--sweep-systems", default="16,32,48,64,96,128",
+                    help="trisweep mode: batch sizes of the FP64 adr1d fine-solve sweep")
+    ap.add_argument("--sweep-chunks", default="8,9,10,11,12,13,14,15,16",
+                    help="trisweep mode: chunk lengths (tri_wchunk) of the one-warp kernel")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-targets", default="",
                     help="serve mode: extra passes 'rate:adr1d_target_ms,...' with admission "
@@ -371,7 +383,8 @@ ONCHIP_DRAM_BYTES_PER_SYSTEM = (38.77e6 + 1.02e6) / 16
 
 
 def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, block: int = 0,
-               block_clusters: int = 0) -> dict:
+               block_clusters: int = 0, refine_digits=(), m: int = 511,
+               refine_mode: int = 0) -> dict:
     """The 2D fine propagator's bandwidth (the 'HBM GB/s frac' part of the
     metric): diff2d (511^2, kappa checkerboard, dt = 1/4096), Jacobi-PCG per
     backward-Euler step, FP32 sketch propagations (rtol 1e-6) and FP64 fine
@@ -380,11 +393,18 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
     achieved = that x iterations / kernel time (CUDA events on the library's
     stream).  With block = 4 the systems are solved four at a time in one
     block Krylov space (fewer iterations per system; `us_per_system_step`
-    compares the kernels per system and step)."""
+    compares the kernels per system and step).  The "f64" entry times the
+    FP64 Krylov kernel itself (krylov_refine = 2); "f64_refine" times the
+    library's default FP64 step for this grid, iterative refinement (FP64
+    residuals, FP32 on-chip CG corrections), by CUDA events on the library's
+    stream around whole propagations (its kernels of both precisions and the
+    host's checks between rounds)."""
+    import torch
     from paper_2508_08873_gb300 import api, workloads as W
-    P = W.diff2d()
+    P = W.diff2d(m=m, T=128 * 32 / 4096)            # dt = 1/4096 at every grid size
     op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
     op.set_krylov(1e-12, 1e-6, 20000)
+    ctx.set_param("krylov_refine", 2)
     ctx.set_param("krylov_onchip", onchip)
     ctx.set_param("krylov_block", block)
     ctx.set_param("krylov_block_clusters", block_clusters)
@@ -425,12 +445,53 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
                         "onchip_shape": {"rows_per_cta": ctx.get_param("krylov_onchip_rows"),
                                          "ctas_per_cluster": ctx.get_param("krylov_onchip_cs"),
                                          "clusters": ctx.get_param("krylov_onchip_clusters")}}
+            if prec == "f64" and onchip == 0 and block == 0:
+                # the default FP64 path for this grid: iterative refinement
+                Xd = torch.from_numpy(X).cuda()
+                Yd = torch.empty_like(Xd)
+                strm = torch.cuda.ExternalStream(ctx.stream)
+
+                def refine(digits):
+                    ctx.set_param("krylov_refine", refine_mode)
+                    ctx.set_param("krylov_refine_digits", digits)
+                    try:
+                        for _ in range(max(1, warmup)):
+                            api.propagate(ctx, op, P.dt, 1, Xd, prec=prec, out=Yd)
+                        it0 = op.krylov_iterations()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        torch.cuda.synchronize()
+                        e0.record(strm)
+                        for _ in range(steps):
+                            api.propagate(ctx, op, P.dt, 1, Xd, prec=prec, out=Yd)
+                        e1.record(strm)
+                        e1.synchronize()
+                        return e0.elapsed_time(e1), op.krylov_iterations() - it0
+                    finally:
+                        ctx.set_param("krylov_refine", 2)
+                        ctx.set_param("krylov_refine_digits", 0)
+
+                ms_r, its_r = refine(0)
+                out["f64_refine"] = {
+                    "systems": nsys, "rtol": 1e-12,
+                    "us_per_system_step": ms_r * 1e3 / (nsys * steps),
+                    "speedup_vs_f64_kernel": out["f64"]["us_per_system_step"] / (ms_r * 1e3 / (nsys * steps)),
+                    "fp32_cg_iterations_per_step": its_r / (nsys * steps),
+                    "inner_rtol": 1e-4,
+                    "kernels": "k_ir_resid + k_ir_reduce (FP64 residual, scaled-norm test), "
+                               "k_ir_scale, k_cg_onchip<float> (correction), k_ir_apply"}
+                for d in refine_digits:
+                    ms_d, its_d = refine(d)
+                    out["f64_refine"].setdefault("by_inner_digits", {})[str(d)] = {
+                        "us_per_system_step": ms_d * 1e3 / (nsys * steps),
+                        "fp32_cg_iterations_per_step": its_d / (nsys * steps)}
     finally:
+        ctx.set_param("krylov_refine", 0)
         ctx.set_param("krylov_onchip", 0)
         ctx.set_param("krylov_block", 0)
         ctx.set_param("krylov_block_clusters", 0)
         op.close()
-    return {"workload": "diff2d 511^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, one "
+    return {"workload": f"diff2d {m}^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, one "
                         "backward-Euler step per system",
             "peak_source": peak_src, "algorithmic_bytes": "6 words per grid point and CG "
                                                           "iteration (x, r, p read + written)",
@@ -446,7 +507,9 @@ def run_krylov(args):
     precs = args.krylov_precs.split(",")
     nsyss = [int(v) for v in args.krylov_systems.split(",")]
     res = krylov_leg(ctx, precs, nsyss, args.steps, args.warmup, args.krylov_onchip,
-                     args.krylov_block, args.krylov_block_clusters)
+                     args.krylov_block, args.krylov_block_clusters,
+                     [int(v) for v in args.refine_digits.split(",") if v], args.krylov_m,
+                     args.krylov_refine)
     head = res["f64" if precs[0] == "f64" else "f32"]
     line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
             "value": head["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,
@@ -599,8 +662,13 @@ def run_cfg3(args):
     f32, f64 = kr["f32"], kr["f64"]
     prop32 = 2 * P.N * ell * P.M * f32["cg_iterations_per_step"] * f32["us_per_iteration_and_system"] * 1e-6
     t_build = dense + prop32
-    t_iter = P.N * P.M * f64["cg_iterations_per_step"] * f64["us_per_iteration_and_system"] * 1e-6 \
-        + sweep[1] * 1e-3
+    # FP64 fine solves: the library's default for this grid (iterative
+    # refinement) when measured, else the FP64 Krylov kernel
+    us64 = kr["f64_refine"]["us_per_system_step"] if "f64_refine" in kr \
+        else f64["cg_iterations_per_step"] * f64["us_per_iteration_and_system"]
+    t_iter = P.N * P.M * us64 * 1e-6 + sweep[1] * 1e-3
+    t_iter_f64_kernel = P.N * P.M * f64["cg_iterations_per_step"] * f64["us_per_iteration_and_system"] \
+        * 1e-6 + sweep[1] * 1e-3
     line = {"metric": "diff2d 511^2 Parareal: build and iteration times at full size (extrapolated "
                       "from full-size measurements)",
             "value": t_build, "unit": "s (build)", "mode": "cfg3", "n_gpus": 1,
@@ -611,8 +679,10 @@ def run_cfg3(args):
             "build_M1_s": t_b1, "build_M1_kernels_ms": {f: v[1] for f, v in kt.items()},
             "dense_part_s": dense, "sketch_propagation_s": prop32, "build_s": t_build,
             "sweep_ms": sweep[1], "iteration_s": t_iter,
+            "iteration_s_f64_krylov_kernel": t_iter_f64_kernel,
             "solves_per_s": {str(k): 1.0 / (t_build + k * t_iter) for k in (1, 4, 16, P.N)},
-            "formula": "T_build = dense + 2 N l M it32 t32; T_iter = N M it64 t64 + sweep; "
+            "formula": "T_build = dense + 2 N l M it32 t32; T_iter = N M t64 + sweep (t64 the "
+                       "FP64 time per system and step: iterative refinement); "
                        "solves/s(k) = 1 / (T_build + k T_iter)"}
     co.close()
     print(json.dumps(line), flush=True)
@@ -735,9 +805,71 @@ def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
             "cls_out": cls_out, "ts_out": ts_out}
 
 
+def run_trisweep(args):
+    """CUDA-event time per launch of the FP64 fine-solve kernels on adr1d
+    (n = 4095, 256 steps) over batch sizes and chunk lengths: the general
+    one-warp cluster kernel (tri_wtoep = 2) and its constant-coefficient
+    variant (tri_wtoep = 1, chunk lengths with n mod MM in {0, MM - 1}), the
+    table the library's chunk rule was read from."""
+    import torch
+    from paper_2508_08873_gb300 import api, workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
+    P = W.adr1d()
+    op = api.Operator.tridiag(ctx, P.lo, P.di, P.up)
+    rng = np.random.default_rng(0)
+    table = {}
+    for nsys in [int(v) for v in args.sweep_systems.split(",")]:
+        X = torch.from_numpy(rng.standard_normal((nsys, P.n))).cuda()
+        Y = torch.empty_like(X)
+        row = {}
+        for mm in [int(v) for v in args.sweep_chunks.split(",")]:
+            for toep, key in ((2, "general"), (1, "constant")):
+                if toep == 1 and P.n % mm and (P.n + 1) % mm:
+                    continue
+                ctx.set_param("tri_wchunk", mm)
+                ctx.set_param("tri_warp", 2)
+                ctx.set_param("tri_wtoep", toep)
+                try:
+                    for _ in range(max(1, args.warmup)):
+                        api.propagate(ctx, op, P.dt, P.M, X, out=Y)
+                    ctx.set_kernel_timing(True)
+                    ctx.reset_kernel_time()
+                    for _ in range(args.steps):
+                        api.propagate(ctx, op, P.dt, P.M, X, out=Y)
+                    nl, ms = ctx.kernel_time("propagate_f64")
+                    ctx.set_kernel_timing(False)
+                    row.setdefault(key, {})[str(mm)] = ms / max(nl, 1)
+                finally:
+                    ctx.set_param("tri_wchunk", 0)
+                    ctx.set_param("tri_warp", 0)
+                    ctx.set_param("tri_wtoep", 0)
+        # the library's own choice for this batch
+        for _ in range(max(1, args.warmup)):
+            api.propagate(ctx, op, P.dt, P.M, X, out=Y)
+        ctx.set_kernel_timing(True)
+        ctx.reset_kernel_time()
+        for _ in range(args.steps):
+            api.propagate(ctx, op, P.dt, P.M, X, out=Y)
+        nl, ms = ctx.kernel_time("propagate_f64")
+        ctx.set_kernel_timing(False)
+        row["default"] = ms / max(nl, 1)
+        table[str(nsys)] = row
+    line = {"metric": "FP64 fine-solve kernel time per launch (adr1d n=4095, M=256)",
+            "unit": "ms", "mode": "trisweep", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64", "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": "adr1d n=4095 M=256, FP64, one-warp cluster kernels"},
+            "table": table}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
+    if args.mode == "trisweep":
+        run_trisweep(args)
+        return
     if args.mode == "serve":
         run_serve(args)
         return

@@ -83,8 +83,8 @@ __global__ void k_ir_rhs(PropSrc src, int n, int s0, int cnt, int j, double dt,
 }
 
 // Residual of the listed systems (list[2 i] = system of the batch):
-// r = D - B X, G = r / dt (the source of the FP32 correction solve, whose
-// right-hand side is dt G), and per block the partial sums of r^T D r,
+// r = D - B X into G (scaled for the FP32 correction solve by k_ir_scale),
+// and per block the partial sums of r^T D r,
 // d^T D d and a^T D a, a = |d| + |B| |x| (D = 1 / diag(B)), in a fixed order.
 __global__ void __launch_bounds__(IR_THREADS) k_ir_resid(int mx, int my, double dt,
                                                         const double* __restrict__ B, long ldb,
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_ir_resid(int mx, int my, double 
       const double d = D[base + k];
       const double r = d - bx;
       const double dinv = B[5 * ldb + k];
-      G[base + k] = r / dt;
+      G[base + k] = r;
       rr += r * r * dinv;
       dd += d * d * dinv;
       ab += fabs(d);
@@ -142,10 +142,14 @@ __global__ void __launch_bounds__(IR_THREADS) k_ir_resid(int mx, int my, double 
 
 // One warp per listed system: the residual test from the partial sums (fixed
 // order); systems above both the tolerance and the rounding level go to the
-// next list (cnt[0] counts them; their order does not affect any result).
-__global__ void k_ir_reduce(int nblk, double rtol2, double floor2, const int* __restrict__ list,
-                            const double* __restrict__ part, int* __restrict__ next,
-                            int* __restrict__ cnt) {
+// next list (cnt[0] counts them; their order does not affect any result),
+// with the scale sigma = ||D^1/2 r|| / sqrt(n) of their residual (the FP32
+// solve runs on r / sigma: a residual of a decayed state can lie below the
+// FP32 range).
+__global__ void k_ir_reduce(int nblk, int n, double rtol2, double floor2,
+                            const int* __restrict__ list, const double* __restrict__ part,
+                            int* __restrict__ next, int* __restrict__ cnt,
+                            double* __restrict__ sigma) {
   const int i = blockIdx.x, lane = threadIdx.x;
   double rr = 0.0, dd = 0.0, aa = 0.0;
   for (int b = lane; b < nblk; b += 32) {
@@ -162,15 +166,29 @@ __global__ void k_ir_reduce(int nblk, double rtol2, double floor2, const int* __
     const int at = atomicAdd(cnt, 1);
     next[2 * at] = list[2 * i];
     next[2 * at + 1] = 0;
+    sigma[list[2 * i]] = sqrt(rr / n);       // rr > 0 here
   }
 }
 
-// X += E on the listed systems
-__global__ void k_ir_apply(int n, const int* __restrict__ list, double* __restrict__ X,
-                           const double* __restrict__ E) {
-  const long base = (long)list[2 * blockIdx.y] * n;
+// G <- G / (dt sigma) on the listed systems: the FP32 solve's source, whose
+// right-hand side dt G is then r / sigma
+__global__ void k_ir_scale(int n, double dt, const int* __restrict__ list,
+                           const double* __restrict__ sigma, double* __restrict__ G) {
+  const int s = list[2 * blockIdx.y];
+  const long base = (long)s * n;
+  const double f = 1.0 / (dt * sigma[s]);
   for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
-    X[base + k] += E[base + k];
+    G[base + k] *= f;
+}
+
+// X += sigma E on the listed systems
+__global__ void k_ir_apply(int n, const int* __restrict__ list, const double* __restrict__ sigma,
+                           double* __restrict__ X, const double* __restrict__ E) {
+  const int s = list[2 * blockIdx.y];
+  const long base = (long)s * n;
+  const double sg = sigma[s];
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+    X[base + k] = fma(sg, E[base + k], X[base + k]);
 }
 
 __global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restrict__ one) {
@@ -196,7 +214,7 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   const size_t vec = (size_t)batch * n;
   const int nblk = (n + IR_THREADS * IR_PTS - 1) / (IR_THREADS * IR_PTS);
   // X, D, G, E (FP64), partial sums, two system lists, the counter, the constant 1
-  const size_t need = sizeof(double) * (4 * vec + (size_t)batch * nblk * 3 + 8) +
+  const size_t need = sizeof(double) * (4 * vec + (size_t)batch * nblk * 3 + (size_t)batch + 8) +
                       sizeof(int) * (4 * (size_t)batch + 8);
   lrp_status s;
   if (op->irws.bytes < need)
@@ -208,7 +226,8 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   double* G = D + vec;
   double* E = G + vec;
   double* part = E + vec;
-  double* one = part + (size_t)batch * nblk * 3;
+  double* sigma = part + (size_t)batch * nblk * 3;
+  double* one = sigma + batch;
   int* listA = reinterpret_cast<int*>(one + 8);
   int* listB = listA + 2 * batch;
   int* cnt = listB + 2 * batch;
@@ -245,7 +264,7 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
         k_ir_resid<<<dim3(nblk, nact), IR_THREADS, 0, st>>>(op->mx, op->my, plan->dt, B64, ldb, cur, X, D,
                                                             G, part);
         cudaMemsetAsync(cnt, 0, sizeof(int), st);
-        k_ir_reduce<<<nact, 32, 0, st>>>(nblk, rtol2, floor2, cur, part, nxt, cnt);
+        k_ir_reduce<<<nact, 32, 0, st>>>(nblk, n, rtol2, floor2, cur, part, nxt, cnt, sigma);
         timer_end(c, fam, ev);
         e = cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (!e) e = cudaStreamSynchronize(st);
@@ -255,9 +274,10 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
         if (nact == 0) break;
         if (round == IR_MAX_ROUNDS || op->max_iter == 0) { notconv = true; break; }
         // the correction of every system still above the tolerance: FP32
-        // CG on B e = dt G = r from e = 0 (zero input, the residual as the
-        // step's source), on chip
+        // CG on B e = dt G = r / sigma from e = 0 (zero input, the scaled
+        // residual as the step's source), on chip
         std::swap(cur, nxt);
+        k_ir_scale<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, plan->dt, cur, sigma, G);
         KryArgs a{};
         a.mx = op->mx;
         a.my = op->my;
@@ -287,7 +307,7 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
         a.iters = iters;
         a.status = istat;
         if ((s = stencil_propagate_onchip(c, op, plan, 1, nact, 1, a))) return s;
-        k_ir_apply<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, cur, X, E);
+        k_ir_apply<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, cur, sigma, X, E);
       }
       if (notconv) break;
     }

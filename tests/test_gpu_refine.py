@@ -99,6 +99,22 @@ def test_refine_full_size_511_default(ctx, orc):
         assert rel(got[v], want[v]) <= 1e-9, (v, rel(got[v], want[v]))
 
 
+@pytest.mark.parametrize("scale", [1e-40, 1e30])
+def test_refine_states_outside_fp32_range(ctx, orc, scale):
+    """States decayed below (or grown above) the FP32 range: the residual is
+    scaled per system before the FP32 correction solve."""
+    op, oop = _diff(ctx, orc, 63, rtol64=1e-13)
+    X = np.random.default_rng(5).standard_normal((2, 63 * 63)) * scale
+    ctx.set_param("krylov_refine", 1)
+    try:
+        got = api.propagate(ctx, op, 1.0 / 4096, 3, X)
+    finally:
+        ctx.set_param("krylov_refine", 0)
+    want = orc.propagate(oop, 1.0 / 4096, 3, X)
+    for v in range(2):
+        assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
+
+
 def test_refine_parareal_and_f64_build(ctx, orc):
     """An all-FP64 build (its sketch batches in refinement batches) and
     Parareal iterates on a 63^2 diffusion problem with the refinement forced,
