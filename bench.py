@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--batch-per-grid", type=int, default=2,
                     help="batch mode: problems per grid size of the uneven 2D batch")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "serve", "krylov", "batch", "cfg3", "trisweep"],
+                    choices=["solve", "serve", "krylov", "batch", "cfg3", "trisweep", "exp3"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
                          "of the 2D Krylov fine propagator (HBM GB/s fraction)")
@@ -477,7 +477,7 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
                     "us_per_system_step": ms_r * 1e3 / (nsys * steps),
                     "speedup_vs_f64_kernel": out["f64"]["us_per_system_step"] / (ms_r * 1e3 / (nsys * steps)),
                     "fp32_cg_iterations_per_step": its_r / (nsys * steps),
-                    "inner_rtol": 1e-4,
+                    "inner_rtol": 1e-3,
                     "kernels": "k_ir_resid + k_ir_reduce (FP64 residual, scaled-norm test), "
                                "k_ir_scale, k_cg_onchip<float> (correction), k_ir_apply"}
                 for d in refine_digits:
@@ -805,6 +805,74 @@ def run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world):
             "cls_out": cls_out, "ts_out": ts_out}
 
 
+def run_exp3(args):
+    """Experiment 3's time-dependent 2D heat equation at its own size (99^2
+    grid, N = 10 intervals of M = 10 steps, R = 6, p = 1; every fine step its
+    own operator): one step = the mixed coarse build + the Parareal solve to
+    tol 1e-8, backward Euler and the SDIRK2-L stepper (the operator at both
+    stage times), CUDA events on the library's stream; the error of the last
+    timed result against the oracle's sequential FP64 fine solution."""
+    import torch
+    from paper_2508_08873_gb300 import api, workloads as W
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    ctx = api.Context(local)
+    stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
+    P = W.heat2d_td()
+    legs = {}
+    outs = {}
+    for scheme in ("be", "sdirk2l"):
+        if scheme == "be":
+            st, c = P.extra["st_t"], P.c
+        else:
+            gam = (2.0 - 2.0 ** 0.5) / 2.0        # SDIRK2-L stage times t_J + (gamma, 1) dt
+            ts = np.array([[(J + cs) * P.dt for cs in (gam, 1.0)] for J in range(P.N * P.M)]).ravel()
+            st = W.heat2d_td_at(P.mx, ts)
+            c = np.sin(5 * np.pi * ts).reshape(P.N * P.M, 2, 1)
+        op = api.Operator.stencil5_td(ctx, P.mx, P.my, st, stepper=scheme)
+
+        def step():
+            co = api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed")
+            u, info = api.parareal_solve(ctx, co, P.u0, P.g, c, K=P.N, tol=1e-8)
+            co.close()
+            return u, info
+
+        for _ in range(max(1, args.warmup)):
+            step()
+        ms = []
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            u, info = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        outs[scheme] = (u, st, c)
+        legs[scheme] = {"ms_per_step": statistics.mean(ms), "solves_per_s": 1e3 / statistics.mean(ms),
+                        "iterations": info["k_done"], "final_bound": info["final_bound"],
+                        "krylov_iterations_total": op.krylov_iterations()}
+        op.close()
+    if rank == 0:
+        from oracle import oracle as orc
+        for scheme, (u, st, c) in outs.items():
+            oop = orc.Stencil5TD(P.mx, P.my, *(st[k] for k in "CWESN"), stepper=scheme)
+            ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0, P.g, c)
+            legs[scheme]["rel_err_vs_oracle"] = orc.rel_err(u, ref)
+    be = legs["be"]
+    line = {"metric": "Parareal solves/s at 1e-8 rel err vs FP64 oracle", "value": be["solves_per_s"],
+            "unit": "solves/s", "mode": "exp3", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": be["ms_per_step"], "higher_is_better": True,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "heat2d_td 99^2 (Experiment 3: time-dependent conductivity, "
+                                   "source) N=10 M=10 R=6 p=1 tol=1e-8",
+                       "step": "build_coarse (mixed) + parareal_solve"},
+            "backward_euler": be, "sdirk2l": legs["sdirk2l"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def run_trisweep(args):
     """CUDA-event time per launch of the FP64 fine-solve kernels on adr1d
     (n = 4095, 256 steps) over batch sizes and chunk lengths: the general
@@ -869,6 +937,9 @@ def main():
     rank, world, local = dist_env()
     if args.mode == "trisweep":
         run_trisweep(args)
+        return
+    if args.mode == "exp3":
+        run_exp3(args)
         return
     if args.mode == "serve":
         run_serve(args)

@@ -147,12 +147,13 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    update, repeated until the FP64 test of the Krylov
  *                    kernels passes or the residual reaches its rounding
  *                    level 8 u_64 ||D^1/2 (|d| + |B||x|)||; at most 60 rounds
- *                    per step, else LRP_ENOTCONV): 0 (default) where the FP32
- *                    on-chip kernel takes the grid and the FP64 one does not
- *                    (e.g. 511 x 511), 1 wherever the FP32 on-chip kernel
- *                    takes the grid, 2 never;
+ *                    per step, else LRP_ENOTCONV): 0 (default) and 1
+ *                    wherever the FP32 on-chip kernel takes the grid (and
+ *                    the block CG was not requested), 2 never (the FP64
+ *                    Krylov kernels: on chip where the grid fits, else in
+ *                    global memory);
  *   "krylov_refine_digits": relative tolerance 10^-digits (1..7) of the FP32
- *                    correction solves (0 = automatic: 1e-4).
+ *                    correction solves (0 = automatic: 1e-3).
  * Results do not depend on these settings beyond rounding (the block
  * solver stops every system on the same residual test as the others). */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);

@@ -58,7 +58,7 @@ struct Ctx {
   int p_krylov_block = 0;    // block CG over this many systems for symmetric 2D operators (0 off, 4)
   int p_krylov_block_clusters = 0;  // clusters in flight of the block CG (0: workspaces within 96 MB)
   int p_krylov_refine = 0;   // FP64 2D steps by iterative refinement: 0 auto, 1 where it applies, 2 never
-  int p_krylov_refine_digits = 0;   // relative tolerance 10^-digits of its FP32 solves (0: 1e-4)
+  int p_krylov_refine_digits = 0;   // relative tolerance 10^-digits of its FP32 solves (0: 1e-3)
   int bk_last[3] = {0, 0, 0};  // last block CG launch: systems per block, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
@@ -347,8 +347,9 @@ lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int
                                     int prec, const KryArgs& base);
 // FP64 steps of symmetric time-invariant 5-point operators by mixed-precision
 // iterative refinement (stencil_refine.cu): FP64 residuals, FP32 on-chip CG
-// corrections, the FP64 Krylov kernels' stopping test.  Applies (automatic
-// mode) where the FP32 on-chip kernel takes the grid and the FP64 one does not.
+// corrections, the FP64 Krylov kernels' stopping test.  Applies (unless
+// krylov_refine = 2, or the block CG was requested and applies) wherever the
+// FP32 on-chip kernel takes the grid.
 bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys);
 lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
                                     const PropIn& in, const PropOut& out, const PropSrc& src);

@@ -659,11 +659,12 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
     if (in.interval0 < 0 || (last + 1) * M > op->nJ)
       return set_err(c, LRP_EINVAL, "time-dependent operator: steps beyond its time grid");
   }
-  if (!sdirk && !td && stencil_refine_applies(c, op, prec, nsys)) {
+  const bool block = !sdirk && !td && stencil_block_applies(c, op, prec, nsys, M, src.Q);
+  if (!block && !sdirk && !td && stencil_refine_applies(c, op, prec, nsys)) {
     c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
+    c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
     return stencil_propagate_refine(c, op, plan, M, nsys, in, out, src);
   }
-  const bool block = !sdirk && !td && stencil_block_applies(c, op, prec, nsys, M, src.Q);
   if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
   const bool onchip = !sdirk && !td && !block && stencil_onchip_applies(c, op, prec, nsys);
   if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;

@@ -31,7 +31,9 @@ pytestmark = pytest.mark.gpu
 def ctx():
     c = api.Context(0)
     c.set_param("krylov_block", 4)
+    c.set_param("krylov_refine", 2)      # single-system comparisons on the Krylov kernels themselves
     yield c
+    c.set_param("krylov_refine", 0)
     c.set_param("krylov_block", 0)
     c.set_param("krylov_block_clusters", 0)
 

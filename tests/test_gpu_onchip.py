@@ -8,7 +8,9 @@ columns that leave a partial last warp, CTAs with fewer rows than the others,
 non-square grids, the row counts per CTA (8 and 16 in FP64, 16 and 32 in
 FP32) and both precisions; the same cases through the kernel with the Krylov vectors in
 global memory (krylov_onchip = 2) check that the two agree with the oracle
-alike.  FP64 at rtol 1e-14 is compared at 1e-10 relative L2: the FP64
+alike.  FP64 steps by iterative refinement (the library's default for these
+grids) are switched off here (krylov_refine = 2) and tested in
+test_gpu_refine.py.  FP64 at rtol 1e-14 is compared at 1e-10 relative L2: the FP64
 cases run the same kernel code and catch any error of its logic.  FP32 (rtol
 1e-6 per step, the sketch setting) is compared at 1e-3 on grids above 128
 rows and 2e-4 below: the error of a step solved to a relative residual rtol
@@ -29,7 +31,9 @@ pytestmark = pytest.mark.gpu
 @pytest.fixture(scope="module")
 def ctx():
     c = api.Context(0)
+    c.set_param("krylov_refine", 2)      # FP64 steps on the FP64 Krylov kernels themselves
     yield c
+    c.set_param("krylov_refine", 0)
     c.set_param("krylov_onchip", 0)
     c.set_param("krylov_cluster", 0)
 

@@ -11,7 +11,7 @@ can fall below that level), so it is held to the same bars: 1e-10 relative L2 at
 (krylov_refine = 1) and on the 511^2 workload where it is the default; the
 kernel with its Krylov vectors in global memory (krylov_refine = 2) is held to
 the same bars on the same inputs.  Every tolerance of the inner FP32 solves
-(krylov_refine_digits 2, 4, 6) reaches the FP64 result; only the number of
+(krylov_refine_digits 2, 4, 6; default 3) reaches the FP64 result; only the number of
 rounds changes.
 """
 import numpy as np
