@@ -623,9 +623,11 @@ def rsvd_interval_indep(op, dt, M, i, R, p, seed, tau=MGS_TAU) -> CoarseInterval
     F' ~ Q X; the SVD of X (its row space orthonormalised, then the small
     SVD) gives U = Q^T Psi_s, S, V = Vh^T Phi_s.  Accuracy: exact when the
     sketches span the whole space (checked by brute force); otherwise below
-    the two-pass variant.  Parity unpinned beyond that and the closed-form
-    spectrum of the heat operator at a loose tolerance.  The least-squares
-    step is lstsq_mgs (Gram-Schmidt QR and back substitution, no LAPACK)."""
+    the two-pass variant.  Pinned also for partial sketches, against the
+    same estimate formed from the dense F' with a library pseudo-inverse and
+    SVD, and by the closed-form heat spectrum at a loose tolerance.  The
+    least-squares step is lstsq_mgs (Gram-Schmidt QR and back substitution,
+    no LAPACK)."""
     n = op.n
     ell = R + p
     ell2 = 2 * ell

@@ -107,3 +107,32 @@ def test_rsvd_indep_heat_spectrum_and_orientation(orc):
     assert np.max(np.abs(c.S[:6] - sig[:6])) <= 1e-7 * sig[0]
     FV = orc.propagate(op, P.dt, P.M, c.V[:, :4].T).T
     np.testing.assert_allclose(FV, c.U[:, :4] * c.S[:4], atol=1e-7 * c.S[0])
+
+
+@pytest.mark.parametrize("maker", ["heat", "adr"])
+def test_rsvd_indep_partial_sketch_equals_pseudoinverse_formula(orc, maker):
+    """A partial sketch (l = R + p < n): the two-sided estimate of Sec. 2.2 is
+    Q^T X with Q = orth(Y), X = (Psi^T Q^T)^+ Psi^T F' (the least-squares
+    core), truncated to rank R.  Built here from the dense F', the same
+    Gaussian vectors and numpy's pseudo-inverse and SVD: the oracle's Gram-
+    Schmidt least squares and Jacobi SVD must give the same rank-R operator
+    and singular values.  A transposed operand, the wrong sketch in the
+    core or a dropped factor changes the result by O(sigma_1)."""
+    n, dt, M, R, p, seed, i = 40, 2e-3, 6, 4, 3, 11, 2
+    lo, di, up = W.heat1d_op(n) if maker == "heat" else W.adr1d_op(n, nu=0.05)
+    op = orc.Tridiag(lo, di, up)
+    Fp = orc.propagate(op, dt, M, np.eye(n)).T                 # F' column by column
+    ell = R + p
+    omega = orc.gauss_block(seed, i, n, ell)                   # rows omega_j
+    psi = orc.gauss_block(seed, i, n, 2 * ell, stream=orc.STREAM_PSI)
+    Qm, _ = np.linalg.qr((omega @ Fp.T).T)                     # n x l basis of range(F' Omega)
+    X = np.linalg.pinv(psi @ Qm) @ (psi @ Fp)                  # l x n least-squares core
+    Us, s, Vt = np.linalg.svd(Qm @ X)
+    Gex = Us[:, :R] @ np.diag(s[:R]) @ Vt[:R]
+    c = orc.rsvd_interval_indep(op, dt, M, i, R, p, seed)
+    np.testing.assert_allclose(c.S, s[:R], rtol=0, atol=1e-9 * s[0])
+    G = c.U @ np.diag(c.S) @ c.V.T
+    np.testing.assert_allclose(G, Gex, rtol=0, atol=1e-9 * s[0])
+    # not the exact truncated SVD: the partial sketch is an estimate
+    sf = np.linalg.svd(Fp, compute_uv=False)
+    assert np.abs(c.S - sf[:R]).max() > 1e-8 * sf[0]
