@@ -79,6 +79,8 @@ def parse():
     ap.add_argument("--krylov-refine", type=int, default=0, choices=[0, 1],
                     help="krylov mode: 1 forces the FP64 iterative refinement where the FP32 "
                          "on-chip kernel takes the grid (0: the library's default)")
+    ap.add_argument("--krylov-adv", action="store_true",
+                    help="krylov mode: the nonsymmetric advection-diffusion operator (BiCGStab)")
     ap.add_argument("--refine-digits", default="",
                     help="krylov mode: also time the FP64 iterative refinement with these inner "
                          "FP32 tolerances 10^-d (comma list)")
@@ -384,7 +386,7 @@ ONCHIP_DRAM_BYTES_PER_SYSTEM = (38.77e6 + 1.02e6) / 16
 
 def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, block: int = 0,
                block_clusters: int = 0, refine_digits=(), m: int = 511,
-               refine_mode: int = 0) -> dict:
+               refine_mode: int = 0, adv: bool = False) -> dict:
     """The 2D fine propagator's bandwidth (the 'HBM GB/s frac' part of the
     metric): diff2d (511^2, kappa checkerboard, dt = 1/4096), Jacobi-PCG per
     backward-Euler step, FP32 sketch propagations (rtol 1e-6) and FP64 fine
@@ -402,6 +404,8 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
     import torch
     from paper_2508_08873_gb300 import api, workloads as W
     P = W.diff2d(m=m, T=128 * 32 / 4096)            # dt = 1/4096 at every grid size
+    if adv:                                         # the nonsymmetric operator (BiCGStab)
+        P.st = W.adv2d_op(m, 0.01)
     op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
     op.set_krylov(1e-12, 1e-6, 20000)
     ctx.set_param("krylov_refine", 2)
@@ -491,8 +495,9 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
         ctx.set_param("krylov_block", 0)
         ctx.set_param("krylov_block_clusters", 0)
         op.close()
-    return {"workload": f"diff2d {m}^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG, one "
-                        "backward-Euler step per system",
+    return {"workload": (f"adv2d {m}^2 nu=0.01, dt=1/4096, Jacobi-BiCGStab" if adv else
+                         f"diff2d {m}^2 kappa 8x8 checkerboard, dt=1/4096, Jacobi-PCG") +
+                        ", one backward-Euler step per system",
             "peak_source": peak_src, "algorithmic_bytes": "6 words per grid point and CG "
                                                           "iteration (x, r, p read + written)",
             **out}
@@ -509,7 +514,7 @@ def run_krylov(args):
     res = krylov_leg(ctx, precs, nsyss, args.steps, args.warmup, args.krylov_onchip,
                      args.krylov_block, args.krylov_block_clusters,
                      [int(v) for v in args.refine_digits.split(",") if v], args.krylov_m,
-                     args.krylov_refine)
+                     args.krylov_refine, args.krylov_adv)
     head = res["f64" if precs[0] == "f64" else "f32"]
     line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
             "value": head["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,

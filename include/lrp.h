@@ -141,17 +141,21 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    a device workspace of the operator);
  *   "krylov_block_clusters": clusters in flight of the block CG (0 =
  *                    automatic: workspaces within 96 MB);
- *   "krylov_refine": FP64 steps of symmetric time-invariant 5-point
- *                    operators by mixed-precision iterative refinement (FP64
- *                    residual, FP32 on-chip CG correction from zero, FP64
- *                    update, repeated until the FP64 test of the Krylov
- *                    kernels passes or the residual reaches its rounding
- *                    level 8 u_64 ||D^1/2 (|d| + |B||x|)||; at most 60 rounds
- *                    per step, else LRP_ENOTCONV): 0 (default) and 1
- *                    wherever the FP32 on-chip kernel takes the grid (and
- *                    the block CG was not requested), 2 never (the FP64
- *                    Krylov kernels: on chip where the grid fits, else in
- *                    global memory);
+ *   "krylov_refine": FP64 steps of time-invariant 5-point operators by
+ *                    mixed-precision iterative refinement (FP64 residual,
+ *                    FP32 correction from zero -- CG on the on-chip kernel
+ *                    for symmetric operators, BiCGStab on the global-memory
+ *                    kernel otherwise -- FP64 update, repeated until the
+ *                    FP64 test of the Krylov kernels passes or the residual
+ *                    reaches its rounding level 8 u_64 ||D^1/2 (|d| +
+ *                    |B||x|)||; at most 60 rounds per step, else
+ *                    LRP_ENOTCONV): 0 (default) or 1: nonsymmetric
+ *                    operators always, symmetric ones wherever the FP32
+ *                    on-chip kernel takes the grid (and the block CG was not
+ *                    requested); 2 never (the FP64 Krylov kernels: on chip
+ *                    where the grid fits, else in global memory).  SDIRK
+ *                    steppers, time-dependent operators and the batched
+ *                    solves keep the FP64 Krylov kernels;
  *   "krylov_refine_digits": relative tolerance 10^-digits (1..7) of the FP32
  *                    correction solves (0 = automatic: 1e-3).
  * Results do not depend on these settings beyond rounding (the block

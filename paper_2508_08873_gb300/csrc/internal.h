@@ -347,10 +347,15 @@ lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int
                                     int prec, const KryArgs& base);
 // FP64 steps of symmetric time-invariant 5-point operators by mixed-precision
 // iterative refinement (stencil_refine.cu): FP64 residuals, FP32 on-chip CG
-// corrections, the FP64 Krylov kernels' stopping test.  Applies (unless
-// krylov_refine = 2, or the block CG was requested and applies) wherever the
-// FP32 on-chip kernel takes the grid.
+// or BiCGStab corrections, the FP64 Krylov kernels' stopping test.  Applies
+// (unless krylov_refine = 2, or the block CG was requested and applies) to
+// nonsymmetric operators, and to symmetric ones wherever the FP32 on-chip
+// kernel takes the grid.
 bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys);
+// One FP32 launch of the global-memory Krylov kernel (k_krylov<float>,
+// backward-Euler steps) for the correction solves of the refinement of
+// nonsymmetric operators; a: the kernel arguments without B, Bs, ws, nvec.
+lrp_status krylov_f32_correction(Ctx* c, Operator* op, StencilPlan* plan, int nsys, KryArgs& a);
 lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
                                     const PropIn& in, const PropOut& out, const PropSrc& src);
 size_t krylov_queue_nvec(int bicg);

@@ -636,6 +636,77 @@ static int cluster_size_for(int mx, int my) {
   return cs;
 }
 
+// Launch shape of k_krylov for a batch: the cluster size with the most CTAs in
+// flight (the largest on a tie: fewest points per CTA, shortest iteration;
+// clusters of 16 fit once per GPC, smaller ones pack the GPCs more densely),
+// with the workspaces of the clusters in flight within 96 MB so that the
+// Krylov vectors stay L2-resident (129 MB L2).
+static void krylov_shape(Ctx* c, const Operator* op, int prec, int nvec, int nsys,
+                         void (*kern)(KryArgs), int* cs_out, int* ncl_out) {
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(KRY_THREADS);
+  const int cs_max = cluster_size_for(op->mx, op->my);
+  const size_t es_ = prec == 0 ? 8 : 4;
+  const size_t ws_one = (size_t)nvec * ((size_t)op->n + 2 * op->mx) * es_;
+  const int ws_cap = (int)std::max<size_t>(1, ((size_t)96 << 20) / ws_one);
+  int cs = cs_max, nclusters = 1;
+  long best = -1;
+  for (int cc = cs_max; cc >= 1 && cc >= cs_max / 4; cc /= 2) {
+    if (c->p_krylov_cluster > 0 && cc != std::min(c->p_krylov_cluster, cs_max)) continue;
+    if ((op->my + cc - 1) / cc * (cc - 1) >= op->my && cc > 1) continue;   // every CTA owns rows
+    attr[0].val.clusterDim.x = cc;
+    cfg.gridDim = dim3(cc);
+    int maxc = 0;
+    cudaError_t e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+    if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / cc); }
+    const int ncl = std::min(std::min(nsys, maxc), ws_cap);
+    const long ctas = (long)ncl * cc;
+    if (ctas > best) { best = ctas; cs = cc; nclusters = ncl; }
+  }
+  *cs_out = cs;
+  *ncl_out = nclusters;
+}
+
+lrp_status krylov_f32_correction(Ctx* c, Operator* op, StencilPlan* plan, int nsys, KryArgs& a) {
+  auto kern = (void (*)(KryArgs))k_krylov<float>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+  if (e) return cuda_err(c, e, "krylov cluster attribute");
+  const int nvec = (int)krylov_queue_nvec(a.bicg);
+  int cs = 1, ncl = 1;
+  krylov_shape(c, op, 1, nvec, nsys, kern, &cs, &ncl);
+  const size_t need = (size_t)ncl * nvec * ((size_t)op->n + 2 * op->mx) * 4;
+  lrp_status s;
+  if (op->kws.bytes < need)
+    if ((s = dev_alloc(c, op->kws, need))) return s;
+  a.B = stencil_B(plan, op, 1);
+  a.Bs = stencil_Bs(plan, op, 1);
+  a.ws = op->kws.ptr;
+  a.nvec = nvec;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = cs;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cfg.blockDim = dim3(KRY_THREADS);
+  cfg.gridDim = dim3(ncl * cs);
+  cfg.stream = c->stream;
+  cudaEvent_t ev = nullptr;
+  timer_begin(c, "propagate_f32", &ev);
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  timer_end(c, "propagate_f32", ev);
+  if (e) return cuda_err(c, e, "k_krylov launch");
+  return LRP_OK;
+}
+
 lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
                              int prec, const PropIn& in, const PropOut& out, const PropSrc& src) {
   if (nsys <= 0) return LRP_OK;
@@ -684,29 +755,8 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   cfg.numAttrs = 1;
   cfg.blockDim = dim3(KRY_THREADS);
   cfg.stream = c->stream;
-  // cluster size: the largest (fewest points per CTA, shortest iteration) among
-  // those that keep the most CTAs in flight for this batch; clusters of 16 fit
-  // once per GPC, smaller ones pack the GPCs more densely
-  // The workspaces of the clusters in flight stay within 96 MB so that the
-  // Krylov vectors remain L2-resident (129 MB L2).
-  const int cs_max = cluster_size_for(op->mx, op->my);
-  const size_t es_ = prec == 0 ? 8 : 4;
-  const size_t ws_one = (size_t)nvec * ((size_t)op->n + 2 * op->mx) * es_;
-  const int ws_cap = (int)std::max<size_t>(1, ((size_t)96 << 20) / ws_one);
-  int cs = cs_max, nclusters = 1;
-  long best = -1;
-  for (int cc = cs_max; cc >= 1 && cc >= cs_max / 4; cc /= 2) {
-    if (c->p_krylov_cluster > 0 && cc != std::min(c->p_krylov_cluster, cs_max)) continue;
-    if ((op->my + cc - 1) / cc * (cc - 1) >= op->my && cc > 1) continue;   // every CTA owns rows
-    attr[0].val.clusterDim.x = cc;
-    cfg.gridDim = dim3(cc);
-    int maxc = 0;
-    e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
-    if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / cc); }
-    const int ncl = std::min(std::min(nsys, maxc), ws_cap);
-    const long ctas = (long)ncl * cc;
-    if (ctas > best) { best = ctas; cs = cc; nclusters = ncl; }
-  }
+  int cs = 1, nclusters = 1;
+  krylov_shape(c, op, prec, nvec, nsys, kern, &cs, &nclusters);
   attr[0].val.clusterDim.x = cs;
   cfg.gridDim = dim3(nclusters * cs);
   const size_t es = prec == 0 ? 8 : 4;

@@ -115,6 +115,33 @@ def test_refine_states_outside_fp32_range(ctx, orc, scale):
         assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
 
 
+@pytest.mark.parametrize("m", [31, 127])
+def test_refine_nonsymmetric_bicgstab(ctx, orc, m):
+    """Upwind advection-diffusion (nonsymmetric): FP32 BiCGStab corrections
+    on the global-memory kernel (the default for nonsymmetric operators), the
+    plain residual test of BiCGStab, with a source and the adjoint."""
+    st = W.adv2d_op(m, 0.01)
+    op = api.Operator.stencil5(ctx, m, m, st)
+    op.set_krylov(1e-14, 1e-6, 20000)
+    oop = orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"])
+    dt, M = 1.0 / 2048, 3
+    rng = np.random.default_rng(30 + m)
+    X = rng.standard_normal((3, m * m))
+    g = rng.standard_normal((1, m * m))
+    c = rng.standard_normal((3, M, 1))
+    ctx.set_param("krylov_refine", 1)
+    try:
+        got = api.propagate(ctx, op, dt, M, X, g=g, c=c)
+        adj = api.propagate(ctx, op, dt, M, X, adjoint=True)
+    finally:
+        ctx.set_param("krylov_refine", 0)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=c)
+    wadj = orc.propagate(oop, dt, M, X, adjoint=True)
+    for v in range(3):
+        assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
+        assert rel(adj[v], wadj[v]) <= 1e-10, (v, rel(adj[v], wadj[v]))
+
+
 def test_refine_parareal_and_f64_build(ctx, orc):
     """An all-FP64 build (its sketch batches in refinement batches) and
     Parareal iterates on a 63^2 diffusion problem with the refinement forced,
