@@ -76,9 +76,10 @@ def parse():
                     help="--mode krylov: clusters in flight of the block CG (0: automatic)")
     ap.add_argument("--krylov-m", type=int, default=511,
                     help="krylov mode: grid size m of the diff2d m x m operator")
-    ap.add_argument("--krylov-refine", type=int, default=0, choices=[0, 1],
+    ap.add_argument("--krylov-refine", type=int, default=0, choices=[0, 1, 2],
                     help="krylov mode: 1 forces the FP64 iterative refinement where the FP32 "
-                         "on-chip kernel takes the grid (0: the library's default)")
+                         "on-chip kernel takes the grid (0: the library's default); batch "
+                         "mode: 2 runs the FP64 fine steps on the FP64 Krylov kernels")
     ap.add_argument("--krylov-adv", action="store_true",
                     help="krylov mode: the nonsymmetric advection-diffusion operator (BiCGStab)")
     ap.add_argument("--refine-digits", default="",
@@ -586,6 +587,7 @@ def run_batch(args):
             Ps.append(W.adv2d(len(Ps), m=m))
     ops = [api.Operator.stencil5(ctx, P.mx, P.my, P.st) for P in Ps]
     P0 = Ps[0]
+    ctx.set_param("krylov_refine", args.krylov_refine)
 
     def step():
         ctx.set_kernel_timing(True)
@@ -621,6 +623,8 @@ def run_batch(args):
                                    "R=24, p=8, BiCGStab, tol=1e-8" % (len(Ps), args.batch_per_grid,
                                                                        list(W.ADV2D_GRIDS))},
             "build_ms": statistics.mean(ms_b), "solve_ms": statistics.mean(ms_s),
+            "fp64_steps": "FP64 Krylov kernels" if args.krylov_refine == 2
+                          else "in-kernel iterative refinement (FP32 BiCGStab corrections)",
             "iterations": [int(k) for k in kd], "grids": [P.mx for P in Ps],
             "kernels": {f: {"launches": v[0], "ms_total": v[1]} for f, v in kt.items()}}
     print(json.dumps(line), flush=True)

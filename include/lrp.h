@@ -153,9 +153,11 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    operators always, symmetric ones wherever the FP32
  *                    on-chip kernel takes the grid (and the block CG was not
  *                    requested); 2 never (the FP64 Krylov kernels: on chip
- *                    where the grid fits, else in global memory).  SDIRK
- *                    steppers, time-dependent operators and the batched
- *                    solves keep the FP64 Krylov kernels;
+ *                    where the grid fits, else in global memory).  The
+ *                    batched solves (lrp_parareal_solve_batch) refine inside
+ *                    their persistent queue kernel unless 2; SDIRK steppers
+ *                    and time-dependent operators keep the FP64 Krylov
+ *                    kernels;
  *   "krylov_refine_digits": relative tolerance 10^-digits (1..7) of the FP32
  *                    correction solves (0 = automatic: 1e-3).
  * Results do not depend on these settings beyond rounding (the block

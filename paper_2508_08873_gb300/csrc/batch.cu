@@ -322,9 +322,13 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
     if (e) return cuda_err(c, e, "batch solve input");
   }
   const int cs = c->p_queue_cluster > 0 ? c->p_queue_cluster : 4;
-  const int nclu = krylov_queue_clusters(c, 0, cs);
+  // FP64 fine steps by in-kernel iterative refinement (FP32 Krylov
+  // corrections) unless krylov_refine = 2
+  const int qprec = c->p_krylov_refine == 2 ? 0 : 2;
+  const int nclu = krylov_queue_clusters(c, qprec, cs);
   const size_t nvec = krylov_queue_nvec(bicg);
-  const size_t ws_stride = ((nvec * maxn * 8 + 255) / 256) * 256;
+  const size_t ws_one = qprec == 2 ? krylov_queue_ir_bytes(maxn) : nvec * maxn * 8;
+  const size_t ws_stride = ((ws_one + 255) / 256) * 256;
   // Queue items interval-major, intervals N-1 down to 0 and within an
   // interval the problems largest grid first: iteration k (intervals >= k)
   // is the prefix of count (N - k) items.  Per problem: a stop flag and
@@ -357,6 +361,9 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
     a.dt = q->dt; a.rtol = op->rtol64; a.max_iter = op->max_iter; a.nvec = (int)nvec;
     a.B = stencil_B(pf[p], op, 0);
     a.Bs = stencil_Bs(pf[p], op, 0);
+    a.B32 = stencil_B(pf[p], op, 1);
+    a.Bs32 = stencil_Bs(pf[p], op, 1);
+    a.rtol_in = c->p_krylov_refine_digits > 0 ? std::pow(10.0, -c->p_krylov_refine_digits) : 1e-3;
     a.in.x = q->ws_u.ptr; a.in.x_f64 = 1; a.in.ldx = op->n;
     a.in.stop = dflag + 2 * p;
     a.out.y = q->ws_F.ptr; a.out.y_f64 = 1; a.out.ldy = op->n;
@@ -431,7 +438,7 @@ lrp_status lrp_parareal_solve_batch(lrp_ctx* c, int count, lrp_coarse* const* co
     const int kb = std::min(K, k + batch);
     batch = std::min(4, 2 * batch);
     for (; k < kb && !s; ++k) {
-      if ((s = krylov_queue_launch(c, 0, d_probs.as<KryArgs>(), d_items.as<int>(), count * (N - k),
+      if ((s = krylov_queue_launch(c, qprec, d_probs.as<KryArgs>(), d_items.as<int>(), count * (N - k),
                                    d_cnt.as<unsigned int>() + k, ws.ptr, ws_stride, cs, nclu)))
         break;
       s = coarse_sweep_ex(c, &hv[(size_t)(k + 1) * count], dargs + (size_t)(k + 1) * count, count, 0);

@@ -324,6 +324,11 @@ struct KryArgs {
   PropSrc src;
   unsigned long long* iters;   // total Krylov iterations
   int* status;                 // bit 0: cap hit, bit 1: breakdown
+  // in-kernel iterative refinement (k_krylov_queue_ir; B, Bs in FP64): the
+  // FP32 plans of the same step matrix and the FP32 solves' tolerance
+  const void* B32;
+  const void* Bs32;
+  double rtol_in;
 };
 lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out);
 // On-chip CG (stencil_onchip.cu): symmetric operators with at most 512 grid
@@ -363,7 +368,10 @@ size_t krylov_queue_nvec(int bicg);
 const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec);
 // The same for KryArgs::Bs (symmetric operators; nullptr otherwise).
 const void* stencil_Bs(const StencilPlan* pl, const Operator* op, int prec);
+// prec: 0 FP64, 1 FP32, 2 FP64 steps by in-kernel iterative refinement
+// (k_krylov_queue_ir, workspace krylov_queue_ir_bytes(n + 2 mx) per cluster)
 int krylov_queue_clusters(Ctx* c, int prec, int cs);
+size_t krylov_queue_ir_bytes(int maxld);
 lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const int* d_items,
                                int nitems, unsigned int* d_counter, void* ws, size_t ws_stride,
                                int cs, int nclusters);

@@ -548,6 +548,298 @@ __global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov(KryArgs a) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// FP64 steps by mixed-precision iterative refinement inside the kernel (the
+// batched queue's fine solves): per step and round, the FP64 residual
+// r = d - B x of the cluster's system and its norms (CG: scaled by 1/diag,
+// BiCGStab: plain; and the rounding level of |d| + |B||x|), one cluster
+// reduction, the test of the FP64 Krylov kernels (rtol, or the rounding
+// level 8 u_64), then FP32 Krylov iterations on B e = r / sigma from e = 0
+// to a.rtol_in and the FP64 update x += sigma e.  Workspace of a cluster:
+// two FP64 vectors (x, d) and ten FP32 vectors, each padded like the others.
+// ---------------------------------------------------------------------------
+constexpr int IRK_ROUNDS = 60;
+constexpr double IRK_FLOOR = 8.0;
+
+__device__ __forceinline__ void krylov_system_ir(const KryArgs& a, cg::cluster_group& cl, ClRed& sh,
+                                                 int& buf, int sys, void* ws_raw,
+                                                 unsigned long long& my_iters, int& my_status) {
+  const int cs = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int n = a.n, mx = a.mx;
+  const size_t ldv = (size_t)n + 2 * mx;
+  const size_t ldb = ldv;
+  const int rows_per = (a.my + cs - 1) / cs;
+  const int k0 = min(a.n, crank * rows_per * mx), k1 = min(a.n, (crank + 1) * rows_per * mx);
+  const bool cgm = !a.bicg;
+  const double* __restrict__ B64 = static_cast<const double*>(a.B);
+  const float* __restrict__ B32 = static_cast<const float*>(a.B32);
+  const float* __restrict__ Bd32 = B32 + 5 * ldb;
+  const float* __restrict__ Bs32 = static_cast<const float*>(a.Bs32);
+  double* x = static_cast<double*>(ws_raw) + mx;
+  double* dv = x + ldv;
+  float* fb = reinterpret_cast<float*>(static_cast<double*>(ws_raw) + 2 * ldv);
+  auto fvec = [&](int v) { return fb + (size_t)v * ldv + mx; };
+  float* rf = fvec(0);   // r / sigma
+  float* ev = fvec(1);   // correction (CG: scaled)
+  float* r = fvec(2);
+  float* p = fvec(3);
+  float* q = fvec(4);    // CG: B^ p; BiCG: v
+  float* rh = fvec(5);
+  float* ph = fvec(6);
+  float* sv = fvec(7);
+  float* shh = fvec(8);
+  float* tv = fvec(9);
+  // zero pads of the two FP64 and ten FP32 vectors (the stencils read them)
+  for (int e = crank * blockDim.x + threadIdx.x; e < 12 * 2 * mx; e += cs * blockDim.x) {
+    const int v = e / (2 * mx), o = e % (2 * mx);
+    const size_t at = o < mx ? (size_t)o : (size_t)n + o;
+    if (v < 2)
+      static_cast<double*>(ws_raw)[(size_t)v * ldv + at] = 0.0;
+    else
+      fb[(size_t)(v - 2) * ldv + at] = 0.0f;
+  }
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    double v = 0.0;
+    if (a.in.x != nullptr)
+      v = a.in.x_f64 ? static_cast<const double*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k]
+                     : (double)static_cast<const float*>(a.in.x)[sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) + k];
+    x[k] = v;
+  }
+  const double* csys = a.src.Q > 0
+      ? a.src.c + sys_offset(a.src.map, a.src.c_slot_stride, a.src.cstride, sys) : nullptr;
+  const double* gsys = (a.src.Q > 0 && a.src.map)
+      ? a.src.g + (long)a.src.map[2 * sys] * a.src.g_slot_stride : a.src.g;
+  const double rtol2 = a.rtol * a.rtol;
+  const double floor2 = (IRK_FLOOR * 0x1p-53) * (IRK_FLOOR * 0x1p-53);
+  const float rtol_in2 = (float)(a.rtol_in * a.rtol_in);
+  // FP64 residual of point k: r, and |d| + |B||x|
+  auto resid = [&](int k, double& ab) -> double {
+    const double t0 = B64[k] * x[k], t1 = B64[ldb + k] * x[k - 1], t2 = B64[2 * ldb + k] * x[k + 1];
+    const double t3 = B64[3 * ldb + k] * x[k - mx], t4 = B64[4 * ldb + k] * x[k + mx];
+    const double d = dv[k];
+    ab = fabs(d) + fabs(t0) + fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4);
+    return d - ((((t0 + t1) + t2) + t3) + t4);
+  };
+  for (int j = 0; j < a.M; ++j) {
+    for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+      double f = 0.0;
+      if (csys)
+        for (int qq = 0; qq < a.src.Q; ++qq) f += csys[(size_t)j * a.src.Q + qq] * gsys[(size_t)qq * n + k];
+      dv[k] = x[k] + a.dt * f;
+    }
+    cl.sync();
+    for (int round = 0;; ++round) {
+      double red[3] = {0.0, 0.0, 0.0};
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        double ab;
+        const double rk = resid(k, ab);
+        const double w = cgm ? B64[5 * ldb + k] : 1.0;
+        red[0] += rk * rk * w;
+        red[1] += dv[k] * dv[k] * w;
+        red[2] += ab * ab * w;
+      }
+      double tot[3];
+      cl_sum<double, 3>(cl, red, tot, sh, buf);
+      if (tot[0] <= rtol2 * tot[1] || tot[0] <= floor2 * tot[2]) break;
+      if (round == IRK_ROUNDS || a.max_iter == 0) { my_status |= 1; break; }
+      const double sig = sqrt(tot[0] / n);
+      // the correction solve's right-hand side and first residual (e = 0)
+      float rr0t[1] = {0.0f};
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        double ab;
+        const float rs = (float)(resid(k, ab) / sig);
+        rf[k] = rs;
+        ev[k] = 0.0f;
+        const float r0 = cgm ? rs * Bs32[5 * ldb + k] : rs;   // CG: S^-1 r
+        r[k] = r0;
+        p[k] = r0;
+        if (!cgm) rh[k] = r0;
+        rr0t[0] += r0 * r0;
+      }
+      double rr0[1];
+      cl_sum<float, 1>(cl, rr0t, rr0, sh, buf);
+      const double tol2 = (double)rtol_in2 * rr0[0];
+      double rr = rr0[0], rho = rr0[0];
+      int it = 0;
+      if (cgm) {
+        struct Sc { float w, e, s, nn, v0, v1, v2, v3, v4; };
+        while (rr > tol2 && it < a.max_iter) {
+          float pqt[1] = {0.0f};
+          for_points<Sc>(k0, k1,
+                         [&](int k) {
+                           return Sc{Bs32[k], Bs32[ldb + k], Bs32[2 * ldb + k], Bs32[3 * ldb + k],
+                                     p[k], p[k - 1], p[k + 1], p[k - mx], p[k + mx]};
+                         },
+                         [&](int k, const Sc& g) {
+                           float qk = g.v0;
+                           qk += g.w * g.v1;
+                           qk += g.e * g.v2;
+                           qk += g.s * g.v3;
+                           qk += g.nn * g.v4;
+                           q[k] = qk;
+                           pqt[0] += g.v0 * qk;
+                         });
+          double pq[1];
+          cl_sum<float, 1>(cl, pqt, pq, sh, buf);
+          if (!(pq[0] > 0.0)) break;                  // the round ends; the FP64 test decides
+          const float alpha = (float)(rho / pq[0]);
+          float rz[1] = {0.0f};
+          struct Up { float x, p, r, q; };
+          for_points<Up>(k0, k1, [&](int k) { return Up{ev[k], p[k], r[k], q[k]}; },
+                         [&](int k, const Up& g) {
+                           ev[k] = g.x + alpha * g.p;
+                           const float rk = g.r - alpha * g.q;
+                           r[k] = rk;
+                           rz[0] += rk * rk;
+                         });
+          double rzd[1];
+          cl_sum<float, 1>(cl, rz, rzd, sh, buf);
+          const float beta = (float)(rzd[0] / rho);
+          rho = rzd[0];
+          rr = rzd[0];
+          ++it;
+          struct Pu { float r, p; };
+          for_points<Pu>(k0, k1, [&](int k) { return Pu{r[k], p[k]}; },
+                         [&](int k, const Pu& g) { p[k] = g.r + beta * g.p; });
+          cl.sync();
+        }
+      } else {
+        struct St { float c0, c1, c2, c3, c4, v0, v1, v2, v3, v4; };
+        auto st_load = [&](int k, const float* v) {
+          return St{B32[k], B32[ldb + k], B32[2 * ldb + k], B32[3 * ldb + k], B32[4 * ldb + k],
+                    v[k], v[k - 1], v[k + 1], v[k - mx], v[k + mx]};
+        };
+        auto st_eval = [](const St& g) {
+          float acc = g.c0 * g.v0;
+          acc += g.c1 * g.v1;
+          acc += g.c2 * g.v2;
+          acc += g.c3 * g.v3;
+          acc += g.c4 * g.v4;
+          return acc;
+        };
+        double rho_prev = rho;
+        float alpha = 1.0f, omega = 1.0f;
+        bool first = true;
+        while (rr > tol2 && it < a.max_iter) {
+          struct Pb { float r, p, q, d; };
+          if (!first) {
+            const float beta = (float)((rho / rho_prev) * ((double)alpha / (double)omega));
+            for_points<Pb>(k0, k1, [&](int k) { return Pb{r[k], p[k], q[k], Bd32[k]}; },
+                           [&](int k, const Pb& g) {
+                             const float pk = g.r + beta * (g.p - omega * g.q);
+                             p[k] = pk;
+                             ph[k] = pk * g.d;
+                           });
+          } else {
+            for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) ph[k] = p[k] * Bd32[k];
+          }
+          first = false;
+          cl.sync();
+          float rvt[1] = {0.0f};
+          struct Sv { St s; float rh; };
+          for_points<Sv>(k0, k1, [&](int k) { return Sv{st_load(k, ph), rh[k]}; },
+                         [&](int k, const Sv& g) {
+                           const float vk = st_eval(g.s);
+                           q[k] = vk;
+                           rvt[0] += g.rh * vk;
+                         });
+          double rv[1];
+          cl_sum<float, 1>(cl, rvt, rv, sh, buf);
+          if (rv[0] == 0.0 || !isfinite(rv[0])) break;
+          alpha = (float)(rho / rv[0]);
+          struct Ss { float r, q, d; };
+          for_points<Ss>(k0, k1, [&](int k) { return Ss{r[k], q[k], Bd32[k]}; },
+                         [&](int k, const Ss& g) {
+                           const float sk = g.r - alpha * g.q;
+                           sv[k] = sk;
+                           shh[k] = sk * g.d;
+                         });
+          cl.sync();
+          float tst[2] = {0.0f, 0.0f};
+          struct Tv { St s; float sv; };
+          for_points<Tv>(k0, k1, [&](int k) { return Tv{st_load(k, shh), sv[k]}; },
+                         [&](int k, const Tv& g) {
+                           const float t = st_eval(g.s);
+                           tv[k] = t;
+                           tst[0] += t * g.sv;
+                           tst[1] += t * t;
+                         });
+          double ts[2];
+          cl_sum<float, 2>(cl, tst, ts, sh, buf);
+          omega = ts[1] > 0.0 ? (float)(ts[0] / ts[1]) : 0.0f;
+          float rrt[2] = {0.0f, 0.0f};
+          struct Xu { float x, ph, shh, sv, tv, rh; };
+          for_points<Xu>(k0, k1,
+                         [&](int k) { return Xu{ev[k], ph[k], shh[k], sv[k], tv[k], rh[k]}; },
+                         [&](int k, const Xu& g) {
+                           ev[k] = g.x + alpha * g.ph + omega * g.shh;
+                           const float rk = g.sv - omega * g.tv;
+                           r[k] = rk;
+                           rrt[0] += g.rh * rk;
+                           rrt[1] += rk * rk;
+                         });
+          double rr2[2];
+          cl_sum<float, 2>(cl, rrt, rr2, sh, buf);
+          rho_prev = rho;
+          rho = rr2[0];
+          rr = rr2[1];
+          ++it;
+          if (rr > tol2 && (omega == 0.0f || rho == 0.0)) break;
+        }
+      }
+      my_iters += it;
+      // x += sigma e (CG: e = S^-1 e^)
+      for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+        const float e = cgm ? ev[k] * Bs32[5 * ldb + k] : ev[k];
+        x[k] = fma(sig, (double)e, x[k]);
+      }
+      cl.sync();
+    }
+  }
+  const long oy = sys_offset(a.out.map, a.out.slot_stride, a.out.ldy, sys);
+  for (int k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
+    if (a.out.y_f64)
+      static_cast<double*>(a.out.y)[oy + k] = x[k];
+    else
+      static_cast<float*>(a.out.y)[oy + k] = (float)x[k];
+  }
+  cl.sync();
+}
+
+__global__ void __launch_bounds__(KRY_THREADS, 2) k_krylov_queue_ir(const KryArgs* __restrict__ probs,
+                                                                  const int* __restrict__ items,
+                                                                  int nitems,
+                                                                  unsigned int* __restrict__ counter,
+                                                                  void* ws_all, size_t ws_stride) {
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ ClRed sh;
+  __shared__ int next_item;
+  const int cs = (int)cl.num_blocks();
+  const int crank = (int)cl.block_rank();
+  const int slot = blockIdx.x / cs;
+  void* ws = static_cast<char*>(ws_all) + (size_t)slot * ws_stride;
+  cl_map(cl, sh);
+  cl.sync();   // every CTA runs before remote stores into its shared memory
+  int buf = 0;
+  while (true) {
+    if (crank == 0 && threadIdx.x == 0) next_item = (int)atomicAdd(counter, 1u);
+    cl.sync();
+    const int it = *cl.map_shared_rank(&next_item, 0);
+    cl.sync();                        // rank 0 may overwrite next_item only after all read it
+    if (it >= nitems) break;
+    const KryArgs& a = probs[items[2 * it]];
+    if (a.in.stop && *a.in.stop) continue;   // the same flag for every CTA of the cluster
+    unsigned long long my_iters = 0;
+    int my_status = 0;
+    krylov_system_ir(a, cl, sh, buf, items[2 * it + 1], ws, my_iters, my_status);
+    if (threadIdx.x == 0 && crank == 0) {
+      if (my_iters) atomicAdd(a.iters, my_iters);
+      if (my_status) atomicOr(a.status, my_status);
+    }
+  }
+}
+
 // Many problems (different grids and operators) in one persistent launch: a
 // device work queue of items (problem, system), largest grids first; each
 // cluster takes the next item from a global counter (rank 0 draws it and
@@ -843,9 +1135,16 @@ const void* stencil_Bs(const StencilPlan* pl, const Operator* op, int prec) {
                    : (const void*)(pl->bs32.as<float>() + op->mx);
 }
 
+using QueueKern = void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t);
+static QueueKern queue_kernel(int prec) {
+  return prec == 0 ? (QueueKern)k_krylov_queue<double>
+       : prec == 1 ? (QueueKern)k_krylov_queue<float> : (QueueKern)k_krylov_queue_ir;
+}
+
+size_t krylov_queue_ir_bytes(int maxld) { return (size_t)maxld * (2 * 8 + 10 * 4); }
+
 int krylov_queue_clusters(Ctx* c, int prec, int cs) {
-  auto kern = prec == 0 ? (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<double>
-                        : (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<float>;
+  auto kern = queue_kernel(prec);
   cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -869,8 +1168,7 @@ lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const i
                                int nitems, unsigned int* d_counter, void* ws, size_t ws_stride,
                                int cs, int nclusters) {
   if (nitems <= 0) return LRP_OK;
-  auto kern = prec == 0 ? (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<double>
-                        : (void (*)(const KryArgs*, const int*, int, unsigned int*, void*, size_t))k_krylov_queue<float>;
+  auto kern = queue_kernel(prec);
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e) return cuda_err(c, e, "queue cluster attribute");
   cudaLaunchConfig_t cfg = {};
@@ -884,7 +1182,7 @@ lrp_status krylov_queue_launch(Ctx* c, int prec, const KryArgs* d_probs, const i
   cfg.blockDim = dim3(KRY_THREADS);
   cfg.gridDim = dim3(nclusters * cs);
   cfg.stream = c->stream;
-  const char* fam = prec == 0 ? "propagate_f64" : "propagate_f32";
+  const char* fam = prec == 1 ? "propagate_f32" : "propagate_f64";
   cudaEvent_t ev = nullptr;
   timer_begin(c, fam, &ev);
   e = cudaLaunchKernelEx(&cfg, kern, d_probs, d_items, nitems, d_counter, ws, ws_stride);

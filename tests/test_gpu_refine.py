@@ -186,3 +186,38 @@ def test_refine_iteration_cap(ctx, orc):
     want = orc.propagate(oop, 1.0 / 4096, 2, X)
     for v in range(2):
         assert rel(got[v], want[v]) <= 1e-10
+
+
+def test_refine_batched_queue(ctx, orc):
+    """The batched uneven solve (persistent device-driven queue) with its FP64
+    fine steps refined inside the kernel (the default) and on the FP64
+    Krylov kernels (krylov_refine = 2): advection-diffusion problems
+    (BiCGStab corrections) and a diffusion problem (CG corrections) on
+    different grids, K = N against the oracle's fine solution and K = 2
+    against each other."""
+    Ps = [W.adv2d(i, m=m, N=4, M=8, R=5, p=3) for i, m in enumerate((31, 15, 23))]
+    D = W.diff2d(m=31, N=4, M=8, R=5, p=3)
+    Ps.append(D)
+    ops = []
+    for P in Ps:
+        op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+        op.set_krylov(1e-14, 1e-6, 20000)
+        ops.append(op)
+    P0 = Ps[0]
+    assert all(abs(P.dt - P0.dt) < 1e-15 for P in Ps)
+    cos = api.build_coarse_batch(ctx, ops, P0.dt, P0.M, P0.N, P0.R, P0.p, 0, prec="f64")
+    u0s = [P.u0 for P in Ps]
+    out_ir, kd = api.parareal_solve_batch(ctx, cos, u0s, K=P0.N)
+    k2_ir, _ = api.parareal_solve_batch(ctx, cos, u0s, K=2)
+    ctx.set_param("krylov_refine", 2)
+    try:
+        out_64, _ = api.parareal_solve_batch(ctx, cos, u0s, K=P0.N)
+        k2_64, _ = api.parareal_solve_batch(ctx, cos, u0s, K=2)
+    finally:
+        ctx.set_param("krylov_refine", 0)
+    for P, a, b, c2, d2 in zip(Ps, out_ir, out_64, k2_ir, k2_64):
+        oop = orc.Stencil5(P.mx, P.my, P.st["C"], P.st["W"], P.st["E"], P.st["S"], P.st["N"])
+        ref = orc.sequential_fine(oop, P.dt, P.M, P.N, P.u0)
+        assert orc.rel_err(a, ref) <= 1e-10, (P.mx, orc.rel_err(a, ref))
+        assert orc.rel_err(b, ref) <= 1e-10
+        assert rel(c2, d2) <= 1e-10
