@@ -80,6 +80,9 @@ def parse():
                     help="krylov mode: 1 forces the FP64 iterative refinement where the FP32 "
                          "on-chip kernel takes the grid (0: the library's default); batch "
                          "mode: 2 runs the FP64 fine steps on the FP64 Krylov kernels")
+    ap.add_argument("--krylov-stage", type=int, default=0, choices=[0, 1],
+                    help="krylov mode: 1 stages the FP32 global-memory kernel's stencil inputs "
+                         "in shared memory by bulk copies (0: read from global memory)")
     ap.add_argument("--krylov-adv", action="store_true",
                     help="krylov mode: the nonsymmetric advection-diffusion operator (BiCGStab)")
     ap.add_argument("--refine-digits", default="",
@@ -387,7 +390,7 @@ ONCHIP_DRAM_BYTES_PER_SYSTEM = (38.77e6 + 1.02e6) / 16
 
 def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, block: int = 0,
                block_clusters: int = 0, refine_digits=(), m: int = 511,
-               refine_mode: int = 0, adv: bool = False) -> dict:
+               refine_mode: int = 0, adv: bool = False, stage: int = 0) -> dict:
     """The 2D fine propagator's bandwidth (the 'HBM GB/s frac' part of the
     metric): diff2d (511^2, kappa checkerboard, dt = 1/4096), Jacobi-PCG per
     backward-Euler step, FP32 sketch propagations (rtol 1e-6) and FP64 fine
@@ -410,6 +413,7 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
     op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
     op.set_krylov(1e-12, 1e-6, 20000)
     ctx.set_param("krylov_refine", 2)
+    ctx.set_param("krylov_stage", stage)
     ctx.set_param("krylov_onchip", onchip)
     ctx.set_param("krylov_block", block)
     ctx.set_param("krylov_block_clusters", block_clusters)
@@ -492,6 +496,7 @@ def krylov_leg(ctx, precs, nsyss, steps: int, warmup: int, onchip: int = 0, bloc
                         "fp32_cg_iterations_per_step": its_d / (nsys * steps)}
     finally:
         ctx.set_param("krylov_refine", 0)
+        ctx.set_param("krylov_stage", 0)
         ctx.set_param("krylov_onchip", 0)
         ctx.set_param("krylov_block", 0)
         ctx.set_param("krylov_block_clusters", 0)
@@ -515,7 +520,7 @@ def run_krylov(args):
     res = krylov_leg(ctx, precs, nsyss, args.steps, args.warmup, args.krylov_onchip,
                      args.krylov_block, args.krylov_block_clusters,
                      [int(v) for v in args.refine_digits.split(",") if v], args.krylov_m,
-                     args.krylov_refine, args.krylov_adv)
+                     args.krylov_refine, args.krylov_adv, args.krylov_stage)
     head = res["f64" if precs[0] == "f64" else "f32"]
     line = {"metric": "2D fine-propagator algorithmic bandwidth (HBM GB/s frac)",
             "value": head["achieved_gbs"], "unit": "GB/s", "n_gpus": 1,

@@ -159,7 +159,14 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    and time-dependent operators keep the FP64 Krylov
  *                    kernels;
  *   "krylov_refine_digits": relative tolerance 10^-digits (1..7) of the FP32
- *                    correction solves (0 = automatic: 1e-3).
+ *                    correction solves (0 = automatic: 1e-3);
+ *   "krylov_stage":  1 stages the stencil input of every FP32 pass of the
+ *                    global-memory Krylov kernel (the CTA's rows and a halo
+ *                    row on each side) in shared memory by one bulk copy of
+ *                    the TMA engine per pass, completion on an mbarrier with
+ *                    bounded waits (LRP_ETIMEOUT); results are bitwise those
+ *                    of 0 (default: the stencil reads global memory through
+ *                    L1), and on GB300 it measured no faster.
  * Results do not depend on these settings beyond rounding (the block
  * solver stops every system on the same residual test as the others). */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);

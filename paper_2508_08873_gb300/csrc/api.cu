@@ -344,6 +344,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "krylov_refine_digits") {
     if (value < 0 || value > 7) return LRP_EINVAL;
     c->p_krylov_refine_digits = value;
+  } else if (k == "krylov_stage") {
+    if (value != 0 && value != 1) return LRP_EINVAL;
+    c->p_krylov_stage = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -365,6 +368,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "krylov_block_clusters") *value = c->p_krylov_block_clusters;
   else if (k == "krylov_refine") *value = c->p_krylov_refine;
   else if (k == "krylov_refine_digits") *value = c->p_krylov_refine_digits;
+  else if (k == "krylov_stage") *value = c->p_krylov_stage;
   else if (k == "krylov_block_last_systems") *value = c->bk_last[0];
   else if (k == "krylov_block_last_cs") *value = c->bk_last[1];
   else if (k == "krylov_block_last_clusters") *value = c->bk_last[2];

@@ -59,6 +59,7 @@ struct Ctx {
   int p_krylov_block_clusters = 0;  // clusters in flight of the block CG (0: workspaces within 96 MB)
   int p_krylov_refine = 0;   // FP64 2D steps by iterative refinement: 0 auto, 1 where it applies, 2 never
   int p_krylov_refine_digits = 0;   // relative tolerance 10^-digits of its FP32 solves (0: 1e-3)
+  int p_krylov_stage = 0;    // FP32 global-memory Krylov kernel: 1 stages stencil inputs by bulk copies, 0 not
   int bk_last[3] = {0, 0, 0};  // last block CG launch: systems per block, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
@@ -329,6 +330,9 @@ struct KryArgs {
   const void* B32;
   const void* Bs32;
   double rtol_in;
+  // FP32 k_krylov: stage the stencil inputs through dynamic shared memory
+  // (bulk copies of the CTA's rows and halo rows); set by the launcher
+  int stage;
 };
 lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPlan** out);
 // On-chip CG (stencil_onchip.cu): symmetric operators with at most 512 grid

@@ -338,6 +338,7 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   op->krylov_iters += hs[0];
   const int stw = (int)(hs[1] & 0xffffffffu);
   if (stw & 2) return set_err(c, LRP_EBREAKDOWN, "Krylov breakdown in an FP32 correction solve");
+  if (stw & 4) return set_err(c, LRP_ETIMEOUT, "a bounded wait of an FP32 correction solve expired");
   if (notconv) return set_err(c, LRP_ENOTCONV, "iterative refinement did not reach the FP64 tolerance");
   return LRP_OK;
 }

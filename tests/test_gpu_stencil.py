@@ -267,3 +267,38 @@ def test_sdirk_2d_build_and_parareal(ctx, orc, scheme):
     with pytest.raises(_native.LrpError) as ei:
         api.build_coarse_batch(ctx, [op], P.dt, P.M, P.N, P.R, P.p, 0, prec="f64")
     assert ei.value.status == _native.LRP_EINVAL
+
+
+@pytest.mark.parametrize("kind,m", [("adv", 63), ("adv", 255), ("diff", 127), ("adv", 511)])
+def test_staged_stencil_inputs_bitwise(ctx, orc, kind, m):
+    """With krylov_stage = 1 the FP32 passes of the global-memory Krylov
+    kernel read their stencil input from a shared-memory tile filled by one
+    bulk copy per pass; the values are the ones in global memory, so the
+    results equal those of the unstaged kernel (the default) bitwise, for
+    BiCGStab and for CG (the on-chip CG switched off), and stay at the FP32
+    tolerance of the oracle."""
+    st = _problem(kind, m)
+    op = api.Operator.stencil5(ctx, m, m, st)
+    dt, M = 1.0 / 4096, 3
+    X = np.random.default_rng(40 + m).standard_normal((5, m * m))
+    ctx.set_param("krylov_onchip", 2)
+    # the same CTAs per cluster in both runs (the partition of the grid, and
+    # so the order of the reductions, follows it)
+    ctx.set_param("krylov_cluster", {63: 1, 127: 2, 255: 8, 511: 16}[m])
+    try:
+        ctx.set_param("krylov_stage", 1)
+        got = api.propagate(ctx, op, dt, M, X, prec="mixed")
+        adj = api.propagate(ctx, op, dt, M, X, adjoint=True, prec="mixed")
+        ctx.set_param("krylov_stage", 0)
+        ref = api.propagate(ctx, op, dt, M, X, prec="mixed")
+        radj = api.propagate(ctx, op, dt, M, X, adjoint=True, prec="mixed")
+    finally:
+        ctx.set_param("krylov_stage", 0)
+        ctx.set_param("krylov_onchip", 0)
+        ctx.set_param("krylov_cluster", 0)
+    assert np.array_equal(got, ref) and np.array_equal(adj, radj)
+    if m <= 127:
+        oop = orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"])
+        want = orc.propagate(oop, dt, M, X[:2])
+        for v in range(2):
+            assert rel(got[v], want[v]) <= 5e-4
