@@ -127,9 +127,10 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    5-point operators with every Krylov vector on chip
  *                    (registers and shared memory of one thread-block
  *                    cluster per system) where the grid allows it (at most
- *                    512 columns and 512 rows in FP32, 256 rows in FP64);
- *                    2 always uses the kernel with its Krylov vectors in
- *                    global memory;
+ *                    512 columns and 512 rows in FP32, 256 rows in FP64;
+ *                    time-dependent operators in FP32, every step on its
+ *                    own couplings); 2 always uses the kernel with its
+ *                    Krylov vectors in global memory;
  *   "krylov_block":  0 (default) or 4: propagations of two or more systems
  *                    without a source on symmetric 5-point operators (at
  *                    most 512 columns in FP32, 256 in FP64, 512 rows) solve

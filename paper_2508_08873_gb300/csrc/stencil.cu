@@ -1163,7 +1163,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
     return stencil_propagate_refine(c, op, plan, M, nsys, in, out, src);
   }
   if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
-  const bool onchip = !sdirk && !td && !block && stencil_onchip_applies(c, op, prec, nsys);
+  const bool onchip = !sdirk && !block && stencil_onchip_applies(c, op, prec, nsys);
   if (!onchip) c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
   using KrK = void (*)(KryArgs);
   auto kern = prec == 0 ? (sdirk ? (td ? (KrK)k_krylov<double, true, true> : (KrK)k_krylov<double, true>)

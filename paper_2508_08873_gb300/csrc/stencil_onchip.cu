@@ -24,6 +24,11 @@ __global__ void k_oc_coef(int mx, int my, int pitch, int rows, const double* __r
   const size_t plane = (size_t)(rows + 2) * pitch;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (rows + 2) * pitch) return;
+  // time-dependent operators: grid row y of the launch is row y of the time
+  // grid (its plan 6 ld values further, its layout 5 planes further)
+  B += (size_t)blockIdx.y * 6 * ld;
+  cf += (size_t)blockIdx.y * 5 * plane / 2;
+  scl += (size_t)blockIdx.y * 5 * plane;
   const int row = t / pitch - 1, col = t % pitch;
   double e = 0.0, nn = 0.0, d = 0.0, si = 0.0, s = 0.0;
   if (row >= 0 && row < my && col < mx) {
@@ -42,14 +47,21 @@ __global__ void k_oc_coef(int mx, int my, int pitch, int rows, const double* __r
   scl[2 * plane + t] = (T)s;
 }
 
+// rows of the time grid a plan holds: one per fine step (two per step with
+// an SDIRK stepper) for time-dependent operators, else one
+static size_t oc_time_rows(const Operator* op) {
+  return op->kind == 3 ? (size_t)op->nJ * (op->stepper ? 2 : 1) : 1;
+}
+
 lrp_status oc_coef_fill(Ctx* c, const Operator* op, const StencilPlan* plan, int prec, int pitch,
                         int rows, DevBuf& buf) {
   const size_t es = prec == 0 ? 8 : 4;
   const size_t tot = (size_t)(rows + 2) * pitch;
-  const size_t need = tot * es * 5;          // (e^, n^) pairs + three scale planes
+  const size_t nrows = oc_time_rows(op);
+  const size_t need = tot * es * 5 * nrows;  // (e^, n^) pairs + three scale planes per row
   lrp_status s;
   if (buf.bytes < need && (s = dev_alloc(c, buf, need))) return s;
-  const int nb = (int)((tot + 255) / 256);
+  const dim3 nb((unsigned)((tot + 255) / 256), (unsigned)nrows);
   if (prec == 0)
     k_oc_coef<double><<<nb, 256, 0, c->stream>>>(
         op->mx, op->my, pitch, rows, plan->b64.as<double>(),
@@ -69,13 +81,15 @@ static int oc_pitch(int mx) {
   return 0;
 }
 
-static Variant oc_variant(int prec, int pitch, int rpt) {
+static Variant oc_variant(int prec, int pitch, int rpt, bool td = false) {
+  if (td) return prec == 1 ? oc::variant_f32_td(pitch, rpt) : Variant{nullptr, 0};
   return prec == 0 ? oc::variant_f64(pitch, rpt) : oc::variant_f32(pitch, rpt);
 }
 
 // The variant for this grid and batch: the most CTAs in flight (then the
 // larger row count); returns rows per CTA (0: none applies).
-static int oc_choose(Ctx* c, int mx, int my, int nsys, int prec, int* cs_out, int* ncl_out) {
+static int oc_choose(Ctx* c, int mx, int my, int nsys, int prec, int* cs_out, int* ncl_out,
+                     bool td = false) {
   const int pitch = oc_pitch(mx);
   if (!pitch || my < 1) return 0;
   const int cands32[2] = {32, 16}, cands64[2] = {16, 8};
@@ -87,7 +101,7 @@ static int oc_choose(Ctx* c, int mx, int my, int nsys, int prec, int* cs_out, in
     const int cs = (my + rpt - 1) / rpt;
     if (cs > oc::MAXCS) continue;
     if (c->p_krylov_cluster > 0 && cs != c->p_krylov_cluster) continue;
-    const Variant v = oc_variant(prec, pitch, rpt);
+    const Variant v = oc_variant(prec, pitch, rpt, td);
     if (!v.fn || v.smem > 227 * 1024) continue;
     if (cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) ||
         cudaFuncSetAttribute(v.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v.smem)) {
@@ -121,22 +135,26 @@ static int oc_choose(Ctx* c, int mx, int my, int nsys, int prec, int* cs_out, in
 
 bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys) {
   if (!op->symmetric || c->p_krylov_onchip == 2) return false;
+  // time-dependent operators: FP32 backward-Euler steps
+  const bool td = op->kind == 3;
+  if (td && (prec != 1 || op->stepper != 0)) return false;
   int cs = 0, ncl = 0;
-  return oc_choose(c, op->mx, op->my, std::max(nsys, 1), prec, &cs, &ncl) > 0;
+  return oc_choose(c, op->mx, op->my, std::max(nsys, 1), prec, &cs, &ncl, td) > 0;
 }
 
 lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
                                     int prec, const KryArgs& base) {
   int cs = 0, ncl = 0;
-  const int rpt = oc_choose(c, op->mx, op->my, nsys, prec, &cs, &ncl);
+  const bool td = op->kind == 3;
+  const int rpt = oc_choose(c, op->mx, op->my, nsys, prec, &cs, &ncl, td);
   if (!rpt) return set_err(c, LRP_EINVAL, "on-chip CG: no launch shape for this grid");
   const int pitch = oc_pitch(op->mx);
   const int rows = cs * rpt;
-  const Variant v = oc_variant(prec, pitch, rpt);
+  const Variant v = oc_variant(prec, pitch, rpt, td);
   DevBuf& cfb = prec == 0 ? plan->oc64 : plan->oc32;
   const size_t es = prec == 0 ? 8 : 4;
   const size_t tot = (size_t)(rows + 2) * pitch;
-  const size_t need = tot * es * 5;          // (e^, n^) pairs + three scale planes
+  const size_t need = tot * es * 5 * oc_time_rows(op);   // (e^, n^) pairs + three scale planes
   lrp_status s;
   if (cfb.bytes < need || plan->oc_rows[prec ? 1 : 0] != rows) {
     if ((s = oc_coef_fill(c, op, plan, prec, pitch, rows, cfb))) return s;
@@ -150,6 +168,8 @@ lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int
   oa.cf = cfb.ptr;
   oa.scl = static_cast<char*>(cfb.ptr) + 2 * tot * es;
   oa.rows = rows;
+  oa.cf_step = (long)(5 * tot / 2);           // pairs from one row of the time grid to the next
+  oa.scl_step = (long)(5 * tot);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;

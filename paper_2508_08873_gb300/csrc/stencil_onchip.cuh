@@ -92,6 +92,9 @@ struct Args {
   const void* cf;
   const void* scl;
   int rows;
+  // time-dependent operators (TD kernels): the layouts of the rows of the
+  // time grid follow one another, cf_step pairs and scl_step scales apart
+  long cf_step, scl_step;
 };
 
 template <typename T, int PITCH, int RPT, bool QSM, int KA>
@@ -146,7 +149,10 @@ LRP_DEV void cl_sum(cg::cluster_group& cl, const T (&v)[NV], SM& sh, int& buf, F
   buf ^= 1;
 }
 
-template <typename T, int PITCH, int RPT, bool QSM, int KA>
+// TD: a time-dependent operator, every fine step its own couplings and scales
+// (the system's steps J0 .. J0 + M - 1 of its interval, reversed for the
+// adjoint; between steps x^ = S x is rescaled to the new diagonal).
+template <typename T, int PITCH, int RPT, bool QSM, int KA, bool TD = false>
 __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
   using T2 = typename V2<T>::t;
   using SM = Smem<T, PITCH, RPT, QSM, KA>;
@@ -161,8 +167,10 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
   const bool has_up = crank > 0, has_dn = crank < cs - 1;
   const size_t plane = (size_t)(oa.rows + 2) * PITCH;
   // this thread's column from our first row on: coupling pairs and scales
-  const T2* __restrict__ cfc = static_cast<const T2*>(oa.cf) + (size_t)(r0 + 1) * PITCH + col;
-  const T* __restrict__ sc = static_cast<const T*>(oa.scl) + (size_t)(r0 + 1) * PITCH + col;
+  const T2* __restrict__ cf0 = static_cast<const T2*>(oa.cf) + (size_t)(r0 + 1) * PITCH + col;
+  const T* __restrict__ sc0 = static_cast<const T*>(oa.scl) + (size_t)(r0 + 1) * PITCH + col;
+  const T2* __restrict__ cfc = cf0;
+  const T* __restrict__ sc = sc0;
 
   extern __shared__ __align__(16) unsigned char oc_smem_raw[];
   SM& sh = *reinterpret_cast<SM*>(oc_smem_raw);
@@ -174,7 +182,16 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
   }
   if (lane == 0)
     for (int i = 0; i < RPT; ++i) sh.wco[i][wid] = cfc[(long)i * PITCH - 1].x;
-  const T s_first = cfc[-PITCH].y;    // n^ of the row above ours: south coupling of row 0
+  T s_first = cfc[-PITCH].y;    // n^ of the row above ours: south coupling of row 0
+  // TD: the couplings and scales of row `row` of the time grid (the warp-edge
+  // couplings are read and used by each warp's lane 0 alone)
+  auto set_row = [&](long row) {
+    cfc = cf0 + row * oa.cf_step;
+    sc = sc0 + row * oa.scl_step;
+    if (lane == 0)
+      for (int i = 0; i < RPT; ++i) sh.wco[i][wid] = cfc[(long)i * PITCH - 1].x;
+    s_first = cfc[-PITCH].y;
+  };
   cl.sync();   // every CTA runs before remote accesses to its shared memory
 
   // where this lane's p of row i goes in the warp-edge table: lanes 0 and 31
@@ -197,6 +214,16 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
   int my_status = 0;
 
   for (int sys = slot; sys < a.nsys; sys += nslots) {
+    long J0 = 0;
+    if constexpr (TD) {
+      // the interval of the system (system map of the input, else of the
+      // output, else of the source; else interval0 + sys / ncol): its steps
+      const int* imap = a.in.map ? a.in.map : a.out.map ? a.out.map : a.src.map;
+      const int interval = imap ? imap[2 * sys + 1] : a.in.interval0 + sys / a.in.ncol;
+      J0 = (long)interval * a.M;
+      if (J0 < 0 || J0 + a.M > a.nJ) continue;   // outside the time grid (checked on the host)
+      set_row(a.adj ? J0 + a.M - 1 : J0);
+    }
     // ---- x^ = S x ------------------------------------------------------------
     const long ox = a.in.gen || a.in.x == nullptr
         ? 0 : sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys);
@@ -230,6 +257,19 @@ __global__ void __launch_bounds__(PITCH, 512 / PITCH) k_cg_onchip(Args oa) {
     };
     T p_up = T(0), r_up = T(0), p_dn = T(0), r_dn = T(0);
     for (int j = 0; j < a.M; ++j) {
+      if constexpr (TD) {
+        if (j > 0) {
+          // the next step's matrix: x^ = S_J x rescaled from the previous S
+          const T* sp = sc;
+          set_row(a.adj ? J0 + a.M - 1 - j : J0 + j);
+          cpa_wait_all();
+          for (int i = 0; i < RPT; ++i)
+            sh.xs[i][col] = sh.xs[i][col] * sp[(long)i * PITCH + plane] * sc[(long)i * PITCH + 2 * plane];
+          sh.xedge[0][col] = sh.xs[0][col];
+          sh.xedge[1][col] = sh.xs[RPT - 1][col];
+          cl.sync();   // the neighbours' halo rows of x^ are read below
+        }
+      }
       // ---- d^ = x^ / c + dt S^-1 f,  r = p = d^ - B^ x^ ----------------------
       cpa_wait_all();
       T red2t[2] = {T(0), T(0)};     // d^.d^, r.r
@@ -423,9 +463,11 @@ struct Variant {
 Variant variant_f32(int pitch, int rpt);
 Variant variant_f64(int pitch, int rpt);
 
-template <typename T, int PITCH, int RPT, bool QSM, int KA>
+Variant variant_f32_td(int pitch, int rpt);
+
+template <typename T, int PITCH, int RPT, bool QSM, int KA, bool TD = false>
 Variant make_variant() {
-  return Variant{(const void*)k_cg_onchip<T, PITCH, RPT, QSM, KA>,
+  return Variant{(const void*)k_cg_onchip<T, PITCH, RPT, QSM, KA, TD>,
                  sizeof(Smem<T, PITCH, RPT, QSM, KA>)};
 }
 

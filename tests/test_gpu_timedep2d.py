@@ -264,3 +264,34 @@ def test_td2d_sdirk_build_and_parareal(ctx, orc, scheme):
     res = orc.parareal(oop, dt, M, N, oco, P.u0, P.g, c, K=2)
     u2, _ = api.parareal_solve(ctx, co, P.u0, P.g, c, K=2)
     assert rel(u2, res.iterates[-1]) <= 1e-10
+
+
+@pytest.mark.parametrize("m", [31, 63, 127])
+def test_td2d_onchip_f32(ctx, orc, m):
+    """FP32 steps of a symmetric time-dependent operator run on the on-chip
+    CG (every step its own couplings and scales, the iterate rescaled
+    between steps), forward with a source and adjoint, within the FP32
+    tolerance of the oracle and of the global-memory kernel."""
+    M = 4
+    st, dt = _case("heat", m, M)
+    op, oop = _ops(ctx, orc, st, m)
+    rng = np.random.default_rng(60 + m)
+    X = rng.standard_normal((3, m * m))
+    g = rng.standard_normal((1, m * m))
+    c = rng.standard_normal((3, M, 1))
+    got = api.propagate(ctx, op, dt, M, X, g=g, c=c, prec="mixed")
+    assert ctx.get_param("krylov_onchip_rows") > 0
+    adj = api.propagate(ctx, op, dt, M, X, adjoint=True, prec="mixed")
+    ctx.set_param("krylov_onchip", 2)
+    try:
+        glob = api.propagate(ctx, op, dt, M, X, g=g, c=c, prec="mixed")
+        assert ctx.get_param("krylov_onchip_rows") == 0
+    finally:
+        ctx.set_param("krylov_onchip", 0)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=c, intervals=0)
+    wadj = orc.propagate(oop, dt, M, X, adjoint=True, intervals=0)
+    tol = 2e-4 if m <= 63 else 1e-3
+    for v in range(3):
+        assert rel(got[v], want[v]) <= tol, (v, rel(got[v], want[v]))
+        assert rel(adj[v], wadj[v]) <= tol, (v, rel(adj[v], wadj[v]))
+        assert rel(glob[v], want[v]) <= tol
