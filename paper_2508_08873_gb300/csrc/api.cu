@@ -44,6 +44,7 @@ void ctx_release(Ctx* c) {
   if (!c || --c->refs > 0) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
+  for (DevBuf* b : {&c->kws, &c->kstat, &c->bws, &c->irws, &c->irstat}) b->release();
   pool_drain(c);
   for (auto& kv : c->timers)
     for (auto& pr : kv.second.pairs) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -57,8 +58,6 @@ Operator::~Operator() {
   plans.clear();
   cplans.clear();
   splans.clear();
-  kws.release();
-  kstat.release();
   for (auto& b : a64) b.release();
   for (auto& b : a32) b.release();
   ctx_release(c);
@@ -480,7 +479,7 @@ void lrp_operator_free(lrp_operator* op) {
 int lrp_operator_size(const lrp_operator* op) { return op ? op->n : 0; }
 
 unsigned long long lrp_operator_krylov_iterations(const lrp_operator* op) {
-  return op ? op->krylov_iters : 0;
+  return op ? op->krylov_iters.load() : 0ULL;
 }
 
 lrp_status lrp_operator_set_krylov(lrp_operator* op, double rtol_f64, double rtol_f32,

@@ -60,6 +60,11 @@ struct Ctx {
   int p_krylov_refine = 0;   // FP64 2D steps by iterative refinement: 0 auto, 1 where it applies, 2 never
   int p_krylov_refine_digits = 0;   // relative tolerance 10^-digits of its FP32 solves (0: 1e-3)
   int p_krylov_stage = 0;    // FP32 global-memory Krylov kernel: 1 stages stencil inputs by bulk copies, 0 not
+  // Scratch of 2D propagations, per context (one host thread and one stream
+  // each, so that a server's contexts and the caller's never share it): the
+  // Krylov workspace and status, the block CG workspace, the refinement's
+  // workspace and inner-solve status.  Released before the pool is drained.
+  DevBuf kws, kstat, bws, irws, irstat;
   int bk_last[3] = {0, 0, 0};  // last block CG launch: systems per block, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
@@ -121,10 +126,15 @@ struct StencilPlan {
   int adjoint = 0;
   DevBuf b64, b32;
   DevBuf bs64, bs32;   // symmetric operators: the scaled matrix of CG (k_stencil_plan_scaled)
-  DevBuf oc64, oc32;   // scaled couplings and scales of the on-chip CG kernel (stencil_onchip.cu)
-  int oc_rows[2] = {0, 0};   // padded grid rows those were laid out for (FP64, FP32)
-  DevBuf bk64, bk32;   // the same, laid out for the block CG kernel (stencil_block.cu)
-  int bk_rows[2] = {0, 0};
+  // scaled couplings and scales laid out for the on-chip and block CG kernels
+  // (stencil_onchip.cu), one per (precision, pitch, padded rows); each is
+  // filled once and never changes (plans are shared by every context that
+  // propagates with the operator, a server's included)
+  struct Layout {
+    int prec = 0, pitch = 0, rows = 0;
+    DevBuf buf;
+  };
+  std::vector<std::unique_ptr<Layout>> layouts;
 };
 
 // Constant-coefficient (Toeplitz) data of a tridiagonal step matrix
@@ -161,10 +171,9 @@ struct Operator {
   std::vector<std::unique_ptr<TriPlan>> plans;
   std::vector<std::unique_ptr<ClPlan>> cplans;
   std::vector<std::unique_ptr<StencilPlan>> splans;
-  DevBuf kws, kstat;       // Krylov workspace and status of 2D propagations
-  DevBuf bws;              // block CG workspace (stencil_block.cu)
-  DevBuf irws, irstat;     // iterative refinement workspace and inner-solve status (stencil_refine.cu)
-  unsigned long long krylov_iters = 0;
+  // Krylov iterations of 2D propagations (contexts of several threads, a
+  // server's, may propagate with one operator)
+  std::atomic<unsigned long long> krylov_iters{0};
 };
 
 struct Coarse {
@@ -346,6 +355,10 @@ bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys);
 // (allocated or grown as needed); T = double for prec 0, else float.
 lrp_status oc_coef_fill(Ctx* c, const Operator* op, const StencilPlan* plan, int prec, int pitch,
                         int rows, DevBuf& buf);
+// The layout of a plan for (prec, pitch, rows): found, or created and filled
+// (the fill completed before it is published).  *ptr: its device address.
+lrp_status plan_layout(Ctx* c, Operator* op, StencilPlan* plan, int prec, int pitch, int rows,
+                       void** ptr);
 // Block CG (stencil_block.cu): symmetric operators, propagations without a
 // source, at least two systems; the systems are taken in blocks of
 // p_krylov_block consecutive ones, each block on one cluster.
@@ -366,7 +379,8 @@ bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys);
 // nonsymmetric operators; a: the kernel arguments without B, Bs, ws, nvec.
 lrp_status krylov_f32_correction(Ctx* c, Operator* op, StencilPlan* plan, int nsys, KryArgs& a);
 lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
-                                    const PropIn& in, const PropOut& out, const PropSrc& src);
+                                    const PropIn& in, const PropOut& out, const PropSrc& src,
+                                    int adjoint);
 size_t krylov_queue_nvec(int bicg);
 // Device pointer of the stencil coefficients for KryArgs::B (past the pad).
 const void* stencil_B(const StencilPlan* pl, const Operator* op, int prec);

@@ -1032,6 +1032,9 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
     e = cudaGetLastError();
     if (e) return cuda_err(c, e, "k_stencil_plan_scaled");
   }
+  // published only once filled: other contexts (a server's) may use it at once
+  e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "k_stencil_plan");
   *out = pl.get();
   op->splans.push_back(std::move(pl));
   return LRP_OK;
@@ -1107,11 +1110,11 @@ lrp_status krylov_f32_correction(Ctx* c, Operator* op, StencilPlan* plan, int ns
   a.stage = stage > 0;
   const size_t need = (size_t)ncl * nvec * ((size_t)op->n + 2 * op->mx) * 4;
   lrp_status s;
-  if (op->kws.bytes < need)
-    if ((s = dev_alloc(c, op->kws, need))) return s;
+  if (c->kws.bytes < need)
+    if ((s = dev_alloc(c, c->kws, need))) return s;
   a.B = stencil_B(plan, op, 1);
   a.Bs = stencil_Bs(plan, op, 1);
-  a.ws = op->kws.ptr;
+  a.ws = c->kws.ptr;
   a.nvec = nvec;
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
@@ -1157,10 +1160,10 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
       return set_err(c, LRP_EINVAL, "time-dependent operator: steps beyond its time grid");
   }
   const bool block = !sdirk && !td && stencil_block_applies(c, op, prec, nsys, M, src.Q);
-  if (!block && !sdirk && !td && stencil_refine_applies(c, op, prec, nsys)) {
+  if (!block && !sdirk && stencil_refine_applies(c, op, prec, nsys)) {
     c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
     c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
-    return stencil_propagate_refine(c, op, plan, M, nsys, in, out, src);
+    return stencil_propagate_refine(c, op, plan, M, nsys, in, out, src, adjoint);
   }
   if (!block) c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
   const bool onchip = !sdirk && !block && stencil_onchip_applies(c, op, prec, nsys);
@@ -1191,11 +1194,11 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
   cfg.dynamicSmemBytes = stage;
   const size_t es = prec == 0 ? 8 : 4;
   const size_t need = (size_t)nclusters * nvec * ((size_t)op->n + 2 * op->mx) * es;
-  if (!onchip && !block && op->kws.bytes < need)
-    if ((s = dev_alloc(c, op->kws, need))) return s;
-  if (!op->kstat.ptr)
-    if ((s = dev_alloc(c, op->kstat, 16))) return s;
-  cudaMemsetAsync(op->kstat.ptr, 0, 16, c->stream);
+  if (!onchip && !block && c->kws.bytes < need)
+    if ((s = dev_alloc(c, c->kws, need))) return s;
+  if (!c->kstat.ptr)
+    if ((s = dev_alloc(c, c->kstat, 16))) return s;
+  cudaMemsetAsync(c->kstat.ptr, 0, 16, c->stream);
   KryArgs a{};
   a.mx = op->mx;
   a.my = op->my;
@@ -1228,13 +1231,13 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
       a.b2 = 1.0;
     }
   }
-  a.ws = op->kws.ptr;
+  a.ws = c->kws.ptr;
   a.nvec = nvec;
   a.in = in;
   a.out = out;
   a.src = src;
-  a.iters = reinterpret_cast<unsigned long long*>(op->kstat.ptr);
-  a.status = reinterpret_cast<int*>(static_cast<char*>(op->kstat.ptr) + 8);
+  a.iters = reinterpret_cast<unsigned long long*>(c->kstat.ptr);
+  a.status = reinterpret_cast<int*>(static_cast<char*>(c->kstat.ptr) + 8);
   a.stage = stage > 0;
   if (block) {
     if ((s = stencil_propagate_block(c, op, plan, M, nsys, prec, a))) return s;
@@ -1249,7 +1252,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
     if (e) return cuda_err(c, e, "k_krylov launch");
   }
   unsigned long long hs[2] = {0, 0};
-  e = cudaMemcpyAsync(hs, op->kstat.ptr, 16, cudaMemcpyDeviceToHost, c->stream);
+  e = cudaMemcpyAsync(hs, c->kstat.ptr, 16, cudaMemcpyDeviceToHost, c->stream);
   if (!e) e = cudaStreamSynchronize(c->stream);
   if (e) return cuda_err(c, e, "k_krylov");
   op->krylov_iters += hs[0];

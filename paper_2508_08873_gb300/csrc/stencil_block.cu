@@ -54,13 +54,9 @@ lrp_status stencil_propagate_block(Ctx* c, Operator* op, StencilPlan* plan, int 
   const int cs = (op->my + v.rb - 1) / v.rb;
   if (cs > bk::MAXCS) return set_err(c, LRP_EINVAL, "block CG: grid has too many rows");
   const int rows = cs * v.rb;
-  const int pi = prec == 0 ? 0 : 1;
-  DevBuf& cfb = prec == 0 ? plan->bk64 : plan->bk32;
+  void* cfp = nullptr;
   lrp_status s;
-  if (!cfb.ptr || plan->bk_rows[pi] != rows) {
-    if ((s = oc_coef_fill(c, op, plan, prec, v.pitch, rows, cfb))) return s;
-    plan->bk_rows[pi] = rows;
-  }
+  if ((s = plan_layout(c, op, plan, prec, v.pitch, rows, &cfp))) return s;
   const size_t es = prec == 0 ? 8 : 4;
   const size_t tot = (size_t)(rows + 2) * v.pitch;
   cudaError_t e = cudaFuncSetAttribute(v.fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -95,20 +91,20 @@ lrp_status stencil_propagate_block(Ctx* c, Operator* op, StencilPlan* plan, int 
       : (int)std::max<size_t>(1, ((size_t)96 << 20) / slot_bytes);
   ncl = std::max(1, std::min(std::min(ncl, maxc), nblk));
   const size_t need = (size_t)ncl * slot_bytes;
-  if (op->bws.bytes < need)
-    if ((s = dev_alloc(c, op->bws, need))) return s;
+  if (c->bws.bytes < need)
+    if ((s = dev_alloc(c, c->bws, need))) return s;
   // the pad rows of every block vector must read as 0
-  e = cudaMemsetAsync(op->bws.ptr, 0, need, c->stream);
+  e = cudaMemsetAsync(c->bws.ptr, 0, need, c->stream);
   if (e) return cuda_err(c, e, "block CG workspace");
   c->bk_last[0] = v.S;
   c->bk_last[1] = cs;
   c->bk_last[2] = ncl;
   bk::Args ba;
   ba.k = base;
-  ba.cf = cfb.ptr;
-  ba.scl = static_cast<char*>(cfb.ptr) + 2 * tot * es;
+  ba.cf = cfp;
+  ba.scl = static_cast<char*>(cfp) + 2 * tot * es;
   ba.rows = rows;
-  ba.ws = op->bws.ptr;
+  ba.ws = c->bws.ptr;
   ba.slot_elems = slot_elems;
   ba.thr = prec == 0 ? 1e-12 : 1e-6;
   cfg.gridDim = dim3(ncl * cs);

@@ -60,7 +60,8 @@ lrp_status oc_coef_fill(Ctx* c, const Operator* op, const StencilPlan* plan, int
   const size_t nrows = oc_time_rows(op);
   const size_t need = tot * es * 5 * nrows;  // (e^, n^) pairs + three scale planes per row
   lrp_status s;
-  if (buf.bytes < need && (s = dev_alloc(c, buf, need))) return s;
+  // owned by the operator's context: plans outlive the contexts that use them
+  if (buf.bytes < need && (s = dev_alloc(op->ctx, buf, need))) return s;
   const dim3 nb((unsigned)((tot + 255) / 256), (unsigned)nrows);
   if (prec == 0)
     k_oc_coef<double><<<nb, 256, 0, c->stream>>>(
@@ -72,6 +73,28 @@ lrp_status oc_coef_fill(Ctx* c, const Operator* op, const StencilPlan* plan, int
         reinterpret_cast<float2*>(buf.ptr), static_cast<float*>(buf.ptr) + 2 * tot);
   cudaError_t e = cudaGetLastError();
   if (e) return cuda_err(c, e, "k_oc_coef");
+  return LRP_OK;
+}
+
+lrp_status plan_layout(Ctx* c, Operator* op, StencilPlan* plan, int prec, int pitch, int rows,
+                       void** ptr) {
+  std::lock_guard<std::mutex> lk(op->plan_mu);
+  for (auto& l : plan->layouts)
+    if (l->prec == prec && l->pitch == pitch && l->rows == rows) {
+      *ptr = l->buf.ptr;
+      return LRP_OK;
+    }
+  auto nl = std::make_unique<StencilPlan::Layout>();
+  nl->prec = prec;
+  nl->pitch = pitch;
+  nl->rows = rows;
+  lrp_status s = oc_coef_fill(c, op, plan, prec, pitch, rows, nl->buf);
+  if (s) return s;
+  // published only once filled: other contexts (a server's) may use it at once
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e) return cuda_err(c, e, "k_oc_coef");
+  *ptr = nl->buf.ptr;
+  plan->layouts.push_back(std::move(nl));
   return LRP_OK;
 }
 
@@ -151,22 +174,18 @@ lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int
   const int pitch = oc_pitch(op->mx);
   const int rows = cs * rpt;
   const Variant v = oc_variant(prec, pitch, rpt, td);
-  DevBuf& cfb = prec == 0 ? plan->oc64 : plan->oc32;
   const size_t es = prec == 0 ? 8 : 4;
   const size_t tot = (size_t)(rows + 2) * pitch;
-  const size_t need = tot * es * 5 * oc_time_rows(op);   // (e^, n^) pairs + three scale planes
+  void* cfp = nullptr;
   lrp_status s;
-  if (cfb.bytes < need || plan->oc_rows[prec ? 1 : 0] != rows) {
-    if ((s = oc_coef_fill(c, op, plan, prec, pitch, rows, cfb))) return s;
-    plan->oc_rows[prec ? 1 : 0] = rows;
-  }
+  if ((s = plan_layout(c, op, plan, prec, pitch, rows, &cfp))) return s;
   c->oc_last[0] = rpt;
   c->oc_last[1] = cs;
   c->oc_last[2] = ncl;
   oc::Args oa;
   oa.k = base;
-  oa.cf = cfb.ptr;
-  oa.scl = static_cast<char*>(cfb.ptr) + 2 * tot * es;
+  oa.cf = cfp;
+  oa.scl = static_cast<char*>(cfp) + 2 * tot * es;
   oa.rows = rows;
   oa.cf_step = (long)(5 * tot / 2);           // pairs from one row of the time grid to the next
   oa.scl_step = (long)(5 * tot);

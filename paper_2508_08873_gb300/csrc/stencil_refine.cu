@@ -91,6 +91,7 @@ __global__ void k_ir_rhs(PropSrc src, int n, int s0, int cnt, int j, double dt,
 // d^T D d and a^T D a, a = |d| + |B| |x| (D = 1 / diag(B)), in a fixed order.
 __global__ void __launch_bounds__(IR_THREADS) k_ir_resid(int mx, int my, int unit,
                                                         const double* __restrict__ B, long ldb,
+                                                        long b_step,
                                                         const int* __restrict__ list,
                                                         const double* __restrict__ X,
                                                         const double* __restrict__ D,
@@ -99,6 +100,7 @@ __global__ void __launch_bounds__(IR_THREADS) k_ir_resid(int mx, int my, int uni
   const int n = mx * my;
   const int s = list[2 * blockIdx.y];
   const long base = (long)s * n;
+  B += (long)list[2 * blockIdx.y + 1] * b_step;   // time-dependent operators: the step's plan
   const int k0 = blockIdx.x * IR_THREADS * IR_PTS;
   double rr = 0.0, dd = 0.0, aa = 0.0;
 #pragma unroll
@@ -168,7 +170,7 @@ __global__ void k_ir_reduce(int nblk, int n, double rtol2, double floor2,
   if (lane == 0 && rr > rtol2 * dd && rr > floor2 * aa) {
     const int at = atomicAdd(cnt, 1);
     next[2 * at] = list[2 * i];
-    next[2 * at + 1] = 0;
+    next[2 * at + 1] = list[2 * i + 1];
     sigma[list[2 * i]] = sqrt(rr / n);       // rr > 0 here
   }
 }
@@ -194,17 +196,32 @@ __global__ void k_ir_apply(int n, const int* __restrict__ list, const double* __
     X[base + k] = fma(sg, E[base + k], X[base + k]);
 }
 
-__global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restrict__ one) {
+// every system of the batch into the list; its second entry is the row of
+// the time grid of the system's step j (time-dependent operators: the
+// interval of the system from the call's maps, else interval0 + s / ncol;
+// the adjoint runs the steps in reversed order), else 0
+__global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restrict__ one, int td,
+                              PropIn in, const int* __restrict__ omap, const int* __restrict__ smap,
+                              int s0, int M, int j, int adj) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cnt) {
+    int row = 0;
+    if (td) {
+      const int sys = s0 + i;
+      const int* imap = in.map ? in.map : omap ? omap : smap;
+      const long J0 = (long)(imap ? imap[2 * sys + 1] : in.interval0 + sys / in.ncol) * M;
+      row = (int)(adj ? J0 + M - 1 - j : J0 + j);
+    }
     list[2 * i] = i;
-    list[2 * i + 1] = 0;
+    list[2 * i + 1] = row;
   }
   if (i == 0) *one = 1.0;
 }
 
 bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys) {
-  if (prec != 0 || op->kind != 1 || op->stepper != 0) return false;
+  if (prec != 0 || (op->kind != 1 && op->kind != 3) || op->stepper != 0) return false;
+  // time-dependent operators: symmetric ones, on the on-chip kernel's TD variant
+  if (op->kind == 3 && !op->symmetric) return false;
   if (c->p_krylov_refine == 2) return false;
   // nonsymmetric operators: FP32 BiCGStab corrections on the global-memory
   // kernel (measured on GB300, adv2d nu = 0.01, dt = 1/4096, 64 systems, us
@@ -214,7 +231,8 @@ bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys) {
 }
 
 lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
-                                    const PropIn& in, const PropOut& out, const PropSrc& src) {
+                                    const PropIn& in, const PropOut& out, const PropSrc& src,
+                                    int adjoint) {
   const int n = op->n;
   const int batch = std::min(nsys, IR_BATCH);
   const size_t vec = (size_t)batch * n;
@@ -223,11 +241,11 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   const size_t need = sizeof(double) * (4 * vec + (size_t)batch * nblk * 3 + (size_t)batch + 8) +
                       sizeof(int) * (4 * (size_t)batch + 8);
   lrp_status s;
-  if (op->irws.bytes < need)
-    if ((s = dev_alloc(c, op->irws, need))) return s;
-  if (!op->irstat.ptr)
-    if ((s = dev_alloc(c, op->irstat, 32))) return s;
-  double* X = op->irws.as<double>();
+  if (c->irws.bytes < need)
+    if ((s = dev_alloc(c, c->irws, need))) return s;
+  if (!c->irstat.ptr)
+    if ((s = dev_alloc(c, c->irstat, 32))) return s;
+  double* X = c->irws.as<double>();
   double* D = X + vec;
   double* G = D + vec;
   double* E = G + vec;
@@ -239,10 +257,11 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   int* cnt = listB + 2 * batch;
   cudaStream_t st = c->stream;
   // the inner FP32 solves: their iterations and status words
-  unsigned long long* iters = reinterpret_cast<unsigned long long*>(op->irstat.ptr);
-  int* istat = reinterpret_cast<int*>(static_cast<char*>(op->irstat.ptr) + 8);
-  cudaMemsetAsync(op->irstat.ptr, 0, 32, st);
+  unsigned long long* iters = reinterpret_cast<unsigned long long*>(c->irstat.ptr);
+  int* istat = reinterpret_cast<int*>(static_cast<char*>(c->irstat.ptr) + 8);
+  cudaMemsetAsync(c->irstat.ptr, 0, 32, st);
   const int bicg = op->symmetric ? 0 : 1;
+  const int td = op->kind == 3 ? 1 : 0;       // every system on its own step's plan
   const double rtol2 = op->rtol64 * op->rtol64;
   const double floor2 = (IR_FLOOR * 0x1p-53) * (IR_FLOOR * 0x1p-53);
   // inner tolerance 1e-3 by default: measured on GB300 (diff2d, dt = 1/4096,
@@ -265,15 +284,16 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
     k_ir_gather<<<gsz, 256, 0, st>>>(in, n, s0, cnt0, X);
     for (int j = 0; j < M; ++j) {
       k_ir_rhs<<<gsz, 256, 0, st>>>(src, n, s0, cnt0, j, plan->dt, X, D);
-      k_ir_list_all<<<(cnt0 + 255) / 256, 256, 0, st>>>(cnt0, listA, one);
+      k_ir_list_all<<<(cnt0 + 255) / 256, 256, 0, st>>>(cnt0, listA, one, td, in, out.map, src.map,
+                                                        s0, M, j, adjoint);
       int nact = cnt0;
       int* cur = listA;
       int* nxt = listB;
       for (int round = 0;; ++round) {
         cudaEvent_t ev = nullptr;
         timer_begin(c, fam, &ev);
-        k_ir_resid<<<dim3(nblk, nact), IR_THREADS, 0, st>>>(op->mx, op->my, bicg, B64, ldb, cur, X, D,
-                                                            G, part);
+        k_ir_resid<<<dim3(nblk, nact), IR_THREADS, 0, st>>>(op->mx, op->my, bicg, B64, ldb,
+                                                            td ? 6 * ldb : 0L, cur, X, D, G, part);
         cudaMemsetAsync(cnt, 0, sizeof(int), st);
         k_ir_reduce<<<nact, 32, 0, st>>>(nblk, n, rtol2, floor2, cur, part, nxt, cnt, sigma);
         timer_end(c, fam, ev);
@@ -293,7 +313,9 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
         a.mx = op->mx;
         a.my = op->my;
         a.n = n;
-        a.M = 1;
+        a.M = 1;                       // TD: the list's second entry is the step's row (M = 1)
+        a.nJ = op->nJ;
+        a.adj = 0;
         a.nsys = nact;
         a.bicg = 0;
         a.dt = plan->dt;
@@ -331,7 +353,7 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
     if (notconv) break;
   }
   unsigned long long hs[2] = {0, 0};
-  e = cudaMemcpyAsync(hs, op->irstat.ptr, 16, cudaMemcpyDeviceToHost, st);
+  e = cudaMemcpyAsync(hs, c->irstat.ptr, 16, cudaMemcpyDeviceToHost, st);
   if (!e) e = cudaStreamSynchronize(st);
   if (!e) e = cudaGetLastError();
   if (e) return cuda_err(c, e, "refinement");

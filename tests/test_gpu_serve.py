@@ -150,3 +150,33 @@ def test_short_requests_not_held_behind_long_ones(setup, orc):
     long_lat = [srv.wait(t, timeout=300)[1]["latency_ms"] for t in long_t]
     assert max(short_lat) < np.median(long_lat), (short_lat, np.median(long_lat))
     srv.close()
+
+
+def test_served_2d_with_concurrent_direct_solves():
+    """2D handles (symmetric diffusion: FP64 steps by iterative refinement;
+    upwind advection: FP32 BiCGStab corrections) served while the caller's
+    context runs direct solves and propagations of other sizes with the same
+    operators: the server's contexts and the caller's keep their own scratch,
+    so every served result equals its direct solve."""
+    ctx = api.Context(0)
+    probs = [W.diff2d(m=31, N=6, M=4, R=5, p=3, T=6 * 4 / 2048), W.adv2d(0, m=31, N=6, M=4, R=5, p=3)]
+    ops, cos = [], []
+    for P in probs:
+        op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+        ops.append(op)
+        cos.append(api.Coarse(ctx, op, P.dt, P.M, P.N, P.R, P.p, P.seed, prec="mixed"))
+    srv = api.Server(ctx, max_slots=8, max_terms=2)
+    reqs = []
+    for k in range(6):
+        P, co = probs[k % 2], cos[k % 2]
+        u0, g, c = W.serving_request(P.n, P.N, P.M, P.dt, 900 + k)
+        reqs.append((srv.submit(co, u0, g[:2], c[:, :2], K=P.N, tol=1e-8), P, co, u0, g[:2], c[:, :2]))
+    # meanwhile, direct work on the same operators with other batch sizes
+    rng = np.random.default_rng(5)
+    for P, op in zip(probs, ops):
+        api.propagate(ctx, op, P.dt, 3, rng.standard_normal((17, P.n)))
+    for t, P, co, u0, g, c in reqs:
+        u, info = srv.wait(t, timeout=120)
+        direct, _ = api.parareal_solve(ctx, co, u0, g, c, K=P.N, tol=1e-8)
+        assert np.linalg.norm(u - direct) <= 1e-12 * np.linalg.norm(direct)
+    srv.close()

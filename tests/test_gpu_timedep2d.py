@@ -295,3 +295,25 @@ def test_td2d_onchip_f32(ctx, orc, m):
         assert rel(got[v], want[v]) <= tol, (v, rel(got[v], want[v]))
         assert rel(adj[v], wadj[v]) <= tol, (v, rel(adj[v], wadj[v]))
         assert rel(glob[v], want[v]) <= tol
+
+
+@pytest.mark.parametrize("adjoint", [False, True])
+def test_td2d_refine_f64(ctx, orc, adjoint):
+    """FP64 steps of a symmetric time-dependent operator by iterative
+    refinement (the default: FP64 residual on the step's own plan, FP32
+    on-chip corrections with that step's couplings) and on the FP64 Krylov
+    kernel (krylov_refine = 2), both against the oracle."""
+    m, M = 63, 4
+    st, dt = _case("heat", m, M)
+    op, oop = _ops(ctx, orc, st, m)
+    X = np.random.default_rng(70 + adjoint).standard_normal((3, m * m))
+    got = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+    ctx.set_param("krylov_refine", 2)
+    try:
+        ref = api.propagate(ctx, op, dt, M, X, adjoint=adjoint)
+    finally:
+        ctx.set_param("krylov_refine", 0)
+    want = orc.propagate(oop, dt, M, X, adjoint=adjoint, intervals=0)
+    for v in range(3):
+        assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
+        assert rel(ref[v], want[v]) <= 1e-10
