@@ -142,7 +142,7 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    a device workspace of the operator);
  *   "krylov_block_clusters": clusters in flight of the block CG (0 =
  *                    automatic: workspaces within 96 MB);
- *   "krylov_refine": FP64 steps of time-invariant 5-point operators by
+ *   "krylov_refine": FP64 steps of 5-point operators by
  *                    mixed-precision iterative refinement (FP64 residual,
  *                    FP32 correction from zero -- CG on the on-chip kernel
  *                    for symmetric operators, BiCGStab on the global-memory
@@ -156,9 +156,10 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    requested); 2 never (the FP64 Krylov kernels: on chip
  *                    where the grid fits, else in global memory).  The
  *                    batched solves (lrp_parareal_solve_batch) refine inside
- *                    their persistent queue kernel unless 2; SDIRK steppers
- *                    and time-dependent operators keep the FP64 Krylov
- *                    kernels;
+ *                    their persistent queue kernel unless 2.  SDIRK steps
+ *                    refine each stage solve on its stage matrix;
+ *                    time-dependent operators refine when symmetric (their
+ *                    nonsymmetric steps keep the FP64 Krylov kernels);
  *   "krylov_refine_digits": relative tolerance 10^-digits (1..7) of the FP32
  *                    correction solves (0 = automatic: 1e-3);
  *   "krylov_stage":  1 stages the stencil input of every FP32 pass of the

@@ -350,6 +350,9 @@ lrp_status stencil_plan(Ctx* c, Operator* op, double dt, int adjoint, StencilPla
 // Both CG kernels stop on the residual of the diagonally scaled system,
 // ||D^1/2 (d - B x)|| <= rtol ||D^1/2 d||, D = diag(B)^-1.
 bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys);
+// Whether the on-chip kernel takes single solves with this operator's (stage)
+// matrices at precision prec, whatever its stepper.
+bool stencil_onchip_fits(Ctx* c, const Operator* op, int prec, int nsys);
 // Scaled couplings (e^, n^) and scales (1/c, 1/sqrt(c), sqrt(c)) of the
 // step matrix laid out [rows + 2][pitch] from grid row -1, into buf
 // (allocated or grown as needed); T = double for prec 0, else float.
@@ -367,12 +370,12 @@ lrp_status stencil_propagate_block(Ctx* c, Operator* op, StencilPlan* plan, int 
                                    int prec, const KryArgs& base);
 lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
                                     int prec, const KryArgs& base);
-// FP64 steps of symmetric time-invariant 5-point operators by mixed-precision
-// iterative refinement (stencil_refine.cu): FP64 residuals, FP32 on-chip CG
-// or BiCGStab corrections, the FP64 Krylov kernels' stopping test.  Applies
-// (unless krylov_refine = 2, or the block CG was requested and applies) to
-// nonsymmetric operators, and to symmetric ones wherever the FP32 on-chip
-// kernel takes the grid.
+// FP64 steps (backward Euler, or each SDIRK stage solve) of 5-point operators
+// by mixed-precision iterative refinement (stencil_refine.cu): FP64
+// residuals, FP32 on-chip CG or BiCGStab corrections, the FP64 Krylov
+// kernels' stopping test.  Applies (unless krylov_refine = 2, or the block CG
+// was requested and applies) to nonsymmetric time-invariant operators, and to
+// symmetric ones wherever the FP32 on-chip kernel takes the grid.
 bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys);
 // One FP32 launch of the global-memory Krylov kernel (k_krylov<float>,
 // backward-Euler steps) for the correction solves of the refinement of

@@ -1160,7 +1160,7 @@ lrp_status stencil_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint
       return set_err(c, LRP_EINVAL, "time-dependent operator: steps beyond its time grid");
   }
   const bool block = !sdirk && !td && stencil_block_applies(c, op, prec, nsys, M, src.Q);
-  if (!block && !sdirk && stencil_refine_applies(c, op, prec, nsys)) {
+  if (!block && stencil_refine_applies(c, op, prec, nsys)) {
     c->bk_last[0] = c->bk_last[1] = c->bk_last[2] = 0;
     c->oc_last[0] = c->oc_last[1] = c->oc_last[2] = 0;
     return stencil_propagate_refine(c, op, plan, M, nsys, in, out, src, adjoint);

@@ -156,13 +156,19 @@ static int oc_choose(Ctx* c, int mx, int my, int nsys, int prec, int* cs_out, in
   return best_rpt;
 }
 
-bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys) {
+bool stencil_onchip_fits(Ctx* c, const Operator* op, int prec, int nsys) {
   if (!op->symmetric || c->p_krylov_onchip == 2) return false;
-  // time-dependent operators: FP32 backward-Euler steps
+  // time-dependent operators: FP32 solves
   const bool td = op->kind == 3;
-  if (td && (prec != 1 || op->stepper != 0)) return false;
+  if (td && prec != 1) return false;
   int cs = 0, ncl = 0;
   return oc_choose(c, op->mx, op->my, std::max(nsys, 1), prec, &cs, &ncl, td) > 0;
+}
+
+bool stencil_onchip_applies(Ctx* c, const Operator* op, int prec, int nsys) {
+  // the kernel runs backward-Euler steps
+  if (op->stepper != 0) return false;
+  return stencil_onchip_fits(c, op, prec, nsys);
 }
 
 lrp_status stencil_propagate_onchip(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,

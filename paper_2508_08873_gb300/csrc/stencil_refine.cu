@@ -1,6 +1,7 @@
-// FP64 backward-Euler steps of 5-point operators by mixed-precision iterative
-// refinement: every step (I + dt A) x = d, d = x_j + dt f(t_{j+1}), is solved
-// to the FP64 tolerance by rounds of
+// FP64 steps of 5-point operators by mixed-precision iterative refinement:
+// every backward-Euler step (I + dt A) x = d, d = x_j + dt f(t_{j+1}) -- and
+// every stage solve of an SDIRK step, (I + gamma dt A) x = d with d the
+// stage's right-hand side -- is solved to the FP64 tolerance by rounds of
 //   r = d - B x          (FP64, from the FP64 step matrix),
 //   B e = r              (FP32, to a looser relative tolerance (1e-3), from
 //                         e = 0: conjugate gradients on the on-chip kernel for
@@ -23,8 +24,9 @@
 // roundoff: the FP32 solve is exact only for the rounded matrix); a system
 // stops as soon as its own residual passes, so that the rounds of a step only
 // run the systems still above the tolerance.  The iterate is warm-started
-// from x_j as in the FP64 kernels.  Systems are processed in batches of at
-// most IR_BATCH with FP64 workspaces of four vectors each.
+// from x_j (an SDIRK stage from the previous stage value) as in the FP64
+// kernels.  Systems are processed in batches of at most IR_BATCH with FP64
+// workspaces of four vectors each (six with an SDIRK stepper).
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -69,9 +71,12 @@ __global__ void k_ir_scatter(PropOut out, int n, int s0, int cnt, const double* 
   }
 }
 
-// right-hand side of step j: D = X + dt f(t_{j+1}) (source sample j)
-__global__ void k_ir_rhs(PropSrc src, int n, int s0, int cnt, int j, double dt,
-                         const double* __restrict__ X, double* __restrict__ D) {
+// right-hand side of a solve: D = au A + a1 W + dt f (W may be null; f the
+// source sample `sample` of each system): backward Euler D = X + dt f(t_{j+1}),
+// SDIRK stage s D = su U0 + s1 U1 + gamma dt f(stage time)
+__global__ void k_ir_rhs(PropSrc src, int n, int s0, int cnt, int sample, double dt, double au,
+                         const double* __restrict__ A, double a1, const double* __restrict__ W,
+                         double* __restrict__ D) {
   const long tot = (long)cnt * n;
   for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x) {
     const int s = (int)(e / n), k = (int)(e % n), sys = s0 + s;
@@ -79,10 +84,19 @@ __global__ void k_ir_rhs(PropSrc src, int n, int s0, int cnt, int j, double dt,
     if (src.Q > 0) {
       const double* csys = src.c + sys_offset(src.map, src.c_slot_stride, src.cstride, sys);
       const double* gsys = src.map ? src.g + (long)src.map[2 * sys] * src.g_slot_stride : src.g;
-      for (int q = 0; q < src.Q; ++q) f += csys[(size_t)j * src.Q + q] * gsys[(size_t)q * n + k];
+      for (int q = 0; q < src.Q; ++q) f += csys[(size_t)sample * src.Q + q] * gsys[(size_t)q * n + k];
     }
-    D[e] = X[e] + dt * f;
+    double d = au * A[e] + dt * f;
+    if (W) d += a1 * W[e];
+    D[e] = d;
   }
+}
+
+// SDIRK step end: X = bu U0 + b1 U1 + b2 X
+__global__ void k_ir_combine(long tot, double bu, const double* __restrict__ U0, double b1,
+                             const double* __restrict__ U1, double b2, double* __restrict__ X) {
+  for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < tot; e += (long)gridDim.x * blockDim.x)
+    X[e] = bu * U0[e] + b1 * U1[e] + b2 * X[e];
 }
 
 // Residual of the listed systems (list[2 i] = system of the batch):
@@ -202,7 +216,7 @@ __global__ void k_ir_apply(int n, const int* __restrict__ list, const double* __
 // the adjoint runs the steps in reversed order), else 0
 __global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restrict__ one, int td,
                               PropIn in, const int* __restrict__ omap, const int* __restrict__ smap,
-                              int s0, int M, int j, int adj) {
+                              int s0, int M, int j, int adj, int sd, int stage, long nrows) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < cnt) {
     int row = 0;
@@ -210,7 +224,13 @@ __global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restric
       const int sys = s0 + i;
       const int* imap = in.map ? in.map : omap ? omap : smap;
       const long J0 = (long)(imap ? imap[2 * sys + 1] : in.interval0 + sys / in.ncol) * M;
-      row = (int)(adj ? J0 + M - 1 - j : J0 + j);
+      const long J = adj ? J0 + M - 1 - j : J0 + j;
+      // SDIRK: the operator at the stage time (rows 2J, 2J + 1; the adjoint
+      // solves with the second stage's matrix first)
+      const long r = sd ? 2 * J + (adj ? 1 - stage : stage) : J;
+      // the callers' maps name intervals inside the time grid (checked where
+      // they are made); a row outside it is never read
+      row = (int)(r < 0 ? 0 : r >= nrows ? nrows - 1 : r);
     }
     list[2 * i] = i;
     list[2 * i + 1] = row;
@@ -219,7 +239,7 @@ __global__ void k_ir_list_all(int cnt, int* __restrict__ list, double* __restric
 }
 
 bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys) {
-  if (prec != 0 || (op->kind != 1 && op->kind != 3) || op->stepper != 0) return false;
+  if (prec != 0 || (op->kind != 1 && op->kind != 3)) return false;
   // time-dependent operators: symmetric ones, on the on-chip kernel's TD variant
   if (op->kind == 3 && !op->symmetric) return false;
   if (c->p_krylov_refine == 2) return false;
@@ -227,7 +247,7 @@ bool stencil_refine_applies(Ctx* c, const Operator* op, int prec, int nsys) {
   // kernel (measured on GB300, adv2d nu = 0.01, dt = 1/4096, 64 systems, us
   // per system and step against FP64 BiCGStab: 511^2 207 / 556, 255^2 35 / 76)
   if (!op->symmetric) return true;
-  return stencil_onchip_applies(c, op, 1, std::min(nsys, IR_BATCH));
+  return stencil_onchip_fits(c, op, 1, std::min(nsys, IR_BATCH));
 }
 
 lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int M, int nsys,
@@ -237,8 +257,11 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   const int batch = std::min(nsys, IR_BATCH);
   const size_t vec = (size_t)batch * n;
   const int nblk = (n + IR_THREADS * IR_PTS - 1) / (IR_THREADS * IR_PTS);
-  // X, D, G, E (FP64), partial sums, two system lists, the counter, the constant 1
-  const size_t need = sizeof(double) * (4 * vec + (size_t)batch * nblk * 3 + (size_t)batch + 8) +
+  // X, D, G, E (FP64; SDIRK: U0, U1 too), partial sums, two system lists,
+  // the counter, the constant 1
+  const bool sd = op->stepper != 0;
+  const size_t nv = sd ? 6 : 4;
+  const size_t need = sizeof(double) * (nv * vec + (size_t)batch * nblk * 3 + (size_t)batch + 8) +
                       sizeof(int) * (4 * (size_t)batch + 8);
   lrp_status s;
   if (c->irws.bytes < need)
@@ -249,7 +272,9 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   double* D = X + vec;
   double* G = D + vec;
   double* E = G + vec;
-  double* part = E + vec;
+  double* U0 = E + vec;                       // SDIRK: the step's start state
+  double* U1 = U0 + (sd ? vec : 0);           // SDIRK: the first stage value
+  double* part = U1 + (sd ? vec : 0);
   double* sigma = part + (size_t)batch * nblk * 3;
   double* one = sigma + batch;
   int* listA = reinterpret_cast<int*>(one + 8);
@@ -262,6 +287,18 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   cudaMemsetAsync(c->irstat.ptr, 0, 32, st);
   const int bicg = op->symmetric ? 0 : 1;
   const int td = op->kind == 3 ? 1 : 0;       // every system on its own step's plan
+  // SDIRK: each stage solve refined on its own stage matrix B = I + gamma dt A
+  // (the plan's dt is gamma dt); the adjoint of a time-dependent operator runs
+  // the transposed step map W2 = B2^-T v, W1 = B1^-T (b1 v + b2 s1 W2),
+  // v' = bu v + b2 su W2 + W1 (the same stage body with these coefficients)
+  StepCoef sc = sd ? step_coefficients(op->stepper) : StepCoef{1.0, 0, 0, 0, 0, 0};
+  if (sd && td && adjoint) {
+    const StepCoef f = sc;
+    sc.su = f.b1;
+    sc.s1 = f.b2 * f.s1;
+    sc.b1 = f.b2 * f.su;
+    sc.b2 = 1.0;
+  }
   const double rtol2 = op->rtol64 * op->rtol64;
   const double floor2 = (IR_FLOOR * 0x1p-53) * (IR_FLOOR * 0x1p-53);
   // inner tolerance 1e-3 by default: measured on GB300 (diff2d, dt = 1/4096,
@@ -282,72 +319,95 @@ lrp_status stencil_propagate_refine(Ctx* c, Operator* op, StencilPlan* plan, int
   for (int s0 = 0; s0 < nsys; s0 += batch) {
     const int cnt0 = std::min(batch, nsys - s0);
     k_ir_gather<<<gsz, 256, 0, st>>>(in, n, s0, cnt0, X);
-    for (int j = 0; j < M; ++j) {
-      k_ir_rhs<<<gsz, 256, 0, st>>>(src, n, s0, cnt0, j, plan->dt, X, D);
-      k_ir_list_all<<<(cnt0 + 255) / 256, 256, 0, st>>>(cnt0, listA, one, td, in, out.map, src.map,
-                                                        s0, M, j, adjoint);
-      int nact = cnt0;
-      int* cur = listA;
-      int* nxt = listB;
-      for (int round = 0;; ++round) {
-        cudaEvent_t ev = nullptr;
-        timer_begin(c, fam, &ev);
-        k_ir_resid<<<dim3(nblk, nact), IR_THREADS, 0, st>>>(op->mx, op->my, bicg, B64, ldb,
-                                                            td ? 6 * ldb : 0L, cur, X, D, G, part);
-        cudaMemsetAsync(cnt, 0, sizeof(int), st);
-        k_ir_reduce<<<nact, 32, 0, st>>>(nblk, n, rtol2, floor2, cur, part, nxt, cnt, sigma);
-        timer_end(c, fam, ev);
-        e = cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
-        if (!e) e = cudaStreamSynchronize(st);
-        if (!e) e = cudaGetLastError();
-        if (e) return cuda_err(c, e, "refinement residual");
-        nact = *hcnt;
-        if (nact == 0) break;
-        if (round == IR_MAX_ROUNDS || op->max_iter == 0) { notconv = true; break; }
-        // the correction of every system still above the tolerance: FP32
-        // CG on B e = dt G = r / sigma from e = 0 (zero input, the scaled
-        // residual as the step's source), on chip
-        std::swap(cur, nxt);
-        k_ir_scale<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, plan->dt, cur, sigma, G);
-        KryArgs a{};
-        a.mx = op->mx;
-        a.my = op->my;
-        a.n = n;
-        a.M = 1;                       // TD: the list's second entry is the step's row (M = 1)
-        a.nJ = op->nJ;
-        a.adj = 0;
-        a.nsys = nact;
-        a.bicg = 0;
-        a.dt = plan->dt;
-        a.rtol = rtol_in;
-        a.max_iter = op->max_iter;
-        a.B = stencil_B(plan, op, 1);
-        a.Bs = stencil_Bs(plan, op, 1);
-        a.in.x = nullptr;
-        a.in.ncol = 1;
-        a.out.y = E;
-        a.out.y_f64 = 1;
-        a.out.map = cur;
-        a.out.slot_stride = n;
-        a.out.ldy = 0;
-        a.src.Q = 1;
-        a.src.g = G;
-        a.src.c = one;
-        a.src.cstride = 0;
-        a.src.map = cur;
-        a.src.c_slot_stride = 0;
-        a.src.g_slot_stride = n;
-        a.iters = iters;
-        a.status = istat;
-        a.bicg = bicg;
-        if (bicg) {
-          if ((s = krylov_f32_correction(c, op, plan, nact, a))) return s;
-        } else if ((s = stencil_propagate_onchip(c, op, plan, 1, nact, 1, a))) {
-          return s;
+    for (int j = 0; j < M && !notconv; ++j) {
+      // the refinement rounds of one solve B x = D (x warm-started in X) for
+      // every system of the batch, stage `stage` of step j
+      auto solve = [&](int stage) -> lrp_status {
+        k_ir_list_all<<<(cnt0 + 255) / 256, 256, 0, st>>>(cnt0, listA, one, td, in, out.map, src.map,
+                                                          s0, M, j, adjoint, sd ? 1 : 0, stage,
+                                                          (long)op->nJ * (sd ? 2 : 1));
+        int nact = cnt0;
+        int* cur = listA;
+        int* nxt = listB;
+        for (int round = 0;; ++round) {
+          cudaEvent_t ev = nullptr;
+          timer_begin(c, fam, &ev);
+          k_ir_resid<<<dim3(nblk, nact), IR_THREADS, 0, st>>>(op->mx, op->my, bicg, B64, ldb,
+                                                              td ? 6 * ldb : 0L, cur, X, D, G, part);
+          cudaMemsetAsync(cnt, 0, sizeof(int), st);
+          k_ir_reduce<<<nact, 32, 0, st>>>(nblk, n, rtol2, floor2, cur, part, nxt, cnt, sigma);
+          timer_end(c, fam, ev);
+          e = cudaMemcpyAsync(hcnt, cnt, sizeof(int), cudaMemcpyDeviceToHost, st);
+          if (!e) e = cudaStreamSynchronize(st);
+          if (!e) e = cudaGetLastError();
+          if (e) return cuda_err(c, e, "refinement residual");
+          nact = *hcnt;
+          if (nact == 0) break;
+          if (round == IR_MAX_ROUNDS || op->max_iter == 0) { notconv = true; break; }
+          // the correction of every system still above the tolerance: FP32
+          // CG on B e = dt G = r / sigma from e = 0 (zero input, the scaled
+          // residual as the step's source), on chip
+          std::swap(cur, nxt);
+          k_ir_scale<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, plan->dt, cur, sigma, G);
+          KryArgs a{};
+          a.mx = op->mx;
+          a.my = op->my;
+          a.n = n;
+          a.M = 1;                       // TD: the list's second entry is the step's row (M = 1)
+          a.nJ = op->nJ * (sd ? 2 : 1);  // rows of the time grid (two per step with SDIRK)
+          a.adj = 0;
+          a.nsys = nact;
+          a.bicg = 0;
+          a.dt = plan->dt;
+          a.rtol = rtol_in;
+          a.max_iter = op->max_iter;
+          a.B = stencil_B(plan, op, 1);
+          a.Bs = stencil_Bs(plan, op, 1);
+          a.in.x = nullptr;
+          a.in.ncol = 1;
+          a.out.y = E;
+          a.out.y_f64 = 1;
+          a.out.map = cur;
+          a.out.slot_stride = n;
+          a.out.ldy = 0;
+          a.src.Q = 1;
+          a.src.g = G;
+          a.src.c = one;
+          a.src.cstride = 0;
+          a.src.map = cur;
+          a.src.c_slot_stride = 0;
+          a.src.g_slot_stride = n;
+          a.iters = iters;
+          a.status = istat;
+          a.bicg = bicg;
+          if (bicg) {
+            if ((s = krylov_f32_correction(c, op, plan, nact, a))) return s;
+          } else if ((s = stencil_propagate_onchip(c, op, plan, 1, nact, 1, a))) {
+            return s;
+          }
+          k_ir_apply<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, cur, sigma, X, E);
         }
-        k_ir_apply<<<dim3((n + 1023) / 1024, nact), 256, 0, st>>>(n, cur, sigma, X, E);
+        return LRP_OK;
+      };
+      if (!sd) {
+        k_ir_rhs<<<gsz, 256, 0, st>>>(src, n, s0, cnt0, j, plan->dt, 1.0, X, 0.0, nullptr, D);
+        if ((s = solve(0))) return s;
+      } else {
+        // U1 = B1^-1 (U0 + gamma dt f_1), U2 = B2^-1 (su U0 + s1 U1 + gamma dt f_2),
+        // X = bu U0 + b1 U1 + b2 U2 (coefficients remapped for the adjoint of a
+        // time-dependent operator, whose step map is then the transposed one)
+        e = cudaMemcpyAsync(U0, X, sizeof(double) * (size_t)cnt0 * n, cudaMemcpyDeviceToDevice, st);
+        if (e) return cuda_err(c, e, "refinement stage copy");
+        k_ir_rhs<<<gsz, 256, 0, st>>>(src, n, s0, cnt0, 2 * j, plan->dt, 1.0, U0, 0.0, nullptr, D);
+        if ((s = solve(0))) return s;
+        if (notconv) break;
+        e = cudaMemcpyAsync(U1, X, sizeof(double) * (size_t)cnt0 * n, cudaMemcpyDeviceToDevice, st);
+        if (e) return cuda_err(c, e, "refinement stage copy");
+        k_ir_rhs<<<gsz, 256, 0, st>>>(src, n, s0, cnt0, 2 * j + 1, plan->dt, sc.su, U0, sc.s1, U1, D);
+        if ((s = solve(1))) return s;
+        if (notconv) break;
+        k_ir_combine<<<gsz, 256, 0, st>>>((long)cnt0 * n, sc.bu, U0, sc.b1, U1, sc.b2, X);
       }
-      if (notconv) break;
     }
     k_ir_scatter<<<gsz, 256, 0, st>>>(out, n, s0, cnt0, X);
     if (notconv) break;

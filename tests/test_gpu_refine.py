@@ -221,3 +221,71 @@ def test_refine_batched_queue(ctx, orc):
         assert orc.rel_err(a, ref) <= 1e-10, (P.mx, orc.rel_err(a, ref))
         assert orc.rel_err(b, ref) <= 1e-10
         assert rel(c2, d2) <= 1e-10
+
+
+def _stage_times(orc, scheme, dt, nJ):
+    cs, _, _ = orc.sdirk_tableau(scheme)
+    return np.array([[(J + cs[s]) * dt for s in range(2)] for J in range(nJ)]).ravel()
+
+
+@pytest.mark.parametrize("scheme", ["sdirk2", "sdirk2l"])
+@pytest.mark.parametrize("case", [("diff", 63), ("adv", 31), ("adv", 127), ("heat_td", 31)])
+@pytest.mark.parametrize("mode", [1, 2])
+def test_refine_sdirk_stages(ctx, orc, scheme, case, mode):
+    """SDIRK steps: each stage solve refined on its stage matrix (1), and the
+    FP64 Krylov kernel's stage body (2), forward with a two-term source at
+    the stage times and adjoint, within 1e-10 of the oracle; the
+    time-dependent heat operator (Experiment 3's conductivity at both stage
+    times of every step) exercises the rows of the stage times and the
+    transposed step map of the adjoint."""
+    kind, m = case
+    M, Q = 3, 2
+    if kind == "heat_td":
+        dt = 0.01
+        st = W.heat2d_td_at(m, _stage_times(orc, scheme, dt, 2 * M))
+        op = api.Operator.stencil5_td(ctx, m, m, st, stepper=scheme)
+        oop = orc.Stencil5TD(m, m, *(st[k] for k in "CWESN"), stepper=scheme)
+        kw = {"intervals": 0}
+    else:
+        dt = 1.0 / 1024
+        st = W.diff2d_op(m, 10 ** np.random.default_rng(m).uniform(0, 2, (8, 8))) \
+            if kind == "diff" else W.adv2d_op(m, 0.01)
+        op = api.Operator.stencil5(ctx, m, m, st)
+        op.set_stepper(scheme)
+        oop = orc.Stencil5(m, m, st["C"], st["W"], st["E"], st["S"], st["N"], stepper=scheme)
+        kw = {}
+    op.set_krylov(1e-14, 1e-6, 20000)
+    rng = np.random.default_rng(40 + m + len(scheme))
+    X = rng.standard_normal((3, m * m))
+    g = rng.standard_normal((Q, m * m))
+    c = rng.standard_normal((3, M, 2, Q))
+    ctx.set_param("krylov_refine", mode)
+    it0 = op.krylov_iterations()
+    try:
+        got = api.propagate(ctx, op, dt, M, X, g=g, c=c)
+        adj = api.propagate(ctx, op, dt, M, X, adjoint=True)
+    finally:
+        ctx.set_param("krylov_refine", 0)
+    want = orc.propagate(oop, dt, M, X, g=g, cvals=c, **kw)
+    wadj = orc.propagate(oop, dt, M, X, adjoint=True, **kw)
+    for v in range(3):
+        assert rel(got[v], want[v]) <= 1e-10, (v, rel(got[v], want[v]))
+        assert rel(adj[v], wadj[v]) <= 1e-10, (v, rel(adj[v], wadj[v]))
+    assert op.krylov_iterations() > it0
+
+
+def test_refine_sdirk_full_size_511(ctx, orc):
+    """diff2d 511^2 at dt = 1/4096 with the SDIRK2-L stepper, FP64 at the
+    fine-solve tolerance 1e-12: the stage solves refined by default."""
+    P = W.diff2d()
+    op = api.Operator.stencil5(ctx, P.mx, P.my, P.st)
+    op.set_krylov(1e-12, 1e-6, 20000)
+    op.set_stepper("sdirk2l")
+    oop = orc.Stencil5(P.mx, P.my, P.st["C"], P.st["W"], P.st["E"], P.st["S"], P.st["N"],
+                       stepper="sdirk2l")
+    rng = np.random.default_rng(19)
+    X = np.stack([P.u0, rng.standard_normal(P.n)])
+    got = api.propagate(ctx, op, P.dt, 2, X)
+    want = orc.propagate(oop, P.dt, 2, X)
+    for v in range(2):
+        assert rel(got[v], want[v]) <= 1e-9, (v, rel(got[v], want[v]))
