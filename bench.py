@@ -8,7 +8,12 @@ R = 16 with p = 8 oversampling, u0 = 5 seeded Gaussian bumps, f = 0.  A step
 builds the coarse solvers (randomized SVD: forward sketch, orthonormalisation,
 adjoint sketch, orthonormalisation, small SVD, lift) and runs one Parareal
 solve to the a posteriori tolerance 1e-8 (fine solves, coarse sweeps, bounds).
-The default arithmetic is the mixed mode (FP32 sketches, FP64 Parareal).
+The default arithmetic is the mixed mode (FP32 sketches, FP64 Parareal),
+with the fine backward-Euler steps computed from FP32 solves and one
+correction round per step whose residual is formed in pairs of FP32 numbers
+(--tri-refine 1: 2.7e-12 from the FP64 kernels' steps over an interval of
+256 steps); the same step is also timed with the fine solves on the FP64
+kernels (--tri-refine 0 times only that).
 
 value: solves/s with inputs resident in HBM (device-timed with CUDA events on
 the library's stream).  e2e: the same through the C ABI with host buffers (the
@@ -41,6 +46,7 @@ TOL = 1e-8
 # DRAM bytes per system of the FP64 fine-solve kernel, from one ncu capture of
 # k_tri_cluster_wt<13, 3> (62 systems: 2.1978 MB read, 0 written)
 F64_DRAM_BYTES_PER_SYSTEM = 2.1978e6 / 62
+IRT_DRAM_BYTES_PER_SYSTEM = None      # the refined FP32 kernel: not yet captured
 WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
 
 
@@ -95,6 +101,11 @@ def parse():
                     help="trisweep mode: batch sizes of the FP64 adr1d fine-solve sweep")
     ap.add_argument("--sweep-chunks", default="8,9,10,11,12,13,14,15,16",
                     help="trisweep mode: chunk lengths (tri_wchunk) of the one-warp kernel")
+    ap.add_argument("--sweep-refine", default="1,2",
+                    help="trisweep: round counts of the refined FP32 fine solves to time ('' = none)")
+    ap.add_argument("--tri-refine", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="1D fine solves from FP32 solves refined by pair residuals: rounds per step "
+                         "(0 = the FP64 kernels; the step is then also timed on them)")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-targets", default="",
                     help="serve mode: extra passes 'rate:adr1d_target_ms,...' with admission "
@@ -887,6 +898,52 @@ def run_exp3(args):
         print(json.dumps(line), flush=True)
 
 
+def fine_roofline(P, kern, k_list, ms_step, steps, rounds):
+    """Roofline entry of the dominant kernel family of the headline step.
+    Algorithmic flops per row and step: the FP64 kernels, Thomas with
+    precomputed pivots (5: one FMA forward, one MUL and one FMA backward);
+    the refined FP32 kernel, per step one solve (5) and per round a solve (5),
+    the pair residual (3 split products 9, six low-part FMAs 12, three
+    two-sums 18, the tail 7) and the pair update (9): 5 + 60 R."""
+    fam = max(("propagate_f64", "propagate_f32"), key=lambda f: kern[f][1])
+    nl, tot = kern[fam]
+    k_mean = statistics.mean(k_list)
+    systems_per_step = (P.N * k_mean - k_mean * (k_mean - 1) / 2) if fam == "propagate_f64" \
+        else 2 * P.N * (P.R + P.p)
+    per_row = (5.0 + 60.0 * rounds) if (fam == "propagate_f64" and rounds) else 5.0
+    flops_step = per_row * P.n * P.M * systems_per_step
+    launches_per_step = nl / steps
+    achieved = flops_step / (tot / steps) / 1e6 if tot > 0 else 0.0   # GFLOP/s
+    refined = fam == "propagate_f64" and rounds > 0
+    peak = FP32_PEAK_GFLOPS if (refined or fam == "propagate_f32") else FP64_PEAK_GFLOPS
+    # per-launch figures over the launches that propagate (one per Parareal
+    # iteration; the launches enqueued after the device-side stop return at
+    # once and are counted apart)
+    real_launches = k_mean if fam == "propagate_f64" else launches_per_step
+    systems_per_launch = systems_per_step / max(real_launches, 1)
+    # DRAM traffic of the FP64 fine-solve kernel, from one ncu capture on GB300
+    # (dram__bytes_read.sum + dram__bytes_write.sum of a 62-system launch of
+    # the 12-row-chunk variant: 2.31 MB read, nothing written back within the
+    # launch), per propagated system, times this run's systems per launch; of
+    # the refined kernel from its own capture (one 62-system launch)
+    traffic = None
+    if fam == "propagate_f64":
+        per_sys = IRT_DRAM_BYTES_PER_SYSTEM if refined else F64_DRAM_BYTES_PER_SYSTEM
+        traffic = per_sys * systems_per_launch if per_sys else None
+    return {"bound": "alu", "kernel": ("k_tri_irt (FP32 + pair residuals)" if refined else fam),
+            "achieved": achieved / 1e3, "peak": peak / 1e3,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+            "flops_per_row_step": per_row,
+            "algorithmic_bytes": 16.0 * P.n * systems_per_launch,
+            "systems_per_launch": systems_per_launch,
+            "launches_per_step": launches_per_step,
+            "noop_launches_per_step": launches_per_step - real_launches,
+            "share_of_step": (tot / steps) / ms_step,
+            "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz nominal (a throughput probe "
+                         "reaches 1.6 FMA/clk/SM = 1.007 TFLOP/s); FP32: 128 FMA/clk/SM; the "
+                         "refined kernel holds one system per SM (62 of 152 SMs at 62 systems)"}
+
+
 def run_trisweep(args):
     """CUDA-event time per launch of the FP64 fine-solve kernels on adr1d
     (n = 4095, 256 steps) over batch sizes and chunk lengths: the general
@@ -937,6 +994,27 @@ def run_trisweep(args):
         nl, ms = ctx.kernel_time("propagate_f64")
         ctx.set_kernel_timing(False)
         row["default"] = ms / max(nl, 1)
+        # FP32 solves refined by pair residuals (tri_refine = 1), per round
+        # count: time per launch and the largest relative difference from the
+        # FP64 kernel's result
+        Yr = torch.empty_like(X)
+        for rounds in [int(v) for v in args.sweep_refine.split(",") if v]:
+            ctx.set_param("tri_refine", 1)
+            ctx.set_param("tri_refine_rounds", rounds)
+            try:
+                for _ in range(max(1, args.warmup)):
+                    api.propagate(ctx, op, P.dt, P.M, X, out=Yr)
+                ctx.set_kernel_timing(True)
+                ctx.reset_kernel_time()
+                for _ in range(args.steps):
+                    api.propagate(ctx, op, P.dt, P.M, X, out=Yr)
+                nl, ms = ctx.kernel_time("propagate_f64")
+                ctx.set_kernel_timing(False)
+            finally:
+                ctx.set_param("tri_refine", 0)
+                ctx.set_param("tri_refine_rounds", 2)
+            d = (torch.linalg.vector_norm(Yr - Y, dim=1) / torch.linalg.vector_norm(Y, dim=1)).max()
+            row["refine_%d" % rounds] = {"ms": ms / max(nl, 1), "max_rel_diff_vs_f64": float(d)}
         table[str(nsys)] = row
     line = {"metric": "FP64 fine-solve kernel time per launch (adr1d n=4095, M=256)",
             "unit": "ms", "mode": "trisweep", "n_gpus": 1, "higher_is_better": False,
@@ -982,6 +1060,9 @@ def main():
     from paper_2508_08873_gb300 import api
 
     ctx = api.Context(local)
+    if args.tri_refine:
+        ctx.set_param("tri_refine", 1)
+        ctx.set_param("tri_refine_rounds", args.tri_refine)
     stream = torch.cuda.ExternalStream(ctx.stream, device=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     u0_d = torch.tensor(P.u0, dtype=torch.float64, device=dev)
@@ -1032,11 +1113,43 @@ def main():
     ctx.set_kernel_timing(False)
     clk = clocks.stop()
     ms_step, value = aggregate_over_ranks(statistics.mean(ms), world, dev)
+    # ---- the same step with the fine solves on the FP64 kernels ---------------
+    f64k = None
+    if args.tri_refine:
+        ctx.set_param("tri_refine", 0)
+        out64 = torch.empty_like(out_d)
+        for _ in range(max(2, args.warmup // 2)):
+            step(op, u0_d, out64)
+        ctx.set_kernel_timing(True)
+        ctx.reset_kernel_time()
+        barrier()
+        ev64, k64 = [], []
+        for s in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            info64 = step(op, u0_d, out64)
+            e1.record(stream)
+            ev64.append((e0, e1))
+            k64.append(info64["k_done"])
+        barrier()
+        kern64 = {f: ctx.kernel_time(f) for f in ("propagate_f64", "propagate_f32")}
+        ctx.set_kernel_timing(False)
+        ctx.set_param("tri_refine", 1)
+        ms64, value64 = aggregate_over_ranks(statistics.mean([a.elapsed_time(b) for a, b in ev64]),
+                                             world, dev)
+        f64k = {"solves_per_s": value64, "ms_per_step": ms64, "iterations": k64[-1],
+                "fine": "FP64 one-warp cluster kernels",
+                "roofline": fine_roofline(P, kern64, k64, ms64, args.steps, 0), "out": out64}
     if args.headline_only:
         extras = None
     else:
         extras = run_extras(args, ctx, op, P, step, stream, u0_d, out_d, flush, world)
+        ctx.set_param("tri_refine", 0)        # all FP64: the FP64 fine-solve kernels
         extras["all_fp64"] = all_fp64_leg(args, ctx, op, P, stream, flush)
+        ctx.set_param("tri_refine", 1 if args.tri_refine else 0)
         extras["krylov_hbm_frac"] = krylov_leg(ctx, ["mixed", "f64"], [64, 16], 3, 1)
         extras["serve"] = serve_leg(ctx, [10.0, 30.0, 100.0], 3.0, quiet=True,
                                     targets=[(100.0, 1000.0)])
@@ -1053,39 +1166,10 @@ def main():
                 extras.pop("ts_out").cpu().numpy(), ref)
             extras["all_fp64"]["rel_err_vs_oracle"] = orc.rel_err(
                 extras["all_fp64"].pop("out").cpu().numpy(), ref)
+        if f64k is not None:
+            f64k["rel_err_vs_oracle"] = orc.rel_err(f64k.pop("out").cpu().numpy(), ref)
     # ---- roofline of the dominant kernel ---------------------------------------
-    fam = max(("propagate_f64", "propagate_f32"), key=lambda f: kern[f][1])
-    nl, tot = kern[fam]
-    # algorithmic FP64/FP32 flops: Thomas with precomputed pivots = 5 flop per
-    # row-step (1 FMA forward, 1 MUL + 1 FMA backward), n rows, M steps, per system
-    k_mean = statistics.mean(k_list)
-    systems_per_step = (P.N * k_mean - k_mean * (k_mean - 1) / 2) if fam == "propagate_f64" \
-        else 2 * P.N * (P.R + P.p)
-    flops_step = 5.0 * P.n * P.M * systems_per_step
-    launches_per_step = nl / args.steps
-    achieved = flops_step / (tot / args.steps) / 1e6 if tot > 0 else 0.0   # GFLOP/s
-    peak = FP64_PEAK_GFLOPS if fam == "propagate_f64" else FP32_PEAK_GFLOPS
-    # DRAM traffic of the FP64 fine-solve kernel, from one ncu capture on GB300
-    # (dram__bytes_read.sum + dram__bytes_write.sum of a 62-system launch of
-    # the 12-row-chunk variant: 2.31 MB read, nothing written back within the
-    # launch), per propagated system, times this run's systems per launch
-    # per-launch figures over the launches that propagate (one per Parareal
-    # iteration; the launches enqueued after the device-side stop return at
-    # once and are counted apart)
-    real_launches = k_mean if fam == "propagate_f64" else launches_per_step
-    systems_per_launch = systems_per_step / max(real_launches, 1)
-    traffic = None
-    if fam == "propagate_f64":
-        traffic = F64_DRAM_BYTES_PER_SYSTEM * systems_per_launch
-    roof = {"bound": "alu", "kernel": fam, "achieved": achieved / 1e3, "peak": peak / 1e3,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
-            "algorithmic_bytes": 16.0 * P.n * systems_per_launch,
-            "systems_per_launch": systems_per_launch,
-            "launches_per_step": launches_per_step,
-            "noop_launches_per_step": launches_per_step - real_launches,
-            "share_of_step": (tot / args.steps) / ms_step,
-            "peak_note": "FP64: 152 SMs x 2 FMA/clk x 2.07 GHz nominal (a throughput probe "
-                         "reaches 1.6 FMA/clk/SM = 1.007 TFLOP/s); FP32: 128 FMA/clk/SM"}
+    roof = fine_roofline(P, kern, k_list, ms_step, args.steps, args.tri_refine)
     kernels = {f: {"launches": v[0], "ms_total": v[1]} for f, v in kern.items()}
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
@@ -1102,6 +1186,10 @@ def main():
                            "l2": "flushed (256 MB write) between timed steps",
                            "parallelism": "replicas" if world > 1 else "1 GPU"},
                 "iterations": k_list[-1], "rel_err_vs_oracle": err,
+                "fine_solves": ("FP32 solves, %d pair-residual correction round(s) per step "
+                                "(k_tri_irt)" % args.tri_refine) if args.tri_refine
+                               else "FP64 one-warp cluster kernels",
+                "fine_f64_kernel": f64k,
                 **(extras or {"e2e": None}),
                 "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
                 "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu,

@@ -168,7 +168,22 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    the TMA engine per pass, completion on an mbarrier with
  *                    bounded waits (LRP_ETIMEOUT); results are bitwise those
  *                    of 0 (default: the stencil reads global memory through
- *                    L1), and on GB300 it measured no faster.
+ *                    L1), and on GB300 it measured no faster;
+ *   "tri_refine":    1 computes the FP64 backward-Euler steps of
+ *                    time-invariant tridiagonal operators (n <= 4096,
+ *                    forward, no source term) from FP32 solves: per step one
+ *                    FP32 solve, then "tri_refine_rounds" corrections, each
+ *                    the FP32 solve of the residual x_j - B y formed in pairs
+ *                    of FP32 numbers (exact products by FMA, two-sum
+ *                    additions, B's FP64 entries as hi + lo pairs), the state
+ *                    carried as a pair (about 48 bits).  One system per CTA.
+ *                    Results are not those of the FP64 kernels: after 256
+ *                    steps of the adr1d operator (n = 4095) they differ by
+ *                    2.7e-12 relative with one round, 1.4e-12 with two
+ *                    (the 48-bit pair form of B enters every step alike).
+ *                    0 (default) keeps the FP64 kernels;
+ *   "tri_refine_rounds": correction rounds per step of tri_refine (1..3,
+ *                    default 2).
  * Results do not depend on these settings beyond rounding (the block
  * solver stops every system on the same residual test as the others). */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);

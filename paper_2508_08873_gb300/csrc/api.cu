@@ -44,7 +44,7 @@ void ctx_release(Ctx* c) {
   if (!c || --c->refs > 0) return;
   cudaSetDevice(c->device);
   cudaStreamSynchronize(c->stream);
-  for (DevBuf* b : {&c->kws, &c->kstat, &c->bws, &c->irws, &c->irstat}) b->release();
+  for (DevBuf* b : {&c->kws, &c->kstat, &c->bws, &c->irws, &c->irstat, &c->triws}) b->release();
   pool_drain(c);
   for (auto& kv : c->timers)
     for (auto& pr : kv.second.pairs) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
@@ -346,6 +346,12 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "krylov_stage") {
     if (value != 0 && value != 1) return LRP_EINVAL;
     c->p_krylov_stage = value;
+  } else if (k == "tri_refine") {
+    if (value != 0 && value != 1) return LRP_EINVAL;
+    c->p_tri_refine = value;
+  } else if (k == "tri_refine_rounds") {
+    if (value < 1 || value > 3) return LRP_EINVAL;
+    c->p_tri_refine_rounds = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -368,6 +374,8 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "krylov_refine") *value = c->p_krylov_refine;
   else if (k == "krylov_refine_digits") *value = c->p_krylov_refine_digits;
   else if (k == "krylov_stage") *value = c->p_krylov_stage;
+  else if (k == "tri_refine") *value = c->p_tri_refine;
+  else if (k == "tri_refine_rounds") *value = c->p_tri_refine_rounds;
   else if (k == "krylov_block_last_systems") *value = c->bk_last[0];
   else if (k == "krylov_block_last_cs") *value = c->bk_last[1];
   else if (k == "krylov_block_last_clusters") *value = c->bk_last[2];
@@ -551,6 +559,8 @@ lrp_status propagate_any(Ctx* c, Operator* op, double dt, int M, int adjoint, in
     if (s) return s;
     return tri_propagate(c, op, plan, M, nsys, prec, in, out, src);
   }
+  if (op->kind == 0 && tri_ir_applies(c, op, prec, adjoint, M, in, src))
+    return tri_propagate_ir(c, op, dt, M, nsys, in, out);
   if (op->kind == 0) {
     // Small batches of long systems: spread every system over a cluster of
     // C CTAs (chunks of m rows, spt systems per thread) so that more SMs take

@@ -60,11 +60,13 @@ struct Ctx {
   int p_krylov_refine = 0;   // FP64 2D steps by iterative refinement: 0 auto, 1 where it applies, 2 never
   int p_krylov_refine_digits = 0;   // relative tolerance 10^-digits of its FP32 solves (0: 1e-3)
   int p_krylov_stage = 0;    // FP32 global-memory Krylov kernel: 1 stages stencil inputs by bulk copies, 0 not
+  int p_tri_refine = 0;      // FP64 1D steps from FP32 solves with pair residuals: 1 on, 0 off
+  int p_tri_refine_rounds = 2;   // correction rounds per step of those steps (1..3)
   // Scratch of 2D propagations, per context (one host thread and one stream
   // each, so that a server's contexts and the caller's never share it): the
   // Krylov workspace and status, the block CG workspace, the refinement's
   // workspace and inner-solve status.  Released before the pool is drained.
-  DevBuf kws, kstat, bws, irws, irstat;
+  DevBuf kws, kstat, bws, irws, irstat, triws;
   int bk_last[3] = {0, 0, 0};  // last block CG launch: systems per block, CTAs per cluster, clusters
   int p_orth_cluster = 0;    // CTAs per cluster of the CGS2 kernel (0 auto, -1 one-CTA kernel)
   int p_tri_spt = 0;         // systems per thread of the cluster tridiagonal kernel (1, 2)
@@ -295,6 +297,13 @@ void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m,
 // Time-dependent tridiagonal operators (tridiag_td.cu): one CTA per system,
 // parallel cyclic reduction of every step's own matrix; system s runs the
 // steps of interval (map ? map[2s+1] : in.interval0 + s / in.ncol).
+// FP64 backward-Euler steps of time-invariant tridiagonal operators (n <=
+// 4096, forward, no source) from FP32 solves, each step refined by residuals
+// in pairs of FP32 numbers (tridiag_ir.cu); applies when tri_refine = 1.
+bool tri_ir_applies(Ctx* c, const Operator* op, int prec, int adjoint, int M, const PropIn& in,
+                    const PropSrc& src);
+lrp_status tri_propagate_ir(Ctx* c, Operator* op, double dt, int M, int nsys, const PropIn& in,
+                            const PropOut& out);
 lrp_status tri_td_propagate(Ctx* c, Operator* op, double dt, int M, int adjoint, int nsys,
                             int prec, const PropIn& in, const PropOut& out, const PropSrc& src);
 
