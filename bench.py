@@ -998,9 +998,13 @@ def run_trisweep(args):
         # count: time per launch and the largest relative difference from the
         # FP64 kernel's result
         Yr = torch.empty_like(X)
-        for rounds in [int(v) for v in args.sweep_refine.split(",") if v]:
+        for rounds, (vname, clus, chunk) in [(int(v), var) for v in args.sweep_refine.split(",") if v
+                                             for var in (("", 0, 0), ("_cta8", 0, 8), ("_cta12", 0, 12),
+                                                         ("_cluster", 1, 0))]:
             ctx.set_param("tri_refine", 1)
             ctx.set_param("tri_refine_rounds", rounds)
+            ctx.set_param("tri_refine_cluster", clus)
+            ctx.set_param("tri_wchunk", chunk)
             try:
                 for _ in range(max(1, args.warmup)):
                     api.propagate(ctx, op, P.dt, P.M, X, out=Yr)
@@ -1013,8 +1017,10 @@ def run_trisweep(args):
             finally:
                 ctx.set_param("tri_refine", 0)
                 ctx.set_param("tri_refine_rounds", 2)
+                ctx.set_param("tri_refine_cluster", 0)
+                ctx.set_param("tri_wchunk", 0)
             d = (torch.linalg.vector_norm(Yr - Y, dim=1) / torch.linalg.vector_norm(Y, dim=1)).max()
-            row["refine_%d" % rounds] = {"ms": ms / max(nl, 1), "max_rel_diff_vs_f64": float(d)}
+            row["refine_%d%s" % (rounds, vname)] = {"ms": ms / max(nl, 1), "max_rel_diff_vs_f64": float(d)}
         table[str(nsys)] = row
     line = {"metric": "FP64 fine-solve kernel time per launch (adr1d n=4095, M=256)",
             "unit": "ms", "mode": "trisweep", "n_gpus": 1, "higher_is_better": False,
@@ -1115,7 +1121,7 @@ def main():
     ms_step, value = aggregate_over_ranks(statistics.mean(ms), world, dev)
     # ---- the same step with the fine solves on the FP64 kernels ---------------
     f64k = None
-    if args.tri_refine:
+    if args.tri_refine and not args.headline_only:
         ctx.set_param("tri_refine", 0)
         out64 = torch.empty_like(out_d)
         for _ in range(max(2, args.warmup // 2)):

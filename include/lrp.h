@@ -183,7 +183,12 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    (the 48-bit pair form of B enters every step alike).
  *                    0 (default) keeps the FP64 kernels;
  *   "tri_refine_rounds": correction rounds per step of tri_refine (1..3,
- *                    default 2).
+ *                    default 2);
+ *   "tri_refine_cluster": 0 (default) one CTA of up to 16 warps per system
+ *                    (block barriers), 1 a cluster of one-warp CTAs per
+ *                    system for constant-coefficient operators (cluster
+ *                    barriers; measured slower on GB300: 0.73 against
+ *                    0.47 ms per 62-system launch of adr1d).
  * Results do not depend on these settings beyond rounding (the block
  * solver stops every system on the same residual test as the others). */
 lrp_status lrp_set_param(lrp_ctx* ctx, const char* name, int value);

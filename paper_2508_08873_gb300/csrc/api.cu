@@ -352,6 +352,9 @@ lrp_status lrp_set_param(lrp_ctx* c, const char* name, int value) {
   } else if (k == "tri_refine_rounds") {
     if (value < 1 || value > 3) return LRP_EINVAL;
     c->p_tri_refine_rounds = value;
+  } else if (k == "tri_refine_cluster") {
+    if (value != 0 && value != 1) return LRP_EINVAL;
+    c->p_tri_refine_cluster = value;
   } else {
     return set_err(c, LRP_EINVAL, "unknown parameter");
   }
@@ -376,6 +379,7 @@ lrp_status lrp_get_param(lrp_ctx* c, const char* name, int* value) {
   else if (k == "krylov_stage") *value = c->p_krylov_stage;
   else if (k == "tri_refine") *value = c->p_tri_refine;
   else if (k == "tri_refine_rounds") *value = c->p_tri_refine_rounds;
+  else if (k == "tri_refine_cluster") *value = c->p_tri_refine_cluster;
   else if (k == "krylov_block_last_systems") *value = c->bk_last[0];
   else if (k == "krylov_block_last_cs") *value = c->bk_last[1];
   else if (k == "krylov_block_last_clusters") *value = c->bk_last[2];

@@ -62,6 +62,7 @@ struct Ctx {
   int p_krylov_stage = 0;    // FP32 global-memory Krylov kernel: 1 stages stencil inputs by bulk copies, 0 not
   int p_tri_refine = 0;      // FP64 1D steps from FP32 solves with pair residuals: 1 on, 0 off
   int p_tri_refine_rounds = 2;   // correction rounds per step of those steps (1..3)
+  int p_tri_refine_cluster = 0;  // those steps: 0 one CTA per system, 1 a cluster of one-warp CTAs
   // Scratch of 2D propagations, per context (one host thread and one stream
   // each, so that a server's contexts and the caller's never share it): the
   // Krylov workspace and status, the block CG workspace, the refinement's

@@ -25,9 +25,13 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include <cooperative_groups.h>
+
 #include "tri_warp.cuh"
 
 namespace lrp {
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -280,13 +284,75 @@ struct IrtCoef {
   float lh, ll, dh, dl, uh, ul;   // pairs of the lower, diagonal, upper entries
 };
 
-template <int MM>
-__global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoef B, int rounds) {
-  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
-  __shared__ float pubg[2][CL_MAXC][4];
-  __shared__ float edge[CL_MAXC][4];       // per warp: first row (hi, lo), last row (hi, lo)
+// Exchanges of the constant-coefficient steps between the C warps of one
+// system: the four values of the super system (as in the one-warp kernels)
+// and each warp's first and last row (the residual's neighbours across a warp
+// edge).  sync() is the barrier after which both are visible.
+// Warps of one CTA: shared memory and a block barrier.
+struct IrtXchBlock {
+  float (*pubg)[CL_MAXC][4];
+  float (*edge)[4];                 // per warp: first row (hi, lo), last row (hi, lo)
+  __device__ __forceinline__ void publish(int pb, int c, int tl, int, float v0, float v1, float v2,
+                                          float v3) {
+    if (tl == 0) {
+      float* d = &pubg[pb][c][0];
+      d[0] = v0; d[1] = v1; d[2] = v2; d[3] = v3;
+    }
+  }
+  __device__ __forceinline__ float slot(int pb, int q, int k) const { return pubg[pb][q][k]; }
+  __device__ __forceinline__ void sync() { __syncthreads(); }
+  __device__ __forceinline__ void put_edges(int c, int tl, int, float fh, float fl_, float lh,
+                                            float ll) {
+    if (tl == 0) { edge[c][0] = fh; edge[c][1] = fl_; }
+    if (tl == 31) { edge[c][2] = lh; edge[c][3] = ll; }
+  }
+  // the row before this warp's first (from warp c-1) and after its last
+  __device__ __forceinline__ void get_edges(int c, int C, float& lh, float& ll, float& rh,
+                                            float& rl) const {
+    lh = c > 0 ? edge[c - 1][2] : 0.f;
+    ll = c > 0 ? edge[c - 1][3] : 0.f;
+    rh = c + 1 < C ? edge[c + 1][0] : 0.f;
+    rl = c + 1 < C ? edge[c + 1][1] : 0.f;
+  }
+};
+
+// One-warp CTAs of a cluster (one per SM where the cluster spreads): lanes
+// store into the other CTAs' shared memory, one cluster barrier.
+struct IrtXchCluster {
+  float (*pubg)[CL_MAXC][4];        // this CTA's receive buffers
+  float* const* rpub;               // the receive buffers of the cluster's CTAs
+  float* eg;                        // this CTA's edges: [0..1] the row before, [2..3] after
+  float* const* reg;                // the edges of the cluster's CTAs
+  __device__ __forceinline__ void publish(int pb, int c, int tl, int C, float v0, float v1,
+                                          float v2, float v3) {
+    if (tl < C) {
+      float* d = rpub[tl] + (pb * CL_MAXC + c) * 4;
+      d[0] = v0; d[1] = v1; d[2] = v2; d[3] = v3;
+    }
+  }
+  __device__ __forceinline__ float slot(int pb, int q, int k) const { return pubg[pb][q][k]; }
+  __device__ __forceinline__ void sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory");
+  }
+  __device__ __forceinline__ void put_edges(int c, int tl, int C, float fh, float fl_, float lh,
+                                            float ll) {
+    if (tl == 0 && c > 0) { reg[c - 1][2] = fh; reg[c - 1][3] = fl_; }
+    if (tl == 31 && c + 1 < C) { reg[c + 1][0] = lh; reg[c + 1][1] = ll; }
+  }
+  __device__ __forceinline__ void get_edges(int c, int C, float& lh, float& ll, float& rh,
+                                            float& rl) const {
+    lh = c > 0 ? eg[0] : 0.f;
+    ll = c > 0 ? eg[1] : 0.f;
+    rh = c + 1 < C ? eg[2] : 0.f;
+    rl = c + 1 < C ? eg[3] : 0.f;
+  }
+};
+
+template <int MM, class X>
+__device__ __forceinline__ void irt_steps(const ClKArgs& a, const IrtCoef& B, int rounds, X& xch,
+                                          int c, int tl, int sys0, int dsys) {
   const int C = a.C, n = a.n;
-  const int c = (int)(threadIdx.x >> 5), tl = (int)(threadIdx.x & 31);
   const int t = c * 32 + tl;
   const int r0 = t * MM;
   const unsigned FULL = 0xffffffffu;
@@ -320,6 +386,8 @@ __global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoe
                                            : (c > 0 ? minv[(c - 1) * CL_MAXC + q] : 0.f))
                            : 0.f;
   int pb = 0;
+  // B^-1 v for the whole system (v: this lane's chunk, v[MM-1] the
+  // interface row); one exchange and barrier
   auto solve = [&](float* v) {
 #pragma unroll
     for (int i = 1; i < MM - 1; ++i) v[i] = __fmaf_rn(-fl[i], v[i - 1], v[i]);
@@ -340,17 +408,13 @@ __global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoe
     const float v1 = __shfl_sync(FULL, z0, 30);
     const float v2 = __shfl_sync(FULL, r, 31);
     const float v3 = __shfl_sync(FULL, v[0], 0);
-    if (tl == 0) {
-      pubg[pb][c][0] = v0;
-      pubg[pb][c][1] = v1;
-      pubg[pb][c][2] = v2;
-      pubg[pb][c][3] = v3;
-    }
-    __syncthreads();
+    xch.publish(pb, c, tl, C, v0, v1, v2, v3);
+    xch.sync();
     float rhs = 0.f;
     if (q < C) {
-      rhs = __fmaf_rn(-sa, pubg[pb][q][1], pubg[pb][q][2]);
-      if (q + 1 < C) rhs = __fmaf_rn(-sc2, pubg[pb][q + 1][3], __fmaf_rn(-sc1, pubg[pb][q + 1][0], rhs));
+      rhs = __fmaf_rn(-sa, xch.slot(pb, q, 1), xch.slot(pb, q, 2));
+      if (q + 1 < C)
+        rhs = __fmaf_rn(-sc2, xch.slot(pb, q + 1, 3), __fmaf_rn(-sc1, xch.slot(pb, q + 1, 0), rhs));
     }
     float Ys = msel * rhs;
 #pragma unroll
@@ -365,7 +429,7 @@ __global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoe
     v[MM - 1] = y;
   };
   float xh[MM], xl[MM], yh[MM], yl[MM];
-  for (int sys = blockIdx.x; sys < a.nsys; sys += gridDim.x) {
+  for (int sys = sys0; sys < a.nsys; sys += dsys) {
     const long ox = a.in.x ? sys_offset(a.in.map, a.in.slot_stride, a.in.ldx, sys) : 0;
 #pragma unroll
     for (int i = 0; i < MM; ++i) {
@@ -389,26 +453,15 @@ __global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoe
       }
       for (int k = 0; k < rounds; ++k) {
         // the rows beside this lane's chunk: neighbouring lanes, and at the
-        // warp's edges the neighbouring warps' rows through shared memory
-        if (tl == 0) {
-          edge[c][0] = yh[0];
-          edge[c][1] = yl[0];
-        }
-        if (tl == 31) {
-          edge[c][2] = yh[MM - 1];
-          edge[c][3] = yl[MM - 1];
-        }
-        __syncthreads();
+        // warp's edges the neighbouring warps' rows
+        xch.put_edges(c, tl, C, yh[0], yl[0], yh[MM - 1], yl[MM - 1]);
+        xch.sync();
         float lh_ = __shfl_up_sync(FULL, yh[MM - 1], 1), ll_ = __shfl_up_sync(FULL, yl[MM - 1], 1);
         float rh_ = __shfl_down_sync(FULL, yh[0], 1), rl_ = __shfl_down_sync(FULL, yl[0], 1);
-        if (tl == 0) {
-          lh_ = c > 0 ? edge[c - 1][2] : 0.f;
-          ll_ = c > 0 ? edge[c - 1][3] : 0.f;
-        }
-        if (tl == 31) {
-          rh_ = c + 1 < C ? edge[c + 1][0] : 0.f;
-          rl_ = c + 1 < C ? edge[c + 1][1] : 0.f;
-        }
+        float elh, ell, erh, erl;
+        xch.get_edges(c, C, elh, ell, erh, erl);
+        if (tl == 0) { lh_ = elh; ll_ = ell; }
+        if (tl == 31) { rh_ = erh; rl_ = erl; }
         // r = X - B Y in pair arithmetic (rows past n: zero)
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
@@ -428,7 +481,7 @@ __global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoe
           tail = __fsub_rn(tail, __fadd_rn(__fadd_rn(e1, e2), __fadd_rn(e3, sm)));
           v[i] = r0 + i < n ? __fadd_rn(s, tail) : 0.f;
         }
-        solve(v);   // its barrier: every lane has read the warp edges
+        solve(v);   // its barrier: every warp has read the edges
 #pragma unroll
         for (int i = 0; i < MM; ++i) {
           float s, e;
@@ -459,13 +512,78 @@ __global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoe
   }
 }
 
+// one system per CTA of C warps
+template <int MM>
+__global__ void __launch_bounds__(ir_threads(MM), 1) k_tri_irt(ClKArgs a, IrtCoef B, int rounds) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  __shared__ float pubg[2][CL_MAXC][4];
+  __shared__ float edge[CL_MAXC][4];
+  IrtXchBlock xch{pubg, edge};
+  irt_steps<MM>(a, B, rounds, xch, (int)(threadIdx.x >> 5), (int)(threadIdx.x & 31),
+                (int)blockIdx.x, (int)gridDim.x);
+}
+
+// one system per cluster of C one-warp CTAs
+template <int MM>
+__global__ void __launch_bounds__(32) k_tri_irt_cl(ClKArgs a, IrtCoef B, int rounds) {
+  if (a.in.stop && *a.in.stop) return;   // the iteration has stopped on the device
+  cg::cluster_group cl = cg::this_cluster();
+  __shared__ float pubg[2][CL_MAXC][4];
+  __shared__ float eg[4];
+  __shared__ float* rpub[CL_MAXC];
+  __shared__ float* reg[CL_MAXC];
+  const int C = a.C;
+  const int c = (int)cl.block_rank();
+  const int tl = threadIdx.x;
+  if (tl < 4) eg[tl] = 0.f;
+  if (tl < C) {
+    rpub[tl] = cl.map_shared_rank(&pubg[0][0][0], tl);
+    reg[tl] = cl.map_shared_rank(&eg[0], tl);
+  }
+  __syncwarp();
+  cl.sync();   // every CTA of the cluster runs before any remote store into its shared memory
+  IrtXchCluster xch{pubg, rpub, eg, reg};
+  irt_steps<MM>(a, B, rounds, xch, c, tl, (int)blockIdx.x / C, (int)gridDim.x / C);
+  cl.sync();   // no CTA leaves while others may still store into its shared memory
+}
+
 template <int MM>
 lrp_status launch_irt(Ctx* c, ClPlan* pl, ClKArgs& a, const IrtCoef& B, int rounds) {
-  const int grid = std::min(a.nsys, c->num_sms);
+  const int C = pl->C;
+  cudaError_t e;
   cudaEvent_t ev = nullptr;
+  if (c->p_tri_refine_cluster && C >= 2) {
+    auto kern = k_tri_irt_cl<MM>;
+    if (C > 8) {
+      e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+      if (e) return cuda_err(c, e, "cluster size 16 not available");
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.blockDim = dim3(32);
+    cfg.gridDim = dim3(C);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = c->stream;
+    int maxc = 0;
+    e = cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg);
+    if (e || maxc < 1) { cudaGetLastError(); maxc = std::max(1, c->num_sms / C); }
+    cfg.gridDim = dim3(std::min(a.nsys, maxc) * C);
+    timer_begin(c, "propagate_f64", &ev);
+    e = cudaLaunchKernelEx(&cfg, kern, a, B, rounds);
+    timer_end(c, "propagate_f64", ev);
+    if (e) return cuda_err(c, e, "k_tri_irt_cl launch");
+    return LRP_OK;
+  }
+  const int grid = std::min(a.nsys, c->num_sms);
   timer_begin(c, "propagate_f64", &ev);
-  k_tri_irt<MM><<<grid, 32 * pl->C, 0, c->stream>>>(a, B, rounds);
-  cudaError_t e = cudaGetLastError();
+  k_tri_irt<MM><<<grid, 32 * C, 0, c->stream>>>(a, B, rounds);
+  e = cudaGetLastError();
   timer_end(c, "propagate_f64", ev);
   if (e) return cuda_err(c, e, "k_tri_irt launch");
   return LRP_OK;
@@ -474,9 +592,11 @@ lrp_status launch_irt(Ctx* c, ClPlan* pl, ClKArgs& a, const IrtCoef& B, int roun
 }  // namespace
 
 // chunk length and warps per system of the refined FP32 path: the longest
-// chunk (16, 12 or 8 rows) whose 32 C chunks cover n with C <= 16 warps
-static bool tri_ir_shape(int n, int* mm, int* C) {
+// chunk (16, 12 or 8 rows; pref, when one of these, alone) whose 32 C chunks
+// cover n within the warps a CTA of that chunk length may have
+static bool tri_ir_shape(int n, int pref, int* mm, int* C) {
   for (int m : {16, 12, 8}) {
+    if ((pref == 8 || pref == 12 || pref == 16) && m != pref) continue;
     const int cw = ((n + m - 1) / m + 31) / 32;
     if (cw >= 1 && 32 * cw <= ir_threads(m) && ir_smem(32 * cw * m) <= 200 * 1024) {
       *mm = m;
@@ -493,14 +613,14 @@ bool tri_ir_applies(Ctx* c, const Operator* op, int prec, int adjoint, int M, co
   if (prec != 0 || adjoint || M <= 0 || op->kind != 0 || op->stepper != 0 || src.Q > 0 || in.gen)
     return false;
   int mm = 0, C = 0;
-  return op->n >= 64 && tri_ir_shape(op->n, &mm, &C);
+  return op->n >= 64 && tri_ir_shape(op->n, c->p_tri_wchunk, &mm, &C);
 }
 
 lrp_status tri_propagate_ir(Ctx* c, Operator* op, double dt, int M, int nsys, const PropIn& in,
                             const PropOut& out) {
   if (nsys <= 0) return LRP_OK;
   int mm = 0, C = 0;
-  if (!tri_ir_shape(op->n, &mm, &C)) return set_err(c, LRP_EINVAL, "refined FP32 tridiagonal: n out of range");
+  if (!tri_ir_shape(op->n, c->p_tri_wchunk, &mm, &C)) return set_err(c, LRP_EINVAL, "refined FP32 tridiagonal: n out of range");
   ClPlan* pl = nullptr;
   lrp_status s = tri_get_cluster_plan(c, op, dt, 0, C, mm, &pl, 1);
   if (s) return s;

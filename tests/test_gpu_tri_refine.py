@@ -8,8 +8,10 @@ entries keeps 48 bits, and its error enters every step alike: measured on
 the adr1d operator, n = 4095, 256 steps, 2.7e-12 from the FP64 kernels for
 one round and 1.4e-12 for two), so one round is held to 2e-11 and two
 rounds to 5e-12; the FP64 kernels to 1e-12 on the same inputs.  Constant-
-coefficient operators (adr1d, heat1d) run the register kernel, the
-variable-coefficient one the shared-memory kernel.
+coefficient operators (adr1d, heat1d) run the register kernel -- on one
+CTA per system or a cluster of one-warp CTAs per system, with 16-row chunks
+and with 8-row chunks (up to 16 warps) -- the variable-coefficient one the
+shared-memory kernel.
 """
 import numpy as np
 import pytest
@@ -59,7 +61,8 @@ def _case(name):
 
 @pytest.mark.parametrize("case", ["adr4095", "adr1023", "adr1500", "heat255", "var700"])
 @pytest.mark.parametrize("rounds,tol", [(1, 2e-11), (2, 5e-12)])
-def test_tri_refine_matches_oracle(ctx, orc, case, rounds, tol):
+@pytest.mark.parametrize("variant", ["cta", "cta8", "cluster", "cluster8"])
+def test_tri_refine_matches_oracle(ctx, orc, case, rounds, tol, variant):
     lo, di, up, dt, M, u0 = _case(case)
     n = lo.shape[0]
     op = api.Operator.tridiag(ctx, lo, di, up)
@@ -69,11 +72,15 @@ def test_tri_refine_matches_oracle(ctx, orc, case, rounds, tol):
     f64 = api.propagate(ctx, op, dt, M, X)
     ctx.set_param("tri_refine", 1)
     ctx.set_param("tri_refine_rounds", rounds)
+    ctx.set_param("tri_refine_cluster", 1 if variant.startswith("cluster") else 0)
+    ctx.set_param("tri_wchunk", 8 if variant.endswith("8") else 0)
     try:
         got = api.propagate(ctx, op, dt, M, X)
     finally:
         ctx.set_param("tri_refine", 0)
         ctx.set_param("tri_refine_rounds", 2)
+        ctx.set_param("tri_refine_cluster", 0)
+        ctx.set_param("tri_wchunk", 0)
     want = orc.propagate(oop, dt, M, X)
     for v in range(X.shape[0]):
         assert rel(got[v], want[v]) <= tol, (v, rel(got[v], want[v]))
@@ -103,8 +110,9 @@ def test_tri_refine_parareal(ctx, orc):
 
 def test_tri_refine_params(ctx):
     for name, bad in (("tri_refine", 2), ("tri_refine", -1), ("tri_refine_rounds", 0),
-                      ("tri_refine_rounds", 4)):
+                      ("tri_refine_rounds", 4), ("tri_refine_cluster", 2)):
         with pytest.raises(_native.LrpError) as ei:
             ctx.set_param(name, bad)
         assert ei.value.status == _native.LRP_EINVAL
     assert ctx.get_param("tri_refine") == 0 and ctx.get_param("tri_refine_rounds") == 2
+    assert ctx.get_param("tri_refine_cluster") == 0
