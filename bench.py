@@ -46,7 +46,9 @@ TOL = 1e-8
 # DRAM bytes per system of the FP64 fine-solve kernel, from one ncu capture of
 # k_tri_cluster_wt<13, 3> (62 systems: 2.1978 MB read, 0 written)
 F64_DRAM_BYTES_PER_SYSTEM = 2.1978e6 / 62
-IRT_DRAM_BYTES_PER_SYSTEM = None      # the refined FP32 kernel: not yet captured
+# and of the refined FP32 fine-solve kernel k_tri_irt<16> (62 systems:
+# 2.1652 MB read, 0 written)
+IRT_DRAM_BYTES_PER_SYSTEM = 2.165248e6 / 62
 WORKLOAD = "adr1d n=4095 N=64 M=256 R=16 p=8 tol=1e-8"
 
 
