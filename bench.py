@@ -8,12 +8,13 @@ R = 16 with p = 8 oversampling, u0 = 5 seeded Gaussian bumps, f = 0.  A step
 builds the coarse solvers (randomized SVD: forward sketch, orthonormalisation,
 adjoint sketch, orthonormalisation, small SVD, lift) and runs one Parareal
 solve to the a posteriori tolerance 1e-8 (fine solves, coarse sweeps, bounds).
-The default arithmetic is the mixed mode (FP32 sketches, FP64 Parareal),
-with the fine backward-Euler steps computed from FP32 solves and one
-correction round per step whose residual is formed in pairs of FP32 numbers
-(--tri-refine 1: 2.7e-12 from the FP64 kernels' steps over an interval of
-256 steps); the same step is also timed with the fine solves on the FP64
-kernels (--tri-refine 0 times only that).
+The default arithmetic is the mixed mode (FP32 sketches, FP64 Parareal on
+the FP64 fine-solve kernels).  Beside it the line times the same step with
+the fine backward-Euler steps computed from FP32 solves and one correction
+round per step whose residual is formed in pairs of FP32 numbers
+(`fine_refined`; about 48-bit steps, 2.7e-12 from the FP64 kernels' steps
+over an interval of 256 steps); --tri-refine R times that variant as the
+headline instead.
 
 value: solves/s with inputs resident in HBM (device-timed with CUDA events on
 the library's stream).  e2e: the same through the C ABI with host buffers (the
@@ -105,9 +106,10 @@ def parse():
                     help="trisweep mode: chunk lengths (tri_wchunk) of the one-warp kernel")
     ap.add_argument("--sweep-refine", default="1,2",
                     help="trisweep: round counts of the refined FP32 fine solves to time ('' = none)")
-    ap.add_argument("--tri-refine", type=int, default=1, choices=[0, 1, 2, 3],
-                    help="1D fine solves from FP32 solves refined by pair residuals: rounds per step "
-                         "(0 = the FP64 kernels; the step is then also timed on them)")
+    ap.add_argument("--tri-refine", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="timed step's 1D fine solves from FP32 solves refined by pair residuals: "
+                         "rounds per step (0 = the FP64 kernels, the workload's precision; the other "
+                         "variant is timed beside it unless --headline-only)")
     ap.add_argument("--rates", default="10,30,100,300,1000")
     ap.add_argument("--serve-targets", default="",
                     help="serve mode: extra passes 'rate:adr1d_target_ms,...' with admission "
@@ -1121,10 +1123,13 @@ def main():
     ctx.set_kernel_timing(False)
     clk = clocks.stop()
     ms_step, value = aggregate_over_ranks(statistics.mean(ms), world, dev)
-    # ---- the same step with the fine solves on the FP64 kernels ---------------
+    # ---- the same step with the other fine solves: the refined FP32 steps
+    # (one pair-residual round) beside the FP64 kernels, or the reverse -------
     f64k = None
-    if args.tri_refine and not args.headline_only:
-        ctx.set_param("tri_refine", 0)
+    alt_rounds = 0 if args.tri_refine else 1
+    if not args.headline_only:
+        ctx.set_param("tri_refine", 1 if alt_rounds else 0)
+        ctx.set_param("tri_refine_rounds", max(alt_rounds, 1))
         out64 = torch.empty_like(out_d)
         for _ in range(max(2, args.warmup // 2)):
             step(op, u0_d, out64)
@@ -1145,12 +1150,15 @@ def main():
         barrier()
         kern64 = {f: ctx.kernel_time(f) for f in ("propagate_f64", "propagate_f32")}
         ctx.set_kernel_timing(False)
-        ctx.set_param("tri_refine", 1)
+        ctx.set_param("tri_refine", 1 if args.tri_refine else 0)
+        ctx.set_param("tri_refine_rounds", max(args.tri_refine, 1))
         ms64, value64 = aggregate_over_ranks(statistics.mean([a.elapsed_time(b) for a, b in ev64]),
                                              world, dev)
         f64k = {"solves_per_s": value64, "ms_per_step": ms64, "iterations": k64[-1],
-                "fine": "FP64 one-warp cluster kernels",
-                "roofline": fine_roofline(P, kern64, k64, ms64, args.steps, 0), "out": out64}
+                "fine": ("FP32 solves, one pair-residual correction round per step (k_tri_irt; "
+                         "about 48-bit steps, not the FP64 arithmetic of the workload)")
+                        if alt_rounds else "FP64 one-warp cluster kernels",
+                "roofline": fine_roofline(P, kern64, k64, ms64, args.steps, alt_rounds), "out": out64}
     if args.headline_only:
         extras = None
     else:
@@ -1197,7 +1205,7 @@ def main():
                 "fine_solves": ("FP32 solves, %d pair-residual correction round(s) per step "
                                 "(k_tri_irt)" % args.tri_refine) if args.tri_refine
                                else "FP64 one-warp cluster kernels",
-                "fine_f64_kernel": f64k,
+                ("fine_f64_kernel" if args.tri_refine else "fine_refined"): f64k,
                 **(extras or {"e2e": None}),
                 "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
                 "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu,
