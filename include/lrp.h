@@ -169,8 +169,9 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    bounded waits (LRP_ETIMEOUT); results are bitwise those
  *                    of 0 (default: the stencil reads global memory through
  *                    L1), and on GB300 it measured no faster;
- *   "tri_refine":    1 computes the FP64 backward-Euler steps of
- *                    time-invariant tridiagonal operators (n <= 4096,
+ *   "tri_refine":    1 computes the backward-Euler steps of FP64
+ *                    propagations of time-invariant tridiagonal operators
+ *                    to about 48 bits instead of in FP64 (n <= 4096,
  *                    forward, no source term) from FP32 solves: per step one
  *                    FP32 solve, then "tri_refine_rounds" corrections, each
  *                    the FP32 solve of the residual x_j - B y formed in pairs

@@ -298,9 +298,10 @@ void tri_toeplitz_coef(const Operator* op, double dt, int adjoint, int M, int m,
 // Time-dependent tridiagonal operators (tridiag_td.cu): one CTA per system,
 // parallel cyclic reduction of every step's own matrix; system s runs the
 // steps of interval (map ? map[2s+1] : in.interval0 + s / in.ncol).
-// FP64 backward-Euler steps of time-invariant tridiagonal operators (n <=
-// 4096, forward, no source) from FP32 solves, each step refined by residuals
-// in pairs of FP32 numbers (tridiag_ir.cu); applies when tri_refine = 1.
+// Backward-Euler steps of FP64 propagations of time-invariant tridiagonal
+// operators (n <= 4096, forward, no source) to about 48 bits from FP32
+// solves, each step refined by residuals in pairs of FP32 numbers
+// (tridiag_ir.cu); applies when tri_refine = 1.
 bool tri_ir_applies(Ctx* c, const Operator* op, int prec, int adjoint, int M, const PropIn& in,
                     const PropSrc& src);
 lrp_status tri_propagate_ir(Ctx* c, Operator* op, double dt, int M, int nsys, const PropIn& in,

@@ -1,5 +1,6 @@
-// FP64-accurate backward-Euler steps of time-invariant tridiagonal operators
-// from FP32 solves: every step (I + dt A) x_{j+1} = x_j is solved by
+// Near-FP64 backward-Euler steps (about 48 bits) of time-invariant
+// tridiagonal operators from FP32 solves, for FP64 propagations that opt in:
+// every step (I + dt A) x_{j+1} = x_j is solved by
 //   y = B^-1 x_j             (FP32, the right-hand side rounded to FP32),
 //   r = x_j - B y            (in pairs of FP32 numbers: products split
 //                             exactly by FMA, sums by two-sum, B held as
