@@ -71,7 +71,7 @@ def parse():
     ap.add_argument("--batch-per-grid", type=int, default=2,
                     help="batch mode: problems per grid size of the uneven 2D batch")
     ap.add_argument("--mode", default="solve",
-                    choices=["solve", "serve", "krylov", "batch", "cfg3", "trisweep", "exp3"],
+                    choices=["solve", "serve", "krylov", "batch", "cfg3", "trisweep", "exp3", "fp64probe"],
                     help="solve: the headline step; serve: Poisson request stream on resident "
                          "coarse solvers (p50/p99 latency per offered rate); krylov: bandwidth "
                          "of the 2D Krylov fine propagator (HBM GB/s fraction)")
@@ -948,6 +948,98 @@ def fine_roofline(P, kern, k_list, ms_step, steps, rounds):
                          "refined kernel holds one system per SM (62 of 152 SMs at 62 systems)"}
 
 
+# FP64 FMA issue probe: one CTA of w warps per SM, 8 independent FMA chains
+# per thread, `active` lanes of each warp computing (the others branch past
+# the loop); printed as one JSON list by the probe program
+FP64_PROBE_SRC = r"""
+#include <cstdio>
+#include <cuda_runtime.h>
+__global__ void k_fp64_fma(double* out, int iters, int active) {
+  const int lane = threadIdx.x & 31;
+  double a[8];
+  for (int c = 0; c < 8; ++c) a[c] = 1.0 + 1e-3 * (threadIdx.x + c);
+  const double x = 0.9999999, y = 1e-7;
+  if (lane < active) {
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) a[c] = fma(a[c], x, y);
+    }
+  }
+  double s = 0.0;
+  for (int c = 0; c < 8; ++c) s += a[c];
+  out[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+int main() {
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) return 1;
+  double* out = nullptr;
+  if (cudaMalloc(&out, (size_t)sms * 512 * sizeof(double)) != cudaSuccess) return 1;
+  const int iters = 1 << 15;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int ws[] = {1, 2, 3, 4, 5, 6, 8};
+  const int acts[] = {1, 8, 32};
+  printf("[");
+  bool first = true;
+  for (int w : ws)
+    for (int act : acts) {
+      k_fp64_fma<<<sms, 32 * w>>>(out, iters, act);
+      cudaEventRecord(e0);
+      k_fp64_fma<<<sms, 32 * w>>>(out, iters, act);
+      cudaEventRecord(e1);
+      if (cudaEventSynchronize(e1) != cudaSuccess) return 2;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      printf("%s{\"warps_per_sm\": %d, \"active_lanes\": %d, \"ms\": %.6f, \"sms\": %d, "
+             "\"warp_fma_per_sm\": %.1f}", first ? "" : ", ", w, act, ms, sms, 8.0 * iters * w);
+      first = false;
+    }
+  printf("]\n");
+  cudaFree(out);
+  return cudaGetLastError() == cudaSuccess ? 0 : 3;
+}
+"""
+
+
+def run_fp64probe(args):
+    """FP64 FMA issue rate of GB300 (the facts behind the FP64 roofline):
+    warps per SM 1..8 (one CTA per SM) with 1, 8 or 32 active lanes; per
+    case the FP64 warp instructions and lanes each SM retires per cycle at
+    the SM clock sampled during the probe.  Compiles the probe with nvcc."""
+    import tempfile
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    with tempfile.TemporaryDirectory() as td:
+        src = os.path.join(td, "probe.cu")
+        exe = os.path.join(td, "probe")
+        with open(src, "w") as f:
+            f.write(FP64_PROBE_SRC)
+        subprocess.run(["nvcc", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-o", exe, src],
+                       check=True)
+        clocks = ClockSampler(local)
+        clocks.start()
+        res = subprocess.run([exe], check=True, capture_output=True, text=True,
+                             env=dict(os.environ, CUDA_VISIBLE_DEVICES=str(local)))
+        clk = clocks.stop()
+    rows = json.loads(res.stdout)
+    mhz = clk.get("sm_mhz") or 2070.0
+    for r in rows:
+        cycles = r["ms"] * 1e-3 * mhz * 1e6
+        r["warp_fma_per_clk_per_sm"] = r["warp_fma_per_sm"] / cycles
+        r["lanes_per_clk_per_sm"] = r["warp_fma_per_clk_per_sm"] * r["active_lanes"]
+        r["cycles_per_warp_fma_per_subpartition"] = min(r["warps_per_sm"], 4) / r["warp_fma_per_clk_per_sm"]
+    full = [r for r in rows if r["active_lanes"] == 32]
+    best = max(full, key=lambda r: r["lanes_per_clk_per_sm"])
+    line = {"metric": "FP64 FMA lanes per clock per SM", "mode": "fp64probe", "n_gpus": 1,
+            "value": best["lanes_per_clk_per_sm"], "unit": "lanes/clk/SM", "higher_is_better": True,
+            "data": "synthetic", "clocks": clk,
+            "fp64_tflops_at_best": best["lanes_per_clk_per_sm"] * 2 * best["sms"] * mhz * 1e-6,
+            "table": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_trisweep(args):
     """CUDA-event time per launch of the FP64 fine-solve kernels on adr1d
     (n = 4095, 256 steps) over batch sizes and chunk lengths: the general
@@ -1039,6 +1131,9 @@ def main():
     rank, world, local = dist_env()
     if args.mode == "trisweep":
         run_trisweep(args)
+        return
+    if args.mode == "fp64probe":
+        run_fp64probe(args)
         return
     if args.mode == "exp3":
         run_exp3(args)
