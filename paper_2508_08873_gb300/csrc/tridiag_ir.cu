@@ -12,22 +12,27 @@
 // residuals) costs less FP32 issue than the single FP64 solve it replaces
 // costs FP64 issue.  Each round gains a factor of about u_32 kappa(B) on the
 // step's error; after R rounds the step error is about (u_32 kappa)^(R+1)
-// plus the pair rounding 2^-48 (measured on the adr1d operator, n = 4095,
-// 256 steps: 1e-12 relative with one round, 1e-13 with two).
+// plus the pair form of B, 2^-48, which enters every step alike (measured
+// on the adr1d operator, n = 4095, 256 steps: 2.7e-12 from the FP64 kernels'
+// result with one round, 1.4e-12 with two).
 //
-// One CTA of C warps per system, every warp 32 chunks of MM rows: the chunk
-// solve, local PCR and C x C super system of the one-warp kernels, with the
-// plan's FP32 factors, not deferred (each solve ends with its spike
-// correction).  The state, the refined iterate and the pair entries of B
-// live in shared memory (residuals read the neighbours' rows there), stored
-// chunk-transposed (row t MM + i at i W + t, W = 32 C chunks) so that the
-// lanes of a warp touch consecutive words.
+// One system per CTA of C warps (or, on request, per cluster of C one-warp
+// CTAs), every warp 32 chunks of MM rows: the chunk solve, local PCR and
+// C x C super system of the one-warp kernels, with the plan's FP32 factors,
+// not deferred (each solve ends with its spike correction).  Constant
+// coefficients (k_tri_irt): B's pair entries are three scalars and a lane's
+// state and iterate stay in its registers; the rows beside a chunk come from
+// the neighbouring lanes by shuffles and from the neighbouring warps through
+// shared memory.  Variable coefficients (k_tri_ir): the state, the iterate
+// and B's pair entries live in shared memory, stored chunk-transposed (row
+// t MM + i at i W + t, W = 32 C chunks) so that the lanes of a warp touch
+// consecutive words.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "common.cuh"
 #include "internal.h"
-#include <cooperative_groups.h>
-
 #include "tri_warp.cuh"
 
 namespace lrp {
