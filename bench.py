@@ -1220,40 +1220,40 @@ def main():
     ms_step, value = aggregate_over_ranks(statistics.mean(ms), world, dev)
     # ---- the same step with the other fine solves: the refined FP32 steps
     # (one pair-residual round) beside the FP64 kernels, or the reverse -------
-    f64k = None
+    alt = None
     alt_rounds = 0 if args.tri_refine else 1
     if not args.headline_only:
         ctx.set_param("tri_refine", 1 if alt_rounds else 0)
         ctx.set_param("tri_refine_rounds", max(alt_rounds, 1))
-        out64 = torch.empty_like(out_d)
+        out_alt = torch.empty_like(out_d)
         for _ in range(max(2, args.warmup // 2)):
-            step(op, u0_d, out64)
+            step(op, u0_d, out_alt)
         ctx.set_kernel_timing(True)
         ctx.reset_kernel_time()
         barrier()
-        ev64, k64 = [], []
+        ev_alt, k_alt = [], []
         for s in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            info64 = step(op, u0_d, out64)
+            info_alt = step(op, u0_d, out_alt)
             e1.record(stream)
-            ev64.append((e0, e1))
-            k64.append(info64["k_done"])
+            ev_alt.append((e0, e1))
+            k_alt.append(info_alt["k_done"])
         barrier()
-        kern64 = {f: ctx.kernel_time(f) for f in ("propagate_f64", "propagate_f32")}
+        kern_alt = {f: ctx.kernel_time(f) for f in ("propagate_f64", "propagate_f32")}
         ctx.set_kernel_timing(False)
         ctx.set_param("tri_refine", 1 if args.tri_refine else 0)
         ctx.set_param("tri_refine_rounds", max(args.tri_refine, 1))
-        ms64, value64 = aggregate_over_ranks(statistics.mean([a.elapsed_time(b) for a, b in ev64]),
+        ms_alt, value_alt = aggregate_over_ranks(statistics.mean([a.elapsed_time(b) for a, b in ev_alt]),
                                              world, dev)
-        f64k = {"solves_per_s": value64, "ms_per_step": ms64, "iterations": k64[-1],
+        alt = {"solves_per_s": value_alt, "ms_per_step": ms_alt, "iterations": k_alt[-1],
                 "fine": ("FP32 solves, one pair-residual correction round per step (k_tri_irt; "
                          "about 48-bit steps, not the FP64 arithmetic of the workload)")
                         if alt_rounds else "FP64 one-warp cluster kernels",
-                "roofline": fine_roofline(P, kern64, k64, ms64, args.steps, alt_rounds), "out": out64}
+                "roofline": fine_roofline(P, kern_alt, k_alt, ms_alt, args.steps, alt_rounds), "out": out_alt}
     if args.headline_only:
         extras = None
     else:
@@ -1277,8 +1277,8 @@ def main():
                 extras.pop("ts_out").cpu().numpy(), ref)
             extras["all_fp64"]["rel_err_vs_oracle"] = orc.rel_err(
                 extras["all_fp64"].pop("out").cpu().numpy(), ref)
-        if f64k is not None:
-            f64k["rel_err_vs_oracle"] = orc.rel_err(f64k.pop("out").cpu().numpy(), ref)
+        if alt is not None:
+            alt["rel_err_vs_oracle"] = orc.rel_err(alt.pop("out").cpu().numpy(), ref)
     # ---- roofline of the dominant kernel ---------------------------------------
     roof = fine_roofline(P, kern, k_list, ms_step, args.steps, args.tri_refine)
     kernels = {f: {"launches": v[0], "ms_total": v[1]} for f, v in kern.items()}
@@ -1300,7 +1300,7 @@ def main():
                 "fine_solves": ("FP32 solves, %d pair-residual correction round(s) per step "
                                 "(k_tri_irt)" % args.tri_refine) if args.tri_refine
                                else "FP64 one-warp cluster kernels",
-                ("fine_f64_kernel" if args.tri_refine else "fine_refined"): f64k,
+                ("fine_f64_kernel" if args.tri_refine else "fine_refined"): alt,
                 **(extras or {"e2e": None}),
                 "gpu_launches": launches, "gpu_launches_per_step": launches / args.steps,
                 "roofline": roof, "kernels": kernels, "clocks": clk, "cpu_baseline": cpu,
