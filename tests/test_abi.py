@@ -48,3 +48,18 @@ def test_create_fails_cleanly_without_device():
     from paper_2508_08873_gb300 import _native, api
     with pytest.raises(_native.LrpError):
         api.Context(0)
+
+
+def test_every_parameter_is_documented_and_readable():
+    """Every name lrp_set_param accepts is documented in include/lrp.h and
+    readable back through lrp_get_param."""
+    api = open(os.path.join(ROOT, "paper_2508_08873_gb300", "csrc", "api.cu")).read()
+    i = api.index("lrp_status lrp_set_param")
+    j = api.index("lrp_status lrp_get_param")
+    k = api.index("\n}\n", j)
+    set_names = set(re.findall(r'k == "([a-z0-9_]+)"', api[i:j]))
+    get_names = set(re.findall(r'k == "([a-z0-9_]+)"', api[j:k]))
+    header = open(os.path.join(ROOT, "include", "lrp.h")).read()
+    assert {"tri_refine", "tri_refine_rounds", "tri_refine_cluster", "krylov_refine"} <= set_names
+    assert not [n for n in set_names | get_names if '"%s"' % n not in header]
+    assert set_names <= get_names, set_names - get_names
