@@ -182,6 +182,11 @@ long lrp_launch_count(lrp_ctx* ctx);
  *                    steps of the adr1d operator (n = 4095) they differ by
  *                    2.7e-12 relative with one round, 1.4e-12 with two
  *                    (the 48-bit pair form of B enters every step alike).
+ *                    Each round gains about u_32 kappa(B) on a step's error
+ *                    and no residual test follows the last round, so it is
+ *                    meant for well-conditioned steps, such as the
+ *                    diagonally dominant backward-Euler matrices of
+ *                    diffusion-advection-reaction operators.
  *                    0 (default) keeps the FP64 kernels;
  *   "tri_refine_rounds": correction rounds per step of tri_refine (1..3,
  *                    default 2);
